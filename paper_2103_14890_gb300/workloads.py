@@ -1,0 +1,148 @@
+"""Seeded synthetic inputs for the collision operator and the IMEX step.
+
+This module only synthesises input data (sums of Gaussians sampled on the
+velocity grid, noise, a seeded triangulation).  It holds none of the
+operator's arithmetic: no transforms, no kernel modes, no moments.  Both the
+CUDA path and the CPU oracle consume what it returns.
+
+The recipes follow the paper's workloads (2-D velocity grids of 16^2/32^2
+points on boxes [-8,8]^2 and [-10,10]^2, Maxwell-molecule and hard-sphere
+kernels, the states of the explosion problem of Sec. 4.2) and are the ones
+the benchmark and the parity tests use.
+"""
+import math
+
+import numpy as np
+
+POLYTROPIC_GAMMA = 2.0   # gas polytropic index used for Mach numbers (Sec. 4)
+
+
+def velocity_nodes(N, L):
+    """Periodic grid v_j = -L + j * 2L/N, j = 0..N-1."""
+    return -L + (2.0 * L / N) * np.arange(N)
+
+
+def _gaussian(dim, N, L, rho, u, theta):
+    """rho (2 pi theta)^(-d/2) exp(-|v-u|^2 / (2 theta)) on the grid; rho, theta
+    of shape (n,), u of shape (n, d).  Returns (n, N^d) float64."""
+    v = velocity_nodes(N, L)
+    n = len(rho)
+    r2 = np.zeros((n,) + (N,) * dim)
+    for i in range(dim):
+        shape = [1] * (dim + 1)
+        shape[i + 1] = N
+        vi = v.reshape(shape)
+        r2 = r2 + (vi - u[:, i].reshape((n,) + (1,) * dim)) ** 2
+    th = theta.reshape((n,) + (1,) * dim)
+    out = rho.reshape((n,) + (1,) * dim) / (2.0 * math.pi * th) ** (dim / 2.0) * np.exp(-r2 / (2.0 * th))
+    return out.reshape(n, N ** dim)
+
+
+def bi_maxwellian(n_cells, dim, N, L, seed, noise=0.0):
+    """Each cell: sum of two Gaussians with density U[0.5,2], mean velocity
+    U[-1,1]^d and temperature U[0.5,1.5]; optionally times (1 + noise*xi),
+    xi ~ U[-1,1] per grid point (multiplicative, so f stays >= 0)."""
+    rng = np.random.default_rng(seed)
+    f = np.zeros((n_cells, N ** dim))
+    for _ in range(2):
+        rho = rng.uniform(0.5, 2.0, n_cells)
+        u = rng.uniform(-1.0, 1.0, (n_cells, dim))
+        th = rng.uniform(0.5, 1.5, n_cells)
+        f += _gaussian(dim, N, L, rho, u, th)
+    if noise:
+        f *= 1.0 + noise * rng.uniform(-1.0, 1.0, f.shape)
+    return f
+
+
+def shifted_maxwellians(n_cells, dim, N, L, seed, mach_max=3.0):
+    """Each cell: two Gaussians, each drifting at Mach U[0, mach_max] (sound
+    speed sqrt(gamma theta), gamma = 2) in a uniform random direction, with
+    temperature U[0.5,1.5] and density U[0.5,2]."""
+    rng = np.random.default_rng(seed)
+    f = np.zeros((n_cells, N ** dim))
+    for _ in range(2):
+        rho = rng.uniform(0.5, 2.0, n_cells)
+        th = rng.uniform(0.5, 1.5, n_cells)
+        mach = rng.uniform(0.0, mach_max, n_cells)
+        direc = rng.normal(size=(n_cells, dim))
+        direc /= np.linalg.norm(direc, axis=1, keepdims=True)
+        u = direc * (mach * np.sqrt(POLYTROPIC_GAMMA * th))[:, None]
+        f += _gaussian(dim, N, L, rho, u, th)
+    return f
+
+
+def single_maxwellian(n_cells, dim, N, L, seed):
+    """Near-equilibrium cells: one Gaussian per cell (same parameter ranges)."""
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.5, 2.0, n_cells)
+    u = rng.uniform(-1.0, 1.0, (n_cells, dim))
+    th = rng.uniform(0.5, 1.5, n_cells)
+    return _gaussian(dim, N, L, rho, u, th)
+
+
+def bkw_initial(N, L, t=0.0):
+    """The 2-D BKW profile of Sec. 4.1 at time t (closed form, used as data)."""
+    v = velocity_nodes(N, L)
+    V1, V2 = np.meshgrid(v, v, indexing="ij")
+    r2 = V1 ** 2 + V2 ** 2
+    S = 1.0 - math.exp(-t / 8.0) / 2.0
+    f = np.exp(-r2 / (2 * S)) / (2 * math.pi * S ** 2) * (2 * S - 1 + (1 - S) / (2 * S) * r2)
+    return f.reshape(1, N * N)
+
+
+def sod_mesh(n_side=100, seed=1004, jitter=0.3):
+    """Jittered n_side x n_side lattice in [0,1]^2, triangulated.  Returns the
+    triangle centroids (n_tri, 2) and the mesh size h = sqrt(mean area).
+    Uses scipy's Delaunay when available, else the structured diagonal split."""
+    rng = np.random.default_rng(seed)
+    hs = 1.0 / (n_side - 1)
+    g = np.linspace(0.0, 1.0, n_side)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    X = X + rng.uniform(-jitter, jitter, X.shape) * hs
+    Y = Y + rng.uniform(-jitter, jitter, Y.shape) * hs
+    X = np.clip(X, 0.0, 1.0)
+    Y = np.clip(Y, 0.0, 1.0)
+    pts = np.stack([X.ravel(), Y.ravel()], axis=1)
+    try:
+        from scipy.spatial import Delaunay
+        tri = Delaunay(pts).simplices
+    except Exception:  # structured split of every lattice square into two triangles
+        idx = np.arange(n_side * n_side).reshape(n_side, n_side)
+        a = idx[:-1, :-1].ravel(); b = idx[1:, :-1].ravel()
+        c = idx[:-1, 1:].ravel(); d = idx[1:, 1:].ravel()
+        tri = np.concatenate([np.stack([a, b, d], 1), np.stack([a, d, c], 1)])
+    P = pts[tri]
+    cent = P.mean(axis=1)
+    area = 0.5 * np.abs((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1])
+                        - (P[:, 2, 0] - P[:, 0, 0]) * (P[:, 1, 1] - P[:, 0, 1]))
+    return cent, float(np.sqrt(area.mean()))
+
+
+def sod_cells(N, L, n_side=100, seed=1004):
+    """Cell data of the density/temperature jump across x = 0.5 (the states of
+    the explosion problem of Sec. 4.2): (rho, u, theta) = (1, 0, 1) left and
+    (0.125, 0, 0.8) right, as Gaussians on the velocity grid."""
+    cent, h = sod_mesh(n_side, seed)
+    left = cent[:, 0] < 0.5
+    n = len(cent)
+    rho = np.where(left, 1.0, 0.125)
+    th = np.where(left, 1.0, 0.8)
+    u = np.zeros((n, 2))
+    return _gaussian(2, N, L, rho, u, th), h
+
+
+def grouped_instances(seed=1005, L=10.0):
+    """Heterogeneous batch: 8 instances with cell counts log-uniform in
+    [1e3, 5e4] and N drawn from {16, 24, 32, 48} (each at least once), plus
+    two 3-D 16^3 instances of 1000 cells.  Returns a list of dicts with
+    dim, N, L, n_cells, seed (inputs are drawn per instance with bi_maxwellian)."""
+    rng = np.random.default_rng(seed)
+    Ns = [16, 24, 32, 48] + list(rng.choice([16, 24, 32, 48], size=4))
+    rng.shuffle(Ns)
+    out = []
+    for i, N in enumerate(Ns):
+        cells = int(round(math.exp(rng.uniform(math.log(1e3), math.log(5e4)))))
+        out.append(dict(dim=2, N=int(N), L=L, n_cells=cells, seed=seed * 100 + i))
+    for i in range(2):
+        out.append(dict(dim=3, N=16, L=L, n_cells=1000, seed=seed * 100 + 8 + i))
+    return out
