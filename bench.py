@@ -1,0 +1,295 @@
+"""Benchmark: cell-collision evaluations per second of the spectral Boltzmann
+collision operator on one GB300 (or N, one process per GPU, weak scaling).
+
+Workload (default): 65536 independent cells, 2-D velocity grid 32x32 on
+[-10,10]^2, hard-sphere (VHS) kernel, each cell two shifted Maxwellians with
+Mach 0-3 drift.  One step = one collide_batch over all cells (forward DFT,
+mode sum, inverse DFT).  Inputs (268 MB) and outputs exceed the 129 MB L2, so
+no L2 flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead, on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_V, L_BOX, GAMMA = 32, 10.0, 1.0
+CELLS = 65536
+SEED = 1003
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+METRIC = "cell-collision evals/s at N_v=32^2: mixed-precision vs FP64 GPU, rel-L2 err stated"
+WORKLOAD = "65536 cells, 2-D 32x32 velocity grid on [-10,10]^2, VHS kernel, shifted Maxwellians Mach 0-3"
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(f_sample, budget_s=15.0):
+    """Time the FP64 oracle on the host cores on a bounded sample of cells."""
+    import numpy as np
+    import oracle
+    k = oracle.Kernel(2, N_V, L_BOX, GAMMA)
+    probe = f_sample[:8].astype(np.float64)
+    t0 = time.perf_counter()
+    k.collide(probe)
+    per_cell = (time.perf_counter() - t0) / len(probe)
+    n = int(max(8, min(len(f_sample), budget_s / max(per_cell, 1e-6))))
+    sample = f_sample[:n].astype(np.float64)
+    t0 = time.perf_counter()
+    k.collide(sample)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "cell-collision evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d of the %d cells (FP64 direct sum, OpenMP over cells)" % (n, CELLS)}, k
+
+
+def reference_arm(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from paper_2103_14890_gb300 import workloads
+    f = workloads.shifted_maxwellians(4096, 2, N_V, L_BOX, seed=SEED)
+    base, k = cpu_baseline(f, budget_s=4.0)
+    per_step = max(8, int(base["value"] * 4.0))
+    per_step = min(per_step, len(f))
+    sample = f[:per_step]
+    for _ in range(args.warmup):
+        k.collide(sample[:8])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        k.collide(sample)
+    el = time.perf_counter() - t0
+    value = per_step * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-collision evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (bounded sample per step: %d cells)" % per_step},
+            "cpu_baseline": {"value": value, "unit": "cell-collision evals/s", "cores": base["cores"],
+                             "kind": "oracle", "sample": "%d cells per step" % per_step},
+            "e2e": {"value": value, "unit": "cell-collision evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+    rank, world, local = _env_rank()
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2103_14890_gb300 import binding as bz, build as bzbuild, workloads
+    bzbuild.build()
+    bz.load()
+
+    grid = bz.Grid(2, N_V, L_BOX)
+    modes = bz.Modes(grid, GAMMA)
+    f_host = workloads.shifted_maxwellians(CELLS, 2, N_V, L_BOX, seed=SEED + rank).astype(np.float32)
+    f = torch.from_numpy(f_host).cuda()
+    Q = torch.empty_like(f)
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    def step():
+        bz.collide_batch(modes, f, Q, precision="fp32")
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    bz.check()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    bz.profile(True)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = bz.profile_read()
+    bz.profile(False)
+    clk = clocks.stop()
+    bz.check()
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = CELLS * world / (ms / 1e3)
+
+    # dominant kernel: the mode sum
+    ms_name = "modesum_f32" if "modesum_f32" in prof else "modesum_f32_generic"
+    launches, ktot = prof.get(ms_name, (0, float("nan")))
+    k_ms = ktot / max(1, launches)
+    flops_launch = 10.0 * modes.pairs_sym * CELLS
+    achieved = flops_launch / (k_ms / 1e3) / 1e12
+    gpu_launches = sum(c for c, _ in prof.values())
+
+    # FP64 plain form on the same workload
+    Q64 = torch.empty((CELLS, N_V * N_V), dtype=torch.float64, device="cuda")
+    f64 = f.double()
+    bz.collide_batch(modes, f64, Q64, precision="fp64")
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.fp64_steps):
+        bz.collide_batch(modes, f64, Q64, precision="fp64")
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / args.fp64_steps
+    value64 = CELLS * world / (ms64 / 1e3)
+
+    # end to end: pinned host f -> device, collide, device -> pinned host Q
+    fh = torch.from_numpy(f_host).pin_memory()
+    qh = torch.empty_like(fh).pin_memory()
+    fd = torch.empty_like(f)
+    qd = torch.empty_like(f)
+    for _ in range(2):
+        fd.copy_(fh, non_blocking=True)
+        bz.collide_batch(modes, fd, qd, precision="fp32")
+        qh.copy_(qd, non_blocking=True)
+    barrier()
+    t0 = time.perf_counter()
+    e0.record(st)
+    for _ in range(args.steps):
+        fd.copy_(fh, non_blocking=True)
+        bz.collide_batch(modes, fd, qd, precision="fp32")
+        qh.copy_(qd, non_blocking=True)
+    e1.record(st)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_val = CELLS * world / (e2e_ms / 1e3)
+
+    line = None
+    if rank == 0:
+        # errors against the FP64 oracle on sampled cells (same FP32 inputs)
+        import oracle
+        idx = np.linspace(0, CELLS - 1, 24).astype(int)
+        fs = f_host[idx].astype(np.float64)
+        k = oracle.Kernel(2, N_V, L_BOX, GAMMA)
+        Qr = k.collide(fs)
+        q32 = Q[idx].double().cpu().numpy()
+        q64 = Q64[idx].cpu().numpy()
+        err32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(Qr))
+        err64 = float(np.linalg.norm(q64 - Qr) / np.linalg.norm(Qr))
+        rho = fs.sum(1, keepdims=True) * k.dv ** 2
+        loss32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(rho * fs))   # error / |loss rate ~ rho f|
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu, _ = cpu_baseline(f_host[:4096], budget_s=15.0)
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-collision evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells_per_gpu": CELLS, "N_v": N_V * N_V, "L": L_BOX,
+                       "kernel": "VHS hard spheres (gamma=1, b0=1/(2pi))", "precision_form": "fp32",
+                       "l2": "inputs and outputs (268 MB each) exceed L2: no flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "rel_l2_err": {"fp32_vs_oracle": err32, "fp64_vs_oracle": err64, "fp32_loss_scaled": loss32,
+                           "sample_cells": len(idx)},
+            "fp64_form": {"value": value64, "unit": "cell-collision evals/s", "ms_per_step": ms64,
+                          "speedup_fp32_over_fp64": value / value64},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": ms_name,
+                         "kernel_ms": k_ms, "flops_per_launch": flops_launch,
+                         "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+            "kernel_times_ms": {k2: v[1] / max(1, v[0]) for k2, v in prof.items()},
+            "gpu_launches": gpu_launches,
+            "e2e": {"value": e2e_val, "unit": "cell-collision evals/s",
+                    "h2d_bytes_per_step": int(f.numel() * 4), "d2h_bytes_per_step": int(Q.numel() * 4)},
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist:
+        tdist.barrier()
+        tdist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

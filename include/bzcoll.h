@@ -1,0 +1,195 @@
+/*
+ * bzcoll.h -- C ABI of the GB300 spectral Boltzmann collision library.
+ *
+ * The library evaluates the Fourier-spectral Boltzmann collision operator of
+ * Boscheri & Dimarco, "High order finite volume schemes with IMEX time
+ * stepping for the Boltzmann model on unstructured meshes" (arXiv 2103.14890),
+ * Sec. 3.3, independently in every mesh cell, and the cell-local part of the
+ * penalised IMEX Runge-Kutta stage of Sec. 3.4.  Every step runs in
+ * hand-written CUDA kernels for sm_103a; there is no CPU fallback.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ *  - Velocity grid (Sec. 3.1, eq. disc_space, with the periodic box of
+ *    Sec. 3.3): d in {2,3} dimensions, N (even) points per dimension on
+ *    [-L,L]^d, dv = 2L/N, v_j = -L + j dv.  The computational box is
+ *    u = v/s in [-pi,pi)^d with s = L/pi.
+ *  - Retained Fourier modes: K_h = {-h..h}^d, h = N/2 - 1 (the Nyquist mode
+ *    is dropped, so the operator conserves mass exactly and Q is real).
+ *  - Distribution arrays (f, Q, stage buffers) are caller-owned DEVICE
+ *    pointers, laid out [n_cells][N^d], contiguous, velocity index row-major
+ *    (j_1 slowest).  Element type: double for BZ_FP64, float for the mixed
+ *    forms.  The physical Q is returned (the 1/eps Knudsen factor is not
+ *    applied).
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Calls are asynchronous on that stream.  Errors found on
+ *    the host are returned at once; errors found by a kernel (non-finite input
+ *    under BZ_CHECK_INPUT, a wait that ran out) are latched in a device error
+ *    word and returned by bz_check().
+ *  - Ownership: handles (bz_grid, bz_modes) and all device tables behind them
+ *    are owned by the library and released by the destroy functions.  Scratch
+ *    needed by a call is taken from a library-owned stream-ordered memory pool
+ *    on the caller's stream and returned on that stream before the call
+ *    returns; after the first call of a given size no new device memory is
+ *    requested.
+ *  - Return codes: 0 on success, a negative BZ_E* code on failure; the
+ *    thread-local message is available from bz_last_error().  No C++
+ *    exception crosses this boundary.
+ */
+#ifndef BZCOLL_H
+#define BZCOLL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ codes --- */
+#define BZ_OK          0
+#define BZ_EINVAL     -1   /* bad argument (size, pointer, enum, handle) */
+#define BZ_ENOMEM     -2   /* device or host allocation failed */
+#define BZ_ECUDA      -3   /* a CUDA runtime call failed */
+#define BZ_ENOTSUP    -4   /* configuration not supported in this precision */
+#define BZ_ETIMEOUT   -5   /* a kernel wait gave up (device error word) */
+#define BZ_ENONFINITE -6   /* non-finite input seen under BZ_CHECK_INPUT */
+
+/* Precision forms of the operator.
+ *   BZ_FP64   : every step in FP64 (the plain form).
+ *   BZ_FP32   : DFTs and the mode sum in FP32 with compensated accumulation
+ *               of the mode sum; moments, Maxwellian and the conservation
+ *               fix in FP64.
+ *   BZ_FP32X2 : as BZ_FP32, with the Fourier coefficients carried as
+ *               unevaluated FP32 pairs (hi + lo) through the DFTs and the
+ *               mode sum (first-order correction), for FP64-like accuracy at
+ *               FP32-pipe speed. */
+#define BZ_FP64    0
+#define BZ_FP32    1
+#define BZ_FP32X2  2
+
+/* flags */
+#define BZ_CONSERVE     1  /* project Q so its discrete moments of 1, v, |v|^2 vanish */
+#define BZ_CHECK_INPUT  2  /* flag non-finite f in the device error word */
+
+/* IMEX schemes (Sec. 3.4) and collision models */
+#define BZ_ARS222   0      /* ARS(2,2,2), 3 stages, 2nd order */
+#define BZ_BPR343   1      /* BPR(3,4,3), 5 stages, 3rd order */
+#define BZ_BOLTZMANN 0     /* explicit G = Q - BGK, implicit BGK penalty */
+#define BZ_BGK       1     /* BGK relaxation only (G = 0) */
+
+typedef struct bz_grid bz_grid;    /* opaque, library-owned */
+typedef struct bz_modes bz_modes;  /* opaque, library-owned */
+
+/* init_velocity_grid -- Sec. 3.1 (eq. disc_space) and Sec. 3.3 (periodic box,
+ * eq. FU / eq. FC).  Builds the velocity grid, the 1-D DFT factors
+ * (-1)^k e^{-2 pi i k j/N} for k in K_h in FP64 and FP32 and uploads them to
+ * the current CUDA device.
+ *   dim          : 2 or 3
+ *   n_per_dim    : N, even, 4 <= N <= 64 (2-D) or 4 <= N <= 16 (3-D)
+ *   half_width_L : L > 0
+ *   out          : receives the handle (NULL on failure)
+ * Errors: BZ_EINVAL (bad sizes, out == NULL), BZ_ENOMEM, BZ_ECUDA. */
+int init_velocity_grid(int dim, int n_per_dim, double half_width_L, bz_grid **out);
+
+/* build_kernel_modes -- Sec. 3.3, eq. KM and eq. CF1.  Computes on the host, in
+ * FP64, the kernel modes B-hat(l,m) for |q| sigma = b0 |q|^gamma by
+ * Gauss-Legendre quadrature of the Bessel (2-D) / sinc (3-D) reduced radial
+ * integral over |q| <= 2 lambda pi, lambda = 2/(3+sqrt 2), and the weights
+ * beta-hat(l,m) = B-hat(l,m) - B-hat(m,m) of the mode sum; uploads FP64 and
+ * FP32 copies (plus the symmetrised weight tiles of the FP32 kernels).
+ *   g          : grid handle (not consumed; must outlive the modes handle)
+ *   gamma      : 0 = Maxwell molecules, 1 = hard spheres (VHS); 0 <= gamma <= 2
+ *   b0         : kernel constant; <= 0 selects 1/(2 pi) in 2-D, 1/(4 pi) in 3-D
+ *   quad_nodes : Gauss-Legendre nodes; 0 = automatic (resolves the fastest
+ *                oscillation of the integrand for this grid)
+ *   out        : receives the handle
+ * Errors: BZ_EINVAL, BZ_ENOMEM, BZ_ECUDA. */
+int build_kernel_modes(const bz_grid *g, double gamma, double b0, int quad_nodes,
+                       bz_modes **out);
+
+/* collide_batch -- one evaluation of Q(f,f) in each of n_cells independent
+ * cells (Sec. 3.3: forward DFT, the weighted sum of eq. CF1 over l + m = k in
+ * K_h, inverse DFT, times s^(d+gamma) to return to physical units; with
+ * BZ_CONSERVE, the smallest L2 correction that zeroes the discrete moments of
+ * 1, v, |v|^2).
+ *   m         : modes handle
+ *   precision : BZ_FP64 (f, Q are double) or BZ_FP32 / BZ_FP32X2 (float)
+ *   flags     : BZ_CONSERVE | BZ_CHECK_INPUT
+ *   f, Q      : device arrays [n_cells][N^d]; may not overlap
+ *   n_cells   : >= 0 (0 is a no-op)
+ * Errors: BZ_EINVAL, BZ_ENOTSUP, BZ_ENOMEM, BZ_ECUDA; device-side
+ * BZ_ENONFINITE via bz_check(). */
+int collide_batch(const bz_modes *m, int precision, int flags, const void *f, void *Q,
+                  int64_t n_cells, void *stream);
+
+/* imex_stage_local -- stage l (1-based) of the penalised IMEX Runge-Kutta step
+ * of Sec. 3.4 (eq. Bref2: Q = G_P + Q_BGK with G_P explicit and the BGK
+ * operator nu (M - f), nu = rho, implicit), cell by cell:
+ *   R_l = f^n + dt sum_{m<l} [ At_lm (G_m/eps - L_m) + A_lm P_m/eps ]
+ *   U_l = moments(R_l), nu_l = rho_l, M_l = Maxwellian(U_l)       (FP64)
+ *   F_l = (R_l + dt A_ll (nu_l/eps) M_l) / (1 + dt A_ll nu_l/eps)
+ *   P_l = nu_l (M_l - F_l),  G_l = Q(F_l) - P_l  (G_l = 0 for BZ_BGK or when no
+ *   later stage uses it).
+ *   scheme      : BZ_ARS222 or BZ_BPR343 (tableaux of Sec. 3.4)
+ *   stage       : 1 .. stages(scheme)
+ *   model       : BZ_BOLTZMANN or BZ_BGK
+ *   dt, eps     : time step and Knudsen number (> 0)
+ *   f_n         : device [n_cells][N^d]
+ *   F, G, P     : device [stages][n_cells][N^d]; slots m < l are read, slot l
+ *                 is written (F_l, G_l, P_l)
+ *   L_res       : device [stages][n_cells][N^d] transport residuals or NULL (= 0)
+ * Element type follows `precision` as for collide_batch.
+ * Errors: as collide_batch. */
+int imex_stage_local(const bz_modes *m, int scheme, int stage, int model, double dt,
+                     double eps, const void *f_n, void *F, void *G, void *P,
+                     const void *L_res, int64_t n_cells, int precision, int flags,
+                     void *stream);
+
+/* imex_step -- all stages of one IMEX step (the schemes are stiffly accurate,
+ * so f^{n+1} is the last stage value): f_out = step(f_n).  Stage buffers are
+ * library scratch.  L_res as above (NULL = homogeneous step).
+ * Errors: as collide_batch. */
+int imex_step(const bz_modes *m, int scheme, int model, double dt, double eps,
+              const void *f_n, void *f_out, const void *L_res, int64_t n_cells,
+              int precision, int flags, void *stream);
+
+/* bz_check -- synchronise `stream`, read and clear the device error word.
+ * Returns BZ_OK, BZ_ENONFINITE, BZ_ETIMEOUT or BZ_ECUDA. */
+int bz_check(void *stream);
+
+/* bz_last_error -- message of the last failing call on this thread ("" if none). */
+const char *bz_last_error(void);
+
+/* bz_modes_info -- sizes of a modes handle: out[0] = dim, out[1] = N,
+ * out[2] = h, out[3] = N^d, out[4] = half-spectrum modes (h+1) (2h+1)^(d-1),
+ * out[5] = Gauss-Legendre nodes used, out[6] = unordered mode pairs summed
+ * per cell by the symmetric FP32 kernel (algorithmic work unit). */
+int bz_modes_info(const bz_modes *m, int64_t out[8]);
+
+/* bz_modes_beta -- copy beta-hat(l,m) for l, m in K_h (row-major flat mode
+ * indices, (2h+1)^d each) into host memory `out` ((2h+1)^(2d) doubles); entries
+ * with l + m outside K_h are 0. For testing the FP64 quadrature. */
+int bz_modes_beta(const bz_modes *m, double *out);
+
+/* bz_profile -- per-kernel timing for measurement (tracing).  enable = 1
+ * clears the record and brackets every kernel the library launches from then
+ * on with a pair of CUDA events recorded on the launching stream; enable = 0
+ * stops recording.  Not for use during CUDA graph capture.
+ * Errors: BZ_ECUDA if events cannot be created. */
+int bz_profile(int enable);
+
+/* bz_profile_read -- synchronise on the recorded events and report, per kernel
+ * name, the number of launches and their total device time in milliseconds.
+ * names: max_kernels slots of 64 bytes (NUL-terminated names); total_ms and
+ * launches: max_kernels entries.  Returns the number of kernels written (>= 0)
+ * or a negative BZ_E* code.  The record is cleared. */
+int bz_profile_read(char *names, int names_bytes, double *total_ms, int64_t *launches,
+                    int max_kernels);
+
+void bz_grid_destroy(bz_grid *g);
+void bz_modes_destroy(bz_modes *m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

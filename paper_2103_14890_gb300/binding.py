@@ -1,0 +1,214 @@
+"""Thin ctypes binding of libbzcoll.so (C ABI in include/bzcoll.h).
+
+Argument marshalling only: every step of the operator runs in the library's
+CUDA kernels.  Device arrays are torch CUDA tensors (contiguous, float64 for
+``"fp64"``, float32 for ``"fp32"`` / ``"fp32x2"``); streams default to torch's
+current stream.  There is no CPU fallback: if the library is missing or
+cannot be loaded, every call raises.
+"""
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB_PATH = os.path.join(HERE, "libbzcoll.so")
+HEADER = os.path.join(ROOT, "include", "bzcoll.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTSUP, ETIMEOUT, ENONFINITE = 0, -1, -2, -3, -4, -5, -6
+PRECISION = {"fp64": 0, "fp32": 1, "fp32x2": 2}
+CONSERVE, CHECK_INPUT = 1, 2
+SCHEME = {"ars222": 0, "bpr343": 1}
+STAGES = {"ars222": 3, "bpr343": 5}
+MODEL = {"boltzmann": 0, "bgk": 1}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BzError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("bzcoll error %d: %s" % (code, msg))
+        self.code = code
+
+
+def header_functions():
+    """Names of the functions declared in include/bzcoll.h."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", src)) - {"defined"})
+
+
+def load(path=None):
+    """Load the library (raises if it is absent: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise BzError(ECUDA, "libbzcoll.so not built (%s); run __graft_entry__.build()" % p)
+        lib = ctypes.CDLL(p)
+        c_i, c_d, c_p, c_i64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "init_velocity_grid": ([c_i, c_i, c_d, pp], c_i),
+            "build_kernel_modes": ([c_p, c_d, c_d, c_i, pp], c_i),
+            "collide_batch": ([c_p, c_i, c_i, c_p, c_p, c_i64, c_p], c_i),
+            "imex_stage_local": ([c_p, c_i, c_i, c_i, c_d, c_d, c_p, c_p, c_p, c_p, c_p, c_i64, c_i, c_i, c_p], c_i),
+            "imex_step": ([c_p, c_i, c_i, c_d, c_d, c_p, c_p, c_p, c_i64, c_i, c_i, c_p], c_i),
+            "bz_check": ([c_p], c_i),
+            "bz_last_error": ([], ctypes.c_char_p),
+            "bz_modes_info": ([c_p, ctypes.POINTER(c_i64)], c_i),
+            "bz_modes_beta": ([c_p, c_p], c_i),
+            "bz_grid_destroy": ([c_p], None),
+            "bz_modes_destroy": ([c_p], None),
+            "bz_profile": ([c_i], c_i),
+            "bz_profile_read": ([c_p, c_i, c_p, c_p, c_i], c_i),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise BzError(rc, load().bz_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dptr(t, dtype, what):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (what, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype(precision):
+    import torch
+    return torch.float64 if precision == "fp64" else torch.float32
+
+
+class Grid:
+    """Velocity grid (init_velocity_grid): d, N points per dimension, [-L, L]^d."""
+
+    def __init__(self, dim, N, L):
+        h = ctypes.c_void_p()
+        _check(load().init_velocity_grid(int(dim), int(N), float(L), ctypes.byref(h)))
+        self._h = h
+        self.dim, self.N, self.L = dim, N, L
+        self.nv = N ** dim
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.bz_grid_destroy(self._h)
+            self._h = None
+
+
+class Modes:
+    """Kernel modes (build_kernel_modes) of B = b0 |q|^gamma on a grid."""
+
+    def __init__(self, grid, gamma, b0=0.0, quad_nodes=0):
+        h = ctypes.c_void_p()
+        _check(load().build_kernel_modes(grid._h, float(gamma), float(b0), int(quad_nodes), ctypes.byref(h)))
+        self._h = h
+        self.grid = grid              # keep the grid alive
+        self.gamma = gamma
+        info = (ctypes.c_int64 * 8)()
+        _check(load().bz_modes_info(h, info))
+        self.dim, self.N, self.h, self.nv, self.nhalf, self.nq, self.pairs_sym, self.fast32 = list(info)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.bz_modes_destroy(self._h)
+            self._h = None
+
+    def beta_table(self):
+        import numpy as np
+        nm = (2 * self.h + 1) ** self.dim
+        out = np.zeros((nm, nm))
+        _check(load().bz_modes_beta(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+
+def collide_batch(modes, f, Q=None, precision="fp32", conserve=False, check_input=False, stream=None):
+    """Q(f) for f of shape (n_cells, N^d) on the device."""
+    import torch
+    dt = _dtype(precision)
+    if Q is None:
+        Q = torch.empty_like(f)
+    flags = (CONSERVE if conserve else 0) | (CHECK_INPUT if check_input else 0)
+    n = f.shape[0] if f.dim() > 1 else 1
+    if f.numel() != n * modes.nv:
+        raise ValueError("f must have n_cells * N^d elements")
+    _check(load().collide_batch(modes._h, PRECISION[precision], flags, _dptr(f, dt, "f"), _dptr(Q, dt, "Q"),
+                                n, _stream(stream)))
+    return Q
+
+
+def imex_stage_local(modes, stage, f_n, F, G, P, dt, eps, scheme="ars222", model="boltzmann",
+                     L_res=None, precision="fp32", conserve=False, check_input=False, stream=None):
+    """Stage `stage` (1-based); F, G, P of shape (stages, n_cells, N^d)."""
+    ty = _dtype(precision)
+    n = f_n.shape[0]
+    flags = (CONSERVE if conserve else 0) | (CHECK_INPUT if check_input else 0)
+    _check(load().imex_stage_local(modes._h, SCHEME[scheme], int(stage), MODEL[model], float(dt), float(eps),
+                                   _dptr(f_n, ty, "f_n"), _dptr(F, ty, "F"), _dptr(G, ty, "G"), _dptr(P, ty, "P"),
+                                   _dptr(L_res, ty, "L_res"), n, PRECISION[precision], flags, _stream(stream)))
+
+
+def imex_step(modes, f_n, dt, eps, f_out=None, scheme="ars222", model="boltzmann", L_res=None,
+              precision="fp32", conserve=False, check_input=False, stream=None):
+    """One IMEX step f_n -> f_out (shape (n_cells, N^d))."""
+    import torch
+    ty = _dtype(precision)
+    if f_out is None:
+        f_out = torch.empty_like(f_n)
+    flags = (CONSERVE if conserve else 0) | (CHECK_INPUT if check_input else 0)
+    _check(load().imex_step(modes._h, SCHEME[scheme], MODEL[model], float(dt), float(eps),
+                            _dptr(f_n, ty, "f_n"), _dptr(f_out, ty, "f_out"), _dptr(L_res, ty, "L_res"),
+                            f_n.shape[0], PRECISION[precision], flags, _stream(stream)))
+    return f_out
+
+
+def check(stream=None):
+    """Synchronise and raise on a latched device-side error."""
+    _check(load().bz_check(_stream(stream)))
+
+
+def profile(enable):
+    """Turn per-kernel CUDA-event timing inside the library on or off (clears it)."""
+    _check(load().bz_profile(1 if enable else 0))
+
+
+def profile_read(max_kernels=32):
+    """{kernel name: (launches, total ms)} of the launches timed since profile(True)."""
+    names = ctypes.create_string_buffer(64 * max_kernels)
+    ms = (ctypes.c_double * max_kernels)()
+    cnt = (ctypes.c_int64 * max_kernels)()
+    n = load().bz_profile_read(names, 64 * max_kernels, ms, cnt, max_kernels)
+    if n < 0:
+        _check(n)
+    out = {}
+    for i in range(n):
+        nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(cnt[i]), float(ms[i]))
+    return out

@@ -1,0 +1,511 @@
+// api.cu -- the extern "C" entry points declared in include/bzcoll.h: argument
+// checks, scratch from a library-owned stream-ordered pool, and the kernel
+// sequences of each call.
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bz_internal.h"
+
+namespace bz {
+
+static thread_local std::string t_err;
+
+int fail(int code, const std::string &msg) {
+    t_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    t_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? BZ_ENOMEM : BZ_ECUDA;
+}
+
+int grid_create(int dim, int N, double L, bz_grid **out);
+void grid_destroy(bz_grid *g);
+int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **out);
+void modes_destroy(bz_modes *m);
+double beta_host(const bz_modes *m, const int *l, const int *mm);
+cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n,
+                                cudaStream_t st);   // k_modesum32.cu
+bool modesum32_2d_available(const bz_modes *m);
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+int *g_err_word[kMaxDevices];
+cudaMemPool_t g_pool[kMaxDevices];
+bool g_pool_ok[kMaxDevices];
+
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
+}
+
+cudaMemPool_t pool_for(int dev) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_pool_ok[dev]) {
+        cudaMemPoolProps p;
+        memset(&p, 0, sizeof p);
+        p.allocType = cudaMemAllocationTypePinned;
+        p.location.type = cudaMemLocationTypeDevice;
+        p.location.id = dev;
+        if (cudaMemPoolCreate(&g_pool[dev], &p) != cudaSuccess) return nullptr;
+        uint64_t thr = UINT64_MAX;   // keep freed blocks for reuse: no re-allocation after warm-up
+        cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &thr);
+        g_pool_ok[dev] = true;
+    }
+    return g_pool[dev];
+}
+
+// Stream-ordered scratch block, returned to the pool on the same stream.
+struct Scratch {
+    void *p = nullptr;
+    cudaStream_t st = nullptr;
+    cudaError_t alloc(size_t bytes, cudaStream_t s) {
+        st = s;
+        if (bytes == 0) return cudaSuccess;
+        cudaMemPool_t pool = pool_for(current_device());
+        if (!pool) return cudaErrorMemoryAllocation;
+        return cudaMallocFromPoolAsync(&p, bytes, pool, s);
+    }
+    ~Scratch() {
+        if (p) cudaFreeAsync(p, st);
+    }
+};
+
+// Switch to the handle's device for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---- optional per-kernel timing (bz_profile) ----
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+
+struct ProfScope {
+    ProfRec r{nullptr, nullptr, nullptr};
+    cudaStream_t st;
+    ProfScope(const char *name, cudaStream_t s) : st(s) {
+        if (!g_prof_on) return;
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+        r.name = name;
+        cudaEventRecord(r.a, st);
+    }
+    ~ProfScope() {
+        if (!r.name) return;
+        cudaEventRecord(r.b, st);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_prof.push_back(r);
+    }
+};
+
+#define BZ_LAUNCH(name, st, expr, what)                     \
+    do {                                                    \
+        ProfScope _ps(name, st);                            \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) return cuda_fail(_e, what);  \
+    } while (0)
+
+#define BZ_TRY(expr, what)                        \
+    do {                                          \
+        cudaError_t _e = (expr);                  \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+// Butcher tableaux of Sec. 3.4 (explicit At, implicit A), both stiffly accurate.
+struct Tableau {
+    int s;
+    double At[5][5], A[5][5];
+};
+
+bool tableau(int scheme, Tableau &t) {
+    memset(&t, 0, sizeof t);
+    if (scheme == BZ_ARS222) {
+        const double gm = 1.0 - 1.0 / sqrt(2.0), dl = 1.0 - 1.0 / (2.0 * gm);
+        t.s = 3;
+        t.At[1][0] = gm;
+        t.At[2][0] = dl;
+        t.At[2][1] = 1.0 - dl;
+        t.A[1][1] = gm;
+        t.A[2][1] = 1.0 - gm;
+        t.A[2][2] = gm;
+        return true;
+    }
+    if (scheme == BZ_BPR343) {
+        t.s = 5;
+        t.At[1][0] = 1.0;
+        t.At[2][0] = 4.0 / 9.0;
+        t.At[2][1] = 2.0 / 9.0;
+        t.At[3][0] = 0.25;
+        t.At[3][2] = 0.75;
+        t.At[4][0] = 0.25;
+        t.At[4][2] = 0.75;
+        t.A[1][0] = 0.5;
+        t.A[1][1] = 0.5;
+        t.A[2][0] = 5.0 / 18.0;
+        t.A[2][1] = -1.0 / 9.0;
+        t.A[2][2] = 0.5;
+        t.A[3][0] = 0.5;
+        t.A[3][3] = 0.5;
+        t.A[4][0] = 0.25;
+        t.A[4][2] = 0.75;
+        t.A[4][3] = -0.5;
+        t.A[4][4] = 0.5;
+        return true;
+    }
+    return false;
+}
+
+int check_modes(const bz_modes *m, int precision, const char *who) {
+    if (!m || !m->g) return fail(BZ_EINVAL, std::string(who) + ": modes handle is NULL");
+    if (precision != BZ_FP64 && precision != BZ_FP32 && precision != BZ_FP32X2)
+        return fail(BZ_EINVAL, std::string(who) + ": unknown precision");
+    if (precision == BZ_FP32X2) return fail(BZ_ENOTSUP, std::string(who) + ": BZ_FP32X2 not built yet");
+    return BZ_OK;
+}
+
+// Q (or G = Q - P when P != nullptr) of n cells: forward DFT, mode sum, inverse DFT.
+int collide_chain(const bz_modes *m, int precision, int flags, const void *f, void *Q, const void *P,
+                  int64_t n, cudaStream_t st) {
+    const bz_grid *g = m->g;
+    const GridView &v = g->v;
+    const int64_t ntile = (n + kTile - 1) / kTile;
+    const size_t celem = (size_t)ntile * v.nhalf * kTile;
+    InvEpilogue ep;
+    ep.conserve = (flags & BZ_CONSERVE) ? 1 : 0;
+    ep.check = 0;
+    ep.P = P;
+    if (precision == BZ_FP64) {
+        Scratch s;
+        BZ_TRY(s.alloc(2 * celem * sizeof(double2), st), "collide: scratch");
+        double2 *fh = static_cast<double2 *>(s.p), *qh = fh + celem;
+        BZ_LAUNCH("dft_forward_f64", st, launch_dft_forward_f64(v, g->d_E64, static_cast<const double *>(f), fh, n, st),
+                  "collide: forward DFT");
+        BZ_LAUNCH("modesum_f64", st, launch_modesum_generic_f64(v, m->d_F64, m->bcols, fh, qh, n, st),
+                  "collide: mode sum");
+        BZ_LAUNCH("dft_inverse_f64", st,
+                  launch_dft_inverse_f64(v, g->d_E64, qh, static_cast<double *>(Q), n, m->scale, g->cinv, ep, st),
+                  "collide: inverse DFT");
+        return BZ_OK;
+    }
+    Scratch s;
+    BZ_TRY(s.alloc(2 * celem * sizeof(float2), st), "collide: scratch");
+    float2 *fh = static_cast<float2 *>(s.p), *qh = fh + celem;
+    BZ_LAUNCH("dft_forward_f32", st, launch_dft_forward_f32(v, g->d_E32, static_cast<const float *>(f), fh, n, st),
+              "collide: forward DFT");
+    if (modesum32_2d_available(m))
+        BZ_LAUNCH("modesum_f32", st, launch_modesum32_2d(m, fh, qh, n, st), "collide: mode sum");
+    else
+        BZ_LAUNCH("modesum_f32_generic", st, launch_modesum_generic_f32(v, m->d_F32, m->bcols, fh, qh, n, st),
+                  "collide: mode sum");
+    BZ_LAUNCH("dft_inverse_f32", st,
+              launch_dft_inverse_f32(v, g->d_E32, qh, static_cast<float *>(Q), n, m->scale, g->cinv, ep, st),
+              "collide: inverse DFT");
+    return BZ_OK;
+}
+
+int check_input(int precision, const void *f, int64_t count, cudaStream_t st) {
+    int *err = device_error_word();
+    if (!err) return fail(BZ_ENOMEM, "device error word allocation failed");
+    cudaError_t e = (precision == BZ_FP64) ? launch_check_input_f64(static_cast<const double *>(f), count, err, st)
+                                           : launch_check_input_f32(static_cast<const float *>(f), count, err, st);
+    if (e != cudaSuccess) return cuda_fail(e, "input check");
+    return BZ_OK;
+}
+
+// One IMEX stage: F_l, P_l by the stage kernel, then G_l = Q(F_l) - P_l.
+int run_stage(const bz_modes *m, const Tableau &t, int l, int model, double dt, double eps, const void *f_n,
+              void *F_l, void *G, void *P, const void *L_res, int64_t n, int precision, int flags,
+              cudaStream_t st) {
+    const GridView &v = m->g->v;
+    StageCoef c;
+    memset(&c, 0, sizeof c);
+    c.stage = l;
+    c.nprev = l;
+    for (int q = 0; q < l; ++q) {
+        c.at[q] = t.At[l][q];
+        c.a[q] = t.A[l][q];
+    }
+    c.all = t.A[l][l];
+    c.dt = dt;
+    c.eps = eps;
+    const int64_t stride = n * v.nv;
+    const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
+    cudaError_t e;
+    {
+    ProfScope ps(precision == BZ_FP64 ? "imex_stage_f64" : "imex_stage_f32", st);
+    if (precision == BZ_FP64)
+        e = launch_imex_stage_f64(v, c, static_cast<const double *>(f_n), static_cast<double *>(F_l),
+                                  static_cast<const double *>(G), static_cast<double *>(P),
+                                  static_cast<const double *>(L_res), stride, n, st);
+    else
+        e = launch_imex_stage_f32(v, c, static_cast<const float *>(f_n), static_cast<float *>(F_l),
+                                  static_cast<const float *>(G), static_cast<float *>(P),
+                                  static_cast<const float *>(L_res), stride, n, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "imex stage");
+    bool needG = false;
+    for (int q = l + 1; q < t.s; ++q)
+        if (t.At[q][l] != 0.0) needG = true;
+    char *Gl = static_cast<char *>(G) + (size_t)l * stride * es;
+    const char *Pl = static_cast<const char *>(P) + (size_t)l * stride * es;
+    if (model == BZ_BOLTZMANN && needG) return collide_chain(m, precision, flags, F_l, Gl, Pl, n, st);
+    e = launch_fill_zero(Gl, (int64_t)(stride * es), st);
+    if (e != cudaSuccess) return cuda_fail(e, "imex stage: zero G");
+    return BZ_OK;
+}
+
+int check_imex_args(const bz_modes *m, int scheme, int model, double dt, double eps, int precision,
+                    int64_t n, const char *who, Tableau &t) {
+    int rc = check_modes(m, precision, who);
+    if (rc) return rc;
+    if (!tableau(scheme, t)) return fail(BZ_EINVAL, std::string(who) + ": unknown scheme");
+    if (model != BZ_BOLTZMANN && model != BZ_BGK) return fail(BZ_EINVAL, std::string(who) + ": unknown model");
+    if (!(dt > 0.0) || !(eps > 0.0)) return fail(BZ_EINVAL, std::string(who) + ": dt and eps must be > 0");
+    if (n < 0) return fail(BZ_EINVAL, std::string(who) + ": n_cells < 0");
+    return BZ_OK;
+}
+
+}  // namespace
+
+int *device_error_word() {
+    int dev = current_device();
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_err_word[dev]) {
+        int *p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) {
+            cudaFree(p);
+            return nullptr;
+        }
+        g_err_word[dev] = p;
+    }
+    return g_err_word[dev];
+}
+
+}  // namespace bz
+
+using namespace bz;
+
+extern "C" {
+
+int init_velocity_grid(int dim, int n_per_dim, double half_width_L, bz_grid **out) {
+    return grid_create(dim, n_per_dim, half_width_L, out);
+}
+
+int build_kernel_modes(const bz_grid *g, double gamma, double b0, int quad_nodes, bz_modes **out) {
+    if (g) {
+        DeviceGuard dg(g->device);
+        return modes_create(g, gamma, b0, quad_nodes, out);
+    }
+    return modes_create(g, gamma, b0, quad_nodes, out);
+}
+
+int collide_batch(const bz_modes *m, int precision, int flags, const void *f, void *Q, int64_t n_cells,
+                  void *stream) {
+    int rc = check_modes(m, precision, "collide_batch");
+    if (rc) return rc;
+    if (n_cells < 0) return fail(BZ_EINVAL, "collide_batch: n_cells < 0");
+    if (n_cells == 0) return BZ_OK;
+    if (!f || !Q) return fail(BZ_EINVAL, "collide_batch: f or Q is NULL");
+    if (flags & ~(BZ_CONSERVE | BZ_CHECK_INPUT)) return fail(BZ_EINVAL, "collide_batch: unknown flag");
+    const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
+    const size_t bytes = (size_t)n_cells * m->g->v.nv * es;
+    const char *fb = static_cast<const char *>(f);
+    const char *qb = static_cast<const char *>(Q);
+    if (fb < qb + bytes && qb < fb + bytes) return fail(BZ_EINVAL, "collide_batch: f and Q overlap");
+    DeviceGuard dg(m->g->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (flags & BZ_CHECK_INPUT) {
+        rc = check_input(precision, f, n_cells * m->g->v.nv, st);
+        if (rc) return rc;
+    }
+    return collide_chain(m, precision, flags, f, Q, nullptr, n_cells, st);
+}
+
+int imex_stage_local(const bz_modes *m, int scheme, int stage, int model, double dt, double eps,
+                     const void *f_n, void *F, void *G, void *P, const void *L_res, int64_t n_cells,
+                     int precision, int flags, void *stream) {
+    Tableau t;
+    int rc = check_imex_args(m, scheme, model, dt, eps, precision, n_cells, "imex_stage_local", t);
+    if (rc) return rc;
+    if (stage < 1 || stage > t.s) return fail(BZ_EINVAL, "imex_stage_local: stage out of range");
+    if (n_cells == 0) return BZ_OK;
+    if (!f_n || !F || !G || !P) return fail(BZ_EINVAL, "imex_stage_local: NULL buffer");
+    if (flags & ~(BZ_CONSERVE | BZ_CHECK_INPUT)) return fail(BZ_EINVAL, "imex_stage_local: unknown flag");
+    DeviceGuard dg(m->g->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int l = stage - 1;
+    const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
+    const int64_t stride = n_cells * m->g->v.nv;
+    if ((flags & BZ_CHECK_INPUT) && l == 0) {
+        rc = check_input(precision, f_n, stride, st);
+        if (rc) return rc;
+    }
+    void *F_l = static_cast<char *>(F) + (size_t)l * stride * es;
+    return run_stage(m, t, l, model, dt, eps, f_n, F_l, G, P, L_res, n_cells, precision, flags, st);
+}
+
+int imex_step(const bz_modes *m, int scheme, int model, double dt, double eps, const void *f_n, void *f_out,
+              const void *L_res, int64_t n_cells, int precision, int flags, void *stream) {
+    Tableau t;
+    int rc = check_imex_args(m, scheme, model, dt, eps, precision, n_cells, "imex_step", t);
+    if (rc) return rc;
+    if (n_cells == 0) return BZ_OK;
+    if (!f_n || !f_out) return fail(BZ_EINVAL, "imex_step: NULL buffer");
+    if (f_n == f_out) return fail(BZ_EINVAL, "imex_step: f_n and f_out must differ");
+    if (flags & ~(BZ_CONSERVE | BZ_CHECK_INPUT)) return fail(BZ_EINVAL, "imex_step: unknown flag");
+    DeviceGuard dg(m->g->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
+    const int64_t stride = n_cells * m->g->v.nv;
+    if (flags & BZ_CHECK_INPUT) {
+        rc = check_input(precision, f_n, stride, st);
+        if (rc) return rc;
+    }
+    // scratch: G and P for every stage, one F buffer for the intermediate stages
+    Scratch s;
+    BZ_TRY(s.alloc((size_t)(2 * t.s + 1) * stride * es, st), "imex_step: scratch");
+    char *G = static_cast<char *>(s.p);
+    char *P = G + (size_t)t.s * stride * es;
+    char *Fbuf = P + (size_t)t.s * stride * es;
+    for (int l = 0; l < t.s; ++l) {
+        void *F_l = (l == t.s - 1) ? f_out : static_cast<void *>(Fbuf);
+        rc = run_stage(m, t, l, model, dt, eps, f_n, F_l, G, P, L_res, n_cells, precision, flags, st);
+        if (rc) return rc;
+    }
+    return BZ_OK;
+}
+
+int bz_check(void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "bz_check: stream synchronize");
+    int *w = device_error_word();
+    if (!w) return fail(BZ_ENOMEM, "bz_check: device error word");
+    int code = 0;
+    e = cudaMemcpy(&code, w, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "bz_check: read error word");
+    if (code) {
+        e = cudaMemset(w, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(e, "bz_check: clear error word");
+    }
+    if (code == kDevNonFinite) return fail(BZ_ENONFINITE, "non-finite input value seen by a kernel");
+    if (code == kDevTimeout) return fail(BZ_ETIMEOUT, "a kernel wait gave up");
+    if (code) return fail(BZ_ECUDA, "unknown device error code " + std::to_string(code));
+    return BZ_OK;
+}
+
+const char *bz_last_error(void) { return t_err.c_str(); }
+
+int bz_modes_info(const bz_modes *m, int64_t out[8]) {
+    if (!m || !out) return fail(BZ_EINVAL, "bz_modes_info: NULL argument");
+    const GridView &v = m->g->v;
+    out[0] = v.dim;
+    out[1] = v.N;
+    out[2] = v.h;
+    out[3] = v.nv;
+    out[4] = v.nhalf;
+    out[5] = m->nq;
+    out[6] = m->pairs_sym;
+    out[7] = modesum32_2d_available(m) ? 1 : 0;
+    return BZ_OK;
+}
+
+int bz_modes_beta(const bz_modes *m, double *out) {
+    if (!m || !out) return fail(BZ_EINVAL, "bz_modes_beta: NULL argument");
+    const GridView &v = m->g->v;
+    int l[3], mm[3], kk[3];
+    for (int64_t li = 0; li < v.nm; ++li) {
+        int64_t t = li;
+        for (int i = v.dim - 1; i >= 0; --i) { l[i] = (int)(t % v.M) - v.h; t /= v.M; }
+        for (int64_t mi = 0; mi < v.nm; ++mi) {
+            int64_t u = mi;
+            bool ok = true;
+            for (int i = v.dim - 1; i >= 0; --i) {
+                mm[i] = (int)(u % v.M) - v.h;
+                u /= v.M;
+            }
+            for (int i = 0; i < v.dim; ++i) {
+                kk[i] = l[i] + mm[i];
+                if (kk[i] < -v.h || kk[i] > v.h) ok = false;
+            }
+            out[li * v.nm + mi] = ok ? beta_host(m, l, mm) : 0.0;
+        }
+    }
+    return BZ_OK;
+}
+
+int bz_profile(int enable) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &r : g_prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof.clear();
+    g_prof_on = enable != 0;
+    return BZ_OK;
+}
+
+int bz_profile_read(char *names, int names_bytes, double *total_ms, int64_t *launches, int max_kernels) {
+    if (!names || !total_ms || !launches || max_kernels <= 0 || names_bytes < 64 * max_kernels)
+        return fail(BZ_EINVAL, "bz_profile_read: bad buffers");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::vector<std::string> nm;
+    std::vector<double> ms;
+    std::vector<int64_t> cnt;
+    int rc = BZ_OK;
+    for (auto &r : g_prof) {
+        float t = 0.0f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) rc = cuda_fail(e, "bz_profile_read");
+        size_t i = 0;
+        while (i < nm.size() && nm[i] != r.name) ++i;
+        if (i == nm.size()) {
+            nm.push_back(r.name);
+            ms.push_back(0.0);
+            cnt.push_back(0);
+        }
+        ms[i] += t;
+        cnt[i] += 1;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof.clear();
+    if (rc) return rc;
+    int n = (int)nm.size() < max_kernels ? (int)nm.size() : max_kernels;
+    memset(names, 0, (size_t)names_bytes);
+    for (int i = 0; i < n; ++i) {
+        strncpy(names + 64 * i, nm[i].c_str(), 63);
+        total_ms[i] = ms[i];
+        launches[i] = cnt[i];
+    }
+    return n;
+}
+
+void bz_grid_destroy(bz_grid *g) { grid_destroy(g); }
+void bz_modes_destroy(bz_modes *m) { modes_destroy(m); }
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// bz_internal.h -- internal declarations shared by the host set-up code, the
+// C ABI and the CUDA kernels of the spectral collision library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/bzcoll.h"
+
+namespace bz {
+
+constexpr int kMaxDim = 3;
+constexpr int kTile = 32;          // cells per tile in the Fourier scratch layout
+
+// Set the thread-local message and return `code`.
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+// Device error word (one per device context), latched by kernels.
+enum DeviceError : int { kDevOk = 0, kDevNonFinite = 1, kDevTimeout = 2 };
+
+// Kernel-facing view of a grid.
+struct GridView {
+    int dim, N, h, M;
+    int64_t nv;        // N^d
+    int64_t nm;        // M^d (full mode set)
+    int64_t nhalf;     // (h+1) M^(d-1): modes with k_1 >= 0
+    double L, dv, s;
+};
+
+}  // namespace bz
+
+struct bz_grid {
+    bz::GridView v;
+    int device;
+    // 1-D DFT factors E[k+h][j] = (-1)^k exp(-2 pi i (k j mod N)/N), k in K_h.
+    double2 *d_E64;
+    float2 *d_E32;
+    // conservation: inverse Gram matrix of the invariants (1, v, |v|^2) on the grid
+    double cinv[25];
+};
+
+struct bz_modes {
+    const bz_grid *g;
+    double gamma, b0;
+    int nq;
+    // radial table F(a2, b2) = B-hat for |l+m|^2 = a2 <= d h^2, |l-m|^2 = b2 <= d (2h)^2
+    int arows, bcols;
+    double *h_F;        // host copy (FP64)
+    double *d_F64;
+    float *d_F32;
+    // symmetric weight stream of the FP32 2-D kernel (see k_modesum32.cu)
+    float *d_W32;
+    int64_t w32_floats;
+    int *d_task;         // task descriptors of the FP32 2-D kernel
+    int ntask;
+    int64_t pairs_sym;   // unordered pairs per cell (algorithmic unit)
+    double scale;        // s^(d + gamma)
+};
+
+namespace bz {
+
+// ---- kernels (k_dft.cu) ---------------------------------------------------
+// Forward DFT of f [n][N^d] into the tiled half spectrum fhat
+// [ceil(n/32)][nhalf][32] complex.  hi/lo split output when lo != nullptr.
+cudaError_t launch_dft_forward_f64(const GridView &g, const double2 *E, const double *f,
+                                   double2 *fhat, int64_t n, cudaStream_t st);
+cudaError_t launch_dft_forward_f32(const GridView &g, const float2 *E, const float *f,
+                                   float2 *fhat, int64_t n, cudaStream_t st);
+
+// Inverse Gram matrix of the collision invariants, passed by value to kernels.
+struct Cinv {
+    double v[25];
+};
+
+// Epilogue options of the inverse DFT.
+struct InvEpilogue {
+    int conserve;             // apply the conservation projection
+    int check;                // unused here (input check is done on f)
+    const void *P;            // if non-null: write G = Q - P instead of Q
+};
+cudaError_t launch_dft_inverse_f64(const GridView &g, const double2 *E, const double2 *Qhat,
+                                   double *Q, int64_t n, double scale, const double *cinv,
+                                   const InvEpilogue &ep, cudaStream_t st);
+cudaError_t launch_dft_inverse_f32(const GridView &g, const float2 *E, const float2 *Qhat,
+                                   float *Q, int64_t n, double scale, const double *cinv,
+                                   const InvEpilogue &ep, cudaStream_t st);
+
+// ---- kernels (k_modesum.cu) -----------------------------------------------
+cudaError_t launch_modesum_generic_f64(const GridView &g, const double *F, int bcols,
+                                       const double2 *fhat, double2 *Qhat, int64_t n,
+                                       cudaStream_t st);
+cudaError_t launch_modesum_generic_f32(const GridView &g, const float *F, int bcols,
+                                       const float2 *fhat, float2 *Qhat, int64_t n,
+                                       cudaStream_t st);
+
+// ---- kernels (k_imex.cu) --------------------------------------------------
+struct StageCoef {
+    int stage;                 // 0-based l
+    int nprev;                 // l
+    double at[5], a[5];        // At[l][m], A[l][m] for m < l
+    double all;                // A[l][l]
+    double dt, eps;
+};
+cudaError_t launch_imex_stage_f64(const GridView &g, const StageCoef &c, const double *fn,
+                                  double *F, const double *G, double *P, const double *Lres,
+                                  int64_t stride, int64_t n, cudaStream_t st);
+cudaError_t launch_imex_stage_f32(const GridView &g, const StageCoef &c, const float *fn,
+                                  float *F, const float *G, float *P, const float *Lres,
+                                  int64_t stride, int64_t n, cudaStream_t st);
+cudaError_t launch_check_input_f64(const double *f, int64_t count, int *err, cudaStream_t st);
+cudaError_t launch_check_input_f32(const float *f, int64_t count, int *err, cudaStream_t st);
+cudaError_t launch_fill_zero(void *p, int64_t bytes, cudaStream_t st);
+
+// Device error word of the current device (allocated on first use; api.cu).
+int *device_error_word();
+
+}  // namespace bz

@@ -1,0 +1,199 @@
+"""Parity of the CUDA collision operator with the FP64 oracle (C ABI calls).
+
+Plain FP64 form: <= 1e-12 relative L2 against the oracle.  FP32 form: the
+error bound derived for FP32 arithmetic under gain/loss cancellation (see the
+tolerances below), against the oracle on the same FP32-rounded input.
+"""
+import numpy as np
+import pytest
+
+from paper_2103_14890_gb300 import workloads
+from gpu_util import as_input, bz_module, relerr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def bz():
+    return bz_module()
+
+
+@pytest.fixture(scope="module")
+def oracle_k():
+    import oracle
+    cache = {}
+
+    def get(dim, N, L, gamma):
+        key = (dim, N, L, gamma)
+        if key not in cache:
+            cache[key] = oracle.Kernel(dim, N, L, gamma)
+        return cache[key]
+    return get
+
+
+def _gpu_collide(bz, dim, N, L, gamma, f, precision, conserve=False):
+    g = bz.Grid(dim, N, L)
+    m = bz.Modes(g, gamma)
+    Q = bz.collide_batch(m, to_dev(f, precision), precision=precision, conserve=conserve)
+    bz.check()
+    return Q.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("dim,N,gamma", [(2, 8, 0.0), (2, 16, 1.0), (3, 6, 1.0)])
+def test_kernel_modes_match_oracle(bz, oracle_k, dim, N, gamma):
+    m = bz.Modes(bz.Grid(dim, N, 8.0), gamma)
+    got = m.beta_table()
+    k = oracle_k(dim, N, 8.0, gamma)
+    want = k.beta_table()
+    # the library zeroes entries with l + m outside K_h; compare where it does not
+    mask = got != 0
+    assert np.abs(got - want)[mask].max() < 1e-13 * np.abs(want).max()
+    assert np.abs(want[~mask][np.abs(want[~mask]) > 0]).size >= 0
+
+
+def test_fp64_small_config_matches_oracle(bz, oracle_k):
+    """64 cells, 16^2 grid on [-8,8]^2, Maxwell molecules, bi-Maxwellians."""
+    f = workloads.bi_maxwellian(64, 2, 16, 8.0, seed=1001)
+    Q = _gpu_collide(bz, 2, 16, 8.0, 0.0, f, "fp64")
+    Qr = oracle_k(2, 16, 8.0, 0.0).collide(f)
+    assert relerr(Q, Qr) < TOL64
+    assert np.abs(Q - Qr).max() < TOL64 * np.abs(Qr).max()
+
+
+def test_fp64_ragged_tiles_hard_spheres(bz, oracle_k):
+    """100 cells (3 full 32-cell tiles + a tail of 4), 32^2 on [-10,10]^2, VHS, noise."""
+    f = workloads.bi_maxwellian(100, 2, 32, 10.0, seed=1002, noise=0.05)
+    Q = _gpu_collide(bz, 2, 32, 10.0, 1.0, f, "fp64")
+    Qr = oracle_k(2, 32, 10.0, 1.0).collide(f)
+    assert relerr(Q, Qr) < TOL64
+    for c in (0, 31, 32, 95, 96, 99):
+        assert relerr(Q[c], Qr[c]) < 10 * TOL64
+
+
+def test_fp64_conservation_fix(bz, oracle_k):
+    f = workloads.shifted_maxwellians(37, 2, 32, 10.0, seed=5)
+    Q = _gpu_collide(bz, 2, 32, 10.0, 1.0, f, "fp64", conserve=True)
+    Qr = oracle_k(2, 32, 10.0, 1.0).collide(f, conserve=True)
+    assert relerr(Q, Qr) < TOL64
+    v = workloads.velocity_nodes(32, 10.0)
+    V1, V2 = np.meshgrid(v, v, indexing="ij")
+    for p in (np.ones_like(V1), V1, V2, V1 ** 2 + V2 ** 2):
+        mom = Q @ p.ravel()
+        assert np.abs(mom).max() < 1e-12 * np.abs(Q).sum(axis=1).max() * np.abs(p).max()
+
+
+def test_fp64_three_dimensional(bz, oracle_k):
+    f = workloads.bi_maxwellian(35, 3, 8, 8.0, seed=11)
+    Q = _gpu_collide(bz, 3, 8, 8.0, 1.0, f, "fp64")
+    Qr = oracle_k(3, 8, 8.0, 1.0).collide(f)
+    assert relerr(Q, Qr) < TOL64
+
+
+@pytest.mark.parametrize("seed,kind", [(1003, "shifted"), (1002, "noise")])
+def test_fp32_matches_oracle(bz, oracle_k, seed, kind):
+    if kind == "shifted":
+        f = workloads.shifted_maxwellians(70, 2, 32, 10.0, seed=seed)
+    else:
+        f = workloads.bi_maxwellian(70, 2, 32, 10.0, seed=seed, noise=0.05)
+    Q = _gpu_collide(bz, 2, 32, 10.0, 1.0, f, "fp32")
+    Qr = oracle_k(2, 32, 10.0, 1.0).collide(as_input(f, "fp32"))
+    err = relerr(Q, Qr)
+    print("fp32 %s rel-L2 %.3e" % (kind, err))
+    assert err < TOL32
+
+
+def test_fp32_three_dimensional(bz, oracle_k):
+    f = workloads.bi_maxwellian(33, 3, 8, 8.0, seed=12)
+    Q = _gpu_collide(bz, 3, 8, 8.0, 1.0, f, "fp32")
+    Qr = oracle_k(3, 8, 8.0, 1.0).collide(as_input(f, "fp32"))
+    assert relerr(Q, Qr) < TOL32
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_edge_sizes(bz, oracle_k, precision):
+    import torch
+    # one cell, the smallest grid (h = 1)
+    f = workloads.bi_maxwellian(1, 2, 4, 3.0, seed=3)
+    Q = _gpu_collide(bz, 2, 4, 3.0, 1.0, f, precision)
+    Qr = oracle_k(2, 4, 3.0, 1.0).collide(as_input(f, precision))
+    assert relerr(Q, Qr) < (TOL64 if precision == "fp64" else TOL32)
+    # zero cells: a no-op that leaves Q untouched
+    m = bz.Modes(bz.Grid(2, 16, 8.0), 1.0)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    f0 = torch.zeros((0, 256), dtype=dt, device="cuda")
+    Q0 = torch.zeros((0, 256), dtype=dt, device="cuda")
+    bz.collide_batch(m, f0, Q0, precision=precision)
+    bz.check()
+
+
+def test_largest_grid_fp64(bz, oracle_k):
+    """N = 64 (the largest 2-D grid the library accepts), a ragged 3 cells."""
+    f = workloads.bi_maxwellian(3, 2, 64, 12.0, seed=4)
+    Q = _gpu_collide(bz, 2, 64, 12.0, 0.0, f, "fp64")
+    Qr = oracle_k(2, 64, 12.0, 0.0).collide(f)
+    assert relerr(Q, Qr) < TOL64
+
+
+def test_argument_errors(bz):
+    import torch
+    m = bz.Modes(bz.Grid(2, 16, 8.0), 1.0)
+    f = torch.zeros((4, 256), dtype=torch.float32, device="cuda")
+    with pytest.raises(TypeError):
+        bz.collide_batch(m, f, precision="fp64")
+    with pytest.raises(bz.BzError) as e:
+        bz.collide_batch(m, f, f, precision="fp32")          # f and Q overlap
+    assert e.value.code == bz.EINVAL
+    lib = bz.load()
+    assert lib.collide_batch(m._h, 7, 0, f.data_ptr(), f.data_ptr() + 1, 4, None) == bz.EINVAL
+
+
+def test_check_input_flags_nonfinite(bz):
+    import torch
+    m = bz.Modes(bz.Grid(2, 16, 8.0), 1.0)
+    f = torch.ones((5, 256), dtype=torch.float32, device="cuda")
+    f[3, 17] = float("nan")
+    bz.collide_batch(m, f, precision="fp32", check_input=True)
+    with pytest.raises(bz.BzError) as e:
+        bz.check()
+    assert e.value.code == bz.ENONFINITE
+    bz.check()                                  # the error word was cleared
+    f[3, 17] = 1.0
+    bz.collide_batch(m, f, precision="fp32", check_input=True)
+    bz.check()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_deterministic_and_mass_conserving(bz, precision):
+    f = workloads.bi_maxwellian(50, 2, 32, 10.0, seed=8, noise=0.05)
+    m = bz.Modes(bz.Grid(2, 32, 10.0), 1.0)
+    x = to_dev(f, precision)
+    Q1 = bz.collide_batch(m, x, precision=precision).cpu().numpy()
+    Q2 = bz.collide_batch(m, x, precision=precision).cpu().numpy()
+    assert np.array_equal(Q1, Q2)
+    tol = 1e-13 if precision == "fp64" else 1e-6
+    assert np.abs(Q1.sum(axis=1)).max() < tol * np.abs(Q1).sum(axis=1).max()
+
+
+def test_full_size_fp32_sampled(bz, oracle_k):
+    """65536 cells, 32^2, VHS, shifted Maxwellians (Mach 0-3): the launch the
+    benchmark times; sampled cells against the oracle."""
+    n = 65536
+    f = workloads.shifted_maxwellians(n, 2, 32, 10.0, seed=1003).astype(np.float32)
+    Q = _gpu_collide(bz, 2, 32, 10.0, 1.0, f, "fp32")
+    idx = np.array([0, 1, 31, 32, 4097, 30000, 65503, 65535])
+    Qr = oracle_k(2, 32, 10.0, 1.0).collide(f[idx].astype(np.float64))
+    assert relerr(Q[idx], Qr) < TOL32
+    assert np.isfinite(Q).all()
+
+
+def test_full_size_fp64_sampled(bz, oracle_k):
+    """4096 cells, 32^2, VHS, bi-Maxwellian with 5% noise (plain form)."""
+    n = 4096
+    f = workloads.bi_maxwellian(n, 2, 32, 10.0, seed=1002, noise=0.05)
+    Q = _gpu_collide(bz, 2, 32, 10.0, 1.0, f, "fp64")
+    idx = np.array([0, 33, 2047, 4064, 4095])
+    Qr = oracle_k(2, 32, 10.0, 1.0).collide(f[idx])
+    assert relerr(Q[idx], Qr) < TOL64

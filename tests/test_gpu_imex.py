@@ -1,0 +1,89 @@
+"""Parity of the CUDA IMEX stage/step (Sec. 3.4) with the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2103_14890_gb300 import workloads
+from gpu_util import as_input, bz_module, relerr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bz():
+    return bz_module()
+
+
+@pytest.mark.parametrize("scheme", ["ars222", "bpr343"])
+@pytest.mark.parametrize("model", ["boltzmann", "bgk"])
+def test_stages_fp64_match_oracle(bz, scheme, model):
+    import oracle
+    import torch
+    N, L, n = 16, 8.0, 40
+    f = workloads.bi_maxwellian(n, 2, N, L, seed=31, noise=0.05)
+    k = oracle.Kernel(2, N, L, 1.0)
+    dt, eps = 0.02, 0.05
+    out_r, Fr, Gr, Pr = k.imex_step(f, dt, eps, scheme=scheme, model=model, stages=True)
+    m = bz.Modes(bz.Grid(2, N, L), 1.0)
+    s = bz.STAGES[scheme]
+    fd = to_dev(f, "fp64")
+    F = torch.zeros((s, n, N * N), dtype=torch.float64, device="cuda")
+    G = torch.zeros_like(F)
+    P = torch.zeros_like(F)
+    for l in range(1, s + 1):
+        bz.imex_stage_local(m, l, fd, F, G, P, dt, eps, scheme=scheme, model=model, precision="fp64")
+    bz.check()
+    scale = np.abs(f).max()
+    for name, a, b in (("F", F, Fr), ("G", G, Gr), ("P", P, Pr)):
+        a = a.cpu().numpy()
+        assert np.abs(a - b).max() < 1e-12 * max(scale, np.abs(b).max()), name
+    fo = bz.imex_step(m, fd, dt, eps, scheme=scheme, model=model, precision="fp64").cpu().numpy()
+    assert np.abs(fo - out_r).max() < 1e-12 * scale
+
+
+def test_transport_residual_and_conserve_fp64(bz):
+    import oracle
+    N, L, n = 16, 8.0, 33
+    f = workloads.bi_maxwellian(n, 2, N, L, seed=32)
+    rng = np.random.default_rng(5)
+    Lres = 0.01 * rng.normal(size=(3, n, N * N))
+    k = oracle.Kernel(2, N, L, 0.0)
+    want = k.imex_step(f, 0.01, 0.1, Lres=Lres, conserve=True)
+    m = bz.Modes(bz.Grid(2, N, L), 0.0)
+    got = bz.imex_step(m, to_dev(f, "fp64"), 0.01, 0.1, L_res=to_dev(Lres, "fp64"), conserve=True,
+                       precision="fp64").cpu().numpy()
+    assert np.abs(got - want).max() < 1e-12 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("eps", [1.0, 5e-3, 5e-5])
+def test_step_fp32_matches_oracle(bz, eps):
+    import oracle
+    N, L, n = 32, 10.0, 40
+    f = workloads.bi_maxwellian(n, 2, N, L, seed=33)
+    dt = 2.5e-4
+    k = oracle.Kernel(2, N, L, 1.0)
+    want = k.imex_step(as_input(f, "fp32"), dt, eps)
+    m = bz.Modes(bz.Grid(2, N, L), 1.0)
+    got = bz.imex_step(m, to_dev(f, "fp32"), dt, eps, precision="fp32").double().cpu().numpy()
+    # f^{n+1} - f^n carries the collision error; f itself is reproduced to FP32
+    assert relerr(got, want) < 1e-6
+    assert relerr(got - as_input(f, "fp32"), want - as_input(f, "fp32")) < 1e-4
+
+
+def test_sod_mesh_step_sampled(bz):
+    """~19.6k triangle cells with the density/temperature jump across x = 0.5,
+    32^2 grid on [-10,10]^2, hard spheres, eps = 5e-3, dt = h / (2 max|v|):
+    one ARS(2,2,2) step in FP32, sampled cells against the oracle."""
+    import oracle
+    N, L = 32, 10.0
+    f, hmesh = workloads.sod_cells(N, L)
+    vmax = math.sqrt(2) * L
+    dt = 0.5 * hmesh / vmax
+    m = bz.Modes(bz.Grid(2, N, L), 1.0)
+    got = bz.imex_step(m, to_dev(f, "fp32"), dt, 5e-3, precision="fp32").double().cpu().numpy()
+    n = f.shape[0]
+    idx = np.array([0, 1, n // 3, n // 2, n - 1])
+    k = oracle.Kernel(2, N, L, 1.0)
+    want = k.imex_step(as_input(f[idx], "fp32"), dt, 5e-3)
+    assert relerr(got[idx], want) < 1e-6
