@@ -54,6 +54,7 @@ struct bz_modes {
     // symmetric weight stream of the FP32 2-D kernel (see k_modesum32.cu)
     float *d_W32;
     int64_t w32_floats;
+    int w32_rowmax;      // largest staged weight row (floats)
     int *d_task;         // task descriptors of the FP32 2-D kernel
     int ntask;
     int64_t pairs_sym;   // unordered pairs per cell (algorithmic unit)

@@ -1,22 +1,289 @@
-// k_modesum32.cu -- register-blocked FP32 mode sum for 2-D grids (filled in
-// by the symmetric sliding-window kernel; until then the generic kernel runs).
+// k_modesum32.cu -- register-blocked FP32 mode sum of eq. CF1 (Sec. 3.3) for
+// 2-D velocity grids with N <= 32.
+//
+// Work reduction (exact algebra, no approximation):
+//   * Q is real, so only k_1 >= 0 is computed (Q-hat_{-k} = conj(Q-hat_k)).
+//   * The product f-hat_l f-hat_m is symmetric in (l, m): pairs with l_1 < m_1
+//     are summed once with the weight beta-hat(l,m) + beta-hat(m,l); pairs with
+//     l_1 = m_1 keep beta-hat(l,m).  So for row k_1 only l_1 in
+//     [k_1 - h, floor(k_1/2)] is visited and m_1 = k_1 - l_1 >= 0 always lies
+//     in the stored half spectrum; f-hat_l with l_1 < 0 is conj(f-hat_{-l}).
+//
+// Layout and blocking:
+//   * one CTA = one tile of 32 cells; the tile's half spectrum (complex FP32,
+//     [mode][cell]) sits in shared memory; lane = cell, so every Fourier load
+//     is a conflict-free 32-cell row and every weight load is warp-uniform.
+//   * a task = (k_1, block of R = 8 consecutive k_2); a thread accumulates R
+//     complex outputs.  Walking l_2 upwards slides the window of f-hat_m
+//     values (m_2 = k_2 - l_2) down by one, so each step loads one new f-hat_m,
+//     one f-hat_l and R weights for 6 R FP32 operations.
+//   * each task's weights form a contiguous stream [l_1][l_2 (padded to a
+//     multiple of R)][r]; one l_1 row is staged into a per-warp shared-memory
+//     double buffer with cp.async while the previous row is being used.
+//   * accumulation: plain FP32 along an l_1 row (<= 32 terms), then a TwoSum
+//     fold of the row sum into a (hi, lo) pair per output.
+#include <vector>
+#include <algorithm>
+#include <cstring>
+
 #include "bz_device.cuh"
 #include "bz_internal.h"
 
 namespace bz {
+
+namespace {
+
+constexpr int R = 8;            // outputs per thread along k_2
+constexpr int kWarps = 16;      // warps per CTA
+constexpr int kTaskInts = 8;    // ints per task record
+
+struct TaskRec {
+    int k1, b, l1lo, nl1, l2lo, nblk, woff, pad;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NPENDING> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPENDING) : "memory");
+}
+
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Stage `nfloat` floats (multiple of 4) of a weight row into shared memory.
+__device__ __forceinline__ void stage_row(float *dst, const float *src, int nfloat, int lane) {
+    for (int i = lane * 4; i < nfloat; i += 128) cp_async16(dst + i, src + i);
+    cp_async_commit();
+}
+
+__global__ void __launch_bounds__(kWarps * 32, 1)
+modesum32_kernel(const float2 *__restrict__ fhat, float2 *__restrict__ Qhat, const float *__restrict__ W,
+                 const int *__restrict__ tasks, int h, int M, int nhalf, int wrow_max, int64_t n) {
+    extern __shared__ __align__(16) float4 smem4[];
+    float2 *Fs = reinterpret_cast<float2 *>(smem4);                  // [nhalf][32]
+    float *wsm = reinterpret_cast<float *>(Fs + (size_t)nhalf * 32);   // [warps][2][wrow_max]
+    const int64_t tile = blockIdx.x;
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(fhat + tile * (int64_t)nhalf * 32);
+        for (int i = threadIdx.x; i < nhalf * 16; i += blockDim.x) smem4[i] = src[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
+    float *wbuf1 = wbuf0 + wrow_max;
+    const int tbeg = tasks[warp], tend = tasks[warp + 1];
+    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + kWarps + 1);
+    const float2 *Fl = Fs + lane;
+    const float2 zero2 = make_float2(0.f, 0.f);
+
+    for (int t = tbeg; t < tend; ++t) {
+        const TaskRec tk = trec[t];
+        const int k20 = -h + R * tk.b;
+        const int rowf = tk.nblk * R * R;                 // floats per l_1 row
+        const float *wsrc = W + tk.woff;
+        float2 hi[R], lo[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) hi[r] = lo[r] = zero2;
+        stage_row(wbuf0, wsrc, rowf, lane);
+        for (int i = 0; i < tk.nl1; ++i) {
+            float *wcur = (i & 1) ? wbuf1 : wbuf0;
+            if (i + 1 < tk.nl1) {
+                stage_row((i & 1) ? wbuf0 : wbuf1, wsrc + (size_t)(i + 1) * rowf, rowf, lane);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            const int l1 = tk.l1lo + i;
+            const int m1 = tk.k1 - l1;                    // >= 0: stored row
+            const int dir = l1 < 0 ? -1 : 1;              // f-hat_l = conj(f-hat_{-l}) for l1 < 0
+            const float sg = (float)dir;
+            const float2 *rowl = Fl + (size_t)(dir * l1) * M * 32;
+            const float2 *rowm = Fl + (size_t)m1 * M * 32;
+            float2 acc[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = zero2;
+            float2 win[2 * R - 1];
+            for (int blk = 0; blk < tk.nblk; ++blk) {
+                const int l2b = tk.l2lo + blk * R;
+                const int mbase = k20 - l2b - (R - 1);    // m_2 of win[0]
+                if (blk == 0) {
+#pragma unroll
+                    for (int j = R; j < 2 * R - 1; ++j) {
+                        const int m2 = mbase + j;
+                        win[j] = (m2 >= -h && m2 <= h) ? rowm[(m2 + h) * 32] : zero2;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 2 * R - 2; j >= R; --j) win[j] = win[j - R];
+                }
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const int m2 = mbase + j;
+                    win[j] = (m2 >= -h && m2 <= h) ? rowm[(m2 + h) * 32] : zero2;
+                }
+                const float *wb = wcur + blk * R * R;
+#pragma unroll
+                for (int s = 0; s < R; ++s) {
+                    const int l2 = l2b + s;
+                    float2 fl = (l2 >= -h && l2 <= h) ? rowl[(dir * l2 + h) * 32] : zero2;
+                    fl.y *= sg;
+                    const float4 wa = *reinterpret_cast<const float4 *>(wb + s * R);
+                    const float4 wc = *reinterpret_cast<const float4 *>(wb + s * R + 4);
+                    const float wv[R] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float2 b = win[r - s + R - 1];
+                        const float tx = wv[r] * fl.x, ty = wv[r] * fl.y;   // weight * f-hat_l
+                        acc[r].x = fmaf(tx, b.x, acc[r].x);
+                        acc[r].x = fmaf(-ty, b.y, acc[r].x);
+                        acc[r].y = fmaf(tx, b.y, acc[r].y);
+                        acc[r].y = fmaf(ty, b.x, acc[r].y);
+                    }
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float s, e;
+                two_sum(hi[r].x, acc[r].x, s, e);
+                hi[r].x = s;
+                lo[r].x += e;
+                two_sum(hi[r].y, acc[r].y, s, e);
+                hi[r].y = s;
+                lo[r].y += e;
+            }
+        }
+        if (tile * 32 + lane < n) {
+            float2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.k1 * M * 32 + lane;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int k2 = k20 + r;
+                if (k2 <= h) out[(k2 + h) * 32] = make_float2(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
+            }
+        }
+    }
+}
+
+size_t smem_bytes(const GridView &g, int wrow_max) {
+    return sizeof(float2) * (size_t)g.nhalf * 32 + sizeof(float) * (size_t)kWarps * 2 * wrow_max;
+}
+
+}  // namespace
+
+// Host part: weight streams and the task table, built once per modes handle.
+double beta_host(const bz_modes *m, const int *l, const int *mm);
 
 int modes_build_fp32_tables(bz_modes *m) {
     m->d_W32 = nullptr;
     m->w32_floats = 0;
     m->d_task = nullptr;
     m->ntask = 0;
+    const GridView &v = m->g->v;
+    if (v.dim != 2 || v.N > 32) return BZ_OK;           // generic kernel handles these
+    const int h = v.h;
+    const int nb = (v.M + R - 1) / R;
+    std::vector<TaskRec> tasks;
+    std::vector<float> W;
+    std::vector<double> cost;
+    for (int k1 = 0; k1 <= h; ++k1) {
+        for (int b = 0; b < nb; ++b) {
+            const int k20 = -h + R * b;
+            const int k2last = std::min(h, k20 + R - 1);
+            int lo = std::max(-h, k20 - h), hi = std::min(h, k2last + h);
+            int len = hi - lo + 1;
+            int npad = (len + R - 1) / R * R;
+            // place the padded range inside [-h, h] where possible
+            int l2lo = lo;
+            if (l2lo + npad - 1 > h) l2lo = std::max(-h - (R - 1), h - npad + 1);
+            TaskRec t;
+            t.k1 = k1;
+            t.b = b;
+            t.l1lo = k1 - h;
+            t.nl1 = k1 / 2 - (k1 - h) + 1;
+            t.l2lo = l2lo;
+            t.nblk = npad / R;
+            t.woff = (int)W.size();
+            t.pad = 0;
+            for (int i = 0; i < t.nl1; ++i) {
+                const int l1 = t.l1lo + i, m1 = k1 - l1;
+                for (int j = 0; j < npad; ++j) {
+                    const int l2 = l2lo + j;
+                    for (int r = 0; r < R; ++r) {
+                        const int k2 = k20 + r, m2 = k2 - l2;
+                        double w = 0.0;
+                        if (k2 <= h && l2 >= -h && l2 <= h && m2 >= -h && m2 <= h) {
+                            int l[2] = {l1, l2}, mm[2] = {m1, m2};
+                            w = beta_host(m, l, mm);
+                            if (l1 < m1) w += beta_host(m, mm, l);
+                        }
+                        W.push_back((float)w);
+                    }
+                }
+            }
+            tasks.push_back(t);
+            cost.push_back((double)t.nl1 * npad);
+        }
+    }
+    // longest-processing-time-first assignment of tasks to the warps of a CTA
+    std::vector<int> order(tasks.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> load(kWarps, 0.0);
+    std::vector<std::vector<int>> per(kWarps);
+    for (int i : order) {
+        int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[w] += cost[i];
+        per[w].push_back(i);
+    }
+    std::vector<int> tab(kWarps + 1 + tasks.size() * kTaskInts);
+    int pos = 0;
+    for (int w = 0; w < kWarps; ++w) {
+        tab[w] = pos;
+        for (int i : per[w]) {
+            std::memcpy(&tab[kWarps + 1 + (size_t)pos * kTaskInts], &tasks[i], sizeof(TaskRec));
+            ++pos;
+        }
+    }
+    tab[kWarps] = pos;
+    int wrow_max = 0;
+    for (auto &t : tasks) wrow_max = std::max(wrow_max, t.nblk * R * R);
+    cudaError_t e = cudaMalloc(&m->d_W32, sizeof(float) * W.size());
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_task, sizeof(int) * tab.size());
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_W32, W.data(), sizeof(float) * W.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_task, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->d_W32);
+        cudaFree(m->d_task);
+        m->d_W32 = nullptr;
+        m->d_task = nullptr;
+        return cuda_fail(e, "build_kernel_modes: FP32 weight stream");
+    }
+    m->w32_floats = (int64_t)W.size();
+    m->ntask = (int)tasks.size();
+    m->w32_rowmax = wrow_max;
     return BZ_OK;
 }
 
 bool modesum32_2d_available(const bz_modes *m) { return m->d_W32 != nullptr; }
 
-cudaError_t launch_modesum32_2d(const bz_modes *, const float2 *, float2 *, int64_t, cudaStream_t) {
-    return cudaErrorNotSupported;
+cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const GridView &v = m->g->v;
+    size_t sm = smem_bytes(v, m->w32_rowmax);
+    cudaError_t e = cudaFuncSetAttribute(modesum32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int64_t ntile = (n + 31) / 32;
+    modesum32_kernel<<<(unsigned)ntile, kWarps * 32, sm, st>>>(fhat, Qhat, m->d_W32, m->d_task, v.h, v.M,
+                                                             (int)v.nhalf, m->w32_rowmax, n);
+    return cudaGetLastError();
 }
 
 }  // namespace bz
