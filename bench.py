@@ -145,6 +145,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=CELLS, help="cells per GPU (small cases for ncu captures)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -163,7 +165,8 @@ def main():
 
     grid = bz.Grid(2, N_V, L_BOX)
     modes = bz.Modes(grid, GAMMA)
-    f_host = workloads.shifted_maxwellians(CELLS, 2, N_V, L_BOX, seed=SEED + rank).astype(np.float32)
+    cells = args.cells
+    f_host = workloads.shifted_maxwellians(cells, 2, N_V, L_BOX, seed=SEED + rank).astype(np.float32)
     f = torch.from_numpy(f_host).cuda()
     Q = torch.empty_like(f)
 
@@ -200,30 +203,49 @@ def main():
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
         ms = float(t.item())
-    value = CELLS * world / (ms / 1e3)
+    value = cells * world / (ms / 1e3)
 
     # dominant kernel: the mode sum
     ms_name = "modesum_f32" if "modesum_f32" in prof else "modesum_f32_generic"
     launches, ktot = prof.get(ms_name, (0, float("nan")))
     k_ms = ktot / max(1, launches)
-    flops_launch = 10.0 * modes.pairs_sym * CELLS
+    flops_launch = 10.0 * modes.pairs_sym * cells
     achieved = flops_launch / (k_ms / 1e3) / 1e12
     gpu_launches = sum(c for c, _ in prof.values())
 
     # FP64 plain form on the same workload
-    Q64 = torch.empty((CELLS, N_V * N_V), dtype=torch.float64, device="cuda")
-    f64 = f.double()
-    bz.collide_batch(modes, f64, Q64, precision="fp64")
-    torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(args.fp64_steps):
+    Q64 = None
+    value64 = ms64 = float("nan")
+    if args.fp64_steps > 0:
+        Q64 = torch.empty((cells, N_V * N_V), dtype=torch.float64, device="cuda")
+        f64 = f.double()
         bz.collide_batch(modes, f64, Q64, precision="fp64")
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms64 = e0.elapsed_time(e1) / args.fp64_steps
-    value64 = CELLS * world / (ms64 / 1e3)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.fp64_steps):
+            bz.collide_batch(modes, f64, Q64, precision="fp64")
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        value64 = cells * world / (ms64 / 1e3)
 
     # end to end: pinned host f -> device, collide, device -> pinned host Q
+    e2e_val = None
+    if not args.no_e2e:
+        e2e_val = _e2e(args, bz, modes, f_host, f, barrier, st, e0, e1, cells, world)
+
+    line = None
+    if rank == 0:
+        _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, value64, prof, ms_name, k_ms,
+                flops_launch, achieved, gpu_launches, e2e_val, clk)
+    if dist:
+        tdist.barrier()
+        tdist.destroy_process_group()
+    return 0
+
+
+def _e2e(args, bz, modes, f_host, f, barrier, st, e0, e1, cells, world):
+    import torch
     fh = torch.from_numpy(f_host).pin_memory()
     qh = torch.empty_like(fh).pin_memory()
     fd = torch.empty_like(f)
@@ -242,20 +264,25 @@ def main():
     e1.record(st)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    e2e_val = CELLS * world / (e2e_ms / 1e3)
+    return cells * world / (e2e_ms / 1e3)
 
-    line = None
-    if rank == 0:
+
+def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, value64, prof, ms_name, k_ms,
+            flops_launch, achieved, gpu_launches, e2e_val, clk):
+    import numpy as np
+    if True:
         # errors against the FP64 oracle on sampled cells (same FP32 inputs)
         import oracle
-        idx = np.linspace(0, CELLS - 1, 24).astype(int)
+        idx = np.linspace(0, cells - 1, 24).astype(int)
         fs = f_host[idx].astype(np.float64)
         k = oracle.Kernel(2, N_V, L_BOX, GAMMA)
         Qr = k.collide(fs)
         q32 = Q[idx].double().cpu().numpy()
-        q64 = Q64[idx].cpu().numpy()
         err32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(Qr))
-        err64 = float(np.linalg.norm(q64 - Qr) / np.linalg.norm(Qr))
+        err64 = None
+        if Q64 is not None:
+            q64 = Q64[idx].cpu().numpy()
+            err64 = float(np.linalg.norm(q64 - Qr) / np.linalg.norm(Qr))
         rho = fs.sum(1, keepdims=True) * k.dv ** 2
         loss32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(rho * fs))   # error / |loss rate ~ rho f|
         cpu = None
@@ -265,14 +292,15 @@ def main():
             "metric": METRIC, "value": value, "unit": "cell-collision evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells_per_gpu": CELLS, "N_v": N_V * N_V, "L": L_BOX,
+            "config": {"workload": WORKLOAD if cells == CELLS else WORKLOAD.replace(str(CELLS), str(cells)),
+                       "cells_per_gpu": cells, "N_v": N_V * N_V, "L": L_BOX,
                        "kernel": "VHS hard spheres (gamma=1, b0=1/(2pi))", "precision_form": "fp32",
                        "l2": "inputs and outputs (268 MB each) exceed L2: no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "rel_l2_err": {"fp32_vs_oracle": err32, "fp64_vs_oracle": err64, "fp32_loss_scaled": loss32,
                            "sample_cells": len(idx)},
             "fp64_form": {"value": value64, "unit": "cell-collision evals/s", "ms_per_step": ms64,
-                          "speedup_fp32_over_fp64": value / value64},
+                          "speedup_fp32_over_fp64": value / value64} if Q64 is not None else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": ms_name,
                          "kernel_ms": k_ms, "flops_per_launch": flops_launch,
@@ -280,15 +308,11 @@ def main():
             "kernel_times_ms": {k2: v[1] / max(1, v[0]) for k2, v in prof.items()},
             "gpu_launches": gpu_launches,
             "e2e": {"value": e2e_val, "unit": "cell-collision evals/s",
-                    "h2d_bytes_per_step": int(f.numel() * 4), "d2h_bytes_per_step": int(Q.numel() * 4)},
+                    "h2d_bytes_per_step": int(Q.numel() * 4), "d2h_bytes_per_step": int(Q.numel() * 4)},
             "clocks": clk,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
-    if dist:
-        tdist.barrier()
-        tdist.destroy_process_group()
-    return 0
 
 
 if __name__ == "__main__":

@@ -211,16 +211,28 @@ int collide_chain(const bz_modes *m, int precision, int flags, const void *f, vo
     Scratch s;
     BZ_TRY(s.alloc(2 * celem * sizeof(float2), st), "collide: scratch");
     float2 *fh = static_cast<float2 *>(s.p), *qh = fh + celem;
-    BZ_LAUNCH("dft_forward_f32", st, launch_dft_forward_f32(v, g->d_E32, static_cast<const float *>(f), fh, n, st),
-              "collide: forward DFT");
+    const bool tile = m->d_T1 != nullptr;
+    if (tile)
+        BZ_LAUNCH("dft_forward_f32", st,
+                  launch_dft32_forward_tile(v, m->d_T1, m->d_T2, static_cast<const float *>(f), fh, n, st),
+                  "collide: forward DFT");
+    else
+        BZ_LAUNCH("dft_forward_f32_generic", st,
+                  launch_dft_forward_f32(v, g->d_E32, static_cast<const float *>(f), fh, n, st),
+                  "collide: forward DFT");
     if (modesum32_2d_available(m))
         BZ_LAUNCH("modesum_f32", st, launch_modesum32_2d(m, fh, qh, n, st), "collide: mode sum");
     else
         BZ_LAUNCH("modesum_f32_generic", st, launch_modesum_generic_f32(v, m->d_F32, m->bcols, fh, qh, n, st),
                   "collide: mode sum");
-    BZ_LAUNCH("dft_inverse_f32", st,
-              launch_dft_inverse_f32(v, g->d_E32, qh, static_cast<float *>(Q), n, m->scale, g->cinv, ep, st),
-              "collide: inverse DFT");
+    if (tile)
+        BZ_LAUNCH("dft_inverse_f32", st,
+                  launch_dft32_inverse_tile(v, m->d_T2i, m->d_T3, qh, static_cast<float *>(Q), n, g->cinv, ep, st),
+                  "collide: inverse DFT");
+    else
+        BZ_LAUNCH("dft_inverse_f32_generic", st,
+                  launch_dft_inverse_f32(v, g->d_E32, qh, static_cast<float *>(Q), n, m->scale, g->cinv, ep, st),
+                  "collide: inverse DFT");
     return BZ_OK;
 }
 

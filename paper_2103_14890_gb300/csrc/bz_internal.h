@@ -58,6 +58,8 @@ struct bz_modes {
     int *d_task;         // task descriptors of the FP32 2-D kernel
     int ntask;
     int64_t pairs_sym;   // unordered pairs per cell (algorithmic unit)
+    // twiddle tables of the tile FP32 DFT kernels (k_dft32.cu), null if unused
+    float2 *d_T1, *d_T2, *d_T2i, *d_T3;
     double scale;        // s^(d + gamma)
 };
 
@@ -88,6 +90,15 @@ cudaError_t launch_dft_inverse_f64(const GridView &g, const double2 *E, const do
 cudaError_t launch_dft_inverse_f32(const GridView &g, const float2 *E, const float2 *Qhat,
                                    float *Q, int64_t n, double scale, const double *cinv,
                                    const InvEpilogue &ep, cudaStream_t st);
+
+// ---- tile FP32 DFT kernels (k_dft32.cu), 2-D, N in {16, 24, 32} -------------
+bool dft32_tile_supported(const GridView &g);
+int dft32_tables(const GridView &g, double scale, float2 **T1, float2 **T2, float2 **T2i, float2 **T3);
+cudaError_t launch_dft32_forward_tile(const GridView &g, const float2 *T1, const float2 *T2, const float *f,
+                                      float2 *fhat, int64_t n, cudaStream_t st);
+cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *T2i, const float2 *T3, const float2 *Qhat,
+                                      float *Q, int64_t n, const double *cinv, const InvEpilogue &ep,
+                                      cudaStream_t st);
 
 // ---- kernels (k_modesum.cu) -----------------------------------------------
 cudaError_t launch_modesum_generic_f64(const GridView &g, const double *F, int bcols,

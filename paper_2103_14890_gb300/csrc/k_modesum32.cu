@@ -37,8 +37,10 @@ constexpr int R = 8;            // outputs per thread along k_2
 constexpr int kWarps = 16;      // warps per CTA
 constexpr int kTaskInts = 8;    // ints per task record
 
+constexpr int kPad = 8;         // zero columns on each side of a shared-memory row
+
 struct TaskRec {
-    int k1, b, l1lo, nl1, l2lo, nblk, woff, pad;
+    int k1, k20, l1lo, nl1, l2lo, nblk, woff, rfirst;   // rfirst: first r this task stores
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -63,16 +65,67 @@ __device__ __forceinline__ void stage_row(float *dst, const float *src, int nflo
     cp_async_commit();
 }
 
+// One l_1 row of a task: acc[r] += sum_l2 w(l2, r) f-hat_l(l2) f-hat_m(k2_0 + r - l2).
+// DIR = +1: f-hat_l read from row l_1 at column l_2; DIR = -1 (l_1 < 0): the
+// conjugate of row -l_1 at column -l_2.  All columns lie inside the zero-padded
+// shared-memory row, so no load needs a bounds check (checked on the host).
+template <int DIR>
+__device__ __forceinline__ void row_pass(const float2 *__restrict__ rowl, const float2 *__restrict__ rowm,
+                                         const float *__restrict__ wrow, int nblk, int l2lo, int mbase0, int c0,
+                                         float2 (&acc)[R]) {
+    float2 win[2 * R - 1];
+    // columns are offset by c0 = h + kPad; a column c is element c * 32
+    const float2 *mp = rowm + (mbase0 + c0) * 32;
+    const float2 *lp = rowl + (DIR * l2lo + c0) * 32;
+#pragma unroll
+    for (int j = R; j < 2 * R - 1; ++j) win[j] = mp[j * 32];
+    for (int blk = 0; blk < nblk; ++blk) {
+        if (blk > 0) {
+#pragma unroll
+            for (int j = 2 * R - 2; j >= R; --j) win[j] = win[j - R];
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) win[j] = mp[j * 32];
+        const float *wb = wrow + blk * R * R;
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            const float2 fl = lp[DIR * s * 32];
+            const float4 wa = *reinterpret_cast<const float4 *>(wb + s * R);
+            const float4 wc = *reinterpret_cast<const float4 *>(wb + s * R + 4);
+            const float wv[R] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float2 b = win[r - s + R - 1];
+                const float tx = wv[r] * fl.x;
+                const float ty = (DIR > 0) ? wv[r] * fl.y : -(wv[r] * fl.y);   // weight * f-hat_l
+                acc[r].x = fmaf(tx, b.x, acc[r].x);
+                acc[r].x = fmaf(-ty, b.y, acc[r].x);
+                acc[r].y = fmaf(tx, b.y, acc[r].y);
+                acc[r].y = fmaf(ty, b.x, acc[r].y);
+            }
+        }
+        mp -= R * 32;              // next block: m_2 window moves down by R
+        lp += DIR * R * 32;        // l_2 moves up by R
+    }
+}
+
 __global__ void __launch_bounds__(kWarps * 32, 1)
 modesum32_kernel(const float2 *__restrict__ fhat, float2 *__restrict__ Qhat, const float *__restrict__ W,
                  const int *__restrict__ tasks, int h, int M, int nhalf, int wrow_max, int64_t n) {
     extern __shared__ __align__(16) float4 smem4[];
-    float2 *Fs = reinterpret_cast<float2 *>(smem4);                  // [nhalf][32]
-    float *wsm = reinterpret_cast<float *>(Fs + (size_t)nhalf * 32);   // [warps][2][wrow_max]
+    const int MP = M + 2 * kPad;                                     // padded row length
+    float2 *Fs = reinterpret_cast<float2 *>(smem4);                  // [h+1][MP][32]
+    float *wsm = reinterpret_cast<float *>(Fs + (size_t)(h + 1) * MP * 32);   // [warps][2][wrow_max]
     const int64_t tile = blockIdx.x;
     {
+        // copy the tile's half spectrum into zero-padded rows
         const float4 *src = reinterpret_cast<const float4 *>(fhat + tile * (int64_t)nhalf * 32);
-        for (int i = threadIdx.x; i < nhalf * 16; i += blockDim.x) smem4[i] = src[i];
+        const int rowq = MP * 16;                                    // float4 per padded row
+        for (int i = threadIdx.x; i < (h + 1) * rowq; i += blockDim.x) {
+            const int row = i / rowq, q = i % rowq;
+            const int col = q / 16 - kPad;                           // unpadded column
+            smem4[i] = (col >= 0 && col < M) ? src[(row * M + col) * 16 + (q % 16)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -81,19 +134,18 @@ modesum32_kernel(const float2 *__restrict__ fhat, float2 *__restrict__ Qhat, con
     const int tbeg = tasks[warp], tend = tasks[warp + 1];
     const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + kWarps + 1);
     const float2 *Fl = Fs + lane;
-    const float2 zero2 = make_float2(0.f, 0.f);
+    const int c0 = h + kPad;
 
     for (int t = tbeg; t < tend; ++t) {
         const TaskRec tk = trec[t];
-        const int k20 = -h + R * tk.b;
         const int rowf = tk.nblk * R * R;                 // floats per l_1 row
         const float *wsrc = W + tk.woff;
-        float2 hi[R], lo[R];
+        float2 hi[R], lo[R], acc[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) hi[r] = lo[r] = zero2;
+        for (int r = 0; r < R; ++r) hi[r] = lo[r] = acc[r] = make_float2(0.f, 0.f);
         stage_row(wbuf0, wsrc, rowf, lane);
         for (int i = 0; i < tk.nl1; ++i) {
-            float *wcur = (i & 1) ? wbuf1 : wbuf0;
+            const float *wcur = (i & 1) ? wbuf1 : wbuf0;
             if (i + 1 < tk.nl1) {
                 stage_row((i & 1) ? wbuf0 : wbuf1, wsrc + (size_t)(i + 1) * rowf, rowf, lane);
                 cp_async_wait<1>();
@@ -103,77 +155,41 @@ modesum32_kernel(const float2 *__restrict__ fhat, float2 *__restrict__ Qhat, con
             __syncwarp();
             const int l1 = tk.l1lo + i;
             const int m1 = tk.k1 - l1;                    // >= 0: stored row
-            const int dir = l1 < 0 ? -1 : 1;              // f-hat_l = conj(f-hat_{-l}) for l1 < 0
-            const float sg = (float)dir;
-            const float2 *rowl = Fl + (size_t)(dir * l1) * M * 32;
-            const float2 *rowm = Fl + (size_t)m1 * M * 32;
-            float2 acc[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = zero2;
-            float2 win[2 * R - 1];
-            for (int blk = 0; blk < tk.nblk; ++blk) {
-                const int l2b = tk.l2lo + blk * R;
-                const int mbase = k20 - l2b - (R - 1);    // m_2 of win[0]
-                if (blk == 0) {
-#pragma unroll
-                    for (int j = R; j < 2 * R - 1; ++j) {
-                        const int m2 = mbase + j;
-                        win[j] = (m2 >= -h && m2 <= h) ? rowm[(m2 + h) * 32] : zero2;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 2 * R - 2; j >= R; --j) win[j] = win[j - R];
-                }
-#pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const int m2 = mbase + j;
-                    win[j] = (m2 >= -h && m2 <= h) ? rowm[(m2 + h) * 32] : zero2;
-                }
-                const float *wb = wcur + blk * R * R;
-#pragma unroll
-                for (int s = 0; s < R; ++s) {
-                    const int l2 = l2b + s;
-                    float2 fl = (l2 >= -h && l2 <= h) ? rowl[(dir * l2 + h) * 32] : zero2;
-                    fl.y *= sg;
-                    const float4 wa = *reinterpret_cast<const float4 *>(wb + s * R);
-                    const float4 wc = *reinterpret_cast<const float4 *>(wb + s * R + 4);
-                    const float wv[R] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float2 b = win[r - s + R - 1];
-                        const float tx = wv[r] * fl.x, ty = wv[r] * fl.y;   // weight * f-hat_l
-                        acc[r].x = fmaf(tx, b.x, acc[r].x);
-                        acc[r].x = fmaf(-ty, b.y, acc[r].x);
-                        acc[r].y = fmaf(tx, b.y, acc[r].y);
-                        acc[r].y = fmaf(ty, b.x, acc[r].y);
-                    }
-                }
-            }
+            const int mbase0 = tk.k20 - tk.l2lo - (R - 1);
+            const float2 *rowm = Fl + (size_t)m1 * MP * 32;
+            if (l1 >= 0)
+                row_pass<1>(Fl + (size_t)l1 * MP * 32, rowm, wcur, tk.nblk, tk.l2lo, mbase0, c0, acc);
+            else
+                row_pass<-1>(Fl + (size_t)(-l1) * MP * 32, rowm, wcur, tk.nblk, tk.l2lo, mbase0, c0, acc);
             __syncwarp();
+            // fold the FP32 row sums into (hi, lo) every second row and after the last
+            if ((i & 1) || i + 1 == tk.nl1) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float s, e;
-                two_sum(hi[r].x, acc[r].x, s, e);
-                hi[r].x = s;
-                lo[r].x += e;
-                two_sum(hi[r].y, acc[r].y, s, e);
-                hi[r].y = s;
-                lo[r].y += e;
+                for (int r = 0; r < R; ++r) {
+                    float s, e;
+                    two_sum(hi[r].x, acc[r].x, s, e);
+                    hi[r].x = s;
+                    lo[r].x += e;
+                    two_sum(hi[r].y, acc[r].y, s, e);
+                    hi[r].y = s;
+                    lo[r].y += e;
+                    acc[r] = make_float2(0.f, 0.f);
+                }
             }
         }
         if (tile * 32 + lane < n) {
             float2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.k1 * M * 32 + lane;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int k2 = k20 + r;
-                if (k2 <= h) out[(k2 + h) * 32] = make_float2(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
+                const int k2 = tk.k20 + r;
+                if (r >= tk.rfirst && k2 <= h) out[(k2 + h) * 32] = make_float2(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
             }
         }
     }
 }
 
 size_t smem_bytes(const GridView &g, int wrow_max) {
-    return sizeof(float2) * (size_t)g.nhalf * 32 + sizeof(float) * (size_t)kWarps * 2 * wrow_max;
+    return sizeof(float2) * (size_t)(g.h + 1) * (g.M + 2 * kPad) * 32 + sizeof(float) * (size_t)kWarps * 2 * wrow_max;
 }
 
 }  // namespace
@@ -187,31 +203,46 @@ int modes_build_fp32_tables(bz_modes *m) {
     m->d_task = nullptr;
     m->ntask = 0;
     const GridView &v = m->g->v;
-    if (v.dim != 2 || v.N > 32) return BZ_OK;           // generic kernel handles these
+    if (v.dim != 2 || v.N > 32 || v.M < R) return BZ_OK;     // the generic kernel handles these
     const int h = v.h;
     const int nb = (v.M + R - 1) / R;
+    const int lo_col = -h - kPad, hi_col = h + kPad;         // addressable padded columns
     std::vector<TaskRec> tasks;
     std::vector<float> W;
     std::vector<double> cost;
     for (int k1 = 0; k1 <= h; ++k1) {
+        int prev_end = -h - 1;
         for (int b = 0; b < nb; ++b) {
-            const int k20 = -h + R * b;
-            const int k2last = std::min(h, k20 + R - 1);
-            int lo = std::max(-h, k20 - h), hi = std::min(h, k2last + h);
-            int len = hi - lo + 1;
-            int npad = (len + R - 1) / R * R;
-            // place the padded range inside [-h, h] where possible
-            int l2lo = lo;
-            if (l2lo + npad - 1 > h) l2lo = std::max(-h - (R - 1), h - npad + 1);
+            // blocks of R consecutive k2; the last one ends at h (it may overlap the
+            // previous block, whose outputs it then does not store)
+            const int k20 = std::min(-h + R * b, h - R + 1);
+            const int k2last = k20 + R - 1;
+            const int lo = std::max(-h, k20 - h), hi = std::min(h, k2last + h);
+            const int len = hi - lo + 1;
+            const int npad = (len + R - 1) / R * R;
+            // choose the padded l2 range so that every l2 and every k2 - l2 stays
+            // inside the zero-padded row
+            int l2lo = lo - (npad - len);
+            bool placed = false;
+            for (int cand = lo - (npad - len); cand <= lo; ++cand) {
+                const int last = cand + npad - 1;
+                if (cand < lo_col || last > hi_col) continue;
+                if (k20 - last < lo_col || k2last - cand > hi_col) continue;
+                l2lo = cand;
+                placed = true;
+                break;
+            }
+            if (!placed) return BZ_OK;                       // grid not covered by the padded layout
             TaskRec t;
             t.k1 = k1;
-            t.b = b;
+            t.k20 = k20;
             t.l1lo = k1 - h;
             t.nl1 = k1 / 2 - (k1 - h) + 1;
             t.l2lo = l2lo;
             t.nblk = npad / R;
             t.woff = (int)W.size();
-            t.pad = 0;
+            t.rfirst = std::max(0, prev_end + 1 - k20);
+            prev_end = k2last;
             for (int i = 0; i < t.nl1; ++i) {
                 const int l1 = t.l1lo + i, m1 = k1 - l1;
                 for (int j = 0; j < npad; ++j) {
@@ -255,6 +286,7 @@ int modes_build_fp32_tables(bz_modes *m) {
     tab[kWarps] = pos;
     int wrow_max = 0;
     for (auto &t : tasks) wrow_max = std::max(wrow_max, t.nblk * R * R);
+    if (smem_bytes(v, wrow_max) > 227 * 1024) return BZ_OK;   // does not fit: generic kernel
     cudaError_t e = cudaMalloc(&m->d_W32, sizeof(float) * W.size());
     if (e == cudaSuccess) e = cudaMalloc(&m->d_task, sizeof(int) * tab.size());
     if (e == cudaSuccess) e = cudaMemcpy(m->d_W32, W.data(), sizeof(float) * W.size(), cudaMemcpyHostToDevice);
