@@ -65,6 +65,7 @@ def load(path=None):
             "bz_grid_destroy": ([c_p], None),
             "bz_modes_destroy": ([c_p], None),
             "bz_profile": ([c_i], c_i),
+            "collide_batch_noalloc": ([c_p, c_i, c_i, c_p, c_p, c_i64, c_p], c_i),
             "bz_profile_read": ([c_p, c_i, c_p, c_p, c_i], c_i),
         }
         for name, (args, res) in sig.items():
@@ -161,6 +162,20 @@ def collide_batch(modes, f, Q=None, precision="fp32", conserve=False, check_inpu
         raise ValueError("f must have n_cells * N^d elements")
     _check(load().collide_batch(modes._h, PRECISION[precision], flags, _dptr(f, dt, "f"), _dptr(Q, dt, "Q"),
                                 n, _stream(stream)))
+    return Q
+
+
+def collide_batch_noalloc(modes, f, Q=None, precision="fp32", conserve=False, stream=None):
+    """Q(f) through the allocation-free entry point (bounded batch, see the header)."""
+    import torch
+    dt = _dtype(precision)
+    if Q is None:
+        Q = torch.empty_like(f)
+    n = f.shape[0] if f.dim() > 1 else 1
+    if f.numel() != n * modes.nv:
+        raise ValueError("f must have n_cells * N^d elements")
+    _check(load().collide_batch_noalloc(modes._h, PRECISION[precision], CONSERVE if conserve else 0,
+                                        _dptr(f, dt, "f"), _dptr(Q, dt, "Q"), n, _stream(stream)))
     return Q
 
 
