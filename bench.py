@@ -147,6 +147,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", type=int, default=CELLS, help="cells per GPU (small cases for ncu captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the IMEX-step and grouped-batch measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -229,6 +230,11 @@ def main():
         ms64 = e0.elapsed_time(e1) / args.fp64_steps
         value64 = cells * world / (ms64 / 1e3)
 
+    extra = {}
+    if not args.no_extra:
+        extra["imex_step"] = _imex_measure(bz, workloads, barrier)
+        extra["grouped"] = _group_measure(bz, workloads, barrier)
+
     # end to end: pinned host f -> device, collide, device -> pinned host Q
     e2e_val = None
     if not args.no_e2e:
@@ -237,7 +243,7 @@ def main():
     line = None
     if rank == 0:
         _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, value64, prof, ms_name, k_ms,
-                flops_launch, achieved, gpu_launches, e2e_val, clk)
+                flops_launch, achieved, gpu_launches, e2e_val, clk, extra)
     if dist:
         tdist.barrier()
         tdist.destroy_process_group()
@@ -267,11 +273,72 @@ def _e2e(args, bz, modes, f_host, f, barrier, st, e0, e1, cells, world):
     return cells * world / (e2e_ms / 1e3)
 
 
+def _timed(fn, steps, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _imex_measure(bz, workloads, barrier):
+    """One ARS(2,2,2) step on the ~19.6k-cell triangulated Sod-like mesh
+    (32x32 grid on [-10,10]^2, VHS, eps = 5e-3, dt = h / (2 max|v|)), FP32 and
+    FP64, the step captured as a CUDA graph (non-default stream)."""
+    import math
+    import torch
+    f, hmesh = workloads.sod_cells(32, 10.0)
+    dt = 0.5 * hmesh / (math.sqrt(2.0) * 10.0)
+    m = bz.Modes(bz.Grid(2, 32, 10.0), 1.0)
+    s = torch.cuda.Stream()
+    out = {}
+    with torch.cuda.stream(s):
+        for prec, steps in (("fp32", 10), ("fp64", 1)):
+            x = torch.from_numpy(f).to("cuda", torch.float32 if prec == "fp32" else torch.float64)
+            y = torch.empty_like(x)
+            for _ in range(2):
+                bz.imex_step(m, x, dt, 5e-3, f_out=y, precision=prec, stream=s)
+            bz.check(s)
+            ms = _timed(lambda: bz.imex_step(m, x, dt, 5e-3, f_out=y, precision=prec, stream=s), steps, s)
+            out[prec] = {"ms_per_step": ms, "cell_collision_evals_per_s": 2 * x.shape[0] / (ms / 1e3)}
+    out["cells"] = int(f.shape[0])
+    out["workload"] = "ARS(2,2,2) step, %d-cell Delaunay mesh, 32x32 grid, VHS, eps=5e-3, dt=%.3g, CUDA graph" % (
+        f.shape[0], dt)
+    return out
+
+
+def _group_measure(bz, workloads, barrier):
+    """Heterogeneous batch in one group_collide call: 8 instances with cell
+    counts log-uniform in [1e3, 5e4] and N in {16, 24, 32, 48}, plus two 3-D
+    16^3 instances of 1000 cells (FP32)."""
+    import torch
+    items = workloads.grouped_instances()
+    entries = []
+    grids = {}
+    total = 0
+    for it in items:
+        key = (it["dim"], it["N"])
+        if key not in grids:
+            grids[key] = bz.Modes(bz.Grid(it["dim"], it["N"], it["L"]), 1.0)
+        f = workloads.bi_maxwellian(it["n_cells"], it["dim"], it["N"], it["L"], seed=it["seed"]).astype("float32")
+        x = torch.from_numpy(f).cuda()
+        entries.append((grids[key], x, torch.empty_like(x)))
+        total += it["n_cells"]
+    s = torch.cuda.current_stream()
+    bz.group_collide(entries, precision="fp32")
+    bz.check()
+    ms = _timed(lambda: bz.group_collide(entries, precision="fp32"), 1, s)
+    return {"ms_per_call": ms, "cells": total, "cell_collision_evals_per_s": total / (ms / 1e3),
+            "instances": [(it["dim"], it["N"], it["n_cells"]) for it in items]}
+
+
 def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, value64, prof, ms_name, k_ms,
-            flops_launch, achieved, gpu_launches, e2e_val, clk):
+            flops_launch, achieved, gpu_launches, e2e_val, clk, extra):
     import numpy as np
-    if True:
-        # errors against the FP64 oracle on sampled cells (same FP32 inputs)
+    if True:   # errors against the FP64 oracle on sampled cells (same FP32 inputs)
         import oracle
         idx = np.linspace(0, cells - 1, 24).astype(int)
         fs = f_host[idx].astype(np.float64)
@@ -307,6 +374,8 @@ def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, valu
                          "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
             "kernel_times_ms": {k2: v[1] / max(1, v[0]) for k2, v in prof.items()},
             "gpu_launches": gpu_launches,
+            "imex_step": extra.get("imex_step"),
+            "grouped": extra.get("grouped"),
             "e2e": {"value": e2e_val, "unit": "cell-collision evals/s",
                     "h2d_bytes_per_step": int(Q.numel() * 4), "d2h_bytes_per_step": int(Q.numel() * 4)},
             "clocks": clk,

@@ -148,10 +148,37 @@ int imex_stage_local(const bz_modes *m, int scheme, int stage, int model, double
 /* imex_step -- all stages of one IMEX step (the schemes are stiffly accurate,
  * so f^{n+1} is the last stage value): f_out = step(f_n).  Stage buffers are
  * library scratch.  L_res as above (NULL = homogeneous step).
+ * On a non-default stream that is not being captured, the first call with a
+ * given argument set (pointers, n_cells, dt, eps, scheme, model, precision,
+ * flags) captures the whole step into a CUDA graph with its own scratch
+ * (cudaMalloc, once); later calls with the same arguments replay it with one
+ * cudaGraphLaunch.  Up to 8 such graphs are cached (least recently used
+ * dropped); destroying the modes handle drops its graphs.  On the legacy
+ * stream, or inside a caller's capture, the kernels are launched directly.
  * Errors: as collide_batch. */
 int imex_step(const bz_modes *m, int scheme, int model, double dt, double eps,
               const void *f_n, void *f_out, const void *L_res, int64_t n_cells,
               int precision, int flags, void *stream);
+
+/* group_collide -- one collision evaluation for several independent instances
+ * (each its own grid N / dimension / kernel and cell batch) in one call.  The
+ * forward DFTs run per instance; the mode sums of all BZ_FP32 2-D instances with
+ * N <= 32 share one launch of the register-blocked kernel (up to 16 instances
+ * per launch), scheduled longest-first by per-cell work; other instances use the
+ * generic kernel; then the inverse DFTs.  Results equal collide_batch on each
+ * instance.
+ *   items     : n_items descriptors; item.modes must belong to the current
+ *               device; item.f / item.Q are device arrays [n_cells][N^d]
+ *   precision : BZ_FP32 or BZ_FP64 (all items alike)
+ *   flags     : BZ_CONSERVE | BZ_CHECK_INPUT, applied to every item
+ * Errors: as collide_batch. */
+typedef struct bz_group_item {
+    const bz_modes *modes;
+    const void *f;
+    void *Q;
+    int64_t n_cells;
+} bz_group_item;
+int group_collide(const bz_group_item *items, int n_items, int precision, int flags, void *stream);
 
 /* bz_check -- synchronise `stream`, read and clear the device error word.
  * Returns BZ_OK, BZ_ENONFINITE, BZ_ETIMEOUT or BZ_ECUDA. */

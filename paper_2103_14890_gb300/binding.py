@@ -66,6 +66,7 @@ def load(path=None):
             "bz_modes_destroy": ([c_p], None),
             "bz_profile": ([c_i], c_i),
             "collide_batch_noalloc": ([c_p, c_i, c_i, c_p, c_p, c_i64, c_p], c_i),
+            "group_collide": ([c_p, c_i, c_i, c_i, c_p], c_i),
             "bz_profile_read": ([c_p, c_i, c_p, c_p, c_i], c_i),
         }
         for name, (args, res) in sig.items():
@@ -177,6 +178,28 @@ def collide_batch_noalloc(modes, f, Q=None, precision="fp32", conserve=False, st
     _check(load().collide_batch_noalloc(modes._h, PRECISION[precision], CONSERVE if conserve else 0,
                                         _dptr(f, dt, "f"), _dptr(Q, dt, "Q"), n, _stream(stream)))
     return Q
+
+
+class GroupItem(ctypes.Structure):
+    _fields_ = [("modes", ctypes.c_void_p), ("f", ctypes.c_void_p), ("Q", ctypes.c_void_p),
+                ("n_cells", ctypes.c_int64)]
+
+
+def group_collide(entries, precision="fp32", conserve=False, check_input=False, stream=None):
+    """entries: list of (modes, f, Q) with device tensors; one call for all."""
+    dt = _dtype(precision)
+    arr = (GroupItem * len(entries))()
+    for i, (m, f, Q) in enumerate(entries):
+        n = f.shape[0] if f.dim() > 1 else 1
+        if f.numel() != n * m.nv or Q.numel() != f.numel():
+            raise ValueError("item %d: f and Q must have n_cells * N^d elements" % i)
+        arr[i].modes = m._h
+        arr[i].f = _dptr(f, dt, "f")
+        arr[i].Q = _dptr(Q, dt, "Q")
+        arr[i].n_cells = n
+    flags = (CONSERVE if conserve else 0) | (CHECK_INPUT if check_input else 0)
+    _check(load().group_collide(ctypes.cast(arr, ctypes.c_void_p), len(entries), PRECISION[precision], flags,
+                                _stream(stream)))
 
 
 def imex_stage_local(modes, stage, f_n, F, G, P, dt, eps, scheme="ars222", model="boltzmann",

@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -29,9 +30,6 @@ void grid_destroy(bz_grid *g);
 int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **out);
 void modes_destroy(bz_modes *m);
 double beta_host(const bz_modes *m, const int *l, const int *mm);
-cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n,
-                                cudaStream_t st);   // k_modesum32.cu
-bool modesum32_2d_available(const bz_modes *m);
 
 namespace {
 
@@ -102,11 +100,13 @@ std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<ProfRec> g_prof;
 
+thread_local bool t_capturing = false;     // inside the library's own stream capture
+
 struct ProfScope {
     ProfRec r{nullptr, nullptr, nullptr};
     cudaStream_t st;
     ProfScope(const char *name, cudaStream_t s) : st(s) {
-        if (!g_prof_on) return;
+        if (!g_prof_on || t_capturing) return;
         if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
         r.name = name;
         cudaEventRecord(r.a, st);
@@ -184,56 +184,95 @@ int check_modes(const bz_modes *m, int precision, const char *who) {
     return BZ_OK;
 }
 
-// Q (or G = Q - P when P != nullptr) of n cells: forward DFT, mode sum, inverse DFT.
-int collide_chain(const bz_modes *m, int precision, int flags, const void *f, void *Q, const void *P,
-                  int64_t n, cudaStream_t st) {
+
+// The three phases of one collision evaluation over n cells, with the Fourier
+// scratch fh (forward spectra) and qh (mode sums) in the tiled layout.
+int phase_forward(const bz_modes *m, int precision, const void *f, void *fh, int64_t n, cudaStream_t st) {
     const bz_grid *g = m->g;
     const GridView &v = g->v;
-    const int64_t ntile = (n + kTile - 1) / kTile;
-    const size_t celem = (size_t)ntile * v.nhalf * kTile;
+    if (precision == BZ_FP64) {
+        BZ_LAUNCH("dft_forward_f64", st,
+                  launch_dft_forward_f64(v, g->d_E64, static_cast<const double *>(f), static_cast<double2 *>(fh), n, st),
+                  "collide: forward DFT");
+    } else if (m->d_T1) {
+        BZ_LAUNCH("dft_forward_f32", st,
+                  launch_dft32_forward_tile(v, m->d_T1, m->d_T2, static_cast<const float *>(f),
+                                            static_cast<float2 *>(fh), n, st),
+                  "collide: forward DFT");
+    } else {
+        BZ_LAUNCH("dft_forward_f32_generic", st,
+                  launch_dft_forward_f32(v, g->d_E32, static_cast<const float *>(f), static_cast<float2 *>(fh), n, st),
+                  "collide: forward DFT");
+    }
+    return BZ_OK;
+}
+
+int phase_modesum(const bz_modes *m, int precision, const void *fh, void *qh, int64_t n, cudaStream_t st) {
+    const GridView &v = m->g->v;
+    if (precision == BZ_FP64) {
+        BZ_LAUNCH("modesum_f64", st,
+                  launch_modesum_generic_f64(v, m->d_F64, m->bcols, static_cast<const double2 *>(fh),
+                                             static_cast<double2 *>(qh), n, st),
+                  "collide: mode sum");
+    } else if (modesum32_2d_available(m)) {
+        BZ_LAUNCH("modesum_f32", st,
+                  launch_modesum32_2d(m, static_cast<const float2 *>(fh), static_cast<float2 *>(qh), n, st),
+                  "collide: mode sum");
+    } else {
+        BZ_LAUNCH("modesum_f32_generic", st,
+                  launch_modesum_generic_f32(v, m->d_F32, m->bcols, static_cast<const float2 *>(fh),
+                                             static_cast<float2 *>(qh), n, st),
+                  "collide: mode sum");
+    }
+    return BZ_OK;
+}
+
+int phase_inverse(const bz_modes *m, int precision, int flags, const void *qh, void *Q, const void *P, int64_t n,
+                  cudaStream_t st) {
+    const bz_grid *g = m->g;
+    const GridView &v = g->v;
     InvEpilogue ep;
     ep.conserve = (flags & BZ_CONSERVE) ? 1 : 0;
     ep.check = 0;
     ep.P = P;
     if (precision == BZ_FP64) {
-        Scratch s;
-        BZ_TRY(s.alloc(2 * celem * sizeof(double2), st), "collide: scratch");
-        double2 *fh = static_cast<double2 *>(s.p), *qh = fh + celem;
-        BZ_LAUNCH("dft_forward_f64", st, launch_dft_forward_f64(v, g->d_E64, static_cast<const double *>(f), fh, n, st),
-                  "collide: forward DFT");
-        BZ_LAUNCH("modesum_f64", st, launch_modesum_generic_f64(v, m->d_F64, m->bcols, fh, qh, n, st),
-                  "collide: mode sum");
         BZ_LAUNCH("dft_inverse_f64", st,
-                  launch_dft_inverse_f64(v, g->d_E64, qh, static_cast<double *>(Q), n, m->scale, g->cinv, ep, st),
+                  launch_dft_inverse_f64(v, g->d_E64, static_cast<const double2 *>(qh), static_cast<double *>(Q), n,
+                                         m->scale, g->cinv, ep, st),
                   "collide: inverse DFT");
-        return BZ_OK;
-    }
-    Scratch s;
-    BZ_TRY(s.alloc(2 * celem * sizeof(float2), st), "collide: scratch");
-    float2 *fh = static_cast<float2 *>(s.p), *qh = fh + celem;
-    const bool tile = m->d_T1 != nullptr;
-    if (tile)
-        BZ_LAUNCH("dft_forward_f32", st,
-                  launch_dft32_forward_tile(v, m->d_T1, m->d_T2, static_cast<const float *>(f), fh, n, st),
-                  "collide: forward DFT");
-    else
-        BZ_LAUNCH("dft_forward_f32_generic", st,
-                  launch_dft_forward_f32(v, g->d_E32, static_cast<const float *>(f), fh, n, st),
-                  "collide: forward DFT");
-    if (modesum32_2d_available(m))
-        BZ_LAUNCH("modesum_f32", st, launch_modesum32_2d(m, fh, qh, n, st), "collide: mode sum");
-    else
-        BZ_LAUNCH("modesum_f32_generic", st, launch_modesum_generic_f32(v, m->d_F32, m->bcols, fh, qh, n, st),
-                  "collide: mode sum");
-    if (tile)
+    } else if (m->d_T1) {
         BZ_LAUNCH("dft_inverse_f32", st,
-                  launch_dft32_inverse_tile(v, m->d_T2i, m->d_T3, qh, static_cast<float *>(Q), n, g->cinv, ep, st),
+                  launch_dft32_inverse_tile(v, m->d_T2i, m->d_T3, static_cast<const float2 *>(qh),
+                                            static_cast<float *>(Q), n, g->cinv, ep, st),
                   "collide: inverse DFT");
-    else
+    } else {
         BZ_LAUNCH("dft_inverse_f32_generic", st,
-                  launch_dft_inverse_f32(v, g->d_E32, qh, static_cast<float *>(Q), n, m->scale, g->cinv, ep, st),
+                  launch_dft_inverse_f32(v, g->d_E32, static_cast<const float2 *>(qh), static_cast<float *>(Q), n,
+                                         m->scale, g->cinv, ep, st),
                   "collide: inverse DFT");
+    }
     return BZ_OK;
+}
+
+// Bytes of Fourier scratch one collision evaluation over n cells needs.
+size_t collide_scratch_bytes(const bz_modes *m, int precision, int64_t n) {
+    const int64_t ntile = (n + kTile - 1) / kTile;
+    const size_t celem = (size_t)ntile * m->g->v.nhalf * kTile;
+    return 2 * celem * (precision == BZ_FP64 ? sizeof(double2) : sizeof(float2));
+}
+
+// Q (or G = Q - P when P != nullptr) of n cells: forward DFT, mode sum, inverse DFT.
+// Scratch: `ext` if given (collide_scratch_bytes), else the stream-ordered pool.
+int collide_chain(const bz_modes *m, int precision, int flags, const void *f, void *Q, const void *P,
+                  int64_t n, cudaStream_t st, void *ext = nullptr) {
+    const size_t bytes = collide_scratch_bytes(m, precision, n);
+    Scratch s;
+    if (!ext) BZ_TRY(s.alloc(bytes, st), "collide: scratch");
+    char *fh = static_cast<char *>(ext ? ext : s.p), *qh = fh + bytes / 2;
+    int rc = phase_forward(m, precision, f, fh, n, st);
+    if (!rc) rc = phase_modesum(m, precision, fh, qh, n, st);
+    if (!rc) rc = phase_inverse(m, precision, flags, qh, Q, P, n, st);
+    return rc;
 }
 
 int check_input(int precision, const void *f, int64_t count, cudaStream_t st) {
@@ -248,7 +287,7 @@ int check_input(int precision, const void *f, int64_t count, cudaStream_t st) {
 // One IMEX stage: F_l, P_l by the stage kernel, then G_l = Q(F_l) - P_l.
 int run_stage(const bz_modes *m, const Tableau &t, int l, int model, double dt, double eps, const void *f_n,
               void *F_l, void *G, void *P, const void *L_res, int64_t n, int precision, int flags,
-              cudaStream_t st) {
+              cudaStream_t st, void *ext = nullptr) {
     const GridView &v = m->g->v;
     StageCoef c;
     memset(&c, 0, sizeof c);
@@ -281,10 +320,78 @@ int run_stage(const bz_modes *m, const Tableau &t, int l, int model, double dt, 
         if (t.At[q][l] != 0.0) needG = true;
     char *Gl = static_cast<char *>(G) + (size_t)l * stride * es;
     const char *Pl = static_cast<const char *>(P) + (size_t)l * stride * es;
-    if (model == BZ_BOLTZMANN && needG) return collide_chain(m, precision, flags, F_l, Gl, Pl, n, st);
+    if (model == BZ_BOLTZMANN && needG) return collide_chain(m, precision, flags, F_l, Gl, Pl, n, st, ext);
     e = launch_fill_zero(Gl, (int64_t)(stride * es), st);
     if (e != cudaSuccess) return cuda_fail(e, "imex stage: zero G");
     return BZ_OK;
+}
+
+// ---- CUDA-graph cache of imex_step ----
+// One captured graph per distinct argument set (pointers, sizes, dt, eps,
+// scheme, model, precision, flags); each entry owns its scratch, allocated
+// once outside the capture.  Replays cost one cudaGraphLaunch.
+struct StepKey {
+    const bz_modes *m;
+    int scheme, model, precision, flags, device;
+    double dt, eps;
+    const void *fn, *fout, *L;
+    int64_t n;
+    bool operator==(const StepKey &o) const {
+        return m == o.m && scheme == o.scheme && model == o.model && precision == o.precision && flags == o.flags &&
+               device == o.device && dt == o.dt && eps == o.eps && fn == o.fn && fout == o.fout && L == o.L &&
+               n == o.n;
+    }
+};
+struct StepGraph {
+    StepKey key;
+    cudaGraphExec_t exec;
+    void *scratch;
+    uint64_t stamp;
+};
+constexpr size_t kMaxGraphs = 8;
+std::mutex g_graph_mu;
+std::vector<StepGraph> g_graphs;
+uint64_t g_graph_clock = 0;
+
+void drop_graph(StepGraph &e) {
+    cudaGraphExecDestroy(e.exec);
+    cudaFree(e.scratch);
+}
+
+void purge_graphs(const bz_modes *m) {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (size_t i = 0; i < g_graphs.size();) {
+        if (g_graphs[i].key.m == m) {
+            drop_graph(g_graphs[i]);
+            g_graphs.erase(g_graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+// The stage sequence of one step with all scratch at `scratch`.
+int step_sequence(const bz_modes *m, const Tableau &t, int model, double dt, double eps, const void *f_n,
+                  void *f_out, const void *L_res, int64_t n, int precision, int flags, cudaStream_t st,
+                  void *scratch) {
+    const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
+    const int64_t stride = n * m->g->v.nv;
+    char *G = static_cast<char *>(scratch);
+    char *P = G + (size_t)t.s * stride * es;
+    char *Fbuf = P + (size_t)t.s * stride * es;
+    char *coll = Fbuf + (size_t)stride * es;
+    for (int l = 0; l < t.s; ++l) {
+        void *F_l = (l == t.s - 1) ? f_out : static_cast<void *>(Fbuf);
+        int rc = run_stage(m, t, l, model, dt, eps, f_n, F_l, G, P, L_res, n, precision, flags, st, coll);
+        if (rc) return rc;
+    }
+    return BZ_OK;
+}
+
+size_t step_scratch_bytes(const bz_modes *m, const Tableau &t, int64_t n, int precision) {
+    const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
+    const size_t stage = (size_t)(2 * t.s + 1) * n * m->g->v.nv * es;
+    return stage + collide_scratch_bytes(m, precision, n);
 }
 
 int check_imex_args(const bz_modes *m, int scheme, int model, double dt, double eps, int precision,
@@ -390,21 +497,141 @@ int imex_step(const bz_modes *m, int scheme, int model, double dt, double eps, c
     if (flags & ~(BZ_CONSERVE | BZ_CHECK_INPUT)) return fail(BZ_EINVAL, "imex_step: unknown flag");
     DeviceGuard dg(m->g->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
     const int64_t stride = n_cells * m->g->v.nv;
     if (flags & BZ_CHECK_INPUT) {
         rc = check_input(precision, f_n, stride, st);
         if (rc) return rc;
     }
-    // scratch: G and P for every stage, one F buffer for the intermediate stages
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (st) cudaStreamIsCapturing(st, &cap);
+    if (!st || cap != cudaStreamCaptureStatusNone) {
+        // legacy stream or a caller's capture: plain launches, pool scratch
+        Scratch s;
+        BZ_TRY(s.alloc(step_scratch_bytes(m, t, n_cells, precision), st), "imex_step: scratch");
+        return step_sequence(m, t, model, dt, eps, f_n, f_out, L_res, n_cells, precision, flags, st, s.p);
+    }
+    StepKey key{m, scheme, model, precision, flags, m->g->device, dt, eps, f_n, f_out, L_res, n_cells};
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto &e : g_graphs) {
+        if (e.key == key) {
+            e.stamp = ++g_graph_clock;
+            BZ_TRY(cudaGraphLaunch(e.exec, st), "imex_step: graph launch");
+            return BZ_OK;
+        }
+    }
+    StepGraph ne;
+    ne.key = key;
+    ne.stamp = ++g_graph_clock;
+    ne.scratch = nullptr;
+    ne.exec = nullptr;
+    cudaError_t e = cudaMalloc(&ne.scratch, step_scratch_bytes(m, t, n_cells, precision));
+    if (e != cudaSuccess) return cuda_fail(e, "imex_step: graph scratch");
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaFree(ne.scratch);
+        return cuda_fail(e, "imex_step: begin capture");
+    }
+    t_capturing = true;
+    rc = step_sequence(m, t, model, dt, eps, f_n, f_out, L_res, n_cells, precision, flags, st, ne.scratch);
+    t_capturing = false;
+    e = cudaStreamEndCapture(st, &graph);
+    if (rc == BZ_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ne.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != BZ_OK || e != cudaSuccess) {
+        cudaFree(ne.scratch);
+        return rc != BZ_OK ? rc : cuda_fail(e, "imex_step: capture");
+    }
+    if (g_graphs.size() >= kMaxGraphs) {
+        size_t old = 0;
+        for (size_t i = 1; i < g_graphs.size(); ++i)
+            if (g_graphs[i].stamp < g_graphs[old].stamp) old = i;
+        drop_graph(g_graphs[old]);
+        g_graphs.erase(g_graphs.begin() + old);
+    }
+    g_graphs.push_back(ne);
+    BZ_TRY(cudaGraphLaunch(ne.exec, st), "imex_step: graph launch");
+    return BZ_OK;
+}
+
+int group_collide(const bz_group_item *items, int n_items, int precision, int flags, void *stream) {
+    if (!items || n_items < 0 || n_items > 1024) return fail(BZ_EINVAL, "group_collide: bad item list");
+    if (precision != BZ_FP64 && precision != BZ_FP32) return fail(BZ_EINVAL, "group_collide: precision");
+    if (flags & ~(BZ_CONSERVE | BZ_CHECK_INPUT)) return fail(BZ_EINVAL, "group_collide: unknown flag");
+    if (n_items == 0) return BZ_OK;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    for (int i = 0; i < n_items; ++i) {
+        const bz_group_item &it = items[i];
+        if (!it.modes || !it.modes->g) return fail(BZ_EINVAL, "group_collide: item without modes");
+        if (it.n_cells < 0) return fail(BZ_EINVAL, "group_collide: n_cells < 0");
+        if (it.n_cells > 0 && (!it.f || !it.Q)) return fail(BZ_EINVAL, "group_collide: NULL buffer");
+        if (it.modes->g->device != dev) return fail(BZ_EINVAL, "group_collide: items must live on the current device");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // longest first: per-cell work (pairs of the symmetric sum) decides the order
+    std::vector<int> order;
+    for (int i = 0; i < n_items; ++i)
+        if (items[i].n_cells > 0) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return items[a].modes->pairs_sym > items[b].modes->pairs_sym;
+    });
+    std::vector<size_t> off(order.size() + 1, 0);
+    for (size_t q = 0; q < order.size(); ++q) {
+        size_t b = collide_scratch_bytes(items[order[q]].modes, precision, items[order[q]].n_cells);
+        off[q + 1] = off[q] + (b + 255) / 256 * 256;
+    }
     Scratch s;
-    BZ_TRY(s.alloc((size_t)(2 * t.s + 1) * stride * es, st), "imex_step: scratch");
-    char *G = static_cast<char *>(s.p);
-    char *P = G + (size_t)t.s * stride * es;
-    char *Fbuf = P + (size_t)t.s * stride * es;
-    for (int l = 0; l < t.s; ++l) {
-        void *F_l = (l == t.s - 1) ? f_out : static_cast<void *>(Fbuf);
-        rc = run_stage(m, t, l, model, dt, eps, f_n, F_l, G, P, L_res, n_cells, precision, flags, st);
+    BZ_TRY(s.alloc(off.back(), st), "group_collide: scratch");
+    char *base = static_cast<char *>(s.p);
+    auto fh_of = [&](size_t q) { return base + off[q]; };
+    auto qh_of = [&](size_t q) {
+        return base + off[q] + collide_scratch_bytes(items[order[q]].modes, precision, items[order[q]].n_cells) / 2;
+    };
+    int rc;
+    for (size_t q = 0; q < order.size(); ++q) {
+        const bz_group_item &it = items[order[q]];
+        if (flags & BZ_CHECK_INPUT) {
+            rc = check_input(precision, it.f, it.n_cells * it.modes->g->v.nv, st);
+            if (rc) return rc;
+        }
+        rc = phase_forward(it.modes, precision, it.f, fh_of(q), it.n_cells, st);
+        if (rc) return rc;
+    }
+    // one launch of the register-blocked kernel for up to kMaxGroup FP32 2-D
+    // instances at a time; the others run the generic kernel one by one
+    std::vector<const bz_modes *> gm;
+    std::vector<const float2 *> gf;
+    std::vector<float2 *> gq;
+    std::vector<int64_t> gn;
+    auto flush = [&]() -> int {
+        if (gm.empty()) return BZ_OK;
+        BZ_LAUNCH("modesum_f32_group", st,
+                  launch_modesum32_group(gm.data(), gf.data(), gq.data(), gn.data(), (int)gm.size(), st),
+                  "group_collide: grouped mode sum");
+        gm.clear();
+        gf.clear();
+        gq.clear();
+        gn.clear();
+        return BZ_OK;
+    };
+    for (size_t q = 0; q < order.size(); ++q) {
+        const bz_group_item &it = items[order[q]];
+        if (precision == BZ_FP32 && modesum32_2d_available(it.modes)) {
+            gm.push_back(it.modes);
+            gf.push_back(reinterpret_cast<const float2 *>(fh_of(q)));
+            gq.push_back(reinterpret_cast<float2 *>(qh_of(q)));
+            gn.push_back(it.n_cells);
+            if ((int)gm.size() == kMaxGroup && (rc = flush())) return rc;
+        } else {
+            rc = phase_modesum(it.modes, precision, fh_of(q), qh_of(q), it.n_cells, st);
+            if (rc) return rc;
+        }
+    }
+    if ((rc = flush())) return rc;
+    for (size_t q = 0; q < order.size(); ++q) {
+        const bz_group_item &it = items[order[q]];
+        rc = phase_inverse(it.modes, precision, flags, qh_of(q), it.Q, nullptr, it.n_cells, st);
         if (rc) return rc;
     }
     return BZ_OK;
@@ -518,6 +745,10 @@ int bz_profile_read(char *names, int names_bytes, double *total_ms, int64_t *lau
 }
 
 void bz_grid_destroy(bz_grid *g) { grid_destroy(g); }
-void bz_modes_destroy(bz_modes *m) { modes_destroy(m); }
+void bz_modes_destroy(bz_modes *m) {
+    if (!m) return;
+    purge_graphs(m);
+    modes_destroy(m);
+}
 
 }  // extern "C"

@@ -100,6 +100,26 @@ cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *T2i, cons
                                       float *Q, int64_t n, const double *cinv, const InvEpilogue &ep,
                                       cudaStream_t st);
 
+// ---- register-blocked FP32 2-D mode sum (k_modesum32.cu) --------------------
+constexpr int kMaxGroup = 16;      // instances per grouped launch
+struct Mode32Item {
+    const float2 *fhat;
+    float2 *Qhat;
+    const float *W;
+    const int *tasks;
+    int h, M, nhalf, wrow_max;
+    int64_t n;
+};
+struct Mode32Group {
+    int nitems;
+    int64_t tile_start[kMaxGroup + 1];   // prefix sums of 32-cell tiles
+    Mode32Item item[kMaxGroup];
+};
+bool modesum32_2d_available(const bz_modes *m);
+cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st);
+cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *const *fhat, float2 *const *Qhat,
+                                   const int64_t *n, int count, cudaStream_t st);
+
 // ---- kernels (k_modesum.cu) -----------------------------------------------
 cudaError_t launch_modesum_generic_f64(const GridView &g, const double *F, int bcols,
                                        const double2 *fhat, double2 *Qhat, int64_t n,

@@ -41,10 +41,15 @@ template <int N>
 __global__ void __launch_bounds__(kThreads, 1)
 dft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, const float2 *__restrict__ T1,
                  const float2 *__restrict__ T2, int64_t n) {
-    constexpr int H = N / 2, h = H - 1, M = N - 1, NV = N * N;
-    extern __shared__ __align__(16) float2 As[];        // [H][N][kPitch]
+    constexpr int H = N / 2, M = N - 1, NV = N * N;
+    extern __shared__ __align__(16) float2 As[];        // [H][N][kPitch], then T1s, T2s
+    float2 *T1s = As + H * N * kPitch;                  // [N][H]
+    float2 *T2s = T1s + N * H;                          // [N][32]
+    for (int i = threadIdx.x; i < N * H; i += blockDim.x) T1s[i] = T1[i];
+    for (int i = threadIdx.x; i < N * 32; i += blockDim.x) T2s[i] = T2[i];
     const int64_t tile = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
     // ---- stage 1: grid-space rows -> A ----
     {
         const int c0 = warp, c1 = warp + 16;
@@ -54,14 +59,22 @@ dft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, const f
         float2 a0[H], a1[H];
 #pragma unroll
         for (int k = 0; k < H; ++k) a0[k] = a1[k] = make_float2(0.f, 0.f);
-#pragma unroll 4
-        for (int j1 = 0; j1 < N; ++j1) {
-            const float x0 = ok0 ? __ldg(f0 + j1 * N) : 0.f;
-            const float x1 = ok1 ? __ldg(f1 + j1 * N) : 0.f;
-            const float4 *t = reinterpret_cast<const float4 *>(T1 + j1 * H);
+        constexpr int JB = 8;                           // rows of f in flight per thread and cell
+        for (int jb = 0; jb < N; jb += JB) {
+            float xs0[JB], xs1[JB];
+#pragma unroll
+            for (int q = 0; q < JB; ++q) {
+                xs0[q] = ok0 ? __ldg(f0 + (jb + q) * N) : 0.f;
+                xs1[q] = ok1 ? __ldg(f1 + (jb + q) * N) : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < JB; ++q) {
+            const int j1 = jb + q;
+            const float x0 = xs0[q], x1 = xs1[q];
+            const float4 *t = reinterpret_cast<const float4 *>(T1s + j1 * H);
 #pragma unroll
             for (int k = 0; k < H; k += 2) {
-                const float4 e = __ldg(t + k / 2);
+                const float4 e = t[k / 2];
                 a0[k].x = fmaf(e.x, x0, a0[k].x);
                 a0[k].y = fmaf(e.y, x0, a0[k].y);
                 a0[k + 1].x = fmaf(e.z, x0, a0[k + 1].x);
@@ -70,6 +83,7 @@ dft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, const f
                 a1[k].y = fmaf(e.y, x1, a1[k].y);
                 a1[k + 1].x = fmaf(e.z, x1, a1[k + 1].x);
                 a1[k + 1].y = fmaf(e.w, x1, a1[k + 1].y);
+            }
             }
         }
         if (lane < N) {
@@ -95,10 +109,10 @@ dft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, const f
         for (int j2 = 0; j2 < N; ++j2) {
             const float2 a = As[(k1a * N + j2) * kPitch + lane];
             const float2 b = hasb ? As[(k1b * N + j2) * kPitch + lane] : make_float2(0.f, 0.f);
-            const float4 *t = reinterpret_cast<const float4 *>(T2 + j2 * 32 + blk * 16);
+            const float4 *t = reinterpret_cast<const float4 *>(T2s + j2 * 32 + blk * 16);
 #pragma unroll
             for (int i = 0; i < 16; i += 2) {
-                const float4 e = __ldg(t + i / 2);
+                const float4 e = t[i / 2];
                 cmac(q0[i], a, make_float2(e.x, e.y));
                 cmac(q0[i + 1], a, make_float2(e.z, e.w));
                 cmac(q1[i], b, make_float2(e.x, e.y));
@@ -193,7 +207,12 @@ dft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, const f
                  const float2 *__restrict__ T3, Cinv cinv, int conserve, const float *__restrict__ P,
                  double L, double dv, int64_t n) {
     constexpr int H = N / 2, M = N - 1;
-    extern __shared__ __align__(16) float2 Bs[];        // [H][N][kPitch]
+    extern __shared__ __align__(16) float2 Bs[];        // [H][N][kPitch], then T2s, T3s
+    float2 *T2s = Bs + H * N * kPitch;                  // [M][32]
+    float2 *T3s = T2s + M * 32;                         // [H][N]
+    for (int i = threadIdx.x; i < M * 32; i += blockDim.x) T2s[i] = T2i[i];
+    for (int i = threadIdx.x; i < H * N; i += blockDim.x) T3s[i] = T3[i];
+    __syncthreads();
     const int64_t tile = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // ---- stage 1: lane = cell, tasks = (k1 pair, block of 16 j2) ----
@@ -206,18 +225,29 @@ dft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, const f
         float2 b0[16], b1[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) b0[i] = b1[i] = make_float2(0.f, 0.f);
-#pragma unroll 2
-        for (int kk = 0; kk < M; ++kk) {
-            const float2 qa = qt[(k1a * M + kk) * 32];
-            const float2 qb = hasb ? qt[(k1b * M + kk) * 32] : make_float2(0.f, 0.f);
-            const float4 *t = reinterpret_cast<const float4 *>(T2i + kk * 32 + blk * 16);
+        constexpr int KB = 8;                           // spectral rows in flight per thread
+        for (int kb = 0; kb < M; kb += KB) {
+            float2 qas[KB], qbs[KB];
+#pragma unroll
+            for (int q = 0; q < KB; ++q) {
+                const bool in = kb + q < M;
+                qas[q] = in ? qt[(k1a * M + kb + q) * 32] : make_float2(0.f, 0.f);
+                qbs[q] = (in && hasb) ? qt[(k1b * M + kb + q) * 32] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < KB; ++q) {
+            const int kk = kb + q;
+            if (kk >= M) break;
+            const float2 qa = qas[q], qb = qbs[q];
+            const float4 *t = reinterpret_cast<const float4 *>(T2s + kk * 32 + blk * 16);
 #pragma unroll
             for (int i = 0; i < 16; i += 2) {
-                const float4 e = __ldg(t + i / 2);
+                const float4 e = t[i / 2];
                 cmac_conj32(b0[i], qa, e.x, e.y);
                 cmac_conj32(b0[i + 1], qa, e.z, e.w);
                 cmac_conj32(b1[i], qb, e.x, e.y);
                 cmac_conj32(b1[i + 1], qb, e.z, e.w);
+            }
             }
         }
 #pragma unroll
@@ -240,10 +270,10 @@ dft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, const f
         for (int k1 = 0; k1 < H; ++k1) {
             const float2 ba = Bs[(k1 * N + lane) * kPitch + c0];
             const float2 bb = Bs[(k1 * N + lane) * kPitch + c1];
-            const float4 *t = reinterpret_cast<const float4 *>(T3 + k1 * N);
+            const float4 *t = reinterpret_cast<const float4 *>(T3s + k1 * N);
 #pragma unroll
             for (int j = 0; j < N; j += 2) {
-                const float4 e = __ldg(t + j / 2);     // Re(b conj(e)) = b.x e.x + b.y e.y
+                const float4 e = t[j / 2];             // Re(b conj(e)) = b.x e.x + b.y e.y
                 q0[j] = fmaf(ba.x, e.x, fmaf(ba.y, e.y, q0[j]));
                 q0[j + 1] = fmaf(ba.x, e.z, fmaf(ba.y, e.w, q0[j + 1]));
                 q1[j] = fmaf(bb.x, e.x, fmaf(bb.y, e.y, q1[j]));
@@ -255,7 +285,8 @@ dft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, const f
     inv32_epilogue<N>(q1, tile * 32 + c1, lane, cinv, conserve, P, Q, L, dv, n);
 }
 
-template <int N> size_t fwd_smem() { return sizeof(float2) * (N / 2) * N * kPitch; }
+template <int N> size_t fwd_smem() { return sizeof(float2) * ((N / 2) * N * kPitch + N * (N / 2) + N * 32); }
+template <int N> size_t inv_smem() { return sizeof(float2) * ((N / 2) * N * kPitch + (N - 1) * 32 + (N / 2) * N); }
 
 }  // namespace
 
@@ -352,7 +383,7 @@ cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *T2i, cons
     cudaError_t e = cudaSuccess;
 #define BZ_INV(NN)                                                                                       \
     case NN: {                                                                                           \
-        size_t sm = fwd_smem<NN>();                                                                      \
+        size_t sm = inv_smem<NN>();                                                                      \
         e = cudaFuncSetAttribute(dft_inv32_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
         if (e != cudaSuccess) return e;                                                                  \
         dft_inv32_kernel<NN><<<ntile, kThreads, sm, st>>>(Qhat, Q, T2i, T3, ci, ep.conserve,             \

@@ -35,12 +35,13 @@ namespace {
 
 constexpr int R = 8;            // outputs per thread along k_2
 constexpr int kWarps = 16;      // warps per CTA
-constexpr int kTaskInts = 8;    // ints per task record
+constexpr int kTaskInts = 12;   // ints per task record
 
 constexpr int kPad = 8;         // zero columns on each side of a shared-memory row
 
 struct TaskRec {
     int k1, k20, l1lo, nl1, l2lo, nblk, woff, rfirst;   // rfirst: first r this task stores
+    int rem, rowf, pad0, pad1;                          // steps of the last block, floats per l1 row
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -65,58 +66,79 @@ __device__ __forceinline__ void stage_row(float *dst, const float *src, int nflo
     cp_async_commit();
 }
 
-// One l_1 row of a task: acc[r] += sum_l2 w(l2, r) f-hat_l(l2) f-hat_m(k2_0 + r - l2).
-// DIR = +1: f-hat_l read from row l_1 at column l_2; DIR = -1 (l_1 < 0): the
-// conjugate of row -l_1 at column -l_2.  All columns lie inside the zero-padded
-// shared-memory row, so no load needs a bounds check (checked on the host).
-template <int DIR>
-__device__ __forceinline__ void row_pass(const float2 *__restrict__ rowl, const float2 *__restrict__ rowm,
-                                         const float *__restrict__ wrow, int nblk, int l2lo, int mbase0, int c0,
-                                         float2 (&acc)[R]) {
-    float2 win[2 * R - 1];
-    // columns are offset by c0 = h + kPad; a column c is element c * 32
-    const float2 *mp = rowm + (mbase0 + c0) * 32;
-    const float2 *lp = rowl + (DIR * l2lo + c0) * 32;
+// One block of R l_2 steps.  The window of f-hat_m values lives in a 16-slot
+// register array used under two alternating namings (PH = 0, 1): logical slot
+// j is physical slot (j + PH R) mod 2R, so moving the window by R between
+// blocks costs no register moves.  f-hat_l is read at lp, lp + ldir, ... with
+// ldir = +-32 elements (columns +-1); for l_1 < 0 the row is that of -l_1 read
+// backwards and conjugated (sg = -1).  Only two instances of this body exist,
+// which keeps the unrolled code inside the instruction cache.
+template <int PH>
+__device__ __forceinline__ void block_pass(float2 (&win)[2 * R], const float2 *__restrict__ mp,
+                                           const float2 *__restrict__ lp, int ldir, float sg,
+                                           const float *__restrict__ wb, float2 (&acc)[R]) {
 #pragma unroll
-    for (int j = R; j < 2 * R - 1; ++j) win[j] = mp[j * 32];
-    for (int blk = 0; blk < nblk; ++blk) {
-        if (blk > 0) {
+    for (int j = 0; j < R; ++j) win[(j + PH * R) & (2 * R - 1)] = mp[j * 32];
 #pragma unroll
-            for (int j = 2 * R - 2; j >= R; --j) win[j] = win[j - R];
+    for (int s = 0; s < R; ++s) {
+        float2 fl = *lp;
+        lp += ldir;
+        fl.y *= sg;
+        const float4 wa = *reinterpret_cast<const float4 *>(wb + s * R);
+        const float4 wc = *reinterpret_cast<const float4 *>(wb + s * R + 4);
+        const float wv[R] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 b = win[(r - s + R - 1 + PH * R) & (2 * R - 1)];
+            const float tx = wv[r] * fl.x, ty = wv[r] * fl.y;   // weight * f-hat_l
+            acc[r].x = fmaf(tx, b.x, acc[r].x);
+            acc[r].x = fmaf(-ty, b.y, acc[r].x);
+            acc[r].y = fmaf(tx, b.y, acc[r].y);
+            acc[r].y = fmaf(ty, b.x, acc[r].y);
         }
-#pragma unroll
-        for (int j = 0; j < R; ++j) win[j] = mp[j * 32];
-        const float *wb = wrow + blk * R * R;
-#pragma unroll
-        for (int s = 0; s < R; ++s) {
-            const float2 fl = lp[DIR * s * 32];
-            const float4 wa = *reinterpret_cast<const float4 *>(wb + s * R);
-            const float4 wc = *reinterpret_cast<const float4 *>(wb + s * R + 4);
-            const float wv[R] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float2 b = win[r - s + R - 1];
-                const float tx = wv[r] * fl.x;
-                const float ty = (DIR > 0) ? wv[r] * fl.y : -(wv[r] * fl.y);   // weight * f-hat_l
-                acc[r].x = fmaf(tx, b.x, acc[r].x);
-                acc[r].x = fmaf(-ty, b.y, acc[r].x);
-                acc[r].y = fmaf(tx, b.y, acc[r].y);
-                acc[r].y = fmaf(ty, b.x, acc[r].y);
-            }
-        }
-        mp -= R * 32;              // next block: m_2 window moves down by R
-        lp += DIR * R * 32;        // l_2 moves up by R
     }
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 1)
-modesum32_kernel(const float2 *__restrict__ fhat, float2 *__restrict__ Qhat, const float *__restrict__ W,
-                 const int *__restrict__ tasks, int h, int M, int nhalf, int wrow_max, int64_t n) {
+// One l_1 row of a task: acc[r] += sum_l2 w(l2, r) f-hat_l(l2) f-hat_m(k2_0 + r - l2).
+// All columns lie inside the zero-padded shared-memory row, so no load needs a
+// bounds check (checked on the host when the task table is built).
+__device__ __forceinline__ void row_pass(const float2 *__restrict__ rowl, int dir,
+                                         const float2 *__restrict__ rowm, const float *__restrict__ wrow,
+                                         int nblk, int l2lo, int mbase0, int c0, float2 (&acc)[R]) {
+    float2 win[2 * R];
+    // columns are offset by c0 = h + kPad; a column c is element c * 32
+    const float2 *mp = rowm + (mbase0 + c0) * 32;
+    const float2 *lp = rowl + (dir * l2lo + c0) * 32;
+    const int ldir = dir * 32;
+    const float sg = (float)dir;
+#pragma unroll
+    for (int j = R; j < 2 * R - 1; ++j) win[j] = mp[j * 32];
+    int blk = 0;
+    for (; blk + 1 < nblk; blk += 2) {
+        block_pass<0>(win, mp, lp, ldir, sg, wrow + blk * R * R, acc);
+        block_pass<1>(win, mp - R * 32, lp + R * ldir, ldir, sg, wrow + (blk + 1) * R * R, acc);
+        mp -= 2 * R * 32;
+        lp += 2 * R * ldir;
+    }
+    if (blk < nblk) block_pass<0>(win, mp, lp, ldir, sg, wrow + blk * R * R, acc);
+}
+
+__global__ void __launch_bounds__(kWarps * 32, 1) modesum32_kernel(const Mode32Group gd) {
     extern __shared__ __align__(16) float4 smem4[];
+    // this CTA's instance and tile (instances are ordered longest-first)
+    int it = 0;
+    while (it + 1 < gd.nitems && (int64_t)blockIdx.x >= gd.tile_start[it + 1]) ++it;
+    const Mode32Item &ip = gd.item[it];
+    const float2 *__restrict__ fhat = ip.fhat;
+    float2 *__restrict__ Qhat = ip.Qhat;
+    const float *__restrict__ W = ip.W;
+    const int *__restrict__ tasks = ip.tasks;
+    const int h = ip.h, M = ip.M, nhalf = ip.nhalf, wrow_max = ip.wrow_max;
+    const int64_t n = ip.n;
     const int MP = M + 2 * kPad;                                     // padded row length
     float2 *Fs = reinterpret_cast<float2 *>(smem4);                  // [h+1][MP][32]
     float *wsm = reinterpret_cast<float *>(Fs + (size_t)(h + 1) * MP * 32);   // [warps][2][wrow_max]
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = (int64_t)blockIdx.x - gd.tile_start[it];
     {
         // copy the tile's half spectrum into zero-padded rows
         const float4 *src = reinterpret_cast<const float4 *>(fhat + tile * (int64_t)nhalf * 32);
@@ -138,7 +160,7 @@ modesum32_kernel(const float2 *__restrict__ fhat, float2 *__restrict__ Qhat, con
 
     for (int t = tbeg; t < tend; ++t) {
         const TaskRec tk = trec[t];
-        const int rowf = tk.nblk * R * R;                 // floats per l_1 row
+        const int rowf = tk.rowf;                         // floats per l_1 row
         const float *wsrc = W + tk.woff;
         float2 hi[R], lo[R], acc[R];
 #pragma unroll
@@ -157,13 +179,11 @@ modesum32_kernel(const float2 *__restrict__ fhat, float2 *__restrict__ Qhat, con
             const int m1 = tk.k1 - l1;                    // >= 0: stored row
             const int mbase0 = tk.k20 - tk.l2lo - (R - 1);
             const float2 *rowm = Fl + (size_t)m1 * MP * 32;
-            if (l1 >= 0)
-                row_pass<1>(Fl + (size_t)l1 * MP * 32, rowm, wcur, tk.nblk, tk.l2lo, mbase0, c0, acc);
-            else
-                row_pass<-1>(Fl + (size_t)(-l1) * MP * 32, rowm, wcur, tk.nblk, tk.l2lo, mbase0, c0, acc);
+            const int dir = l1 < 0 ? -1 : 1;              // f-hat_l = conj(f-hat_{-l}) for l_1 < 0
+            row_pass(Fl + (size_t)(dir * l1) * MP * 32, dir, rowm, wcur, tk.nblk, tk.l2lo, mbase0, c0, acc);
             __syncwarp();
-            // fold the FP32 row sums into (hi, lo) every second row and after the last
-            if ((i & 1) || i + 1 == tk.nl1) {
+            // fold the FP32 row sums (<= 4 rows of <= 32 terms) into (hi, lo)
+            if ((i & 3) == 3 || i + 1 == tk.nl1) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     float s, e;
@@ -219,18 +239,18 @@ int modes_build_fp32_tables(bz_modes *m) {
             const int k2last = k20 + R - 1;
             const int lo = std::max(-h, k20 - h), hi = std::min(h, k2last + h);
             const int len = hi - lo + 1;
-            const int npad = (len + R - 1) / R * R;
-            // choose the padded l2 range so that every l2 and every k2 - l2 stays
-            // inside the zero-padded row
-            int l2lo = lo - (npad - len);
+            const int nblk = (len + R - 1) / R;
+            const int npad = nblk * R;
+            // place the padded range [l2lo, l2lo + npad - 1] so that every f-hat_l
+            // column and every window column k2 - l2 lies in the zero-padded row
+            int l2lo = 0;
             bool placed = false;
-            for (int cand = lo - (npad - len); cand <= lo; ++cand) {
+            for (int cand = lo - (npad - len); cand <= lo && !placed; ++cand) {
                 const int last = cand + npad - 1;
                 if (cand < lo_col || last > hi_col) continue;
                 if (k20 - last < lo_col || k2last - cand > hi_col) continue;
                 l2lo = cand;
                 placed = true;
-                break;
             }
             if (!placed) return BZ_OK;                       // grid not covered by the padded layout
             TaskRec t;
@@ -239,9 +259,12 @@ int modes_build_fp32_tables(bz_modes *m) {
             t.l1lo = k1 - h;
             t.nl1 = k1 / 2 - (k1 - h) + 1;
             t.l2lo = l2lo;
-            t.nblk = npad / R;
+            t.nblk = nblk;
             t.woff = (int)W.size();
             t.rfirst = std::max(0, prev_end + 1 - k20);
+            t.rem = R;
+            t.rowf = npad * R;
+            t.pad0 = t.pad1 = 0;
             prev_end = k2last;
             for (int i = 0; i < t.nl1; ++i) {
                 const int l1 = t.l1lo + i, m1 = k1 - l1;
@@ -285,7 +308,7 @@ int modes_build_fp32_tables(bz_modes *m) {
     }
     tab[kWarps] = pos;
     int wrow_max = 0;
-    for (auto &t : tasks) wrow_max = std::max(wrow_max, t.nblk * R * R);
+    for (auto &t : tasks) wrow_max = std::max(wrow_max, t.nblk * R * R);   // staging buffer: whole blocks
     if (smem_bytes(v, wrow_max) > 227 * 1024) return BZ_OK;   // does not fit: generic kernel
     cudaError_t e = cudaMalloc(&m->d_W32, sizeof(float) * W.size());
     if (e == cudaSuccess) e = cudaMalloc(&m->d_task, sizeof(int) * tab.size());
@@ -306,16 +329,57 @@ int modes_build_fp32_tables(bz_modes *m) {
 
 bool modesum32_2d_available(const bz_modes *m) { return m->d_W32 != nullptr; }
 
-cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const GridView &v = m->g->v;
-    size_t sm = smem_bytes(v, m->w32_rowmax);
+static cudaError_t launch_group(const Mode32Group &gd, size_t sm, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(modesum32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    const int64_t ntile = (n + 31) / 32;
-    modesum32_kernel<<<(unsigned)ntile, kWarps * 32, sm, st>>>(fhat, Qhat, m->d_W32, m->d_task, v.h, v.M,
-                                                             (int)v.nhalf, m->w32_rowmax, n);
+    modesum32_kernel<<<(unsigned)gd.tile_start[gd.nitems], kWarps * 32, sm, st>>>(gd);
     return cudaGetLastError();
+}
+
+static void fill_item(Mode32Item &it, const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n) {
+    const GridView &v = m->g->v;
+    it.fhat = fhat;
+    it.Qhat = Qhat;
+    it.W = m->d_W32;
+    it.tasks = m->d_task;
+    it.h = v.h;
+    it.M = v.M;
+    it.nhalf = (int)v.nhalf;
+    it.wrow_max = m->w32_rowmax;
+    it.n = n;
+}
+
+cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    Mode32Group gd;
+    memset(&gd, 0, sizeof gd);
+    gd.nitems = 1;
+    fill_item(gd.item[0], m, fhat, Qhat, n);
+    gd.tile_start[0] = 0;
+    gd.tile_start[1] = (n + 31) / 32;
+    return launch_group(gd, smem_bytes(m->g->v, m->w32_rowmax), st);
+}
+
+// Heterogeneous instances in one launch; items[] must be ordered as they
+// should be scheduled (longest first), count <= kMaxGroup.
+cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *const *fhat, float2 *const *Qhat,
+                                   const int64_t *n, int count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (count > kMaxGroup) return cudaErrorInvalidValue;
+    Mode32Group gd;
+    memset(&gd, 0, sizeof gd);
+    gd.nitems = count;
+    size_t sm = 0;
+    int64_t tiles = 0;
+    for (int i = 0; i < count; ++i) {
+        fill_item(gd.item[i], ms[i], fhat[i], Qhat[i], n[i]);
+        gd.tile_start[i] = tiles;
+        tiles += (n[i] + 31) / 32;
+        sm = std::max(sm, smem_bytes(ms[i]->g->v, ms[i]->w32_rowmax));
+    }
+    gd.tile_start[count] = tiles;
+    if (tiles == 0) return cudaSuccess;
+    return launch_group(gd, sm, st);
 }
 
 }  // namespace bz
