@@ -26,13 +26,17 @@ N_V, L_BOX, GAMMA = 32, 10.0, 1.0
 CELLS = 65536
 SEED = 1003
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+# DRAM bytes (read + write) of one modesum32_kernel launch (R = 8 variant) on the
+# 65536-cell workload, from one ncu capture of dram__bytes_read.sum and
+# dram__bytes_write.sum; reported only for that workload and variant.
+MODESUM_TRAFFIC_65536 = 260828160 + 209905152
 METRIC = "cell-collision evals/s at N_v=32^2: mixed-precision vs FP64 GPU, rel-L2 err stated"
 WORKLOAD = "65536 cells, 2-D 32x32 velocity grid on [-10,10]^2, VHS kernel, shifted Maxwellians Mach 0-3"
 
 
 def _env_rank():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
-        int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2103_14890_gb300.dist import rank_env
+    return rank_env()
 
 
 class ClockSampler:
@@ -200,10 +204,8 @@ def main():
     bz.profile(False)
     clk = clocks.stop()
     bz.check()
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2103_14890_gb300.dist import max_over_ranks
+    ms = max_over_ranks(ms, device="cuda")          # the slowest rank sets the job's time
     value = cells * world / (ms / 1e3)
 
     # dominant kernel: the mode sum
@@ -338,50 +340,52 @@ def _group_measure(bz, workloads, barrier):
 def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, value64, prof, ms_name, k_ms,
             flops_launch, achieved, gpu_launches, e2e_val, clk, extra):
     import numpy as np
-    if True:   # errors against the FP64 oracle on sampled cells (same FP32 inputs)
-        import oracle
-        idx = np.linspace(0, cells - 1, 24).astype(int)
-        fs = f_host[idx].astype(np.float64)
-        k = oracle.Kernel(2, N_V, L_BOX, GAMMA)
-        Qr = k.collide(fs)
-        q32 = Q[idx].double().cpu().numpy()
-        err32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(Qr))
-        err64 = None
-        if Q64 is not None:
-            q64 = Q64[idx].cpu().numpy()
-            err64 = float(np.linalg.norm(q64 - Qr) / np.linalg.norm(Qr))
-        rho = fs.sum(1, keepdims=True) * k.dv ** 2
-        loss32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(rho * fs))   # error / |loss rate ~ rho f|
-        cpu = None
-        if not args.no_cpu_baseline:
-            cpu, _ = cpu_baseline(f_host[:4096], budget_s=15.0)
-        line = {
-            "metric": METRIC, "value": value, "unit": "cell-collision evals/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if cells == CELLS else WORKLOAD.replace(str(CELLS), str(cells)),
-                       "cells_per_gpu": cells, "N_v": N_V * N_V, "L": L_BOX,
-                       "kernel": "VHS hard spheres (gamma=1, b0=1/(2pi))", "precision_form": "fp32",
-                       "l2": "inputs and outputs (268 MB each) exceed L2: no flush",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "rel_l2_err": {"fp32_vs_oracle": err32, "fp64_vs_oracle": err64, "fp32_loss_scaled": loss32,
-                           "sample_cells": len(idx)},
-            "fp64_form": {"value": value64, "unit": "cell-collision evals/s", "ms_per_step": ms64,
-                          "speedup_fp32_over_fp64": value / value64} if Q64 is not None else None,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": ms_name,
-                         "kernel_ms": k_ms, "flops_per_launch": flops_launch,
-                         "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
-            "kernel_times_ms": {k2: v[1] / max(1, v[0]) for k2, v in prof.items()},
-            "gpu_launches": gpu_launches,
-            "imex_step": extra.get("imex_step"),
-            "grouped": extra.get("grouped"),
-            "e2e": {"value": e2e_val, "unit": "cell-collision evals/s",
-                    "h2d_bytes_per_step": int(Q.numel() * 4), "d2h_bytes_per_step": int(Q.numel() * 4)},
-            "clocks": clk,
-            "cpu_baseline": cpu,
-        }
-        print(json.dumps(line))
+    import oracle
+    # errors against the FP64 oracle on sampled cells (same FP32 inputs)
+    idx = np.linspace(0, cells - 1, 24).astype(int)
+    fs = f_host[idx].astype(np.float64)
+    k = oracle.Kernel(2, N_V, L_BOX, GAMMA)
+    Qr = k.collide(fs)
+    q32 = Q[idx].double().cpu().numpy()
+    err32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(Qr))
+    err64 = None
+    if Q64 is not None:
+        q64 = Q64[idx].cpu().numpy()
+        err64 = float(np.linalg.norm(q64 - Qr) / np.linalg.norm(Qr))
+    rho = fs.sum(1, keepdims=True) * k.dv ** 2
+    loss32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(rho * fs))   # error / |loss rate ~ rho f|
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu, _ = cpu_baseline(f_host[:4096], budget_s=15.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-collision evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if cells == CELLS else WORKLOAD.replace(str(CELLS), str(cells)),
+                   "cells_per_gpu": cells, "N_v": N_V * N_V, "L": L_BOX,
+                   "kernel": "VHS hard spheres (gamma=1, b0=1/(2pi))", "precision_form": "fp32",
+                   "l2": "inputs and outputs (268 MB each) exceed L2: no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "rel_l2_err": {"fp32_vs_oracle": err32, "fp64_vs_oracle": err64, "fp32_loss_scaled": loss32,
+                       "sample_cells": len(idx)},
+        "fp64_form": {"value": value64, "unit": "cell-collision evals/s", "ms_per_step": ms64,
+                      "speedup_fp32_over_fp64": value / value64} if Q64 is not None else None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": MODESUM_TRAFFIC_65536 if (cells == CELLS and modes.modesum_r == 8) else None,
+                     "kernel": ms_name,
+                     "kernel_ms": k_ms, "flops_per_launch": flops_launch,
+                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "kernel_times_ms": {k2: v[1] / max(1, v[0]) for k2, v in prof.items()},
+        "gpu_launches": gpu_launches,
+        "imex_step": extra.get("imex_step"),
+        "grouped": extra.get("grouped"),
+        "e2e": {"value": e2e_val, "unit": "cell-collision evals/s",
+                "h2d_bytes_per_step": int(Q.numel() * 4), "d2h_bytes_per_step": int(Q.numel() * 4)},
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
 
 
 if __name__ == "__main__":

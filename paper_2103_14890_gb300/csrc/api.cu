@@ -615,20 +615,25 @@ int group_collide(const bz_group_item *items, int n_items, int precision, int fl
         gn.clear();
         return BZ_OK;
     };
-    for (size_t q = 0; q < order.size(); ++q) {
-        const bz_group_item &it = items[order[q]];
-        if (precision == BZ_FP32 && modesum32_2d_available(it.modes)) {
+    // one grouped launch per kernel variant (items keep the longest-first order)
+    for (int var = 0; var < 2; ++var) {
+        for (size_t q = 0; q < order.size(); ++q) {
+            const bz_group_item &it = items[order[q]];
+            if (precision != BZ_FP32 || !modesum32_2d_available(it.modes) || it.modes->variant != var) continue;
             gm.push_back(it.modes);
             gf.push_back(reinterpret_cast<const float2 *>(fh_of(q)));
             gq.push_back(reinterpret_cast<float2 *>(qh_of(q)));
             gn.push_back(it.n_cells);
             if ((int)gm.size() == kMaxGroup && (rc = flush())) return rc;
-        } else {
-            rc = phase_modesum(it.modes, precision, fh_of(q), qh_of(q), it.n_cells, st);
-            if (rc) return rc;
         }
+        if ((rc = flush())) return rc;
     }
-    if ((rc = flush())) return rc;
+    for (size_t q = 0; q < order.size(); ++q) {
+        const bz_group_item &it = items[order[q]];
+        if (precision == BZ_FP32 && modesum32_2d_available(it.modes)) continue;
+        rc = phase_modesum(it.modes, precision, fh_of(q), qh_of(q), it.n_cells, st);
+        if (rc) return rc;
+    }
     for (size_t q = 0; q < order.size(); ++q) {
         const bz_group_item &it = items[order[q]];
         rc = phase_inverse(it.modes, precision, flags, qh_of(q), it.Q, nullptr, it.n_cells, st);
@@ -668,7 +673,7 @@ int bz_modes_info(const bz_modes *m, int64_t out[8]) {
     out[4] = v.nhalf;
     out[5] = m->nq;
     out[6] = m->pairs_sym;
-    out[7] = modesum32_2d_available(m) ? 1 : 0;
+    out[7] = modesum32_2d_available(m) ? m->modesum_R : 0;
     return BZ_OK;
 }
 

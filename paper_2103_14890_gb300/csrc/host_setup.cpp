@@ -258,8 +258,10 @@ void modes_destroy(bz_modes *m) {
     if (!m) return;
     cudaFree(m->d_F64);
     cudaFree(m->d_F32);
-    cudaFree(m->d_W32);
-    cudaFree(m->d_task);
+    for (int v = 0; v < 2; ++v) {
+        cudaFree(m->var_W[v]);
+        cudaFree(m->var_task[v]);
+    }
     cudaFree(m->d_T1);
     cudaFree(m->d_T2);
     cudaFree(m->d_T2i);

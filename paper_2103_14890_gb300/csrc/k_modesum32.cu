@@ -13,8 +13,10 @@
 //   * one CTA = one tile of 32 cells; the tile's half spectrum (complex FP32,
 //     [mode][cell]) sits in shared memory; lane = cell, so every Fourier load
 //     is a conflict-free 32-cell row and every weight load is warp-uniform.
-//   * a task = (k_1, block of R = 8 consecutive k_2); a thread accumulates R
-//     complex outputs.  Walking l_2 upwards slides the window of f-hat_m
+//   * a task = (k_1, block of R consecutive k_2); a thread accumulates R
+//     complex outputs.  Two variants are compiled, R = 8 with 16 warps per CTA
+//     and R = 4 with 32 warps; the faster one for a grid is chosen once by
+//     timing both (autotune below).  Walking l_2 upwards slides the window of f-hat_m
 //     values (m_2 = k_2 - l_2) down by one, so each step loads one new f-hat_m,
 //     one f-hat_l and R weights for 6 R FP32 operations.
 //   * each task's weights form a contiguous stream [l_1][l_2 (padded to a
@@ -22,9 +24,15 @@
 //     double buffer with cp.async while the previous row is being used.
 //   * accumulation: plain FP32 along an l_1 row (<= 32 terms), then a TwoSum
 //     fold of the row sum into a (hi, lo) pair per output.
-#include <vector>
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "bz_device.cuh"
 #include "bz_internal.h"
@@ -33,8 +41,12 @@ namespace bz {
 
 namespace {
 
-constexpr int R = 8;            // outputs per thread along k_2
-constexpr int kWarps = 16;      // warps per CTA
+// Kernel variants (outputs per thread R along k_2, warps per CTA); the
+// autotuner picks one per grid.
+struct Variant {
+    int R, warps;
+};
+constexpr Variant kVariants[2] = {{8, 16}, {4, 32}};
 constexpr int kTaskInts = 12;   // ints per task record
 
 constexpr int kPad = 8;         // zero columns on each side of a shared-memory row
@@ -66,30 +78,36 @@ __device__ __forceinline__ void stage_row(float *dst, const float *src, int nflo
     cp_async_commit();
 }
 
-// One block of R l_2 steps.  The window of f-hat_m values lives in a 16-slot
+// One block of R l_2 steps.  The window of f-hat_m values lives in a 2R-slot
 // register array used under two alternating namings (PH = 0, 1): logical slot
 // j is physical slot (j + PH R) mod 2R, so moving the window by R between
 // blocks costs no register moves.  f-hat_l is read at lp, lp + ldir, ... with
 // ldir = +-32 elements (columns +-1); for l_1 < 0 the row is that of -l_1 read
 // backwards and conjugated (sg = -1).  Only two instances of this body exist,
 // which keeps the unrolled code inside the instruction cache.
-template <int PH>
-__device__ __forceinline__ void block_pass(float2 (&win)[2 * R], const float2 *__restrict__ mp,
+template <int RR, int PH>
+__device__ __forceinline__ void block_pass(float2 (&win)[2 * RR], const float2 *__restrict__ mp,
                                            const float2 *__restrict__ lp, int ldir, float sg,
-                                           const float *__restrict__ wb, float2 (&acc)[R]) {
+                                           const float *__restrict__ wb, float2 (&acc)[RR]) {
 #pragma unroll
-    for (int j = 0; j < R; ++j) win[(j + PH * R) & (2 * R - 1)] = mp[j * 32];
+    for (int j = 0; j < RR; ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * 32];
 #pragma unroll
-    for (int s = 0; s < R; ++s) {
+    for (int s = 0; s < RR; ++s) {
         float2 fl = *lp;
         lp += ldir;
         fl.y *= sg;
-        const float4 wa = *reinterpret_cast<const float4 *>(wb + s * R);
-        const float4 wc = *reinterpret_cast<const float4 *>(wb + s * R + 4);
-        const float wv[R] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
+        float wv[RR];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float2 b = win[(r - s + R - 1 + PH * R) & (2 * R - 1)];
+        for (int q = 0; q < RR; q += 4) {
+            const float4 w4 = *reinterpret_cast<const float4 *>(wb + s * RR + q);
+            wv[q] = w4.x;
+            wv[q + 1] = w4.y;
+            wv[q + 2] = w4.z;
+            wv[q + 3] = w4.w;
+        }
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+            const float2 b = win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)];
             const float tx = wv[r] * fl.x, ty = wv[r] * fl.y;   // weight * f-hat_l
             acc[r].x = fmaf(tx, b.x, acc[r].x);
             acc[r].x = fmaf(-ty, b.y, acc[r].x);
@@ -102,28 +120,30 @@ __device__ __forceinline__ void block_pass(float2 (&win)[2 * R], const float2 *_
 // One l_1 row of a task: acc[r] += sum_l2 w(l2, r) f-hat_l(l2) f-hat_m(k2_0 + r - l2).
 // All columns lie inside the zero-padded shared-memory row, so no load needs a
 // bounds check (checked on the host when the task table is built).
+template <int RR>
 __device__ __forceinline__ void row_pass(const float2 *__restrict__ rowl, int dir,
                                          const float2 *__restrict__ rowm, const float *__restrict__ wrow,
-                                         int nblk, int l2lo, int mbase0, int c0, float2 (&acc)[R]) {
-    float2 win[2 * R];
+                                         int nblk, int l2lo, int mbase0, int c0, float2 (&acc)[RR]) {
+    float2 win[2 * RR];
     // columns are offset by c0 = h + kPad; a column c is element c * 32
     const float2 *mp = rowm + (mbase0 + c0) * 32;
     const float2 *lp = rowl + (dir * l2lo + c0) * 32;
     const int ldir = dir * 32;
     const float sg = (float)dir;
 #pragma unroll
-    for (int j = R; j < 2 * R - 1; ++j) win[j] = mp[j * 32];
+    for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * 32];
     int blk = 0;
     for (; blk + 1 < nblk; blk += 2) {
-        block_pass<0>(win, mp, lp, ldir, sg, wrow + blk * R * R, acc);
-        block_pass<1>(win, mp - R * 32, lp + R * ldir, ldir, sg, wrow + (blk + 1) * R * R, acc);
-        mp -= 2 * R * 32;
-        lp += 2 * R * ldir;
+        block_pass<RR, 0>(win, mp, lp, ldir, sg, wrow + blk * RR * RR, acc);
+        block_pass<RR, 1>(win, mp - RR * 32, lp + RR * ldir, ldir, sg, wrow + (blk + 1) * RR * RR, acc);
+        mp -= 2 * RR * 32;
+        lp += 2 * RR * ldir;
     }
-    if (blk < nblk) block_pass<0>(win, mp, lp, ldir, sg, wrow + blk * R * R, acc);
+    if (blk < nblk) block_pass<RR, 0>(win, mp, lp, ldir, sg, wrow + blk * RR * RR, acc);
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 1) modesum32_kernel(const Mode32Group gd) {
+template <int RR, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Group gd) {
     extern __shared__ __align__(16) float4 smem4[];
     // this CTA's instance and tile (instances are ordered longest-first)
     int it = 0;
@@ -154,7 +174,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) modesum32_kernel(const Mode32G
     float *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
     float *wbuf1 = wbuf0 + wrow_max;
     const int tbeg = tasks[warp], tend = tasks[warp + 1];
-    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + kWarps + 1);
+    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS + 1);
     const float2 *Fl = Fs + lane;
     const int c0 = h + kPad;
 
@@ -162,9 +182,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1) modesum32_kernel(const Mode32G
         const TaskRec tk = trec[t];
         const int rowf = tk.rowf;                         // floats per l_1 row
         const float *wsrc = W + tk.woff;
-        float2 hi[R], lo[R], acc[R];
+        float2 hi[RR], lo[RR], acc[RR];
 #pragma unroll
-        for (int r = 0; r < R; ++r) hi[r] = lo[r] = acc[r] = make_float2(0.f, 0.f);
+        for (int r = 0; r < RR; ++r) hi[r] = lo[r] = acc[r] = make_float2(0.f, 0.f);
         stage_row(wbuf0, wsrc, rowf, lane);
         for (int i = 0; i < tk.nl1; ++i) {
             const float *wcur = (i & 1) ? wbuf1 : wbuf0;
@@ -177,15 +197,15 @@ __global__ void __launch_bounds__(kWarps * 32, 1) modesum32_kernel(const Mode32G
             __syncwarp();
             const int l1 = tk.l1lo + i;
             const int m1 = tk.k1 - l1;                    // >= 0: stored row
-            const int mbase0 = tk.k20 - tk.l2lo - (R - 1);
+            const int mbase0 = tk.k20 - tk.l2lo - (RR - 1);
             const float2 *rowm = Fl + (size_t)m1 * MP * 32;
             const int dir = l1 < 0 ? -1 : 1;              // f-hat_l = conj(f-hat_{-l}) for l_1 < 0
-            row_pass(Fl + (size_t)(dir * l1) * MP * 32, dir, rowm, wcur, tk.nblk, tk.l2lo, mbase0, c0, acc);
+            row_pass<RR>(Fl + (size_t)(dir * l1) * MP * 32, dir, rowm, wcur, tk.nblk, tk.l2lo, mbase0, c0, acc);
             __syncwarp();
             // fold the FP32 row sums (<= 4 rows of <= 32 terms) into (hi, lo)
             if ((i & 3) == 3 || i + 1 == tk.nl1) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
+                for (int r = 0; r < RR; ++r) {
                     float s, e;
                     two_sum(hi[r].x, acc[r].x, s, e);
                     hi[r].x = s;
@@ -200,7 +220,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) modesum32_kernel(const Mode32G
         if (tile * 32 + lane < n) {
             float2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.k1 * M * 32 + lane;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < RR; ++r) {
                 const int k2 = tk.k20 + r;
                 if (r >= tk.rfirst && k2 <= h) out[(k2 + h) * 32] = make_float2(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
             }
@@ -208,8 +228,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1) modesum32_kernel(const Mode32G
     }
 }
 
-size_t smem_bytes(const GridView &g, int wrow_max) {
-    return sizeof(float2) * (size_t)(g.h + 1) * (g.M + 2 * kPad) * 32 + sizeof(float) * (size_t)kWarps * 2 * wrow_max;
+size_t smem_bytes(const GridView &g, int wrow_max, int warps) {
+    return sizeof(float2) * (size_t)(g.h + 1) * (g.M + 2 * kPad) * 32 + sizeof(float) * (size_t)warps * 2 * wrow_max;
 }
 
 }  // namespace
@@ -217,15 +237,15 @@ size_t smem_bytes(const GridView &g, int wrow_max) {
 // Host part: weight streams and the task table, built once per modes handle.
 double beta_host(const bz_modes *m, const int *l, const int *mm);
 
-int modes_build_fp32_tables(bz_modes *m) {
-    m->d_W32 = nullptr;
-    m->w32_floats = 0;
-    m->d_task = nullptr;
-    m->ntask = 0;
-    const GridView &v = m->g->v;
-    if (v.dim != 2 || v.N > 32 || v.M < R) return BZ_OK;     // the generic kernel handles these
-    const int h = v.h;
-    const int nb = (v.M + R - 1) / R;
+// Weight stream and task table of one variant (slot v); false if the grid is
+// not covered by this kernel (the generic kernel then serves it).
+static bool build_variant(bz_modes *m, int v, int &rc) {
+    const int R = kVariants[v].R, kWarps = kVariants[v].warps;
+    rc = BZ_OK;
+    const GridView &gv = m->g->v;
+    if (gv.dim != 2 || gv.N > 32 || gv.M < R) return false;
+    const int h = gv.h;
+    const int nb = (gv.M + R - 1) / R;
     const int lo_col = -h - kPad, hi_col = h + kPad;         // addressable padded columns
     std::vector<TaskRec> tasks;
     std::vector<float> W;
@@ -252,7 +272,7 @@ int modes_build_fp32_tables(bz_modes *m) {
                 l2lo = cand;
                 placed = true;
             }
-            if (!placed) return BZ_OK;                       // grid not covered by the padded layout
+            if (!placed) return false;                       // grid not covered by the padded layout
             TaskRec t;
             t.k1 = k1;
             t.k20 = k20;
@@ -309,77 +329,212 @@ int modes_build_fp32_tables(bz_modes *m) {
     tab[kWarps] = pos;
     int wrow_max = 0;
     for (auto &t : tasks) wrow_max = std::max(wrow_max, t.nblk * R * R);   // staging buffer: whole blocks
-    if (smem_bytes(v, wrow_max) > 227 * 1024) return BZ_OK;   // does not fit: generic kernel
-    cudaError_t e = cudaMalloc(&m->d_W32, sizeof(float) * W.size());
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_task, sizeof(int) * tab.size());
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_W32, W.data(), sizeof(float) * W.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_task, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
+    if (smem_bytes(gv, wrow_max, kWarps) > 227 * 1024) return false;   // does not fit: generic kernel
+    float *dW = nullptr;
+    int *dT = nullptr;
+    cudaError_t e = cudaMalloc(&dW, sizeof(float) * W.size());
+    if (e == cudaSuccess) e = cudaMalloc(&dT, sizeof(int) * tab.size());
+    if (e == cudaSuccess) e = cudaMemcpy(dW, W.data(), sizeof(float) * W.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dT, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(m->d_W32);
-        cudaFree(m->d_task);
-        m->d_W32 = nullptr;
-        m->d_task = nullptr;
-        return cuda_fail(e, "build_kernel_modes: FP32 weight stream");
+        cudaFree(dW);
+        cudaFree(dT);
+        rc = cuda_fail(e, "build_kernel_modes: FP32 weight stream");
+        return false;
     }
-    m->w32_floats = (int64_t)W.size();
-    m->ntask = (int)tasks.size();
-    m->w32_rowmax = wrow_max;
-    return BZ_OK;
+    m->var_W[v] = dW;
+    m->var_task[v] = dT;
+    m->var_rowmax[v] = wrow_max;
+    return true;
 }
 
 bool modesum32_2d_available(const bz_modes *m) { return m->d_W32 != nullptr; }
 
-static cudaError_t launch_group(const Mode32Group &gd, size_t sm, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(modesum32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    modesum32_kernel<<<(unsigned)gd.tile_start[gd.nitems], kWarps * 32, sm, st>>>(gd);
+static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStream_t st) {
+    cudaError_t e;
+    const unsigned grid = (unsigned)gd.tile_start[gd.nitems];
+    if (kVariants[v].R == 8) {
+        e = cudaFuncSetAttribute(modesum32_kernel<8, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        modesum32_kernel<8, 16><<<grid, 16 * 32, sm, st>>>(gd);
+    } else {
+        e = cudaFuncSetAttribute(modesum32_kernel<4, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        modesum32_kernel<4, 32><<<grid, 32 * 32, sm, st>>>(gd);
+    }
     return cudaGetLastError();
 }
 
-static void fill_item(Mode32Item &it, const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n) {
-    const GridView &v = m->g->v;
+static void fill_item(Mode32Item &it, const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n) {
+    const GridView &gv = m->g->v;
     it.fhat = fhat;
     it.Qhat = Qhat;
-    it.W = m->d_W32;
-    it.tasks = m->d_task;
-    it.h = v.h;
-    it.M = v.M;
-    it.nhalf = (int)v.nhalf;
-    it.wrow_max = m->w32_rowmax;
+    it.W = m->var_W[v];
+    it.tasks = m->var_task[v];
+    it.h = gv.h;
+    it.M = gv.M;
+    it.nhalf = (int)gv.nhalf;
+    it.wrow_max = m->var_rowmax[v];
     it.n = n;
 }
 
-cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
+static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n,
+                                  cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     Mode32Group gd;
     memset(&gd, 0, sizeof gd);
     gd.nitems = 1;
-    fill_item(gd.item[0], m, fhat, Qhat, n);
+    fill_item(gd.item[0], m, v, fhat, Qhat, n);
     gd.tile_start[0] = 0;
     gd.tile_start[1] = (n + 31) / 32;
-    return launch_group(gd, smem_bytes(m->g->v, m->w32_rowmax), st);
+    return launch_group(gd, v, smem_bytes(m->g->v, m->var_rowmax[v], kVariants[v].warps), st);
 }
 
-// Heterogeneous instances in one launch; items[] must be ordered as they
-// should be scheduled (longest first), count <= kMaxGroup.
+cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
+    return launch_variant(m, m->variant, fhat, Qhat, n, st);
+}
+
+// Heterogeneous instances in one launch; all items must use the same kernel
+// variant and be ordered as they should be scheduled (longest first);
+// count <= kMaxGroup.
 cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *const *fhat, float2 *const *Qhat,
                                    const int64_t *n, int count, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     if (count > kMaxGroup) return cudaErrorInvalidValue;
+    const int v = ms[0]->variant;
     Mode32Group gd;
     memset(&gd, 0, sizeof gd);
     gd.nitems = count;
     size_t sm = 0;
     int64_t tiles = 0;
     for (int i = 0; i < count; ++i) {
-        fill_item(gd.item[i], ms[i], fhat[i], Qhat[i], n[i]);
+        if (ms[i]->variant != v) return cudaErrorInvalidValue;
+        fill_item(gd.item[i], ms[i], v, fhat[i], Qhat[i], n[i]);
         gd.tile_start[i] = tiles;
         tiles += (n[i] + 31) / 32;
-        sm = std::max(sm, smem_bytes(ms[i]->g->v, ms[i]->w32_rowmax));
+        sm = std::max(sm, smem_bytes(ms[i]->g->v, ms[i]->var_rowmax[v], kVariants[v].warps));
     }
     gd.tile_start[count] = tiles;
     if (tiles == 0) return cudaSuccess;
-    return launch_group(gd, sm, st);
+    return launch_group(gd, v, sm, st);
+}
+
+// ---- autotuner ------------------------------------------------------------
+// Times every buildable variant once per (dimension, N, SM count) on a
+// synthetic batch (zero spectra: the kernel's cost does not depend on the
+// values) of two CTAs per SM and keeps the fastest.  Results are cached for
+// the process and, when BZ_TUNE_CACHE names a file, in that file as lines
+// "dim N sms R".
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tune;
+
+static int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+static void tune_file_load() {
+    const char *path = getenv("BZ_TUNE_CACHE");
+    if (!path) return;
+    FILE *fp = fopen(path, "r");
+    if (!fp) return;
+    int d, N, sms, r;
+    while (fscanf(fp, "%d %d %d %d", &d, &N, &sms, &r) == 4) g_tune[std::make_tuple(d, N, sms)] = r;
+    fclose(fp);
+}
+
+static void tune_file_store(int d, int N, int sms, int r) {
+    const char *path = getenv("BZ_TUNE_CACHE");
+    if (!path) return;
+    FILE *fp = fopen(path, "a");
+    if (!fp) return;
+    fprintf(fp, "%d %d %d %d\n", d, N, sms, r);
+    fclose(fp);
+}
+
+static int autotune(bz_modes *m, int &rc) {
+    rc = BZ_OK;
+    const GridView &gv = m->g->v;
+    int avail[2], na = 0;
+    for (int v = 0; v < 2; ++v)
+        if (m->var_W[v]) avail[na++] = v;
+    if (na == 1) return avail[0];
+    const int sms = sm_count();
+    const auto key = std::make_tuple(gv.dim, gv.N, sms);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tune.empty()) tune_file_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end())
+        for (int q = 0; q < na; ++q)
+            if (kVariants[avail[q]].R == it->second) return avail[q];
+    const int64_t n = (int64_t)2 * sms * 32;
+    const size_t bytes = 2 * sizeof(float2) * (size_t)((n + 31) / 32) * gv.nhalf * 32;
+    void *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, bytes);
+    if (e == cudaSuccess) e = cudaMemset(buf, 0, bytes);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    float best = 1e30f;
+    int pick = avail[0];
+    const float2 *fh = static_cast<const float2 *>(buf);
+    float2 *qh = static_cast<float2 *>(buf) + bytes / (2 * sizeof(float2));
+    for (int q = 0; q < na && e == cudaSuccess; ++q) {
+        const int v = avail[q];
+        e = launch_variant(m, v, fh, qh, n, nullptr);                  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(a, nullptr);
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = launch_variant(m, v, fh, qh, n, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(b, nullptr);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            pick = v;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e, "build_kernel_modes: autotune");
+        return avail[0];
+    }
+    g_tune[key] = kVariants[pick].R;
+    tune_file_store(gv.dim, gv.N, sms, kVariants[pick].R);
+    return pick;
+}
+
+int modes_build_fp32_tables(bz_modes *m) {
+    m->d_W32 = nullptr;
+    m->d_task = nullptr;
+    m->variant = 0;
+    int rc = BZ_OK;
+    bool any = false;
+    for (int v = 0; v < 2; ++v) {
+        m->var_W[v] = nullptr;
+        m->var_task[v] = nullptr;
+        m->var_rowmax[v] = 0;
+        if (build_variant(m, v, rc)) any = true;
+        if (rc) return rc;
+    }
+    if (!any) return BZ_OK;
+    const char *force = getenv("BZ_MODESUM_R");   // fixed choice (measurement of one variant)
+    int v = -1;
+    if (force) {
+        for (int q = 0; q < 2; ++q)
+            if (m->var_W[q] && kVariants[q].R == atoi(force)) v = q;
+    }
+    if (v < 0) v = autotune(m, rc);
+    if (rc) return rc;
+    m->variant = v;
+    m->d_W32 = m->var_W[v];
+    m->d_task = m->var_task[v];
+    m->w32_rowmax = m->var_rowmax[v];
+    m->modesum_R = kVariants[v].R;
+    return BZ_OK;
 }
 
 }  // namespace bz

@@ -54,6 +54,31 @@ def test_kernel_modes_match_oracle(bz, oracle_k, dim, N, gamma):
     assert np.abs(want[~mask][np.abs(want[~mask]) > 0]).size >= 0
 
 
+def test_fast_kernels_selected(bz):
+    """The register-blocked FP32 mode sum serves every 2-D grid with 16 <= N <= 32
+    (a silent fall back to the generic kernel would hide a table-building bug)."""
+    for N in (16, 24, 32):
+        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_r in (4, 8), N
+    assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_r == 0
+
+
+@pytest.mark.parametrize("R", [4, 8])
+@pytest.mark.parametrize("N", [16, 24, 32])
+def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, N, R):
+    """Both register-blocked variants (fixed through BZ_MODESUM_R, bypassing the
+    autotuner) against the oracle: 70 cells = 2 full tiles and a ragged tail."""
+    monkeypatch.setenv("BZ_MODESUM_R", str(R))
+    L = 10.0
+    m = bz.Modes(bz.Grid(2, N, L), 1.0)
+    assert m.modesum_r == R
+    f = workloads.bi_maxwellian(70, 2, N, L, seed=1100 + N)
+    fin = as_input(f, "fp32")
+    Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32")
+    bz.check()
+    Qr = oracle_k(2, N, L, 1.0).collide(fin)
+    assert relerr(Q.double().cpu().numpy(), Qr) < TOL32
+
+
 def test_fp64_small_config_matches_oracle(bz, oracle_k):
     """64 cells, 16^2 grid on [-8,8]^2, Maxwell molecules, bi-Maxwellians."""
     f = workloads.bi_maxwellian(64, 2, 16, 8.0, seed=1001)

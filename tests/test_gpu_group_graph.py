@@ -37,6 +37,24 @@ def test_group_collide_matches_per_instance(bz, precision):
         assert np.array_equal(got, ref)            # same kernels, same arithmetic
 
 
+def test_group_collide_mixed_variants(bz, monkeypatch):
+    """Instances on different register-blocked variants (R = 4 and R = 8) in one
+    call: one grouped launch per variant, results equal to per-instance calls."""
+    import torch
+    entries, refs = [], []
+    for i, (N, R, n) in enumerate([(32, 8, 80), (24, 4, 50), (32, 4, 33), (16, 8, 70)]):
+        monkeypatch.setenv("BZ_MODESUM_R", str(R))
+        m = bz.Modes(bz.Grid(2, N, 10.0), 1.0)
+        assert m.modesum_r == R
+        f = to_dev(workloads.bi_maxwellian(n, 2, N, 10.0, seed=90 + i), "fp32")
+        refs.append(bz.collide_batch(m, f, precision="fp32").cpu().numpy())
+        entries.append((m, f, torch.full_like(f, float("nan"))))
+    bz.group_collide(entries, precision="fp32")
+    bz.check()
+    for (m, f, Q), ref in zip(entries, refs):
+        assert np.array_equal(Q.cpu().numpy(), ref)
+
+
 def test_group_collide_matches_oracle(bz):
     import oracle
     dim, N, L, n = 2, 24, 10.0, 40
