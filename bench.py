@@ -26,7 +26,7 @@ N_V, L_BOX, GAMMA = 32, 10.0, 1.0
 CELLS = 65536
 SEED = 1003
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
-# DRAM bytes (read + write) of one modesum32_kernel launch (R = 8 variant) on the
+# DRAM bytes (read + write) of one modesum32_kernel launch (variant 1) on the
 # 65536-cell workload, from one ncu capture of dram__bytes_read.sum and
 # dram__bytes_write.sum; reported only for that workload and variant.
 MODESUM_TRAFFIC_65536 = 260828160 + 209905152
@@ -92,22 +92,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(f_sample, budget_s=15.0):
-    """Time the FP64 oracle on the host cores on a bounded sample of cells."""
+def cpu_baseline(f_host, budget_s=15.0, check_idx=()):
+    """The cpu_baseline leg: time the FP64 oracle on the host cores on a bounded
+    sample of cells (the cells in check_idx plus the first cells of the batch,
+    sized to about budget_s of work).  Returns the baseline entry, the sampled
+    cell indices and the oracle's Q on them (used to state the GPU error)."""
     import numpy as np
     import oracle
     k = oracle.Kernel(2, N_V, L_BOX, GAMMA)
-    probe = f_sample[:8].astype(np.float64)
+    probe = f_host[:8].astype(np.float64)
     t0 = time.perf_counter()
     k.collide(probe)
     per_cell = (time.perf_counter() - t0) / len(probe)
-    n = int(max(8, min(len(f_sample), budget_s / max(per_cell, 1e-6))))
-    sample = f_sample[:n].astype(np.float64)
+    n = int(max(8, min(len(f_host), budget_s / max(per_cell, 1e-6))))
+    idx = np.unique(np.concatenate([np.asarray(check_idx, dtype=np.int64),
+                                    np.arange(max(0, n - len(check_idx)), dtype=np.int64)]))
+    sample = f_host[idx].astype(np.float64)
     t0 = time.perf_counter()
-    k.collide(sample)
+    Qr = k.collide(sample)
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "cell-collision evals/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "%d of the %d cells (FP64 direct sum, OpenMP over cells)" % (n, CELLS)}, k
+    entry = {"value": len(idx) / dt, "unit": "cell-collision evals/s", "cores": oracle.num_threads(),
+             "kind": "oracle",
+             "sample": "%d of the %d cells (FP64 direct sum, OpenMP over cells)" % (len(idx), len(f_host))}
+    return entry, idx, Qr, k
 
 
 def reference_arm(args):
@@ -117,7 +124,7 @@ def reference_arm(args):
     import numpy as np
     from paper_2103_14890_gb300 import workloads
     f = workloads.shifted_maxwellians(4096, 2, N_V, L_BOX, seed=SEED)
-    base, k = cpu_baseline(f, budget_s=4.0)
+    base, _, _, k = cpu_baseline(f, budget_s=4.0)
     per_step = max(8, int(base["value"] * 4.0))
     per_step = min(per_step, len(f))
     sample = f[:per_step]
@@ -275,6 +282,11 @@ def _e2e(args, bz, modes, f_host, f, barrier, st, e0, e1, cells, world):
     return cells * world / (e2e_ms / 1e3)
 
 
+def torch_index(idx):
+    import torch
+    return torch.from_numpy(idx).to("cuda")
+
+
 def _timed(fn, steps, stream):
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -315,48 +327,70 @@ def _imex_measure(bz, workloads, barrier):
 def _group_measure(bz, workloads, barrier):
     """Heterogeneous batch in one group_collide call: 8 instances with cell
     counts log-uniform in [1e3, 5e4] and N in {16, 24, 32, 48}, plus two 3-D
-    16^3 instances of 1000 cells (FP32)."""
+    16^3 instances of 1000 cells; FP32 form timed against the FP64 form on the
+    same inputs (rel-L2 of FP32 against FP64 over all cells)."""
     import torch
     items = workloads.grouped_instances()
-    entries = []
     grids = {}
+    hosts = []
     total = 0
     for it in items:
         key = (it["dim"], it["N"])
         if key not in grids:
             grids[key] = bz.Modes(bz.Grid(it["dim"], it["N"], it["L"]), 1.0)
-        f = workloads.bi_maxwellian(it["n_cells"], it["dim"], it["N"], it["L"], seed=it["seed"]).astype("float32")
-        x = torch.from_numpy(f).cuda()
-        entries.append((grids[key], x, torch.empty_like(x)))
+        hosts.append(workloads.bi_maxwellian(it["n_cells"], it["dim"], it["N"], it["L"], seed=it["seed"]))
         total += it["n_cells"]
     s = torch.cuda.current_stream()
-    bz.group_collide(entries, precision="fp32")
-    bz.check()
-    ms = _timed(lambda: bz.group_collide(entries, precision="fp32"), 1, s)
-    return {"ms_per_call": ms, "cells": total, "cell_collision_evals_per_s": total / (ms / 1e3),
-            "instances": [(it["dim"], it["N"], it["n_cells"]) for it in items]}
+    out = {"cells": total, "instances": [(it["dim"], it["N"], it["n_cells"]) for it in items],
+           "variants": {"%dd N=%d" % k: m.modesum_variant for k, m in grids.items()}}
+    results = {}
+    for prec in ("fp32", "fp64"):
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        entries = []
+        for it, f in zip(items, hosts):
+            x = torch.from_numpy(f).to("cuda", dt)
+            entries.append((grids[(it["dim"], it["N"])], x, torch.empty_like(x)))
+        bz.group_collide(entries, precision=prec)
+        bz.check()
+        ms = _timed(lambda: bz.group_collide(entries, precision=prec), 1, s)
+        out[prec] = {"ms_per_call": ms, "cell_collision_evals_per_s": total / (ms / 1e3)}
+        results[prec] = [Q for (_, _, Q) in entries]
+        del entries
+    # FP32 form against the FP64 GPU form on every cell of every instance
+    num = den = 0.0
+    for a, b in zip(results["fp32"], results["fp64"]):
+        num += ((a.double() - b) ** 2).sum().item()
+        den += (b ** 2).sum().item()
+    out["rel_l2_fp32_vs_fp64_gpu"] = (num / den) ** 0.5
+    out["speedup_fp32_over_fp64"] = out["fp64"]["ms_per_call"] / out["fp32"]["ms_per_call"]
+    return out
 
 
 def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, value64, prof, ms_name, k_ms,
             flops_launch, achieved, gpu_launches, e2e_val, clk, extra):
     import numpy as np
-    import oracle
-    # errors against the FP64 oracle on sampled cells (same FP32 inputs)
-    idx = np.linspace(0, cells - 1, 24).astype(int)
-    fs = f_host[idx].astype(np.float64)
-    k = oracle.Kernel(2, N_V, L_BOX, GAMMA)
-    Qr = k.collide(fs)
-    q32 = Q[idx].double().cpu().numpy()
-    err32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(Qr))
-    err64 = None
-    if Q64 is not None:
-        q64 = Q64[idx].cpu().numpy()
-        err64 = float(np.linalg.norm(q64 - Qr) / np.linalg.norm(Qr))
-    rho = fs.sum(1, keepdims=True) * k.dv ** 2
-    loss32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(rho * fs))   # error / |loss rate ~ rho f|
+    # errors: against the FP64 oracle on the cells its timed run covers (same
+    # FP32-rounded inputs), else the FP32 form against the FP64 GPU form
     cpu = None
+    err32 = err64 = loss32 = None
+    err32_vs64 = None
+    if Q64 is not None:
+        d = (Q.double() - Q64).norm().item()
+        err32_vs64 = d / Q64.norm().item()
     if not args.no_cpu_baseline:
-        cpu, _ = cpu_baseline(f_host[:4096], budget_s=15.0)
+        spread = np.linspace(0, cells - 1, 24).astype(np.int64)
+        cpu, idx, Qr, k = cpu_baseline(f_host, budget_s=15.0, check_idx=spread)
+        ti = torch_index(idx)
+        q32 = Q[ti].double().cpu().numpy()
+        err32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(Qr))
+        if Q64 is not None:
+            err64 = float(np.linalg.norm(Q64[ti].cpu().numpy() - Qr) / np.linalg.norm(Qr))
+        fs = f_host[idx].astype(np.float64)
+        rho = fs.sum(1, keepdims=True) * k.dv ** 2
+        loss32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(rho * fs))   # error / |loss rate ~ rho f|
+        nchk = len(idx)
+    else:
+        nchk = 0
     line = {
         "metric": METRIC, "value": value, "unit": "cell-collision evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -367,12 +401,12 @@ def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, valu
                    "l2": "inputs and outputs (268 MB each) exceed L2: no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "rel_l2_err": {"fp32_vs_oracle": err32, "fp64_vs_oracle": err64, "fp32_loss_scaled": loss32,
-                       "sample_cells": len(idx)},
+                       "oracle_cells": nchk, "fp32_vs_fp64_gpu_all_cells": err32_vs64},
         "fp64_form": {"value": value64, "unit": "cell-collision evals/s", "ms_per_step": ms64,
                       "speedup_fp32_over_fp64": value / value64} if Q64 is not None else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": MODESUM_TRAFFIC_65536 if (cells == CELLS and modes.modesum_r == 8) else None,
+                     "traffic": MODESUM_TRAFFIC_65536 if (cells == CELLS and modes.modesum_variant == 1) else None,
                      "kernel": ms_name,
                      "kernel_ms": k_ms, "flops_per_launch": flops_launch,
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},

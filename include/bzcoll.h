@@ -97,13 +97,15 @@ int init_velocity_grid(int dim, int n_per_dim, double half_width_L, bz_grid **ou
  * integral over |q| <= 2 lambda pi, lambda = 2/(3+sqrt 2), and the weights
  * beta-hat(l,m) = B-hat(l,m) - B-hat(m,m) of the mode sum; uploads FP64 and
  * FP32 copies (plus the symmetrised weight tiles of the FP32 kernels).
- * For 2-D grids with N <= 32 the register-blocked FP32 mode-sum kernel has two
- * variants (4 or 8 outputs per thread); the first build for a (dim, N, SM
- * count) times both on the current device (a few ms, zero spectra) and keeps
- * the faster.  The choice is cached in the process and, if the environment
- * variable BZ_TUNE_CACHE names a writable file, appended there as lines
- * "dim N sms R" and read back by later processes.  BZ_MODESUM_R=4 or 8 fixes
- * the variant without timing.  The call synchronises the current device.
+ * For 2-D grids with N <= 48 the register-blocked FP32 mode-sum kernel has
+ * three variants (see bz_modes_info); the first build for a (dim, N, SM count)
+ * times those that fit the grid on the current device (a few ms, zero spectra)
+ * and keeps the fastest.  The choice is cached in the process and, if the
+ * environment variable BZ_TUNE_CACHE names a writable file, appended there as
+ * lines "dim N sms variant" and read back by later processes.
+ * BZ_MODESUM_VARIANT=1, 2 or 3 fixes the variant without timing (ignored if
+ * that variant does not fit the grid).  The call synchronises the current
+ * device.
  *   g          : grid handle (not consumed; must outlive the modes handle)
  *   gamma      : 0 = Maxwell molecules, 1 = hard spheres (VHS); 0 <= gamma <= 2
  *   b0         : kernel constant; <= 0 selects 1/(2 pi) in 2-D, 1/(4 pi) in 3-D
@@ -198,8 +200,10 @@ const char *bz_last_error(void);
  * out[2] = h, out[3] = N^d, out[4] = half-spectrum modes (h+1) (2h+1)^(d-1),
  * out[5] = Gauss-Legendre nodes used, out[6] = unordered mode pairs summed
  * per cell by the symmetric FP32 kernel (algorithmic work unit), out[7] =
- * outputs per thread of the register-blocked FP32 kernel selected for this
- * grid (4 or 8), 0 if FP32 mode sums run on the generic kernel. */
+ * register-blocked FP32 mode-sum variant in use: 1 = 8 outputs per thread,
+ * 16 warps, 32-cell tiles; 2 = 4 outputs per thread, 32 warps, 32-cell tiles;
+ * 3 = 4 outputs per thread, 16 warps, 16-cell tiles; 0 = FP32 mode sums run
+ * on the generic kernel (3-D grids, 2-D grids with N > 48). */
 int bz_modes_info(const bz_modes *m, int64_t out[8]);
 
 /* bz_modes_beta -- copy beta-hat(l,m) for l, m in K_h (row-major flat mode

@@ -136,8 +136,8 @@ class Modes:
         self.gamma = gamma
         info = (ctypes.c_int64 * 8)()
         _check(load().bz_modes_info(h, info))
-        self.dim, self.N, self.h, self.nv, self.nhalf, self.nq, self.pairs_sym, self.modesum_r = list(info)
-        self.fast32 = self.modesum_r > 0   # register-blocked FP32 mode-sum kernel in use
+        self.dim, self.N, self.h, self.nv, self.nhalf, self.nq, self.pairs_sym, self.modesum_variant = list(info)
+        self.fast32 = self.modesum_variant > 0   # register-blocked FP32 mode-sum kernel in use
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

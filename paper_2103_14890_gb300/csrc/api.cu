@@ -616,7 +616,7 @@ int group_collide(const bz_group_item *items, int n_items, int precision, int fl
         return BZ_OK;
     };
     // one grouped launch per kernel variant (items keep the longest-first order)
-    for (int var = 0; var < 2; ++var) {
+    for (int var = 0; var < 3; ++var) {
         for (size_t q = 0; q < order.size(); ++q) {
             const bz_group_item &it = items[order[q]];
             if (precision != BZ_FP32 || !modesum32_2d_available(it.modes) || it.modes->variant != var) continue;
@@ -673,7 +673,7 @@ int bz_modes_info(const bz_modes *m, int64_t out[8]) {
     out[4] = v.nhalf;
     out[5] = m->nq;
     out[6] = m->pairs_sym;
-    out[7] = modesum32_2d_available(m) ? m->modesum_R : 0;
+    out[7] = modesum32_2d_available(m) ? m->modesum_variant : 0;
     return BZ_OK;
 }
 

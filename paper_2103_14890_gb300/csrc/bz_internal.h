@@ -54,13 +54,13 @@ struct bz_modes {
     // symmetric weight streams and task tables of the FP32 2-D kernel, one per
     // variant (k_modesum32.cu); d_W32 / d_task / w32_rowmax alias the variant
     // in use (null if the generic kernel serves this grid)
-    float *var_W[2];
-    int *var_task[2];
-    int var_rowmax[2];
-    int variant;         // index of the selected variant
-    int modesum_R;       // its outputs per thread (0: generic kernel)
+    float *var_W[3];
+    int *var_task[3];
+    int var_rowmax[3];
+    int variant;          // index of the selected variant
+    int modesum_variant;  // variant id reported to callers (index + 1; 0: generic kernel)
     float *d_W32;
-    int w32_rowmax;      // largest staged weight row (floats)
+    int w32_rowmax;       // largest staged weight row (floats)
     int *d_task;
     int64_t pairs_sym;   // unordered pairs per cell (algorithmic unit)
     // twiddle tables of the tile FP32 DFT kernels (k_dft32.cu), null if unused

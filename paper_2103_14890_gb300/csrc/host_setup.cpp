@@ -258,7 +258,7 @@ void modes_destroy(bz_modes *m) {
     if (!m) return;
     cudaFree(m->d_F64);
     cudaFree(m->d_F32);
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < 3; ++v) {
         cudaFree(m->var_W[v]);
         cudaFree(m->var_task[v]);
     }

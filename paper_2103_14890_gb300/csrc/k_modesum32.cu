@@ -1,5 +1,5 @@
 // k_modesum32.cu -- register-blocked FP32 mode sum of eq. CF1 (Sec. 3.3) for
-// 2-D velocity grids with N <= 32.
+// 2-D velocity grids with N <= 48.
 //
 // Work reduction (exact algebra, no approximation):
 //   * Q is real, so only k_1 >= 0 is computed (Q-hat_{-k} = conj(Q-hat_k)).
@@ -10,20 +10,29 @@
 //     in the stored half spectrum; f-hat_l with l_1 < 0 is conj(f-hat_{-l}).
 //
 // Layout and blocking:
-//   * one CTA = one tile of 32 cells; the tile's half spectrum (complex FP32,
-//     [mode][cell]) sits in shared memory; lane = cell, so every Fourier load
-//     is a conflict-free 32-cell row and every weight load is warp-uniform.
-//   * a task = (k_1, block of R consecutive k_2); a thread accumulates R
-//     complex outputs.  Two variants are compiled, R = 8 with 16 warps per CTA
-//     and R = 4 with 32 warps; the faster one for a grid is chosen once by
-//     timing both (autotune below).  Walking l_2 upwards slides the window of f-hat_m
-//     values (m_2 = k_2 - l_2) down by one, so each step loads one new f-hat_m,
-//     one f-hat_l and R weights for 6 R FP32 operations.
+//   * one CTA = one tile of C cells (C = 32, or 16 for grids whose spectrum
+//     does not fit 32 cells in shared memory); the tile's half spectrum
+//     (complex FP32, [mode][cell]) sits in shared memory with lane % C = cell,
+//     so every weight load is uniform over the lanes that share it and every
+//     Fourier load is a conflict-free row of C cells.
+//   * a task = (k_1, block of RT consecutive k_2).  With C = 32 a thread owns
+//     all RT = R outputs of its cell; with C = 16 the two half-warps split the
+//     block, each thread owning R = RT/2 of them.  Walking l_2 upwards slides
+//     the window of f-hat_m values (m_2 = k_2 - l_2) down by one, so each step
+//     loads one new f-hat_m, one f-hat_l and R weights for 6 R FP32 operations.
 //   * each task's weights form a contiguous stream [l_1][l_2 (padded to a
-//     multiple of R)][r]; one l_1 row is staged into a per-warp shared-memory
+//     multiple of RT)][r]; one l_1 row is staged into a per-warp shared-memory
 //     double buffer with cp.async while the previous row is being used.
-//   * accumulation: plain FP32 along an l_1 row (<= 32 terms), then a TwoSum
-//     fold of the row sum into a (hi, lo) pair per output.
+//   * the rows of the spectrum are stored back to back, with kPad zero columns
+//     before the first and after the last row only.  A column index that falls
+//     outside [-h, h] therefore reads a neighbouring row's (finite) value or a
+//     zero, and always meets a zero weight: the weight stream is zero wherever
+//     l_2, m_2 or k_2 leaves K_h.  The host checks that every column touched
+//     stays within kPad of [-h, h].
+//   * accumulation: plain FP32 along an l_1 row (<= 48 terms), then a TwoSum
+//     fold of the row sum into a (hi, lo) pair per output every 4 rows.
+//   * several kernel variants (R, warps, C) are compiled; the fastest one for a
+//     grid is chosen once by timing (autotune below).
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -41,19 +50,21 @@ namespace bz {
 
 namespace {
 
-// Kernel variants (outputs per thread R along k_2, warps per CTA); the
-// autotuner picks one per grid.
+// Kernel variants: outputs per thread R along k_2, warps per CTA, cells per
+// CTA.  Variant ids reported by bz_modes_info are index + 1.
 struct Variant {
-    int R, warps;
+    int R, warps, cells;
 };
-constexpr Variant kVariants[2] = {{8, 16}, {4, 32}};
+constexpr int kNumVariants = 3;
+constexpr Variant kVariants[kNumVariants] = {{8, 16, 32}, {4, 32, 32}, {4, 16, 16}};
+static_assert(kNumVariants == sizeof(bz_modes::var_W) / sizeof(float *), "one table slot per variant");
 constexpr int kTaskInts = 12;   // ints per task record
 
-constexpr int kPad = 8;         // zero columns on each side of a shared-memory row
+constexpr int kPad = 8;         // zero guard columns before the first and after the last row
 
 struct TaskRec {
-    int k1, k20, l1lo, nl1, l2lo, nblk, woff, rfirst;   // rfirst: first r this task stores
-    int rem, rowf, pad0, pad1;                          // steps of the last block, floats per l1 row
+    int k1, k20, l1lo, nl1, l2lo, nblk, woff, rfirst;   // rfirst: first r (of RT) this task stores
+    int rem, rowf, pad0, pad1;                          // floats per l1 row in rowf
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -81,16 +92,17 @@ __device__ __forceinline__ void stage_row(float *dst, const float *src, int nflo
 // One block of R l_2 steps.  The window of f-hat_m values lives in a 2R-slot
 // register array used under two alternating namings (PH = 0, 1): logical slot
 // j is physical slot (j + PH R) mod 2R, so moving the window by R between
-// blocks costs no register moves.  f-hat_l is read at lp, lp + ldir, ... with
-// ldir = +-32 elements (columns +-1); for l_1 < 0 the row is that of -l_1 read
-// backwards and conjugated (sg = -1).  Only two instances of this body exist,
-// which keeps the unrolled code inside the instruction cache.
-template <int RR, int PH>
+// blocks costs no register moves.  Columns are CS elements apart; f-hat_l is
+// read at lp, lp + ldir, ... with ldir = +-CS (columns +-1); for l_1 < 0 the
+// row is that of -l_1 read backwards and conjugated (sg = -1).  The weights
+// of step s are wb[s * WS + r].  Only two instances of this body exist per
+// variant, which keeps the unrolled code inside the instruction cache.
+template <int RR, int CS, int WS, int PH>
 __device__ __forceinline__ void block_pass(float2 (&win)[2 * RR], const float2 *__restrict__ mp,
                                            const float2 *__restrict__ lp, int ldir, float sg,
                                            const float *__restrict__ wb, float2 (&acc)[RR]) {
 #pragma unroll
-    for (int j = 0; j < RR; ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * 32];
+    for (int j = 0; j < RR; ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
 #pragma unroll
     for (int s = 0; s < RR; ++s) {
         float2 fl = *lp;
@@ -99,7 +111,7 @@ __device__ __forceinline__ void block_pass(float2 (&win)[2 * RR], const float2 *
         float wv[RR];
 #pragma unroll
         for (int q = 0; q < RR; q += 4) {
-            const float4 w4 = *reinterpret_cast<const float4 *>(wb + s * RR + q);
+            const float4 w4 = *reinterpret_cast<const float4 *>(wb + s * WS + q);
             wv[q] = w4.x;
             wv[q + 1] = w4.y;
             wv[q + 2] = w4.z;
@@ -117,33 +129,35 @@ __device__ __forceinline__ void block_pass(float2 (&win)[2 * RR], const float2 *
     }
 }
 
-// One l_1 row of a task: acc[r] += sum_l2 w(l2, r) f-hat_l(l2) f-hat_m(k2_0 + r - l2).
-// All columns lie inside the zero-padded shared-memory row, so no load needs a
-// bounds check (checked on the host when the task table is built).
-template <int RR>
+// One l_1 row of a task for this thread's R outputs:
+// acc[r] += sum_l2 w(l2, r) f-hat_l(l2) f-hat_m(k2_0 + r - l2).
+// rowl / rowm point at column 0 of the rows |l_1| and m_1 (this thread's cell);
+// wrow at this thread's first weight of the row.
+template <int RR, int CS, int WS>
 __device__ __forceinline__ void row_pass(const float2 *__restrict__ rowl, int dir,
                                          const float2 *__restrict__ rowm, const float *__restrict__ wrow,
-                                         int nblk, int l2lo, int mbase0, int c0, float2 (&acc)[RR]) {
+                                         int nblk, int l2lo, int mbase0, float2 (&acc)[RR]) {
     float2 win[2 * RR];
-    // columns are offset by c0 = h + kPad; a column c is element c * 32
-    const float2 *mp = rowm + (mbase0 + c0) * 32;
-    const float2 *lp = rowl + (dir * l2lo + c0) * 32;
-    const int ldir = dir * 32;
+    const float2 *mp = rowm + mbase0 * CS;
+    const float2 *lp = rowl + dir * l2lo * CS;
+    const int ldir = dir * CS;
     const float sg = (float)dir;
 #pragma unroll
-    for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * 32];
+    for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * CS];
     int blk = 0;
     for (; blk + 1 < nblk; blk += 2) {
-        block_pass<RR, 0>(win, mp, lp, ldir, sg, wrow + blk * RR * RR, acc);
-        block_pass<RR, 1>(win, mp - RR * 32, lp + RR * ldir, ldir, sg, wrow + (blk + 1) * RR * RR, acc);
-        mp -= 2 * RR * 32;
+        block_pass<RR, CS, WS, 0>(win, mp, lp, ldir, sg, wrow + blk * RR * WS, acc);
+        block_pass<RR, CS, WS, 1>(win, mp - RR * CS, lp + RR * ldir, ldir, sg, wrow + (blk + 1) * RR * WS, acc);
+        mp -= 2 * RR * CS;
         lp += 2 * RR * ldir;
     }
-    if (blk < nblk) block_pass<RR, 0>(win, mp, lp, ldir, sg, wrow + blk * RR * RR, acc);
+    if (blk < nblk) block_pass<RR, CS, WS, 0>(win, mp, lp, ldir, sg, wrow + blk * RR * WS, acc);
 }
 
-template <int RR, int WARPS>
+template <int RR, int WARPS, int CELLS>
 __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Group gd) {
+    constexpr int G = 32 / CELLS;     // lane groups splitting a task's outputs
+    constexpr int RT = RR * G;        // outputs per task
     extern __shared__ __align__(16) float4 smem4[];
     // this CTA's instance and tile (instances are ordered longest-first)
     int it = 0;
@@ -155,28 +169,29 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
     const int *__restrict__ tasks = ip.tasks;
     const int h = ip.h, M = ip.M, nhalf = ip.nhalf, wrow_max = ip.wrow_max;
     const int64_t n = ip.n;
-    const int MP = M + 2 * kPad;                                     // padded row length
-    float2 *Fs = reinterpret_cast<float2 *>(smem4);                  // [h+1][MP][32]
-    float *wsm = reinterpret_cast<float *>(Fs + (size_t)(h + 1) * MP * 32);   // [warps][2][wrow_max]
-    const int64_t tile = (int64_t)blockIdx.x - gd.tile_start[it];
+    const int64_t cta = (int64_t)blockIdx.x - gd.tile_start[it];
+    const int64_t tile = cta / G;                                    // 32-cell tile of the scratch layout
+    const int sub = (int)(cta % G);                                  // which CELLS-cell part of it
+    float2 *Fs = reinterpret_cast<float2 *>(smem4);                  // [kPad + nhalf + kPad][CELLS]
+    float *wsm = reinterpret_cast<float *>(Fs + (size_t)(nhalf + 2 * kPad) * CELLS);   // [warps][2][wrow_max]
     {
-        // copy the tile's half spectrum into zero-padded rows
-        const float4 *src = reinterpret_cast<const float4 *>(fhat + tile * (int64_t)nhalf * 32);
-        const int rowq = MP * 16;                                    // float4 per padded row
-        for (int i = threadIdx.x; i < (h + 1) * rowq; i += blockDim.x) {
-            const int row = i / rowq, q = i % rowq;
-            const int col = q / 16 - kPad;                           // unpadded column
-            smem4[i] = (col >= 0 && col < M) ? src[(row * M + col) * 16 + (q % 16)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        // copy this CTA's cells of the tile's half spectrum, zero the guards
+        constexpr int Q4 = CELLS / 2;                                // float4 per mode
+        const float4 *src = reinterpret_cast<const float4 *>(fhat + tile * (int64_t)nhalf * 32) + sub * Q4;
+        const int body = nhalf * Q4, guard = kPad * Q4;
+        for (int i = threadIdx.x; i < body + 2 * guard; i += blockDim.x) {
+            const int b = i - guard;
+            smem4[i] = (b >= 0 && b < body) ? src[(b / Q4) * 16 + (b % Q4)] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cell = lane % CELLS, grp = lane / CELLS;
     float *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
     float *wbuf1 = wbuf0 + wrow_max;
     const int tbeg = tasks[warp], tend = tasks[warp + 1];
     const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS + 1);
-    const float2 *Fl = Fs + lane;
-    const int c0 = h + kPad;
+    const float2 *F0 = Fs + (size_t)(kPad + h) * CELLS + cell;      // (row 0, column 0) of this cell
 
     for (int t = tbeg; t < tend; ++t) {
         const TaskRec tk = trec[t];
@@ -185,6 +200,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
         float2 hi[RR], lo[RR], acc[RR];
 #pragma unroll
         for (int r = 0; r < RR; ++r) hi[r] = lo[r] = acc[r] = make_float2(0.f, 0.f);
+        const int k20 = tk.k20 + grp * RR;                // this thread's first output column
+        const int mbase0 = k20 - tk.l2lo - (RR - 1);
         stage_row(wbuf0, wsrc, rowf, lane);
         for (int i = 0; i < tk.nl1; ++i) {
             const float *wcur = (i & 1) ? wbuf1 : wbuf0;
@@ -197,12 +214,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
             __syncwarp();
             const int l1 = tk.l1lo + i;
             const int m1 = tk.k1 - l1;                    // >= 0: stored row
-            const int mbase0 = tk.k20 - tk.l2lo - (RR - 1);
-            const float2 *rowm = Fl + (size_t)m1 * MP * 32;
             const int dir = l1 < 0 ? -1 : 1;              // f-hat_l = conj(f-hat_{-l}) for l_1 < 0
-            row_pass<RR>(Fl + (size_t)(dir * l1) * MP * 32, dir, rowm, wcur, tk.nblk, tk.l2lo, mbase0, c0, acc);
+            row_pass<RR, CELLS, RT>(F0 + (size_t)(dir * l1) * M * CELLS, dir, F0 + (size_t)m1 * M * CELLS,
+                                    wcur + grp * RR, tk.nblk * G, tk.l2lo, mbase0, acc);
             __syncwarp();
-            // fold the FP32 row sums (<= 4 rows of <= 32 terms) into (hi, lo)
+            // fold the FP32 row sums (<= 4 rows) into (hi, lo)
             if ((i & 3) == 3 || i + 1 == tk.nl1) {
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
@@ -217,19 +233,21 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
                 }
             }
         }
-        if (tile * 32 + lane < n) {
-            float2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.k1 * M * 32 + lane;
+        const int64_t c = tile * 32 + sub * CELLS + cell;
+        if (c < n) {
+            float2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.k1 * M * 32 + sub * CELLS + cell;
 #pragma unroll
             for (int r = 0; r < RR; ++r) {
-                const int k2 = tk.k20 + r;
-                if (r >= tk.rfirst && k2 <= h) out[(k2 + h) * 32] = make_float2(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
+                const int k2 = k20 + r;
+                if (grp * RR + r >= tk.rfirst && k2 <= h) out[(k2 + h) * 32] = make_float2(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
             }
         }
     }
 }
 
-size_t smem_bytes(const GridView &g, int wrow_max, int warps) {
-    return sizeof(float2) * (size_t)(g.h + 1) * (g.M + 2 * kPad) * 32 + sizeof(float) * (size_t)warps * 2 * wrow_max;
+size_t smem_bytes(const GridView &g, int wrow_max, int v) {
+    return sizeof(float2) * (size_t)(g.nhalf + 2 * kPad) * kVariants[v].cells +
+           sizeof(float) * (size_t)kVariants[v].warps * 2 * wrow_max;
 }
 
 }  // namespace
@@ -238,15 +256,18 @@ size_t smem_bytes(const GridView &g, int wrow_max, int warps) {
 double beta_host(const bz_modes *m, const int *l, const int *mm);
 
 // Weight stream and task table of one variant (slot v); false if the grid is
-// not covered by this kernel (the generic kernel then serves it).
+// not covered by this variant (another variant or the generic kernel serves it).
 static bool build_variant(bz_modes *m, int v, int &rc) {
-    const int R = kVariants[v].R, kWarps = kVariants[v].warps;
+    const int R = kVariants[v].R * (32 / kVariants[v].cells);   // outputs per task (RT)
+    const int kWarps = kVariants[v].warps;
     rc = BZ_OK;
     const GridView &gv = m->g->v;
-    if (gv.dim != 2 || gv.N > 32 || gv.M < R) return false;
+    if (gv.dim != 2 || gv.N > 48 || gv.M < R) return false;
+    // shared memory of the spectrum alone must leave room for the weight buffers
+    if (sizeof(float2) * (size_t)(gv.nhalf + 2 * kPad) * kVariants[v].cells > 200 * 1024) return false;
     const int h = gv.h;
     const int nb = (gv.M + R - 1) / R;
-    const int lo_col = -h - kPad, hi_col = h + kPad;         // addressable padded columns
+    const int lo_col = -h - kPad, hi_col = h + kPad;         // addressable columns
     std::vector<TaskRec> tasks;
     std::vector<float> W;
     std::vector<double> cost;
@@ -262,7 +283,7 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
             const int nblk = (len + R - 1) / R;
             const int npad = nblk * R;
             // place the padded range [l2lo, l2lo + npad - 1] so that every f-hat_l
-            // column and every window column k2 - l2 lies in the zero-padded row
+            // column and every window column k2 - l2 lies within kPad of [-h, h]
             int l2lo = 0;
             bool placed = false;
             for (int cand = lo - (npad - len); cand <= lo && !placed; ++cand) {
@@ -272,7 +293,7 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
                 l2lo = cand;
                 placed = true;
             }
-            if (!placed) return false;                       // grid not covered by the padded layout
+            if (!placed) return false;
             TaskRec t;
             t.k1 = k1;
             t.k20 = k20;
@@ -329,7 +350,7 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
     tab[kWarps] = pos;
     int wrow_max = 0;
     for (auto &t : tasks) wrow_max = std::max(wrow_max, t.nblk * R * R);   // staging buffer: whole blocks
-    if (smem_bytes(gv, wrow_max, kWarps) > 227 * 1024) return false;   // does not fit: generic kernel
+    if (smem_bytes(gv, wrow_max, v) > 227 * 1024) return false;   // does not fit
     float *dW = nullptr;
     int *dT = nullptr;
     cudaError_t e = cudaMalloc(&dW, sizeof(float) * W.size());
@@ -350,19 +371,22 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
 
 bool modesum32_2d_available(const bz_modes *m) { return m->d_W32 != nullptr; }
 
-static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStream_t st) {
-    cudaError_t e;
-    const unsigned grid = (unsigned)gd.tile_start[gd.nitems];
-    if (kVariants[v].R == 8) {
-        e = cudaFuncSetAttribute(modesum32_kernel<8, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        modesum32_kernel<8, 16><<<grid, 16 * 32, sm, st>>>(gd);
-    } else {
-        e = cudaFuncSetAttribute(modesum32_kernel<4, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        modesum32_kernel<4, 32><<<grid, 32 * 32, sm, st>>>(gd);
-    }
+template <int RR, int WARPS, int CELLS>
+static cudaError_t launch_instance(const Mode32Group &gd, size_t sm, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(modesum32_kernel<RR, WARPS, CELLS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    modesum32_kernel<RR, WARPS, CELLS><<<(unsigned)gd.tile_start[gd.nitems], WARPS * 32, sm, st>>>(gd);
     return cudaGetLastError();
+}
+
+static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStream_t st) {
+    switch (v) {
+        case 0: return launch_instance<8, 16, 32>(gd, sm, st);
+        case 1: return launch_instance<4, 32, 32>(gd, sm, st);
+        case 2: return launch_instance<4, 16, 16>(gd, sm, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 static void fill_item(Mode32Item &it, const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n) {
@@ -378,6 +402,12 @@ static void fill_item(Mode32Item &it, const bz_modes *m, int v, const float2 *fh
     it.n = n;
 }
 
+// CTAs of an instance of n cells: one per CELLS cells of each 32-cell tile.
+static int64_t ctas_for(int v, int64_t n) {
+    const int G = 32 / kVariants[v].cells;
+    return ((n + 31) / 32) * G;
+}
+
 static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n,
                                   cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
@@ -386,8 +416,8 @@ static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, 
     gd.nitems = 1;
     fill_item(gd.item[0], m, v, fhat, Qhat, n);
     gd.tile_start[0] = 0;
-    gd.tile_start[1] = (n + 31) / 32;
-    return launch_group(gd, v, smem_bytes(m->g->v, m->var_rowmax[v], kVariants[v].warps), st);
+    gd.tile_start[1] = ctas_for(v, n);
+    return launch_group(gd, v, smem_bytes(m->g->v, m->var_rowmax[v], v), st);
 }
 
 cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
@@ -406,25 +436,28 @@ cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *cons
     memset(&gd, 0, sizeof gd);
     gd.nitems = count;
     size_t sm = 0;
-    int64_t tiles = 0;
+    int64_t ctas = 0;
     for (int i = 0; i < count; ++i) {
         if (ms[i]->variant != v) return cudaErrorInvalidValue;
         fill_item(gd.item[i], ms[i], v, fhat[i], Qhat[i], n[i]);
-        gd.tile_start[i] = tiles;
-        tiles += (n[i] + 31) / 32;
-        sm = std::max(sm, smem_bytes(ms[i]->g->v, ms[i]->var_rowmax[v], kVariants[v].warps));
+        gd.tile_start[i] = ctas;
+        ctas += ctas_for(v, n[i]);
+        sm = std::max(sm, smem_bytes(ms[i]->g->v, ms[i]->var_rowmax[v], v));
     }
-    gd.tile_start[count] = tiles;
-    if (tiles == 0) return cudaSuccess;
+    gd.tile_start[count] = ctas;
+    if (ctas == 0) return cudaSuccess;
+    if (sm > 227 * 1024) return cudaErrorInvalidValue;
     return launch_group(gd, v, sm, st);
 }
+
+int modesum32_variant_count() { return kNumVariants; }
 
 // ---- autotuner ------------------------------------------------------------
 // Times every buildable variant once per (dimension, N, SM count) on a
 // synthetic batch (zero spectra: the kernel's cost does not depend on the
-// values) of two CTAs per SM and keeps the fastest.  Results are cached for
-// the process and, when BZ_TUNE_CACHE names a file, in that file as lines
-// "dim N sms R".
+// values) of two 32-cell tiles per SM and keeps the fastest.  Results are
+// cached for the process and, when BZ_TUNE_CACHE names a file, in that file as
+// lines "dim N sms variant" (variant = index + 1).
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int>, int> g_tune;
 
@@ -440,25 +473,25 @@ static void tune_file_load() {
     if (!path) return;
     FILE *fp = fopen(path, "r");
     if (!fp) return;
-    int d, N, sms, r;
-    while (fscanf(fp, "%d %d %d %d", &d, &N, &sms, &r) == 4) g_tune[std::make_tuple(d, N, sms)] = r;
+    int d, N, sms, id;
+    while (fscanf(fp, "%d %d %d %d", &d, &N, &sms, &id) == 4) g_tune[std::make_tuple(d, N, sms)] = id - 1;
     fclose(fp);
 }
 
-static void tune_file_store(int d, int N, int sms, int r) {
+static void tune_file_store(int d, int N, int sms, int v) {
     const char *path = getenv("BZ_TUNE_CACHE");
     if (!path) return;
     FILE *fp = fopen(path, "a");
     if (!fp) return;
-    fprintf(fp, "%d %d %d %d\n", d, N, sms, r);
+    fprintf(fp, "%d %d %d %d\n", d, N, sms, v + 1);
     fclose(fp);
 }
 
 static int autotune(bz_modes *m, int &rc) {
     rc = BZ_OK;
     const GridView &gv = m->g->v;
-    int avail[2], na = 0;
-    for (int v = 0; v < 2; ++v)
+    int avail[kNumVariants], na = 0;
+    for (int v = 0; v < kNumVariants; ++v)
         if (m->var_W[v]) avail[na++] = v;
     if (na == 1) return avail[0];
     const int sms = sm_count();
@@ -468,7 +501,7 @@ static int autotune(bz_modes *m, int &rc) {
     auto it = g_tune.find(key);
     if (it != g_tune.end())
         for (int q = 0; q < na; ++q)
-            if (kVariants[avail[q]].R == it->second) return avail[q];
+            if (avail[q] == it->second) return avail[q];
     const int64_t n = (int64_t)2 * sms * 32;
     const size_t bytes = 2 * sizeof(float2) * (size_t)((n + 31) / 32) * gv.nhalf * 32;
     void *buf = nullptr;
@@ -502,8 +535,8 @@ static int autotune(bz_modes *m, int &rc) {
         rc = cuda_fail(e, "build_kernel_modes: autotune");
         return avail[0];
     }
-    g_tune[key] = kVariants[pick].R;
-    tune_file_store(gv.dim, gv.N, sms, kVariants[pick].R);
+    g_tune[key] = pick;
+    tune_file_store(gv.dim, gv.N, sms, pick);
     return pick;
 }
 
@@ -511,9 +544,10 @@ int modes_build_fp32_tables(bz_modes *m) {
     m->d_W32 = nullptr;
     m->d_task = nullptr;
     m->variant = 0;
+    m->modesum_variant = 0;
     int rc = BZ_OK;
     bool any = false;
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < kNumVariants; ++v) {
         m->var_W[v] = nullptr;
         m->var_task[v] = nullptr;
         m->var_rowmax[v] = 0;
@@ -521,11 +555,11 @@ int modes_build_fp32_tables(bz_modes *m) {
         if (rc) return rc;
     }
     if (!any) return BZ_OK;
-    const char *force = getenv("BZ_MODESUM_R");   // fixed choice (measurement of one variant)
+    const char *force = getenv("BZ_MODESUM_VARIANT");   // fixed choice (1-based id), no timing
     int v = -1;
     if (force) {
-        for (int q = 0; q < 2; ++q)
-            if (m->var_W[q] && kVariants[q].R == atoi(force)) v = q;
+        const int id = atoi(force) - 1;
+        if (id >= 0 && id < kNumVariants && m->var_W[id]) v = id;
     }
     if (v < 0) v = autotune(m, rc);
     if (rc) return rc;
@@ -533,7 +567,7 @@ int modes_build_fp32_tables(bz_modes *m) {
     m->d_W32 = m->var_W[v];
     m->d_task = m->var_task[v];
     m->w32_rowmax = m->var_rowmax[v];
-    m->modesum_R = kVariants[v].R;
+    m->modesum_variant = v + 1;
     return BZ_OK;
 }
 

@@ -55,23 +55,40 @@ def test_kernel_modes_match_oracle(bz, oracle_k, dim, N, gamma):
 
 
 def test_fast_kernels_selected(bz):
-    """The register-blocked FP32 mode sum serves every 2-D grid with 16 <= N <= 32
+    """The register-blocked FP32 mode sum serves every 2-D grid with 16 <= N <= 48
     (a silent fall back to the generic kernel would hide a table-building bug)."""
     for N in (16, 24, 32):
-        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_r in (4, 8), N
-    assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_r == 0
+        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant in (1, 2, 3), N
+    assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_variant == 3    # only 16-cell tiles fit
+    assert bz.Modes(bz.Grid(2, 64, 10.0), 1.0).modesum_variant == 0
+    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant == 0
 
 
-@pytest.mark.parametrize("R", [4, 8])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("N", [16, 24, 32])
-def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, N, R):
-    """Both register-blocked variants (fixed through BZ_MODESUM_R, bypassing the
-    autotuner) against the oracle: 70 cells = 2 full tiles and a ragged tail."""
-    monkeypatch.setenv("BZ_MODESUM_R", str(R))
+def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, N, variant):
+    """Every register-blocked variant (fixed through BZ_MODESUM_VARIANT, bypassing
+    the autotuner) against the oracle: 70 cells = 2 full tiles and a ragged tail."""
+    monkeypatch.setenv("BZ_MODESUM_VARIANT", str(variant))
     L = 10.0
     m = bz.Modes(bz.Grid(2, N, L), 1.0)
-    assert m.modesum_r == R
+    assert m.modesum_variant == variant
     f = workloads.bi_maxwellian(70, 2, N, L, seed=1100 + N)
+    fin = as_input(f, "fp32")
+    Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32")
+    bz.check()
+    Qr = oracle_k(2, N, L, 1.0).collide(fin)
+    assert relerr(Q.double().cpu().numpy(), Qr) < TOL32
+
+
+@pytest.mark.parametrize("n", [1, 16, 17, 45])
+def test_fp32_48_grid_16_cell_tiles(bz, oracle_k, n):
+    """48^2 grid on [-10,10]^2 (16-cell tiles): single cell, exactly one CTA,
+    one past it, and a ragged 32-cell tile pair, against the oracle."""
+    N, L = 48, 10.0
+    m = bz.Modes(bz.Grid(2, N, L), 1.0)
+    assert m.modesum_variant == 3
+    f = workloads.bi_maxwellian(n, 2, N, L, seed=1200 + n)
     fin = as_input(f, "fp32")
     Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32")
     bz.check()

@@ -38,14 +38,15 @@ def test_group_collide_matches_per_instance(bz, precision):
 
 
 def test_group_collide_mixed_variants(bz, monkeypatch):
-    """Instances on different register-blocked variants (R = 4 and R = 8) in one
-    call: one grouped launch per variant, results equal to per-instance calls."""
+    """Instances on different register-blocked variants in one call (one grouped
+    launch per variant), results equal to per-instance calls."""
     import torch
     entries, refs = [], []
-    for i, (N, R, n) in enumerate([(32, 8, 80), (24, 4, 50), (32, 4, 33), (16, 8, 70)]):
-        monkeypatch.setenv("BZ_MODESUM_R", str(R))
+    for i, (N, var, n) in enumerate([(32, 1, 80), (24, 2, 50), (32, 3, 33), (16, 1, 70), (48, 3, 21),
+                                     (24, 3, 40)]):
+        monkeypatch.setenv("BZ_MODESUM_VARIANT", str(var))
         m = bz.Modes(bz.Grid(2, N, 10.0), 1.0)
-        assert m.modesum_r == R
+        assert m.modesum_variant == var
         f = to_dev(workloads.bi_maxwellian(n, 2, N, 10.0, seed=90 + i), "fp32")
         refs.append(bz.collide_batch(m, f, precision="fp32").cpu().numpy())
         entries.append((m, f, torch.full_like(f, float("nan"))))
