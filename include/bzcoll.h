@@ -74,6 +74,8 @@ extern "C" {
 /* IMEX schemes (Sec. 3.4) and collision models */
 #define BZ_ARS222   0      /* ARS(2,2,2), 3 stages, 2nd order */
 #define BZ_BPR343   1      /* BPR(3,4,3), 5 stages, 3rd order */
+#define BZ_IMEX_EULER 2    /* first-order IMEX Euler, 2 stages (forward Euler
+                              explicit part, backward Euler penalty) */
 #define BZ_BOLTZMANN 0     /* explicit G = Q - BGK, implicit BGK penalty */
 #define BZ_BGK       1     /* BGK relaxation only (G = 0) */
 
@@ -139,7 +141,9 @@ int collide_batch(const bz_modes *m, int precision, int flags, const void *f, vo
  *   F_l = (R_l + dt A_ll (nu_l/eps) M_l) / (1 + dt A_ll nu_l/eps)
  *   P_l = nu_l (M_l - F_l),  G_l = Q(F_l) - P_l  (G_l = 0 for BZ_BGK or when no
  *   later stage uses it).
- *   scheme      : BZ_ARS222 or BZ_BPR343 (tableaux of Sec. 3.4)
+ *   scheme      : BZ_ARS222, BZ_BPR343 (tableaux of Sec. 3.4) or BZ_IMEX_EULER
+ *                 (the first-order scheme Sec. 3.4 names without a tableau:
+ *                 At = [[0,0],[1,0]], A = [[0,0],[0,1]])
  *   stage       : 1 .. stages(scheme)
  *   model       : BZ_BOLTZMANN or BZ_BGK
  *   dt, eps     : time step and Knudsen number (> 0)

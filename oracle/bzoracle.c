@@ -479,8 +479,8 @@ void orc_maxwellian(const orc_grid *g, const double *U, double *Mout) {
 #define MAXS 5
 
 /* Butcher tableaux of Sec. 3.4.  Explicit At (strictly lower) and implicit
- * A (lower, diagonal included); both schemes are stiffly accurate (last row =
- * weights), so f^{n+1} is the last stage value. */
+ * A (lower, diagonal included); all three schemes are stiffly accurate (last
+ * row = weights), so f^{n+1} is the last stage value. */
 static int tableau(int scheme, int *s, double At[MAXS][MAXS], double A[MAXS][MAXS]) {
     memset(At, 0, sizeof(double) * MAXS * MAXS);
     memset(A, 0, sizeof(double) * MAXS * MAXS);
@@ -504,6 +504,15 @@ static int tableau(int scheme, int *s, double At[MAXS][MAXS], double A[MAXS][MAX
         A[2][0] = 5.0 / 18.0; A[2][1] = -1.0 / 9.0; A[2][2] = 0.5;
         A[3][0] = 0.5; A[3][3] = 0.5;
         A[4][0] = 0.25; A[4][2] = 0.75; A[4][3] = -0.5; A[4][4] = 0.5;
+        return 0;
+    }
+    if (scheme == 2) {               /* first-order IMEX Euler: forward Euler for
+                                        the explicit part, backward Euler for the
+                                        implicit penalty (Sec. 3.4 names it but
+                                        prints no tableau) */
+        *s = 2;
+        At[1][0] = 1.0;
+        A[1][1] = 1.0;
         return 0;
     }
     return -1;

@@ -90,7 +90,7 @@ void   orc_moments(const orc_grid *g, const double *f, double *U);
 void   orc_maxwellian(const orc_grid *g, const double *U, double *Mout);
 
 /* Penalised IMEX Runge-Kutta local step for a batch of cells.
- *   scheme: 0 = ARS(2,2,2), 1 = BPR(3,4,3)
+ *   scheme: 0 = ARS(2,2,2), 1 = BPR(3,4,3), 2 = first-order IMEX Euler
  *   model : 0 = Boltzmann (explicit G = Q - BGK, implicit BGK penalty),
  *           1 = BGK only (G = 0)
  *   Lres  : optional transport residuals [stages][ncells][nv] or NULL.

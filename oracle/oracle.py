@@ -98,9 +98,9 @@ def radial_bhat(dim, gamma, b0, nq, a, b):
     return load().orc_radial_Bhat(dim, gamma, b0, nq, float(a), float(b))
 
 
-SCHEMES = {"ars222": 0, "bpr343": 1}
+SCHEMES = {"ars222": 0, "bpr343": 1, "euler": 2}
 MODELS = {"boltzmann": 0, "bgk": 1}
-STAGES = {"ars222": 3, "bpr343": 5}
+STAGES = {"ars222": 3, "bpr343": 5, "euler": 2}
 
 
 class Kernel:

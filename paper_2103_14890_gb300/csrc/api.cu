@@ -132,7 +132,7 @@ struct ProfScope {
         if (_e != cudaSuccess) return cuda_fail(_e, what); \
     } while (0)
 
-// Butcher tableaux of Sec. 3.4 (explicit At, implicit A), both stiffly accurate.
+// Butcher tableaux of Sec. 3.4 (explicit At, implicit A), all stiffly accurate.
 struct Tableau {
     int s;
     double At[5][5], A[5][5];
@@ -171,6 +171,12 @@ bool tableau(int scheme, Tableau &t) {
         t.A[4][2] = 0.75;
         t.A[4][3] = -0.5;
         t.A[4][4] = 0.5;
+        return true;
+    }
+    if (scheme == BZ_IMEX_EULER) {
+        t.s = 2;
+        t.At[1][0] = 1.0;
+        t.A[1][1] = 1.0;
         return true;
     }
     return false;

@@ -15,7 +15,7 @@ def bz():
     return bz_module()
 
 
-@pytest.mark.parametrize("scheme", ["ars222", "bpr343"])
+@pytest.mark.parametrize("scheme", ["ars222", "bpr343", "euler"])
 @pytest.mark.parametrize("model", ["boltzmann", "bgk"])
 def test_stages_fp64_match_oracle(bz, scheme, model):
     import oracle
@@ -56,7 +56,7 @@ def test_transport_residual_and_conserve_fp64(bz):
     assert np.abs(got - want).max() < 1e-12 * np.abs(f).max()
 
 
-@pytest.mark.parametrize("scheme", ["ars222", "bpr343"])
+@pytest.mark.parametrize("scheme", ["ars222", "bpr343", "euler"])
 def test_stiff_step_fp64_matches_oracle(bz, scheme):
     """dt/eps = 5 (eps = 5e-5): the plain form still reproduces the oracle."""
     import oracle

@@ -2,8 +2,9 @@
 
 - BGK-only model: the step is the implicit Runge-Kutta method applied to the
   linear relaxation, so f^{n+1} - M = R(z) (f^n - M) with z = -dt rho/eps and
-  R the stability function of the implicit tableau (closed form for ARS(2,2,2),
-  numpy linear algebra for BPR(3,4,3); tableaux typed from the paper);
+  R the stability function of the implicit tableau (closed form for ARS(2,2,2)
+  and for IMEX Euler, R(z) = 1/(1 - z); numpy linear algebra for BPR(3,4,3);
+  tableaux typed from the paper);
 - Boltzmann model: moments are conserved by the step when Q is conserving;
   the stiff limit keeps a Maxwellian a Maxwellian (asymptotic preservation);
   the global error falls at the order of the scheme.
@@ -19,6 +20,8 @@ G = 1.0 - 1.0 / math.sqrt(2.0)
 
 
 def _A_impl(scheme):
+    if scheme == "euler":
+        return np.array([[0, 0], [0, 1]], float)
     if scheme == "ars222":
         return np.array([[0, 0, 0], [0, G, 0], [0, 1 - G, G]], float)
     return np.array([[0, 0, 0, 0, 0],
@@ -40,9 +43,42 @@ def test_ars_closed_form_matches_linear_algebra():
     for z in (-0.1, -3.0, -1e4):
         closed = (1 + (1 - 2 * G) * z) / (1 - G * z) ** 2
         assert abs(closed - _stability("ars222", z)) < 1e-14 * max(1, abs(closed))
+        assert abs(1 / (1 - z) - _stability("euler", z)) < 1e-15
 
 
-@pytest.mark.parametrize("scheme", ["ars222", "bpr343"])
+def test_euler_bgk_step_closed_form(oracle_mod):
+    """IMEX Euler on the BGK model: f^{n+1} = (f^n + c M)/(1 + c), c = dt rho/eps,
+    with M the Maxwellian of f^n (backward Euler of the linear relaxation)."""
+    k = oracle_mod.Kernel(2, 16, 8.0, 0.0)
+    f = workloads.bi_maxwellian(2, 2, 16, 8.0, seed=24)
+    dt, eps = 0.03, 0.01
+    out = k.imex_step(f, dt, eps, scheme="euler", model="bgk")
+    for fn, fo in zip(f, out):
+        U = k.moments(fn)
+        c = dt * U[0] / eps
+        want = (fn + c * k.maxwellian(U).ravel()) / (1 + c)
+        assert np.abs(fo - want).max() < 1e-14 * np.abs(fn).max()
+
+
+def test_euler_boltzmann_step_is_explicit_plus_penalty(oracle_mod):
+    """IMEX Euler on the Boltzmann model, written out: G = Q(f) - rho (M - f),
+    R = f + dt G/eps, then the backward-Euler penalty with the moments of R."""
+    k = oracle_mod.Kernel(2, 16, 8.0, 1.0)
+    f = workloads.bi_maxwellian(2, 2, 16, 8.0, seed=25)
+    dt, eps = 0.02, 0.1
+    out = k.imex_step(f, dt, eps, scheme="euler")
+    Q = k.collide(f)
+    for i, fn in enumerate(f):
+        U = k.moments(fn)
+        G1 = Q[i] - U[0] * (k.maxwellian(U).ravel() - fn)
+        R = fn + dt * G1 / eps
+        U2 = k.moments(R)
+        c = dt * U2[0] / eps
+        want = (R + c * k.maxwellian(U2).ravel()) / (1 + c)
+        assert np.abs(out[i] - want).max() < 1e-13 * np.abs(fn).max()
+
+
+@pytest.mark.parametrize("scheme", ["ars222", "bpr343", "euler"])
 @pytest.mark.parametrize("dt_over_eps", [0.05, 1.0, 40.0, 1e6])
 def test_bgk_model_amplification(oracle_mod, scheme, dt_over_eps):
     N, L = 32, 10.0
@@ -123,7 +159,7 @@ def _bkw(r2, t):
     return np.exp(-r2 / (2 * S)) / (2 * math.pi * S ** 2) * (2 * S - 1 + (1 - S) / (2 * S) * r2)
 
 
-@pytest.mark.parametrize("scheme,order", [("ars222", 2), ("bpr343", 3)])
+@pytest.mark.parametrize("scheme,order", [("euler", 1), ("ars222", 2), ("bpr343", 3)])
 def test_time_order_on_bkw(oracle_mod, scheme, order):
     """eps = 1, Maxwell molecules: error against a fine-step run of the same
     scheme on the same grid falls as dt^order."""
