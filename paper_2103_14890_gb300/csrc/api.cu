@@ -249,7 +249,7 @@ int phase_inverse(const bz_modes *m, int precision, int flags, const void *qh, v
     } else if (m->d_T1) {
         BZ_LAUNCH("dft_inverse_f32", st,
                   launch_dft32_inverse_tile(v, m->d_T2i, m->d_T3, static_cast<const float2 *>(qh),
-                                            static_cast<float *>(Q), n, g->cinv, ep, st),
+                                            static_cast<float *>(Q), n, m->scale, g->cinv, ep, st),
                   "collide: inverse DFT");
     } else {
         BZ_LAUNCH("dft_inverse_f32_generic", st,

@@ -102,8 +102,8 @@ int dft32_tables(const GridView &g, double scale, float2 **T1, float2 **T2, floa
 cudaError_t launch_dft32_forward_tile(const GridView &g, const float2 *T1, const float2 *T2, const float *f,
                                       float2 *fhat, int64_t n, cudaStream_t st);
 cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *T2i, const float2 *T3, const float2 *Qhat,
-                                      float *Q, int64_t n, const double *cinv, const InvEpilogue &ep,
-                                      cudaStream_t st);
+                                      float *Q, int64_t n, double scale, const double *cinv,
+                                      const InvEpilogue &ep, cudaStream_t st);
 
 // ---- register-blocked FP32 2-D mode sum (k_modesum32.cu) --------------------
 constexpr int kMaxGroup = 16;      // instances per grouped launch

@@ -1,6 +1,11 @@
 // k_dft32.cu -- tile-based FP32 forward / inverse DFT for 2-D grids with
 // N in {16, 24, 32} (Sec. 3.3, eq. FC and eq. FU sampled on the grid).
 //
+// N = 16 and 32 use register-resident radix-2 FFTs (fft_fwd32_kernel,
+// fft_inv32_kernel, below); N = 24 uses the dense matrix form
+// (dft_fwd32_kernel, dft_inv32_kernel).  Both compute the same sums; the FFT
+// needs about a fifth of the instructions.
+//
 // One CTA handles one tile of 32 cells (the unit of the tiled Fourier layout
 // [tile][mode][cell]).  The 2-D transform is separable:
 //   forward  A[k1][j2]  = sum_j1 E1[j1][k1] f[j1][j2]           (k1 = 0..h)
@@ -285,6 +290,192 @@ dft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, const f
     inv32_epilogue<N>(q1, tile * 32 + c1, lane, cinv, conserve, P, Q, L, dv, n);
 }
 
+
+// ---------------------------------------------------------------------------
+// Radix-2 FFT form (N = 16, 32).
+//
+// With omega = e^{2 pi i / N} and u_j = -pi + 2 pi j / N, e^{-i k u_j} =
+// (-1)^k omega^{-k j}, so
+//   f-hat[k1][k2] = N^-2 (-1)^(k1+k2) sum_j1 sum_j2 f[j1][j2] omega^-(k1 j1 + k2 j2)
+//   Q[j1][j2]     = s^(d+gamma) Re sum_{k1 >= 0} c_k1 (-1)^k1 omega^(k1 j1)
+//                   sum_k2 (-1)^k2 Q-hat[k1][k2] omega^(k2 j2).
+// Forward: per column j2, a real length-N transform over j1 (packed into a
+// complex length-N/2 FFT plus the even/odd untangling), k1 = 0..N/2-1 kept;
+// per row k1, a complex length-N FFT over j2, k2 = -h..h kept.  Inverse:
+// per row k1, a complex length-N inverse FFT over k2 (the Nyquist slot k2 =
+// N/2 is zero); per column j2, a Hermitian-to-real inverse over k1 through a
+// complex length-N/2 inverse FFT.  All loops are unrolled with compile-time
+// indices, so the data stay in registers and the twiddles are constant-bank
+// operands.
+
+__constant__ float2 c_w32[32];          // e^{-2 pi i k / 32}, k = 0..31
+
+constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+constexpr int bitrev(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+// In-place radix-2 decimation-in-time FFT of length L <= 32 whose input sits
+// in bit-reversed order; output in natural order.  SIGN = -1: sum x_n
+// e^{-2 pi i k n / L}; SIGN = +1: sum x_n e^{+2 pi i k n / L} (unnormalised).
+template <int L, int SIGN>
+__device__ __forceinline__ void fft_dit(float2 (&a)[L]) {
+#pragma unroll
+    for (int m = 1; m < L; m <<= 1) {
+#pragma unroll
+        for (int g = 0; g < L; g += 2 * m) {
+#pragma unroll
+            for (int j = 0; j < m; ++j) {
+                const float2 b = a[g + j + m];
+                float2 t;
+                if (j == 0) {
+                    t = b;
+                } else if (2 * j == m) {                       // twiddle -i (forward) or +i (inverse)
+                    t = SIGN < 0 ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x);
+                } else {
+                    const float2 w = c_w32[j * (32 / (2 * m))];
+                    const float wy = SIGN < 0 ? w.y : -w.y;    // conj for the inverse
+                    t = make_float2(b.x * w.x - b.y * wy, b.x * wy + b.y * w.x);
+                }
+                const float2 u = a[g + j];
+                a[g + j] = make_float2(u.x + t.x, u.y + t.y);
+                a[g + j + m] = make_float2(u.x - t.x, u.y - t.y);
+            }
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1)
+fft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, int64_t n) {
+    constexpr int H = N / 2, M = N - 1, NV = N * N, LH = ilog2(H), LN = ilog2(N);
+    extern __shared__ __align__(16) float2 As[];        // [H][N][kPitch]
+    const int64_t tile = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // ---- stage 1: lane = column j2 of cells warp and warp + 16; real FFT over j1 ----
+    if (lane < N) {
+#pragma unroll 1
+        for (int c = warp; c < 32; c += 16) {
+            const int64_t g = tile * 32 + c;
+            const bool ok = g < n;
+            const float *fc = f + g * NV + lane;
+            float2 z[H];
+#pragma unroll
+            for (int p = 0; p < H; ++p) {
+                const float x0 = ok ? __ldg(fc + (2 * p) * N) : 0.f;
+                const float x1 = ok ? __ldg(fc + (2 * p + 1) * N) : 0.f;
+                z[bitrev(p, LH)] = make_float2(x0, x1);   // packed even / odd samples
+            }
+            fft_dit<H, -1>(z);
+            // untangle: X[k] = E[k] + omega^-k O[k], E = (Z_k + conj Z_-k)/2,
+            // O = (Z_k - conj Z_-k)/(2i); scale (-1)^k / N
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                const float2 zk = z[k], zc = z[(H - k) % H];
+                const float ex = 0.5f * (zk.x + zc.x), ey = 0.5f * (zk.y - zc.y);
+                const float ox = 0.5f * (zk.y + zc.y), oy = -0.5f * (zk.x - zc.x);
+                const float2 w = c_w32[k * (32 / N)];
+                const float xr = ex + (w.x * ox - w.y * oy);
+                const float xi = ey + (w.x * oy + w.y * ox);
+                const float sc = (k & 1) ? -1.f / N : 1.f / N;
+                As[(k * N + lane) * kPitch + c] = make_float2(xr * sc, xi * sc);
+            }
+        }
+    }
+    __syncthreads();
+    // ---- stage 2: lane = cell, warp = row k1; complex FFT over j2 ----
+    const int64_t gc = tile * 32 + lane;
+#pragma unroll 1
+    for (int k1 = warp; k1 < H; k1 += 16) {
+        float2 a[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) a[bitrev(j, LN)] = As[(k1 * N + j) * kPitch + lane];
+        fft_dit<N, -1>(a);
+        if (gc < n) {
+            float2 *out = fhat + tile * (int64_t)(H * M) * 32 + (int64_t)k1 * M * 32 + lane;
+#pragma unroll
+            for (int kk = 0; kk < M; ++kk) {
+                const int k2 = kk - (H - 1);
+                const float sc = (k2 & 1) ? -1.f / N : 1.f / N;
+                const float2 v = a[k2 & (N - 1)];
+                out[kk * 32] = make_float2(v.x * sc, v.y * sc);
+            }
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1)
+fft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, float scale, Cinv cinv, int conserve,
+                 const float *__restrict__ P, double L, double dv, int64_t n) {
+    constexpr int H = N / 2, M = N - 1, LH = ilog2(H), LN = ilog2(N);
+    extern __shared__ __align__(16) float2 Bs[];        // [H][N][kPitch]
+    const int64_t tile = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // ---- stage 1: lane = cell, warp = row k1; inverse complex FFT over k2 ----
+    const float2 *qt = Qhat + tile * (int64_t)(H * M) * 32 + lane;
+#pragma unroll 1
+    for (int k1 = warp; k1 < H; k1 += 16) {
+        float2 a[N];
+        a[bitrev(H, LN)] = make_float2(0.f, 0.f);       // Nyquist slot k2 = N/2
+#pragma unroll
+        for (int kk = 0; kk < M; ++kk) {
+            const int k2 = kk - (H - 1);
+            const float2 v = qt[(k1 * M + kk) * 32];
+            a[bitrev(k2 & (N - 1), LN)] = (k2 & 1) ? make_float2(-v.x, -v.y) : v;
+        }
+        fft_dit<N, +1>(a);
+        const float sc = (k1 & 1) ? -scale : scale;     // s^(d+gamma) (-1)^k1
+#pragma unroll
+        for (int j = 0; j < N; ++j) Bs[(k1 * N + j) * kPitch + lane] = make_float2(a[j].x * sc, a[j].y * sc);
+    }
+    __syncthreads();
+    // ---- stage 2: lane = column j2 of cells warp and warp + 16; Hermitian-to-real over k1 ----
+#pragma unroll 1
+    for (int c = warp; c < 32; c += 16) {
+        float q[N];
+        if (lane < N) {
+            float2 x[H + 1];
+#pragma unroll
+            for (int k = 0; k < H; ++k) x[k] = Bs[(k * N + lane) * kPitch + c];
+            x[0].y = 0.f;                                // real part of the k1 = 0 row
+            x[H] = make_float2(0.f, 0.f);
+            // Z[k] = E[k] + i O[k], E = X_k + conj X_{H-k}, O = (X_k - conj X_{H-k}) omega^k
+            float2 z[H];
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                const float2 xk = x[k], xc = make_float2(x[H - k].x, -x[H - k].y);
+                float ex, ey, ox, oy;
+                if (k == 0) {
+                    ex = xk.x; ey = xk.y; ox = xk.x; oy = xk.y;
+                } else {
+                    ex = xk.x + xc.x;
+                    ey = xk.y + xc.y;
+                    const float dx = xk.x - xc.x, dy = xk.y - xc.y;
+                    const float2 w = c_w32[k * (32 / N)];           // omega^k = conj(w)
+                    ox = dx * w.x + dy * w.y;
+                    oy = dy * w.x - dx * w.y;
+                }
+                z[bitrev(k, LH)] = make_float2(ex - oy, ey + ox);
+            }
+            fft_dit<H, +1>(z);
+#pragma unroll
+            for (int p = 0; p < H; ++p) {
+                q[2 * p] = z[p].x;
+                q[2 * p + 1] = z[p].y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) q[j] = 0.f;
+        }
+        inv32_epilogue<N>(q, tile * 32 + c, lane, cinv, conserve, P, Q, L, dv, n);
+    }
+}
+
+template <int N> size_t fft_smem() { return sizeof(float2) * (size_t)(N / 2) * N * kPitch; }
+
 template <int N> size_t fwd_smem() { return sizeof(float2) * ((N / 2) * N * kPitch + N * (N / 2) + N * 32); }
 template <int N> size_t inv_smem() { return sizeof(float2) * ((N / 2) * N * kPitch + (N - 1) * 32 + (N / 2) * N); }
 
@@ -332,6 +523,11 @@ int dft32_tables(const GridView &g, double scale, float2 **out_T1, float2 **out_
             double c = (k == 0 ? 1.0 : 2.0) * scale;
             T3[(size_t)k * N + j] = make_float2((float)(c * e.first), (float)(c * e.second));
         }
+    // twiddles of the FFT kernels, on the current device (constant memory is per device)
+    float2 w32[32];
+    for (int k = 0; k < 32; ++k) w32[k] = make_float2((float)cos(2.0 * M_PI * k / 32), (float)-sin(2.0 * M_PI * k / 32));
+    cudaError_t ew = cudaMemcpyToSymbol(c_w32, w32, sizeof w32);
+    if (ew != cudaSuccess) return cuda_fail(ew, "build_kernel_modes: FFT twiddles");
     float2 *d[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<float2> *src[4] = {&T1, &T2, &T2i, &T3};
     for (int i = 0; i < 4; ++i) {
@@ -363,18 +559,27 @@ cudaError_t launch_dft32_forward_tile(const GridView &g, const float2 *T1, const
         dft_fwd32_kernel<NN><<<ntile, kThreads, sm, st>>>(f, fhat, T1, T2, n);                           \
         break;                                                                                           \
     }
+#define BZ_FFT_FWD(NN)                                                                                   \
+    case NN: {                                                                                           \
+        size_t sm = fft_smem<NN>();                                                                      \
+        e = cudaFuncSetAttribute(fft_fwd32_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        if (e != cudaSuccess) return e;                                                                  \
+        fft_fwd32_kernel<NN><<<ntile, kThreads, sm, st>>>(f, fhat, n);                                   \
+        break;                                                                                           \
+    }
     switch (g.N) {
-        BZ_FWD(16)
+        BZ_FFT_FWD(16)
         BZ_FWD(24)
-        BZ_FWD(32)
+        BZ_FFT_FWD(32)
         default: return cudaErrorInvalidValue;
     }
 #undef BZ_FWD
+#undef BZ_FFT_FWD
     return cudaGetLastError();
 }
 
 cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *T2i, const float2 *T3, const float2 *Qhat,
-                                      float *Q, int64_t n, const double *cinv, const InvEpilogue &ep,
+                                      float *Q, int64_t n, double scale, const double *cinv, const InvEpilogue &ep,
                                       cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const unsigned ntile = (unsigned)((n + 31) / 32);
@@ -390,13 +595,23 @@ cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *T2i, cons
                                                           static_cast<const float *>(ep.P), g.L, g.dv, n); \
         break;                                                                                           \
     }
+#define BZ_FFT_INV(NN)                                                                                   \
+    case NN: {                                                                                           \
+        size_t sm = fft_smem<NN>();                                                                      \
+        e = cudaFuncSetAttribute(fft_inv32_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        if (e != cudaSuccess) return e;                                                                  \
+        fft_inv32_kernel<NN><<<ntile, kThreads, sm, st>>>(Qhat, Q, (float)scale, ci, ep.conserve,        \
+                                                          static_cast<const float *>(ep.P), g.L, g.dv, n); \
+        break;                                                                                           \
+    }
     switch (g.N) {
-        BZ_INV(16)
+        BZ_FFT_INV(16)
         BZ_INV(24)
-        BZ_INV(32)
+        BZ_FFT_INV(32)
         default: return cudaErrorInvalidValue;
     }
 #undef BZ_INV
+#undef BZ_FFT_INV
     return cudaGetLastError();
 }
 
