@@ -347,18 +347,23 @@ __device__ __forceinline__ void fft_dit(float2 (&a)[L]) {
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(kThreads, 1)
+// One CTA handles C cells (C = 32: a whole 32-cell tile of the Fourier layout,
+// or C = 16: half of one, so that two CTAs fit an SM and one's memory traffic
+// overlaps the other's arithmetic) with 16 C threads.
+template <int N, int C>
+__global__ void __launch_bounds__(C * 16)
 fft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, int64_t n) {
     constexpr int H = N / 2, M = N - 1, NV = N * N, LH = ilog2(H), LN = ilog2(N);
-    extern __shared__ __align__(16) float2 As[];        // [H][N][kPitch]
-    const int64_t tile = blockIdx.x;
+    constexpr int NW = C / 2, P = C + 1;                // warps; cell pitch of the shared rows
+    extern __shared__ __align__(16) float2 As[];        // [H][N][P]
+    const int64_t tile = blockIdx.x / (32 / C);
+    const int sub = (int)(blockIdx.x % (32 / C)) * C;   // first cell of this CTA within the tile
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // ---- stage 1: lane = column j2 of cells warp and warp + 16; real FFT over j1 ----
+    // ---- stage 1: lane = column j2 of cells warp, warp + NW, ...; real FFT over j1 ----
     if (lane < N) {
 #pragma unroll 1
-        for (int c = warp; c < 32; c += 16) {
-            const int64_t g = tile * 32 + c;
+        for (int c = warp; c < C; c += NW) {
+            const int64_t g = tile * 32 + sub + c;
             const bool ok = g < n;
             const float *fc = f + g * NV + lane;
             float2 z[H];
@@ -380,21 +385,22 @@ fft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, int64_t
                 const float xr = ex + (w.x * ox - w.y * oy);
                 const float xi = ey + (w.x * oy + w.y * ox);
                 const float sc = (k & 1) ? -1.f / N : 1.f / N;
-                As[(k * N + lane) * kPitch + c] = make_float2(xr * sc, xi * sc);
+                As[(k * N + lane) * P + c] = make_float2(xr * sc, xi * sc);
             }
         }
     }
     __syncthreads();
-    // ---- stage 2: lane = cell, warp = row k1; complex FFT over j2 ----
-    const int64_t gc = tile * 32 + lane;
+    // ---- stage 2: thread = (cell, row k1); complex FFT over j2 ----
+    const int cell = threadIdx.x % C;
+    const int64_t gc = tile * 32 + sub + cell;
 #pragma unroll 1
-    for (int k1 = warp; k1 < H; k1 += 16) {
+    for (int k1 = threadIdx.x / C; k1 < H; k1 += 16) {
         float2 a[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) a[bitrev(j, LN)] = As[(k1 * N + j) * kPitch + lane];
+        for (int j = 0; j < N; ++j) a[bitrev(j, LN)] = As[(k1 * N + j) * P + cell];
         fft_dit<N, -1>(a);
         if (gc < n) {
-            float2 *out = fhat + tile * (int64_t)(H * M) * 32 + (int64_t)k1 * M * 32 + lane;
+            float2 *out = fhat + tile * (int64_t)(H * M) * 32 + (int64_t)k1 * M * 32 + sub + cell;
 #pragma unroll
             for (int kk = 0; kk < M; ++kk) {
                 const int k2 = kk - (H - 1);
@@ -406,40 +412,45 @@ fft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, int64_t
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int N, int C>
+__global__ void __launch_bounds__(C * 16)
 fft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, float scale, Cinv cinv, int conserve,
-                 const float *__restrict__ P, double L, double dv, int64_t n) {
+                 const float *__restrict__ P_, double L, double dv, int64_t n) {
     constexpr int H = N / 2, M = N - 1, LH = ilog2(H), LN = ilog2(N);
-    extern __shared__ __align__(16) float2 Bs[];        // [H][N][kPitch]
-    const int64_t tile = blockIdx.x;
+    constexpr int NW = C / 2, P = C + 1;
+    extern __shared__ __align__(16) float2 Bs[];        // [H][N][P]
+    const int64_t tile = blockIdx.x / (32 / C);
+    const int sub = (int)(blockIdx.x % (32 / C)) * C;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // ---- stage 1: lane = cell, warp = row k1; inverse complex FFT over k2 ----
-    const float2 *qt = Qhat + tile * (int64_t)(H * M) * 32 + lane;
+    // ---- stage 1: thread = (cell, row k1); inverse complex FFT over k2 ----
+    {
+        const int cell = threadIdx.x % C;
+        const float2 *qt = Qhat + tile * (int64_t)(H * M) * 32 + sub + cell;
 #pragma unroll 1
-    for (int k1 = warp; k1 < H; k1 += 16) {
-        float2 a[N];
-        a[bitrev(H, LN)] = make_float2(0.f, 0.f);       // Nyquist slot k2 = N/2
+        for (int k1 = threadIdx.x / C; k1 < H; k1 += 16) {
+            float2 a[N];
+            a[bitrev(H, LN)] = make_float2(0.f, 0.f);   // Nyquist slot k2 = N/2
 #pragma unroll
-        for (int kk = 0; kk < M; ++kk) {
-            const int k2 = kk - (H - 1);
-            const float2 v = qt[(k1 * M + kk) * 32];
-            a[bitrev(k2 & (N - 1), LN)] = (k2 & 1) ? make_float2(-v.x, -v.y) : v;
+            for (int kk = 0; kk < M; ++kk) {
+                const int k2 = kk - (H - 1);
+                const float2 v = qt[(k1 * M + kk) * 32];
+                a[bitrev(k2 & (N - 1), LN)] = (k2 & 1) ? make_float2(-v.x, -v.y) : v;
+            }
+            fft_dit<N, +1>(a);
+            const float sc = (k1 & 1) ? -scale : scale; // s^(d+gamma) (-1)^k1
+#pragma unroll
+            for (int j = 0; j < N; ++j) Bs[(k1 * N + j) * P + cell] = make_float2(a[j].x * sc, a[j].y * sc);
         }
-        fft_dit<N, +1>(a);
-        const float sc = (k1 & 1) ? -scale : scale;     // s^(d+gamma) (-1)^k1
-#pragma unroll
-        for (int j = 0; j < N; ++j) Bs[(k1 * N + j) * kPitch + lane] = make_float2(a[j].x * sc, a[j].y * sc);
     }
     __syncthreads();
-    // ---- stage 2: lane = column j2 of cells warp and warp + 16; Hermitian-to-real over k1 ----
+    // ---- stage 2: lane = column j2 of cells warp, warp + NW, ...; Hermitian-to-real over k1 ----
 #pragma unroll 1
-    for (int c = warp; c < 32; c += 16) {
+    for (int c = warp; c < C; c += NW) {
         float q[N];
         if (lane < N) {
             float2 x[H + 1];
 #pragma unroll
-            for (int k = 0; k < H; ++k) x[k] = Bs[(k * N + lane) * kPitch + c];
+            for (int k = 0; k < H; ++k) x[k] = Bs[(k * N + lane) * P + c];
             x[0].y = 0.f;                                // real part of the k1 = 0 row
             x[H] = make_float2(0.f, 0.f);
             // Z[k] = E[k] + i O[k], E = X_k + conj X_{H-k}, O = (X_k - conj X_{H-k}) omega^k
@@ -470,11 +481,12 @@ fft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, float s
 #pragma unroll
             for (int j = 0; j < N; ++j) q[j] = 0.f;
         }
-        inv32_epilogue<N>(q, tile * 32 + c, lane, cinv, conserve, P, Q, L, dv, n);
+        inv32_epilogue<N>(q, tile * 32 + sub + c, lane, cinv, conserve, P_, Q, L, dv, n);
     }
 }
 
-template <int N> size_t fft_smem() { return sizeof(float2) * (size_t)(N / 2) * N * kPitch; }
+template <int N, int C> size_t fft_smem() { return sizeof(float2) * (size_t)(N / 2) * N * (C + 1); }
+constexpr int kFftCells = 16;   // cells per CTA of the FFT kernels
 
 template <int N> size_t fwd_smem() { return sizeof(float2) * ((N / 2) * N * kPitch + N * (N / 2) + N * 32); }
 template <int N> size_t inv_smem() { return sizeof(float2) * ((N / 2) * N * kPitch + (N - 1) * 32 + (N / 2) * N); }
@@ -561,10 +573,10 @@ cudaError_t launch_dft32_forward_tile(const GridView &g, const float2 *T1, const
     }
 #define BZ_FFT_FWD(NN)                                                                                   \
     case NN: {                                                                                           \
-        size_t sm = fft_smem<NN>();                                                                      \
-        e = cudaFuncSetAttribute(fft_fwd32_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        size_t sm = fft_smem<NN, kFftCells>();                                                           \
+        e = cudaFuncSetAttribute(fft_fwd32_kernel<NN, kFftCells>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
         if (e != cudaSuccess) return e;                                                                  \
-        fft_fwd32_kernel<NN><<<ntile, kThreads, sm, st>>>(f, fhat, n);                                   \
+        fft_fwd32_kernel<NN, kFftCells><<<ntile * (32 / kFftCells), kFftCells * 16, sm, st>>>(f, fhat, n); \
         break;                                                                                           \
     }
     switch (g.N) {
@@ -597,11 +609,11 @@ cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *T2i, cons
     }
 #define BZ_FFT_INV(NN)                                                                                   \
     case NN: {                                                                                           \
-        size_t sm = fft_smem<NN>();                                                                      \
-        e = cudaFuncSetAttribute(fft_inv32_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        size_t sm = fft_smem<NN, kFftCells>();                                                           \
+        e = cudaFuncSetAttribute(fft_inv32_kernel<NN, kFftCells>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
         if (e != cudaSuccess) return e;                                                                  \
-        fft_inv32_kernel<NN><<<ntile, kThreads, sm, st>>>(Qhat, Q, (float)scale, ci, ep.conserve,        \
-                                                          static_cast<const float *>(ep.P), g.L, g.dv, n); \
+        fft_inv32_kernel<NN, kFftCells><<<ntile * (32 / kFftCells), kFftCells * 16, sm, st>>>(           \
+            Qhat, Q, (float)scale, ci, ep.conserve, static_cast<const float *>(ep.P), g.L, g.dv, n);     \
         break;                                                                                           \
     }
     switch (g.N) {
