@@ -200,10 +200,9 @@ int phase_forward(const bz_modes *m, int precision, const void *f, void *fh, int
         BZ_LAUNCH("dft_forward_f64", st,
                   launch_dft_forward_f64(v, g->d_E64, static_cast<const double *>(f), static_cast<double2 *>(fh), n, st),
                   "collide: forward DFT");
-    } else if (m->d_T1) {
+    } else if (m->tile_dft) {
         BZ_LAUNCH("dft_forward_f32", st,
-                  launch_dft32_forward_tile(v, m->d_T1, m->d_T2, static_cast<const float *>(f),
-                                            static_cast<float2 *>(fh), n, st),
+                  launch_dft32_forward_tile(v, static_cast<const float *>(f), static_cast<float2 *>(fh), n, st),
                   "collide: forward DFT");
     } else {
         BZ_LAUNCH("dft_forward_f32_generic", st,
@@ -246,10 +245,10 @@ int phase_inverse(const bz_modes *m, int precision, int flags, const void *qh, v
                   launch_dft_inverse_f64(v, g->d_E64, static_cast<const double2 *>(qh), static_cast<double *>(Q), n,
                                          m->scale, g->cinv, ep, st),
                   "collide: inverse DFT");
-    } else if (m->d_T1) {
+    } else if (m->tile_dft) {
         BZ_LAUNCH("dft_inverse_f32", st,
-                  launch_dft32_inverse_tile(v, m->d_T2i, m->d_T3, static_cast<const float2 *>(qh),
-                                            static_cast<float *>(Q), n, m->scale, g->cinv, ep, st),
+                  launch_dft32_inverse_tile(v, static_cast<const float2 *>(qh), static_cast<float *>(Q), n, m->scale,
+                                            g->cinv, ep, st),
                   "collide: inverse DFT");
     } else {
         BZ_LAUNCH("dft_inverse_f32_generic", st,

@@ -63,8 +63,7 @@ struct bz_modes {
     int w32_rowmax;       // largest staged weight row (floats)
     int *d_task;
     int64_t pairs_sym;   // unordered pairs per cell (algorithmic unit)
-    // twiddle tables of the tile FP32 DFT kernels (k_dft32.cu), null if unused
-    float2 *d_T1, *d_T2, *d_T2i, *d_T3;
+    int tile_dft;        // 1: the tile FFT kernels of k_dft32.cu serve this grid
     double scale;        // s^(d + gamma)
 };
 
@@ -96,14 +95,12 @@ cudaError_t launch_dft_inverse_f32(const GridView &g, const float2 *E, const flo
                                    float *Q, int64_t n, double scale, const double *cinv,
                                    const InvEpilogue &ep, cudaStream_t st);
 
-// ---- tile FP32 DFT kernels (k_dft32.cu), 2-D, N in {16, 24, 32} -------------
+// ---- tile FP32 FFT kernels (k_dft32.cu), 2-D, N in {16, 24, 32, 48} ---------
 bool dft32_tile_supported(const GridView &g);
-int dft32_tables(const GridView &g, double scale, float2 **T1, float2 **T2, float2 **T2i, float2 **T3);
-cudaError_t launch_dft32_forward_tile(const GridView &g, const float2 *T1, const float2 *T2, const float *f,
-                                      float2 *fhat, int64_t n, cudaStream_t st);
-cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *T2i, const float2 *T3, const float2 *Qhat,
-                                      float *Q, int64_t n, double scale, const double *cinv,
-                                      const InvEpilogue &ep, cudaStream_t st);
+int dft32_setup();   // twiddles on the current device
+cudaError_t launch_dft32_forward_tile(const GridView &g, const float *f, float2 *fhat, int64_t n, cudaStream_t st);
+cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *Qhat, float *Q, int64_t n, double scale,
+                                      const double *cinv, const InvEpilogue &ep, cudaStream_t st);
 
 // ---- register-blocked FP32 2-D mode sum (k_modesum32.cu) --------------------
 constexpr int kMaxGroup = 16;      // instances per grouped launch

@@ -241,8 +241,10 @@ int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **o
     }
     m->pairs_sym = symmetric_pair_count(v);
     int rc = modes_build_fp32_tables(m);
-    if (rc == BZ_OK && dft32_tile_supported(v))
-        rc = dft32_tables(v, m->scale, &m->d_T1, &m->d_T2, &m->d_T2i, &m->d_T3);
+    if (rc == BZ_OK && dft32_tile_supported(v)) {
+        rc = dft32_setup();
+        m->tile_dft = rc == BZ_OK;
+    }
     if (rc != BZ_OK) {
         cudaFree(m->d_F64);
         cudaFree(m->d_F32);
@@ -262,10 +264,6 @@ void modes_destroy(bz_modes *m) {
         cudaFree(m->var_W[v]);
         cudaFree(m->var_task[v]);
     }
-    cudaFree(m->d_T1);
-    cudaFree(m->d_T2);
-    cudaFree(m->d_T2i);
-    cudaFree(m->d_T3);
     free(m->h_F);
     free(m);
 }

@@ -1,31 +1,17 @@
-// k_dft32.cu -- tile-based FP32 forward / inverse DFT for 2-D grids with
-// N in {16, 24, 32} (Sec. 3.3, eq. FC and eq. FU sampled on the grid).
+// k_dft32.cu -- tile-based FP32 forward / inverse DFT of the collision operator
+// (Sec. 3.3, eq. FC and eq. FU sampled on the grid) for 2-D grids with N in
+// {16, 24, 32, 48}, computed by FFTs held in registers.
 //
-// N = 16 and 32 use register-resident radix-2 FFTs (fft_fwd32_kernel,
-// fft_inv32_kernel, below); N = 24 uses the dense matrix form
-// (dft_fwd32_kernel, dft_inv32_kernel).  Both compute the same sums; the FFT
-// needs about a fifth of the instructions.
-//
-// One CTA handles one tile of 32 cells (the unit of the tiled Fourier layout
-// [tile][mode][cell]).  The 2-D transform is separable:
-//   forward  A[k1][j2]  = sum_j1 E1[j1][k1] f[j1][j2]           (k1 = 0..h)
-//            fhat[k1][k2] = sum_j2 A[k1][j2] E2[j2][k2]          (k2 = -h..h)
-//   inverse  B[k1][j2]  = sum_k2 Qhat[k1][k2] conj(E2[j2][k2])
-//            Q[j1][j2]  = sum_k1 c_k1 Re(B[k1][j2] conj(E1[j1][k1]))
-// with E(k, j) = (-1)^k exp(-2 pi i k j/N) / N (forward; the 1/N of each axis
-// folded in) and c_0 = s^(d+gamma), c_{k1>0} = 2 s^(d+gamma) for the inverse
-// (Hermitian half spectrum, physical scale folded in).
-//
-// Thread mapping: the grid-space stages use warp = cell pair, lane = j2 (rows
-// of f / Q are coalesced 128-byte lines); the spectral stages use lane = cell
-// (rows of the tiled layout are coalesced 256-byte lines) and warp = (pair of
-// k1 rows, block of 16 k2 or j2).  Twiddles are read as warp-uniform float4
-// (two complex values).  The intermediate A / B lives in shared memory as
-// [k1][j2][cell] with the cell stride padded to 33 to spread banks.
+// The 2-D transform is separable; each axis is an FFT of length N (or of
+// length N/2 for the real axis, by packing even and odd samples into one
+// complex sequence).  A CTA handles C cells of the tiled Fourier layout
+// [tile][mode][cell]; the intermediate A (forward) / B (inverse) lives in
+// shared memory as [k1][j2][cell] with the cell stride padded to C + 1.
+// Thread mapping: the grid-space stage (f or Q columns) uses one thread per
+// (cell, column j2), so rows of f / Q are coalesced across the columns; the
+// spectral stage uses one thread per (cell, row k1), so a mode's C cells are
+// one coalesced segment of the tiled layout.
 #include <math.h>
-
-#include <utility>
-#include <vector>
 
 #include "bz_device.cuh"
 #include "bz_internal.h"
@@ -33,118 +19,6 @@
 namespace bz {
 
 namespace {
-
-constexpr int kThreads = 512;
-constexpr int kPitch = 33;          // cells per (k1, j2) row of A / B in shared memory
-
-// Twiddle tables (built on the host per grid, in global memory):
-//   T1[j][k1]  : (-1)^k1 e^{-2 pi i k1 j/N}/N for k1 = 0..H-1       (forward stage 1)
-//   T2[j][kk]  : E(kk - h, j)/N for kk = 0..M-1, rows padded to 32   (forward stage 2 / inverse stage 1)
-//   T3[k1][j]  : c_k1 E(k1, j) (no 1/N), j = 0..N-1                   (inverse stage 2)
-
-template <int N>
-__global__ void __launch_bounds__(kThreads, 1)
-dft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, const float2 *__restrict__ T1,
-                 const float2 *__restrict__ T2, int64_t n) {
-    constexpr int H = N / 2, M = N - 1, NV = N * N;
-    extern __shared__ __align__(16) float2 As[];        // [H][N][kPitch], then T1s, T2s
-    float2 *T1s = As + H * N * kPitch;                  // [N][H]
-    float2 *T2s = T1s + N * H;                          // [N][32]
-    for (int i = threadIdx.x; i < N * H; i += blockDim.x) T1s[i] = T1[i];
-    for (int i = threadIdx.x; i < N * 32; i += blockDim.x) T2s[i] = T2[i];
-    const int64_t tile = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    // ---- stage 1: grid-space rows -> A ----
-    {
-        const int c0 = warp, c1 = warp + 16;
-        const int64_t g0 = tile * 32 + c0, g1 = tile * 32 + c1;
-        const bool ok0 = g0 < n && lane < N, ok1 = g1 < n && lane < N;
-        const float *f0 = f + g0 * NV + lane, *f1 = f + g1 * NV + lane;
-        float2 a0[H], a1[H];
-#pragma unroll
-        for (int k = 0; k < H; ++k) a0[k] = a1[k] = make_float2(0.f, 0.f);
-        constexpr int JB = 8;                           // rows of f in flight per thread and cell
-        for (int jb = 0; jb < N; jb += JB) {
-            float xs0[JB], xs1[JB];
-#pragma unroll
-            for (int q = 0; q < JB; ++q) {
-                xs0[q] = ok0 ? __ldg(f0 + (jb + q) * N) : 0.f;
-                xs1[q] = ok1 ? __ldg(f1 + (jb + q) * N) : 0.f;
-            }
-#pragma unroll
-            for (int q = 0; q < JB; ++q) {
-            const int j1 = jb + q;
-            const float x0 = xs0[q], x1 = xs1[q];
-            const float4 *t = reinterpret_cast<const float4 *>(T1s + j1 * H);
-#pragma unroll
-            for (int k = 0; k < H; k += 2) {
-                const float4 e = t[k / 2];
-                a0[k].x = fmaf(e.x, x0, a0[k].x);
-                a0[k].y = fmaf(e.y, x0, a0[k].y);
-                a0[k + 1].x = fmaf(e.z, x0, a0[k + 1].x);
-                a0[k + 1].y = fmaf(e.w, x0, a0[k + 1].y);
-                a1[k].x = fmaf(e.x, x1, a1[k].x);
-                a1[k].y = fmaf(e.y, x1, a1[k].y);
-                a1[k + 1].x = fmaf(e.z, x1, a1[k + 1].x);
-                a1[k + 1].y = fmaf(e.w, x1, a1[k + 1].y);
-            }
-            }
-        }
-        if (lane < N) {
-#pragma unroll
-            for (int k = 0; k < H; ++k) {
-                As[(k * N + lane) * kPitch + c0] = a0[k];
-                As[(k * N + lane) * kPitch + c1] = a1[k];
-            }
-        }
-    }
-    __syncthreads();
-    // ---- stage 2: lane = cell, tasks = (k1 pair, block of 16 k2) ----
-    constexpr int NP = (H + 1) / 2, NB = (M + 15) / 16;
-    const int64_t gc = tile * 32 + lane;
-    for (int task = warp; task < NP * NB; task += 16) {
-        const int p = task % NP, blk = task / NP;
-        const int k1a = 2 * p, k1b = 2 * p + 1;
-        const bool hasb = k1b < H;
-        float2 q0[16], q1[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) q0[i] = q1[i] = make_float2(0.f, 0.f);
-#pragma unroll 2
-        for (int j2 = 0; j2 < N; ++j2) {
-            const float2 a = As[(k1a * N + j2) * kPitch + lane];
-            const float2 b = hasb ? As[(k1b * N + j2) * kPitch + lane] : make_float2(0.f, 0.f);
-            const float4 *t = reinterpret_cast<const float4 *>(T2s + j2 * 32 + blk * 16);
-#pragma unroll
-            for (int i = 0; i < 16; i += 2) {
-                const float4 e = t[i / 2];
-                cmac(q0[i], a, make_float2(e.x, e.y));
-                cmac(q0[i + 1], a, make_float2(e.z, e.w));
-                cmac(q1[i], b, make_float2(e.x, e.y));
-                cmac(q1[i + 1], b, make_float2(e.z, e.w));
-            }
-        }
-        if (gc < n) {
-            float2 *out = fhat + tile * (int64_t)(H * M) * 32 + lane;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int kk = blk * 16 + i;
-                if (kk < M) {
-                    out[(k1a * M + kk) * 32] = q0[i];
-                    if (hasb) out[(k1b * M + kk) * 32] = q1[i];
-                }
-            }
-        }
-    }
-}
-
-// acc += q * conj(e)
-__device__ __forceinline__ void cmac_conj32(float2 &acc, float2 q, float ex, float ey) {
-    acc.x = fmaf(q.x, ex, acc.x);
-    acc.x = fmaf(q.y, ey, acc.x);
-    acc.y = fmaf(q.y, ex, acc.y);
-    acc.y = fmaf(-q.x, ey, acc.y);
-}
 
 // Inverse-DFT epilogue of one cell held as one column j2 = lane per thread:
 // optional conservation projection, optional G = Q - P, coalesced store.
@@ -205,91 +79,6 @@ __device__ __forceinline__ void inv32_epilogue(float (&q)[N], int64_t cell, int 
         for (int j = 0; j < N; ++j) out[j * N] = pc ? q[j] - pc[j * N] : q[j];
     }
 }
-
-template <int N>
-__global__ void __launch_bounds__(kThreads, 1)
-dft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, const float2 *__restrict__ T2i,
-                 const float2 *__restrict__ T3, Cinv cinv, int conserve, const float *__restrict__ P,
-                 double L, double dv, int64_t n) {
-    constexpr int H = N / 2, M = N - 1;
-    extern __shared__ __align__(16) float2 Bs[];        // [H][N][kPitch], then T2s, T3s
-    float2 *T2s = Bs + H * N * kPitch;                  // [M][32]
-    float2 *T3s = T2s + M * 32;                         // [H][N]
-    for (int i = threadIdx.x; i < M * 32; i += blockDim.x) T2s[i] = T2i[i];
-    for (int i = threadIdx.x; i < H * N; i += blockDim.x) T3s[i] = T3[i];
-    __syncthreads();
-    const int64_t tile = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // ---- stage 1: lane = cell, tasks = (k1 pair, block of 16 j2) ----
-    constexpr int NP = (H + 1) / 2, NB = (N + 15) / 16;
-    const float2 *qt = Qhat + tile * (int64_t)(H * M) * 32 + lane;
-    for (int task = warp; task < NP * NB; task += 16) {
-        const int p = task % NP, blk = task / NP;
-        const int k1a = 2 * p, k1b = 2 * p + 1;
-        const bool hasb = k1b < H;
-        float2 b0[16], b1[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) b0[i] = b1[i] = make_float2(0.f, 0.f);
-        constexpr int KB = 8;                           // spectral rows in flight per thread
-        for (int kb = 0; kb < M; kb += KB) {
-            float2 qas[KB], qbs[KB];
-#pragma unroll
-            for (int q = 0; q < KB; ++q) {
-                const bool in = kb + q < M;
-                qas[q] = in ? qt[(k1a * M + kb + q) * 32] : make_float2(0.f, 0.f);
-                qbs[q] = (in && hasb) ? qt[(k1b * M + kb + q) * 32] : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int q = 0; q < KB; ++q) {
-            const int kk = kb + q;
-            if (kk >= M) break;
-            const float2 qa = qas[q], qb = qbs[q];
-            const float4 *t = reinterpret_cast<const float4 *>(T2s + kk * 32 + blk * 16);
-#pragma unroll
-            for (int i = 0; i < 16; i += 2) {
-                const float4 e = t[i / 2];
-                cmac_conj32(b0[i], qa, e.x, e.y);
-                cmac_conj32(b0[i + 1], qa, e.z, e.w);
-                cmac_conj32(b1[i], qb, e.x, e.y);
-                cmac_conj32(b1[i + 1], qb, e.z, e.w);
-            }
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int j2 = blk * 16 + i;
-            if (j2 < N) {
-                Bs[(k1a * N + j2) * kPitch + lane] = b0[i];
-                if (hasb) Bs[(k1b * N + j2) * kPitch + lane] = b1[i];
-            }
-        }
-    }
-    __syncthreads();
-    // ---- stage 2: warp = cell pair, lane = j2 ----
-    const int c0 = warp, c1 = warp + 16;
-    float q0[N], q1[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) q0[j] = q1[j] = 0.f;
-    if (lane < N) {
-#pragma unroll 2
-        for (int k1 = 0; k1 < H; ++k1) {
-            const float2 ba = Bs[(k1 * N + lane) * kPitch + c0];
-            const float2 bb = Bs[(k1 * N + lane) * kPitch + c1];
-            const float4 *t = reinterpret_cast<const float4 *>(T3s + k1 * N);
-#pragma unroll
-            for (int j = 0; j < N; j += 2) {
-                const float4 e = t[j / 2];             // Re(b conj(e)) = b.x e.x + b.y e.y
-                q0[j] = fmaf(ba.x, e.x, fmaf(ba.y, e.y, q0[j]));
-                q0[j + 1] = fmaf(ba.x, e.z, fmaf(ba.y, e.w, q0[j + 1]));
-                q1[j] = fmaf(bb.x, e.x, fmaf(bb.y, e.y, q1[j]));
-                q1[j + 1] = fmaf(bb.x, e.z, fmaf(bb.y, e.w, q1[j + 1]));
-            }
-        }
-    }
-    inv32_epilogue<N>(q0, tile * 32 + c0, lane, cinv, conserve, P, Q, L, dv, n);
-    inv32_epilogue<N>(q1, tile * 32 + c1, lane, cinv, conserve, P, Q, L, dv, n);
-}
-
 
 // ---------------------------------------------------------------------------
 // Radix-2 FFT form (N = 16, 32).
@@ -485,92 +274,299 @@ fft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, float s
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Mixed-radix form for N = 24 and 48 (N/2 and N are 3 * 2^p).  Same sums as
+// above; a length-3Q transform is split by Cooley-Tukey into Q-point
+// transforms of the three residue classes n = Q n1 + n2 (3-point DFTs over
+// n1, twiddles omega_L^(n2 k1), then Q-point FFTs over n2; output index
+// k1 + 3 k2).  A 48-column cell does not fit one warp, so the column stages
+// use TPC = 32 or 64 threads per cell (one or two whole warps).
+
+__constant__ float2 c_w48[48];          // e^{-2 pi i k / 48}, k = 0..47
+
+// Transform of length L (2^p <= 32, or 3 * 2^p <= 48) from natural to
+// natural order; SIGN as in fft_dit.
+template <int L, int SIGN>
+__device__ __forceinline__ void fft_nat(float2 (&a)[L]) {
+    if constexpr ((L & (L - 1)) == 0) {
+        float2 b[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) b[bitrev(i, ilog2(L))] = a[i];
+        fft_dit<L, SIGN>(b);
+#pragma unroll
+        for (int i = 0; i < L; ++i) a[i] = b[i];
+    } else {
+        static_assert(L % 3 == 0 && L <= 48, "length 3 * 2^p <= 48");
+        constexpr int Q = L / 3;
+        constexpr float kS3 = 0.866025403784438647f;    // sqrt(3) / 2
+        float2 y0[Q], y1[Q], y2[Q];
+#pragma unroll
+        for (int n2 = 0; n2 < Q; ++n2) {
+            const float2 p = a[n2], q = a[Q + n2], r = a[2 * Q + n2];
+            const float sx = q.x + r.x, sy = q.y + r.y, dx = q.x - r.x, dy = q.y - r.y;
+            y0[n2] = make_float2(p.x + sx, p.y + sy);
+            const float mx = p.x - 0.5f * sx, my = p.y - 0.5f * sy;
+            // -i (sqrt3/2) d for the forward transform, +i (sqrt3/2) d for the inverse
+            const float ix = SIGN < 0 ? kS3 * dy : -kS3 * dy, iy = SIGN < 0 ? -kS3 * dx : kS3 * dx;
+            float2 u1 = make_float2(mx + ix, my + iy), u2 = make_float2(mx - ix, my - iy);
+            if (n2 > 0) {
+                const float2 w1 = c_w48[n2 * (48 / L)], w2 = c_w48[2 * n2 * (48 / L)];
+                const float w1y = SIGN < 0 ? w1.y : -w1.y, w2y = SIGN < 0 ? w2.y : -w2.y;
+                u1 = make_float2(u1.x * w1.x - u1.y * w1y, u1.x * w1y + u1.y * w1.x);
+                u2 = make_float2(u2.x * w2.x - u2.y * w2y, u2.x * w2y + u2.y * w2.x);
+            }
+            y1[n2] = u1;
+            y2[n2] = u2;
+        }
+        fft_nat<Q, SIGN>(y0);
+        fft_nat<Q, SIGN>(y1);
+        fft_nat<Q, SIGN>(y2);
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) {
+            a[3 * k2] = y0[k2];
+            a[3 * k2 + 1] = y1[k2];
+            a[3 * k2 + 2] = y2[k2];
+        }
+    }
+}
+
+// e^{-2 pi i k / N} for N in {16, 24, 32, 48}
+template <int N> __device__ __forceinline__ float2 tw(int k) {
+    if constexpr (N == 16 || N == 32) return c_w32[k * (32 / N)];
+    else return c_w48[k * (48 / N)];
+}
+
+template <int N> constexpr int threads_per_cell() { return N <= 32 ? 32 : 64; }
+
+template <int N, int C>
+__global__ void __launch_bounds__(C * threads_per_cell<N>())
+fftg_fwd_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, int64_t n) {
+    constexpr int H = N / 2, M = N - 1, NV = N * N, P = C + 1, T = C * threads_per_cell<N>();
+    extern __shared__ __align__(16) float2 As[];        // [H][N][P]
+    const int64_t tile = blockIdx.x / (32 / C);
+    const int sub = (int)(blockIdx.x % (32 / C)) * C;
+    // ---- stage 1: thread = (cell, column j2); real transform over j1 ----
+#pragma unroll 1
+    for (int t = threadIdx.x; t < C * N; t += T) {
+        const int c = t / N, j2 = t % N;
+        const int64_t g = tile * 32 + sub + c;
+        const bool ok = g < n;
+        const float *fc = f + g * NV + j2;
+        float2 z[H];
+#pragma unroll
+        for (int p = 0; p < H; ++p)
+            z[p] = make_float2(ok ? __ldg(fc + (2 * p) * N) : 0.f, ok ? __ldg(fc + (2 * p + 1) * N) : 0.f);
+        fft_nat<H, -1>(z);
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const float2 zk = z[k], zc = z[(H - k) % H];
+            const float ex = 0.5f * (zk.x + zc.x), ey = 0.5f * (zk.y - zc.y);
+            const float ox = 0.5f * (zk.y + zc.y), oy = -0.5f * (zk.x - zc.x);
+            const float2 w = tw<N>(k);
+            const float xr = ex + (w.x * ox - w.y * oy);
+            const float xi = ey + (w.x * oy + w.y * ox);
+            const float sc = (k & 1) ? -1.f / N : 1.f / N;
+            As[(k * N + j2) * P + c] = make_float2(xr * sc, xi * sc);
+        }
+    }
+    __syncthreads();
+    // ---- stage 2: thread = (cell, row k1); complex transform over j2 ----
+#pragma unroll 1
+    for (int t = threadIdx.x; t < C * H; t += T) {
+        const int c = t % C, k1 = t / C;
+        const int64_t g = tile * 32 + sub + c;
+        float2 a[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) a[j] = As[(k1 * N + j) * P + c];
+        fft_nat<N, -1>(a);
+        if (g < n) {
+            float2 *out = fhat + tile * (int64_t)(H * M) * 32 + (int64_t)k1 * M * 32 + sub + c;
+#pragma unroll
+            for (int kk = 0; kk < M; ++kk) {
+                const int k2 = kk - (H - 1);
+                const float sc = (k2 & 1) ? -1.f / N : 1.f / N;
+                const float2 v = a[(k2 + N) % N];
+                out[kk * 32] = make_float2(v.x * sc, v.y * sc);
+            }
+        }
+    }
+}
+
+// Epilogue for one column j2 of one cell, TPC threads per cell (whole warps):
+// conservation projection (moments reduced over the cell's warps in a fixed
+// order), G = Q - P, store.  red: shared scratch of (T/32) * 4 doubles.
+template <int N, int TPC>
+__device__ __forceinline__ void invg_epilogue(float (&q)[N], int64_t cell, int j2, const Cinv &cinv,
+                                              int conserve, const float *__restrict__ P,
+                                              float *__restrict__ Q, double L, double dv, int64_t n,
+                                              double *red) {
+    constexpr int NV = N * N;
+    const bool col = j2 < N;
+    const float v2 = (float)(-L + j2 * dv);
+    if (conserve) {
+        double mom[4];
+        {
+            float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f, s3 = 0.f, e3 = 0.f;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const float v1 = (float)(-L + j * dv);
+                const float t0 = col ? q[j] : 0.f;
+                float s, bb;
+                s = s0 + t0; bb = s - s0; e0 += (s0 - (s - bb)) + (t0 - bb); s0 = s;
+                const float t1 = v1 * t0;
+                s = s1 + t1; bb = s - s1; e1 += (s1 - (s - bb)) + (t1 - bb); s1 = s;
+                const float t3 = v1 * v1 * t0;
+                s = s3 + t3; bb = s - s3; e3 += (s3 - (s - bb)) + (t3 - bb); s3 = s;
+            }
+            const double S0 = (double)s0 + e0, S1 = (double)s1 + e1, S3 = (double)s3 + e3;
+            const double vv = col ? (double)(-L + j2 * dv) : 0.0;
+            mom[0] = S0;
+            mom[1] = S1;
+            mom[2] = vv * S0;
+            mom[3] = S3 + vv * vv * S0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mom[k] += __shfl_xor_sync(0xffffffffu, mom[k], o);
+        if constexpr (TPC > 32) {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) red[warp * 4 + k] = mom[k];
+            __syncthreads();
+            const int w0 = warp - warp % (TPC / 32);   // first warp of this cell
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                double s = 0.0;
+#pragma unroll
+                for (int w = 0; w < TPC / 32; ++w) s += red[(w0 + w) * 4 + k];
+                mom[k] = s;
+            }
+            __syncthreads();
+        }
+        double x[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) s += cinv.v[a * 4 + c] * mom[c];
+            x[a] = s;
+        }
+        const float x0 = (float)x[0], x1 = (float)x[1], x2 = (float)x[2], x3 = (float)x[3];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const float v1 = (float)(-L + j * dv);
+            q[j] -= x0 + x1 * v1 + x2 * v2 + x3 * (v1 * v1 + v2 * v2);
+        }
+    }
+    if (cell < n && col) {
+        float *out = Q + cell * NV + j2;
+        const float *pc = P ? P + cell * NV + j2 : nullptr;
+#pragma unroll
+        for (int j = 0; j < N; ++j) out[j * N] = pc ? q[j] - pc[j * N] : q[j];
+    }
+}
+
+template <int N, int C>
+__global__ void __launch_bounds__(C * threads_per_cell<N>())
+fftg_inv_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, float scale, Cinv cinv, int conserve,
+                const float *__restrict__ P_, double L, double dv, int64_t n) {
+    constexpr int H = N / 2, M = N - 1, P = C + 1, TPC = threads_per_cell<N>(), T = C * TPC;
+    extern __shared__ __align__(16) float2 Bs[];        // [H][N][P], then T/32 * 4 doubles
+    double *red = reinterpret_cast<double *>(Bs + (size_t)H * N * P);
+    const int64_t tile = blockIdx.x / (32 / C);
+    const int sub = (int)(blockIdx.x % (32 / C)) * C;
+    // ---- stage 1: thread = (cell, row k1); inverse complex transform over k2 ----
+#pragma unroll 1
+    for (int t = threadIdx.x; t < C * H; t += T) {
+        const int c = t % C, k1 = t / C;
+        const float2 *qt = Qhat + tile * (int64_t)(H * M) * 32 + sub + c;
+        float2 a[N];
+        a[H] = make_float2(0.f, 0.f);                   // Nyquist slot k2 = N/2
+#pragma unroll
+        for (int kk = 0; kk < M; ++kk) {
+            const int k2 = kk - (H - 1);
+            const float2 v = qt[(k1 * M + kk) * 32];
+            a[(k2 + N) % N] = (k2 & 1) ? make_float2(-v.x, -v.y) : v;
+        }
+        fft_nat<N, +1>(a);
+        const float sc = (k1 & 1) ? -scale : scale;     // s^(d+gamma) (-1)^k1
+#pragma unroll
+        for (int j = 0; j < N; ++j) Bs[(k1 * N + j) * P + c] = make_float2(a[j].x * sc, a[j].y * sc);
+    }
+    __syncthreads();
+    // ---- stage 2: thread = (cell, column j2), TPC threads per cell ----
+    const int c = threadIdx.x / TPC, j2 = threadIdx.x % TPC;
+    float q[N];
+    if (j2 < N) {
+        float2 x[H + 1];
+#pragma unroll
+        for (int k = 0; k < H; ++k) x[k] = Bs[(k * N + j2) * P + c];
+        x[0].y = 0.f;                                    // real part of the k1 = 0 row
+        x[H] = make_float2(0.f, 0.f);
+        float2 z[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const float2 xk = x[k], xc = make_float2(x[H - k].x, -x[H - k].y);
+            float ex, ey, ox, oy;
+            if (k == 0) {
+                ex = xk.x; ey = xk.y; ox = xk.x; oy = xk.y;
+            } else {
+                ex = xk.x + xc.x;
+                ey = xk.y + xc.y;
+                const float dx = xk.x - xc.x, dy = xk.y - xc.y;
+                const float2 w = tw<N>(k);                   // omega^k = conj(w)
+                ox = dx * w.x + dy * w.y;
+                oy = dy * w.x - dx * w.y;
+            }
+            z[k] = make_float2(ex - oy, ey + ox);
+        }
+        fft_nat<H, +1>(z);
+#pragma unroll
+        for (int p = 0; p < H; ++p) {
+            q[2 * p] = z[p].x;
+            q[2 * p + 1] = z[p].y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) q[j] = 0.f;
+    }
+    invg_epilogue<N, TPC>(q, tile * 32 + sub + c, j2, cinv, conserve, P_, Q, L, dv, n, red);
+}
+
+template <int N, int C> size_t fftg_smem() {
+    return sizeof(float2) * (size_t)(N / 2) * N * (C + 1) + sizeof(double) * 4 * (C * threads_per_cell<N>() / 32);
+}
+template <int N> constexpr int fftg_cells() { return N <= 32 ? 16 : 8; }
+
 template <int N, int C> size_t fft_smem() { return sizeof(float2) * (size_t)(N / 2) * N * (C + 1); }
 constexpr int kFftCells = 16;   // cells per CTA of the FFT kernels
 
-template <int N> size_t fwd_smem() { return sizeof(float2) * ((N / 2) * N * kPitch + N * (N / 2) + N * 32); }
-template <int N> size_t inv_smem() { return sizeof(float2) * ((N / 2) * N * kPitch + (N - 1) * 32 + (N / 2) * N); }
 
 }  // namespace
 
-bool dft32_tile_supported(const GridView &g) { return g.dim == 2 && (g.N == 16 || g.N == 24 || g.N == 32); }
+bool dft32_tile_supported(const GridView &g) {
+    return g.dim == 2 && (g.N == 16 || g.N == 24 || g.N == 32 || g.N == 48);
+}
 
-// Host-built twiddle tables for the tile kernels (see the table comments above).
-int dft32_tables(const GridView &g, double scale, float2 **out_T1, float2 **out_T2, float2 **out_T2i,
-                 float2 **out_T3) {
-    const int N = g.N, H = g.h + 1, h = g.h, M = g.M;
-    std::vector<float2> T1((size_t)N * H), T2((size_t)N * 32), T2i((size_t)M * 32), T3((size_t)H * N);
-    auto E = [&](int k, int j) {              // (-1)^k exp(-2 pi i (k j mod N)/N)
-        long r = ((long)k * j) % N;
-        if (r < 0) r += N;
-        double ang = 2.0 * M_PI * (double)r / N, sg = (k & 1) ? -1.0 : 1.0;
-        return std::make_pair(sg * cos(ang), -sg * sin(ang));
-    };
-    for (int j = 0; j < N; ++j)
-        for (int k = 0; k < H; ++k) {
-            auto e = E(k, j);
-            T1[(size_t)j * H + k] = make_float2((float)(e.first / N), (float)(e.second / N));
-        }
-    for (int j = 0; j < N; ++j)
-        for (int kk = 0; kk < 32; ++kk) {
-            float2 v = make_float2(0.f, 0.f);
-            if (kk < M) {
-                auto e = E(kk - h, j);
-                v = make_float2((float)(e.first / N), (float)(e.second / N));
-            }
-            T2[(size_t)j * 32 + kk] = v;
-        }
-    for (int kk = 0; kk < M; ++kk)
-        for (int j = 0; j < 32; ++j) {
-            float2 v = make_float2(0.f, 0.f);
-            if (j < N) {
-                auto e = E(kk - h, j);
-                v = make_float2((float)e.first, (float)e.second);
-            }
-            T2i[(size_t)kk * 32 + j] = v;
-        }
-    for (int k = 0; k < H; ++k)
-        for (int j = 0; j < N; ++j) {
-            auto e = E(k, j);
-            double c = (k == 0 ? 1.0 : 2.0) * scale;
-            T3[(size_t)k * N + j] = make_float2((float)(c * e.first), (float)(c * e.second));
-        }
-    // twiddles of the FFT kernels, on the current device (constant memory is per device)
-    float2 w32[32];
+// Twiddles of the FFT kernels on the current device (constant memory is per
+// device, so this runs for every modes handle, on its device).
+int dft32_setup() {
+    float2 w32[32], w48[48];
     for (int k = 0; k < 32; ++k) w32[k] = make_float2((float)cos(2.0 * M_PI * k / 32), (float)-sin(2.0 * M_PI * k / 32));
-    cudaError_t ew = cudaMemcpyToSymbol(c_w32, w32, sizeof w32);
-    if (ew != cudaSuccess) return cuda_fail(ew, "build_kernel_modes: FFT twiddles");
-    float2 *d[4] = {nullptr, nullptr, nullptr, nullptr};
-    std::vector<float2> *src[4] = {&T1, &T2, &T2i, &T3};
-    for (int i = 0; i < 4; ++i) {
-        cudaError_t e = cudaMalloc(&d[i], sizeof(float2) * src[i]->size());
-        if (e == cudaSuccess)
-            e = cudaMemcpy(d[i], src[i]->data(), sizeof(float2) * src[i]->size(), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            for (int q = 0; q <= i; ++q) cudaFree(d[q]);
-            return cuda_fail(e, "build_kernel_modes: DFT tables");
-        }
-    }
-    *out_T1 = d[0];
-    *out_T2 = d[1];
-    *out_T2i = d[2];
-    *out_T3 = d[3];
+    for (int k = 0; k < 48; ++k) w48[k] = make_float2((float)cos(2.0 * M_PI * k / 48), (float)-sin(2.0 * M_PI * k / 48));
+    cudaError_t e = cudaMemcpyToSymbol(c_w32, w32, sizeof w32);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w48, w48, sizeof w48);
+    if (e != cudaSuccess) return cuda_fail(e, "build_kernel_modes: FFT twiddles");
     return BZ_OK;
 }
 
-cudaError_t launch_dft32_forward_tile(const GridView &g, const float2 *T1, const float2 *T2, const float *f,
-                                      float2 *fhat, int64_t n, cudaStream_t st) {
+cudaError_t launch_dft32_forward_tile(const GridView &g, const float *f, float2 *fhat, int64_t n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const unsigned ntile = (unsigned)((n + 31) / 32);
     cudaError_t e = cudaSuccess;
-#define BZ_FWD(NN)                                                                                       \
-    case NN: {                                                                                           \
-        size_t sm = fwd_smem<NN>();                                                                      \
-        e = cudaFuncSetAttribute(dft_fwd32_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        if (e != cudaSuccess) return e;                                                                  \
-        dft_fwd32_kernel<NN><<<ntile, kThreads, sm, st>>>(f, fhat, T1, T2, n);                           \
-        break;                                                                                           \
-    }
 #define BZ_FFT_FWD(NN)                                                                                   \
     case NN: {                                                                                           \
         size_t sm = fft_smem<NN, kFftCells>();                                                           \
@@ -579,34 +575,34 @@ cudaError_t launch_dft32_forward_tile(const GridView &g, const float2 *T1, const
         fft_fwd32_kernel<NN, kFftCells><<<ntile * (32 / kFftCells), kFftCells * 16, sm, st>>>(f, fhat, n); \
         break;                                                                                           \
     }
+#define BZ_FFTG_FWD(NN)                                                                                  \
+    case NN: {                                                                                           \
+        constexpr int C = fftg_cells<NN>();                                                              \
+        size_t sm = fftg_smem<NN, C>();                                                                  \
+        e = cudaFuncSetAttribute(fftg_fwd_kernel<NN, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        if (e != cudaSuccess) return e;                                                                  \
+        fftg_fwd_kernel<NN, C><<<ntile * (32 / C), C * threads_per_cell<NN>(), sm, st>>>(f, fhat, n);    \
+        break;                                                                                           \
+    }
     switch (g.N) {
         BZ_FFT_FWD(16)
-        BZ_FWD(24)
+        BZ_FFTG_FWD(24)
         BZ_FFT_FWD(32)
+        BZ_FFTG_FWD(48)
         default: return cudaErrorInvalidValue;
     }
-#undef BZ_FWD
+#undef BZ_FFTG_FWD
 #undef BZ_FFT_FWD
     return cudaGetLastError();
 }
 
-cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *T2i, const float2 *T3, const float2 *Qhat,
-                                      float *Q, int64_t n, double scale, const double *cinv, const InvEpilogue &ep,
-                                      cudaStream_t st) {
+cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *Qhat, float *Q, int64_t n, double scale,
+                                      const double *cinv, const InvEpilogue &ep, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const unsigned ntile = (unsigned)((n + 31) / 32);
     Cinv ci;
     for (int i = 0; i < 25; ++i) ci.v[i] = cinv[i];
     cudaError_t e = cudaSuccess;
-#define BZ_INV(NN)                                                                                       \
-    case NN: {                                                                                           \
-        size_t sm = inv_smem<NN>();                                                                      \
-        e = cudaFuncSetAttribute(dft_inv32_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        if (e != cudaSuccess) return e;                                                                  \
-        dft_inv32_kernel<NN><<<ntile, kThreads, sm, st>>>(Qhat, Q, T2i, T3, ci, ep.conserve,             \
-                                                          static_cast<const float *>(ep.P), g.L, g.dv, n); \
-        break;                                                                                           \
-    }
 #define BZ_FFT_INV(NN)                                                                                   \
     case NN: {                                                                                           \
         size_t sm = fft_smem<NN, kFftCells>();                                                           \
@@ -616,13 +612,24 @@ cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *T2i, cons
             Qhat, Q, (float)scale, ci, ep.conserve, static_cast<const float *>(ep.P), g.L, g.dv, n);     \
         break;                                                                                           \
     }
+#define BZ_FFTG_INV(NN)                                                                                  \
+    case NN: {                                                                                           \
+        constexpr int C = fftg_cells<NN>();                                                              \
+        size_t sm = fftg_smem<NN, C>();                                                                  \
+        e = cudaFuncSetAttribute(fftg_inv_kernel<NN, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        if (e != cudaSuccess) return e;                                                                  \
+        fftg_inv_kernel<NN, C><<<ntile * (32 / C), C * threads_per_cell<NN>(), sm, st>>>(                \
+            Qhat, Q, (float)scale, ci, ep.conserve, static_cast<const float *>(ep.P), g.L, g.dv, n);     \
+        break;                                                                                           \
+    }
     switch (g.N) {
         BZ_FFT_INV(16)
-        BZ_INV(24)
+        BZ_FFTG_INV(24)
         BZ_FFT_INV(32)
+        BZ_FFTG_INV(48)
         default: return cudaErrorInvalidValue;
     }
-#undef BZ_INV
+#undef BZ_FFTG_INV
 #undef BZ_FFT_INV
     return cudaGetLastError();
 }

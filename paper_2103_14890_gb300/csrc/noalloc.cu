@@ -78,13 +78,13 @@ int run_with_scratch(const bz_modes *m, int precision, int flags, const void *f,
         float2 *fh = static_cast<float2 *>(scratch), *qh = fh + celem;
         const float *fin = static_cast<const float *>(f);
         float *qout = static_cast<float *>(Q);
-        e = m->d_T1 ? launch_dft32_forward_tile(v, m->d_T1, m->d_T2, fin, fh, n, st)
+        e = m->tile_dft ? launch_dft32_forward_tile(v, fin, fh, n, st)
                     : launch_dft_forward_f32(v, g->d_E32, fin, fh, n, st);
         if (e == cudaSuccess)
             e = modesum32_2d_available(m) ? launch_modesum32_2d(m, fh, qh, n, st)
                                           : launch_modesum_generic_f32(v, m->d_F32, m->bcols, fh, qh, n, st);
         if (e == cudaSuccess)
-            e = m->d_T1 ? launch_dft32_inverse_tile(v, m->d_T2i, m->d_T3, qh, qout, n, m->scale, g->cinv, ep, st)
+            e = m->tile_dft ? launch_dft32_inverse_tile(v, qh, qout, n, m->scale, g->cinv, ep, st)
                         : launch_dft_inverse_f32(v, g->d_E32, qh, qout, n, m->scale, g->cinv, ep, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "collide_batch_noalloc: kernel launch");

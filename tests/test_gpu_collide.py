@@ -127,6 +127,23 @@ def test_fp64_conservation_fix(bz, oracle_k):
         assert np.abs(mom).max() < 1e-12 * np.abs(Q).sum(axis=1).max() * np.abs(p).max()
 
 
+@pytest.mark.parametrize("N,n", [(16, 33), (24, 40), (32, 37), (48, 21)])
+def test_fp32_conservation_fix_every_tile_fft(bz, oracle_k, N, n):
+    """FP32 form with BZ_CONSERVE on every grid the tile FFT kernels serve
+    (the 48^2 epilogue reduces each cell's moments over two warps): against
+    the oracle's projected Q, and moments of 1, v, |v|^2 at FP32 level."""
+    L = 10.0
+    f = workloads.bi_maxwellian(n, 2, N, L, seed=1300 + N)
+    Q = _gpu_collide(bz, 2, N, L, 1.0, f, "fp32", conserve=True)
+    Qr = oracle_k(2, N, L, 1.0).collide(as_input(f, "fp32"), conserve=True)
+    assert relerr(Q, Qr) < TOL32
+    v = workloads.velocity_nodes(N, L)
+    V1, V2 = np.meshgrid(v, v, indexing="ij")
+    for p in (np.ones_like(V1), V1, V2, V1 ** 2 + V2 ** 2):
+        mom = Q @ p.ravel()
+        assert np.abs(mom).max() < 1e-5 * np.abs(Q).sum(axis=1).max() * np.abs(p).max()
+
+
 def test_fp64_three_dimensional(bz, oracle_k):
     f = workloads.bi_maxwellian(35, 3, 8, 8.0, seed=11)
     Q = _gpu_collide(bz, 3, 8, 8.0, 1.0, f, "fp64")
@@ -207,10 +224,10 @@ def test_check_input_flags_nonfinite(bz):
     bz.check()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_deterministic_and_mass_conserving(bz, precision):
-    f = workloads.bi_maxwellian(50, 2, 32, 10.0, seed=8, noise=0.05)
-    m = bz.Modes(bz.Grid(2, 32, 10.0), 1.0)
+@pytest.mark.parametrize("precision,N", [("fp64", 32), ("fp32", 32), ("fp32", 48), ("fp32", 24)])
+def test_deterministic_and_mass_conserving(bz, precision, N):
+    f = workloads.bi_maxwellian(50, 2, N, 10.0, seed=8, noise=0.05)
+    m = bz.Modes(bz.Grid(2, N, 10.0), 1.0)
     x = to_dev(f, precision)
     Q1 = bz.collide_batch(m, x, precision=precision).cpu().numpy()
     Q2 = bz.collide_batch(m, x, precision=precision).cpu().numpy()
