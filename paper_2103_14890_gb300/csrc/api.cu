@@ -219,9 +219,9 @@ int phase_modesum(const bz_modes *m, int precision, const void *fh, void *qh, in
                   launch_modesum_generic_f64(v, m->d_F64, m->bcols, static_cast<const double2 *>(fh),
                                              static_cast<double2 *>(qh), n, st),
                   "collide: mode sum");
-    } else if (modesum32_2d_available(m)) {
+    } else if (modesum32_available(m)) {
         BZ_LAUNCH("modesum_f32", st,
-                  launch_modesum32_2d(m, static_cast<const float2 *>(fh), static_cast<float2 *>(qh), n, st),
+                  launch_modesum32(m, static_cast<const float2 *>(fh), static_cast<float2 *>(qh), n, st),
                   "collide: mode sum");
     } else {
         BZ_LAUNCH("modesum_f32_generic", st,
@@ -621,10 +621,10 @@ int group_collide(const bz_group_item *items, int n_items, int precision, int fl
         return BZ_OK;
     };
     // one grouped launch per kernel variant (items keep the longest-first order)
-    for (int var = 0; var < 3; ++var) {
+    for (int var = 0; var < kModesumVariants; ++var) {
         for (size_t q = 0; q < order.size(); ++q) {
             const bz_group_item &it = items[order[q]];
-            if (precision != BZ_FP32 || !modesum32_2d_available(it.modes) || it.modes->variant != var) continue;
+            if (precision != BZ_FP32 || !modesum32_available(it.modes) || it.modes->variant != var) continue;
             gm.push_back(it.modes);
             gf.push_back(reinterpret_cast<const float2 *>(fh_of(q)));
             gq.push_back(reinterpret_cast<float2 *>(qh_of(q)));
@@ -635,7 +635,7 @@ int group_collide(const bz_group_item *items, int n_items, int precision, int fl
     }
     for (size_t q = 0; q < order.size(); ++q) {
         const bz_group_item &it = items[order[q]];
-        if (precision == BZ_FP32 && modesum32_2d_available(it.modes)) continue;
+        if (precision == BZ_FP32 && modesum32_available(it.modes)) continue;
         rc = phase_modesum(it.modes, precision, fh_of(q), qh_of(q), it.n_cells, st);
         if (rc) return rc;
     }
@@ -678,7 +678,7 @@ int bz_modes_info(const bz_modes *m, int64_t out[8]) {
     out[4] = v.nhalf;
     out[5] = m->nq;
     out[6] = m->pairs_sym;
-    out[7] = modesum32_2d_available(m) ? m->modesum_variant : 0;
+    out[7] = modesum32_available(m) ? m->modesum_variant : 0;
     return BZ_OK;
 }
 

@@ -42,6 +42,8 @@ struct bz_grid {
     double cinv[25];
 };
 
+constexpr int kModesumVariants = 4;   // register-blocked FP32 mode-sum kernel variants
+
 struct bz_modes {
     const bz_grid *g;
     double gamma, b0;
@@ -54,9 +56,10 @@ struct bz_modes {
     // symmetric weight streams and task tables of the FP32 2-D kernel, one per
     // variant (k_modesum32.cu); d_W32 / d_task / w32_rowmax alias the variant
     // in use (null if the generic kernel serves this grid)
-    float *var_W[3];
-    int *var_task[3];
-    int var_rowmax[3];
+    float *var_W[kModesumVariants];
+    int *var_task[kModesumVariants];
+    int2 *var_rows[kModesumVariants];   // row-pair table of the tasks
+    int var_rowmax[kModesumVariants];
     int variant;          // index of the selected variant
     int modesum_variant;  // variant id reported to callers (index + 1; 0: generic kernel)
     float *d_W32;
@@ -109,6 +112,7 @@ struct Mode32Item {
     float2 *Qhat;
     const float *W;
     const int *tasks;
+    const int2 *rows;
     int h, M, nhalf, wrow_max;
     int64_t n;
 };
@@ -117,8 +121,8 @@ struct Mode32Group {
     int64_t tile_start[kMaxGroup + 1];   // prefix sums of 32-cell tiles
     Mode32Item item[kMaxGroup];
 };
-bool modesum32_2d_available(const bz_modes *m);
-cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st);
+bool modesum32_available(const bz_modes *m);
+cudaError_t launch_modesum32(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st);
 cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *const *fhat, float2 *const *Qhat,
                                    const int64_t *n, int count, cudaStream_t st);
 

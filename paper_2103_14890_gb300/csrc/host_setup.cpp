@@ -260,9 +260,10 @@ void modes_destroy(bz_modes *m) {
     if (!m) return;
     cudaFree(m->d_F64);
     cudaFree(m->d_F32);
-    for (int v = 0; v < 3; ++v) {
+    for (int v = 0; v < kModesumVariants; ++v) {
         cudaFree(m->var_W[v]);
         cudaFree(m->var_task[v]);
+        cudaFree(m->var_rows[v]);
     }
     free(m->h_F);
     free(m);

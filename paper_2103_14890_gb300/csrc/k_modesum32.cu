@@ -1,13 +1,17 @@
 // k_modesum32.cu -- register-blocked FP32 mode sum of eq. CF1 (Sec. 3.3) for
-// 2-D velocity grids with N <= 48.
+// 2-D velocity grids with N <= 48 and 3-D grids with N <= 16.
 //
 // Work reduction (exact algebra, no approximation):
 //   * Q is real, so only k_1 >= 0 is computed (Q-hat_{-k} = conj(Q-hat_k)).
 //   * The product f-hat_l f-hat_m is symmetric in (l, m): pairs with l_1 < m_1
 //     are summed once with the weight beta-hat(l,m) + beta-hat(m,l); pairs with
-//     l_1 = m_1 keep beta-hat(l,m).  So for row k_1 only l_1 in
-//     [k_1 - h, floor(k_1/2)] is visited and m_1 = k_1 - l_1 >= 0 always lies
-//     in the stored half spectrum; f-hat_l with l_1 < 0 is conj(f-hat_{-l}).
+//     l_1 = m_1 keep beta-hat(l,m).  So for outputs with first index k_1 only
+//     l_1 in [k_1 - h, floor(k_1/2)] is visited and m_1 = k_1 - l_1 >= 0 always
+//     lies in the stored half spectrum; f-hat_l with l_1 < 0 is conj(f-hat_{-l}).
+//   * A "row" is the line of modes along the last axis with all other indices
+//     fixed: (k_1) in 2-D, (k_1, k_2) in 3-D.  Each task lists the pairs of
+//     rows (row of l, row of m) it visits in a row table, so the kernel body is
+//     the same in both dimensions.
 //
 // Layout and blocking:
 //   * one CTA = one tile of C cells (C = 32, or 16 for grids whose spectrum
@@ -55,16 +59,15 @@ namespace {
 struct Variant {
     int R, warps, cells;
 };
-constexpr int kNumVariants = 3;
-constexpr Variant kVariants[kNumVariants] = {{8, 16, 32}, {4, 32, 32}, {4, 16, 16}};
-static_assert(kNumVariants == sizeof(bz_modes::var_W) / sizeof(float *), "one table slot per variant");
+constexpr int kNumVariants = kModesumVariants;
+constexpr Variant kVariants[kNumVariants] = {{8, 16, 32}, {4, 32, 32}, {4, 16, 16}, {4, 16, 8}};
 constexpr int kTaskInts = 12;   // ints per task record
 
 constexpr int kPad = 8;         // zero guard columns before the first and after the last row
 
 struct TaskRec {
-    int k1, k20, l1lo, nl1, l2lo, nblk, woff, rfirst;   // rfirst: first r (of RT) this task stores
-    int rem, rowf, pad0, pad1;                          // floats per l1 row in rowf
+    int orow, k20, rowoff, nrows, l2lo, nblk, woff, rfirst;   // rfirst: first r (of RT) this task stores
+    int rowf, pad0, pad1, pad2;                               // rowf: weight floats per row pair
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -167,6 +170,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
     float2 *__restrict__ Qhat = ip.Qhat;
     const float *__restrict__ W = ip.W;
     const int *__restrict__ tasks = ip.tasks;
+    const int2 *__restrict__ rows = ip.rows;
     const int h = ip.h, M = ip.M, nhalf = ip.nhalf, wrow_max = ip.wrow_max;
     const int64_t n = ip.n;
     const int64_t cta = (int64_t)blockIdx.x - gd.tile_start[it];
@@ -202,24 +206,26 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
         for (int r = 0; r < RR; ++r) hi[r] = lo[r] = acc[r] = make_float2(0.f, 0.f);
         const int k20 = tk.k20 + grp * RR;                // this thread's first output column
         const int mbase0 = k20 - tk.l2lo - (RR - 1);
+        const int2 *trow = rows + tk.rowoff;
+        int2 rp = __ldg(trow);                            // (2 * row of l + (l read reversed), row of m)
         stage_row(wbuf0, wsrc, rowf, lane);
-        for (int i = 0; i < tk.nl1; ++i) {
+        for (int i = 0; i < tk.nrows; ++i) {
             const float *wcur = (i & 1) ? wbuf1 : wbuf0;
-            if (i + 1 < tk.nl1) {
+            const int2 rnext = (i + 1 < tk.nrows) ? __ldg(trow + i + 1) : rp;
+            if (i + 1 < tk.nrows) {
                 stage_row((i & 1) ? wbuf0 : wbuf1, wsrc + (size_t)(i + 1) * rowf, rowf, lane);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
             }
             __syncwarp();
-            const int l1 = tk.l1lo + i;
-            const int m1 = tk.k1 - l1;                    // >= 0: stored row
-            const int dir = l1 < 0 ? -1 : 1;              // f-hat_l = conj(f-hat_{-l}) for l_1 < 0
-            row_pass<RR, CELLS, RT>(F0 + (size_t)(dir * l1) * M * CELLS, dir, F0 + (size_t)m1 * M * CELLS,
+            const int dir = (rp.x & 1) ? -1 : 1;          // f-hat_l = conj(f-hat_{-l}): row of -l read backwards
+            row_pass<RR, CELLS, RT>(F0 + (size_t)(rp.x >> 1) * M * CELLS, dir, F0 + (size_t)rp.y * M * CELLS,
                                     wcur + grp * RR, tk.nblk * G, tk.l2lo, mbase0, acc);
+            rp = rnext;
             __syncwarp();
             // fold the FP32 row sums (<= 4 rows) into (hi, lo)
-            if ((i & 3) == 3 || i + 1 == tk.nl1) {
+            if ((i & 3) == 3 || i + 1 == tk.nrows) {
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
                     float s, e;
@@ -235,11 +241,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
         }
         const int64_t c = tile * 32 + sub * CELLS + cell;
         if (c < n) {
-            float2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.k1 * M * 32 + sub * CELLS + cell;
+            float2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.orow * M * 32 + sub * CELLS + cell;
 #pragma unroll
             for (int r = 0; r < RR; ++r) {
                 const int k2 = k20 + r;
-                if (grp * RR + r >= tk.rfirst && k2 <= h) out[(k2 + h) * 32] = make_float2(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
+                if (grp * RR + r >= tk.rfirst && k2 <= h)
+                    out[(k2 + h) * 32] = make_float2(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
             }
         }
     }
@@ -255,76 +262,107 @@ size_t smem_bytes(const GridView &g, int wrow_max, int v) {
 // Host part: weight streams and the task table, built once per modes handle.
 double beta_host(const bz_modes *m, const int *l, const int *mm);
 
-// Weight stream and task table of one variant (slot v); false if the grid is
-// not covered by this variant (another variant or the generic kernel serves it).
+// Weight stream, task table and row table of one variant (slot v); false if
+// the grid is not covered by this variant (another variant or the generic
+// kernel serves it).
 static bool build_variant(bz_modes *m, int v, int &rc) {
     const int R = kVariants[v].R * (32 / kVariants[v].cells);   // outputs per task (RT)
     const int kWarps = kVariants[v].warps;
     rc = BZ_OK;
     const GridView &gv = m->g->v;
-    if (gv.dim != 2 || gv.N > 48 || gv.M < R) return false;
+    const int d = gv.dim, h = gv.h, M = gv.M;
+    if (!((d == 2 && gv.N <= 48) || (d == 3 && gv.N <= 16))) return false;
     // shared memory of the spectrum alone must leave room for the weight buffers
     if (sizeof(float2) * (size_t)(gv.nhalf + 2 * kPad) * kVariants[v].cells > 200 * 1024) return false;
-    const int h = gv.h;
-    const int nb = (gv.M + R - 1) / R;
+    const int nb = (M + R - 1) / R;
     const int lo_col = -h - kPad, hi_col = h + kPad;         // addressable columns
     std::vector<TaskRec> tasks;
     std::vector<float> W;
+    std::vector<int2> rowtab;
     std::vector<double> cost;
+    const int nmid = (d == 3) ? M : 1;                      // values of the middle index (3-D)
+    struct Pair { int l[2], m[2]; };                         // leading indices of l and m
     for (int k1 = 0; k1 <= h; ++k1) {
-        int prev_end = -h - 1;
-        for (int b = 0; b < nb; ++b) {
-            // blocks of R consecutive k2; the last one ends at h (it may overlap the
-            // previous block, whose outputs it then does not store)
-            const int k20 = std::min(-h + R * b, h - R + 1);
-            const int k2last = k20 + R - 1;
-            const int lo = std::max(-h, k20 - h), hi = std::min(h, k2last + h);
-            const int len = hi - lo + 1;
-            const int nblk = (len + R - 1) / R;
-            const int npad = nblk * R;
-            // place the padded range [l2lo, l2lo + npad - 1] so that every f-hat_l
-            // column and every window column k2 - l2 lies within kPad of [-h, h]
-            int l2lo = 0;
-            bool placed = false;
-            for (int cand = lo - (npad - len); cand <= lo && !placed; ++cand) {
-                const int last = cand + npad - 1;
-                if (cand < lo_col || last > hi_col) continue;
-                if (k20 - last < lo_col || k2last - cand > hi_col) continue;
-                l2lo = cand;
-                placed = true;
-            }
-            if (!placed) return false;
-            TaskRec t;
-            t.k1 = k1;
-            t.k20 = k20;
-            t.l1lo = k1 - h;
-            t.nl1 = k1 / 2 - (k1 - h) + 1;
-            t.l2lo = l2lo;
-            t.nblk = nblk;
-            t.woff = (int)W.size();
-            t.rfirst = std::max(0, prev_end + 1 - k20);
-            t.rem = R;
-            t.rowf = npad * R;
-            t.pad0 = t.pad1 = 0;
-            prev_end = k2last;
-            for (int i = 0; i < t.nl1; ++i) {
-                const int l1 = t.l1lo + i, m1 = k1 - l1;
-                for (int j = 0; j < npad; ++j) {
-                    const int l2 = l2lo + j;
-                    for (int r = 0; r < R; ++r) {
-                        const int k2 = k20 + r, m2 = k2 - l2;
-                        double w = 0.0;
-                        if (k2 <= h && l2 >= -h && l2 <= h && m2 >= -h && m2 <= h) {
-                            int l[2] = {l1, l2}, mm[2] = {m1, m2};
-                            w = beta_host(m, l, mm);
-                            if (l1 < m1) w += beta_host(m, mm, l);
-                        }
-                        W.push_back((float)w);
-                    }
+        for (int i2 = 0; i2 < nmid; ++i2) {
+            const int k2 = (d == 3) ? i2 - h : 0;
+            const int orow = (d == 3) ? k1 * M + i2 : k1;
+            std::vector<Pair> pairs;                         // row pairs visited for this output row
+            for (int l1 = k1 - h; l1 <= k1 / 2; ++l1) {
+                const int m1 = k1 - l1;
+                if (d == 2) {
+                    pairs.push_back({{l1, 0}, {m1, 0}});
+                } else {
+                    for (int l2 = std::max(-h, k2 - h); l2 <= std::min(h, k2 + h); ++l2)
+                        pairs.push_back({{l1, l2}, {m1, k2 - l2}});
                 }
             }
-            tasks.push_back(t);
-            cost.push_back((double)t.nl1 * npad);
+            int prev_end = -h - 1;
+            for (int b = 0; b < nb; ++b) {
+                // blocks of R consecutive last-axis outputs; the last one ends at h
+                // (it may overlap the previous block, whose outputs it then does
+                // not store); a block wider than the row starts at -h
+                const int k20 = std::max(-h, std::min(-h + R * b, h - R + 1));
+                const int k2last = k20 + R - 1;
+                const int lo = std::max(-h, k20 - h), hi = std::min(h, k2last + h);
+                const int len = hi - lo + 1;
+                const int nblk = (len + R - 1) / R;
+                const int npad = nblk * R;
+                // place the padded range [l2lo, l2lo + npad - 1] so that every f-hat_l
+                // column and every window column k - l lies within kPad of [-h, h]
+                int l2lo = 0;
+                bool placed = false;
+                for (int cand = lo - (npad - len); cand <= lo && !placed; ++cand) {
+                    const int last = cand + npad - 1;
+                    if (cand < lo_col || last > hi_col) continue;
+                    if (k20 - last < lo_col || k2last - cand > hi_col) continue;
+                    l2lo = cand;
+                    placed = true;
+                }
+                if (!placed) return false;
+                TaskRec t;
+                t.orow = orow;
+                t.k20 = k20;
+                t.rowoff = (int)rowtab.size();
+                t.nrows = (int)pairs.size();
+                t.l2lo = l2lo;
+                t.nblk = nblk;
+                t.woff = (int)W.size();
+                t.rfirst = std::max(0, prev_end + 1 - k20);
+                t.rowf = npad * R;
+                t.pad0 = t.pad1 = t.pad2 = 0;
+                prev_end = k2last;
+                for (const Pair &p : pairs) {
+                    // row of l (that of -l read backwards when l_1 < 0) and row of m
+                    const bool neg = p.l[0] < 0;
+                    const int a1 = neg ? -p.l[0] : p.l[0], a2 = neg ? -p.l[1] : p.l[1];
+                    const int lrow = (d == 3) ? a1 * M + (a2 + h) : a1;
+                    const int mrow = (d == 3) ? p.m[0] * M + (p.m[1] + h) : p.m[0];
+                    rowtab.push_back(make_int2(2 * lrow + (neg ? 1 : 0), mrow));
+                    for (int j = 0; j < npad; ++j) {
+                        const int lz = l2lo + j;
+                        for (int r = 0; r < R; ++r) {
+                            const int kz = k20 + r, mz = kz - lz;
+                            double w = 0.0;
+                            if (kz <= h && lz >= -h && lz <= h && mz >= -h && mz <= h) {
+                                int l[3], mm[3];
+                                l[0] = p.l[0];
+                                mm[0] = p.m[0];
+                                if (d == 3) {
+                                    l[1] = p.l[1];
+                                    mm[1] = p.m[1];
+                                }
+                                l[d - 1] = lz;
+                                mm[d - 1] = mz;
+                                w = beta_host(m, l, mm);
+                                if (p.l[0] < p.m[0]) w += beta_host(m, mm, l);
+                            }
+                            W.push_back((float)w);
+                        }
+                    }
+                }
+                tasks.push_back(t);
+                cost.push_back((double)t.nrows * npad);
+            }
         }
     }
     // longest-processing-time-first assignment of tasks to the warps of a CTA
@@ -353,23 +391,28 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
     if (smem_bytes(gv, wrow_max, v) > 227 * 1024) return false;   // does not fit
     float *dW = nullptr;
     int *dT = nullptr;
+    int2 *dR = nullptr;
     cudaError_t e = cudaMalloc(&dW, sizeof(float) * W.size());
     if (e == cudaSuccess) e = cudaMalloc(&dT, sizeof(int) * tab.size());
+    if (e == cudaSuccess) e = cudaMalloc(&dR, sizeof(int2) * rowtab.size());
     if (e == cudaSuccess) e = cudaMemcpy(dW, W.data(), sizeof(float) * W.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dT, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dR, rowtab.data(), sizeof(int2) * rowtab.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(dW);
         cudaFree(dT);
+        cudaFree(dR);
         rc = cuda_fail(e, "build_kernel_modes: FP32 weight stream");
         return false;
     }
     m->var_W[v] = dW;
     m->var_task[v] = dT;
+    m->var_rows[v] = dR;
     m->var_rowmax[v] = wrow_max;
     return true;
 }
 
-bool modesum32_2d_available(const bz_modes *m) { return m->d_W32 != nullptr; }
+bool modesum32_available(const bz_modes *m) { return m->d_W32 != nullptr; }
 
 template <int RR, int WARPS, int CELLS>
 static cudaError_t launch_instance(const Mode32Group &gd, size_t sm, cudaStream_t st) {
@@ -385,6 +428,7 @@ static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStr
         case 0: return launch_instance<8, 16, 32>(gd, sm, st);
         case 1: return launch_instance<4, 32, 32>(gd, sm, st);
         case 2: return launch_instance<4, 16, 16>(gd, sm, st);
+        case 3: return launch_instance<4, 16, 8>(gd, sm, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -395,6 +439,7 @@ static void fill_item(Mode32Item &it, const bz_modes *m, int v, const float2 *fh
     it.Qhat = Qhat;
     it.W = m->var_W[v];
     it.tasks = m->var_task[v];
+    it.rows = m->var_rows[v];
     it.h = gv.h;
     it.M = gv.M;
     it.nhalf = (int)gv.nhalf;
@@ -420,7 +465,7 @@ static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, 
     return launch_group(gd, v, smem_bytes(m->g->v, m->var_rowmax[v], v), st);
 }
 
-cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
+cudaError_t launch_modesum32(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
     return launch_variant(m, m->variant, fhat, Qhat, n, st);
 }
 
@@ -502,7 +547,9 @@ static int autotune(bz_modes *m, int &rc) {
     if (it != g_tune.end())
         for (int q = 0; q < na; ++q)
             if (avail[q] == it->second) return avail[q];
-    const int64_t n = (int64_t)2 * sms * 32;
+    // six 32-cell tiles per SM (several waves, so the tail does not decide);
+    // two rounds over the variants, best of three launches each
+    const int64_t n = (int64_t)6 * sms * 32;
     const size_t bytes = 2 * sizeof(float2) * (size_t)((n + 31) / 32) * gv.nhalf * 32;
     void *buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, bytes);
@@ -510,24 +557,28 @@ static int autotune(bz_modes *m, int &rc) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
-    float best = 1e30f;
-    int pick = avail[0];
+    float best[kNumVariants];
+    for (int q = 0; q < kNumVariants; ++q) best[q] = 1e30f;
     const float2 *fh = static_cast<const float2 *>(buf);
     float2 *qh = static_cast<float2 *>(buf) + bytes / (2 * sizeof(float2));
-    for (int q = 0; q < na && e == cudaSuccess; ++q) {
-        const int v = avail[q];
-        e = launch_variant(m, v, fh, qh, n, nullptr);                  // warm-up
-        if (e == cudaSuccess) e = cudaEventRecord(a, nullptr);
-        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = launch_variant(m, v, fh, qh, n, nullptr);
-        if (e == cudaSuccess) e = cudaEventRecord(b, nullptr);
-        if (e == cudaSuccess) e = cudaEventSynchronize(b);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-        if (e == cudaSuccess && ms < best) {
-            best = ms;
-            pick = v;
+    for (int round = 0; round < 2 && e == cudaSuccess; ++round) {
+        for (int q = 0; q < na && e == cudaSuccess; ++q) {
+            const int v = avail[q];
+            e = launch_variant(m, v, fh, qh, n, nullptr);              // warm-up
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                e = cudaEventRecord(a, nullptr);
+                if (e == cudaSuccess) e = launch_variant(m, v, fh, qh, n, nullptr);
+                if (e == cudaSuccess) e = cudaEventRecord(b, nullptr);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+                if (e == cudaSuccess) best[v] = std::min(best[v], ms);
+            }
         }
     }
+    int pick = avail[0];
+    for (int q = 1; q < na; ++q)
+        if (best[avail[q]] < best[pick]) pick = avail[q];
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
     cudaFree(buf);
@@ -550,6 +601,7 @@ int modes_build_fp32_tables(bz_modes *m) {
     for (int v = 0; v < kNumVariants; ++v) {
         m->var_W[v] = nullptr;
         m->var_task[v] = nullptr;
+        m->var_rows[v] = nullptr;
         m->var_rowmax[v] = 0;
         if (build_variant(m, v, rc)) any = true;
         if (rc) return rc;

@@ -50,9 +50,9 @@ int noalloc_scratch(void **out) {
 }
 }  // namespace
 
-cudaError_t launch_modesum32_2d(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n,
+cudaError_t launch_modesum32(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n,
                                 cudaStream_t st);
-bool modesum32_2d_available(const bz_modes *m);
+bool modesum32_available(const bz_modes *m);
 
 namespace {
 // The kernel sequence of collide_batch (forward DFT, mode sum, inverse DFT)
@@ -81,7 +81,7 @@ int run_with_scratch(const bz_modes *m, int precision, int flags, const void *f,
         e = m->tile_dft ? launch_dft32_forward_tile(v, fin, fh, n, st)
                     : launch_dft_forward_f32(v, g->d_E32, fin, fh, n, st);
         if (e == cudaSuccess)
-            e = modesum32_2d_available(m) ? launch_modesum32_2d(m, fh, qh, n, st)
+            e = modesum32_available(m) ? launch_modesum32(m, fh, qh, n, st)
                                           : launch_modesum_generic_f32(v, m->d_F32, m->bcols, fh, qh, n, st);
         if (e == cudaSuccess)
             e = m->tile_dft ? launch_dft32_inverse_tile(v, qh, qout, n, m->scale, g->cinv, ep, st)

@@ -56,28 +56,45 @@ def test_kernel_modes_match_oracle(bz, oracle_k, dim, N, gamma):
 
 def test_fast_kernels_selected(bz):
     """The register-blocked FP32 mode sum serves every 2-D grid with 16 <= N <= 48
-    (a silent fall back to the generic kernel would hide a table-building bug)."""
+    and the 3-D grids up to 16^3 (a silent fall back to the generic kernel would
+    hide a table-building bug)."""
     for N in (16, 24, 32):
         assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant in (1, 2, 3), N
     assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_variant == 3    # only 16-cell tiles fit
+    assert bz.Modes(bz.Grid(3, 16, 10.0), 1.0).modesum_variant == 4    # 8-cell tiles, 3-D rows
+    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant in (1, 2, 3)   # 16-wide blocks overhang a 7-mode row
     assert bz.Modes(bz.Grid(2, 64, 10.0), 1.0).modesum_variant == 0
-    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant == 0
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
-@pytest.mark.parametrize("N", [16, 24, 32])
-def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, N, variant):
+@pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3)]
+                         + [(2, 16, 4), (3, 8, 1), (3, 8, 2), (3, 8, 3)])
+def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, dim, N, variant):
     """Every register-blocked variant (fixed through BZ_MODESUM_VARIANT, bypassing
     the autotuner) against the oracle: 70 cells = 2 full tiles and a ragged tail."""
     monkeypatch.setenv("BZ_MODESUM_VARIANT", str(variant))
     L = 10.0
-    m = bz.Modes(bz.Grid(2, N, L), 1.0)
+    m = bz.Modes(bz.Grid(dim, N, L), 1.0)
     assert m.modesum_variant == variant
-    f = workloads.bi_maxwellian(70, 2, N, L, seed=1100 + N)
+    f = workloads.bi_maxwellian(70, dim, N, L, seed=1100 + N)
     fin = as_input(f, "fp32")
     Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32")
     bz.check()
-    Qr = oracle_k(2, N, L, 1.0).collide(fin)
+    Qr = oracle_k(dim, N, L, 1.0).collide(fin)
+    assert relerr(Q.double().cpu().numpy(), Qr) < TOL32
+
+
+@pytest.mark.parametrize("n", [1, 8, 13])
+def test_fp32_3d_16_grid_8_cell_tiles(bz, oracle_k, n):
+    """16^3 grid on [-10,10]^3 (register-blocked 3-D path, 8-cell tiles): one
+    cell, exactly one CTA, and one and a half CTAs, against the oracle."""
+    N, L = 16, 10.0
+    m = bz.Modes(bz.Grid(3, N, L), 1.0)
+    assert m.modesum_variant == 4
+    f = workloads.bi_maxwellian(n, 3, N, L, seed=1400 + n)
+    fin = as_input(f, "fp32")
+    Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32")
+    bz.check()
+    Qr = oracle_k(3, N, L, 1.0).collide(fin)
     assert relerr(Q.double().cpu().numpy(), Qr) < TOL32
 
 

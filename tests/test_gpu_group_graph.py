@@ -42,12 +42,12 @@ def test_group_collide_mixed_variants(bz, monkeypatch):
     launch per variant), results equal to per-instance calls."""
     import torch
     entries, refs = [], []
-    for i, (N, var, n) in enumerate([(32, 1, 80), (24, 2, 50), (32, 3, 33), (16, 1, 70), (48, 3, 21),
-                                     (24, 3, 40)]):
+    for i, (d, N, var, n) in enumerate([(2, 32, 1, 80), (2, 24, 2, 50), (2, 32, 3, 33), (2, 16, 1, 70),
+                                        (2, 48, 3, 21), (2, 24, 3, 40), (3, 16, 4, 11), (2, 16, 4, 9)]):
         monkeypatch.setenv("BZ_MODESUM_VARIANT", str(var))
-        m = bz.Modes(bz.Grid(2, N, 10.0), 1.0)
+        m = bz.Modes(bz.Grid(d, N, 10.0), 1.0)
         assert m.modesum_variant == var
-        f = to_dev(workloads.bi_maxwellian(n, 2, N, 10.0, seed=90 + i), "fp32")
+        f = to_dev(workloads.bi_maxwellian(n, d, N, 10.0, seed=90 + i), "fp32")
         refs.append(bz.collide_batch(m, f, precision="fp32").cpu().numpy())
         entries.append((m, f, torch.full_like(f, float("nan"))))
     bz.group_collide(entries, precision="fp32")
