@@ -58,7 +58,6 @@ struct bz_modes {
     // in use (null if the generic kernel serves this grid)
     float *var_W[kModesumVariants];
     int *var_task[kModesumVariants];
-    int2 *var_rows[kModesumVariants];   // row-pair table of the tasks
     int var_rowmax[kModesumVariants];
     int variant;          // index of the selected variant
     int modesum_variant;  // variant id reported to callers (index + 1; 0: generic kernel)
@@ -112,7 +111,6 @@ struct Mode32Item {
     float2 *Qhat;
     const float *W;
     const int *tasks;
-    const int2 *rows;
     int h, M, nhalf, wrow_max;
     int64_t n;
 };

@@ -263,7 +263,6 @@ void modes_destroy(bz_modes *m) {
     for (int v = 0; v < kModesumVariants; ++v) {
         cudaFree(m->var_W[v]);
         cudaFree(m->var_task[v]);
-        cudaFree(m->var_rows[v]);
     }
     free(m->h_F);
     free(m);

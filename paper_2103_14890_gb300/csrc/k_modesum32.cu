@@ -9,8 +9,8 @@
 //     l_1 in [k_1 - h, floor(k_1/2)] is visited and m_1 = k_1 - l_1 >= 0 always
 //     lies in the stored half spectrum; f-hat_l with l_1 < 0 is conj(f-hat_{-l}).
 //   * A "row" is the line of modes along the last axis with all other indices
-//     fixed: (k_1) in 2-D, (k_1, k_2) in 3-D.  Each task lists the pairs of
-//     rows (row of l, row of m) it visits in a row table, so the kernel body is
+//     fixed: (k_1) in 2-D, (k_1, k_2) in 3-D.  Each task's weight stream names
+//     the pairs of rows (row of l, row of m) it visits, so the kernel body is
 //     the same in both dimensions.
 //
 // Layout and blocking:
@@ -24,9 +24,10 @@
 //     block, each thread owning R = RT/2 of them.  Walking l_2 upwards slides
 //     the window of f-hat_m values (m_2 = k_2 - l_2) down by one, so each step
 //     loads one new f-hat_m, one f-hat_l and R weights for 6 R FP32 operations.
-//   * each task's weights form a contiguous stream [l_1][l_2 (padded to a
-//     multiple of RT)][r]; one l_1 row is staged into a per-warp shared-memory
-//     double buffer with cp.async while the previous row is being used.
+//   * each task's weights form a contiguous stream of row pairs, each a
+//     16-byte header (which rows of l and m) followed by [l (padded to a
+//     multiple of RT)][r]; one row pair is staged into a per-warp
+//     shared-memory double buffer with cp.async while the previous one is used.
 //   * the rows of the spectrum are stored back to back, with kPad zero columns
 //     before the first and after the last row only.  A column index that falls
 //     outside [-h, h] therefore reads a neighbouring row's (finite) value or a
@@ -64,10 +65,11 @@ constexpr Variant kVariants[kNumVariants] = {{8, 16, 32}, {4, 32, 32}, {4, 16, 1
 constexpr int kTaskInts = 12;   // ints per task record
 
 constexpr int kPad = 8;         // zero guard columns before the first and after the last row
+constexpr int kRowHead = 4;     // floats of row-pair header in front of each weight row (16 bytes)
 
 struct TaskRec {
-    int orow, k20, rowoff, nrows, l2lo, nblk, woff, rfirst;   // rfirst: first r (of RT) this task stores
-    int rowf, pad0, pad1, pad2;                               // rowf: weight floats per row pair
+    int orow, k20, nrows, l2lo, nblk, woff, rfirst;   // rfirst: first r (of RT) this task stores
+    int rowf, pad0, pad1, pad2, pad3;                 // rowf: floats per row pair (header + weights)
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -170,7 +172,6 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
     float2 *__restrict__ Qhat = ip.Qhat;
     const float *__restrict__ W = ip.W;
     const int *__restrict__ tasks = ip.tasks;
-    const int2 *__restrict__ rows = ip.rows;
     const int h = ip.h, M = ip.M, nhalf = ip.nhalf, wrow_max = ip.wrow_max;
     const int64_t n = ip.n;
     const int64_t cta = (int64_t)blockIdx.x - gd.tile_start[it];
@@ -206,12 +207,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
         for (int r = 0; r < RR; ++r) hi[r] = lo[r] = acc[r] = make_float2(0.f, 0.f);
         const int k20 = tk.k20 + grp * RR;                // this thread's first output column
         const int mbase0 = k20 - tk.l2lo - (RR - 1);
-        const int2 *trow = rows + tk.rowoff;
-        int2 rp = __ldg(trow);                            // (2 * row of l + (l read reversed), row of m)
         stage_row(wbuf0, wsrc, rowf, lane);
         for (int i = 0; i < tk.nrows; ++i) {
             const float *wcur = (i & 1) ? wbuf1 : wbuf0;
-            const int2 rnext = (i + 1 < tk.nrows) ? __ldg(trow + i + 1) : rp;
             if (i + 1 < tk.nrows) {
                 stage_row((i & 1) ? wbuf0 : wbuf1, wsrc + (size_t)(i + 1) * rowf, rowf, lane);
                 cp_async_wait<1>();
@@ -219,10 +217,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
                 cp_async_wait<0>();
             }
             __syncwarp();
-            const int dir = (rp.x & 1) ? -1 : 1;          // f-hat_l = conj(f-hat_{-l}): row of -l read backwards
-            row_pass<RR, CELLS, RT>(F0 + (size_t)(rp.x >> 1) * M * CELLS, dir, F0 + (size_t)rp.y * M * CELLS,
-                                    wcur + grp * RR, tk.nblk * G, tk.l2lo, mbase0, acc);
-            rp = rnext;
+            // row header: element offsets of the rows of l and m, and the
+            // direction of l (-1: f-hat_l = conj(f-hat_{-l}), row of -l read backwards)
+            const int4 hd = *reinterpret_cast<const int4 *>(wcur);
+            row_pass<RR, CELLS, RT>(F0 + hd.x, hd.z, F0 + hd.y, wcur + kRowHead + grp * RR, tk.nblk * G, tk.l2lo,
+                                    mbase0, acc);
             __syncwarp();
             // fold the FP32 row sums (<= 4 rows) into (hi, lo)
             if ((i & 3) == 3 || i + 1 == tk.nrows) {
@@ -262,7 +261,7 @@ size_t smem_bytes(const GridView &g, int wrow_max, int v) {
 // Host part: weight streams and the task table, built once per modes handle.
 double beta_host(const bz_modes *m, const int *l, const int *mm);
 
-// Weight stream, task table and row table of one variant (slot v); false if
+// Weight stream (with row-pair headers) and task table of one variant (slot v); false if
 // the grid is not covered by this variant (another variant or the generic
 // kernel serves it).
 static bool build_variant(bz_modes *m, int v, int &rc) {
@@ -278,7 +277,6 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
     const int lo_col = -h - kPad, hi_col = h + kPad;         // addressable columns
     std::vector<TaskRec> tasks;
     std::vector<float> W;
-    std::vector<int2> rowtab;
     std::vector<double> cost;
     const int nmid = (d == 3) ? M : 1;                      // values of the middle index (3-D)
     struct Pair { int l[2], m[2]; };                         // leading indices of l and m
@@ -322,14 +320,13 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
                 TaskRec t;
                 t.orow = orow;
                 t.k20 = k20;
-                t.rowoff = (int)rowtab.size();
                 t.nrows = (int)pairs.size();
                 t.l2lo = l2lo;
                 t.nblk = nblk;
                 t.woff = (int)W.size();
                 t.rfirst = std::max(0, prev_end + 1 - k20);
-                t.rowf = npad * R;
-                t.pad0 = t.pad1 = t.pad2 = 0;
+                t.rowf = kRowHead + npad * R;
+                t.pad0 = t.pad1 = t.pad2 = t.pad3 = 0;
                 prev_end = k2last;
                 for (const Pair &p : pairs) {
                     // row of l (that of -l read backwards when l_1 < 0) and row of m
@@ -337,7 +334,13 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
                     const int a1 = neg ? -p.l[0] : p.l[0], a2 = neg ? -p.l[1] : p.l[1];
                     const int lrow = (d == 3) ? a1 * M + (a2 + h) : a1;
                     const int mrow = (d == 3) ? p.m[0] * M + (p.m[1] + h) : p.m[0];
-                    rowtab.push_back(make_int2(2 * lrow + (neg ? 1 : 0), mrow));
+                    const int cs = kVariants[v].cells;
+                    const int head[kRowHead] = {lrow * M * cs, mrow * M * cs, neg ? -1 : 1, 0};
+                    for (int q = 0; q < kRowHead; ++q) {
+                        float x;
+                        std::memcpy(&x, &head[q], sizeof x);
+                        W.push_back(x);
+                    }
                     for (int j = 0; j < npad; ++j) {
                         const int lz = l2lo + j;
                         for (int r = 0; r < R; ++r) {
@@ -387,27 +390,22 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
     }
     tab[kWarps] = pos;
     int wrow_max = 0;
-    for (auto &t : tasks) wrow_max = std::max(wrow_max, t.nblk * R * R);   // staging buffer: whole blocks
+    for (auto &t : tasks) wrow_max = std::max(wrow_max, t.rowf);   // staging buffer: one row pair
     if (smem_bytes(gv, wrow_max, v) > 227 * 1024) return false;   // does not fit
     float *dW = nullptr;
     int *dT = nullptr;
-    int2 *dR = nullptr;
     cudaError_t e = cudaMalloc(&dW, sizeof(float) * W.size());
     if (e == cudaSuccess) e = cudaMalloc(&dT, sizeof(int) * tab.size());
-    if (e == cudaSuccess) e = cudaMalloc(&dR, sizeof(int2) * rowtab.size());
     if (e == cudaSuccess) e = cudaMemcpy(dW, W.data(), sizeof(float) * W.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dT, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(dR, rowtab.data(), sizeof(int2) * rowtab.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(dW);
         cudaFree(dT);
-        cudaFree(dR);
         rc = cuda_fail(e, "build_kernel_modes: FP32 weight stream");
         return false;
     }
     m->var_W[v] = dW;
     m->var_task[v] = dT;
-    m->var_rows[v] = dR;
     m->var_rowmax[v] = wrow_max;
     return true;
 }
@@ -439,7 +437,6 @@ static void fill_item(Mode32Item &it, const bz_modes *m, int v, const float2 *fh
     it.Qhat = Qhat;
     it.W = m->var_W[v];
     it.tasks = m->var_task[v];
-    it.rows = m->var_rows[v];
     it.h = gv.h;
     it.M = gv.M;
     it.nhalf = (int)gv.nhalf;
@@ -601,7 +598,6 @@ int modes_build_fp32_tables(bz_modes *m) {
     for (int v = 0; v < kNumVariants; ++v) {
         m->var_W[v] = nullptr;
         m->var_task[v] = nullptr;
-        m->var_rows[v] = nullptr;
         m->var_rowmax[v] = 0;
         if (build_variant(m, v, rc)) any = true;
         if (rc) return rc;
