@@ -133,6 +133,23 @@ int build_kernel_modes(const bz_grid *g, double gamma, double b0, int quad_nodes
 int collide_batch(const bz_modes *m, int precision, int flags, const void *f, void *Q,
                   int64_t n_cells, void *stream);
 
+/* collide_batch_host -- collide_batch on HOST buffers (the operator of Sec.
+ * 3.3 for callers whose distributions live in host memory).
+ *   f_host, Q_host : host arrays [n_cells][N^d], float64 for BZ_FP64, float32
+ *                    for BZ_FP32; caller-owned, must not overlap
+ *   other arguments: as collide_batch
+ * The batch moves in chunks of 32 x (SM count) cells (4864 on a 152-SM GPU)
+ * through two device slots taken from the library's pool: the copy of chunk c+1 to the device, the collision of
+ * chunk c on `stream` and the copy of chunk c-1 back run concurrently (two
+ * library-owned copy streams, ordered by events).  Asynchronous like the other
+ * calls: Q_host is complete once `stream` has completed (bz_check(stream) or
+ * cudaStreamSynchronize).  The copies overlap only if the host buffers are
+ * page-locked (cudaHostAlloc / cudaHostRegister); pageable buffers give the
+ * same results without overlap.  Not available inside a stream capture.
+ * Errors: as collide_batch; BZ_EINVAL inside a capture. */
+int collide_batch_host(const bz_modes *m, int precision, int flags, const void *f_host, void *Q_host,
+                       int64_t n_cells, void *stream);
+
 /* imex_stage_local -- stage l (1-based) of the penalised IMEX Runge-Kutta step
  * of Sec. 3.4 (eq. Bref2: Q = G_P + Q_BGK with G_P explicit and the BGK
  * operator nu (M - f), nu = rho, implicit), cell by cell:

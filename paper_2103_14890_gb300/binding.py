@@ -66,6 +66,7 @@ def load(path=None):
             "bz_modes_destroy": ([c_p], None),
             "bz_profile": ([c_i], c_i),
             "collide_batch_noalloc": ([c_p, c_i, c_i, c_p, c_p, c_i64, c_p], c_i),
+            "collide_batch_host": ([c_p, c_i, c_i, c_p, c_p, c_i64, c_p], c_i),
             "group_collide": ([c_p, c_i, c_i, c_i, c_p], c_i),
             "bz_profile_read": ([c_p, c_i, c_p, c_p, c_i], c_i),
         }
@@ -178,6 +179,48 @@ def collide_batch_noalloc(modes, f, Q=None, precision="fp32", conserve=False, st
         raise ValueError("f must have n_cells * N^d elements")
     _check(load().collide_batch_noalloc(modes._h, PRECISION[precision], CONSERVE if conserve else 0,
                                         _dptr(f, dt, "f"), _dptr(Q, dt, "Q"), n, _stream(stream)))
+    return Q
+
+
+def _hptr(a, dtype_name, what):
+    """Host pointer of a contiguous CPU torch tensor or numpy array."""
+    import numpy as np
+    try:
+        import torch
+    except ImportError:        # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        if a.is_cuda:
+            raise TypeError("%s must be a host (CPU) tensor" % what)
+        if str(a.dtype) != "torch." + dtype_name:
+            raise TypeError("%s must be %s, got %s" % (what, dtype_name, a.dtype))
+        if not a.is_contiguous():
+            raise ValueError("%s must be contiguous" % what)
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype_name):
+            raise TypeError("%s must be %s, got %s" % (what, dtype_name, a.dtype))
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("%s must be C-contiguous" % what)
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError("%s must be a CPU torch tensor or a numpy array" % what)
+
+
+def collide_batch_host(modes, f, Q=None, precision="fp32", conserve=False, check_input=False, stream=None):
+    """Q(f) for HOST f of shape (n_cells, N^d) (CPU torch tensor, pinned for
+    overlap, or numpy array); Q is returned in the same kind of container and
+    is complete once the stream has completed."""
+    import numpy as np
+    name = "float64" if precision == "fp64" else "float32"
+    if Q is None:
+        Q = np.empty_like(f) if isinstance(f, np.ndarray) else f.new_empty(f.shape).pin_memory() \
+            if f.is_pinned() else f.new_empty(f.shape)
+    n = f.shape[0] if len(f.shape) > 1 else 1
+    if int(np.prod(f.shape)) != n * modes.nv or int(np.prod(Q.shape)) != n * modes.nv:
+        raise ValueError("f and Q must have n_cells * N^d elements")
+    flags = (CONSERVE if conserve else 0) | (CHECK_INPUT if check_input else 0)
+    _check(load().collide_batch_host(modes._h, PRECISION[precision], flags, _hptr(f, name, "f"),
+                                     _hptr(Q, name, "Q"), n, _stream(stream)))
     return Q
 
 

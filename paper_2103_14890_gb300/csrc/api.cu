@@ -410,6 +410,33 @@ int check_imex_args(const bz_modes *m, int scheme, int model, double dt, double 
     return BZ_OK;
 }
 
+// ---- host-buffer entry point --------------------------------------------
+// Copy streams per device (non-blocking, created on first use).
+cudaStream_t g_copy_streams[kMaxDevices][2];
+bool g_copy_ok[kMaxDevices];
+
+int copy_streams(int dev, cudaStream_t out[2]) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_copy_ok[dev]) {
+        for (int i = 0; i < 2; ++i) {
+            cudaError_t e = cudaStreamCreateWithFlags(&g_copy_streams[dev][i], cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "collide_batch_host: copy stream");
+        }
+        g_copy_ok[dev] = true;
+    }
+    out[0] = g_copy_streams[dev][0];
+    out[1] = g_copy_streams[dev][1];
+    return BZ_OK;
+}
+
+// Cells per pipeline stage of collide_batch_host: one wave of 32-cell CTAs of
+// the mode-sum kernel (one per SM), so that no chunk leaves SMs idle at its end.
+int64_t host_chunk_cells(int dev) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 128;
+    return (int64_t)sms * 32;
+}
+
 }  // namespace
 
 int *device_error_word() {
@@ -466,6 +493,84 @@ int collide_batch(const bz_modes *m, int precision, int flags, const void *f, vo
         if (rc) return rc;
     }
     return collide_chain(m, precision, flags, f, Q, nullptr, n_cells, st);
+}
+
+int collide_batch_host(const bz_modes *m, int precision, int flags, const void *f_host, void *Q_host,
+                       int64_t n_cells, void *stream) {
+    int rc = check_modes(m, precision, "collide_batch_host");
+    if (rc) return rc;
+    if (n_cells < 0) return fail(BZ_EINVAL, "collide_batch_host: n_cells < 0");
+    if (n_cells == 0) return BZ_OK;
+    if (!f_host || !Q_host) return fail(BZ_EINVAL, "collide_batch_host: f or Q is NULL");
+    if (flags & ~(BZ_CONSERVE | BZ_CHECK_INPUT)) return fail(BZ_EINVAL, "collide_batch_host: unknown flag");
+    DeviceGuard dg(m->g->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return fail(BZ_EINVAL, "collide_batch_host: not available inside a stream capture");
+    const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
+    const size_t cell_bytes = (size_t)m->g->v.nv * es;
+    const int64_t chunk = std::min(n_cells, host_chunk_cells(m->g->device));
+    const int64_t nchunks = (n_cells + chunk - 1) / chunk;
+    cudaStream_t cp[2];
+    if ((rc = copy_streams(m->g->device, cp))) return rc;
+    cudaStream_t s_in = cp[0], s_out = cp[1];
+    // two device slots of (f, Q) chunks, from the pool on the caller's stream
+    Scratch buf;
+    BZ_TRY(buf.alloc(4 * chunk * cell_bytes, st), "collide_batch_host: chunk buffers");
+    char *fd[2], *qd[2];
+    for (int i = 0; i < 2; ++i) {
+        fd[i] = static_cast<char *>(buf.p) + (size_t)(2 * i) * chunk * cell_bytes;
+        qd[i] = static_cast<char *>(buf.p) + (size_t)(2 * i + 1) * chunk * cell_bytes;
+    }
+    // events: ready (buffers allocated), in[i] (f chunk copied), done[i]
+    // (collision of slot i finished: f slot free, Q slot ready), out[i] (Q
+    // slot copied back: free)
+    cudaEvent_t ev[7] = {};
+    for (int i = 0; i < 7; ++i) {
+        cudaError_t e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (int q = 0; q < i; ++q) cudaEventDestroy(ev[q]);
+            return cuda_fail(e, "collide_batch_host: events");
+        }
+    }
+    cudaEvent_t ready = ev[0], in[2] = {ev[1], ev[2]}, done[2] = {ev[3], ev[4]}, out[2] = {ev[5], ev[6]};
+    auto run = [&]() -> int {
+        BZ_TRY(cudaEventRecord(ready, st), "collide_batch_host: record");
+        BZ_TRY(cudaStreamWaitEvent(s_in, ready, 0), "collide_batch_host: wait");
+        BZ_TRY(cudaStreamWaitEvent(s_out, ready, 0), "collide_batch_host: wait");
+        for (int64_t c = 0; c < nchunks; ++c) {
+            const int i = (int)(c & 1);
+            const int64_t off = c * chunk, nc = std::min(chunk, n_cells - off);
+            const size_t bytes = (size_t)nc * cell_bytes;
+            if (c >= 2) BZ_TRY(cudaStreamWaitEvent(s_in, done[i], 0), "collide_batch_host: wait");
+            BZ_TRY(cudaMemcpyAsync(fd[i], static_cast<const char *>(f_host) + (size_t)off * cell_bytes, bytes,
+                                   cudaMemcpyHostToDevice, s_in),
+                   "collide_batch_host: host to device copy");
+            BZ_TRY(cudaEventRecord(in[i], s_in), "collide_batch_host: record");
+            BZ_TRY(cudaStreamWaitEvent(st, in[i], 0), "collide_batch_host: wait");
+            if (c >= 2) BZ_TRY(cudaStreamWaitEvent(st, out[i], 0), "collide_batch_host: wait");
+            if (flags & BZ_CHECK_INPUT) {
+                int r2 = check_input(precision, fd[i], nc * m->g->v.nv, st);
+                if (r2) return r2;
+            }
+            int r2 = collide_chain(m, precision, flags, fd[i], qd[i], nullptr, nc, st);
+            if (r2) return r2;
+            BZ_TRY(cudaEventRecord(done[i], st), "collide_batch_host: record");
+            BZ_TRY(cudaStreamWaitEvent(s_out, done[i], 0), "collide_batch_host: wait");
+            BZ_TRY(cudaMemcpyAsync(static_cast<char *>(Q_host) + (size_t)off * cell_bytes, qd[i], bytes,
+                                   cudaMemcpyDeviceToHost, s_out),
+                   "collide_batch_host: device to host copy");
+            BZ_TRY(cudaEventRecord(out[i], s_out), "collide_batch_host: record");
+        }
+        // the caller's stream completes after the last copies back; then the
+        // chunk buffers return to the pool in its order
+        for (int i = 0; i < 2 && i < nchunks; ++i) BZ_TRY(cudaStreamWaitEvent(st, out[i], 0), "collide_batch_host: wait");
+        return BZ_OK;
+    };
+    rc = run();
+    for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+    return rc;
 }
 
 int imex_stage_local(const bz_modes *m, int scheme, int stage, int model, double dt, double eps,
