@@ -29,7 +29,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop 
 # DRAM bytes (read + write) of one modesum32_kernel launch (variant 1) on the
 # 65536-cell workload, from one ncu capture of dram__bytes_read.sum and
 # dram__bytes_write.sum; reported only for that workload and variant.
-MODESUM_TRAFFIC_65536 = None
+MODESUM_TRAFFIC_65536 = 260825856 + 209953024
 METRIC = "cell-collision evals/s at N_v=32^2: mixed-precision vs FP64 GPU, rel-L2 err stated"
 WORKLOAD = "65536 cells, 2-D 32x32 velocity grid on [-10,10]^2, VHS kernel, shifted Maxwellians Mach 0-3"
 
