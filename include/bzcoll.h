@@ -105,9 +105,11 @@ int init_velocity_grid(int dim, int n_per_dim, double half_width_L, bz_grid **ou
  * and keeps the fastest.  The choice is cached in the process and, if the
  * environment variable BZ_TUNE_CACHE names a writable file, appended there as
  * lines "dim N sms variant" and read back by later processes.
- * BZ_MODESUM_VARIANT=1, 2 or 3 fixes the variant without timing (ignored if
- * that variant does not fit the grid).  The call synchronises the current
- * device.
+ * BZ_MODESUM_VARIANT=1, 2, 3 or 4 fixes the variant without timing (ignored
+ * if that variant does not fit the grid).  With a 32-cell variant chosen by
+ * timing, collide calls run the whole waves of CTAs on it and the last partial
+ * wave on the 16-cell variant (a second launch); a fixed variant runs every
+ * tile.  The call synchronises the current device.
  *   g          : grid handle (not consumed; must outlive the modes handle)
  *   gamma      : 0 = Maxwell molecules, 1 = hard spheres (VHS); 0 <= gamma <= 2
  *   b0         : kernel constant; <= 0 selects 1/(2 pi) in 2-D, 1/(4 pi) in 3-D

@@ -60,6 +60,7 @@ struct bz_modes {
     int *var_task[kModesumVariants];
     int var_rowmax[kModesumVariants];
     int variant;          // index of the selected variant
+    int variant_fixed;    // 1: chosen by BZ_MODESUM_VARIANT (no last-wave split)
     int modesum_variant;  // variant id reported to callers (index + 1; 0: generic kernel)
     float *d_W32;
     int w32_rowmax;       // largest staged weight row (floats)
@@ -121,6 +122,9 @@ struct Mode32Group {
 };
 bool modesum32_available(const bz_modes *m);
 cudaError_t launch_modesum32(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st);
+int64_t modesum32_split(const bz_modes *m, int64_t n, int *tail_v);
+cudaError_t launch_modesum32_part(const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n,
+                                  cudaStream_t st);
 cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *const *fhat, float2 *const *Qhat,
                                    const int64_t *n, int count, cudaStream_t st);
 

@@ -462,8 +462,38 @@ static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, 
     return launch_group(gd, v, smem_bytes(m->g->v, m->var_rowmax[v], v), st);
 }
 
+static int sm_count();
+
+// A launch over n cells ends with a partial wave of 32-cell CTAs; the SMs that
+// run one CTA fewer idle meanwhile.  When the 16-cell variant fits the grid,
+// the whole waves run on the selected variant and the remaining tiles on the
+// 16-cell one (twice the CTAs, each half as long).  Returns the cells of the
+// main part and sets *tail_v to the tail's variant (-1: no split).
+int64_t modesum32_split(const bz_modes *m, int64_t n, int *tail_v) {
+    *tail_v = -1;
+    if (m->variant_fixed || kVariants[m->variant].cells != 32 || !m->var_W[2]) return n;
+    const int64_t sms = sm_count();
+    const int64_t ntiles = (n + 31) / 32, full = (ntiles / sms) * sms;
+    if (full == ntiles) return n;
+    *tail_v = 2;
+    return full * 32;
+}
+
+cudaError_t launch_modesum32_part(const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n,
+                                  cudaStream_t st) {
+    return launch_variant(m, v, fhat, Qhat, n, st);
+}
+
 cudaError_t launch_modesum32(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
-    return launch_variant(m, m->variant, fhat, Qhat, n, st);
+    int tv = -1;
+    const int64_t nm = modesum32_split(m, n, &tv);
+    cudaError_t e = cudaSuccess;
+    if (nm > 0) e = launch_variant(m, m->variant, fhat, Qhat, nm, st);
+    if (e == cudaSuccess && tv >= 0 && n > nm) {
+        const size_t off = (size_t)(nm / 32) * m->g->v.nhalf * 32;   // whole 32-cell tiles
+        e = launch_variant(m, tv, fhat + off, Qhat + off, n - nm, st);
+    }
+    return e;
 }
 
 // Heterogeneous instances in one launch; all items must use the same kernel
@@ -592,6 +622,7 @@ int modes_build_fp32_tables(bz_modes *m) {
     m->d_W32 = nullptr;
     m->d_task = nullptr;
     m->variant = 0;
+    m->variant_fixed = 0;
     m->modesum_variant = 0;
     int rc = BZ_OK;
     bool any = false;
@@ -609,6 +640,7 @@ int modes_build_fp32_tables(bz_modes *m) {
         const int id = atoi(force) - 1;
         if (id >= 0 && id < kNumVariants && m->var_W[id]) v = id;
     }
+    m->variant_fixed = v >= 0;      // a fixed variant also serves the last partial wave
     if (v < 0) v = autotune(m, rc);
     if (rc) return rc;
     m->variant = v;

@@ -83,6 +83,30 @@ def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, dim, N, variant):
     assert relerr(Q.double().cpu().numpy(), Qr) < TOL32
 
 
+def test_last_wave_split_is_exact(bz, monkeypatch):
+    """With a timed 32-cell variant, whole waves of CTAs run on it and the last
+    partial wave on the 16-cell variant: every cell must equal a run of the
+    corresponding variant alone (cells are independent)."""
+    import torch
+    N, L = 32, 10.0
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = sms * 32 + 70
+    f = workloads.bi_maxwellian(n, 2, N, L, seed=1500)
+    m = bz.Modes(bz.Grid(2, N, L), 1.0)
+    if m.modesum_variant not in (1, 2):
+        pytest.skip("timed variant is not a 32-cell one")
+    Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32").cpu().numpy()
+    monkeypatch.setenv("BZ_MODESUM_VARIANT", str(m.modesum_variant))
+    m_main = bz.Modes(bz.Grid(2, N, L), 1.0)
+    monkeypatch.setenv("BZ_MODESUM_VARIANT", "3")
+    m_tail = bz.Modes(bz.Grid(2, N, L), 1.0)
+    Qa = bz.collide_batch(m_main, to_dev(f[:sms * 32], "fp32"), precision="fp32").cpu().numpy()
+    Qb = bz.collide_batch(m_tail, to_dev(f[sms * 32:], "fp32"), precision="fp32").cpu().numpy()
+    bz.check()
+    assert np.array_equal(Q[:sms * 32], Qa)
+    assert np.array_equal(Q[sms * 32:], Qb)
+
+
 @pytest.mark.parametrize("n", [1, 8, 13])
 def test_fp32_3d_16_grid_8_cell_tiles(bz, oracle_k, n):
     """16^3 grid on [-10,10]^3 (register-blocked 3-D path, 8-cell tiles): one
