@@ -98,21 +98,19 @@ __device__ __forceinline__ void stage_row(float *dst, const float *src, int nflo
 // register array used under two alternating namings (PH = 0, 1): logical slot
 // j is physical slot (j + PH R) mod 2R, so moving the window by R between
 // blocks costs no register moves.  Columns are CS elements apart; f-hat_l is
-// read at lp, lp + ldir, ... with ldir = +-CS (columns +-1); for l_1 < 0 the
-// row is that of -l_1 read backwards and conjugated (sg = -1).  The weights
-// of step s are wb[s * WS + r].  Only two instances of this body exist per
-// variant, which keeps the unrolled code inside the instruction cache.
-template <int RR, int CS, int WS, int PH>
+// read at lp, lp + DIR CS, ...: for DIR = -1 (l_1 < 0) the row is that of -l_1
+// read backwards and f-hat_l = conj of the value read, which only flips the
+// signs of two FMA operands.  The weights of step s are wb[s * WS + r].  Four
+// instances of this body exist per variant (PH x DIR); one row uses two.
+template <int RR, int CS, int WS, int PH, int DIR>
 __device__ __forceinline__ void block_pass(float2 (&win)[2 * RR], const float2 *__restrict__ mp,
-                                           const float2 *__restrict__ lp, int ldir, float sg,
-                                           const float *__restrict__ wb, float2 (&acc)[RR]) {
+                                           const float2 *__restrict__ lp, const float *__restrict__ wb,
+                                           float2 (&acc)[RR]) {
 #pragma unroll
     for (int j = 0; j < RR; ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
 #pragma unroll
     for (int s = 0; s < RR; ++s) {
-        float2 fl = *lp;
-        lp += ldir;
-        fl.y *= sg;
+        const float2 fl = lp[s * DIR * CS];
         float wv[RR];
 #pragma unroll
         for (int q = 0; q < RR; q += 4) {
@@ -125,38 +123,43 @@ __device__ __forceinline__ void block_pass(float2 (&win)[2 * RR], const float2 *
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
             const float2 b = win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)];
-            const float tx = wv[r] * fl.x, ty = wv[r] * fl.y;   // weight * f-hat_l
-            acc[r].x = fmaf(tx, b.x, acc[r].x);
-            acc[r].x = fmaf(-ty, b.y, acc[r].x);
-            acc[r].y = fmaf(tx, b.y, acc[r].y);
-            acc[r].y = fmaf(ty, b.x, acc[r].y);
+            const float tx = wv[r] * fl.x, ty = wv[r] * fl.y;   // weight * value read
+            if (DIR > 0) {                                      // acc += w f-hat_l b
+                acc[r].x = fmaf(tx, b.x, acc[r].x);
+                acc[r].x = fmaf(-ty, b.y, acc[r].x);
+                acc[r].y = fmaf(tx, b.y, acc[r].y);
+                acc[r].y = fmaf(ty, b.x, acc[r].y);
+            } else {                                            // acc += w conj(value) b
+                acc[r].x = fmaf(tx, b.x, acc[r].x);
+                acc[r].x = fmaf(ty, b.y, acc[r].x);
+                acc[r].y = fmaf(tx, b.y, acc[r].y);
+                acc[r].y = fmaf(-ty, b.x, acc[r].y);
+            }
         }
     }
 }
 
-// One l_1 row of a task for this thread's R outputs:
+// One row pair of a task for this thread's R outputs:
 // acc[r] += sum_l2 w(l2, r) f-hat_l(l2) f-hat_m(k2_0 + r - l2).
-// rowl / rowm point at column 0 of the rows |l_1| and m_1 (this thread's cell);
-// wrow at this thread's first weight of the row.
-template <int RR, int CS, int WS>
-__device__ __forceinline__ void row_pass(const float2 *__restrict__ rowl, int dir,
-                                         const float2 *__restrict__ rowm, const float *__restrict__ wrow,
-                                         int nblk, int l2lo, int mbase0, float2 (&acc)[RR]) {
+// rowl / rowm point at column 0 of the rows of l (or -l) and m (this thread's
+// cell); wrow at this thread's first weight of the row.
+template <int RR, int CS, int WS, int DIR>
+__device__ __forceinline__ void row_pass(const float2 *__restrict__ rowl, const float2 *__restrict__ rowm,
+                                         const float *__restrict__ wrow, int nblk, int l2lo, int mbase0,
+                                         float2 (&acc)[RR]) {
     float2 win[2 * RR];
     const float2 *mp = rowm + mbase0 * CS;
-    const float2 *lp = rowl + dir * l2lo * CS;
-    const int ldir = dir * CS;
-    const float sg = (float)dir;
+    const float2 *lp = rowl + DIR * l2lo * CS;
 #pragma unroll
     for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * CS];
     int blk = 0;
     for (; blk + 1 < nblk; blk += 2) {
-        block_pass<RR, CS, WS, 0>(win, mp, lp, ldir, sg, wrow + blk * RR * WS, acc);
-        block_pass<RR, CS, WS, 1>(win, mp - RR * CS, lp + RR * ldir, ldir, sg, wrow + (blk + 1) * RR * WS, acc);
+        block_pass<RR, CS, WS, 0, DIR>(win, mp, lp, wrow + blk * RR * WS, acc);
+        block_pass<RR, CS, WS, 1, DIR>(win, mp - RR * CS, lp + RR * DIR * CS, wrow + (blk + 1) * RR * WS, acc);
         mp -= 2 * RR * CS;
-        lp += 2 * RR * ldir;
+        lp += 2 * RR * DIR * CS;
     }
-    if (blk < nblk) block_pass<RR, CS, WS, 0>(win, mp, lp, ldir, sg, wrow + blk * RR * WS, acc);
+    if (blk < nblk) block_pass<RR, CS, WS, 0, DIR>(win, mp, lp, wrow + blk * RR * WS, acc);
 }
 
 template <int RR, int WARPS, int CELLS>
@@ -220,8 +223,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
             // row header: element offsets of the rows of l and m, and the
             // direction of l (-1: f-hat_l = conj(f-hat_{-l}), row of -l read backwards)
             const int4 hd = *reinterpret_cast<const int4 *>(wcur);
-            row_pass<RR, CELLS, RT>(F0 + hd.x, hd.z, F0 + hd.y, wcur + kRowHead + grp * RR, tk.nblk * G, tk.l2lo,
-                                    mbase0, acc);
+            if (hd.z > 0)
+                row_pass<RR, CELLS, RT, 1>(F0 + hd.x, F0 + hd.y, wcur + kRowHead + grp * RR, tk.nblk * G, tk.l2lo,
+                                           mbase0, acc);
+            else
+                row_pass<RR, CELLS, RT, -1>(F0 + hd.x, F0 + hd.y, wcur + kRowHead + grp * RR, tk.nblk * G,
+                                            tk.l2lo, mbase0, acc);
             __syncwarp();
             // fold the FP32 row sums (<= 4 rows) into (hi, lo)
             if ((i & 3) == 3 || i + 1 == tk.nrows) {
