@@ -214,8 +214,12 @@ int phase_forward(const bz_modes *m, int precision, const void *f, void *fh, int
 
 int phase_modesum(const bz_modes *m, int precision, const void *fh, void *qh, int64_t n, cudaStream_t st) {
     const GridView &v = m->g->v;
-    if (precision == BZ_FP64) {
+    if (precision == BZ_FP64 && modesum64_available(m)) {
         BZ_LAUNCH("modesum_f64", st,
+                  launch_modesum64(m, static_cast<const double2 *>(fh), static_cast<double2 *>(qh), n, st),
+                  "collide: mode sum");
+    } else if (precision == BZ_FP64) {
+        BZ_LAUNCH("modesum_f64_generic", st,
                   launch_modesum_generic_f64(v, m->d_F64, m->bcols, static_cast<const double2 *>(fh),
                                              static_cast<double2 *>(qh), n, st),
                   "collide: mode sum");

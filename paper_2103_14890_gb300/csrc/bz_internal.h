@@ -61,6 +61,9 @@ struct bz_modes {
     int var_rowmax[kModesumVariants];
     int variant;          // index of the selected variant
     int variant_fixed;    // 1: chosen by BZ_MODESUM_VARIANT (no last-wave split)
+    void *w64;            // FP64 weight stream and task table (16-cell tiles), null if unused
+    int *task64;
+    int rowmax64;
     int modesum_variant;  // variant id reported to callers (index + 1; 0: generic kernel)
     float *d_W32;
     int w32_rowmax;       // largest staged weight row (floats)
@@ -108,9 +111,9 @@ cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *Qhat, flo
 // ---- register-blocked FP32 2-D mode sum (k_modesum32.cu) --------------------
 constexpr int kMaxGroup = 16;      // instances per grouped launch
 struct Mode32Item {
-    const float2 *fhat;
-    float2 *Qhat;
-    const float *W;
+    const void *fhat;     // float2 or double2 spectra, tiled layout
+    void *Qhat;
+    const void *W;        // weight stream of the kernel's scalar type
     const int *tasks;
     int h, M, nhalf, wrow_max;
     int64_t n;
@@ -123,6 +126,8 @@ struct Mode32Group {
 bool modesum32_available(const bz_modes *m);
 cudaError_t launch_modesum32(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st);
 int64_t modesum32_split(const bz_modes *m, int64_t n, int *tail_v);
+bool modesum64_available(const bz_modes *m);
+cudaError_t launch_modesum64(const bz_modes *m, const double2 *fhat, double2 *Qhat, int64_t n, cudaStream_t st);
 cudaError_t launch_modesum32_part(const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n,
                                   cudaStream_t st);
 cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *const *fhat, float2 *const *Qhat,

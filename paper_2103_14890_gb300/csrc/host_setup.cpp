@@ -260,6 +260,8 @@ void modes_destroy(bz_modes *m) {
     if (!m) return;
     cudaFree(m->d_F64);
     cudaFree(m->d_F32);
+    cudaFree(m->w64);
+    cudaFree(m->task64);
     for (int v = 0; v < kModesumVariants; ++v) {
         cudaFree(m->var_W[v]);
         cudaFree(m->var_task[v]);

@@ -154,10 +154,11 @@ __global__ void __launch_bounds__(256) imex_stage2d_kernel(GridView g, StageCoef
     const double theta = (2.0 * E / rho - (u1 * u1 + u2 * u2)) / 2.0;
     const double pref = rho / (2.0 * M_PI * theta);
     const double inv2t = 0.5 / theta;
-    // separable Maxwellian: this lane's column factor and row factor j1 = lane
+    // separable Maxwellian: this lane's column factor and row factor j1 = lane;
+    // exponents in FP64, the exponential in the state precision
     const double d2 = vv - u2, d1 = (-g.L + lane * g.dv) - u1;
-    const T fcol = (T)(pref * exp(-d2 * d2 * inv2t));
-    const T frow_l = (T)exp(-d1 * d1 * inv2t);
+    const T fcol = (T)pref * exp((T)(-d2 * d2 * inv2t));
+    const T frow_l = exp((T)(-d1 * d1 * inv2t));
     const double cc = c.dt * c.all * rho / c.eps;
     const T cT = (T)cc, denom = (T)(1.0 / (1.0 + cc)), rhoT = (T)rho;
     T *Fo = F + base;

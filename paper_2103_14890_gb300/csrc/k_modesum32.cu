@@ -65,11 +65,11 @@ constexpr Variant kVariants[kNumVariants] = {{8, 16, 32}, {4, 32, 32}, {4, 16, 1
 constexpr int kTaskInts = 12;   // ints per task record
 
 constexpr int kPad = 8;         // zero guard columns before the first and after the last row
-constexpr int kRowHead = 4;     // floats of row-pair header in front of each weight row (16 bytes)
+constexpr int kRowHeadBytes = 16;   // row-pair header in front of each weight row
 
 struct TaskRec {
     int orow, k20, nrows, l2lo, nblk, woff, rfirst;   // rfirst: first r (of RT) this task stores
-    int rowf, pad0, pad1, pad2, pad3;                 // rowf: floats per row pair (header + weights)
+    int rowf, pad0, pad1, pad2, pad3;                 // rowf: elements per row pair (header + weights)
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -82,16 +82,34 @@ template <int NPENDING> __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Knuth's TwoSum: s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+template <typename T> __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
     s = a + b;
-    float bb = s - a;
+    T bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
 
-// Stage `nfloat` floats (multiple of 4) of a weight row into shared memory.
-__device__ __forceinline__ void stage_row(float *dst, const float *src, int nfloat, int lane) {
-    for (int i = lane * 4; i < nfloat; i += 128) cp_async16(dst + i, src + i);
+// Stage `nbytes` bytes (multiple of 16) of a weight row into shared memory.
+__device__ __forceinline__ void stage_row(void *dst, const void *src, int nbytes, int lane) {
+    char *d = static_cast<char *>(dst);
+    const char *g = static_cast<const char *>(src);
+    for (int i = lane * 16; i < nbytes; i += 512) cp_async16(d + i, g + i);
     cp_async_commit();
+}
+
+// R consecutive weights (16-byte aligned) into registers.
+__device__ __forceinline__ void load_w4(float *wv, const float *p) {
+    const float4 w4 = *reinterpret_cast<const float4 *>(p);
+    wv[0] = w4.x;
+    wv[1] = w4.y;
+    wv[2] = w4.z;
+    wv[3] = w4.w;
+}
+__device__ __forceinline__ void load_w4(double *wv, const double *p) {
+    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    wv[0] = a.x;
+    wv[1] = a.y;
+    wv[2] = b.x;
+    wv[3] = b.y;
 }
 
 // One block of R l_2 steps.  The window of f-hat_m values lives in a 2R-slot
@@ -102,38 +120,34 @@ __device__ __forceinline__ void stage_row(float *dst, const float *src, int nflo
 // read backwards and f-hat_l = conj of the value read, which only flips the
 // signs of two FMA operands.  The weights of step s are wb[s * WS + r].  Four
 // instances of this body exist per variant (PH x DIR); one row uses two.
-template <int RR, int CS, int WS, int PH, int DIR>
-__device__ __forceinline__ void block_pass(float2 (&win)[2 * RR], const float2 *__restrict__ mp,
-                                           const float2 *__restrict__ lp, const float *__restrict__ wb,
-                                           float2 (&acc)[RR]) {
+template <typename T, int RR, int CS, int WS, int PH, int DIR>
+__device__ __forceinline__ void block_pass(typename C2<T>::type (&win)[2 * RR],
+                                           const typename C2<T>::type *__restrict__ mp,
+                                           const typename C2<T>::type *__restrict__ lp, const T *__restrict__ wb,
+                                           typename C2<T>::type (&acc)[RR]) {
+    using V2 = typename C2<T>::type;
 #pragma unroll
     for (int j = 0; j < RR; ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
 #pragma unroll
     for (int s = 0; s < RR; ++s) {
-        const float2 fl = lp[s * DIR * CS];
-        float wv[RR];
+        const V2 fl = lp[s * DIR * CS];
+        T wv[RR];
 #pragma unroll
-        for (int q = 0; q < RR; q += 4) {
-            const float4 w4 = *reinterpret_cast<const float4 *>(wb + s * WS + q);
-            wv[q] = w4.x;
-            wv[q + 1] = w4.y;
-            wv[q + 2] = w4.z;
-            wv[q + 3] = w4.w;
-        }
+        for (int q = 0; q < RR; q += 4) load_w4(wv + q, wb + s * WS + q);
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
-            const float2 b = win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)];
-            const float tx = wv[r] * fl.x, ty = wv[r] * fl.y;   // weight * value read
+            const V2 b = win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)];
+            const T tx = wv[r] * fl.x, ty = wv[r] * fl.y;       // weight * value read
             if (DIR > 0) {                                      // acc += w f-hat_l b
-                acc[r].x = fmaf(tx, b.x, acc[r].x);
-                acc[r].x = fmaf(-ty, b.y, acc[r].x);
-                acc[r].y = fmaf(tx, b.y, acc[r].y);
-                acc[r].y = fmaf(ty, b.x, acc[r].y);
+                acc[r].x = fma(tx, b.x, acc[r].x);
+                acc[r].x = fma(-ty, b.y, acc[r].x);
+                acc[r].y = fma(tx, b.y, acc[r].y);
+                acc[r].y = fma(ty, b.x, acc[r].y);
             } else {                                            // acc += w conj(value) b
-                acc[r].x = fmaf(tx, b.x, acc[r].x);
-                acc[r].x = fmaf(ty, b.y, acc[r].x);
-                acc[r].y = fmaf(tx, b.y, acc[r].y);
-                acc[r].y = fmaf(-ty, b.x, acc[r].y);
+                acc[r].x = fma(tx, b.x, acc[r].x);
+                acc[r].x = fma(ty, b.y, acc[r].x);
+                acc[r].y = fma(tx, b.y, acc[r].y);
+                acc[r].y = fma(-ty, b.x, acc[r].y);
             }
         }
     }
@@ -143,78 +157,82 @@ __device__ __forceinline__ void block_pass(float2 (&win)[2 * RR], const float2 *
 // acc[r] += sum_l2 w(l2, r) f-hat_l(l2) f-hat_m(k2_0 + r - l2).
 // rowl / rowm point at column 0 of the rows of l (or -l) and m (this thread's
 // cell); wrow at this thread's first weight of the row.
-template <int RR, int CS, int WS, int DIR>
-__device__ __forceinline__ void row_pass(const float2 *__restrict__ rowl, const float2 *__restrict__ rowm,
-                                         const float *__restrict__ wrow, int nblk, int l2lo, int mbase0,
-                                         float2 (&acc)[RR]) {
-    float2 win[2 * RR];
-    const float2 *mp = rowm + mbase0 * CS;
-    const float2 *lp = rowl + DIR * l2lo * CS;
+template <typename T, int RR, int CS, int WS, int DIR>
+__device__ __forceinline__ void row_pass(const typename C2<T>::type *__restrict__ rowl,
+                                         const typename C2<T>::type *__restrict__ rowm, const T *__restrict__ wrow,
+                                         int nblk, int l2lo, int mbase0, typename C2<T>::type (&acc)[RR]) {
+    using V2 = typename C2<T>::type;
+    V2 win[2 * RR];
+    const V2 *mp = rowm + mbase0 * CS;
+    const V2 *lp = rowl + DIR * l2lo * CS;
 #pragma unroll
     for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * CS];
     int blk = 0;
     for (; blk + 1 < nblk; blk += 2) {
-        block_pass<RR, CS, WS, 0, DIR>(win, mp, lp, wrow + blk * RR * WS, acc);
-        block_pass<RR, CS, WS, 1, DIR>(win, mp - RR * CS, lp + RR * DIR * CS, wrow + (blk + 1) * RR * WS, acc);
+        block_pass<T, RR, CS, WS, 0, DIR>(win, mp, lp, wrow + blk * RR * WS, acc);
+        block_pass<T, RR, CS, WS, 1, DIR>(win, mp - RR * CS, lp + RR * DIR * CS, wrow + (blk + 1) * RR * WS, acc);
         mp -= 2 * RR * CS;
         lp += 2 * RR * DIR * CS;
     }
-    if (blk < nblk) block_pass<RR, CS, WS, 0, DIR>(win, mp, lp, wrow + blk * RR * WS, acc);
+    if (blk < nblk) block_pass<T, RR, CS, WS, 0, DIR>(win, mp, lp, wrow + blk * RR * WS, acc);
 }
 
-template <int RR, int WARPS, int CELLS>
+template <typename T, int RR, int WARPS, int CELLS>
 __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Group gd) {
+    using V2 = typename C2<T>::type;
     constexpr int G = 32 / CELLS;     // lane groups splitting a task's outputs
     constexpr int RT = RR * G;        // outputs per task
-    extern __shared__ __align__(16) float4 smem4[];
+    constexpr int HEAD = kRowHeadBytes / (int)sizeof(T);
+    extern __shared__ __align__(16) uint4 smem16[];
     // this CTA's instance and tile (instances are ordered longest-first)
     int it = 0;
     while (it + 1 < gd.nitems && (int64_t)blockIdx.x >= gd.tile_start[it + 1]) ++it;
     const Mode32Item &ip = gd.item[it];
-    const float2 *__restrict__ fhat = ip.fhat;
-    float2 *__restrict__ Qhat = ip.Qhat;
-    const float *__restrict__ W = ip.W;
+    const V2 *__restrict__ fhat = static_cast<const V2 *>(ip.fhat);
+    V2 *__restrict__ Qhat = static_cast<V2 *>(ip.Qhat);
+    const T *__restrict__ W = static_cast<const T *>(ip.W);
     const int *__restrict__ tasks = ip.tasks;
     const int h = ip.h, M = ip.M, nhalf = ip.nhalf, wrow_max = ip.wrow_max;
     const int64_t n = ip.n;
     const int64_t cta = (int64_t)blockIdx.x - gd.tile_start[it];
     const int64_t tile = cta / G;                                    // 32-cell tile of the scratch layout
     const int sub = (int)(cta % G);                                  // which CELLS-cell part of it
-    float2 *Fs = reinterpret_cast<float2 *>(smem4);                  // [kPad + nhalf + kPad][CELLS]
-    float *wsm = reinterpret_cast<float *>(Fs + (size_t)(nhalf + 2 * kPad) * CELLS);   // [warps][2][wrow_max]
+    V2 *Fs = reinterpret_cast<V2 *>(smem16);                         // [kPad + nhalf + kPad][CELLS]
+    T *wsm = reinterpret_cast<T *>(Fs + (size_t)(nhalf + 2 * kPad) * CELLS);   // [warps][2][wrow_max]
     {
         // copy this CTA's cells of the tile's half spectrum, zero the guards
-        constexpr int Q4 = CELLS / 2;                                // float4 per mode
-        const float4 *src = reinterpret_cast<const float4 *>(fhat + tile * (int64_t)nhalf * 32) + sub * Q4;
+        constexpr int VEC = 16 / (int)sizeof(V2);                    // cells per 16-byte vector
+        constexpr int Q4 = CELLS / VEC, ROW = 32 / VEC;              // vectors per mode: this CTA, whole tile
+        const uint4 *src = reinterpret_cast<const uint4 *>(fhat + tile * (int64_t)nhalf * 32) + sub * Q4;
         const int body = nhalf * Q4, guard = kPad * Q4;
         for (int i = threadIdx.x; i < body + 2 * guard; i += blockDim.x) {
             const int b = i - guard;
-            smem4[i] = (b >= 0 && b < body) ? src[(b / Q4) * 16 + (b % Q4)] : make_float4(0.f, 0.f, 0.f, 0.f);
+            smem16[i] = (b >= 0 && b < body) ? src[(b / Q4) * ROW + (b % Q4)] : make_uint4(0u, 0u, 0u, 0u);
         }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cell = lane % CELLS, grp = lane / CELLS;
-    float *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
-    float *wbuf1 = wbuf0 + wrow_max;
+    T *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
+    T *wbuf1 = wbuf0 + wrow_max;
     const int tbeg = tasks[warp], tend = tasks[warp + 1];
     const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS + 1);
-    const float2 *F0 = Fs + (size_t)(kPad + h) * CELLS + cell;      // (row 0, column 0) of this cell
+    const V2 *F0 = Fs + (size_t)(kPad + h) * CELLS + cell;          // (row 0, column 0) of this cell
 
     for (int t = tbeg; t < tend; ++t) {
         const TaskRec tk = trec[t];
-        const int rowf = tk.rowf;                         // floats per l_1 row
-        const float *wsrc = W + tk.woff;
-        float2 hi[RR], lo[RR], acc[RR];
+        const int rowf = tk.rowf;                         // elements per row pair
+        const T *wsrc = W + tk.woff;
+        V2 hi[RR], lo[RR], acc[RR];
 #pragma unroll
-        for (int r = 0; r < RR; ++r) hi[r] = lo[r] = acc[r] = make_float2(0.f, 0.f);
+        for (int r = 0; r < RR; ++r) hi[r] = lo[r] = acc[r] = cmk<V2>(0, 0);
         const int k20 = tk.k20 + grp * RR;                // this thread's first output column
         const int mbase0 = k20 - tk.l2lo - (RR - 1);
-        stage_row(wbuf0, wsrc, rowf, lane);
+        stage_row(wbuf0, wsrc, rowf * (int)sizeof(T), lane);
         for (int i = 0; i < tk.nrows; ++i) {
-            const float *wcur = (i & 1) ? wbuf1 : wbuf0;
+            const T *wcur = (i & 1) ? wbuf1 : wbuf0;
             if (i + 1 < tk.nrows) {
-                stage_row((i & 1) ? wbuf0 : wbuf1, wsrc + (size_t)(i + 1) * rowf, rowf, lane);
+                stage_row((i & 1) ? wbuf0 : wbuf1, wsrc + (size_t)(i + 1) * rowf, rowf * (int)sizeof(T), lane);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
@@ -224,43 +242,43 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
             // direction of l (-1: f-hat_l = conj(f-hat_{-l}), row of -l read backwards)
             const int4 hd = *reinterpret_cast<const int4 *>(wcur);
             if (hd.z > 0)
-                row_pass<RR, CELLS, RT, 1>(F0 + hd.x, F0 + hd.y, wcur + kRowHead + grp * RR, tk.nblk * G, tk.l2lo,
-                                           mbase0, acc);
+                row_pass<T, RR, CELLS, RT, 1>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G, tk.l2lo,
+                                              mbase0, acc);
             else
-                row_pass<RR, CELLS, RT, -1>(F0 + hd.x, F0 + hd.y, wcur + kRowHead + grp * RR, tk.nblk * G,
-                                            tk.l2lo, mbase0, acc);
+                row_pass<T, RR, CELLS, RT, -1>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G,
+                                               tk.l2lo, mbase0, acc);
             __syncwarp();
-            // fold the FP32 row sums (<= 4 rows) into (hi, lo)
+            // fold the row sums (<= 4 rows) into (hi, lo)
             if ((i & 3) == 3 || i + 1 == tk.nrows) {
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
-                    float s, e;
+                    T s, e;
                     two_sum(hi[r].x, acc[r].x, s, e);
                     hi[r].x = s;
                     lo[r].x += e;
                     two_sum(hi[r].y, acc[r].y, s, e);
                     hi[r].y = s;
                     lo[r].y += e;
-                    acc[r] = make_float2(0.f, 0.f);
+                    acc[r] = cmk<V2>(0, 0);
                 }
             }
         }
         const int64_t c = tile * 32 + sub * CELLS + cell;
         if (c < n) {
-            float2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.orow * M * 32 + sub * CELLS + cell;
+            V2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.orow * M * 32 + sub * CELLS + cell;
 #pragma unroll
             for (int r = 0; r < RR; ++r) {
                 const int k2 = k20 + r;
                 if (grp * RR + r >= tk.rfirst && k2 <= h)
-                    out[(k2 + h) * 32] = make_float2(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
+                    out[(k2 + h) * 32] = cmk<V2>(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
             }
         }
     }
 }
 
-size_t smem_bytes(const GridView &g, int wrow_max, int v) {
-    return sizeof(float2) * (size_t)(g.nhalf + 2 * kPad) * kVariants[v].cells +
-           sizeof(float) * (size_t)kVariants[v].warps * 2 * wrow_max;
+template <typename T> size_t smem_bytes(const GridView &g, int wrow_max, int v) {
+    return 2 * sizeof(T) * (size_t)(g.nhalf + 2 * kPad) * kVariants[v].cells +
+           sizeof(T) * (size_t)kVariants[v].warps * 2 * wrow_max;
 }
 
 }  // namespace
@@ -268,10 +286,12 @@ size_t smem_bytes(const GridView &g, int wrow_max, int v) {
 // Host part: weight streams and the task table, built once per modes handle.
 double beta_host(const bz_modes *m, const int *l, const int *mm);
 
-// Weight stream (with row-pair headers) and task table of one variant (slot v); false if
-// the grid is not covered by this variant (another variant or the generic
-// kernel serves it).
-static bool build_variant(bz_modes *m, int v, int &rc) {
+// Weight stream (with row-pair headers) and task table of one variant, with
+// weights of type T; false if the grid is not covered by this variant (another
+// variant or the generic kernel serves it).
+template <typename T>
+static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, int *outRowmax) {
+    constexpr int HEAD = kRowHeadBytes / (int)sizeof(T);
     const int R = kVariants[v].R * (32 / kVariants[v].cells);   // outputs per task (RT)
     const int kWarps = kVariants[v].warps;
     rc = BZ_OK;
@@ -279,11 +299,11 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
     const int d = gv.dim, h = gv.h, M = gv.M;
     if (!((d == 2 && gv.N <= 48) || (d == 3 && gv.N <= 16))) return false;
     // shared memory of the spectrum alone must leave room for the weight buffers
-    if (sizeof(float2) * (size_t)(gv.nhalf + 2 * kPad) * kVariants[v].cells > 200 * 1024) return false;
+    if (2 * sizeof(T) * (size_t)(gv.nhalf + 2 * kPad) * kVariants[v].cells > 200 * 1024) return false;
     const int nb = (M + R - 1) / R;
     const int lo_col = -h - kPad, hi_col = h + kPad;         // addressable columns
     std::vector<TaskRec> tasks;
-    std::vector<float> W;
+    std::vector<T> W;
     std::vector<double> cost;
     const int nmid = (d == 3) ? M : 1;                      // values of the middle index (3-D)
     struct Pair { int l[2], m[2]; };                         // leading indices of l and m
@@ -332,7 +352,7 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
                 t.nblk = nblk;
                 t.woff = (int)W.size();
                 t.rfirst = std::max(0, prev_end + 1 - k20);
-                t.rowf = kRowHead + npad * R;
+                t.rowf = HEAD + npad * R;
                 t.pad0 = t.pad1 = t.pad2 = t.pad3 = 0;
                 prev_end = k2last;
                 for (const Pair &p : pairs) {
@@ -342,12 +362,11 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
                     const int lrow = (d == 3) ? a1 * M + (a2 + h) : a1;
                     const int mrow = (d == 3) ? p.m[0] * M + (p.m[1] + h) : p.m[0];
                     const int cs = kVariants[v].cells;
-                    const int head[kRowHead] = {lrow * M * cs, mrow * M * cs, neg ? -1 : 1, 0};
-                    for (int q = 0; q < kRowHead; ++q) {
-                        float x;
-                        std::memcpy(&x, &head[q], sizeof x);
-                        W.push_back(x);
-                    }
+                    const int head[4] = {lrow * M * cs, mrow * M * cs, neg ? -1 : 1, 0};
+                    static_assert(sizeof head == kRowHeadBytes, "16-byte row header");
+                    T hw[HEAD];
+                    std::memcpy(hw, head, sizeof head);
+                    for (int q = 0; q < HEAD; ++q) W.push_back(hw[q]);
                     for (int j = 0; j < npad; ++j) {
                         const int lz = l2lo + j;
                         for (int r = 0; r < R; ++r) {
@@ -366,7 +385,7 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
                                 w = beta_host(m, l, mm);
                                 if (p.l[0] < p.m[0]) w += beta_host(m, mm, l);
                             }
-                            W.push_back((float)w);
+                            W.push_back((T)w);
                         }
                     }
                 }
@@ -398,56 +417,57 @@ static bool build_variant(bz_modes *m, int v, int &rc) {
     tab[kWarps] = pos;
     int wrow_max = 0;
     for (auto &t : tasks) wrow_max = std::max(wrow_max, t.rowf);   // staging buffer: one row pair
-    if (smem_bytes(gv, wrow_max, v) > 227 * 1024) return false;   // does not fit
-    float *dW = nullptr;
+    if (smem_bytes<T>(gv, wrow_max, v) > 227 * 1024) return false;   // does not fit
+    T *dW = nullptr;
     int *dT = nullptr;
-    cudaError_t e = cudaMalloc(&dW, sizeof(float) * W.size());
+    cudaError_t e = cudaMalloc(&dW, sizeof(T) * W.size());
     if (e == cudaSuccess) e = cudaMalloc(&dT, sizeof(int) * tab.size());
-    if (e == cudaSuccess) e = cudaMemcpy(dW, W.data(), sizeof(float) * W.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dW, W.data(), sizeof(T) * W.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dT, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(dW);
         cudaFree(dT);
-        rc = cuda_fail(e, "build_kernel_modes: FP32 weight stream");
+        rc = cuda_fail(e, "build_kernel_modes: weight stream");
         return false;
     }
-    m->var_W[v] = dW;
-    m->var_task[v] = dT;
-    m->var_rowmax[v] = wrow_max;
+    *outW = dW;
+    *outT = dT;
+    *outRowmax = wrow_max;
     return true;
 }
 
 bool modesum32_available(const bz_modes *m) { return m->d_W32 != nullptr; }
 
-template <int RR, int WARPS, int CELLS>
+template <typename T, int RR, int WARPS, int CELLS>
 static cudaError_t launch_instance(const Mode32Group &gd, size_t sm, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(modesum32_kernel<RR, WARPS, CELLS>,
+    cudaError_t e = cudaFuncSetAttribute(modesum32_kernel<T, RR, WARPS, CELLS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    modesum32_kernel<RR, WARPS, CELLS><<<(unsigned)gd.tile_start[gd.nitems], WARPS * 32, sm, st>>>(gd);
+    modesum32_kernel<T, RR, WARPS, CELLS><<<(unsigned)gd.tile_start[gd.nitems], WARPS * 32, sm, st>>>(gd);
     return cudaGetLastError();
 }
 
 static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStream_t st) {
     switch (v) {
-        case 0: return launch_instance<8, 16, 32>(gd, sm, st);
-        case 1: return launch_instance<4, 32, 32>(gd, sm, st);
-        case 2: return launch_instance<4, 16, 16>(gd, sm, st);
-        case 3: return launch_instance<4, 16, 8>(gd, sm, st);
+        case 0: return launch_instance<float, 8, 16, 32>(gd, sm, st);
+        case 1: return launch_instance<float, 4, 32, 32>(gd, sm, st);
+        case 2: return launch_instance<float, 4, 16, 16>(gd, sm, st);
+        case 3: return launch_instance<float, 4, 16, 8>(gd, sm, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-static void fill_item(Mode32Item &it, const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n) {
+static void fill_item(Mode32Item &it, const bz_modes *m, const void *W, const int *tasks, int rowmax,
+                      const void *fhat, void *Qhat, int64_t n) {
     const GridView &gv = m->g->v;
     it.fhat = fhat;
     it.Qhat = Qhat;
-    it.W = m->var_W[v];
-    it.tasks = m->var_task[v];
+    it.W = W;
+    it.tasks = tasks;
     it.h = gv.h;
     it.M = gv.M;
     it.nhalf = (int)gv.nhalf;
-    it.wrow_max = m->var_rowmax[v];
+    it.wrow_max = rowmax;
     it.n = n;
 }
 
@@ -463,10 +483,28 @@ static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, 
     Mode32Group gd;
     memset(&gd, 0, sizeof gd);
     gd.nitems = 1;
-    fill_item(gd.item[0], m, v, fhat, Qhat, n);
+    fill_item(gd.item[0], m, m->var_W[v], m->var_task[v], m->var_rowmax[v], fhat, Qhat, n);
     gd.tile_start[0] = 0;
     gd.tile_start[1] = ctas_for(v, n);
-    return launch_group(gd, v, smem_bytes(m->g->v, m->var_rowmax[v], v), st);
+    return launch_group(gd, v, smem_bytes<float>(m->g->v, m->var_rowmax[v], v), st);
+}
+
+// FP64 form: the same kernel on double spectra and weights, 16-cell tiles
+// (variant index kFp64Variant), no last-wave split.
+constexpr int kFp64Variant = 2;
+
+bool modesum64_available(const bz_modes *m) { return m->w64 != nullptr; }
+
+cudaError_t launch_modesum64(const bz_modes *m, const double2 *fhat, double2 *Qhat, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (!m->w64) return cudaErrorInvalidValue;
+    Mode32Group gd;
+    memset(&gd, 0, sizeof gd);
+    gd.nitems = 1;
+    fill_item(gd.item[0], m, m->w64, m->task64, m->rowmax64, fhat, Qhat, n);
+    gd.tile_start[0] = 0;
+    gd.tile_start[1] = ctas_for(kFp64Variant, n);
+    return launch_instance<double, 4, 16, 16>(gd, smem_bytes<double>(m->g->v, m->rowmax64, kFp64Variant), st);
 }
 
 static int sm_count();
@@ -518,10 +556,11 @@ cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *cons
     int64_t ctas = 0;
     for (int i = 0; i < count; ++i) {
         if (ms[i]->variant != v) return cudaErrorInvalidValue;
-        fill_item(gd.item[i], ms[i], v, fhat[i], Qhat[i], n[i]);
+        fill_item(gd.item[i], ms[i], ms[i]->var_W[v], ms[i]->var_task[v], ms[i]->var_rowmax[v], fhat[i], Qhat[i],
+                  n[i]);
         gd.tile_start[i] = ctas;
         ctas += ctas_for(v, n[i]);
-        sm = std::max(sm, smem_bytes(ms[i]->g->v, ms[i]->var_rowmax[v], v));
+        sm = std::max(sm, smem_bytes<float>(ms[i]->g->v, ms[i]->var_rowmax[v], v));
     }
     gd.tile_start[count] = ctas;
     if (ctas == 0) return cudaSuccess;
@@ -637,9 +676,18 @@ int modes_build_fp32_tables(bz_modes *m) {
         m->var_W[v] = nullptr;
         m->var_task[v] = nullptr;
         m->var_rowmax[v] = 0;
-        if (build_variant(m, v, rc)) any = true;
+        void *w = nullptr;
+        if (build_variant<float>(m, v, rc, &w, &m->var_task[v], &m->var_rowmax[v])) {
+            m->var_W[v] = static_cast<float *>(w);
+            any = true;
+        }
         if (rc) return rc;
     }
+    // FP64 tables (16-cell tiles) where the double spectrum fits shared memory
+    m->w64 = nullptr;
+    m->task64 = nullptr;
+    m->rowmax64 = 0;
+    if (!build_variant<double>(m, kFp64Variant, rc, &m->w64, &m->task64, &m->rowmax64) && rc) return rc;
     if (!any) return BZ_OK;
     const char *force = getenv("BZ_MODESUM_VARIANT");   // fixed choice (1-based id), no timing
     int v = -1;
