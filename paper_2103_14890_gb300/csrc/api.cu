@@ -196,8 +196,12 @@ int check_modes(const bz_modes *m, int precision, const char *who) {
 int phase_forward(const bz_modes *m, int precision, const void *f, void *fh, int64_t n, cudaStream_t st) {
     const bz_grid *g = m->g;
     const GridView &v = g->v;
-    if (precision == BZ_FP64) {
+    if (precision == BZ_FP64 && m->tile_dft) {
         BZ_LAUNCH("dft_forward_f64", st,
+                  launch_dft64_forward_tile(v, static_cast<const double *>(f), static_cast<double2 *>(fh), n, st),
+                  "collide: forward DFT");
+    } else if (precision == BZ_FP64) {
+        BZ_LAUNCH("dft_forward_f64_generic", st,
                   launch_dft_forward_f64(v, g->d_E64, static_cast<const double *>(f), static_cast<double2 *>(fh), n, st),
                   "collide: forward DFT");
     } else if (m->tile_dft) {
@@ -254,8 +258,13 @@ int phase_inverse(const bz_modes *m, int precision, int flags, const void *qh, v
     ep.conserve = (flags & BZ_CONSERVE) ? 1 : 0;
     ep.check = 0;
     ep.P = P;
-    if (precision == BZ_FP64) {
+    if (precision == BZ_FP64 && m->tile_dft) {
         BZ_LAUNCH("dft_inverse_f64", st,
+                  launch_dft64_inverse_tile(v, static_cast<const double2 *>(qh), static_cast<double *>(Q), n, m->scale,
+                                            g->cinv, ep, st),
+                  "collide: inverse DFT");
+    } else if (precision == BZ_FP64) {
+        BZ_LAUNCH("dft_inverse_f64_generic", st,
                   launch_dft_inverse_f64(v, g->d_E64, static_cast<const double2 *>(qh), static_cast<double *>(Q), n,
                                          m->scale, g->cinv, ep, st),
                   "collide: inverse DFT");

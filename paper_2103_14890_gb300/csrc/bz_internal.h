@@ -101,11 +101,15 @@ cudaError_t launch_dft_inverse_f32(const GridView &g, const float2 *E, const flo
                                    float *Q, int64_t n, double scale, const double *cinv,
                                    const InvEpilogue &ep, cudaStream_t st);
 
-// ---- tile FP32 FFT kernels (k_dft32.cu), 2-D, N in {16, 24, 32, 48} ---------
+// ---- tile FFT kernels (k_dft32.cu), FP32 and FP64, 2-D, N in {16, 24, 32, 48} ----
 bool dft32_tile_supported(const GridView &g);
 int dft32_setup();   // twiddles on the current device
 cudaError_t launch_dft32_forward_tile(const GridView &g, const float *f, float2 *fhat, int64_t n, cudaStream_t st);
 cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *Qhat, float *Q, int64_t n, double scale,
+                                      const double *cinv, const InvEpilogue &ep, cudaStream_t st);
+cudaError_t launch_dft64_forward_tile(const GridView &g, const double *f, double2 *fhat, int64_t n,
+                                      cudaStream_t st);
+cudaError_t launch_dft64_inverse_tile(const GridView &g, const double2 *Qhat, double *Q, int64_t n, double scale,
                                       const double *cinv, const InvEpilogue &ep, cudaStream_t st);
 
 // ---- register-blocked FP32 2-D mode sum (k_modesum32.cu) --------------------

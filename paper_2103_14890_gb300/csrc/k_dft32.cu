@@ -22,28 +22,29 @@ namespace {
 
 // Inverse-DFT epilogue of one cell held as one column j2 = lane per thread:
 // optional conservation projection, optional G = Q - P, coalesced store.
-template <int N>
-__device__ __forceinline__ void inv32_epilogue(float (&q)[N], int64_t cell, int lane, const Cinv &cinv,
-                                               int conserve, const float *__restrict__ P, float *__restrict__ Q,
+template <typename T, int N>
+__device__ __forceinline__ void inv32_epilogue(T (&q)[N], int64_t cell, int lane, const Cinv &cinv,
+                                               int conserve, const T *__restrict__ P, T *__restrict__ Q,
                                                double L, double dv, int64_t n) {
+    using S = T;
     constexpr int NV = N * N;
-    const float v2 = (float)(-L + lane * dv);          // velocity of column j2
+    const S v2 = (S)(-L + lane * dv);          // velocity of column j2
     if (conserve) {
         // moments of Q over the cell: FP32 partials along j1 with a TwoSum
         // error term, combined in FP64 across the lanes; then the projection
         // Q -= phi . (C C^T)^{-1} (C Q) with phi = (1, v1, v2, |v|^2)
         double mom[4];
         {
-            float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f, s3 = 0.f, e3 = 0.f;
+            S s0 = (S)0., e0 = (S)0., s1 = (S)0., e1 = (S)0., s3 = (S)0., e3 = (S)0.;
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                const float v1 = (float)(-L + j * dv);
-                const float t0 = lane < N ? q[j] : 0.f;
-                float s, bb;
+                const S v1 = (S)(-L + j * dv);
+                const S t0 = lane < N ? q[j] : (S)0.;
+                S s, bb;
                 s = s0 + t0; bb = s - s0; e0 += (s0 - (s - bb)) + (t0 - bb); s0 = s;
-                const float t1 = v1 * t0;
+                const S t1 = v1 * t0;
                 s = s1 + t1; bb = s - s1; e1 += (s1 - (s - bb)) + (t1 - bb); s1 = s;
-                const float t3 = v1 * v1 * t0;
+                const S t3 = v1 * v1 * t0;
                 s = s3 + t3; bb = s - s3; e3 += (s3 - (s - bb)) + (t3 - bb); s3 = s;
             }
             const double S0 = (double)s0 + e0, S1 = (double)s1 + e1, S3 = (double)s3 + e3;
@@ -65,16 +66,16 @@ __device__ __forceinline__ void inv32_epilogue(float (&q)[N], int64_t cell, int 
             for (int c = 0; c < 4; ++c) s += cinv.v[a * 4 + c] * mom[c];
             x[a] = s;
         }
-        const float x0 = (float)x[0], x1 = (float)x[1], x2 = (float)x[2], x3 = (float)x[3];
+        const S x0 = (S)x[0], x1 = (S)x[1], x2 = (S)x[2], x3 = (S)x[3];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            const float v1 = (float)(-L + j * dv);
+            const S v1 = (S)(-L + j * dv);
             q[j] -= x0 + x1 * v1 + x2 * v2 + x3 * (v1 * v1 + v2 * v2);
         }
     }
     if (cell < n && lane < N) {
-        float *out = Q + cell * NV + lane;
-        const float *pc = P ? P + cell * NV + lane : nullptr;
+        S *out = Q + cell * NV + lane;
+        const S *pc = P ? P + cell * NV + lane : nullptr;
 #pragma unroll
         for (int j = 0; j < N; ++j) out[j * N] = pc ? q[j] - pc[j * N] : q[j];
     }
@@ -98,6 +99,11 @@ __device__ __forceinline__ void inv32_epilogue(float (&q)[N], int64_t cell, int 
 // operands.
 
 __constant__ float2 c_w32[32];          // e^{-2 pi i k / 32}, k = 0..31
+__constant__ double2 c_w32d[32];
+
+template <typename V> __device__ __forceinline__ V tw32(int k);
+template <> __device__ __forceinline__ float2 tw32<float2>(int k) { return c_w32[k]; }
+template <> __device__ __forceinline__ double2 tw32<double2>(int k) { return c_w32d[k]; }
 
 constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 constexpr int bitrev(int i, int bits) {
@@ -109,28 +115,30 @@ constexpr int bitrev(int i, int bits) {
 // In-place radix-2 decimation-in-time FFT of length L <= 32 whose input sits
 // in bit-reversed order; output in natural order.  SIGN = -1: sum x_n
 // e^{-2 pi i k n / L}; SIGN = +1: sum x_n e^{+2 pi i k n / L} (unnormalised).
-template <int L, int SIGN>
-__device__ __forceinline__ void fft_dit(float2 (&a)[L]) {
+template <int L, int SIGN, typename V>
+__device__ __forceinline__ void fft_dit(V (&a)[L]) {
+    using S = decltype(V::x);
+    using V2 = V;
 #pragma unroll
     for (int m = 1; m < L; m <<= 1) {
 #pragma unroll
         for (int g = 0; g < L; g += 2 * m) {
 #pragma unroll
             for (int j = 0; j < m; ++j) {
-                const float2 b = a[g + j + m];
-                float2 t;
+                const V2 b = a[g + j + m];
+                V2 t;
                 if (j == 0) {
                     t = b;
                 } else if (2 * j == m) {                       // twiddle -i (forward) or +i (inverse)
-                    t = SIGN < 0 ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x);
+                    t = SIGN < 0 ? cmk<V2>(b.y, -b.x) : cmk<V2>(-b.y, b.x);
                 } else {
-                    const float2 w = c_w32[j * (32 / (2 * m))];
-                    const float wy = SIGN < 0 ? w.y : -w.y;    // conj for the inverse
-                    t = make_float2(b.x * w.x - b.y * wy, b.x * wy + b.y * w.x);
+                    const V w = tw32<V>(j * (32 / (2 * m)));
+                    const S wy = SIGN < 0 ? w.y : -w.y;    // conj for the inverse
+                    t = cmk<V2>(b.x * w.x - b.y * wy, b.x * wy + b.y * w.x);
                 }
-                const float2 u = a[g + j];
-                a[g + j] = make_float2(u.x + t.x, u.y + t.y);
-                a[g + j + m] = make_float2(u.x - t.x, u.y - t.y);
+                const V2 u = a[g + j];
+                a[g + j] = cmk<V2>(u.x + t.x, u.y + t.y);
+                a[g + j + m] = cmk<V2>(u.x - t.x, u.y - t.y);
             }
         }
     }
@@ -139,12 +147,15 @@ __device__ __forceinline__ void fft_dit(float2 (&a)[L]) {
 // One CTA handles C cells (C = 32: a whole 32-cell tile of the Fourier layout,
 // or C = 16: half of one, so that two CTAs fit an SM and one's memory traffic
 // overlaps the other's arithmetic) with 16 C threads.
-template <int N, int C>
+template <typename T, int N, int C>
 __global__ void __launch_bounds__(C * 16)
-fft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, int64_t n) {
+fft_fwd32_kernel(const T *__restrict__ f, typename C2<T>::type *__restrict__ fhat, int64_t n) {
+    using V2 = typename C2<T>::type;
+    using S = T;
     constexpr int H = N / 2, M = N - 1, NV = N * N, LH = ilog2(H), LN = ilog2(N);
     constexpr int NW = C / 2, P = C + 1;                // warps; cell pitch of the shared rows
-    extern __shared__ __align__(16) float2 As[];        // [H][N][P]
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2 *As = reinterpret_cast<V2 *>(smem_raw);        // [H][N][P]
     const int64_t tile = blockIdx.x / (32 / C);
     const int sub = (int)(blockIdx.x % (32 / C)) * C;   // first cell of this CTA within the tile
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -154,27 +165,27 @@ fft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, int64_t
         for (int c = warp; c < C; c += NW) {
             const int64_t g = tile * 32 + sub + c;
             const bool ok = g < n;
-            const float *fc = f + g * NV + lane;
-            float2 z[H];
+            const S *fc = f + g * NV + lane;
+            V2 z[H];
 #pragma unroll
             for (int p = 0; p < H; ++p) {
-                const float x0 = ok ? __ldg(fc + (2 * p) * N) : 0.f;
-                const float x1 = ok ? __ldg(fc + (2 * p + 1) * N) : 0.f;
-                z[bitrev(p, LH)] = make_float2(x0, x1);   // packed even / odd samples
+                const S x0 = ok ? __ldg(fc + (2 * p) * N) : (S)0.;
+                const S x1 = ok ? __ldg(fc + (2 * p + 1) * N) : (S)0.;
+                z[bitrev(p, LH)] = cmk<V2>(x0, x1);   // packed even / odd samples
             }
             fft_dit<H, -1>(z);
             // untangle: X[k] = E[k] + omega^-k O[k], E = (Z_k + conj Z_-k)/2,
             // O = (Z_k - conj Z_-k)/(2i); scale (-1)^k / N
 #pragma unroll
             for (int k = 0; k < H; ++k) {
-                const float2 zk = z[k], zc = z[(H - k) % H];
-                const float ex = 0.5f * (zk.x + zc.x), ey = 0.5f * (zk.y - zc.y);
-                const float ox = 0.5f * (zk.y + zc.y), oy = -0.5f * (zk.x - zc.x);
-                const float2 w = c_w32[k * (32 / N)];
-                const float xr = ex + (w.x * ox - w.y * oy);
-                const float xi = ey + (w.x * oy + w.y * ox);
-                const float sc = (k & 1) ? -1.f / N : 1.f / N;
-                As[(k * N + lane) * P + c] = make_float2(xr * sc, xi * sc);
+                const V2 zk = z[k], zc = z[(H - k) % H];
+                const S ex = (S)0.5 * (zk.x + zc.x), ey = (S)0.5 * (zk.y - zc.y);
+                const S ox = (S)0.5 * (zk.y + zc.y), oy = -(S)0.5 * (zk.x - zc.x);
+                const V2 w = tw32<V2>(k * (32 / N));
+                const S xr = ex + (w.x * ox - w.y * oy);
+                const S xi = ey + (w.x * oy + w.y * ox);
+                const S sc = (k & 1) ? -(S)1. / N : (S)1. / N;
+                As[(k * N + lane) * P + c] = cmk<V2>(xr * sc, xi * sc);
             }
         }
     }
@@ -184,81 +195,84 @@ fft_fwd32_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, int64_t
     const int64_t gc = tile * 32 + sub + cell;
 #pragma unroll 1
     for (int k1 = threadIdx.x / C; k1 < H; k1 += 16) {
-        float2 a[N];
+        V2 a[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) a[bitrev(j, LN)] = As[(k1 * N + j) * P + cell];
         fft_dit<N, -1>(a);
         if (gc < n) {
-            float2 *out = fhat + tile * (int64_t)(H * M) * 32 + (int64_t)k1 * M * 32 + sub + cell;
+            V2 *out = fhat + tile * (int64_t)(H * M) * 32 + (int64_t)k1 * M * 32 + sub + cell;
 #pragma unroll
             for (int kk = 0; kk < M; ++kk) {
                 const int k2 = kk - (H - 1);
-                const float sc = (k2 & 1) ? -1.f / N : 1.f / N;
-                const float2 v = a[k2 & (N - 1)];
-                out[kk * 32] = make_float2(v.x * sc, v.y * sc);
+                const S sc = (k2 & 1) ? -(S)1. / N : (S)1. / N;
+                const V2 v = a[k2 & (N - 1)];
+                out[kk * 32] = cmk<V2>(v.x * sc, v.y * sc);
             }
         }
     }
 }
 
-template <int N, int C>
+template <typename T, int N, int C>
 __global__ void __launch_bounds__(C * 16)
-fft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, float scale, Cinv cinv, int conserve,
-                 const float *__restrict__ P_, double L, double dv, int64_t n) {
+fft_inv32_kernel(const typename C2<T>::type *__restrict__ Qhat, T *__restrict__ Q, T scale, Cinv cinv,
+                 int conserve, const T *__restrict__ P_, double L, double dv, int64_t n) {
+    using V2 = typename C2<T>::type;
+    using S = T;
     constexpr int H = N / 2, M = N - 1, LH = ilog2(H), LN = ilog2(N);
     constexpr int NW = C / 2, P = C + 1;
-    extern __shared__ __align__(16) float2 Bs[];        // [H][N][P]
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2 *Bs = reinterpret_cast<V2 *>(smem_raw);        // [H][N][P]
     const int64_t tile = blockIdx.x / (32 / C);
     const int sub = (int)(blockIdx.x % (32 / C)) * C;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // ---- stage 1: thread = (cell, row k1); inverse complex FFT over k2 ----
     {
         const int cell = threadIdx.x % C;
-        const float2 *qt = Qhat + tile * (int64_t)(H * M) * 32 + sub + cell;
+        const V2 *qt = Qhat + tile * (int64_t)(H * M) * 32 + sub + cell;
 #pragma unroll 1
         for (int k1 = threadIdx.x / C; k1 < H; k1 += 16) {
-            float2 a[N];
-            a[bitrev(H, LN)] = make_float2(0.f, 0.f);   // Nyquist slot k2 = N/2
+            V2 a[N];
+            a[bitrev(H, LN)] = cmk<V2>((S)0., (S)0.);   // Nyquist slot k2 = N/2
 #pragma unroll
             for (int kk = 0; kk < M; ++kk) {
                 const int k2 = kk - (H - 1);
-                const float2 v = qt[(k1 * M + kk) * 32];
-                a[bitrev(k2 & (N - 1), LN)] = (k2 & 1) ? make_float2(-v.x, -v.y) : v;
+                const V2 v = qt[(k1 * M + kk) * 32];
+                a[bitrev(k2 & (N - 1), LN)] = (k2 & 1) ? cmk<V2>(-v.x, -v.y) : v;
             }
             fft_dit<N, +1>(a);
-            const float sc = (k1 & 1) ? -scale : scale; // s^(d+gamma) (-1)^k1
+            const S sc = (k1 & 1) ? -scale : scale; // s^(d+gamma) (-1)^k1
 #pragma unroll
-            for (int j = 0; j < N; ++j) Bs[(k1 * N + j) * P + cell] = make_float2(a[j].x * sc, a[j].y * sc);
+            for (int j = 0; j < N; ++j) Bs[(k1 * N + j) * P + cell] = cmk<V2>(a[j].x * sc, a[j].y * sc);
         }
     }
     __syncthreads();
     // ---- stage 2: lane = column j2 of cells warp, warp + NW, ...; Hermitian-to-real over k1 ----
 #pragma unroll 1
     for (int c = warp; c < C; c += NW) {
-        float q[N];
+        S q[N];
         if (lane < N) {
-            float2 x[H + 1];
+            V2 x[H + 1];
 #pragma unroll
             for (int k = 0; k < H; ++k) x[k] = Bs[(k * N + lane) * P + c];
-            x[0].y = 0.f;                                // real part of the k1 = 0 row
-            x[H] = make_float2(0.f, 0.f);
+            x[0].y = (S)0.;                                // real part of the k1 = 0 row
+            x[H] = cmk<V2>((S)0., (S)0.);
             // Z[k] = E[k] + i O[k], E = X_k + conj X_{H-k}, O = (X_k - conj X_{H-k}) omega^k
-            float2 z[H];
+            V2 z[H];
 #pragma unroll
             for (int k = 0; k < H; ++k) {
-                const float2 xk = x[k], xc = make_float2(x[H - k].x, -x[H - k].y);
-                float ex, ey, ox, oy;
+                const V2 xk = x[k], xc = cmk<V2>(x[H - k].x, -x[H - k].y);
+                S ex, ey, ox, oy;
                 if (k == 0) {
                     ex = xk.x; ey = xk.y; ox = xk.x; oy = xk.y;
                 } else {
                     ex = xk.x + xc.x;
                     ey = xk.y + xc.y;
-                    const float dx = xk.x - xc.x, dy = xk.y - xc.y;
-                    const float2 w = c_w32[k * (32 / N)];           // omega^k = conj(w)
+                    const S dx = xk.x - xc.x, dy = xk.y - xc.y;
+                    const V2 w = tw32<V2>(k * (32 / N));           // omega^k = conj(w)
                     ox = dx * w.x + dy * w.y;
                     oy = dy * w.x - dx * w.y;
                 }
-                z[bitrev(k, LH)] = make_float2(ex - oy, ey + ox);
+                z[bitrev(k, LH)] = cmk<V2>(ex - oy, ey + ox);
             }
             fft_dit<H, +1>(z);
 #pragma unroll
@@ -268,9 +282,9 @@ fft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, float s
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < N; ++j) q[j] = 0.f;
+            for (int j = 0; j < N; ++j) q[j] = (S)0.;
         }
-        inv32_epilogue<N>(q, tile * 32 + sub + c, lane, cinv, conserve, P_, Q, L, dv, n);
+        inv32_epilogue<T, N>(q, tile * 32 + sub + c, lane, cinv, conserve, P_, Q, L, dv, n);
     }
 }
 
@@ -284,13 +298,20 @@ fft_inv32_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, float s
 // use TPC = 32 or 64 threads per cell (one or two whole warps).
 
 __constant__ float2 c_w48[48];          // e^{-2 pi i k / 48}, k = 0..47
+__constant__ double2 c_w48d[48];
+
+template <typename V> __device__ __forceinline__ V tw48(int k);
+template <> __device__ __forceinline__ float2 tw48<float2>(int k) { return c_w48[k]; }
+template <> __device__ __forceinline__ double2 tw48<double2>(int k) { return c_w48d[k]; }
 
 // Transform of length L (2^p <= 32, or 3 * 2^p <= 48) from natural to
 // natural order; SIGN as in fft_dit.
-template <int L, int SIGN>
-__device__ __forceinline__ void fft_nat(float2 (&a)[L]) {
+template <int L, int SIGN, typename V>
+__device__ __forceinline__ void fft_nat(V (&a)[L]) {
+    using S = decltype(V::x);
+    using V2 = V;
     if constexpr ((L & (L - 1)) == 0) {
-        float2 b[L];
+        V2 b[L];
 #pragma unroll
         for (int i = 0; i < L; ++i) b[bitrev(i, ilog2(L))] = a[i];
         fft_dit<L, SIGN>(b);
@@ -299,22 +320,22 @@ __device__ __forceinline__ void fft_nat(float2 (&a)[L]) {
     } else {
         static_assert(L % 3 == 0 && L <= 48, "length 3 * 2^p <= 48");
         constexpr int Q = L / 3;
-        constexpr float kS3 = 0.866025403784438647f;    // sqrt(3) / 2
-        float2 y0[Q], y1[Q], y2[Q];
+        constexpr S kS3 = (S)0.866025403784438647;    // sqrt(3) / 2
+        V2 y0[Q], y1[Q], y2[Q];
 #pragma unroll
         for (int n2 = 0; n2 < Q; ++n2) {
-            const float2 p = a[n2], q = a[Q + n2], r = a[2 * Q + n2];
-            const float sx = q.x + r.x, sy = q.y + r.y, dx = q.x - r.x, dy = q.y - r.y;
-            y0[n2] = make_float2(p.x + sx, p.y + sy);
-            const float mx = p.x - 0.5f * sx, my = p.y - 0.5f * sy;
+            const V2 p = a[n2], q = a[Q + n2], r = a[2 * Q + n2];
+            const S sx = q.x + r.x, sy = q.y + r.y, dx = q.x - r.x, dy = q.y - r.y;
+            y0[n2] = cmk<V2>(p.x + sx, p.y + sy);
+            const S mx = p.x - (S)0.5 * sx, my = p.y - (S)0.5 * sy;
             // -i (sqrt3/2) d for the forward transform, +i (sqrt3/2) d for the inverse
-            const float ix = SIGN < 0 ? kS3 * dy : -kS3 * dy, iy = SIGN < 0 ? -kS3 * dx : kS3 * dx;
-            float2 u1 = make_float2(mx + ix, my + iy), u2 = make_float2(mx - ix, my - iy);
+            const S ix = SIGN < 0 ? kS3 * dy : -kS3 * dy, iy = SIGN < 0 ? -kS3 * dx : kS3 * dx;
+            V2 u1 = cmk<V2>(mx + ix, my + iy), u2 = cmk<V2>(mx - ix, my - iy);
             if (n2 > 0) {
-                const float2 w1 = c_w48[n2 * (48 / L)], w2 = c_w48[2 * n2 * (48 / L)];
-                const float w1y = SIGN < 0 ? w1.y : -w1.y, w2y = SIGN < 0 ? w2.y : -w2.y;
-                u1 = make_float2(u1.x * w1.x - u1.y * w1y, u1.x * w1y + u1.y * w1.x);
-                u2 = make_float2(u2.x * w2.x - u2.y * w2y, u2.x * w2y + u2.y * w2.x);
+                const V w1 = tw48<V>(n2 * (48 / L)), w2 = tw48<V>(2 * n2 * (48 / L));
+                const S w1y = SIGN < 0 ? w1.y : -w1.y, w2y = SIGN < 0 ? w2.y : -w2.y;
+                u1 = cmk<V2>(u1.x * w1.x - u1.y * w1y, u1.x * w1y + u1.y * w1.x);
+                u2 = cmk<V2>(u2.x * w2.x - u2.y * w2y, u2.x * w2y + u2.y * w2.x);
             }
             y1[n2] = u1;
             y2[n2] = u2;
@@ -332,62 +353,65 @@ __device__ __forceinline__ void fft_nat(float2 (&a)[L]) {
 }
 
 // e^{-2 pi i k / N} for N in {16, 24, 32, 48}
-template <int N> __device__ __forceinline__ float2 tw(int k) {
-    if constexpr (N == 16 || N == 32) return c_w32[k * (32 / N)];
-    else return c_w48[k * (48 / N)];
+template <int N, typename V> __device__ __forceinline__ V tw(int k) {
+    if constexpr (N == 16 || N == 32) return tw32<V>(k * (32 / N));
+    else return tw48<V>(k * (48 / N));
 }
 
 template <int N> constexpr int threads_per_cell() { return N <= 32 ? 32 : 64; }
 
-template <int N, int C>
+template <typename T, int N, int C>
 __global__ void __launch_bounds__(C * threads_per_cell<N>())
-fftg_fwd_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, int64_t n) {
-    constexpr int H = N / 2, M = N - 1, NV = N * N, P = C + 1, T = C * threads_per_cell<N>();
-    extern __shared__ __align__(16) float2 As[];        // [H][N][P]
+fftg_fwd_kernel(const T *__restrict__ f, typename C2<T>::type *__restrict__ fhat, int64_t n) {
+    using V2 = typename C2<T>::type;
+    using S = T;
+    constexpr int H = N / 2, M = N - 1, NV = N * N, P = C + 1, NT = C * threads_per_cell<N>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2 *As = reinterpret_cast<V2 *>(smem_raw);        // [H][N][P]
     const int64_t tile = blockIdx.x / (32 / C);
     const int sub = (int)(blockIdx.x % (32 / C)) * C;
     // ---- stage 1: thread = (cell, column j2); real transform over j1 ----
 #pragma unroll 1
-    for (int t = threadIdx.x; t < C * N; t += T) {
+    for (int t = threadIdx.x; t < C * N; t += NT) {
         const int c = t / N, j2 = t % N;
         const int64_t g = tile * 32 + sub + c;
         const bool ok = g < n;
-        const float *fc = f + g * NV + j2;
-        float2 z[H];
+        const S *fc = f + g * NV + j2;
+        V2 z[H];
 #pragma unroll
         for (int p = 0; p < H; ++p)
-            z[p] = make_float2(ok ? __ldg(fc + (2 * p) * N) : 0.f, ok ? __ldg(fc + (2 * p + 1) * N) : 0.f);
+            z[p] = cmk<V2>(ok ? __ldg(fc + (2 * p) * N) : (S)0., ok ? __ldg(fc + (2 * p + 1) * N) : (S)0.);
         fft_nat<H, -1>(z);
 #pragma unroll
         for (int k = 0; k < H; ++k) {
-            const float2 zk = z[k], zc = z[(H - k) % H];
-            const float ex = 0.5f * (zk.x + zc.x), ey = 0.5f * (zk.y - zc.y);
-            const float ox = 0.5f * (zk.y + zc.y), oy = -0.5f * (zk.x - zc.x);
-            const float2 w = tw<N>(k);
-            const float xr = ex + (w.x * ox - w.y * oy);
-            const float xi = ey + (w.x * oy + w.y * ox);
-            const float sc = (k & 1) ? -1.f / N : 1.f / N;
-            As[(k * N + j2) * P + c] = make_float2(xr * sc, xi * sc);
+            const V2 zk = z[k], zc = z[(H - k) % H];
+            const S ex = (S)0.5 * (zk.x + zc.x), ey = (S)0.5 * (zk.y - zc.y);
+            const S ox = (S)0.5 * (zk.y + zc.y), oy = -(S)0.5 * (zk.x - zc.x);
+            const V2 w = tw<N, V2>(k);
+            const S xr = ex + (w.x * ox - w.y * oy);
+            const S xi = ey + (w.x * oy + w.y * ox);
+            const S sc = (k & 1) ? -(S)1. / N : (S)1. / N;
+            As[(k * N + j2) * P + c] = cmk<V2>(xr * sc, xi * sc);
         }
     }
     __syncthreads();
     // ---- stage 2: thread = (cell, row k1); complex transform over j2 ----
 #pragma unroll 1
-    for (int t = threadIdx.x; t < C * H; t += T) {
+    for (int t = threadIdx.x; t < C * H; t += NT) {
         const int c = t % C, k1 = t / C;
         const int64_t g = tile * 32 + sub + c;
-        float2 a[N];
+        V2 a[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) a[j] = As[(k1 * N + j) * P + c];
         fft_nat<N, -1>(a);
         if (g < n) {
-            float2 *out = fhat + tile * (int64_t)(H * M) * 32 + (int64_t)k1 * M * 32 + sub + c;
+            V2 *out = fhat + tile * (int64_t)(H * M) * 32 + (int64_t)k1 * M * 32 + sub + c;
 #pragma unroll
             for (int kk = 0; kk < M; ++kk) {
                 const int k2 = kk - (H - 1);
-                const float sc = (k2 & 1) ? -1.f / N : 1.f / N;
-                const float2 v = a[(k2 + N) % N];
-                out[kk * 32] = make_float2(v.x * sc, v.y * sc);
+                const S sc = (k2 & 1) ? -(S)1. / N : (S)1. / N;
+                const V2 v = a[(k2 + N) % N];
+                out[kk * 32] = cmk<V2>(v.x * sc, v.y * sc);
             }
         }
     }
@@ -396,27 +420,28 @@ fftg_fwd_kernel(const float *__restrict__ f, float2 *__restrict__ fhat, int64_t 
 // Epilogue for one column j2 of one cell, TPC threads per cell (whole warps):
 // conservation projection (moments reduced over the cell's warps in a fixed
 // order), G = Q - P, store.  red: shared scratch of (T/32) * 4 doubles.
-template <int N, int TPC>
-__device__ __forceinline__ void invg_epilogue(float (&q)[N], int64_t cell, int j2, const Cinv &cinv,
-                                              int conserve, const float *__restrict__ P,
-                                              float *__restrict__ Q, double L, double dv, int64_t n,
+template <typename T, int N, int TPC>
+__device__ __forceinline__ void invg_epilogue(T (&q)[N], int64_t cell, int j2, const Cinv &cinv,
+                                              int conserve, const T *__restrict__ P,
+                                              T *__restrict__ Q, double L, double dv, int64_t n,
                                               double *red) {
+    using S = T;
     constexpr int NV = N * N;
     const bool col = j2 < N;
-    const float v2 = (float)(-L + j2 * dv);
+    const S v2 = (S)(-L + j2 * dv);
     if (conserve) {
         double mom[4];
         {
-            float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f, s3 = 0.f, e3 = 0.f;
+            S s0 = (S)0., e0 = (S)0., s1 = (S)0., e1 = (S)0., s3 = (S)0., e3 = (S)0.;
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                const float v1 = (float)(-L + j * dv);
-                const float t0 = col ? q[j] : 0.f;
-                float s, bb;
+                const S v1 = (S)(-L + j * dv);
+                const S t0 = col ? q[j] : (S)0.;
+                S s, bb;
                 s = s0 + t0; bb = s - s0; e0 += (s0 - (s - bb)) + (t0 - bb); s0 = s;
-                const float t1 = v1 * t0;
+                const S t1 = v1 * t0;
                 s = s1 + t1; bb = s - s1; e1 += (s1 - (s - bb)) + (t1 - bb); s1 = s;
-                const float t3 = v1 * v1 * t0;
+                const S t3 = v1 * v1 * t0;
                 s = s3 + t3; bb = s - s3; e3 += (s3 - (s - bb)) + (t3 - bb); s3 = s;
             }
             const double S0 = (double)s0 + e0, S1 = (double)s1 + e1, S3 = (double)s3 + e3;
@@ -454,74 +479,77 @@ __device__ __forceinline__ void invg_epilogue(float (&q)[N], int64_t cell, int j
             for (int c = 0; c < 4; ++c) s += cinv.v[a * 4 + c] * mom[c];
             x[a] = s;
         }
-        const float x0 = (float)x[0], x1 = (float)x[1], x2 = (float)x[2], x3 = (float)x[3];
+        const S x0 = (S)x[0], x1 = (S)x[1], x2 = (S)x[2], x3 = (S)x[3];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            const float v1 = (float)(-L + j * dv);
+            const S v1 = (S)(-L + j * dv);
             q[j] -= x0 + x1 * v1 + x2 * v2 + x3 * (v1 * v1 + v2 * v2);
         }
     }
     if (cell < n && col) {
-        float *out = Q + cell * NV + j2;
-        const float *pc = P ? P + cell * NV + j2 : nullptr;
+        S *out = Q + cell * NV + j2;
+        const S *pc = P ? P + cell * NV + j2 : nullptr;
 #pragma unroll
         for (int j = 0; j < N; ++j) out[j * N] = pc ? q[j] - pc[j * N] : q[j];
     }
 }
 
-template <int N, int C>
+template <typename T, int N, int C>
 __global__ void __launch_bounds__(C * threads_per_cell<N>())
-fftg_inv_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, float scale, Cinv cinv, int conserve,
-                const float *__restrict__ P_, double L, double dv, int64_t n) {
-    constexpr int H = N / 2, M = N - 1, P = C + 1, TPC = threads_per_cell<N>(), T = C * TPC;
-    extern __shared__ __align__(16) float2 Bs[];        // [H][N][P], then T/32 * 4 doubles
+fftg_inv_kernel(const typename C2<T>::type *__restrict__ Qhat, T *__restrict__ Q, T scale, Cinv cinv,
+                int conserve, const T *__restrict__ P_, double L, double dv, int64_t n) {
+    using V2 = typename C2<T>::type;
+    using S = T;
+    constexpr int H = N / 2, M = N - 1, P = C + 1, TPC = threads_per_cell<N>(), NT = C * TPC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2 *Bs = reinterpret_cast<V2 *>(smem_raw);        // [H][N][P], then NT/32 * 4 doubles
     double *red = reinterpret_cast<double *>(Bs + (size_t)H * N * P);
     const int64_t tile = blockIdx.x / (32 / C);
     const int sub = (int)(blockIdx.x % (32 / C)) * C;
     // ---- stage 1: thread = (cell, row k1); inverse complex transform over k2 ----
 #pragma unroll 1
-    for (int t = threadIdx.x; t < C * H; t += T) {
+    for (int t = threadIdx.x; t < C * H; t += NT) {
         const int c = t % C, k1 = t / C;
-        const float2 *qt = Qhat + tile * (int64_t)(H * M) * 32 + sub + c;
-        float2 a[N];
-        a[H] = make_float2(0.f, 0.f);                   // Nyquist slot k2 = N/2
+        const V2 *qt = Qhat + tile * (int64_t)(H * M) * 32 + sub + c;
+        V2 a[N];
+        a[H] = cmk<V2>((S)0., (S)0.);                   // Nyquist slot k2 = N/2
 #pragma unroll
         for (int kk = 0; kk < M; ++kk) {
             const int k2 = kk - (H - 1);
-            const float2 v = qt[(k1 * M + kk) * 32];
-            a[(k2 + N) % N] = (k2 & 1) ? make_float2(-v.x, -v.y) : v;
+            const V2 v = qt[(k1 * M + kk) * 32];
+            a[(k2 + N) % N] = (k2 & 1) ? cmk<V2>(-v.x, -v.y) : v;
         }
         fft_nat<N, +1>(a);
-        const float sc = (k1 & 1) ? -scale : scale;     // s^(d+gamma) (-1)^k1
+        const S sc = (k1 & 1) ? -scale : scale;     // s^(d+gamma) (-1)^k1
 #pragma unroll
-        for (int j = 0; j < N; ++j) Bs[(k1 * N + j) * P + c] = make_float2(a[j].x * sc, a[j].y * sc);
+        for (int j = 0; j < N; ++j) Bs[(k1 * N + j) * P + c] = cmk<V2>(a[j].x * sc, a[j].y * sc);
     }
     __syncthreads();
     // ---- stage 2: thread = (cell, column j2), TPC threads per cell ----
     const int c = threadIdx.x / TPC, j2 = threadIdx.x % TPC;
-    float q[N];
+    S q[N];
     if (j2 < N) {
-        float2 x[H + 1];
+        V2 x[H + 1];
 #pragma unroll
         for (int k = 0; k < H; ++k) x[k] = Bs[(k * N + j2) * P + c];
-        x[0].y = 0.f;                                    // real part of the k1 = 0 row
-        x[H] = make_float2(0.f, 0.f);
-        float2 z[H];
+        x[0].y = (S)0.;                                    // real part of the k1 = 0 row
+        x[H] = cmk<V2>((S)0., (S)0.);
+        V2 z[H];
 #pragma unroll
         for (int k = 0; k < H; ++k) {
-            const float2 xk = x[k], xc = make_float2(x[H - k].x, -x[H - k].y);
-            float ex, ey, ox, oy;
+            const V2 xk = x[k], xc = cmk<V2>(x[H - k].x, -x[H - k].y);
+            S ex, ey, ox, oy;
             if (k == 0) {
                 ex = xk.x; ey = xk.y; ox = xk.x; oy = xk.y;
             } else {
                 ex = xk.x + xc.x;
                 ey = xk.y + xc.y;
-                const float dx = xk.x - xc.x, dy = xk.y - xc.y;
-                const float2 w = tw<N>(k);                   // omega^k = conj(w)
+                const S dx = xk.x - xc.x, dy = xk.y - xc.y;
+                const V2 w = tw<N, V2>(k);                   // omega^k = conj(w)
                 ox = dx * w.x + dy * w.y;
                 oy = dy * w.x - dx * w.y;
             }
-            z[k] = make_float2(ex - oy, ey + ox);
+            z[k] = cmk<V2>(ex - oy, ey + ox);
         }
         fft_nat<H, +1>(z);
 #pragma unroll
@@ -531,19 +559,89 @@ fftg_inv_kernel(const float2 *__restrict__ Qhat, float *__restrict__ Q, float sc
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < N; ++j) q[j] = 0.f;
+        for (int j = 0; j < N; ++j) q[j] = (S)0.;
     }
-    invg_epilogue<N, TPC>(q, tile * 32 + sub + c, j2, cinv, conserve, P_, Q, L, dv, n, red);
+    invg_epilogue<T, N, TPC>(q, tile * 32 + sub + c, j2, cinv, conserve, P_, Q, L, dv, n, red);
 }
 
-template <int N, int C> size_t fftg_smem() {
-    return sizeof(float2) * (size_t)(N / 2) * N * (C + 1) + sizeof(double) * 4 * (C * threads_per_cell<N>() / 32);
+template <typename T, int N, int C> size_t fftg_smem() {
+    return 2 * sizeof(T) * (size_t)(N / 2) * N * (C + 1) + sizeof(double) * 4 * (C * threads_per_cell<N>() / 32);
 }
-template <int N> constexpr int fftg_cells() { return N <= 32 ? 16 : 8; }
+template <typename T, int N, int C> size_t fft_smem() { return 2 * sizeof(T) * (size_t)(N / 2) * N * (C + 1); }
 
-template <int N, int C> size_t fft_smem() { return sizeof(float2) * (size_t)(N / 2) * N * (C + 1); }
-constexpr int kFftCells = 16;   // cells per CTA of the FFT kernels
+// Cells per CTA: FP32 16 (8 for 48^2, whose columns take two warps per cell);
+// FP64 half of that (twice the bytes per value).
+template <typename T, int N> constexpr int fft_cells() {
+    return (N == 48 ? 8 : 16) / (sizeof(T) == 8 ? 2 : 1);
+}
 
+template <typename T, int N>
+cudaError_t fwd_tile(const T *f, typename C2<T>::type *fhat, int64_t n, cudaStream_t st) {
+    constexpr int C = fft_cells<T, N>();
+    const unsigned grid = (unsigned)(((n + 31) / 32) * (32 / C));
+    cudaError_t e;
+    if constexpr (N == 16 || N == 32) {
+        const size_t sm = fft_smem<T, N, C>();
+        e = cudaFuncSetAttribute(fft_fwd32_kernel<T, N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        fft_fwd32_kernel<T, N, C><<<grid, C * 16, sm, st>>>(f, fhat, n);
+    } else {
+        const size_t sm = fftg_smem<T, N, C>();
+        e = cudaFuncSetAttribute(fftg_fwd_kernel<T, N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        fftg_fwd_kernel<T, N, C><<<grid, C * threads_per_cell<N>(), sm, st>>>(f, fhat, n);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t inv_tile(const GridView &g, const typename C2<T>::type *Qhat, T *Q, int64_t n, double scale,
+                     const Cinv &ci, const InvEpilogue &ep, cudaStream_t st) {
+    constexpr int C = fft_cells<T, N>();
+    const unsigned grid = (unsigned)(((n + 31) / 32) * (32 / C));
+    const T *P = static_cast<const T *>(ep.P);
+    cudaError_t e;
+    if constexpr (N == 16 || N == 32) {
+        const size_t sm = fft_smem<T, N, C>();
+        e = cudaFuncSetAttribute(fft_inv32_kernel<T, N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        fft_inv32_kernel<T, N, C><<<grid, C * 16, sm, st>>>(Qhat, Q, (T)scale, ci, ep.conserve, P, g.L, g.dv, n);
+    } else {
+        const size_t sm = fftg_smem<T, N, C>();
+        e = cudaFuncSetAttribute(fftg_inv_kernel<T, N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        fftg_inv_kernel<T, N, C><<<grid, C * threads_per_cell<N>(), sm, st>>>(Qhat, Q, (T)scale, ci, ep.conserve,
+                                                                             P, g.L, g.dv, n);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t fwd_any(const GridView &g, const T *f, typename C2<T>::type *fhat, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    switch (g.N) {
+        case 16: return fwd_tile<T, 16>(f, fhat, n, st);
+        case 24: return fwd_tile<T, 24>(f, fhat, n, st);
+        case 32: return fwd_tile<T, 32>(f, fhat, n, st);
+        case 48: return fwd_tile<T, 48>(f, fhat, n, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t inv_any(const GridView &g, const typename C2<T>::type *Qhat, T *Q, int64_t n, double scale,
+                    const double *cinv, const InvEpilogue &ep, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    Cinv ci;
+    for (int i = 0; i < 25; ++i) ci.v[i] = cinv[i];
+    switch (g.N) {
+        case 16: return inv_tile<T, 16>(g, Qhat, Q, n, scale, ci, ep, st);
+        case 24: return inv_tile<T, 24>(g, Qhat, Q, n, scale, ci, ep, st);
+        case 32: return inv_tile<T, 32>(g, Qhat, Q, n, scale, ci, ep, st);
+        case 48: return inv_tile<T, 48>(g, Qhat, Q, n, scale, ci, ep, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 }  // namespace
 
@@ -555,83 +653,37 @@ bool dft32_tile_supported(const GridView &g) {
 // device, so this runs for every modes handle, on its device).
 int dft32_setup() {
     float2 w32[32], w48[48];
-    for (int k = 0; k < 32; ++k) w32[k] = make_float2((float)cos(2.0 * M_PI * k / 32), (float)-sin(2.0 * M_PI * k / 32));
-    for (int k = 0; k < 48; ++k) w48[k] = make_float2((float)cos(2.0 * M_PI * k / 48), (float)-sin(2.0 * M_PI * k / 48));
+    double2 d32[32], d48[48];
+    for (int k = 0; k < 32; ++k) {
+        d32[k] = make_double2(cos(2.0 * M_PI * k / 32), -sin(2.0 * M_PI * k / 32));
+        w32[k] = make_float2((float)d32[k].x, (float)d32[k].y);
+    }
+    for (int k = 0; k < 48; ++k) {
+        d48[k] = make_double2(cos(2.0 * M_PI * k / 48), -sin(2.0 * M_PI * k / 48));
+        w48[k] = make_float2((float)d48[k].x, (float)d48[k].y);
+    }
     cudaError_t e = cudaMemcpyToSymbol(c_w32, w32, sizeof w32);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w48, w48, sizeof w48);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w32d, d32, sizeof d32);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w48d, d48, sizeof d48);
     if (e != cudaSuccess) return cuda_fail(e, "build_kernel_modes: FFT twiddles");
     return BZ_OK;
 }
 
 cudaError_t launch_dft32_forward_tile(const GridView &g, const float *f, float2 *fhat, int64_t n, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const unsigned ntile = (unsigned)((n + 31) / 32);
-    cudaError_t e = cudaSuccess;
-#define BZ_FFT_FWD(NN)                                                                                   \
-    case NN: {                                                                                           \
-        size_t sm = fft_smem<NN, kFftCells>();                                                           \
-        e = cudaFuncSetAttribute(fft_fwd32_kernel<NN, kFftCells>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        if (e != cudaSuccess) return e;                                                                  \
-        fft_fwd32_kernel<NN, kFftCells><<<ntile * (32 / kFftCells), kFftCells * 16, sm, st>>>(f, fhat, n); \
-        break;                                                                                           \
-    }
-#define BZ_FFTG_FWD(NN)                                                                                  \
-    case NN: {                                                                                           \
-        constexpr int C = fftg_cells<NN>();                                                              \
-        size_t sm = fftg_smem<NN, C>();                                                                  \
-        e = cudaFuncSetAttribute(fftg_fwd_kernel<NN, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        if (e != cudaSuccess) return e;                                                                  \
-        fftg_fwd_kernel<NN, C><<<ntile * (32 / C), C * threads_per_cell<NN>(), sm, st>>>(f, fhat, n);    \
-        break;                                                                                           \
-    }
-    switch (g.N) {
-        BZ_FFT_FWD(16)
-        BZ_FFTG_FWD(24)
-        BZ_FFT_FWD(32)
-        BZ_FFTG_FWD(48)
-        default: return cudaErrorInvalidValue;
-    }
-#undef BZ_FFTG_FWD
-#undef BZ_FFT_FWD
-    return cudaGetLastError();
+    return fwd_any<float>(g, f, fhat, n, st);
 }
-
+cudaError_t launch_dft64_forward_tile(const GridView &g, const double *f, double2 *fhat, int64_t n,
+                                      cudaStream_t st) {
+    return fwd_any<double>(g, f, fhat, n, st);
+}
 cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *Qhat, float *Q, int64_t n, double scale,
                                       const double *cinv, const InvEpilogue &ep, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const unsigned ntile = (unsigned)((n + 31) / 32);
-    Cinv ci;
-    for (int i = 0; i < 25; ++i) ci.v[i] = cinv[i];
-    cudaError_t e = cudaSuccess;
-#define BZ_FFT_INV(NN)                                                                                   \
-    case NN: {                                                                                           \
-        size_t sm = fft_smem<NN, kFftCells>();                                                           \
-        e = cudaFuncSetAttribute(fft_inv32_kernel<NN, kFftCells>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        if (e != cudaSuccess) return e;                                                                  \
-        fft_inv32_kernel<NN, kFftCells><<<ntile * (32 / kFftCells), kFftCells * 16, sm, st>>>(           \
-            Qhat, Q, (float)scale, ci, ep.conserve, static_cast<const float *>(ep.P), g.L, g.dv, n);     \
-        break;                                                                                           \
-    }
-#define BZ_FFTG_INV(NN)                                                                                  \
-    case NN: {                                                                                           \
-        constexpr int C = fftg_cells<NN>();                                                              \
-        size_t sm = fftg_smem<NN, C>();                                                                  \
-        e = cudaFuncSetAttribute(fftg_inv_kernel<NN, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        if (e != cudaSuccess) return e;                                                                  \
-        fftg_inv_kernel<NN, C><<<ntile * (32 / C), C * threads_per_cell<NN>(), sm, st>>>(                \
-            Qhat, Q, (float)scale, ci, ep.conserve, static_cast<const float *>(ep.P), g.L, g.dv, n);     \
-        break;                                                                                           \
-    }
-    switch (g.N) {
-        BZ_FFT_INV(16)
-        BZ_FFTG_INV(24)
-        BZ_FFT_INV(32)
-        BZ_FFTG_INV(48)
-        default: return cudaErrorInvalidValue;
-    }
-#undef BZ_FFTG_INV
-#undef BZ_FFT_INV
-    return cudaGetLastError();
+    return inv_any<float>(g, Qhat, Q, n, scale, cinv, ep, st);
+}
+cudaError_t launch_dft64_inverse_tile(const GridView &g, const double2 *Qhat, double *Q, int64_t n, double scale,
+                                      const double *cinv, const InvEpilogue &ep, cudaStream_t st) {
+    return inv_any<double>(g, Qhat, Q, n, scale, cinv, ep, st);
 }
 
 }  // namespace bz

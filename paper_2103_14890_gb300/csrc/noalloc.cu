@@ -70,12 +70,15 @@ int run_with_scratch(const bz_modes *m, int precision, int flags, const void *f,
     cudaError_t e;
     if (precision == BZ_FP64) {
         double2 *fh = static_cast<double2 *>(scratch), *qh = fh + celem;
-        e = launch_dft_forward_f64(v, g->d_E64, static_cast<const double *>(f), fh, n, st);
+        e = m->tile_dft ? launch_dft64_forward_tile(v, static_cast<const double *>(f), fh, n, st)
+                        : launch_dft_forward_f64(v, g->d_E64, static_cast<const double *>(f), fh, n, st);
         if (e == cudaSuccess)
             e = modesum64_available(m) ? launch_modesum64(m, fh, qh, n, st)
                                        : launch_modesum_generic_f64(v, m->d_F64, m->bcols, fh, qh, n, st);
         if (e == cudaSuccess)
-            e = launch_dft_inverse_f64(v, g->d_E64, qh, static_cast<double *>(Q), n, m->scale, g->cinv, ep, st);
+            e = m->tile_dft ? launch_dft64_inverse_tile(v, qh, static_cast<double *>(Q), n, m->scale, g->cinv, ep, st)
+                            : launch_dft_inverse_f64(v, g->d_E64, qh, static_cast<double *>(Q), n, m->scale, g->cinv,
+                                                     ep, st);
     } else {
         float2 *fh = static_cast<float2 *>(scratch), *qh = fh + celem;
         const float *fin = static_cast<const float *>(f);
