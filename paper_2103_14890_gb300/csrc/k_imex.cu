@@ -86,11 +86,18 @@ __global__ void __launch_bounds__(kThreads) imex_stage_kernel(GridView g, StageC
 }
 
 // Fast 2-D path (N <= 32): one warp per cell, lane = column j2, loop over
-// rows j1.  Moments: per-lane sums along j1 in the state precision (FP32: with
-// a TwoSum error term), combined across the warp in FP64.  The Maxwellian of
-// a 2-D grid factorises, M(v1, v2) = pref e1(v1) e2(v2), so each lane evaluates
-// two exponentials in FP64 (its row and its column factor) instead of one per
-// grid point.
+// rows j1, 16 cells per CTA.  FP64 work is what limits this kernel on a GPU
+// whose FP64 rate is 1/74 of FP32, so it is arranged to keep the FP64 pipe's
+// lanes busy with distinct work:
+//   * per lane, sums along j1 in the state precision (FP32: with a TwoSum
+//     error term), turned into FP64 once (S0, S1, S3 and the v2 products);
+//   * the 32 lane partials of each cell are summed in FP64 by one thread per
+//     (cell, moment) from shared memory, not by a shuffle tree on every lane;
+//   * the Maxwellian parameters (rho, u, theta, ...) of the CTA's 16 cells are
+//     computed by 16 lanes of one warp, one cell per lane;
+//   * the Maxwellian of a 2-D grid factorises, M(v1, v2) = pref e1(v1) e2(v2):
+//     each lane forms its row and column offsets v - u in FP64 and the rest of
+//     the exponent and the exponential in the state precision.
 template <typename T>
 __device__ __forceinline__ void acc2(T &s, T &e, T x) {
     if constexpr (sizeof(T) == 4) {
@@ -102,17 +109,22 @@ __device__ __forceinline__ void acc2(T &s, T &e, T x) {
     }
 }
 
+constexpr int kStageCells = 16;   // cells (warps) per CTA of the 2-D stage kernel
+
 template <typename T, int N>
-__global__ void __launch_bounds__(256) imex_stage2d_kernel(GridView g, StageCoef c, const T *__restrict__ fn,
-                                                           T *__restrict__ F, const T *__restrict__ G,
-                                                           T *__restrict__ P, const T *__restrict__ Lres,
-                                                           int64_t stride, int64_t n) {
-    const int lane = threadIdx.x & 31;
-    const int64_t cell = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (cell >= n) return;
+__global__ void __launch_bounds__(kStageCells * 32) imex_stage2d_kernel(GridView g, StageCoef c,
+                                                                       const T *__restrict__ fn, T *__restrict__ F,
+                                                                       const T *__restrict__ G, T *__restrict__ P,
+                                                                       const T *__restrict__ Lres, int64_t stride,
+                                                                       int64_t n) {
+    __shared__ double part[kStageCells][4][33];   // per-lane moment partials (pitch 33: no bank conflicts)
+    __shared__ double par[kStageCells][8];        // rho, u1, u2, inv2t, pref, c, 1/(1+c)
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t cell = (int64_t)blockIdx.x * kStageCells + wib;
+    const bool live = cell < n;
     constexpr int NV = N * N;
-    const bool on = lane < N;
-    const int64_t base = cell * NV + (on ? lane : 0);
+    const bool on = lane < N && live;
+    const int64_t base = (live ? cell : 0) * NV + (lane < N ? lane : 0);
     const T dt = (T)c.dt, ieps = (T)(1.0 / c.eps);
     T R[N];
 #pragma unroll
@@ -130,37 +142,60 @@ __global__ void __launch_bounds__(256) imex_stage2d_kernel(GridView g, StageCoef
             }
         }
     }
-    // moments: sums along the column (j1), then across lanes in FP64
-    T s0 = 0, e0 = 0, s1 = 0, e1 = 0, s3 = 0, e3 = 0;
-    const T L = (T)g.L, dv = (T)g.dv;
+    // this lane's partial moments (column j2 = lane)
+    {
+        T s0 = 0, e0 = 0, s1 = 0, e1 = 0, s3 = 0, e3 = 0;
+        const T L = (T)g.L, dv = (T)g.dv;
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-        const T v1 = fma((T)j, dv, -L);
-        acc2(s0, e0, R[j]);
-        acc2(s1, e1, v1 * R[j]);
-        acc2(s3, e3, v1 * v1 * R[j]);
+        for (int j = 0; j < N; ++j) {
+            const T v1 = fma((T)j, dv, -L);
+            acc2(s0, e0, R[j]);
+            acc2(s1, e1, v1 * R[j]);
+            acc2(s3, e3, v1 * v1 * R[j]);
+        }
+        const double vv = -g.L + lane * g.dv;
+        const double S0 = (double)s0 + (double)e0, S1 = (double)s1 + (double)e1, S3 = (double)s3 + (double)e3;
+        part[wib][0][lane] = S0;
+        part[wib][1][lane] = S1;
+        part[wib][2][lane] = vv * S0;
+        part[wib][3][lane] = S3 + vv * vv * S0;
     }
-    const double vv = on ? -g.L + lane * g.dv : 0.0;
-    double S0 = (double)s0 + (double)e0, S1 = (double)s1 + (double)e1, S3 = (double)s3 + (double)e3;
-    double mom[4] = {S0, S1, vv * S0, S3 + vv * vv * S0};
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mom[k] += __shfl_xor_sync(0xffffffffu, mom[k], o);
-    const double w = g.dv * g.dv;
-    const double rho = w * mom[0];
-    const double u1 = w * mom[1] / rho, u2 = w * mom[2] / rho;
-    const double E = 0.5 * w * mom[3];
-    const double theta = (2.0 * E / rho - (u1 * u1 + u2 * u2)) / 2.0;
-    const double pref = rho / (2.0 * M_PI * theta);
-    const double inv2t = 0.5 / theta;
+    __syncthreads();
+    // sums over the 32 lanes of each cell: thread (cell, moment), in a fixed order
+    double tot = 0.0;
+    if (threadIdx.x < kStageCells * 4) {
+        const int cc = threadIdx.x >> 2, q = threadIdx.x & 3;
+        for (int l = 0; l < 32; ++l) tot += part[cc][q][l];
+        part[cc][q][32] = tot;
+    }
+    __syncthreads();
+    // Maxwellian parameters, one cell per lane of warp 0
+    if (threadIdx.x < kStageCells) {
+        const int cc = threadIdx.x;
+        const double w = g.dv * g.dv;
+        const double rho = w * part[cc][0][32];
+        const double u1 = w * part[cc][1][32] / rho, u2 = w * part[cc][2][32] / rho;
+        const double E = 0.5 * w * part[cc][3][32];
+        const double theta = (2.0 * E / rho - (u1 * u1 + u2 * u2)) / 2.0;
+        const double cst = c.dt * c.all * rho / c.eps;
+        par[cc][0] = rho;
+        par[cc][1] = u1;
+        par[cc][2] = u2;
+        par[cc][3] = 0.5 / theta;
+        par[cc][4] = rho / (2.0 * M_PI * theta);
+        par[cc][5] = cst;
+        par[cc][6] = 1.0 / (1.0 + cst);
+    }
+    __syncthreads();
+    if (!live) return;
     // separable Maxwellian: this lane's column factor and row factor j1 = lane;
-    // exponents in FP64, the exponential in the state precision
-    const double d2 = vv - u2, d1 = (-g.L + lane * g.dv) - u1;
-    const T fcol = (T)pref * exp((T)(-d2 * d2 * inv2t));
-    const T frow_l = exp((T)(-d1 * d1 * inv2t));
-    const double cc = c.dt * c.all * rho / c.eps;
-    const T cT = (T)cc, denom = (T)(1.0 / (1.0 + cc)), rhoT = (T)rho;
+    // offsets v - u in FP64, the rest of the exponent and the exp in T
+    const double vl = -g.L + lane * g.dv;
+    const T d2 = (T)(vl - par[wib][2]), d1 = (T)(vl - par[wib][1]);
+    const T i2t = (T)par[wib][3];
+    const T fcol = (T)par[wib][4] * exp(-d2 * d2 * i2t);
+    const T frow_l = exp(-d1 * d1 * i2t);
+    const T cT = (T)par[wib][5], denom = (T)par[wib][6], rhoT = (T)par[wib][0];
     T *Fo = F + base;
     T *Po = P + (int64_t)c.stage * stride + base;
 #pragma unroll
@@ -189,10 +224,11 @@ cudaError_t stage(const GridView &g, const StageCoef &c, const T *fn, T *F, cons
                   const T *Lres, int64_t stride, int64_t n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     if (g.dim == 2 && (g.N == 16 || g.N == 24 || g.N == 32)) {
-        const unsigned blocks = (unsigned)((n + 7) / 8);
-        if (g.N == 16) imex_stage2d_kernel<T, 16><<<blocks, 256, 0, st>>>(g, c, fn, F, G, P, Lres, stride, n);
-        if (g.N == 24) imex_stage2d_kernel<T, 24><<<blocks, 256, 0, st>>>(g, c, fn, F, G, P, Lres, stride, n);
-        if (g.N == 32) imex_stage2d_kernel<T, 32><<<blocks, 256, 0, st>>>(g, c, fn, F, G, P, Lres, stride, n);
+        const unsigned blocks = (unsigned)((n + kStageCells - 1) / kStageCells);
+        const unsigned thr = kStageCells * 32;
+        if (g.N == 16) imex_stage2d_kernel<T, 16><<<blocks, thr, 0, st>>>(g, c, fn, F, G, P, Lres, stride, n);
+        if (g.N == 24) imex_stage2d_kernel<T, 24><<<blocks, thr, 0, st>>>(g, c, fn, F, G, P, Lres, stride, n);
+        if (g.N == 32) imex_stage2d_kernel<T, 32><<<blocks, thr, 0, st>>>(g, c, fn, F, G, P, Lres, stride, n);
         return cudaGetLastError();
     }
     size_t sm = sizeof(double) * 32 * 5 + sizeof(T) * (size_t)g.nv;
