@@ -574,6 +574,8 @@ template <typename T, int N, int C> size_t fft_smem() { return 2 * sizeof(T) * (
 template <typename T, int N> constexpr int fft_cells() {
     return (N == 48 ? 8 : 16) / (sizeof(T) == 8 ? 2 : 1);
 }
+// The inverse keeps 128 registers per thread; 8-cell CTAs let four share an SM.
+template <typename T, int N> constexpr int ifft_cells() { return (N == 16 || N == 32) ? 8 : fft_cells<T, N>(); }
 
 template <typename T, int N>
 cudaError_t fwd_tile(const T *f, typename C2<T>::type *fhat, int64_t n, cudaStream_t st) {
@@ -597,7 +599,7 @@ cudaError_t fwd_tile(const T *f, typename C2<T>::type *fhat, int64_t n, cudaStre
 template <typename T, int N>
 cudaError_t inv_tile(const GridView &g, const typename C2<T>::type *Qhat, T *Q, int64_t n, double scale,
                      const Cinv &ci, const InvEpilogue &ep, cudaStream_t st) {
-    constexpr int C = fft_cells<T, N>();
+    constexpr int C = ifft_cells<T, N>();
     const unsigned grid = (unsigned)(((n + 31) / 32) * (32 / C));
     const T *P = static_cast<const T *>(ep.P);
     cudaError_t e;

@@ -86,15 +86,15 @@ __global__ void __launch_bounds__(kThreads) imex_stage_kernel(GridView g, StageC
 }
 
 // Fast 2-D path (N <= 32): one warp per cell, lane = column j2, loop over
-// rows j1, 16 cells per CTA.  FP64 work is what limits this kernel on a GPU
+// rows j1, 8 cells per CTA.  FP64 work is what limits this kernel on a GPU
 // whose FP64 rate is 1/74 of FP32, so it is arranged to keep the FP64 pipe's
 // lanes busy with distinct work:
 //   * per lane, sums along j1 in the state precision (FP32: with a TwoSum
 //     error term), turned into FP64 once (S0, S1, S3 and the v2 products);
-//   * the 32 lane partials of each cell are summed in FP64 by one thread per
+//   * the 32 lane partials of each cell are summed in FP64 by four threads per
 //     (cell, moment) from shared memory, not by a shuffle tree on every lane;
-//   * the Maxwellian parameters (rho, u, theta, ...) of the CTA's 16 cells are
-//     computed by 16 lanes of one warp, one cell per lane;
+//   * the Maxwellian parameters (rho, u, theta, ...) of the CTA's 8 cells are
+//     computed by 8 lanes of one warp, one cell per lane;
 //   * the Maxwellian of a 2-D grid factorises, M(v1, v2) = pref e1(v1) e2(v2):
 //     each lane forms its row and column offsets v - u in FP64 and the rest of
 //     the exponent and the exponential in the state precision.
@@ -109,7 +109,7 @@ __device__ __forceinline__ void acc2(T &s, T &e, T x) {
     }
 }
 
-constexpr int kStageCells = 16;   // cells (warps) per CTA of the 2-D stage kernel
+constexpr int kStageCells = 8;    // cells (warps) per CTA of the 2-D stage kernel (two CTAs per SM)
 
 template <typename T, int N>
 __global__ void __launch_bounds__(kStageCells * 32) imex_stage2d_kernel(GridView g, StageCoef c,
@@ -161,12 +161,16 @@ __global__ void __launch_bounds__(kStageCells * 32) imex_stage2d_kernel(GridView
         part[wib][3][lane] = S3 + vv * vv * S0;
     }
     __syncthreads();
-    // sums over the 32 lanes of each cell: thread (cell, moment), in a fixed order
-    double tot = 0.0;
-    if (threadIdx.x < kStageCells * 4) {
-        const int cc = threadIdx.x >> 2, q = threadIdx.x & 3;
-        for (int l = 0; l < 32; ++l) tot += part[cc][q][l];
-        part[cc][q][32] = tot;
+    // sums over the 32 lanes of each cell: four threads per (cell, moment) sum
+    // eight partials each, then combine by shuffles (a fixed order)
+    if (threadIdx.x < kStageCells * 16) {
+        const int cc = threadIdx.x >> 4, q = (threadIdx.x >> 2) & 3, pp = threadIdx.x & 3;
+        double tot = 0.0;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) tot += part[cc][q][pp * 8 + l];
+        tot += __shfl_xor_sync(0xffffffffu, tot, 1);
+        tot += __shfl_xor_sync(0xffffffffu, tot, 2);
+        if (pp == 0) part[cc][q][32] = tot;
     }
     __syncthreads();
     // Maxwellian parameters, one cell per lane of warp 0

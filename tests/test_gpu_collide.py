@@ -185,6 +185,18 @@ def test_fp32_conservation_fix_every_tile_fft(bz, oracle_k, N, n):
         assert np.abs(mom).max() < 1e-5 * np.abs(Q).sum(axis=1).max() * np.abs(p).max()
 
 
+@pytest.mark.parametrize("N,n", [(24, 9), (48, 5)])
+@pytest.mark.parametrize("conserve", [False, True])
+def test_fp64_mixed_radix_fft_grids(bz, oracle_k, N, n, conserve):
+    """FP64 form on the grids whose tile FFTs are mixed radix (24 = 3 x 8,
+    48 = 3 x 16; 48^2 mode sums on the generic kernel) against the oracle."""
+    L = 10.0
+    f = workloads.bi_maxwellian(n, 2, N, L, seed=1600 + N)
+    Q = _gpu_collide(bz, 2, N, L, 1.0, f, "fp64", conserve=conserve)
+    Qr = oracle_k(2, N, L, 1.0).collide(f, conserve=conserve)
+    assert relerr(Q, Qr) < TOL64
+
+
 def test_fp64_three_dimensional(bz, oracle_k):
     f = workloads.bi_maxwellian(35, 3, 8, 8.0, seed=11)
     Q = _gpu_collide(bz, 3, 8, 8.0, 1.0, f, "fp64")
