@@ -26,10 +26,11 @@ N_V, L_BOX, GAMMA = 32, 10.0, 1.0
 CELLS = 65536
 SEED = 1003
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
-# DRAM bytes (read + write) of one modesum32_kernel launch (variant 1) on the
-# 65536-cell workload, from one ncu capture of dram__bytes_read.sum and
-# dram__bytes_write.sum; reported only for that workload and variant.
-MODESUM_TRAFFIC_65536 = None
+# DRAM bytes (read + write) of the mode-sum phase of one step (the launch over
+# the whole waves and the last-wave launch) on the 65536-cell workload, from one
+# ncu capture of dram__bytes_read.sum and dram__bytes_write.sum; reported only
+# for that workload.
+MODESUM_TRAFFIC_65536 = 251873792 + 200191232 + 9887744 + 0
 METRIC = "cell-collision evals/s at N_v=32^2: mixed-precision vs FP64 GPU, rel-L2 err stated"
 WORKLOAD = "65536 cells, 2-D 32x32 velocity grid on [-10,10]^2, VHS kernel, shifted Maxwellians Mach 0-3"
 
@@ -405,7 +406,7 @@ def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, valu
                       "speedup_fp32_over_fp64": value / value64} if Q64 is not None else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": MODESUM_TRAFFIC_65536 if (cells == CELLS and modes.modesum_variant == 1) else None,
+                     "traffic": MODESUM_TRAFFIC_65536 if cells == CELLS else None,
                      "kernel": ms_name,
                      "kernel_ms": k_ms, "flops_per_launch": flops_launch,
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
