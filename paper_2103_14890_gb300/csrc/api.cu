@@ -592,6 +592,15 @@ int collide_batch_host(const bz_modes *m, int precision, int flags, const void *
         return BZ_OK;
     };
     rc = run();
+    if (rc) {
+        // an error part-way: let the caller's stream wait for the copies already
+        // queued on the copy streams, so the chunk buffers are not returned to
+        // the pool while a copy still uses them
+        for (int i = 0; i < 2; ++i) {
+            cudaStream_t cs2 = i ? s_out : s_in;
+            if (cudaEventRecord(ev[5 + i], cs2) == cudaSuccess) cudaStreamWaitEvent(st, ev[5 + i], 0);
+        }
+    }
     for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
     return rc;
 }
