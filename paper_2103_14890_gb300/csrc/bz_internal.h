@@ -61,9 +61,10 @@ struct bz_modes {
     int var_rowmax[kModesumVariants];
     int variant;          // index of the selected variant
     int variant_fixed;    // 1: chosen by BZ_MODESUM_VARIANT (no last-wave split)
-    void *w64;            // FP64 weight stream and task table (16-cell tiles), null if unused
+    void *w64;            // FP64 weight stream and task table, null if unused
     int *task64;
     int rowmax64;
+    int variant64;        // layout of the FP64 tables (entry of the variant list), -1 if none
     int modesum_variant;  // variant id reported to callers (index + 1; 0: generic kernel)
     float *d_W32;
     int w32_rowmax;       // largest staged weight row (floats)

@@ -42,6 +42,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -60,8 +61,10 @@ namespace {
 struct Variant {
     int R, warps, cells;
 };
-constexpr int kNumVariants = kModesumVariants;
-constexpr Variant kVariants[kNumVariants] = {{8, 16, 32}, {4, 32, 32}, {4, 16, 16}, {4, 16, 8}};
+constexpr int kNumVariants = kModesumVariants;   // FP32 variants (timed by the autotuner)
+// entries 0..3: the FP32 variants; entry 4: an FP64-only layout (2 outputs per
+// thread, 8 warps, 8-cell tiles) for grids whose FP64 spectrum needs it
+constexpr Variant kVariants[kNumVariants + 1] = {{8, 16, 32}, {4, 32, 32}, {4, 16, 16}, {4, 16, 8}, {2, 8, 8}};
 constexpr int kTaskInts = 12;   // ints per task record
 
 constexpr int kPad = 8;         // zero guard columns before the first and after the last row
@@ -133,7 +136,15 @@ __device__ __forceinline__ void block_pass(typename C2<T>::type (&win)[2 * RR],
         const V2 fl = lp[s * DIR * CS];
         T wv[RR];
 #pragma unroll
-        for (int q = 0; q < RR; q += 4) load_w4(wv + q, wb + s * WS + q);
+        if constexpr (RR % 4 == 0) {
+#pragma unroll
+            for (int q = 0; q < RR; q += 4) load_w4(wv + q, wb + s * WS + q);
+        } else {
+            static_assert(RR == 2 && sizeof(T) == 8, "two-output blocks are used by the FP64 form only");
+            const double2 w2 = *reinterpret_cast<const double2 *>(wb + s * WS);
+            wv[0] = w2.x;
+            wv[1] = w2.y;
+        }
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
             const V2 b = win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)];
@@ -489,9 +500,10 @@ static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, 
     return launch_group(gd, v, smem_bytes<float>(m->g->v, m->var_rowmax[v], v), st);
 }
 
-// FP64 form: the same kernel on double spectra and weights, 16-cell tiles
-// (variant index kFp64Variant), no last-wave split.
-constexpr int kFp64Variant = 2;
+// FP64 form: the same kernel on double spectra and weights, on 16-cell tiles
+// (variant entry 2) or, where the double spectrum of 16 cells does not fit
+// shared memory (48^2), on 8-cell tiles (entry 4); no last-wave split.
+constexpr int kFp64Variants[2] = {2, 4};
 
 bool modesum64_available(const bz_modes *m) { return m->w64 != nullptr; }
 
@@ -503,8 +515,10 @@ cudaError_t launch_modesum64(const bz_modes *m, const double2 *fhat, double2 *Qh
     gd.nitems = 1;
     fill_item(gd.item[0], m, m->w64, m->task64, m->rowmax64, fhat, Qhat, n);
     gd.tile_start[0] = 0;
-    gd.tile_start[1] = ctas_for(kFp64Variant, n);
-    return launch_instance<double, 4, 16, 16>(gd, smem_bytes<double>(m->g->v, m->rowmax64, kFp64Variant), st);
+    gd.tile_start[1] = ctas_for(m->variant64, n);
+    const size_t sm = smem_bytes<double>(m->g->v, m->rowmax64, m->variant64);
+    if (m->variant64 == 2) return launch_instance<double, 4, 16, 16>(gd, sm, st);
+    return launch_instance<double, 2, 8, 8>(gd, sm, st);
 }
 
 static int sm_count();
@@ -579,10 +593,18 @@ int modesum32_variant_count() { return kNumVariants; }
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int>, int> g_tune;
 
+// SM count of the current device (cached per device; 0 entries are unset).
 static int sm_count() {
-    int dev = 0, n = 0;
+    static std::atomic<int> cache[64];
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (dev >= 0 && dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
     return n;
 }
 
@@ -687,7 +709,12 @@ int modes_build_fp32_tables(bz_modes *m) {
     m->w64 = nullptr;
     m->task64 = nullptr;
     m->rowmax64 = 0;
-    if (!build_variant<double>(m, kFp64Variant, rc, &m->w64, &m->task64, &m->rowmax64) && rc) return rc;
+    m->variant64 = -1;
+    for (int q = 0; q < 2 && m->variant64 < 0; ++q) {
+        if (build_variant<double>(m, kFp64Variants[q], rc, &m->w64, &m->task64, &m->rowmax64))
+            m->variant64 = kFp64Variants[q];
+        if (rc) return rc;
+    }
     if (!any) return BZ_OK;
     const char *force = getenv("BZ_MODESUM_VARIANT");   // fixed choice (1-based id), no timing
     int v = -1;

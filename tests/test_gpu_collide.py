@@ -185,7 +185,7 @@ def test_fp32_conservation_fix_every_tile_fft(bz, oracle_k, N, n):
         assert np.abs(mom).max() < 1e-5 * np.abs(Q).sum(axis=1).max() * np.abs(p).max()
 
 
-@pytest.mark.parametrize("N,n", [(24, 9), (48, 5)])
+@pytest.mark.parametrize("N,n", [(24, 9), (48, 5), (48, 13)])
 @pytest.mark.parametrize("conserve", [False, True])
 def test_fp64_mixed_radix_fft_grids(bz, oracle_k, N, n, conserve):
     """FP64 form on the grids whose tile FFTs are mixed radix (24 = 3 x 8,
