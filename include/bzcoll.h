@@ -194,11 +194,11 @@ int imex_step(const bz_modes *m, int scheme, int model, double dt, double eps,
 
 /* group_collide -- one collision evaluation for several independent instances
  * (each its own grid N / dimension / kernel and cell batch) in one call.  The
- * forward DFTs run per instance; the mode sums of all BZ_FP32 2-D instances with
- * N <= 32 share one launch of the register-blocked kernel (up to 16 instances
- * per launch), scheduled longest-first by per-cell work; other instances use the
- * generic kernel; then the inverse DFTs.  Results equal collide_batch on each
- * instance.
+ * forward DFTs run per instance; the FP32 mode sums of all instances served by
+ * the register-blocked kernel (2-D N <= 48, 3-D N <= 16) share one launch per
+ * kernel variant (up to 16 instances per launch), scheduled longest-first by
+ * per-cell work; other instances (and the FP64 form) use one launch each; then
+ * the inverse DFTs.  Results equal collide_batch on each instance.
  *   items     : n_items descriptors; item.modes must belong to the current
  *               device; item.f / item.Q are device arrays [n_cells][N^d]
  *   precision : BZ_FP32 or BZ_FP64 (all items alike)

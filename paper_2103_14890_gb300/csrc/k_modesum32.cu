@@ -582,8 +582,6 @@ cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *cons
     return launch_group(gd, v, sm, st);
 }
 
-int modesum32_variant_count() { return kNumVariants; }
-
 // ---- autotuner ------------------------------------------------------------
 // Times every buildable variant once per (dimension, N, SM count) on a
 // synthetic batch (zero spectra: the kernel's cost does not depend on the
