@@ -164,6 +164,7 @@ static int default_nodes(const orc_grid *g) {
  * B-hat(m,m) has |l-m| = 0 and is read at the transposed position, which holds
  * the same number because F(a,b) is formed symmetrically. */
 int orc_kernel_init(orc_kernel *k, const orc_grid *g, double gamma, double b0, int nq) {
+    memset(k, 0, sizeof *k);
     k->g = *g;
     k->gamma = gamma;
     k->b0 = (b0 > 0) ? b0 : (g->dim == 2 ? 1.0 / (2.0 * M_PI) : 1.0 / (4.0 * M_PI));
@@ -207,10 +208,76 @@ int orc_kernel_init(orc_kernel *k, const orc_grid *g, double gamma, double b0, i
     return 0;
 }
 
-void orc_kernel_free(orc_kernel *k) { free(k->F); k->F = NULL; }
+void orc_kernel_free(orc_kernel *k) {
+    free(k->F);
+    free(k->alpha);
+    free(k->alphap);
+    k->F = k->alpha = k->alphap = NULL;
+}
 
-/* B-hat(l,m) of eq. KM through a = |l+m|, b = |l-m|. */
+/* ------------------------------------------ fast spectral (Carleman) --- */
+
+/* Sec. 3.3, eq. defQBCarleman / eq. Btilde / eq. FKM, for Maxwell molecules
+ * in 2-D.  With |q| sigma = b0 the Carleman weight is the constant
+ * B-tilde = 2 b0.  Writing x = rho e_theta and y = rho' e_theta^perp
+ * (theta in [0, pi), rho and rho' over the whole line) resolves delta(x.y):
+ * dx dy delta(x.y) becomes drho drho' dtheta.  The truncation x, y in
+ * B_0(R), R = 2 lambda pi (the same radius as |q| <= 2 lambda pi of eq. KM),
+ * bounds rho and rho' by R, so
+ *   B_F(l,m) = 2 b0 int_0^pi phi(l.e_theta) phi(m.e_theta^perp) dtheta,
+ *   phi(xi)  = int_{-R}^{R} e^{i rho xi} drho = 2 sin(R xi) / xi.
+ * The theta integral is taken by the ndirs-point rectangle rule on
+ * theta_p = p pi / ndirs (the integrand has period pi), which is the
+ * decomposition B_F(l,m) ~ sum_p alpha_p(l) alpha'_p(m) that turns eq. ode
+ * into ndirs convolutions, with
+ *   alpha_p(k) = (2 b0 pi / ndirs) phi(k.e_p),  alpha'_p(k) = phi(k.e_p^perp). */
+static double carleman_phi(double xi) {
+    double R = cutoff_radius();
+    return 2.0 * R * sinc(R * xi);
+}
+
+int orc_fast_kernel_init(orc_kernel *k, const orc_grid *g, double b0, int ndirs) {
+    if (!k || !g || g->dim != 2 || ndirs < 1) return -1;
+    memset(k, 0, sizeof *k);
+    k->g = *g;
+    k->gamma = 0.0;
+    k->b0 = (b0 > 0) ? b0 : 1.0 / (2.0 * M_PI);
+    k->ndirs = ndirs;
+    k->alpha = (double *)malloc(sizeof(double) * (size_t)ndirs * g->nm);
+    k->alphap = (double *)malloc(sizeof(double) * (size_t)ndirs * g->nm);
+    if (!k->alpha || !k->alphap) {
+        orc_kernel_free(k);
+        return -1;
+    }
+    double w = 2.0 * k->b0 * M_PI / ndirs;
+    int kk[3];
+    for (int p = 0; p < ndirs; ++p) {
+        double th = M_PI * p / ndirs;
+        double e1 = cos(th), e2 = sin(th);          /* e_p */
+        for (int64_t ki = 0; ki < g->nm; ++ki) {
+            mode_index(g, ki, kk);
+            double x = kk[0] * e1 + kk[1] * e2;       /* k . e_p */
+            double y = -kk[0] * e2 + kk[1] * e1;      /* k . e_p^perp, e_p^perp = (-sin, cos) */
+            k->alpha[(size_t)p * g->nm + ki] = w * carleman_phi(x);
+            k->alphap[(size_t)p * g->nm + ki] = carleman_phi(y);
+        }
+    }
+    return 0;
+}
+
+/* B_F(l,m) = sum_p alpha_p(l) alpha'_p(m), summed in order of p. */
+static double fast_Bhat(const orc_kernel *k, const int *l, const int *m) {
+    int64_t li = mode_flat(&k->g, l), mi = mode_flat(&k->g, m);
+    double acc = 0.0;
+    for (int p = 0; p < k->ndirs; ++p)
+        acc += k->alpha[(size_t)p * k->g.nm + li] * k->alphap[(size_t)p * k->g.nm + mi];
+    return acc;
+}
+
+/* B-hat(l,m) of eq. KM through a = |l+m|, b = |l-m| (or B_F(l,m) of the fast
+ * method when the kernel was built by orc_fast_kernel_init). */
 double orc_Bhat(const orc_kernel *k, const int *l, const int *m) {
+    if (k->ndirs > 0) return fast_Bhat(k, l, m);
     int a2 = 0, b2 = 0;
     for (int i = 0; i < k->g.dim; ++i) {
         a2 += (l[i] + m[i]) * (l[i] + m[i]);

@@ -54,6 +54,11 @@ typedef struct {
     int arows;        /* cached |l+m|^2 values: 0 .. d h^2 */
     int amax2;        /* largest cached |l-m|^2: d (2h)^2 */
     double *F;        /* arows x (amax2+1) entries, F[a2*(amax2+1)+b2] */
+    /* Fast spectral method (Carleman form), 2-D only: ndirs > 0 replaces the
+     * radial table by the direction factors below (orc_fast_kernel_init). */
+    int ndirs;        /* A, number of collision directions; 0 for eq. KM */
+    double *alpha;    /* [ndirs][nm]: alpha_p(k)  */
+    double *alphap;   /* [ndirs][nm]: alpha'_p(k) */
 } orc_kernel;
 
 int    orc_grid_init(orc_grid *g, int dim, int N, double L);
@@ -68,6 +73,14 @@ double orc_radial_Bhat(int dim, double gamma, double b0, int nq, double a, doubl
 
 int    orc_kernel_init(orc_kernel *k, const orc_grid *g, double gamma, double b0, int nq);
 void   orc_kernel_free(orc_kernel *k);
+/* Fast spectral method of Sec. 3.3 (eq. defQBCarleman, eq. Btilde, eq. FKM,
+ * eq. ode) for Maxwell molecules in 2-D (|q| sigma = b0, b0 <= 0: 1/(2 pi)):
+ * the kernel modes become B_F(l,m) = sum_p alpha_p(l) alpha'_p(m) over ndirs
+ * collision directions.  Every other function below then evaluates the fast
+ * operator (orc_Bhat returns B_F, orc_collide and the IMEX step use it).
+ * Returns -1 for dim != 2 or ndirs < 1. */
+int    orc_fast_kernel_init(orc_kernel *k, const orc_grid *g, double b0, int ndirs);
+
 /* B-hat(l,m) and beta-hat(l,m) = B-hat(l,m) - B-hat(m,m), l,m given as
  * integer d-vectors. */
 double orc_Bhat(const orc_kernel *k, const int *l, const int *m);

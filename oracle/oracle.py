@@ -30,7 +30,8 @@ class _Grid(ctypes.Structure):
 
 class _Kernel(ctypes.Structure):
     _fields_ = [("g", _Grid), ("gamma", _d), ("b0", _d), ("nq", _i), ("arows", _i),
-                ("amax2", _i), ("F", ctypes.POINTER(_d))]
+                ("amax2", _i), ("F", ctypes.POINTER(_d)), ("ndirs", _i),
+                ("alpha", ctypes.POINTER(_d)), ("alphap", ctypes.POINTER(_d))]
 
 
 def build(force=False):
@@ -59,6 +60,7 @@ def load():
     lib.orc_radial_Bhat.restype = _d
     lib.orc_kernel_init.argtypes = [P(_Kernel), P(_Grid), _d, _d, _i]
     lib.orc_kernel_free.argtypes = [P(_Kernel)]
+    lib.orc_fast_kernel_init.argtypes = [P(_Kernel), P(_Grid), _d, _i]
     lib.orc_Bhat.argtypes = [P(_Kernel), _p, _p]
     lib.orc_Bhat.restype = _d
     lib.orc_beta.argtypes = [P(_Kernel), _p, _p]
@@ -104,17 +106,28 @@ STAGES = {"ars222": 3, "bpr343": 5, "euler": 2}
 
 
 class Kernel:
-    """Velocity grid plus kernel modes B(|q|) = b0 |q|^gamma (b0 <= 0: default)."""
+    """Velocity grid plus kernel modes B(|q|) = b0 |q|^gamma (b0 <= 0: default).
 
-    def __init__(self, dim, N, L, gamma, b0=0.0, nq=0):
+    ndirs > 0 selects the fast spectral (Carleman) form of the kernel modes
+    with that many collision directions (2-D, gamma = 0 only); see
+    ``FastKernel``."""
+
+    def __init__(self, dim, N, L, gamma, b0=0.0, nq=0, ndirs=0):
         lib = load()
         self._g = _Grid()
         if lib.orc_grid_init(ctypes.byref(self._g), dim, N, float(L)) != 0:
             raise ValueError("bad grid (dim=%r N=%r L=%r)" % (dim, N, L))
         self._k = _Kernel()
-        if lib.orc_kernel_init(ctypes.byref(self._k), ctypes.byref(self._g), float(gamma),
-                               float(b0), int(nq)) != 0:
+        if ndirs:
+            if gamma != 0.0 or dim != 2:
+                raise ValueError("the fast (Carleman) form is built for 2-D Maxwell molecules")
+            if lib.orc_fast_kernel_init(ctypes.byref(self._k), ctypes.byref(self._g), float(b0),
+                                        int(ndirs)) != 0:
+                raise ValueError("bad fast-method parameters (ndirs=%r)" % (ndirs,))
+        elif lib.orc_kernel_init(ctypes.byref(self._k), ctypes.byref(self._g), float(gamma),
+                                 float(b0), int(nq)) != 0:
             raise MemoryError("oracle kernel table allocation failed")
+        self.ndirs = int(ndirs)
         g = self._g
         self.dim, self.N, self.h, self.M = g.dim, g.N, g.h, g.M
         self.nv, self.nm = g.nv, g.nm
@@ -235,3 +248,9 @@ class Kernel:
         if rc != 0:
             raise RuntimeError("oracle imex failed")
         return out
+
+
+def FastKernel(N, L, ndirs, b0=0.0):
+    """Kernel modes of the fast spectral method (Sec. 3.3, eq. ode / eq. FKM) for
+    2-D Maxwell molecules with ``ndirs`` collision directions."""
+    return Kernel(2, N, L, 0.0, b0=b0, ndirs=ndirs)
