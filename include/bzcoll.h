@@ -120,6 +120,30 @@ int init_velocity_grid(int dim, int n_per_dim, double half_width_L, bz_grid **ou
 int build_kernel_modes(const bz_grid *g, double gamma, double b0, int quad_nodes,
                        bz_modes **out);
 
+/* build_fast_modes -- the fast spectral form of Sec. 3.3 (Carleman
+ * representation, eq. defQBCarleman with the weight of eq. Btilde; kernel
+ * modes of eq. FKM; mode sum of eq. ode) for 2-D Maxwell molecules,
+ * |q| sigma = b0.  With x = rho e_theta, y = rho' e_theta^perp the kernel
+ * modes are B_F(l,m) = 2 b0 int_0^pi phi(l.e_theta) phi(m.e_theta^perp) dtheta,
+ * phi(xi) = 2 sin(R xi)/xi, R = 2 lambda pi; the rectangle rule on
+ * theta_p = p pi / n_dirs splits them into n_dirs products
+ * alpha_p(l) alpha'_p(m), and the mode sum becomes n_dirs + 1 convolutions
+ * (the last one the loss term B_F(m,m)), evaluated by FFTs on a zero-padded
+ * P x P grid (P >= 3h + 1; bz_fast_info).  The direction factors are built on
+ * the host in FP64 and uploaded in FP64 and FP32.  The returned handle is a
+ * bz_modes accepted by every call that takes one (collide_batch,
+ * collide_batch_host, collide_batch_noalloc, group_collide, imex_stage_local,
+ * imex_step, bz_modes_beta); those calls then evaluate the fast operator with
+ * the same forward / inverse transforms and epilogues.  It does not change
+ * the meaning of the precision argument: BZ_FP64 or BZ_FP32 arithmetic.
+ *   g      : grid handle, dim = 2 and N in {8, 16, 24, 32}
+ *   b0     : kernel constant; <= 0 selects 1/(2 pi)
+ *   n_dirs : number of collision directions A, 1 <= A <= 1024
+ *   out    : receives the handle (release with bz_modes_destroy)
+ * Errors: BZ_EINVAL (NULL pointer, n_dirs out of range), BZ_ENOTSUP (grid not
+ * served: 3-D or another N), BZ_ENOMEM, BZ_ECUDA. */
+int build_fast_modes(const bz_grid *g, double b0, int n_dirs, bz_modes **out);
+
 /* collide_batch -- one evaluation of Q(f,f) in each of n_cells independent
  * cells (Sec. 3.3: forward DFT, the weighted sum of eq. CF1 over l + m = k in
  * K_h, inverse DFT, times s^(d+gamma) to return to physical units; with
@@ -229,9 +253,16 @@ const char *bz_last_error(void);
  * on the generic kernel (3-D grids, 2-D grids with N > 48). */
 int bz_modes_info(const bz_modes *m, int64_t out[8]);
 
+/* bz_fast_info -- out[0] = method of a modes handle (0: eq. KM / eq. CF1
+ * direct sum, 1: fast form of build_fast_modes), out[1] = collision
+ * directions A, out[2] = padded FFT length P, out[3] = cells per CTA of the
+ * fast kernel (out[1..3] are 0 for method 0). */
+int bz_fast_info(const bz_modes *m, int64_t out[4]);
+
 /* bz_modes_beta -- copy beta-hat(l,m) for l, m in K_h (row-major flat mode
  * indices, (2h+1)^d each) into host memory `out` ((2h+1)^(2d) doubles); entries
- * with l + m outside K_h are 0. For testing the FP64 quadrature. */
+ * with l + m outside K_h are 0. For testing the FP64 quadrature (for a fast
+ * handle: sum_p alpha_p(l) alpha'_p(m) - B_F(m,m) from the FP64 factors). */
 int bz_modes_beta(const bz_modes *m, double *out);
 
 /* bz_profile -- per-kernel timing for measurement (tracing).  enable = 1

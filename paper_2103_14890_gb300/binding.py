@@ -69,6 +69,8 @@ def load(path=None):
             "collide_batch_host": ([c_p, c_i, c_i, c_p, c_p, c_i64, c_p], c_i),
             "group_collide": ([c_p, c_i, c_i, c_i, c_p], c_i),
             "bz_profile_read": ([c_p, c_i, c_p, c_p, c_i], c_i),
+            "build_fast_modes": ([c_p, c_d, c_i, pp], c_i),
+            "bz_fast_info": ([c_p, ctypes.POINTER(c_i64)], c_i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -129,12 +131,18 @@ class Grid:
 class Modes:
     """Kernel modes (build_kernel_modes) of B = b0 |q|^gamma on a grid."""
 
-    def __init__(self, grid, gamma, b0=0.0, quad_nodes=0):
+    def __init__(self, grid, gamma, b0=0.0, quad_nodes=0, _handle=None):
         h = ctypes.c_void_p()
-        _check(load().build_kernel_modes(grid._h, float(gamma), float(b0), int(quad_nodes), ctypes.byref(h)))
+        if _handle is None:
+            _check(load().build_kernel_modes(grid._h, float(gamma), float(b0), int(quad_nodes), ctypes.byref(h)))
+        else:
+            h = _handle
         self._h = h
         self.grid = grid              # keep the grid alive
         self.gamma = gamma
+        fi = (ctypes.c_int64 * 4)()
+        _check(load().bz_fast_info(h, fi))
+        self.method, self.ndirs, self.pad, self.fast_cells = list(fi)
         info = (ctypes.c_int64 * 8)()
         _check(load().bz_modes_info(h, info))
         self.dim, self.N, self.h, self.nv, self.nhalf, self.nq, self.pairs_sym, self.modesum_variant = list(info)
@@ -151,6 +159,17 @@ class Modes:
         out = np.zeros((nm, nm))
         _check(load().bz_modes_beta(self._h, out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+
+class FastModes(Modes):
+    """Kernel modes of the fast spectral (Carleman) form (build_fast_modes):
+    2-D Maxwell molecules, ``ndirs`` collision directions.  Accepted by every
+    call that takes a Modes object."""
+
+    def __init__(self, grid, ndirs, b0=0.0):
+        h = ctypes.c_void_p()
+        _check(load().build_fast_modes(grid._h, float(b0), int(ndirs), ctypes.byref(h)))
+        super().__init__(grid, 0.0, _handle=h)
 
 
 def collide_batch(modes, f, Q=None, precision="fp32", conserve=False, check_input=False, stream=None):

@@ -28,8 +28,10 @@ int cuda_fail(cudaError_t e, const char *what) {
 int grid_create(int dim, int N, double L, bz_grid **out);
 void grid_destroy(bz_grid *g);
 int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **out);
+int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out);
 void modes_destroy(bz_modes *m);
 double beta_host(const bz_modes *m, const int *l, const int *mm);
+double fast_beta_host(const bz_modes *m, int64_t li, int64_t mi);
 
 namespace {
 
@@ -218,7 +220,15 @@ int phase_forward(const bz_modes *m, int precision, const void *f, void *fh, int
 
 int phase_modesum(const bz_modes *m, int precision, const void *fh, void *qh, int64_t n, cudaStream_t st) {
     const GridView &v = m->g->v;
-    if (precision == BZ_FP64 && modesum64_available(m)) {
+    if (m->method == 1 && precision == BZ_FP64) {
+        BZ_LAUNCH("fast_f64", st,
+                  launch_fast_f64(m, static_cast<const double2 *>(fh), static_cast<double2 *>(qh), n, st),
+                  "collide: fast spectral convolutions");
+    } else if (m->method == 1) {
+        BZ_LAUNCH("fast_f32", st,
+                  launch_fast_f32(m, static_cast<const float2 *>(fh), static_cast<float2 *>(qh), n, st),
+                  "collide: fast spectral convolutions");
+    } else if (precision == BZ_FP64 && modesum64_available(m)) {
         BZ_LAUNCH("modesum_f64", st,
                   launch_modesum64(m, static_cast<const double2 *>(fh), static_cast<double2 *>(qh), n, st),
                   "collide: mode sum");
@@ -494,6 +504,10 @@ int build_kernel_modes(const bz_grid *g, double gamma, double b0, int quad_nodes
         return modes_create(g, gamma, b0, quad_nodes, out);
     }
     return modes_create(g, gamma, b0, quad_nodes, out);
+}
+
+int build_fast_modes(const bz_grid *g, double b0, int n_dirs, bz_modes **out) {
+    return fast_modes_create(g, b0, n_dirs, out);
 }
 
 int collide_batch(const bz_modes *m, int precision, int flags, const void *f, void *Q, int64_t n_cells,
@@ -819,6 +833,15 @@ int bz_modes_info(const bz_modes *m, int64_t out[8]) {
     return BZ_OK;
 }
 
+int bz_fast_info(const bz_modes *m, int64_t out[4]) {
+    if (!m || !out) return fail(BZ_EINVAL, "bz_fast_info: NULL argument");
+    out[0] = m->method;
+    out[1] = m->method == 1 ? m->ndirs : 0;
+    out[2] = m->method == 1 ? fast_pad_length(m->g->v.N) : 0;
+    out[3] = m->method == 1 ? fast_cells_per_cta(m->g->v.N) : 0;
+    return BZ_OK;
+}
+
 int bz_modes_beta(const bz_modes *m, double *out) {
     if (!m || !out) return fail(BZ_EINVAL, "bz_modes_beta: NULL argument");
     const GridView &v = m->g->v;
@@ -837,7 +860,7 @@ int bz_modes_beta(const bz_modes *m, double *out) {
                 kk[i] = l[i] + mm[i];
                 if (kk[i] < -v.h || kk[i] > v.h) ok = false;
             }
-            out[li * v.nm + mi] = ok ? beta_host(m, l, mm) : 0.0;
+            out[li * v.nm + mi] = !ok ? 0.0 : m->method == 1 ? fast_beta_host(m, li, mi) : beta_host(m, l, mm);
         }
     }
     return BZ_OK;

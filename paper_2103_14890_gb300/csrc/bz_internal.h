@@ -72,6 +72,14 @@ struct bz_modes {
     int64_t pairs_sym;   // unordered pairs per cell (algorithmic unit)
     int tile_dft;        // 1: the tile FFT kernels of k_dft32.cu serve this grid
     double scale;        // s^(d + gamma)
+    // fast spectral (Carleman) form, k_fast.cu: method 1 replaces the mode sum
+    // of eq. CF1 by ndirs + 1 FFT convolutions with the direction factors
+    // [(ndirs + 1)][M][M] complex: (alpha_p + i alpha'_p)(k), then (1 + i Lambda)(k)
+    int method;          // 0: eq. KM / eq. CF1 direct sum; 1: fast form
+    int ndirs;
+    double *h_fast;      // host FP64 copy (interleaved re, im)
+    double2 *d_fast64;
+    float2 *d_fast32;
 };
 
 namespace bz {
@@ -137,6 +145,14 @@ cudaError_t launch_modesum32_part(const bz_modes *m, int v, const float2 *fhat, 
                                   cudaStream_t st);
 cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *const *fhat, float2 *const *Qhat,
                                    const int64_t *n, int count, cudaStream_t st);
+
+// ---- fast spectral form (k_fast.cu), 2-D, N in {8, 16, 24, 32} ------------
+bool fast_supported(const GridView &g);
+int fast_pad_length(int N);        // P of the zero-padded convolution grid
+int fast_cells_per_cta(int N);
+int fast_setup();                  // twiddles of k_fast.cu on the current device
+cudaError_t launch_fast_f32(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st);
+cudaError_t launch_fast_f64(const bz_modes *m, const double2 *fhat, double2 *Qhat, int64_t n, cudaStream_t st);
 
 // ---- kernels (k_modesum.cu) -----------------------------------------------
 cudaError_t launch_modesum_generic_f64(const GridView &g, const double *F, int bcols,

@@ -202,6 +202,7 @@ void grid_destroy(bz_grid *g) {
 }
 
 int modes_build_fp32_tables(bz_modes *m);   // k_modesum32.cu host part
+void modes_destroy(bz_modes *m);
 int64_t symmetric_pair_count(const GridView &g);
 
 int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **out) {
@@ -256,8 +257,89 @@ int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **o
     return BZ_OK;
 }
 
+// Fast spectral form (Sec. 3.3, eq. defQBCarleman / eq. Btilde / eq. FKM /
+// eq. ode), 2-D Maxwell molecules |q| sigma = b0.  The Carleman weight is the
+// constant 2 b0; with x = rho e_theta, y = rho' e_theta^perp (theta in
+// [0, pi), |rho|, |rho'| <= R, R = 2 lambda pi the truncation radius),
+//   B_F(l,m) = 2 b0 int_0^pi phi(l.e_theta) phi(m.e_theta^perp) dtheta,
+//   phi(xi) = int_{-R}^{R} e^{i rho xi} drho = 2 sin(R xi) / xi,
+// and the rectangle rule on theta_p = p pi / A gives the direction factors
+// alpha_p(k) = (2 pi b0 / A) phi(k.e_p), alpha'_p(k) = phi(k.e_p^perp).
+// The loss weight is Lambda(m) = B_F(m,m) = sum_p alpha_p(m) alpha'_p(m).
+int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out) {
+    if (!out) return fail(BZ_EINVAL, "build_fast_modes: out is NULL");
+    *out = nullptr;
+    if (!g) return fail(BZ_EINVAL, "build_fast_modes: grid is NULL");
+    if (ndirs < 1 || ndirs > 1024) return fail(BZ_EINVAL, "build_fast_modes: n_dirs in [1, 1024]");
+    const GridView &v = g->v;
+    if (!fast_supported(v))
+        return fail(BZ_ENOTSUP, "build_fast_modes: the fast form is built for 2-D grids with N in {8, 16, 24, 32}");
+    bz_modes *m = (bz_modes *)calloc(1, sizeof(bz_modes));
+    if (!m) return fail(BZ_ENOMEM, "build_fast_modes: host allocation");
+    m->g = g;
+    m->gamma = 0.0;
+    m->b0 = (b0 > 0.0) ? b0 : 1.0 / (2.0 * M_PI);
+    m->scale = pow(v.s, 2.0);
+    m->method = 1;
+    m->ndirs = ndirs;
+    m->variant = -1;
+    m->variant64 = -1;
+    m->pairs_sym = symmetric_pair_count(v);
+    const int M = v.M, h = v.h;
+    const size_t nmm = (size_t)M * M;
+    const double R = 2.0 * (2.0 / (3.0 + sqrt(2.0))) * M_PI;
+    auto phi = [R](double xi) { return xi == 0.0 ? 2.0 * R : 2.0 * sin(R * xi) / xi; };
+    const double wa = 2.0 * M_PI * m->b0 / ndirs;
+    std::vector<double> cf(2 * (ndirs + 1) * nmm, 0.0), lam(nmm, 0.0);
+    for (int p = 0; p < ndirs; ++p) {
+        const double th = M_PI * p / ndirs, ct = cos(th), st = sin(th);
+        for (int k1 = -h; k1 <= h; ++k1)
+            for (int k2 = -h; k2 <= h; ++k2) {
+                const size_t i = (size_t)(k1 + h) * M + (k2 + h);
+                const double a = wa * phi(k1 * ct + k2 * st);      // k . e_p
+                const double b = phi(-k1 * st + k2 * ct);          // k . e_p^perp
+                cf[2 * ((size_t)p * nmm + i)] = a;
+                cf[2 * ((size_t)p * nmm + i) + 1] = b;
+                lam[i] += a * b;
+            }
+    }
+    for (size_t i = 0; i < nmm; ++i) {
+        cf[2 * ((size_t)ndirs * nmm + i)] = 1.0;
+        cf[2 * ((size_t)ndirs * nmm + i) + 1] = lam[i];
+    }
+    std::vector<float> cf32(cf.size());
+    for (size_t i = 0; i < cf.size(); ++i) cf32[i] = (float)cf[i];
+    m->h_fast = (double *)malloc(sizeof(double) * cf.size());
+    cudaError_t e = m->h_fast ? cudaSuccess : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) {
+        memcpy(m->h_fast, cf.data(), sizeof(double) * cf.size());
+        e = cudaMalloc(&m->d_fast64, sizeof(double) * cf.size());
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_fast32, sizeof(float) * cf.size());
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_fast64, cf.data(), sizeof(double) * cf.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_fast32, cf32.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        modes_destroy(m);
+        return cuda_fail(e, "build_fast_modes: direction factors");
+    }
+    int rc = fast_setup();
+    if (rc == BZ_OK && dft32_tile_supported(v)) {
+        rc = dft32_setup();
+        m->tile_dft = rc == BZ_OK;
+    }
+    if (rc != BZ_OK) {
+        modes_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return BZ_OK;
+}
+
 void modes_destroy(bz_modes *m) {
     if (!m) return;
+    cudaFree(m->d_fast64);
+    cudaFree(m->d_fast32);
+    free(m->h_fast);
     cudaFree(m->d_F64);
     cudaFree(m->d_F32);
     cudaFree(m->w64);
@@ -281,6 +363,16 @@ double beta_host(const bz_modes *m, const int *l, const int *mm) {
         c2 += 4 * mm[i] * mm[i];
     }
     return m->h_F[(size_t)a2 * m->bcols + b2] - m->h_F[c2];
+}
+
+// beta-hat_F(l,m) = B_F(l,m) - Lambda(m) of the fast form, from the direction
+// factors (flat mode indices of K_h, 2-D).
+double fast_beta_host(const bz_modes *m, int64_t li, int64_t mi) {
+    const size_t nmm = (size_t)m->g->v.nm;
+    double acc = 0.0;
+    for (int p = 0; p < m->ndirs; ++p)
+        acc += m->h_fast[2 * (p * nmm + li)] * m->h_fast[2 * (p * nmm + mi) + 1];
+    return acc - m->h_fast[2 * ((size_t)m->ndirs * nmm + mi) + 1];
 }
 
 // Unordered pairs {l, m} with l + m = k summed per cell by the symmetric

@@ -15,6 +15,7 @@
 
 #include "bz_device.cuh"
 #include "bz_internal.h"
+#include "fft_reg.cuh"
 
 namespace bz {
 
@@ -97,52 +98,6 @@ __device__ __forceinline__ void inv32_epilogue(T (&q)[N], int64_t cell, int lane
 // complex length-N/2 inverse FFT.  All loops are unrolled with compile-time
 // indices, so the data stay in registers and the twiddles are constant-bank
 // operands.
-
-__constant__ float2 c_w32[32];          // e^{-2 pi i k / 32}, k = 0..31
-__constant__ double2 c_w32d[32];
-
-template <typename V> __device__ __forceinline__ V tw32(int k);
-template <> __device__ __forceinline__ float2 tw32<float2>(int k) { return c_w32[k]; }
-template <> __device__ __forceinline__ double2 tw32<double2>(int k) { return c_w32d[k]; }
-
-constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
-constexpr int bitrev(int i, int bits) {
-    int r = 0;
-    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
-    return r;
-}
-
-// In-place radix-2 decimation-in-time FFT of length L <= 32 whose input sits
-// in bit-reversed order; output in natural order.  SIGN = -1: sum x_n
-// e^{-2 pi i k n / L}; SIGN = +1: sum x_n e^{+2 pi i k n / L} (unnormalised).
-template <int L, int SIGN, typename V>
-__device__ __forceinline__ void fft_dit(V (&a)[L]) {
-    using S = decltype(V::x);
-    using V2 = V;
-#pragma unroll
-    for (int m = 1; m < L; m <<= 1) {
-#pragma unroll
-        for (int g = 0; g < L; g += 2 * m) {
-#pragma unroll
-            for (int j = 0; j < m; ++j) {
-                const V2 b = a[g + j + m];
-                V2 t;
-                if (j == 0) {
-                    t = b;
-                } else if (2 * j == m) {                       // twiddle -i (forward) or +i (inverse)
-                    t = SIGN < 0 ? cmk<V2>(b.y, -b.x) : cmk<V2>(-b.y, b.x);
-                } else {
-                    const V w = tw32<V>(j * (32 / (2 * m)));
-                    const S wy = SIGN < 0 ? w.y : -w.y;    // conj for the inverse
-                    t = cmk<V2>(b.x * w.x - b.y * wy, b.x * wy + b.y * w.x);
-                }
-                const V2 u = a[g + j];
-                a[g + j] = cmk<V2>(u.x + t.x, u.y + t.y);
-                a[g + j + m] = cmk<V2>(u.x - t.x, u.y - t.y);
-            }
-        }
-    }
-}
 
 // One CTA handles C cells (C = 32: a whole 32-cell tile of the Fourier layout,
 // or C = 16: half of one, so that two CTAs fit an SM and one's memory traffic
@@ -296,67 +251,6 @@ fft_inv32_kernel(const typename C2<T>::type *__restrict__ Qhat, T *__restrict__ 
 // n1, twiddles omega_L^(n2 k1), then Q-point FFTs over n2; output index
 // k1 + 3 k2).  A 48-column cell does not fit one warp, so the column stages
 // use TPC = 32 or 64 threads per cell (one or two whole warps).
-
-__constant__ float2 c_w48[48];          // e^{-2 pi i k / 48}, k = 0..47
-__constant__ double2 c_w48d[48];
-
-template <typename V> __device__ __forceinline__ V tw48(int k);
-template <> __device__ __forceinline__ float2 tw48<float2>(int k) { return c_w48[k]; }
-template <> __device__ __forceinline__ double2 tw48<double2>(int k) { return c_w48d[k]; }
-
-// Transform of length L (2^p <= 32, or 3 * 2^p <= 48) from natural to
-// natural order; SIGN as in fft_dit.
-template <int L, int SIGN, typename V>
-__device__ __forceinline__ void fft_nat(V (&a)[L]) {
-    using S = decltype(V::x);
-    using V2 = V;
-    if constexpr ((L & (L - 1)) == 0) {
-        V2 b[L];
-#pragma unroll
-        for (int i = 0; i < L; ++i) b[bitrev(i, ilog2(L))] = a[i];
-        fft_dit<L, SIGN>(b);
-#pragma unroll
-        for (int i = 0; i < L; ++i) a[i] = b[i];
-    } else {
-        static_assert(L % 3 == 0 && L <= 48, "length 3 * 2^p <= 48");
-        constexpr int Q = L / 3;
-        constexpr S kS3 = (S)0.866025403784438647;    // sqrt(3) / 2
-        V2 y0[Q], y1[Q], y2[Q];
-#pragma unroll
-        for (int n2 = 0; n2 < Q; ++n2) {
-            const V2 p = a[n2], q = a[Q + n2], r = a[2 * Q + n2];
-            const S sx = q.x + r.x, sy = q.y + r.y, dx = q.x - r.x, dy = q.y - r.y;
-            y0[n2] = cmk<V2>(p.x + sx, p.y + sy);
-            const S mx = p.x - (S)0.5 * sx, my = p.y - (S)0.5 * sy;
-            // -i (sqrt3/2) d for the forward transform, +i (sqrt3/2) d for the inverse
-            const S ix = SIGN < 0 ? kS3 * dy : -kS3 * dy, iy = SIGN < 0 ? -kS3 * dx : kS3 * dx;
-            V2 u1 = cmk<V2>(mx + ix, my + iy), u2 = cmk<V2>(mx - ix, my - iy);
-            if (n2 > 0) {
-                const V w1 = tw48<V>(n2 * (48 / L)), w2 = tw48<V>(2 * n2 * (48 / L));
-                const S w1y = SIGN < 0 ? w1.y : -w1.y, w2y = SIGN < 0 ? w2.y : -w2.y;
-                u1 = cmk<V2>(u1.x * w1.x - u1.y * w1y, u1.x * w1y + u1.y * w1.x);
-                u2 = cmk<V2>(u2.x * w2.x - u2.y * w2y, u2.x * w2y + u2.y * w2.x);
-            }
-            y1[n2] = u1;
-            y2[n2] = u2;
-        }
-        fft_nat<Q, SIGN>(y0);
-        fft_nat<Q, SIGN>(y1);
-        fft_nat<Q, SIGN>(y2);
-#pragma unroll
-        for (int k2 = 0; k2 < Q; ++k2) {
-            a[3 * k2] = y0[k2];
-            a[3 * k2 + 1] = y1[k2];
-            a[3 * k2 + 2] = y2[k2];
-        }
-    }
-}
-
-// e^{-2 pi i k / N} for N in {16, 24, 32, 48}
-template <int N, typename V> __device__ __forceinline__ V tw(int k) {
-    if constexpr (N == 16 || N == 32) return tw32<V>(k * (32 / N));
-    else return tw48<V>(k * (48 / N));
-}
 
 template <int N> constexpr int threads_per_cell() { return N <= 32 ? 32 : 64; }
 
@@ -654,20 +548,7 @@ bool dft32_tile_supported(const GridView &g) {
 // Twiddles of the FFT kernels on the current device (constant memory is per
 // device, so this runs for every modes handle, on its device).
 int dft32_setup() {
-    float2 w32[32], w48[48];
-    double2 d32[32], d48[48];
-    for (int k = 0; k < 32; ++k) {
-        d32[k] = make_double2(cos(2.0 * M_PI * k / 32), -sin(2.0 * M_PI * k / 32));
-        w32[k] = make_float2((float)d32[k].x, (float)d32[k].y);
-    }
-    for (int k = 0; k < 48; ++k) {
-        d48[k] = make_double2(cos(2.0 * M_PI * k / 48), -sin(2.0 * M_PI * k / 48));
-        w48[k] = make_float2((float)d48[k].x, (float)d48[k].y);
-    }
-    cudaError_t e = cudaMemcpyToSymbol(c_w32, w32, sizeof w32);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w48, w48, sizeof w48);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w32d, d32, sizeof d32);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w48d, d48, sizeof d48);
+    cudaError_t e = upload_fft_twiddles();
     if (e != cudaSuccess) return cuda_fail(e, "build_kernel_modes: FFT twiddles");
     return BZ_OK;
 }

@@ -1,0 +1,225 @@
+// k_fast.cu -- the fast spectral form of the collision operator (Sec. 3.3,
+// Carleman representation: eq. defQBCarleman, eq. Btilde, eq. FKM, eq. ode)
+// for 2-D Maxwell molecules, evaluated as FFT convolutions.
+//
+// With the direction decomposition B_F(l,m) ~ sum_p alpha_p(l) alpha'_p(m)
+// over A collision directions, the mode sum of eq. ode is
+//   Q-hat_k = sum_p sum_{l+m=k} (alpha_p f-hat)_l (alpha'_p f-hat)_m
+//           - sum_{l+m=k} f-hat_l (Lambda f-hat)_m,     Lambda(m) = B_F(m,m),
+// A + 1 products of band-limited functions.  Each product is formed on a
+// zero-padded P x P grid with P >= 3h + 1, where the circular convolution of
+// two spectra supported in K_h equals the linear one at every k in K_h.
+// alpha_p, alpha'_p and Lambda are real and even and f-hat is Hermitian, so
+// a = IDFT(alpha_p f-hat) and b = IDFT(alpha'_p f-hat) are real: one complex
+// inverse transform of (alpha_p + i alpha'_p) f-hat yields a + i b and the
+// product is Re * Im.  The sum g of the A + 1 products goes back through one
+// real forward transform; Q-hat keeps k in K_h with k_1 >= 0 (tiled layout).
+//
+// A CTA takes C cells with C * P = 96 threads.  Per direction: pass A, one
+// thread per (cell, k1 in [-h, h]) transforms along k2 into Y (shared);
+// pass B, one thread per (cell, j2) transforms Y along k1 and accumulates the
+// product into g (shared; each thread owns its column of g for the whole
+// call).  Then pass C (thread per (cell, j2)) transforms g along j1 for
+// k1 = 0..h, and pass D (thread per (cell, k1)) along j2, scales by P^-2 and
+// stores Q-hat.  Every shared-memory array keeps the cell index fastest, so
+// consecutive threads touch consecutive words.
+#include <limits.h>
+
+#include "bz_device.cuh"
+#include "bz_internal.h"
+#include "fft_reg.cuh"
+
+namespace bz {
+
+namespace {
+
+constexpr int kFastThreads = 96;
+
+// Smallest register-FFT length >= n (lengths 2^p <= 32 and 3 * 2^p <= 48).
+constexpr int fast_pad(int n) {
+    return n <= 2 ? 2 : n <= 3 ? 3 : n <= 4 ? 4 : n <= 6 ? 6 : n <= 8 ? 8 : n <= 12 ? 12
+         : n <= 16 ? 16 : n <= 24 ? 24 : n <= 32 ? 32 : n <= 48 ? 48 : 0;
+}
+
+template <int N> struct FastShape {
+    static constexpr int H = N / 2 - 1, M = 2 * H + 1;
+    static constexpr int P = fast_pad(3 * H + 1);
+    static constexpr int C = kFastThreads / P;
+    static_assert(P > 0 && C * P == kFastThreads, "grid not served by the fast kernel");
+    static constexpr int TS = P * C + C;                       // padded k1 stride of pass C/D
+    static constexpr int nYa = M * P * C, nYb = (H + 1) * TS;
+    static constexpr int nY = nYa > nYb ? nYa : nYb;           // complex
+    static constexpr int nF = (H + 1) * M * C;                 // complex
+    static constexpr int nG = P * P * C;                       // real
+};
+
+template <typename T, int N> constexpr size_t fast_smem() {
+    using Sh = FastShape<N>;
+    return 2 * sizeof(T) * (size_t)(Sh::nY + Sh::nF) + sizeof(T) * (size_t)Sh::nG;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kFastThreads)
+fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>::type *__restrict__ qh,
+                    const typename C2<T>::type *__restrict__ coef, int ndirs, int64_t nhalf, int64_t n) {
+    using V2 = typename C2<T>::type;
+    using S = T;
+    using Sh = FastShape<N>;
+    constexpr int H = Sh::H, M = Sh::M, P = Sh::P, C = Sh::C, TS = Sh::TS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2 *Y = reinterpret_cast<V2 *>(smem_raw);     // pass A/B: [P][M][C]; pass C/D: [H+1][TS]
+    V2 *F = Y + Sh::nY;                           // half spectrum [H+1][M][C]
+    S *G = reinterpret_cast<S *>(F + Sh::nF);     // products [P][P][C]
+    const int tid = threadIdx.x;
+    const int64_t cell0 = (int64_t)blockIdx.x * C;
+
+    for (int i = tid; i < Sh::nF; i += kFastThreads) {
+        const int c = i % C, mode = i / C;
+        const int64_t cell = cell0 + c;
+        F[i] = cell < n ? fh[tiled_index(cell, mode, nhalf)] : cmk<V2>((S)0., (S)0.);
+    }
+    __syncthreads();
+
+    const int c = tid % C, col = tid / C;
+    for (int p = 0; p <= ndirs; ++p) {            // p == ndirs: the loss term
+        // pass A: (cell c, row k1): along k2, sum_k2 w(k) f-hat(k) e^{+2 pi i j2 k2 / P}
+        if (tid < C * M) {
+            const int k1 = col - H;
+            const V2 *crow = coef + ((size_t)p * M + (k1 + H)) * M;
+            V2 a[P];
+#pragma unroll
+            for (int j = 0; j < P; ++j) a[j] = cmk<V2>((S)0., (S)0.);
+#pragma unroll
+            for (int k2 = -H; k2 <= H; ++k2) {
+                V2 fv;
+                if (k1 >= 0) {
+                    fv = F[(k1 * M + k2 + H) * C + c];
+                } else {                          // f-hat(k) = conj f-hat(-k)
+                    const V2 t = F[(-k1 * M - k2 + H) * C + c];
+                    fv = cmk<V2>(t.x, -t.y);
+                }
+                const V2 w = __ldg(crow + k2 + H);
+                a[(k2 + P) % P] = cmk<V2>(w.x * fv.x - w.y * fv.y, w.x * fv.y + w.y * fv.x);
+            }
+            fft_nat<P, +1>(a);
+#pragma unroll
+            for (int j2 = 0; j2 < P; ++j2) Y[(j2 * M + k1 + H) * C + c] = a[j2];
+        }
+        __syncthreads();
+        // pass B: (cell c, column j2): along k1, then g += Re * Im (gain) or -= (loss)
+        {
+            const int j2 = col;
+            V2 b[P];
+#pragma unroll
+            for (int j = 0; j < P; ++j) b[j] = cmk<V2>((S)0., (S)0.);
+#pragma unroll
+            for (int k1 = -H; k1 <= H; ++k1) b[(k1 + P) % P] = Y[(j2 * M + k1 + H) * C + c];
+            fft_nat<P, +1>(b);
+            S *g = G + j2 * C + c;
+            if (p == 0) {
+#pragma unroll
+                for (int j1 = 0; j1 < P; ++j1) g[j1 * P * C] = b[j1].x * b[j1].y;
+            } else if (p < ndirs) {
+#pragma unroll
+                for (int j1 = 0; j1 < P; ++j1) g[j1 * P * C] = fma(b[j1].x, b[j1].y, g[j1 * P * C]);
+            } else {
+#pragma unroll
+                for (int j1 = 0; j1 < P; ++j1) g[j1 * P * C] = fma(-b[j1].x, b[j1].y, g[j1 * P * C]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // pass C: (cell c, column j2): real transform of g along j1, k1 = 0..h,
+    // through a complex length-P/2 FFT of (g[2q] + i g[2q+1]) and the
+    // even/odd untangling X(k) = E(k) + e^{-2 pi i k / P} O(k)
+    {
+        constexpr int P2 = P / 2;
+        const int j2 = col;
+        const S *g = G + j2 * C + c;
+        V2 z[P2];
+#pragma unroll
+        for (int q = 0; q < P2; ++q) z[q] = cmk<V2>(g[(2 * q) * P * C], g[(2 * q + 1) * P * C]);
+        fft_nat<P2, -1>(z);
+#pragma unroll
+        for (int k1 = 0; k1 <= H; ++k1) {
+            const V2 zk = z[k1 % P2], zc = z[(P2 - k1) % P2];
+            const S ex = (S)0.5 * (zk.x + zc.x), ey = (S)0.5 * (zk.y - zc.y);
+            const S ox = (S)0.5 * (zk.y + zc.y), oy = -(S)0.5 * (zk.x - zc.x);
+            const V2 w = twl<P, V2>(k1);
+            Y[k1 * TS + j2 * C + c] = cmk<V2>(ex + (w.x * ox - w.y * oy), ey + (w.x * oy + w.y * ox));
+        }
+    }
+    __syncthreads();
+    // pass D: (cell c, row k1 >= 0): along j2, keep k2 in [-h, h], scale P^-2
+    if (tid < C * (H + 1)) {
+        const int k1 = col;
+        V2 a[P];
+#pragma unroll
+        for (int j2 = 0; j2 < P; ++j2) a[j2] = Y[k1 * TS + j2 * C + c];
+        fft_nat<P, -1>(a);
+        const int64_t cell = cell0 + c;
+        if (cell < n) {
+            const S sc = (S)(1.0 / ((double)P * (double)P));
+#pragma unroll
+            for (int k2 = -H; k2 <= H; ++k2) {
+                const V2 v = a[(k2 + P) % P];
+                qh[tiled_index(cell, (int64_t)k1 * M + k2 + H, nhalf)] = cmk<V2>(v.x * sc, v.y * sc);
+            }
+        }
+    }
+}
+
+template <typename T, int N>
+cudaError_t launch_fast_n(const GridView &g, const typename C2<T>::type *fh, typename C2<T>::type *qh,
+                          const typename C2<T>::type *coef, int ndirs, int64_t n, cudaStream_t st) {
+    constexpr size_t sm = fast_smem<T, N>();
+    constexpr int C = FastShape<N>::C;
+    const int64_t blocks = (n + C - 1) / C;
+    if (blocks > INT_MAX) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fast_collide_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    fast_collide_kernel<T, N><<<(unsigned)blocks, kFastThreads, sm, st>>>(fh, qh, coef, ndirs, g.nhalf, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fast_any(const bz_modes *m, const typename C2<T>::type *fh, typename C2<T>::type *qh, int64_t n,
+                            cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const GridView &g = m->g->v;
+    const void *cv = sizeof(T) == 8 ? static_cast<const void *>(m->d_fast64) : static_cast<const void *>(m->d_fast32);
+    const auto *coef = static_cast<const typename C2<T>::type *>(cv);
+    switch (g.N) {
+        case 8: return launch_fast_n<T, 8>(g, fh, qh, coef, m->ndirs, n, st);
+        case 16: return launch_fast_n<T, 16>(g, fh, qh, coef, m->ndirs, n, st);
+        case 24: return launch_fast_n<T, 24>(g, fh, qh, coef, m->ndirs, n, st);
+        case 32: return launch_fast_n<T, 32>(g, fh, qh, coef, m->ndirs, n, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool fast_supported(const GridView &g) {
+    return g.dim == 2 && (g.N == 8 || g.N == 16 || g.N == 24 || g.N == 32);
+}
+
+int fast_pad_length(int N) { return fast_pad(3 * (N / 2 - 1) + 1); }
+int fast_cells_per_cta(int N) { return kFastThreads / fast_pad_length(N); }
+
+int fast_setup() {
+    cudaError_t e = upload_fft_twiddles();
+    if (e != cudaSuccess) return cuda_fail(e, "build_fast_modes: FFT twiddles");
+    return BZ_OK;
+}
+
+cudaError_t launch_fast_f32(const bz_modes *m, const float2 *fh, float2 *qh, int64_t n, cudaStream_t st) {
+    return launch_fast_any<float>(m, fh, qh, n, st);
+}
+cudaError_t launch_fast_f64(const bz_modes *m, const double2 *fh, double2 *qh, int64_t n, cudaStream_t st) {
+    return launch_fast_any<double>(m, fh, qh, n, st);
+}
+
+}  // namespace bz

@@ -135,7 +135,6 @@ __device__ __forceinline__ void block_pass(typename C2<T>::type (&win)[2 * RR],
     for (int s = 0; s < RR; ++s) {
         const V2 fl = lp[s * DIR * CS];
         T wv[RR];
-#pragma unroll
         if constexpr (RR % 4 == 0) {
 #pragma unroll
             for (int q = 0; q < RR; q += 4) load_w4(wv + q, wb + s * WS + q);

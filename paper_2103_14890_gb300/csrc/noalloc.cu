@@ -73,8 +73,9 @@ int run_with_scratch(const bz_modes *m, int precision, int flags, const void *f,
         e = m->tile_dft ? launch_dft64_forward_tile(v, static_cast<const double *>(f), fh, n, st)
                         : launch_dft_forward_f64(v, g->d_E64, static_cast<const double *>(f), fh, n, st);
         if (e == cudaSuccess)
-            e = modesum64_available(m) ? launch_modesum64(m, fh, qh, n, st)
-                                       : launch_modesum_generic_f64(v, m->d_F64, m->bcols, fh, qh, n, st);
+            e = m->method == 1          ? launch_fast_f64(m, fh, qh, n, st)
+                : modesum64_available(m) ? launch_modesum64(m, fh, qh, n, st)
+                                         : launch_modesum_generic_f64(v, m->d_F64, m->bcols, fh, qh, n, st);
         if (e == cudaSuccess)
             e = m->tile_dft ? launch_dft64_inverse_tile(v, qh, static_cast<double *>(Q), n, m->scale, g->cinv, ep, st)
                             : launch_dft_inverse_f64(v, g->d_E64, qh, static_cast<double *>(Q), n, m->scale, g->cinv,
@@ -86,8 +87,9 @@ int run_with_scratch(const bz_modes *m, int precision, int flags, const void *f,
         e = m->tile_dft ? launch_dft32_forward_tile(v, fin, fh, n, st)
                     : launch_dft_forward_f32(v, g->d_E32, fin, fh, n, st);
         if (e == cudaSuccess)
-            e = modesum32_available(m) ? launch_modesum32(m, fh, qh, n, st)
-                                          : launch_modesum_generic_f32(v, m->d_F32, m->bcols, fh, qh, n, st);
+            e = m->method == 1          ? launch_fast_f32(m, fh, qh, n, st)
+                : modesum32_available(m) ? launch_modesum32(m, fh, qh, n, st)
+                                         : launch_modesum_generic_f32(v, m->d_F32, m->bcols, fh, qh, n, st);
         if (e == cudaSuccess)
             e = m->tile_dft ? launch_dft32_inverse_tile(v, qh, qout, n, m->scale, g->cinv, ep, st)
                         : launch_dft_inverse_f32(v, g->d_E32, qh, qout, n, m->scale, g->cinv, ep, st);

@@ -44,6 +44,9 @@ def test_host_side_argument_errors(lib):
     assert lib.bz_modes_info(None, info) == b.EINVAL
     assert lib.bz_modes_beta(None, None) == b.EINVAL
     assert lib.bz_profile_read(None, 0, None, None, 0) == b.EINVAL
+    assert lib.build_fast_modes(None, 0.0, 8, ctypes.byref(out)) == b.EINVAL
+    assert lib.build_fast_modes(None, 0.0, 8, None) == b.EINVAL
+    assert lib.bz_fast_info(None, (ctypes.c_int64 * 4)()) == b.EINVAL
 
 
 def test_missing_library_fails_loudly(tmp_path):
