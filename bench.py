@@ -33,6 +33,27 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop 
 MODESUM_TRAFFIC_65536 = 251873792 + 200191232 + 9887744 + 0
 METRIC = "cell-collision evals/s at N_v=32^2: mixed-precision vs FP64 GPU, rel-L2 err stated"
 WORKLOAD = "65536 cells, 2-D 32x32 velocity grid on [-10,10]^2, VHS kernel, shifted Maxwellians Mach 0-3"
+FAST_WORKLOAD = ("65536 cells, 2-D 32x32 velocity grid on [-10,10]^2, Maxwell molecules, fast spectral "
+                 "(Carleman) form with %d directions, shifted Maxwellians Mach 0-3")
+
+
+def fast_flops_per_cell(N, ndirs):
+    """Algorithmic FP32 work of one fast-form evaluation (mode-sum phase):
+    nominal 5 n log2 n flops per complex length-n FFT; per direction (and once
+    more for the loss term) one complex multiply per retained mode, 2h+1 row
+    and P column transforms of length P, and one multiply-add per padded
+    point; then P/2-length real transforms of the P columns (plus the 10-flop
+    untangling of each kept row) and h+1 row transforms.  For an even number
+    of directions, direction p + A/2 gives direction p's product, so A/2
+    products are formed."""
+    h = N // 2 - 1
+    M = 2 * h + 1
+    P = next(L for L in (2, 3, 4, 6, 8, 12, 16, 24, 32, 48) if L >= 3 * h + 1)
+    fft = lambda n: 5.0 * n * math.log2(n)
+    per_dir = 6.0 * M * M + (M + P) * fft(P) + 2.0 * P * P
+    final = P * (fft(P // 2) + 10.0 * (h + 1)) + (h + 1) * fft(P)
+    nconv = ndirs // 2 if ndirs % 2 == 0 else ndirs     # paired directions share one product
+    return (nconv + 1) * per_dir + final
 
 
 def _env_rank():
@@ -93,14 +114,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(f_host, budget_s=15.0, check_idx=()):
+def cpu_baseline(f_host, budget_s=15.0, check_idx=(), ndirs=0):
     """The cpu_baseline leg: time the FP64 oracle on the host cores on a bounded
     sample of cells (the cells in check_idx plus the first cells of the batch,
     sized to about budget_s of work).  Returns the baseline entry, the sampled
-    cell indices and the oracle's Q on them (used to state the GPU error)."""
+    cell indices and the oracle's Q on them (used to state the GPU error).
+    ndirs > 0: the oracle's fast (Carleman) modes, Maxwell molecules."""
     import numpy as np
     import oracle
-    k = oracle.Kernel(2, N_V, L_BOX, GAMMA)
+    k = oracle.FastKernel(N_V, L_BOX, ndirs) if ndirs else oracle.Kernel(2, N_V, L_BOX, GAMMA)
     probe = f_host[:8].astype(np.float64)
     t0 = time.perf_counter()
     k.collide(probe)
@@ -114,7 +136,8 @@ def cpu_baseline(f_host, budget_s=15.0, check_idx=()):
     dt = time.perf_counter() - t0
     entry = {"value": len(idx) / dt, "unit": "cell-collision evals/s", "cores": oracle.num_threads(),
              "kind": "oracle",
-             "sample": "%d of the %d cells (FP64 direct sum, OpenMP over cells)" % (len(idx), len(f_host))}
+             "sample": "%d of the %d cells (FP64 %s, OpenMP over cells)" % (
+                 len(idx), len(f_host), "fast-form pair sum" if ndirs else "direct sum")}
     return entry, idx, Qr, k
 
 
@@ -160,6 +183,9 @@ def main():
     ap.add_argument("--cells", type=int, default=CELLS, help="cells per GPU (small cases for ncu captures)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the IMEX-step and grouped-batch measurements")
+    ap.add_argument("--method", default="direct", choices=["direct", "fast"],
+                    help="fast: time the fast spectral form (Maxwell molecules) as the main line instead")
+    ap.add_argument("--ndirs", type=int, default=8, help="collision directions of the fast form")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -177,7 +203,8 @@ def main():
     bz.load()
 
     grid = bz.Grid(2, N_V, L_BOX)
-    modes = bz.Modes(grid, GAMMA)
+    fast = args.method == "fast"
+    modes = bz.FastModes(grid, args.ndirs) if fast else bz.Modes(grid, GAMMA)
     cells = args.cells
     f_host = workloads.shifted_maxwellians(cells, 2, N_V, L_BOX, seed=SEED + rank).astype(np.float32)
     f = torch.from_numpy(f_host).cuda()
@@ -216,14 +243,14 @@ def main():
     ms = max_over_ranks(ms, device="cuda")          # the slowest rank sets the job's time
     value = cells * world / (ms / 1e3)
 
-    # dominant kernel: the mode sum
-    ms_name = "modesum_f32" if "modesum_f32" in prof else "modesum_f32_generic"
+    # dominant kernel: the mode sum (or the fast form's convolutions)
+    ms_name = "fast_f32" if fast else "modesum_f32" if "modesum_f32" in prof else "modesum_f32_generic"
     launches, ktot = prof.get(ms_name, (0, float("nan")))
     k_ms = ktot / max(1, launches)
     if "modesum_f32_tail" in prof:          # the last partial wave runs as a second launch
         tl, tt = prof["modesum_f32_tail"]
         k_ms += tt / max(1, tl)
-    flops_launch = 10.0 * modes.pairs_sym * cells
+    flops_launch = (fast_flops_per_cell(N_V, args.ndirs) if fast else 10.0 * modes.pairs_sym) * cells
     achieved = flops_launch / (k_ms / 1e3) / 1e12
     gpu_launches = sum(c for c, _ in prof.values())
 
@@ -244,9 +271,11 @@ def main():
         value64 = cells * world / (ms64 / 1e3)
 
     extra = {}
-    if not args.no_extra:
+    if not args.no_extra and not fast:
         extra["imex_step"] = _imex_measure(bz, workloads, barrier)
         extra["grouped"] = _group_measure(bz, workloads, barrier)
+        extra["fast_spectral"] = _fast_measure(bz, f, f_host, st, args.ndirs,
+                                               check=not args.no_cpu_baseline)
 
     # end to end: pinned host f -> device, collide, device -> pinned host Q
     e2e_val = None
@@ -366,6 +395,62 @@ def _group_measure(bz, workloads, barrier):
     return out
 
 
+def _fast_measure(bz, f, f_host, st, ndirs, check=True):
+    """The fast spectral (Carleman) form on the same 65536 cells, Maxwell
+    molecules: FP32 and FP64 throughput, the FP32 direct sum with the same
+    kernel for comparison, the fast kernel's roofline on the FP32 peak, and
+    the FP32 error against the oracle's fast modes on sampled cells."""
+    import numpy as np
+    import torch
+    cells = f.shape[0]
+    grid = bz.Grid(2, N_V, L_BOX)
+    out = {"workload": FAST_WORKLOAD % ndirs, "ndirs": ndirs}
+    mf = bz.FastModes(grid, ndirs)
+    out["pad"] = mf.pad
+    Q = torch.empty_like(f)
+    for _ in range(3):
+        bz.collide_batch(mf, f, Q, precision="fp32")
+    bz.check()
+    bz.profile(True)
+    ms = _timed(lambda: bz.collide_batch(mf, f, Q, precision="fp32"), 10, st)
+    prof = bz.profile_read()
+    bz.profile(False)
+    kl, kt = prof.get("fast_f32", (1, float("nan")))
+    k_ms = kt / max(1, kl)
+    fl = fast_flops_per_cell(N_V, ndirs) * cells
+    out["fp32"] = {"ms_per_step": ms, "cell_collision_evals_per_s": cells / (ms / 1e3),
+                   "kernel_ms": {k: v[1] / max(1, v[0]) for k, v in prof.items()}}
+    out["roofline"] = {"bound": "alu", "kernel": "fast_f32", "kernel_ms": k_ms, "flops_per_launch": fl,
+                       "achieved": fl / (k_ms / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": fl / (k_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
+                       "flop_count": "nominal 5 n log2 n per complex length-n FFT (bench.fast_flops_per_cell)"}
+    f64 = f.double()
+    Q64 = torch.empty_like(f64)
+    bz.collide_batch(mf, f64, Q64, precision="fp64")
+    ms64 = _timed(lambda: bz.collide_batch(mf, f64, Q64, precision="fp64"), 1, st)
+    out["fp64"] = {"ms_per_step": ms64, "cell_collision_evals_per_s": cells / (ms64 / 1e3)}
+    md = bz.Modes(grid, 0.0)
+    Qd = torch.empty_like(f)
+    bz.collide_batch(md, f, Qd, precision="fp32")
+    msd = _timed(lambda: bz.collide_batch(md, f, Qd, precision="fp32"), 10, st)
+    out["direct_fp32_same_kernel"] = {"ms_per_step": msd, "cell_collision_evals_per_s": cells / (msd / 1e3)}
+    out["speedup_fast_over_direct_fp32"] = msd / ms
+    bz.check()
+    out["rel_l2_fp32_vs_fp64_gpu_all_cells"] = ((Q.double() - Q64).norm() / Q64.norm()).item()
+    if check:
+        import oracle
+        k = oracle.FastKernel(N_V, L_BOX, ndirs)
+        idx = np.linspace(0, cells - 1, 12).astype(np.int64)
+        fs = f_host[idx].astype(np.float64)
+        Qr = k.collide(fs)
+        q32 = Q[torch_index(idx)].double().cpu().numpy()
+        rho = fs.sum(1, keepdims=True) * k.dv ** 2
+        out["fp32_vs_oracle"] = {"rel_l2": float(np.linalg.norm(q32 - Qr) / np.linalg.norm(Qr)),
+                                 "loss_scaled": float(np.linalg.norm(q32 - Qr) / np.linalg.norm(rho * fs)),
+                                 "cells": len(idx)}
+    return out
+
+
 def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, value64, prof, ms_name, k_ms,
             flops_launch, achieved, gpu_launches, e2e_val, clk, extra):
     import numpy as np
@@ -379,7 +464,8 @@ def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, valu
         err32_vs64 = d / Q64.norm().item()
     if not args.no_cpu_baseline:
         spread = np.linspace(0, cells - 1, 24).astype(np.int64)
-        cpu, idx, Qr, k = cpu_baseline(f_host, budget_s=15.0, check_idx=spread)
+        cpu, idx, Qr, k = cpu_baseline(f_host, budget_s=15.0, check_idx=spread,
+                                       ndirs=args.ndirs if args.method == "fast" else 0)
         ti = torch_index(idx)
         q32 = Q[ti].double().cpu().numpy()
         err32 = float(np.linalg.norm(q32 - Qr) / np.linalg.norm(Qr))
@@ -395,9 +481,12 @@ def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, valu
         "metric": METRIC, "value": value, "unit": "cell-collision evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if cells == CELLS else WORKLOAD.replace(str(CELLS), str(cells)),
+        "config": {"workload": (FAST_WORKLOAD % args.ndirs if args.method == "fast" else WORKLOAD).replace(
+                       str(CELLS), str(cells)),
                    "cells_per_gpu": cells, "N_v": N_V * N_V, "L": L_BOX,
-                   "kernel": "VHS hard spheres (gamma=1, b0=1/(2pi))", "precision_form": "fp32",
+                   "kernel": ("Maxwell molecules (gamma=0, b0=1/(2pi)), fast form, %d directions" % args.ndirs
+                              if args.method == "fast" else "VHS hard spheres (gamma=1, b0=1/(2pi))"),
+                   "precision_form": "fp32",
                    "l2": "inputs and outputs (268 MB each) exceed L2: no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "rel_l2_err": {"fp32_vs_oracle": err32, "fp64_vs_oracle": err64, "fp32_loss_scaled": loss32,
@@ -406,7 +495,7 @@ def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, valu
                       "speedup_fp32_over_fp64": value / value64} if Q64 is not None else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": MODESUM_TRAFFIC_65536 if cells == CELLS else None,
+                     "traffic": MODESUM_TRAFFIC_65536 if cells == CELLS and args.method == "direct" else None,
                      "kernel": ms_name,
                      "kernel_ms": k_ms, "flops_per_launch": flops_launch,
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
@@ -414,6 +503,7 @@ def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, valu
         "gpu_launches": gpu_launches,
         "imex_step": extra.get("imex_step"),
         "grouped": extra.get("grouped"),
+        "fast_spectral": extra.get("fast_spectral"),
         "e2e": {"value": e2e_val, "unit": "cell-collision evals/s",
                 "h2d_bytes_per_step": int(Q.numel() * 4), "d2h_bytes_per_step": int(Q.numel() * 4)},
         "clocks": clk,

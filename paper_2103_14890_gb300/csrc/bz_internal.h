@@ -73,10 +73,14 @@ struct bz_modes {
     int tile_dft;        // 1: the tile FFT kernels of k_dft32.cu serve this grid
     double scale;        // s^(d + gamma)
     // fast spectral (Carleman) form, k_fast.cu: method 1 replaces the mode sum
-    // of eq. CF1 by ndirs + 1 FFT convolutions with the direction factors
-    // [(ndirs + 1)][M][M] complex: (alpha_p + i alpha'_p)(k), then (1 + i Lambda)(k)
+    // of eq. CF1 by nconv + 1 FFT convolutions with the direction factors
+    // [(nconv + 1)][M][M] complex: (c_p alpha_p + i alpha'_p)(k), then
+    // (1 + i Lambda)(k).  For even ndirs, direction p + ndirs/2 is direction p
+    // with alpha and alpha' exchanged (same gain product), so nconv = ndirs/2
+    // and c_p = 2; for odd ndirs nconv = ndirs and c_p = 1.
     int method;          // 0: eq. KM / eq. CF1 direct sum; 1: fast form
     int ndirs;
+    int nconv;
     double *h_fast;      // host FP64 copy (interleaved re, im)
     double2 *d_fast64;
     float2 *d_fast32;

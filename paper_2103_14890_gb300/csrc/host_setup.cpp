@@ -266,6 +266,11 @@ int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **o
 // and the rectangle rule on theta_p = p pi / A gives the direction factors
 // alpha_p(k) = (2 pi b0 / A) phi(k.e_p), alpha'_p(k) = phi(k.e_p^perp).
 // The loss weight is Lambda(m) = B_F(m,m) = sum_p alpha_p(m) alpha'_p(m).
+// For even A, e_{p+A/2} = e_p^perp and e_{p+A/2}^perp = -e_p, so (with phi
+// even) alpha_{p+A/2} = w alpha'_p and alpha'_{p+A/2} = alpha_p / w,
+// w = 2 pi b0 / A: the two directions give the same gain product
+// IDFT(alpha f-hat) IDFT(alpha' f-hat), and the kernel evaluates A/2 of them
+// with weight 2 (the l <-> m symmetry of the gain sum).
 int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out) {
     if (!out) return fail(BZ_EINVAL, "build_fast_modes: out is NULL");
     *out = nullptr;
@@ -282,6 +287,9 @@ int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out) {
     m->scale = pow(v.s, 2.0);
     m->method = 1;
     m->ndirs = ndirs;
+    m->nconv = (ndirs % 2 == 0) ? ndirs / 2 : ndirs;
+    const int nconv = m->nconv;
+    const double cw = (ndirs % 2 == 0) ? 2.0 : 1.0;
     m->variant = -1;
     m->variant64 = -1;
     m->pairs_sym = symmetric_pair_count(v);
@@ -290,7 +298,7 @@ int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out) {
     const double R = 2.0 * (2.0 / (3.0 + sqrt(2.0))) * M_PI;
     auto phi = [R](double xi) { return xi == 0.0 ? 2.0 * R : 2.0 * sin(R * xi) / xi; };
     const double wa = 2.0 * M_PI * m->b0 / ndirs;
-    std::vector<double> cf(2 * (ndirs + 1) * nmm, 0.0), lam(nmm, 0.0);
+    std::vector<double> cf(2 * (nconv + 1) * nmm, 0.0), lam(nmm, 0.0);
     for (int p = 0; p < ndirs; ++p) {
         const double th = M_PI * p / ndirs, ct = cos(th), st = sin(th);
         for (int k1 = -h; k1 <= h; ++k1)
@@ -298,14 +306,16 @@ int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out) {
                 const size_t i = (size_t)(k1 + h) * M + (k2 + h);
                 const double a = wa * phi(k1 * ct + k2 * st);      // k . e_p
                 const double b = phi(-k1 * st + k2 * ct);          // k . e_p^perp
-                cf[2 * ((size_t)p * nmm + i)] = a;
-                cf[2 * ((size_t)p * nmm + i) + 1] = b;
+                if (p < nconv) {
+                    cf[2 * ((size_t)p * nmm + i)] = cw * a;
+                    cf[2 * ((size_t)p * nmm + i) + 1] = b;
+                }
                 lam[i] += a * b;
             }
     }
     for (size_t i = 0; i < nmm; ++i) {
-        cf[2 * ((size_t)ndirs * nmm + i)] = 1.0;
-        cf[2 * ((size_t)ndirs * nmm + i) + 1] = lam[i];
+        cf[2 * ((size_t)nconv * nmm + i)] = 1.0;
+        cf[2 * ((size_t)nconv * nmm + i) + 1] = lam[i];
     }
     std::vector<float> cf32(cf.size());
     for (size_t i = 0; i < cf.size(); ++i) cf32[i] = (float)cf[i];
@@ -369,10 +379,17 @@ double beta_host(const bz_modes *m, const int *l, const int *mm) {
 // factors (flat mode indices of K_h, 2-D).
 double fast_beta_host(const bz_modes *m, int64_t li, int64_t mi) {
     const size_t nmm = (size_t)m->g->v.nm;
+    const double *c = m->h_fast;
     double acc = 0.0;
-    for (int p = 0; p < m->ndirs; ++p)
-        acc += m->h_fast[2 * (p * nmm + li)] * m->h_fast[2 * (p * nmm + mi) + 1];
-    return acc - m->h_fast[2 * ((size_t)m->ndirs * nmm + mi) + 1];
+    for (int p = 0; p < m->nconv; ++p) {
+        if (m->nconv == m->ndirs) {
+            acc += c[2 * (p * nmm + li)] * c[2 * (p * nmm + mi) + 1];
+        } else {   // directions p and p + A/2 from the stored factors (alpha doubled)
+            acc += 0.5 * (c[2 * (p * nmm + li)] * c[2 * (p * nmm + mi) + 1] +
+                          c[2 * (p * nmm + li) + 1] * c[2 * (p * nmm + mi)]);
+        }
+    }
+    return acc - c[2 * ((size_t)m->nconv * nmm + mi) + 1];
 }
 
 // Unordered pairs {l, m} with l + m = k summed per cell by the symmetric

@@ -6,7 +6,9 @@
 // over A collision directions, the mode sum of eq. ode is
 //   Q-hat_k = sum_p sum_{l+m=k} (alpha_p f-hat)_l (alpha'_p f-hat)_m
 //           - sum_{l+m=k} f-hat_l (Lambda f-hat)_m,     Lambda(m) = B_F(m,m),
-// A + 1 products of band-limited functions.  Each product is formed on a
+// A + 1 products of band-limited functions (A/2 + 1 for even A: direction
+// p + A/2 is direction p with alpha and alpha' exchanged, which leaves the
+// gain product unchanged, so the host folds it into direction p's weight).  Each product is formed on a
 // zero-padded P x P grid with P >= 3h + 1, where the circular convolution of
 // two spectra supported in K_h equals the linear one at every k in K_h.
 // alpha_p, alpha'_p and Lambda are real and even and f-hat is Hermitian, so
@@ -23,6 +25,13 @@
 // k1 = 0..h, and pass D (thread per (cell, k1)) along j2, scales by P^-2 and
 // stores Q-hat.  Every shared-memory array keeps the cell index fastest, so
 // consecutive threads touch consecutive words.
+//
+// Two other organisations were measured on a GB300 and were slower at A = 8
+// (65536 cells, 32^2): two warp groups running pass A of direction p and
+// pass B of direction p - 1 at the same time on a double-buffered Y (fewer
+// CTAs per SM, idle warps at the pipeline's fill and drain: +23 %), and one
+// shared FFT body for all passes with cp.async loads of the half spectrum
+// (the paired-cell pass C it needs runs on half the threads: +3 %).
 #include <limits.h>
 
 #include "bz_device.cuh"
@@ -61,7 +70,7 @@ template <typename T, int N> constexpr size_t fast_smem() {
 template <typename T, int N>
 __global__ void __launch_bounds__(kFastThreads)
 fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>::type *__restrict__ qh,
-                    const typename C2<T>::type *__restrict__ coef, int ndirs, int64_t nhalf, int64_t n) {
+                    const typename C2<T>::type *__restrict__ coef, int nconv, int64_t nhalf, int64_t n) {
     using V2 = typename C2<T>::type;
     using S = T;
     using Sh = FastShape<N>;
@@ -81,7 +90,7 @@ fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>:
     __syncthreads();
 
     const int c = tid % C, col = tid / C;
-    for (int p = 0; p <= ndirs; ++p) {            // p == ndirs: the loss term
+    for (int p = 0; p <= nconv; ++p) {            // p == nconv: the loss term
         // pass A: (cell c, row k1): along k2, sum_k2 w(k) f-hat(k) e^{+2 pi i j2 k2 / P}
         if (tid < C * M) {
             const int k1 = col - H;
@@ -119,7 +128,7 @@ fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>:
             if (p == 0) {
 #pragma unroll
                 for (int j1 = 0; j1 < P; ++j1) g[j1 * P * C] = b[j1].x * b[j1].y;
-            } else if (p < ndirs) {
+            } else if (p < nconv) {
 #pragma unroll
                 for (int j1 = 0; j1 < P; ++j1) g[j1 * P * C] = fma(b[j1].x, b[j1].y, g[j1 * P * C]);
             } else {
@@ -172,7 +181,7 @@ fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>:
 
 template <typename T, int N>
 cudaError_t launch_fast_n(const GridView &g, const typename C2<T>::type *fh, typename C2<T>::type *qh,
-                          const typename C2<T>::type *coef, int ndirs, int64_t n, cudaStream_t st) {
+                          const typename C2<T>::type *coef, int nconv, int64_t n, cudaStream_t st) {
     constexpr size_t sm = fast_smem<T, N>();
     constexpr int C = FastShape<N>::C;
     const int64_t blocks = (n + C - 1) / C;
@@ -180,7 +189,7 @@ cudaError_t launch_fast_n(const GridView &g, const typename C2<T>::type *fh, typ
     cudaError_t e = cudaFuncSetAttribute(fast_collide_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
-    fast_collide_kernel<T, N><<<(unsigned)blocks, kFastThreads, sm, st>>>(fh, qh, coef, ndirs, g.nhalf, n);
+    fast_collide_kernel<T, N><<<(unsigned)blocks, kFastThreads, sm, st>>>(fh, qh, coef, nconv, g.nhalf, n);
     return cudaGetLastError();
 }
 
@@ -192,10 +201,10 @@ cudaError_t launch_fast_any(const bz_modes *m, const typename C2<T>::type *fh, t
     const void *cv = sizeof(T) == 8 ? static_cast<const void *>(m->d_fast64) : static_cast<const void *>(m->d_fast32);
     const auto *coef = static_cast<const typename C2<T>::type *>(cv);
     switch (g.N) {
-        case 8: return launch_fast_n<T, 8>(g, fh, qh, coef, m->ndirs, n, st);
-        case 16: return launch_fast_n<T, 16>(g, fh, qh, coef, m->ndirs, n, st);
-        case 24: return launch_fast_n<T, 24>(g, fh, qh, coef, m->ndirs, n, st);
-        case 32: return launch_fast_n<T, 32>(g, fh, qh, coef, m->ndirs, n, st);
+        case 8: return launch_fast_n<T, 8>(g, fh, qh, coef, m->nconv, n, st);
+        case 16: return launch_fast_n<T, 16>(g, fh, qh, coef, m->nconv, n, st);
+        case 24: return launch_fast_n<T, 24>(g, fh, qh, coef, m->nconv, n, st);
+        case 32: return launch_fast_n<T, 32>(g, fh, qh, coef, m->nconv, n, st);
         default: return cudaErrorInvalidValue;
     }
 }
