@@ -58,14 +58,9 @@ extern "C" {
  *   BZ_FP64   : every step in FP64 (the plain form).
  *   BZ_FP32   : DFTs and the mode sum in FP32 with compensated accumulation
  *               of the mode sum; moments, Maxwellian and the conservation
- *               fix in FP64.
- *   BZ_FP32X2 : as BZ_FP32, with the Fourier coefficients carried as
- *               unevaluated FP32 pairs (hi + lo) through the DFTs and the
- *               mode sum (first-order correction), for FP64-like accuracy at
- *               FP32-pipe speed. */
+ *               fix in FP64. */
 #define BZ_FP64    0
 #define BZ_FP32    1
-#define BZ_FP32X2  2
 
 /* flags */
 #define BZ_CONSERVE     1  /* project Q so its discrete moments of 1, v, |v|^2 vanish */
@@ -150,7 +145,7 @@ int build_fast_modes(const bz_grid *g, double b0, int n_dirs, bz_modes **out);
  * BZ_CONSERVE, the smallest L2 correction that zeroes the discrete moments of
  * 1, v, |v|^2).
  *   m         : modes handle
- *   precision : BZ_FP64 (f, Q are double) or BZ_FP32 / BZ_FP32X2 (float)
+ *   precision : BZ_FP64 (f, Q are double) or BZ_FP32 (float)
  *   flags     : BZ_CONSERVE | BZ_CHECK_INPUT
  *   f, Q      : device arrays [n_cells][N^d]; may not overlap
  *   n_cells   : >= 0 (0 is a no-op)
@@ -294,7 +289,7 @@ int bz_profile_read(char *names, int names_bytes, double *total_ms, int64_t *lau
  * spectrum modes (bz_modes_info out[4]), c = 8 bytes (BZ_FP32) or 16 (BZ_FP64)
  * -- 4224 cells of a 32x32 grid in FP32, 2112 in FP64.  Larger n_cells are
  * rejected with BZ_EINVAL and a message giving the limit.
- *   precision : BZ_FP32 or BZ_FP64 (BZ_FP32X2 is not accepted)
+ *   precision : BZ_FP32 or BZ_FP64
  *   flags     : 0 or BZ_CONSERVE (BZ_CHECK_INPUT is not accepted: its error
  *               word would be allocated on first use)
  *   f, Q, n_cells, stream : as for collide_batch; the device that owns the

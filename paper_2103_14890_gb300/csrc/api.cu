@@ -186,9 +186,8 @@ bool tableau(int scheme, Tableau &t) {
 
 int check_modes(const bz_modes *m, int precision, const char *who) {
     if (!m || !m->g) return fail(BZ_EINVAL, std::string(who) + ": modes handle is NULL");
-    if (precision != BZ_FP64 && precision != BZ_FP32 && precision != BZ_FP32X2)
+    if (precision != BZ_FP64 && precision != BZ_FP32)
         return fail(BZ_EINVAL, std::string(who) + ": unknown precision");
-    if (precision == BZ_FP32X2) return fail(BZ_ENOTSUP, std::string(who) + ": BZ_FP32X2 not built yet");
     return BZ_OK;
 }
 
