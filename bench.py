@@ -311,6 +311,11 @@ def _e2e(args, bz, modes, f_host, f, barrier, st, e0, e1, cells, world):
     return cells * world / (e2e_ms / 1e3)
 
 
+def workloads_mod():
+    from paper_2103_14890_gb300 import workloads
+    return workloads
+
+
 def torch_index(idx):
     import torch
     return torch.from_numpy(idx).to("cuda")
@@ -435,6 +440,32 @@ def _fast_measure(bz, f, f_host, st, ndirs, check=True):
     msd = _timed(lambda: bz.collide_batch(md, f, Qd, precision="fp32"), 10, st)
     out["direct_fp32_same_kernel"] = {"ms_per_step": msd, "cell_collision_evals_per_s": cells / (msd / 1e3)}
     out["speedup_fast_over_direct_fp32"] = msd / ms
+    # 48^2 grid (zero-padded to 72^2), 16384 cells: fast form against the direct sum
+    g48 = bz.Grid(2, 48, L_BOX)
+    f48 = torch.from_numpy(workloads_mod().shifted_maxwellians(16384, 2, 48, L_BOX, seed=SEED + 48)).to(
+        "cuda", torch.float32)
+    q48 = torch.empty_like(f48)
+    res48 = {}
+    for name, m48 in (("fast", bz.FastModes(g48, ndirs)), ("direct", bz.Modes(g48, 0.0))):
+        bz.collide_batch(m48, f48, q48, precision="fp32")
+        t48 = _timed(lambda: bz.collide_batch(m48, f48, q48, precision="fp32"), 5, st)
+        res48[name] = {"ms_per_step": t48, "cell_collision_evals_per_s": f48.shape[0] / (t48 / 1e3)}
+    res48["speedup_fast_over_direct"] = res48["direct"]["ms_per_step"] / res48["fast"]["ms_per_step"]
+    out["grid_48x48_16384_cells_fp32"] = res48
+    # the paper's production configuration: ARS(2,2,2) steps with the fast
+    # operator (Maxwell molecules) on the 19802-cell mesh, CUDA graph
+    fs, hmesh = workloads_mod().sod_cells(N_V, L_BOX)
+    dt = 0.5 * hmesh / (math.sqrt(2.0) * L_BOX)
+    s2 = torch.cuda.Stream()
+    with torch.cuda.stream(s2):
+        x = torch.from_numpy(fs).to("cuda", torch.float32)
+        y = torch.empty_like(x)
+        for _ in range(2):
+            bz.imex_step(mf, x, dt, 5e-3, f_out=y, precision="fp32", stream=s2)
+        bz.check(s2)
+        msi = _timed(lambda: bz.imex_step(mf, x, dt, 5e-3, f_out=y, precision="fp32", stream=s2), 10, s2)
+    out["imex_step_fp32"] = {"ms_per_step": msi, "cell_collision_evals_per_s": 2 * x.shape[0] / (msi / 1e3),
+                             "workload": "ARS(2,2,2) step, %d-cell Delaunay mesh, eps=5e-3, CUDA graph" % x.shape[0]}
     bz.check()
     out["rel_l2_fp32_vs_fp64_gpu_all_cells"] = ((Q.double() - Q64).norm() / Q64.norm()).item()
     if check:

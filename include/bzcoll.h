@@ -131,7 +131,7 @@ int build_kernel_modes(const bz_grid *g, double gamma, double b0, int quad_nodes
  * imex_step, bz_modes_beta); those calls then evaluate the fast operator with
  * the same forward / inverse transforms and epilogues.  It does not change
  * the meaning of the precision argument: BZ_FP64 or BZ_FP32 arithmetic.
- *   g      : grid handle, dim = 2 and N in {8, 16, 24, 32}
+ *   g      : grid handle, dim = 2 and N in {8, 16, 24, 32, 48}
  *   b0     : kernel constant; <= 0 selects 1/(2 pi)
  *   n_dirs : number of collision directions A, 1 <= A <= 1024
  *   out    : receives the handle (release with bz_modes_destroy)

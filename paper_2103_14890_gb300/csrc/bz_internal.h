@@ -150,7 +150,7 @@ cudaError_t launch_modesum32_part(const bz_modes *m, int v, const float2 *fhat, 
 cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *const *fhat, float2 *const *Qhat,
                                    const int64_t *n, int count, cudaStream_t st);
 
-// ---- fast spectral form (k_fast.cu), 2-D, N in {8, 16, 24, 32} ------------
+// ---- fast spectral form (k_fast.cu), 2-D, N in {8, 16, 24, 32, 48} --------
 bool fast_supported(const GridView &g);
 int fast_pad_length(int N);        // P of the zero-padded convolution grid
 int fast_cells_per_cta(int N);

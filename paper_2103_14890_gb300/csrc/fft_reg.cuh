@@ -1,5 +1,5 @@
-// fft_reg.cuh -- register-resident FFTs of small lengths (2^p <= 32 and
-// 3 * 2^p <= 48), unrolled with compile-time indices so that the data stay in
+// fft_reg.cuh -- register-resident FFTs of small lengths (2^p <= 32,
+// 3 * 2^p <= 48 and 72), unrolled with compile-time indices so that the data stay in
 // registers and the twiddles are constant-bank operands.  Each translation
 // unit that includes this header gets its own copy of the twiddle tables in
 // constant memory and must fill it with upload_fft_twiddles() on every device
@@ -60,19 +60,32 @@ __device__ __forceinline__ void fft_dit(V (&a)[L]) {
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-radix form for lengths 3 * 2^p: a length-3Q transform is split by
-// Cooley-Tukey into Q-point transforms of the three residue classes
-// n = Q n1 + n2 (3-point DFTs over n1, twiddles omega_L^(n2 k1), then Q-point
-// FFTs over n2; output index k1 + 3 k2).
+// Mixed-radix form for lengths 3 * 2^p (<= 48) and 72: a length-3Q transform
+// is split by Cooley-Tukey into Q-point transforms of the three residue
+// classes n = Q n1 + n2 (3-point DFTs over n1, twiddles omega_L^(n2 k1), then
+// Q-point FFTs over n2; output index k1 + 3 k2).
 
 __constant__ float2 c_w48[48];          // e^{-2 pi i k / 48}, k = 0..47
 __constant__ double2 c_w48d[48];
+__constant__ float2 c_w72[72];          // e^{-2 pi i k / 72}, k = 0..71
+__constant__ double2 c_w72d[72];
 
 template <typename V> __device__ __forceinline__ V tw48(int k);
 template <> __device__ __forceinline__ float2 tw48<float2>(int k) { return c_w48[k]; }
 template <> __device__ __forceinline__ double2 tw48<double2>(int k) { return c_w48d[k]; }
+template <typename V> __device__ __forceinline__ V tw72(int k);
+template <> __device__ __forceinline__ float2 tw72<float2>(int k) { return c_w72[k]; }
+template <> __device__ __forceinline__ double2 tw72<double2>(int k) { return c_w72d[k]; }
 
-// Transform of length L (2^p <= 32, or 3 * 2^p <= 48) from natural to
+// e^{-2 pi i k / L} for any L dividing 32, 48 or 72
+template <int L, typename V> __device__ __forceinline__ V twl(int k) {
+    static_assert(32 % L == 0 || 48 % L == 0 || 72 % L == 0, "length divides 32, 48 or 72");
+    if constexpr (32 % L == 0) return tw32<V>(k * (32 / L));
+    else if constexpr (48 % L == 0) return tw48<V>(k * (48 / L));
+    else return tw72<V>(k * (72 / L));
+}
+
+// Transform of length L (2^p <= 32, 3 * 2^p <= 48, or 72) from natural to
 // natural order; SIGN as in fft_dit.
 template <int L, int SIGN, typename V>
 __device__ __forceinline__ void fft_nat(V (&a)[L]) {
@@ -86,7 +99,7 @@ __device__ __forceinline__ void fft_nat(V (&a)[L]) {
 #pragma unroll
         for (int i = 0; i < L; ++i) a[i] = b[i];
     } else {
-        static_assert(L % 3 == 0 && L <= 48, "length 3 * 2^p <= 48");
+        static_assert(L % 3 == 0 && (L <= 48 || L == 72), "length 3 * 2^p <= 48 or 72");
         constexpr int Q = L / 3;
         constexpr S kS3 = (S)0.866025403784438647;    // sqrt(3) / 2
         V2 y0[Q], y1[Q], y2[Q];
@@ -100,7 +113,7 @@ __device__ __forceinline__ void fft_nat(V (&a)[L]) {
             const S ix = SIGN < 0 ? kS3 * dy : -kS3 * dy, iy = SIGN < 0 ? -kS3 * dx : kS3 * dx;
             V2 u1 = cmk<V2>(mx + ix, my + iy), u2 = cmk<V2>(mx - ix, my - iy);
             if (n2 > 0) {
-                const V w1 = tw48<V>(n2 * (48 / L)), w2 = tw48<V>(2 * n2 * (48 / L));
+                const V w1 = twl<L, V>(n2), w2 = twl<L, V>(2 * n2);
                 const S w1y = SIGN < 0 ? w1.y : -w1.y, w2y = SIGN < 0 ? w2.y : -w2.y;
                 u1 = cmk<V2>(u1.x * w1.x - u1.y * w1y, u1.x * w1y + u1.y * w1.x);
                 u2 = cmk<V2>(u2.x * w2.x - u2.y * w2y, u2.x * w2y + u2.y * w2.x);
@@ -126,17 +139,10 @@ template <int N, typename V> __device__ __forceinline__ V tw(int k) {
     else return tw48<V>(k * (48 / N));
 }
 
-// e^{-2 pi i k / L} for any L dividing 32 or 48
-template <int L, typename V> __device__ __forceinline__ V twl(int k) {
-    static_assert(32 % L == 0 || 48 % L == 0, "length divides 32 or 48");
-    if constexpr (32 % L == 0) return tw32<V>(k * (32 / L));
-    else return tw48<V>(k * (48 / L));
-}
-
 // Fill this translation unit's twiddle tables on the current device.
 inline cudaError_t upload_fft_twiddles() {
-    float2 w32[32], w48[48];
-    double2 d32[32], d48[48];
+    float2 w32[32], w48[48], w72[72];
+    double2 d32[32], d48[48], d72[72];
     for (int k = 0; k < 32; ++k) {
         d32[k] = make_double2(cos(2.0 * M_PI * k / 32), -sin(2.0 * M_PI * k / 32));
         w32[k] = make_float2((float)d32[k].x, (float)d32[k].y);
@@ -145,10 +151,16 @@ inline cudaError_t upload_fft_twiddles() {
         d48[k] = make_double2(cos(2.0 * M_PI * k / 48), -sin(2.0 * M_PI * k / 48));
         w48[k] = make_float2((float)d48[k].x, (float)d48[k].y);
     }
+    for (int k = 0; k < 72; ++k) {
+        d72[k] = make_double2(cos(2.0 * M_PI * k / 72), -sin(2.0 * M_PI * k / 72));
+        w72[k] = make_float2((float)d72[k].x, (float)d72[k].y);
+    }
     cudaError_t e = cudaMemcpyToSymbol(c_w32, w32, sizeof w32);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w48, w48, sizeof w48);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w32d, d32, sizeof d32);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w48d, d48, sizeof d48);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w72, w72, sizeof w72);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_w72d, d72, sizeof d72);
     return e;
 }
 

@@ -278,7 +278,7 @@ int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out) {
     if (ndirs < 1 || ndirs > 1024) return fail(BZ_EINVAL, "build_fast_modes: n_dirs in [1, 1024]");
     const GridView &v = g->v;
     if (!fast_supported(v))
-        return fail(BZ_ENOTSUP, "build_fast_modes: the fast form is built for 2-D grids with N in {8, 16, 24, 32}");
+        return fail(BZ_ENOTSUP, "build_fast_modes: the fast form is built for 2-D grids with N in {8, 16, 24, 32, 48}");
     bz_modes *m = (bz_modes *)calloc(1, sizeof(bz_modes));
     if (!m) return fail(BZ_ENOMEM, "build_fast_modes: host allocation");
     m->g = g;

@@ -17,7 +17,8 @@
 // product is Re * Im.  The sum g of the A + 1 products goes back through one
 // real forward transform; Q-hat keeps k in K_h with k_1 >= 0 (tiled layout).
 //
-// A CTA takes C cells with C * P = 96 threads.  Per direction: pass A, one
+// A CTA takes C cells with C * P threads (96 for P <= 48; 144 FP32 / 72 FP64
+// threads for the P = 72 of 48^2 grids).  Per direction: pass A, one
 // thread per (cell, k1 in [-h, h]) transforms along k2 into Y (shared);
 // pass B, one thread per (cell, j2) transforms Y along k1 and accumulates the
 // product into g (shared; each thread owns its column of g for the whole
@@ -42,19 +43,22 @@ namespace bz {
 
 namespace {
 
-constexpr int kFastThreads = 96;
-
-// Smallest register-FFT length >= n (lengths 2^p <= 32 and 3 * 2^p <= 48).
+// Smallest register-FFT length >= n (lengths 2^p <= 32, 3 * 2^p <= 48, 72).
 constexpr int fast_pad(int n) {
     return n <= 2 ? 2 : n <= 3 ? 3 : n <= 4 ? 4 : n <= 6 ? 6 : n <= 8 ? 8 : n <= 12 ? 12
-         : n <= 16 ? 16 : n <= 24 ? 24 : n <= 32 ? 32 : n <= 48 ? 48 : 0;
+         : n <= 16 ? 16 : n <= 24 ? 24 : n <= 32 ? 32 : n <= 48 ? 48 : n <= 72 ? 72 : 0;
 }
 
-template <int N> struct FastShape {
+// Cells per CTA: C * P = 96 threads for P <= 48; for P = 72 (48^2 grids) two
+// FP32 cells (144 threads) or one FP64 cell, whose scratch fills 111 KB.
+constexpr int fast_cells(int P, int bytes) { return P <= 48 ? 96 / P : (bytes == 4 ? 2 : 1); }
+
+template <typename T, int N> struct FastShape {
     static constexpr int H = N / 2 - 1, M = 2 * H + 1;
     static constexpr int P = fast_pad(3 * H + 1);
-    static constexpr int C = kFastThreads / P;
-    static_assert(P > 0 && C * P == kFastThreads, "grid not served by the fast kernel");
+    static constexpr int C = fast_cells(P, (int)sizeof(T));
+    static constexpr int NT = C * P;                           // threads per CTA
+    static_assert(P > 0 && C * M <= NT, "grid not served by the fast kernel");
     static constexpr int TS = P * C + C;                       // padded k1 stride of pass C/D
     static constexpr int nYa = M * P * C, nYb = (H + 1) * TS;
     static constexpr int nY = nYa > nYb ? nYa : nYb;           // complex
@@ -63,17 +67,17 @@ template <int N> struct FastShape {
 };
 
 template <typename T, int N> constexpr size_t fast_smem() {
-    using Sh = FastShape<N>;
+    using Sh = FastShape<T, N>;
     return 2 * sizeof(T) * (size_t)(Sh::nY + Sh::nF) + sizeof(T) * (size_t)Sh::nG;
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kFastThreads)
+__global__ void __launch_bounds__(FastShape<T, N>::NT)
 fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>::type *__restrict__ qh,
                     const typename C2<T>::type *__restrict__ coef, int nconv, int64_t nhalf, int64_t n) {
     using V2 = typename C2<T>::type;
     using S = T;
-    using Sh = FastShape<N>;
+    using Sh = FastShape<T, N>;
     constexpr int H = Sh::H, M = Sh::M, P = Sh::P, C = Sh::C, TS = Sh::TS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2 *Y = reinterpret_cast<V2 *>(smem_raw);     // pass A/B: [P][M][C]; pass C/D: [H+1][TS]
@@ -82,7 +86,7 @@ fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>:
     const int tid = threadIdx.x;
     const int64_t cell0 = (int64_t)blockIdx.x * C;
 
-    for (int i = tid; i < Sh::nF; i += kFastThreads) {
+    for (int i = tid; i < Sh::nF; i += Sh::NT) {
         const int c = i % C, mode = i / C;
         const int64_t cell = cell0 + c;
         F[i] = cell < n ? fh[tiled_index(cell, mode, nhalf)] : cmk<V2>((S)0., (S)0.);
@@ -183,13 +187,13 @@ template <typename T, int N>
 cudaError_t launch_fast_n(const GridView &g, const typename C2<T>::type *fh, typename C2<T>::type *qh,
                           const typename C2<T>::type *coef, int nconv, int64_t n, cudaStream_t st) {
     constexpr size_t sm = fast_smem<T, N>();
-    constexpr int C = FastShape<N>::C;
+    constexpr int C = FastShape<T, N>::C;
     const int64_t blocks = (n + C - 1) / C;
     if (blocks > INT_MAX) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fast_collide_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
-    fast_collide_kernel<T, N><<<(unsigned)blocks, kFastThreads, sm, st>>>(fh, qh, coef, nconv, g.nhalf, n);
+    fast_collide_kernel<T, N><<<(unsigned)blocks, FastShape<T, N>::NT, sm, st>>>(fh, qh, coef, nconv, g.nhalf, n);
     return cudaGetLastError();
 }
 
@@ -205,6 +209,7 @@ cudaError_t launch_fast_any(const bz_modes *m, const typename C2<T>::type *fh, t
         case 16: return launch_fast_n<T, 16>(g, fh, qh, coef, m->nconv, n, st);
         case 24: return launch_fast_n<T, 24>(g, fh, qh, coef, m->nconv, n, st);
         case 32: return launch_fast_n<T, 32>(g, fh, qh, coef, m->nconv, n, st);
+        case 48: return launch_fast_n<T, 48>(g, fh, qh, coef, m->nconv, n, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -212,11 +217,11 @@ cudaError_t launch_fast_any(const bz_modes *m, const typename C2<T>::type *fh, t
 }  // namespace
 
 bool fast_supported(const GridView &g) {
-    return g.dim == 2 && (g.N == 8 || g.N == 16 || g.N == 24 || g.N == 32);
+    return g.dim == 2 && (g.N == 8 || g.N == 16 || g.N == 24 || g.N == 32 || g.N == 48);
 }
 
 int fast_pad_length(int N) { return fast_pad(3 * (N / 2 - 1) + 1); }
-int fast_cells_per_cta(int N) { return kFastThreads / fast_pad_length(N); }
+int fast_cells_per_cta(int N) { return fast_cells(fast_pad_length(N), 4); }
 
 int fast_setup() {
     cudaError_t e = upload_fft_twiddles();

@@ -72,14 +72,16 @@ def test_fast_weights_match_oracle(bz, okf, N, ndirs):
 
 
 def test_fast_shapes(bz):
-    """Padded length P >= 3h + 1 (no aliasing into K_h) and C * P = 96."""
-    for N, P in [(8, 12), (16, 24), (24, 48), (32, 48)]:
+    """Padded length P >= 3h + 1 (no aliasing into K_h); C * P = 96 threads per
+    CTA, 144 for the P = 72 of 48^2."""
+    for N, P in [(8, 12), (16, 24), (24, 48), (32, 48), (48, 72)]:
         m = _modes(bz, N, 4)
         assert m.pad == P and P >= 3 * (N // 2 - 1) + 1
-        assert m.fast_cells * m.pad == 96
+        assert m.fast_cells * m.pad == (96 if P <= 48 else 144)
 
 
-@pytest.mark.parametrize("N,ndirs,n", [(8, 1, 70), (16, 4, 70), (24, 8, 37), (32, 8, 70), (32, 3, 5)])
+@pytest.mark.parametrize("N,ndirs,n", [(8, 1, 70), (16, 4, 70), (24, 8, 37), (32, 8, 70), (32, 3, 5),
+                                       (48, 8, 3), (48, 5, 2)])
 def test_fast_fp64_matches_oracle(bz, okf, N, ndirs, n):
     f = workloads.bi_maxwellian(n, 2, N, L, seed=2100 + N + ndirs)
     m = _modes(bz, N, ndirs)
@@ -89,7 +91,8 @@ def test_fast_fp64_matches_oracle(bz, okf, N, ndirs, n):
     assert relerr(Q.cpu().numpy(), Qr) < TOL64
 
 
-@pytest.mark.parametrize("N,ndirs,n", [(8, 2, 70), (16, 8, 70), (24, 8, 37), (32, 8, 70), (32, 16, 33)])
+@pytest.mark.parametrize("N,ndirs,n", [(8, 2, 70), (16, 8, 70), (24, 8, 37), (32, 8, 70), (32, 16, 33),
+                                       (48, 8, 5)])
 def test_fast_fp32_matches_oracle(bz, okf, N, ndirs, n):
     f = workloads.shifted_maxwellians(n, 2, N, L, seed=2200 + N + ndirs)
     m = _modes(bz, N, ndirs)
@@ -150,6 +153,26 @@ def test_fast_imex_step_matches_oracle(bz, okf):
     assert relerr(out.cpu().numpy(), want) < TOL64
 
 
+@pytest.mark.parametrize("eps", [1.0, 5e-3])
+def test_fast_imex_step_fp32_within_budget(bz, okf, eps):
+    """FP32 step with the fast operator: the FP32 rounding of the state plus the
+    FP32 collision error entering every stage through dt G / eps (amplified by at
+    most ~2 dt/eps (1 + dt rho / eps) by the ARS(2,2,2) coefficients)."""
+    N, ndirs, n, dt = 32, 8, 40, 2.5e-4
+    f = workloads.bi_maxwellian(n, 2, N, L, seed=2650)
+    fin = as_input(f, "fp32")
+    k = okf(N, ndirs)
+    want = k.imex_step(fin, dt, eps)
+    m = _modes(bz, N, ndirs)
+    got = bz.imex_step(m, to_dev(f, "fp32"), dt, eps, precision="fp32").double().cpu().numpy()
+    q_err = np.linalg.norm(bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32").double().cpu().numpy()
+                           - k.collide(fin))
+    bz.check()
+    rho = fin.sum(axis=1).max() * (2 * L / N) ** 2
+    budget = 8 * 2.0 ** -24 * np.linalg.norm(fin) + 4 * (dt / eps) * (1 + dt * rho / eps) * q_err
+    assert np.linalg.norm(got - want) < budget
+
+
 def test_fast_group_noalloc_and_host_paths_agree(bz):
     """A fast instance inside group_collide (next to a direct one), the
     allocation-free entry and the host pipeline all give collide_batch's bits."""
@@ -190,8 +213,10 @@ def test_fast_argument_errors(bz):
     out = ctypes.c_void_p()
     g3 = bz.Grid(3, 8, L)
     assert lib.build_fast_modes(g3._h, 0.0, 8, ctypes.byref(out)) == bz.ENOTSUP
-    g48 = bz.Grid(2, 48, L)
-    assert lib.build_fast_modes(g48._h, 0.0, 8, ctypes.byref(out)) == bz.ENOTSUP
+    g64 = bz.Grid(2, 64, L)
+    assert lib.build_fast_modes(g64._h, 0.0, 8, ctypes.byref(out)) == bz.ENOTSUP
+    g12 = bz.Grid(2, 12, L)
+    assert lib.build_fast_modes(g12._h, 0.0, 8, ctypes.byref(out)) == bz.ENOTSUP
     g = bz.Grid(2, 32, L)
     assert lib.build_fast_modes(g._h, 0.0, 0, ctypes.byref(out)) == bz.EINVAL
     assert lib.build_fast_modes(g._h, 0.0, 8, None) == bz.EINVAL
