@@ -1,0 +1,194 @@
+"""Plain FP64 oracle of the finite-volume transport residual of Sec. 3.2.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests and by the benchmark's
+CPU-baseline leg; the CUDA library never imports it.  It shares no code with
+the library (geometry, stencils, reconstruction and fluxes are written here
+from the paper's definitions; every loop runs over cells in index order and is
+vectorised only over the discrete velocities).
+
+What is computed, per polygonal cell P_i and discrete velocity v_k (2-D
+space, 2-D velocity grid v = (-L + j1 dv, -L + j2 dv), k = j1 N + j2):
+
+  L_{k,i} = (1/|P_i|) sum over the faces e of P_i of |e| F(f_L, f_R; v_k . n_e)
+
+with F the Rusanov flux of the linear flux v f (eq. finite_vol5):
+  F = (v.n)(f_L + f_R)/2 - |v.n| (f_R - f_L)/2,
+f_L, f_R the reconstructed values on either side at the face midpoint (the
+midpoint rule is exact for reconstructions of degree <= 1), and a
+transmissive boundary (f_R = f_L on faces without a neighbour).
+
+Reconstruction (eq. CWENO:Popt, CWENO:P0, CWENO:Prec, eqn.weights) for the
+degree M = 1: with the zero-mean Taylor basis about the barycentre x_b
+(eq. Dubiner_phi_spatial), every polynomial that keeps the cell average is
+p(x) = fbar_i + g . (x - x_b,i), and the cell average of p over P_j is
+fbar_i + g . (x_b,j - x_b,i).  Hence
+  - p_opt: g_opt = least-squares solution over the central stencil of
+    n_e = 2 * M(M) = 6 cells (the cell and its 5 nearest cells);
+  - p^L (L = 1..#sectors): the gradient that reproduces the averages of the
+    sector's two other cells exactly;
+  - p^0 = (p_opt - sum_L lambda_L p^L) / lambda_0;
+  - f^w = sum_s omega_s p^s with omega_s proportional to
+    lambda_s / (sigma_s + eps)^r, eps = 1e-14, r = 4 (printed values),
+    sigma_s = h_i^2 |g_s|^2.
+For M = 0, f^w = fbar (first order).
+
+Readings of points the paper leaves open (each listed in the design notes):
+  - central stencil: the 5 cells nearest to P_i by barycentre distance
+    among the cells that share a vertex with P_i or with one of its
+    vertex neighbours (ties by cell index);
+  - sectors: for every pair of consecutive faces of P_i that both have a
+    neighbour, the stencil {P_i, neighbour across the first, neighbour across
+    the second}; a sector whose two barycentre offsets are (numerically)
+    collinear is dropped;
+  - linear weights lambda_0 = 3/4 and lambda_L = (1/4) / #sectors (lambda_0 =
+    1 with no sector);
+  - h_i = the largest distance from the barycentre to a vertex of P_i;
+  - sigma_s = h_i^2 |g_s|^2, the gradient part of the usual smoothness
+    indicator for a linear polynomial.
+"""
+import numpy as np
+
+LAMBDA0 = 0.75
+EPS = 1e-14
+R_EXP = 4
+
+
+class Mesh:
+    """Geometry of a polygonal mesh: vertices xy (n_vtx, 2), cells as a list of
+    vertex-index lists (any orientation; stored counter-clockwise)."""
+
+    def __init__(self, xy, cells):
+        self.xy = np.asarray(xy, dtype=np.float64)
+        self.cells = []
+        n = len(cells)
+        self.area = np.zeros(n)
+        self.bary = np.zeros((n, 2))
+        self.h = np.zeros(n)
+        for i, c in enumerate(cells):
+            c = [int(v) for v in c]
+            P = self.xy[c]
+            x, y = P[:, 0], P[:, 1]
+            xn, yn = np.roll(x, -1), np.roll(y, -1)
+            cross = x * yn - xn * y
+            a = 0.5 * cross.sum()                    # shoelace
+            if a < 0:
+                c = c[::-1]
+                P = self.xy[c]
+                x, y = P[:, 0], P[:, 1]
+                xn, yn = np.roll(x, -1), np.roll(y, -1)
+                cross = x * yn - xn * y
+                a = 0.5 * cross.sum()
+            self.cells.append(c)
+            self.area[i] = a
+            self.bary[i] = [((x + xn) * cross).sum() / (6 * a), ((y + yn) * cross).sum() / (6 * a)]
+            self.h[i] = np.sqrt(((P - self.bary[i]) ** 2).sum(axis=1)).max()
+        # faces: edge a -> b of a counter-clockwise polygon has the outward
+        # normal (y_b - y_a, -(x_b - x_a)) / |e|; the neighbour owns edge b -> a
+        owner = {}
+        for i, c in enumerate(self.cells):
+            for q in range(len(c)):
+                owner[(c[q], c[(q + 1) % len(c)])] = i
+        self.faces = []          # per cell: list of (neighbour or -1, length, nx, ny, midx, midy)
+        for i, c in enumerate(self.cells):
+            fl = []
+            for q in range(len(c)):
+                a, b = c[q], c[(q + 1) % len(c)]
+                d = self.xy[b] - self.xy[a]
+                ln = float(np.hypot(d[0], d[1]))
+                mid = 0.5 * (self.xy[a] + self.xy[b])
+                fl.append((owner.get((b, a), -1), ln, d[1] / ln, -d[0] / ln, mid[0], mid[1]))
+            self.faces.append(fl)
+        # vertex -> cells
+        vc = [[] for _ in range(len(self.xy))]
+        for i, c in enumerate(self.cells):
+            for v in c:
+                vc[v].append(i)
+        self.vertex_cells = vc
+
+    def vertex_neighbours(self, i):
+        s = set()
+        for v in self.cells[i]:
+            s.update(self.vertex_cells[v])
+        s.discard(i)
+        return s
+
+    def central_stencil(self, i, count=5):
+        cand = set()
+        first = self.vertex_neighbours(i)
+        cand.update(first)
+        for j in first:
+            cand.update(self.vertex_neighbours(j))
+        cand.discard(i)
+        d = [(float(np.hypot(*(self.bary[j] - self.bary[i]))), j) for j in cand]
+        d.sort()
+        return [j for _, j in d[:count]]
+
+    def sectors(self, i):
+        fl = self.faces[i]
+        out = []
+        for q in range(len(fl)):
+            a, b = fl[q][0], fl[(q + 1) % len(fl)][0]
+            if a < 0 or b < 0:
+                continue
+            A = np.array([self.bary[a] - self.bary[i], self.bary[b] - self.bary[i]])
+            if abs(np.linalg.det(A)) <= 1e-12 * float(np.abs(A).max()) ** 2:
+                continue
+            out.append((a, b))
+        return out
+
+
+def velocity_grid(N, L):
+    v = -L + (2.0 * L / N) * np.arange(N)
+    V1, V2 = np.meshgrid(v, v, indexing="ij")
+    return V1.ravel(), V2.ravel()
+
+
+def reconstruct_gradients(mesh, f, order):
+    """CWENO gradient g (n_cells, 2, nv) of f^w in every cell; zero for order 1."""
+    f = np.asarray(f, dtype=np.float64)
+    n, nv = f.shape
+    g = np.zeros((n, 2, nv))
+    if order == 1:
+        return g
+    for i in range(n):
+        st = mesh.central_stencil(i)
+        A = np.array([mesh.bary[j] - mesh.bary[i] for j in st])            # (5, 2)
+        d = np.array([f[j] - f[i] for j in st])                             # (5, nv)
+        g_opt = np.linalg.lstsq(A, d, rcond=None)[0]                        # (2, nv)
+        secs = mesh.sectors(i)
+        if not secs:
+            g[i] = g_opt
+            continue
+        lam_l = (1.0 - LAMBDA0) / len(secs)
+        gs = []
+        for a, b in secs:
+            A2 = np.array([mesh.bary[a] - mesh.bary[i], mesh.bary[b] - mesh.bary[i]])
+            gs.append(np.linalg.solve(A2, np.array([f[a] - f[i], f[b] - f[i]])))
+        g0 = (g_opt - lam_l * sum(gs)) / LAMBDA0
+        polys = [g0] + gs
+        lams = [LAMBDA0] + [lam_l] * len(gs)
+        h2 = mesh.h[i] ** 2
+        wt = [lm / (h2 * (gg ** 2).sum(axis=0) + EPS) ** R_EXP for lm, gg in zip(lams, polys)]
+        tot = sum(wt)
+        g[i] = sum((w / tot) * gg for w, gg in zip(wt, polys))
+    return g
+
+
+def transport_residual(mesh, f, N, L, order=2):
+    """L_{k,i} of the module docstring for f of shape (n_cells, N*N)."""
+    f = np.asarray(f, dtype=np.float64)
+    v1, v2 = velocity_grid(N, L)
+    g = reconstruct_gradients(mesh, f, order)
+    out = np.zeros_like(f)
+    for i in range(len(f)):
+        acc = np.zeros(f.shape[1])
+        for (j, ln, nx, ny, mx, my) in mesh.faces[i]:
+            vn = v1 * nx + v2 * ny
+            fl = f[i] + g[i, 0] * (mx - mesh.bary[i, 0]) + g[i, 1] * (my - mesh.bary[i, 1])
+            if j < 0:
+                fr = fl
+            else:
+                fr = f[j] + g[j, 0] * (mx - mesh.bary[j, 0]) + g[j, 1] * (my - mesh.bary[j, 1])
+            acc += ln * (0.5 * vn * (fl + fr) - 0.5 * np.abs(vn) * (fr - fl))
+        out[i] = acc / mesh.area[i]
+    return out

@@ -90,10 +90,12 @@ def bkw_initial(N, L, t=0.0):
     return f.reshape(1, N * N)
 
 
-def sod_mesh(n_side=100, seed=1004, jitter=0.3):
-    """Jittered n_side x n_side lattice in [0,1]^2, triangulated.  Returns the
-    triangle centroids (n_tri, 2) and the mesh size h = sqrt(mean area).
-    Uses scipy's Delaunay when available, else the structured diagonal split."""
+def sod_triangulation(n_side=100, seed=1004, jitter=0.3):
+    """Jittered n_side x n_side lattice in [0,1]^2 (interior nodes moved by up
+    to jitter x spacing, boundary nodes clipped to the square), triangulated.
+    Returns the vertices (n_vtx, 2) and the triangles (n_tri, 3) as vertex
+    indices.  Uses scipy's Delaunay when available, else the structured
+    diagonal split of every lattice square."""
     rng = np.random.default_rng(seed)
     hs = 1.0 / (n_side - 1)
     g = np.linspace(0.0, 1.0, n_side)
@@ -111,6 +113,13 @@ def sod_mesh(n_side=100, seed=1004, jitter=0.3):
         a = idx[:-1, :-1].ravel(); b = idx[1:, :-1].ravel()
         c = idx[:-1, 1:].ravel(); d = idx[1:, 1:].ravel()
         tri = np.concatenate([np.stack([a, b, d], 1), np.stack([a, d, c], 1)])
+    return pts, np.ascontiguousarray(tri, dtype=np.int64)
+
+
+def sod_mesh(n_side=100, seed=1004, jitter=0.3):
+    """Triangle centroids (n_tri, 2) of sod_triangulation and the mesh size
+    h = sqrt(mean area)."""
+    pts, tri = sod_triangulation(n_side, seed, jitter)
     P = pts[tri]
     cent = P.mean(axis=1)
     area = 0.5 * np.abs((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1])

@@ -1,0 +1,153 @@
+"""Pins for the oracle's finite-volume transport residual (Sec. 3.2: CWENO
+reconstruction and Rusanov fluxes, eq. finite_vol5 / eq. ho).
+
+Checked against what geometry and calculus fix, not against the oracle itself:
+  - areas tile the domain (the convex hull of a Delaunay mesh, the unit square
+    of a polygonal one); every closed polygon has sum |e| n_e = 0;
+  - a linear field a + b.x has cell averages a + b.x_b; every reconstruction
+    of degree 1 reproduces it, so the residual is v.b exactly in every cell
+    (interior and transmissive boundary alike): pins normals, lengths, areas,
+    face midpoints, the neighbour pairing and the flux's sign;
+  - a constant field has zero residual in both orders;
+  - interior fluxes cancel in pairs: sum |P_i| L_i equals the boundary flux;
+  - the first-order form reduces to upwinding, written out by hand on one cell;
+  - near a jump the nonlinear weights leave far fewer out-of-range face
+    values than the unweighted least-squares gradient.
+"""
+import numpy as np
+import pytest
+
+from paper_2103_14890_gb300 import workloads
+
+
+@pytest.fixture(scope="module")
+def fv():
+    from oracle import fv
+    return fv
+
+
+@pytest.fixture(scope="module")
+def mesh(fv):
+    pts, tri = workloads.sod_triangulation(n_side=12, seed=7)
+    return fv.Mesh(pts, tri)
+
+
+def _quad_tri_mesh(fv):
+    """Unit square: a 6 x 6 grid of quadrilaterals, the lower-left half of
+    them split into two triangles (a mixed polygonal mesh)."""
+    n = 6
+    g = np.linspace(0, 1, n + 1)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    rng = np.random.default_rng(3)
+    X[1:-1, 1:-1] += rng.uniform(-0.2, 0.2, (n - 1, n - 1)) / n
+    Y[1:-1, 1:-1] += rng.uniform(-0.2, 0.2, (n - 1, n - 1)) / n
+    pts = np.stack([X.ravel(), Y.ravel()], 1)
+    idx = np.arange((n + 1) ** 2).reshape(n + 1, n + 1)
+    cells = []
+    for a in range(n):
+        for b in range(n):
+            q = [idx[a, b], idx[a + 1, b], idx[a + 1, b + 1], idx[a, b + 1]]
+            if a + b < n - 1:
+                cells += [[q[0], q[1], q[2]], [q[0], q[2], q[3]]]
+            else:
+                cells.append(q)
+    return fv.Mesh(pts, cells)
+
+
+def test_geometry_closes(fv, mesh):
+    from scipy.spatial import ConvexHull
+    hull = ConvexHull(mesh.xy).volume          # a Delaunay triangulation covers the hull
+    for m, total in ((mesh, hull), (_quad_tri_mesh(fv), 1.0)):
+        assert abs(m.area.sum() - total) < 1e-12
+        for fl in m.faces:
+            s = np.zeros(2)
+            for (_, ln, nx, ny, _, _) in fl:
+                s += ln * np.array([nx, ny])
+            assert np.abs(s).max() < 1e-14
+        # every interior face is seen from both sides with opposite normals
+        for i, fl in enumerate(m.faces):
+            for (j, ln, nx, ny, mx, my) in fl:
+                if j >= 0:
+                    back = [f for f in m.faces[j] if f[0] == i]
+                    assert len(back) == 1 and abs(back[0][1] - ln) < 1e-15
+                    assert abs(back[0][2] + nx) < 1e-14 and abs(back[0][3] + ny) < 1e-14
+
+
+@pytest.mark.parametrize("which", ["tri", "mixed"])
+def test_linear_field_gives_exact_divergence(fv, mesh, which):
+    m = mesh if which == "tri" else _quad_tri_mesh(fv)
+    N, L = 8, 3.0
+    v1, v2 = fv.velocity_grid(N, L)
+    a = np.linspace(0.5, 1.5, N * N)
+    b = np.stack([np.linspace(-2, 1, N * N), np.linspace(0.3, -0.7, N * N)])
+    f = a[None, :] + m.bary[:, :1] * b[0][None, :] + m.bary[:, 1:] * b[1][None, :]
+    Lr = fv.transport_residual(m, f, N, L, order=2)
+    want = (v1 * b[0] + v2 * b[1])[None, :]
+    assert np.abs(Lr - want).max() < 1e-9 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_constant_field_has_zero_residual(fv, mesh, order):
+    f = np.full((len(mesh.cells), 16), 0.37)
+    assert np.abs(fv.transport_residual(mesh, f, 4, 2.0, order=order)).max() < 1e-12
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_interior_fluxes_cancel(fv, mesh, order):
+    rng = np.random.default_rng(1)
+    N, L = 4, 2.0
+    f = rng.uniform(0.1, 1.0, (len(mesh.cells), N * N))
+    Lr = fv.transport_residual(mesh, f, N, L, order=order)
+    v1, v2 = fv.velocity_grid(N, L)
+    g = fv.reconstruct_gradients(mesh, f, order)
+    bnd = np.zeros(N * N)
+    for i, fl in enumerate(mesh.faces):
+        for (j, ln, nx, ny, mx, my) in fl:
+            if j < 0:
+                fv_ = f[i] + g[i, 0] * (mx - mesh.bary[i, 0]) + g[i, 1] * (my - mesh.bary[i, 1])
+                bnd += ln * (v1 * nx + v2 * ny) * fv_
+    assert np.abs((mesh.area[:, None] * Lr).sum(0) - bnd).max() < 1e-12 * np.abs(bnd).max()
+
+
+def test_first_order_is_upwind_by_hand(fv, mesh):
+    """Cell 0 with every neighbour: L = sum_e |e| (v.n)^+ f_i + (v.n)^- f_j / |P|."""
+    rng = np.random.default_rng(2)
+    N, L = 4, 2.0
+    f = rng.uniform(0.1, 1.0, (len(mesh.cells), N * N))
+    Lr = fv.transport_residual(mesh, f, N, L, order=1)
+    v1, v2 = fv.velocity_grid(N, L)
+    i = int(np.argmax([min(fc[0] for fc in fl) for fl in mesh.faces]))   # an interior cell
+    acc = np.zeros(N * N)
+    for (j, ln, nx, ny, _, _) in mesh.faces[i]:
+        vn = v1 * nx + v2 * ny
+        acc += ln * np.where(vn > 0, vn * f[i], vn * f[j])
+    assert np.abs(Lr[i] - acc / mesh.area[i]).max() < 1e-13 * np.abs(acc / mesh.area[i]).max()
+
+
+def test_weno_limits_overshoot_at_a_jump(fv):
+    """Faces whose reconstructed value leaves [0.125, 1] by more than 5 % of the
+    jump: the nonlinear weights cut their number well below that of the
+    unweighted least-squares gradient (cells whose every sector crosses the
+    jump keep an overshoot: on a triangle mesh a cell can have two face
+    neighbours across it)."""
+    pts, tri = workloads.sod_triangulation(n_side=20, seed=9)
+    m = fv.Mesh(pts, tri)
+    f = np.where(m.bary[:, 0] < 0.5, 1.0, 0.125)[:, None] * np.ones((1, 4))
+    g = fv.reconstruct_gradients(m, f, 2)
+
+    def count(grad):
+        n = 0
+        for i, fl in enumerate(m.faces):
+            gi = grad(i)
+            for (_, _, _, _, mx, my) in fl:
+                val = f[i, 0] + gi[0] * (mx - m.bary[i, 0]) + gi[1] * (my - m.bary[i, 1])
+                n += max(val - 1.0, 0.125 - val) > 0.05 * 0.875
+        return n
+
+    def least_squares(i):
+        st = m.central_stencil(i)
+        A = np.array([m.bary[j] - m.bary[i] for j in st])
+        return np.linalg.lstsq(A, np.array([f[j, 0] - f[i, 0] for j in st]), rcond=None)[0]
+
+    n_w, n_ls = count(lambda i: g[i, :, 0]), count(least_squares)
+    assert n_ls > 20 and n_w < n_ls / 2
