@@ -76,6 +76,7 @@ extern "C" {
 
 typedef struct bz_grid bz_grid;    /* opaque, library-owned */
 typedef struct bz_modes bz_modes;  /* opaque, library-owned */
+typedef struct bz_mesh bz_mesh;    /* opaque, library-owned (transport step) */
 
 /* init_velocity_grid -- Sec. 3.1 (eq. disc_space) and Sec. 3.3 (periodic box,
  * eq. FU / eq. FC).  Builds the velocity grid, the 1-D DFT factors
@@ -230,6 +231,63 @@ typedef struct bz_group_item {
     int64_t n_cells;
 } bz_group_item;
 int group_collide(const bz_group_item *items, int n_items, int precision, int flags, void *stream);
+
+/* ------------------------------------------------ transport step --- */
+
+/* build_fv_mesh -- the finite-volume mesh of Sec. 3.2: polygonal cells in 2-D
+ * physical space, their geometry, face pairing and CWENO stencils.  Cells may
+ * be given in either orientation and are stored counter-clockwise; an edge
+ * owned by one cell only is a boundary face (transmissive: the outer state
+ * equals the inner one).  order 1: piecewise-constant reconstruction (the
+ * first-order scheme of eq. finite_vol5); order 2: CWENO of degree 1
+ * (eq. CWENO:Popt / CWENO:P0 / CWENO:Prec / eqn.weights): the optimal
+ * polynomial by constrained least squares over the cell and its 5 nearest
+ * cells (by barycentre, among the cells sharing a vertex with the cell or
+ * with one of its vertex neighbours), one sector polynomial per pair of
+ * consecutive faces with neighbours on both, linear weights 3/4 (central) and
+ * 1/4 shared by the sectors, smoothness h^2 |grad p|^2 (h: largest
+ * barycentre-to-vertex distance), eps = 1e-14, r = 4.  The tables are built
+ * in FP64 on the host and uploaded to the current device in FP64 and FP32.
+ *   n_vertices, xy     : vertices, xy[2 v] = x, xy[2 v + 1] = y (host)
+ *   n_cells            : cells, 1 .. 2^30
+ *   cell_ptr           : n_cells + 1 offsets into cell_vertices, cell_ptr[0] = 0
+ *   cell_vertices      : vertex indices of every cell (3 to 8 per cell)
+ *   order              : 1 or 2
+ *   out                : receives the handle (release with bz_mesh_destroy)
+ * Errors: BZ_EINVAL (bad sizes or indices, degenerate or overlapping cells),
+ * BZ_ENOMEM, BZ_ECUDA. */
+int build_fv_mesh(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
+                  const int64_t *cell_vertices, int order, bz_mesh **out);
+
+/* transport_residual -- <L(f^w)>_x of eq. ho for every cell and discrete
+ * velocity: L[i][k] = (1/|P_i|) sum over the faces e of P_i of
+ * |e| F(f_L, f_R; v_k . n_e), with F the Rusanov flux of v f,
+ * F = (v.n)(f_L + f_R)/2 - |v.n| (f_R - f_L)/2, f_L, f_R the reconstructed
+ * values at the face midpoint.  The velocity grid is g's (2-D only; v_k as in
+ * the collision operator).
+ *   f, L      : device arrays [n_cells][N^2] (n_cells of the mesh), double for
+ *               BZ_FP64, float for BZ_FP32; must not overlap
+ * Scratch (order 2: 2 n_cells N^2 values) comes from the stream-ordered pool.
+ * Errors: BZ_EINVAL, BZ_ENOTSUP (3-D grid), BZ_ECUDA. */
+int transport_residual(const bz_mesh *mesh, const bz_grid *g, int precision, const void *f, void *L,
+                       void *stream);
+
+/* imex_step_fv -- one penalised IMEX step of the full scheme of Sec. 3.4
+ * (eq. GIMEX_n / eq. GIMEX_n2) on the mesh: the stages of imex_step with the
+ * transport residual of every stage value computed by transport_residual and
+ * entering the explicit part of the later stages.  The correction Delta Q of
+ * the paper vanishes for this reconstruction, which keeps the cell averages.
+ * f_n, f_out: device arrays [n_cells][N^2]; other arguments as imex_step.
+ * Errors: BZ_EINVAL, BZ_ENOTSUP (3-D grid), BZ_ENOMEM, BZ_ECUDA. */
+int imex_step_fv(const bz_modes *m, const bz_mesh *mesh, int scheme, int model, double dt, double eps,
+                 const void *f_n, void *f_out, int precision, int flags, void *stream);
+
+/* bz_mesh_info -- out[0] = cells, out[1] = interior faces, out[2] = boundary
+ * faces, out[3] = most faces of a cell, out[4] = order. */
+int bz_mesh_info(const bz_mesh *mesh, int64_t out[5]);
+
+/* bz_mesh_destroy -- release a mesh handle (NULL is ignored). */
+void bz_mesh_destroy(bz_mesh *mesh);
 
 /* bz_check -- synchronise `stream`, read and clear the device error word.
  * Returns BZ_OK, BZ_ENONFINITE, BZ_ETIMEOUT or BZ_ECUDA. */

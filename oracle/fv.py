@@ -23,7 +23,9 @@ degree M = 1: with the zero-mean Taylor basis about the barycentre x_b
 p(x) = fbar_i + g . (x - x_b,i), and the cell average of p over P_j is
 fbar_i + g . (x_b,j - x_b,i).  Hence
   - p_opt: g_opt = least-squares solution over the central stencil of
-    n_e = 2 * M(M) = 6 cells (the cell and its 5 nearest cells);
+    n_e = 2 * M(M) = 6 cells (the cell and its 5 nearest cells), from its
+    normal equations A^T A g = A^T d (A: barycentre offsets, d: differences
+    of the averages);
   - p^L (L = 1..#sectors): the gradient that reproduces the averages of the
     sector's two other cells exactly;
   - p^0 = (p_opt - sum_L lambda_L p^L) / lambda_0;
@@ -66,22 +68,14 @@ class Mesh:
         self.h = np.zeros(n)
         for i, c in enumerate(cells):
             c = [int(v) for v in c]
-            P = self.xy[c]
-            x, y = P[:, 0], P[:, 1]
-            xn, yn = np.roll(x, -1), np.roll(y, -1)
-            cross = x * yn - xn * y
-            a = 0.5 * cross.sum()                    # shoelace
+            a, b = self._shoelace(c)
             if a < 0:
                 c = c[::-1]
-                P = self.xy[c]
-                x, y = P[:, 0], P[:, 1]
-                xn, yn = np.roll(x, -1), np.roll(y, -1)
-                cross = x * yn - xn * y
-                a = 0.5 * cross.sum()
+                a, b = self._shoelace(c)
             self.cells.append(c)
             self.area[i] = a
-            self.bary[i] = [((x + xn) * cross).sum() / (6 * a), ((y + yn) * cross).sum() / (6 * a)]
-            self.h[i] = np.sqrt(((P - self.bary[i]) ** 2).sum(axis=1)).max()
+            self.bary[i] = b
+            self.h[i] = np.sqrt(((self.xy[c] - b) ** 2).sum(axis=1)).max()
         # faces: edge a -> b of a counter-clockwise polygon has the outward
         # normal (y_b - y_a, -(x_b - x_a)) / |e|; the neighbour owns edge b -> a
         owner = {}
@@ -104,6 +98,17 @@ class Mesh:
             for v in c:
                 vc[v].append(i)
         self.vertex_cells = vc
+
+    def _shoelace(self, c):
+        """Signed area and barycentre of the polygon c, with coordinates taken
+        relative to its first vertex (the shoelace sums then do not cancel)."""
+        P = self.xy[c] - self.xy[c[0]]
+        x, y = P[:, 0], P[:, 1]
+        xn, yn = np.roll(x, -1), np.roll(y, -1)
+        cross = x * yn - xn * y
+        a = 0.5 * cross.sum()
+        b = self.xy[c[0]] + np.array([((x + xn) * cross).sum(), ((y + yn) * cross).sum()]) / (6 * a)
+        return a, b
 
     def vertex_neighbours(self, i):
         s = set()
@@ -154,7 +159,7 @@ def reconstruct_gradients(mesh, f, order):
         st = mesh.central_stencil(i)
         A = np.array([mesh.bary[j] - mesh.bary[i] for j in st])            # (5, 2)
         d = np.array([f[j] - f[i] for j in st])                             # (5, nv)
-        g_opt = np.linalg.lstsq(A, d, rcond=None)[0]                        # (2, nv)
+        g_opt = np.linalg.solve(A.T @ A, A.T @ d)       # normal equations of the least-squares fit
         secs = mesh.sectors(i)
         if not secs:
             g[i] = g_opt

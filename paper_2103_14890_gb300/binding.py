@@ -71,6 +71,11 @@ def load(path=None):
             "bz_profile_read": ([c_p, c_i, c_p, c_p, c_i], c_i),
             "build_fast_modes": ([c_p, c_d, c_i, pp], c_i),
             "bz_fast_info": ([c_p, ctypes.POINTER(c_i64)], c_i),
+            "build_fv_mesh": ([c_i, c_p, c_i64, c_p, c_p, c_i, pp], c_i),
+            "transport_residual": ([c_p, c_p, c_i, c_p, c_p, c_p], c_i),
+            "imex_step_fv": ([c_p, c_p, c_i, c_i, c_d, c_d, c_p, c_p, c_i, c_i, c_p], c_i),
+            "bz_mesh_info": ([c_p, ctypes.POINTER(c_i64)], c_i),
+            "bz_mesh_destroy": ([c_p], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -170,6 +175,60 @@ class FastModes(Modes):
         h = ctypes.c_void_p()
         _check(load().build_fast_modes(grid._h, float(b0), int(ndirs), ctypes.byref(h)))
         super().__init__(grid, 0.0, _handle=h)
+
+
+class Mesh:
+    """Finite-volume mesh of the transport step (build_fv_mesh): vertices xy
+    (n_vtx, 2) and cells, either an (n_cells, k) integer array or a list of
+    vertex lists; order 1 (first order) or 2 (CWENO of degree 1)."""
+
+    def __init__(self, xy, cells, order=2):
+        import numpy as np
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        cells = [list(map(int, c)) for c in cells]
+        ptr = np.zeros(len(cells) + 1, dtype=np.int64)
+        ptr[1:] = np.cumsum([len(c) for c in cells])
+        vtx = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.int64) for c in cells]))
+        h = ctypes.c_void_p()
+        _check(load().build_fv_mesh(int(len(xy)), xy.ctypes.data_as(ctypes.c_void_p), int(len(cells)),
+                                    ptr.ctypes.data_as(ctypes.c_void_p), vtx.ctypes.data_as(ctypes.c_void_p),
+                                    int(order), ctypes.byref(h)))
+        self._h = h
+        info = (ctypes.c_int64 * 5)()
+        _check(load().bz_mesh_info(h, info))
+        self.n_cells, self.n_faces_interior, self.n_faces_boundary, self.max_faces, self.order = list(info)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.bz_mesh_destroy(self._h)
+            self._h = None
+
+
+def transport_residual(mesh, grid, f, L=None, precision="fp32", stream=None):
+    """<L(f^w)>_x for f of shape (n_cells, N^2) on the device."""
+    import torch
+    dt = _dtype(precision)
+    if L is None:
+        L = torch.empty_like(f)
+    if f.numel() != mesh.n_cells * grid.nv or L.numel() != f.numel():
+        raise ValueError("f and L must have n_cells * N^2 elements")
+    _check(load().transport_residual(mesh._h, grid._h, PRECISION[precision], _dptr(f, dt, "f"), _dptr(L, dt, "L"),
+                                     _stream(stream)))
+    return L
+
+
+def imex_step_fv(modes, mesh, f_n, dt, eps, f_out=None, scheme="ars222", model="boltzmann", precision="fp32",
+                 conserve=False, check_input=False, stream=None):
+    """One IMEX step of the finite-volume scheme (transport + collisions) on the mesh."""
+    import torch
+    ty = _dtype(precision)
+    if f_out is None:
+        f_out = torch.empty_like(f_n)
+    flags = (CONSERVE if conserve else 0) | (CHECK_INPUT if check_input else 0)
+    _check(load().imex_step_fv(modes._h, mesh._h, SCHEME[scheme], MODEL[model], float(dt), float(eps),
+                               _dptr(f_n, ty, "f_n"), _dptr(f_out, ty, "f_out"), PRECISION[precision], flags,
+                               _stream(stream)))
+    return f_out
 
 
 def collide_batch(modes, f, Q=None, precision="fp32", conserve=False, check_input=False, stream=None):

@@ -29,6 +29,9 @@ int grid_create(int dim, int N, double L, bz_grid **out);
 void grid_destroy(bz_grid *g);
 int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **out);
 int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out);
+int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
+                   const int64_t *cell_vertices, int order, bz_mesh **out);
+void fv_mesh_destroy(bz_mesh *m);
 void modes_destroy(bz_modes *m);
 double beta_host(const bz_modes *m, const int *l, const int *mm);
 double fast_beta_host(const bz_modes *m, int64_t li, int64_t mi);
@@ -312,6 +315,43 @@ int collide_chain(const bz_modes *m, int precision, int flags, const void *f, vo
     return rc;
 }
 
+// Transport residual L [cell][nv] of f over the mesh: CWENO gradients into
+// scratch (`ext` if given: transport_scratch_bytes), then the fluxes.
+size_t transport_scratch_bytes(const bz_mesh *mesh, const bz_grid *g, int precision) {
+    if (mesh->order != 2) return 0;
+    return (size_t)2 * mesh->n_cells * g->v.nv * (precision == BZ_FP64 ? sizeof(double) : sizeof(float));
+}
+
+int transport_chain(const bz_mesh *mesh, const bz_grid *g, int precision, const void *f, void *L, cudaStream_t st,
+                    void *ext = nullptr) {
+    const GridView &v = g->v;
+    Scratch s;
+    void *G = nullptr;
+    if (mesh->order == 2) {
+        if (!ext) BZ_TRY(s.alloc(transport_scratch_bytes(mesh, g, precision), st), "transport: scratch");
+        G = ext ? ext : s.p;
+        if (precision == BZ_FP64)
+            BZ_LAUNCH("fv_gradient_f64", st,
+                      launch_fv_gradient_f64(mesh, v, static_cast<const double *>(f), static_cast<double *>(G), st),
+                      "transport: reconstruction");
+        else
+            BZ_LAUNCH("fv_gradient_f32", st,
+                      launch_fv_gradient_f32(mesh, v, static_cast<const float *>(f), static_cast<float *>(G), st),
+                      "transport: reconstruction");
+    }
+    if (precision == BZ_FP64)
+        BZ_LAUNCH("fv_flux_f64", st,
+                  launch_fv_flux_f64(mesh, v, static_cast<const double *>(f), static_cast<const double *>(G),
+                                     static_cast<double *>(L), st),
+                  "transport: fluxes");
+    else
+        BZ_LAUNCH("fv_flux_f32", st,
+                  launch_fv_flux_f32(mesh, v, static_cast<const float *>(f), static_cast<const float *>(G),
+                                     static_cast<float *>(L), st),
+                  "transport: fluxes");
+    return BZ_OK;
+}
+
 int check_input(int precision, const void *f, int64_t count, cudaStream_t st) {
     int *err = device_error_word();
     if (!err) return fail(BZ_ENOMEM, "device error word allocation failed");
@@ -421,6 +461,34 @@ int step_sequence(const bz_modes *m, const Tableau &t, int model, double dt, dou
         void *F_l = (l == t.s - 1) ? f_out : static_cast<void *>(Fbuf);
         int rc = run_stage(m, t, l, model, dt, eps, f_n, F_l, G, P, L_res, n, precision, flags, st, coll);
         if (rc) return rc;
+    }
+    return BZ_OK;
+}
+
+// The stage sequence coupled to the transport step: after stage l the
+// residual L_l = <L(F_l^w)>_x of the stage value enters the explicit part of
+// every later stage (eq. GIMEX_n; the correction Delta Q vanishes for a
+// reconstruction that keeps the cell averages).  Scratch: step scratch, then
+// [stages][cell][nv] residuals, then the reconstruction's gradients.
+int step_sequence_fv(const bz_modes *m, const bz_mesh *mesh, const Tableau &t, int model, double dt, double eps,
+                     const void *f_n, void *f_out, int64_t n, int precision, int flags, cudaStream_t st,
+                     void *scratch, size_t step_bytes) {
+    const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
+    const int64_t stride = n * m->g->v.nv;
+    char *G = static_cast<char *>(scratch);
+    char *P = G + (size_t)t.s * stride * es;
+    char *Fbuf = P + (size_t)t.s * stride * es;
+    char *coll = Fbuf + (size_t)stride * es;
+    char *Lbuf = static_cast<char *>(scratch) + step_bytes;
+    char *tsc = Lbuf + (size_t)t.s * stride * es;
+    for (int l = 0; l < t.s; ++l) {
+        void *F_l = (l == t.s - 1) ? f_out : static_cast<void *>(Fbuf);
+        int rc = run_stage(m, t, l, model, dt, eps, f_n, F_l, G, P, Lbuf, n, precision, flags, st, coll);
+        if (rc) return rc;
+        if (l < t.s - 1) {
+            rc = transport_chain(mesh, m->g, precision, F_l, Lbuf + (size_t)l * stride * es, st, tsc);
+            if (rc) return rc;
+        }
     }
     return BZ_OK;
 }
@@ -708,6 +776,63 @@ int imex_step(const bz_modes *m, int scheme, int model, double dt, double eps, c
     BZ_TRY(cudaGraphLaunch(ne.exec, st), "imex_step: graph launch");
     return BZ_OK;
 }
+
+int imex_step_fv(const bz_modes *m, const bz_mesh *mesh, int scheme, int model, double dt, double eps,
+                 const void *f_n, void *f_out, int precision, int flags, void *stream) {
+    Tableau t;
+    if (!mesh) return fail(BZ_EINVAL, "imex_step_fv: mesh is NULL");
+    int rc = check_imex_args(m, scheme, model, dt, eps, precision, mesh->n_cells, "imex_step_fv", t);
+    if (rc) return rc;
+    if (m->g->v.dim != 2) return fail(BZ_ENOTSUP, "imex_step_fv: the transport step needs a 2-D velocity grid");
+    if (mesh->device != m->g->device) return fail(BZ_EINVAL, "imex_step_fv: mesh and modes on different devices");
+    if (!f_n || !f_out) return fail(BZ_EINVAL, "imex_step_fv: NULL buffer");
+    if (f_n == f_out) return fail(BZ_EINVAL, "imex_step_fv: f_n and f_out must differ");
+    if (flags & ~(BZ_CONSERVE | BZ_CHECK_INPUT)) return fail(BZ_EINVAL, "imex_step_fv: unknown flag");
+    DeviceGuard dg(m->g->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = mesh->n_cells;
+    const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
+    if (flags & BZ_CHECK_INPUT) {
+        rc = check_input(precision, f_n, n * m->g->v.nv, st);
+        if (rc) return rc;
+    }
+    const size_t step_bytes = (step_scratch_bytes(m, t, n, precision) + 255) / 256 * 256;
+    const size_t bytes = step_bytes + (size_t)t.s * n * m->g->v.nv * es + transport_scratch_bytes(mesh, m->g, precision);
+    Scratch s;
+    BZ_TRY(s.alloc(bytes, st), "imex_step_fv: scratch");
+    return step_sequence_fv(m, mesh, t, model, dt, eps, f_n, f_out, n, precision, flags, st, s.p, step_bytes);
+}
+
+int build_fv_mesh(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
+                  const int64_t *cell_vertices, int order, bz_mesh **out) {
+    return fv_mesh_create(n_vertices, xy, n_cells, cell_ptr, cell_vertices, order, out);
+}
+
+int transport_residual(const bz_mesh *mesh, const bz_grid *g, int precision, const void *f, void *L, void *stream) {
+    if (!mesh || !g) return fail(BZ_EINVAL, "transport_residual: NULL mesh or grid");
+    if (precision != BZ_FP64 && precision != BZ_FP32) return fail(BZ_EINVAL, "transport_residual: unknown precision");
+    if (g->v.dim != 2) return fail(BZ_ENOTSUP, "transport_residual: the transport step needs a 2-D velocity grid");
+    if (mesh->device != g->device) return fail(BZ_EINVAL, "transport_residual: mesh and grid on different devices");
+    if (!f || !L) return fail(BZ_EINVAL, "transport_residual: f or L is NULL");
+    const size_t bytes = (size_t)mesh->n_cells * g->v.nv * (precision == BZ_FP64 ? sizeof(double) : sizeof(float));
+    const char *fb = static_cast<const char *>(f);
+    const char *lb = static_cast<const char *>(L);
+    if (fb < lb + bytes && lb < fb + bytes) return fail(BZ_EINVAL, "transport_residual: f and L overlap");
+    DeviceGuard dg(g->device);
+    return transport_chain(mesh, g, precision, f, L, static_cast<cudaStream_t>(stream));
+}
+
+int bz_mesh_info(const bz_mesh *mesh, int64_t out[5]) {
+    if (!mesh || !out) return fail(BZ_EINVAL, "bz_mesh_info: NULL argument");
+    out[0] = mesh->n_cells;
+    out[1] = mesh->n_faces_interior;
+    out[2] = mesh->n_faces_boundary;
+    out[3] = mesh->max_faces;
+    out[4] = mesh->order;
+    return BZ_OK;
+}
+
+void bz_mesh_destroy(bz_mesh *mesh) { fv_mesh_destroy(mesh); }
 
 int group_collide(const bz_group_item *items, int n_items, int precision, int flags, void *stream) {
     if (!items || n_items < 0 || n_items > 1024) return fail(BZ_EINVAL, "group_collide: bad item list");

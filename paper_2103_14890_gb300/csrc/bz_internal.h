@@ -87,6 +87,41 @@ struct bz_modes {
 };
 
 namespace bz {
+// Finite-volume mesh of the transport step (fv_mesh.cpp, k_transport.cu):
+// polygonal cells with at most kFvMaxFaces faces, per-cell tables in
+// [cell][slot] layout, FP64 and FP32 copies of the real-valued ones.
+constexpr int kFvMaxFaces = 8;
+constexpr int kFvCentral = 5;       // central stencil: the cell and its 5 nearest cells (2 x 3 cells)
+
+template <typename T> struct FvTables {
+    const T *inv_area;      // [cell]
+    const T *h2;            // [cell] h_i^2
+    const T *fn;            // [cell][face][2]  |e| n_e
+    const T *off_i;         // [cell][face][2]  x_face - x_b,i
+    const T *off_j;         // [cell][face][2]  x_face - x_b,j (neighbour side)
+    const T *Rc;            // [cell][2][kFvCentral] least-squares gradient rows
+    const T *Rs;            // [cell][face][4]  sector inverses (row-major 2 x 2)
+};
+}  // namespace bz
+
+struct bz_mesh {
+    int device;
+    int order;              // 1: piecewise constant, 2: CWENO with degree-1 polynomials
+    int64_t n_cells, n_faces_interior, n_faces_boundary;
+    int max_faces;
+    int *d_nface;           // [cell] faces
+    int *d_nb;              // [cell][face] neighbour, -1 boundary
+    int *d_ncen;            // [cell] central stencil size (<= kFvCentral)
+    int *d_cen;             // [cell][kFvCentral]
+    int *d_nsec;            // [cell] sectors
+    int *d_sec;             // [cell][face][2] sector cells
+    void *d_real64;         // one block holding the FvTables<double> arrays
+    void *d_real32;         // one block holding the FvTables<float> arrays
+    bz::FvTables<double> t64;
+    bz::FvTables<float> t32;
+};
+
+namespace bz {
 
 // ---- kernels (k_dft.cu) ---------------------------------------------------
 // Forward DFT of f [n][N^d] into the tiled half spectrum fhat
@@ -183,6 +218,18 @@ cudaError_t launch_imex_stage_f32(const GridView &g, const StageCoef &c, const f
 cudaError_t launch_check_input_f64(const double *f, int64_t count, int *err, cudaStream_t st);
 cudaError_t launch_check_input_f32(const float *f, int64_t count, int *err, cudaStream_t st);
 cudaError_t launch_fill_zero(void *p, int64_t bytes, cudaStream_t st);
+
+// ---- transport residual (k_transport.cu) ----------------------------------
+// G [cell][2][nv] CWENO gradients (order 2 only), then
+// L [cell][nv] = (1/|P_i|) sum_e |e| F_Rusanov(f_L, f_R; v . n_e).
+cudaError_t launch_fv_gradient_f64(const bz_mesh *mesh, const GridView &g, const double *f, double *G,
+                                   cudaStream_t st);
+cudaError_t launch_fv_gradient_f32(const bz_mesh *mesh, const GridView &g, const float *f, float *G,
+                                   cudaStream_t st);
+cudaError_t launch_fv_flux_f64(const bz_mesh *mesh, const GridView &g, const double *f, const double *G, double *L,
+                               cudaStream_t st);
+cudaError_t launch_fv_flux_f32(const bz_mesh *mesh, const GridView &g, const float *f, const float *G, float *L,
+                               cudaStream_t st);
 
 // Device error word of the current device (allocated on first use; api.cu).
 int *device_error_word();

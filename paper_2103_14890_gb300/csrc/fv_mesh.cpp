@@ -1,0 +1,313 @@
+// fv_mesh.cpp -- host set-up of the finite-volume transport step (Sec. 3.2):
+// polygon geometry, face pairing, CWENO stencils and their reconstruction
+// matrices, uploaded once per mesh.
+//
+// Geometry.  Every cell is stored counter-clockwise (shoelace sign); its area
+// and barycentre x_b come from the polygon formulas, h_i is the largest
+// distance from x_b to a vertex (the characteristic length that scales the
+// smoothness indicators).  Edge a -> b of a counter-clockwise polygon has the
+// outward normal (y_b - y_a, -(x_b - x_a)) / |e|; the cell owning edge b -> a
+// is the neighbour; an edge without one is a (transmissive) boundary face.
+//
+// CWENO of degree 1 (eq. CWENO:Popt, CWENO:P0, CWENO:Prec).  With the
+// zero-mean Taylor basis about x_b (eq. Dubiner_phi_spatial) a polynomial
+// that keeps the cell average is fbar_i + g . (x - x_b,i), and its average
+// over P_j is fbar_i + g . (x_b,j - x_b,i).  So
+//   - the optimal polynomial's gradient is the least-squares solution over
+//     the central stencil: g_opt = (A^T A)^-1 A^T d, A's rows the barycentre
+//     offsets of the 2 M(M) - 1 = 5 nearest cells (among the cells that share
+//     a vertex with P_i or with one of its vertex neighbours; ties by index),
+//     d the differences of their averages to fbar_i;
+//   - a sector polynomial (cell, neighbour across face q, neighbour across
+//     face q + 1) reproduces both averages: g_L = A_L^-1 d_L, skipped when
+//     the two offsets are numerically collinear.
+// The device keeps R_c = (A^T A)^-1 A^T and A_L^-1 per cell; the nonlinear
+// weights are formed per velocity by the gradient kernel.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "bz_internal.h"
+
+namespace bz {
+
+namespace {
+
+struct HostMesh {
+    int64_t n = 0;
+    std::vector<int> nface, nb, ncen, cen, nsec, sec;
+    std::vector<double> inv_area, h2, fn, off_i, off_j, Rc, Rs;
+};
+
+template <typename T>
+FvTables<T> carve(void *base, int64_t n) {
+    T *p = static_cast<T *>(base);
+    FvTables<T> t;
+    t.inv_area = p; p += n;
+    t.h2 = p; p += n;
+    t.fn = p; p += n * kFvMaxFaces * 2;
+    t.off_i = p; p += n * kFvMaxFaces * 2;
+    t.off_j = p; p += n * kFvMaxFaces * 2;
+    t.Rc = p; p += n * 2 * kFvCentral;
+    t.Rs = p;
+    return t;
+}
+constexpr int64_t kRealPerCell = 1 + 1 + 3 * kFvMaxFaces * 2 + 2 * kFvCentral + kFvMaxFaces * 4;
+
+void fill_real(const HostMesh &h, std::vector<double> &out) {
+    const int64_t n = h.n;
+    out.assign((size_t)(n * kRealPerCell), 0.0);
+    double *p = out.data();
+    auto put = [&p](const std::vector<double> &v) {
+        memcpy(p, v.data(), sizeof(double) * v.size());
+        p += v.size();
+    };
+    put(h.inv_area);
+    put(h.h2);
+    put(h.fn);
+    put(h.off_i);
+    put(h.off_j);
+    put(h.Rc);
+    put(h.Rs);
+}
+
+template <typename X> cudaError_t upload(X **d, const std::vector<X> &v) {
+    cudaError_t e = cudaMalloc(d, sizeof(X) * v.size());
+    if (e == cudaSuccess) e = cudaMemcpy(*d, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+}  // namespace
+
+void fv_mesh_destroy(bz_mesh *m) {
+    if (!m) return;
+    cudaFree(m->d_nface);
+    cudaFree(m->d_nb);
+    cudaFree(m->d_ncen);
+    cudaFree(m->d_cen);
+    cudaFree(m->d_nsec);
+    cudaFree(m->d_sec);
+    cudaFree(m->d_real64);
+    cudaFree(m->d_real32);
+    free(m);
+}
+
+int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
+                   const int64_t *cell_vertices, int order, bz_mesh **out) {
+    if (!out) return fail(BZ_EINVAL, "build_fv_mesh: out is NULL");
+    *out = nullptr;
+    if (n_vertices < 3 || !xy) return fail(BZ_EINVAL, "build_fv_mesh: need >= 3 vertices and their coordinates");
+    if (n_cells < 1 || n_cells > (int64_t)1 << 30 || !cell_ptr || !cell_vertices)
+        return fail(BZ_EINVAL, "build_fv_mesh: bad cell list");
+    if (order != 1 && order != 2) return fail(BZ_EINVAL, "build_fv_mesh: order must be 1 or 2");
+    if (cell_ptr[0] != 0) return fail(BZ_EINVAL, "build_fv_mesh: cell_ptr[0] must be 0");
+    const int64_t n = n_cells;
+    HostMesh h;
+    h.n = n;
+    std::vector<std::vector<int64_t>> cells((size_t)n);
+    std::vector<double> area(n), bx(n), by(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t a = cell_ptr[i], b = cell_ptr[i + 1];
+        if (b - a < 3 || b - a > kFvMaxFaces)
+            return fail(BZ_EINVAL, "build_fv_mesh: cells need 3 to 8 vertices");
+        std::vector<int64_t> c(cell_vertices + a, cell_vertices + b);
+        for (int64_t v : c)
+            if (v < 0 || v >= n_vertices) return fail(BZ_EINVAL, "build_fv_mesh: vertex index out of range");
+        // shoelace area and polygon barycentre, coordinates relative to the
+        // first vertex (absolute coordinates would cancel in the cross
+        // products of a small cell); store counter-clockwise
+        auto geom = [&](const std::vector<int64_t> &cc, double &A, double &cx, double &cy) {
+            A = cx = cy = 0.0;
+            const size_t k = cc.size();
+            const double ox = xy[2 * cc[0]], oy = xy[2 * cc[0] + 1];
+            for (size_t q = 0; q < k; ++q) {
+                const double x0 = xy[2 * cc[q]] - ox, y0 = xy[2 * cc[q] + 1] - oy;
+                const double x1 = xy[2 * cc[(q + 1) % k]] - ox, y1 = xy[2 * cc[(q + 1) % k] + 1] - oy;
+                const double cr = x0 * y1 - x1 * y0;
+                A += cr;
+                cx += (x0 + x1) * cr;
+                cy += (y0 + y1) * cr;
+            }
+            A *= 0.5;
+            cx = ox + cx / (6.0 * A);
+            cy = oy + cy / (6.0 * A);
+        };
+        double A, cx, cy;
+        geom(c, A, cx, cy);
+        if (A < 0) {
+            std::reverse(c.begin(), c.end());
+            geom(c, A, cx, cy);
+        }
+        if (!(A > 0)) return fail(BZ_EINVAL, "build_fv_mesh: degenerate cell (zero area)");
+        area[i] = A;
+        bx[i] = cx;
+        by[i] = cy;
+        double hm = 0.0;
+        for (int64_t v : c) hm = std::max(hm, hypot(xy[2 * v] - cx, xy[2 * v + 1] - cy));
+        h.inv_area.push_back(1.0 / A);
+        h.h2.push_back(hm * hm);
+        cells[i] = std::move(c);
+    }
+    // directed edge -> owning cell
+    std::unordered_map<uint64_t, int64_t> owner;
+    owner.reserve((size_t)(n * 4));
+    auto key = [](int64_t a, int64_t b) { return ((uint64_t)a << 32) | (uint64_t)b; };
+    for (int64_t i = 0; i < n; ++i) {
+        const auto &c = cells[i];
+        for (size_t q = 0; q < c.size(); ++q) {
+            if (!owner.emplace(key(c[q], c[(q + 1) % c.size()]), i).second)
+                return fail(BZ_EINVAL, "build_fv_mesh: an edge is used twice in the same direction (overlapping or "
+                                       "inconsistently oriented cells)");
+        }
+    }
+    h.nface.assign(n, 0);
+    h.nb.assign(n * kFvMaxFaces, -1);
+    h.fn.assign(n * kFvMaxFaces * 2, 0.0);
+    h.off_i.assign(n * kFvMaxFaces * 2, 0.0);
+    h.off_j.assign(n * kFvMaxFaces * 2, 0.0);
+    int64_t interior = 0, boundary = 0;
+    int maxf = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const auto &c = cells[i];
+        const int k = (int)c.size();
+        h.nface[i] = k;
+        maxf = std::max(maxf, k);
+        for (int q = 0; q < k; ++q) {
+            const int64_t a = c[q], b = c[(q + 1) % k];
+            const double dx = xy[2 * b] - xy[2 * a], dy = xy[2 * b + 1] - xy[2 * a + 1];
+            const double mx = 0.5 * (xy[2 * a] + xy[2 * b]), my = 0.5 * (xy[2 * a + 1] + xy[2 * b + 1]);
+            const size_t s = (size_t)i * kFvMaxFaces + q;
+            h.fn[2 * s] = dy;                 // |e| n_e = (dy, -dx)
+            h.fn[2 * s + 1] = -dx;
+            h.off_i[2 * s] = mx - bx[i];
+            h.off_i[2 * s + 1] = my - by[i];
+            auto it = owner.find(key(b, a));
+            if (it != owner.end()) {
+                const int64_t j = it->second;
+                h.nb[s] = (int)j;
+                h.off_j[2 * s] = mx - bx[j];
+                h.off_j[2 * s + 1] = my - by[j];
+                ++interior;
+            } else {
+                ++boundary;
+            }
+        }
+    }
+    h.ncen.assign(n, 0);
+    h.cen.assign(n * kFvCentral, 0);
+    h.Rc.assign(n * 2 * kFvCentral, 0.0);
+    h.nsec.assign(n, 0);
+    h.sec.assign(n * kFvMaxFaces * 2, 0);
+    h.Rs.assign(n * kFvMaxFaces * 4, 0.0);
+    if (order == 2) {
+        // vertex -> cells
+        std::vector<int64_t> vptr(n_vertices + 1, 0), vcell;
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t v : cells[i]) ++vptr[v + 1];
+        for (int v = 0; v < n_vertices; ++v) vptr[v + 1] += vptr[v];
+        vcell.assign(vptr[n_vertices], 0);
+        std::vector<int64_t> fillp(vptr.begin(), vptr.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t v : cells[i]) vcell[fillp[v]++] = i;
+        auto vertex_neighbours = [&](int64_t i, std::vector<int64_t> &out) {
+            for (int64_t v : cells[i])
+                for (int64_t p = vptr[v]; p < vptr[v + 1]; ++p)
+                    if (vcell[p] != i) out.push_back(vcell[p]);
+        };
+        std::vector<int64_t> ring, cand;
+        std::vector<std::pair<double, int64_t>> dist;
+        for (int64_t i = 0; i < n; ++i) {
+            ring.clear();
+            vertex_neighbours(i, ring);
+            cand = ring;
+            for (int64_t j : ring) vertex_neighbours(j, cand);
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            dist.clear();
+            for (int64_t j : cand)
+                if (j != i) dist.emplace_back(hypot(bx[j] - bx[i], by[j] - by[i]), j);
+            std::sort(dist.begin(), dist.end());
+            const int nc = (int)std::min<size_t>(kFvCentral, dist.size());
+            double ata[3] = {0, 0, 0};
+            for (int q = 0; q < nc; ++q) {
+                const int64_t j = dist[q].second;
+                h.cen[i * kFvCentral + q] = (int)j;
+                const double ax = bx[j] - bx[i], ay = by[j] - by[i];
+                ata[0] += ax * ax;
+                ata[1] += ax * ay;
+                ata[2] += ay * ay;
+            }
+            h.ncen[i] = nc;
+            const double det = ata[0] * ata[2] - ata[1] * ata[1];
+            if (nc >= 2 && det > 1e-300) {
+                const double i00 = ata[2] / det, i01 = -ata[1] / det, i11 = ata[0] / det;
+                for (int q = 0; q < nc; ++q) {
+                    const int64_t j = dist[q].second;
+                    const double ax = bx[j] - bx[i], ay = by[j] - by[i];
+                    h.Rc[(i * 2 + 0) * kFvCentral + q] = i00 * ax + i01 * ay;
+                    h.Rc[(i * 2 + 1) * kFvCentral + q] = i01 * ax + i11 * ay;
+                }
+            }
+            // sectors: consecutive faces with neighbours on both
+            const int k = h.nface[i];
+            int ns = 0;
+            for (int q = 0; q < k; ++q) {
+                const int a = h.nb[i * kFvMaxFaces + q], b = h.nb[i * kFvMaxFaces + (q + 1) % k];
+                if (a < 0 || b < 0) continue;
+                const double a0 = bx[a] - bx[i], a1 = by[a] - by[i], b0 = bx[b] - bx[i], b1 = by[b] - by[i];
+                const double mxa = std::max(std::max(fabs(a0), fabs(a1)), std::max(fabs(b0), fabs(b1)));
+                const double dt = a0 * b1 - a1 * b0;
+                if (fabs(dt) <= 1e-12 * mxa * mxa) continue;
+                // A = [[a0, a1], [b0, b1]] (rows: offsets), g = A^-1 (d_a, d_b)
+                double *R = &h.Rs[((size_t)i * kFvMaxFaces + ns) * 4];
+                R[0] = b1 / dt;
+                R[1] = -a1 / dt;
+                R[2] = -b0 / dt;
+                R[3] = a0 / dt;
+                h.sec[((size_t)i * kFvMaxFaces + ns) * 2] = a;
+                h.sec[((size_t)i * kFvMaxFaces + ns) * 2 + 1] = b;
+                ++ns;
+            }
+            h.nsec[i] = ns;
+        }
+    }
+    bz_mesh *m = (bz_mesh *)calloc(1, sizeof(bz_mesh));
+    if (!m) return fail(BZ_ENOMEM, "build_fv_mesh: host allocation");
+    cudaGetDevice(&m->device);
+    m->order = order;
+    m->n_cells = n;
+    m->n_faces_interior = interior / 2;
+    m->n_faces_boundary = boundary;
+    m->max_faces = maxf;
+    std::vector<double> real;
+    fill_real(h, real);
+    std::vector<float> real32(real.size());
+    for (size_t q = 0; q < real.size(); ++q) real32[q] = (float)real[q];
+    cudaError_t e = upload(&m->d_nface, h.nface);
+    if (e == cudaSuccess) e = upload(&m->d_nb, h.nb);
+    if (e == cudaSuccess) e = upload(&m->d_ncen, h.ncen);
+    if (e == cudaSuccess) e = upload(&m->d_cen, h.cen);
+    if (e == cudaSuccess) e = upload(&m->d_nsec, h.nsec);
+    if (e == cudaSuccess) e = upload(&m->d_sec, h.sec);
+    double *r64 = nullptr;
+    float *r32 = nullptr;
+    if (e == cudaSuccess) e = upload(&r64, real);
+    m->d_real64 = r64;
+    if (e == cudaSuccess) e = upload(&r32, real32);
+    m->d_real32 = r32;
+    if (e != cudaSuccess) {
+        fv_mesh_destroy(m);
+        return cuda_fail(e, "build_fv_mesh: device tables");
+    }
+    m->t64 = carve<double>(m->d_real64, n);
+    m->t32 = carve<float>(m->d_real32, n);
+    *out = m;
+    return BZ_OK;
+}
+
+}  // namespace bz

@@ -127,6 +127,25 @@ def sod_mesh(n_side=100, seed=1004, jitter=0.3):
     return cent, float(np.sqrt(area.mean()))
 
 
+def mesh_states(bary, N, L, jump=False):
+    """Maxwellians on the velocity grid for cells with barycentres bary
+    (n, 2): smooth fields rho = 1 + 0.3 sin(2 pi x) cos(2 pi y),
+    u = 0.3 (cos(2 pi y), sin(2 pi x)), theta = 1 + 0.2 cos(2 pi (x + y)); with
+    jump=True the explosion-problem states (1, 0, 1) for x < 0.5 and
+    (0.125, 0, 0.8) for x >= 0.5 instead."""
+    x, y = bary[:, 0], bary[:, 1]
+    if jump:
+        left = x < 0.5
+        rho = np.where(left, 1.0, 0.125)
+        th = np.where(left, 1.0, 0.8)
+        u = np.zeros((len(x), 2))
+    else:
+        rho = 1.0 + 0.3 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+        u = 0.3 * np.stack([np.cos(2 * np.pi * y), np.sin(2 * np.pi * x)], axis=1)
+        th = 1.0 + 0.2 * np.cos(2 * np.pi * (x + y))
+    return _gaussian(2, N, L, rho, u, th)
+
+
 def sod_cells(N, L, n_side=100, seed=1004):
     """Cell data of the density/temperature jump across x = 0.5 (the states of
     the explosion problem of Sec. 4.2): (rho, u, theta) = (1, 0, 1) left and

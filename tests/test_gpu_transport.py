@@ -1,0 +1,207 @@
+"""Parity of the CUDA transport step (Sec. 3.2: CWENO reconstruction, Rusanov
+fluxes; Sec. 3.4: the step coupled to the IMEX stages) with the FP64 oracle
+(`oracle/fv.py`), through the C ABI.
+
+Tolerance: a running-error bound of the residual.  L is a sum of face fluxes
+scaled by 1/|P_i|; on a sliver cell the fluxes cancel to a small L, so its
+rounding is set by the magnitudes summed, not by L.  The test evaluates the
+residual once more with every quantity replaced by its magnitude,
+  M_ik = (1/|P_i|) sum_e |e| (|v_1 n_1| + |v_2 n_2|) (|f_L| + |f_R|),
+  |f_L| <= |f_i| + |x_f - x_b,i|_1 G_i,
+with G_i the largest gradient any CWENO polynomial of the cell can take from
+the magnitudes of its stencil (|R| applied to |f_j| + |f_i|; the weighted
+combination is convex), and requires |L_gpu - L_oracle| <= 64 u M_ik
+element by element, u = 2^-53 for BZ_FP64 and 2^-24 for BZ_FP32 (about 40
+roundings lie on the path from the averages to L), plus the same sums of the
+absolute rounding error of subnormal values (the Maxwellian tails of f fall
+below the FP32 normal range).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2103_14890_gb300 import workloads
+from gpu_util import as_input, bz_module, relerr, to_dev
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+U64, ETA64 = 2.0 ** -53, 2.0 ** -1075
+U32, ETA32 = 2.0 ** -24, 2.0 ** -150
+
+
+@pytest.fixture(scope="module")
+def bz():
+    return bz_module()
+
+
+@pytest.fixture(scope="module")
+def fvo():
+    from oracle import fv
+    return fv
+
+
+def _tri(n_side, seed=7):
+    return workloads.sod_triangulation(n_side=n_side, seed=seed)
+
+
+def _mixed():
+    n = 8
+    g = np.linspace(0, 1, n + 1)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    rng = np.random.default_rng(3)
+    X[1:-1, 1:-1] += rng.uniform(-0.2, 0.2, (n - 1, n - 1)) / n
+    Y[1:-1, 1:-1] += rng.uniform(-0.2, 0.2, (n - 1, n - 1)) / n
+    pts = np.stack([X.ravel(), Y.ravel()], 1)
+    idx = np.arange((n + 1) ** 2).reshape(n + 1, n + 1)
+    cells = []
+    for a in range(n):
+        for b in range(n):
+            q = [idx[a, b], idx[a + 1, b], idx[a + 1, b + 1], idx[a, b + 1]]
+            if (a + b) % 3 == 0:
+                cells += [[q[0], q[1], q[2]], [q[0], q[2], q[3]]]
+            else:
+                cells.append(q[::-1] if (a * b) % 2 else q)      # both orientations
+    return pts, cells
+
+
+def _magnitude(om, f, N, L, order, fvo):
+    """M_ik of the module docstring."""
+    v1, v2 = fvo.velocity_grid(N, L)
+    af = np.abs(np.asarray(f, dtype=np.float64))
+    n = len(om.cells)
+    G = np.zeros_like(af)
+    if order == 2:
+        for i in range(n):
+            st = om.central_stencil(i)
+            A = np.array([om.bary[j] - om.bary[i] for j in st])
+            R = np.abs(np.linalg.inv(A.T @ A) @ A.T)
+            gc = (R @ (af[st] + af[i])).max(axis=0)
+            gs = []
+            for a, b in om.sectors(i):
+                Rs = np.abs(np.linalg.inv(np.array([om.bary[a] - om.bary[i], om.bary[b] - om.bary[i]])))
+                gs.append((Rs @ np.stack([af[a] + af[i], af[b] + af[i]])).max(axis=0))
+            cand = [gc] + gs
+            if gs:
+                cand.append((gc + 0.25 * sum(gs) / len(gs)) / 0.75)
+            G[i] = np.max(cand, axis=0)
+    M = np.zeros_like(af)
+    for i, fl in enumerate(om.faces):
+        for (j, ln, nx, ny, mx, my) in fl:
+            avn = ln * (np.abs(v1 * nx) + np.abs(v2 * ny))
+            fl_ = af[i] + G[i] * (abs(mx - om.bary[i, 0]) + abs(my - om.bary[i, 1]))
+            fr_ = fl_ if j < 0 else af[j] + G[j] * (abs(mx - om.bary[j, 0]) + abs(my - om.bary[j, 1]))
+            M[i] += avn * (fl_ + fr_)
+        M[i] /= om.area[i]
+    return M
+
+
+def _check(got, want, om, fin, N, L, order, fvo, u, eta):
+    """err <= 64 (u M(|f|) + eta M(1)): eta is the absolute error of a rounding
+    in the subnormal range (2^-150 in FP32), which the tails of f reach; M(1)
+    carries it through the same sums."""
+    err = np.abs(got - want)
+    bound = 64 * (u * _magnitude(om, fin, N, L, order, fvo) +
+                  eta * _magnitude(om, np.ones_like(fin), N, L, order, fvo))
+    assert (err <= bound).all(), float((err / np.maximum(bound, 1e-300)).max())
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("mesh_kind,N,jump", [("tri", 8, False), ("tri", 8, True), ("mixed", 8, False),
+                                              ("tri", 32, False)])
+def test_transport_fp64_matches_oracle(bz, fvo, order, mesh_kind, N, jump):
+    Lv = 8.0
+    pts, cells = _tri(10 if N == 32 else 16) if mesh_kind == "tri" else _mixed()
+    om = fvo.Mesh(pts, cells)
+    f = workloads.mesh_states(om.bary, N, Lv, jump=jump)
+    m = bz.Mesh(pts, cells, order=order)
+    assert m.n_cells == len(om.cells)
+    g = bz.Grid(2, N, Lv)
+    Lr = bz.transport_residual(m, g, to_dev(f, "fp64"), precision="fp64")
+    bz.check()
+    want = fvo.transport_residual(om, f, N, Lv, order=order)
+    _check(Lr.cpu().numpy(), want, om, f, N, Lv, order, fvo, U64, ETA64)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("jump", [False, True])
+def test_transport_fp32_within_bound(bz, fvo, order, jump):
+    N, Lv = 16, 8.0
+    pts, cells = _tri(14)
+    om = fvo.Mesh(pts, cells)
+    f = workloads.mesh_states(om.bary, N, Lv, jump=jump)
+    fin = as_input(f, "fp32")
+    m = bz.Mesh(pts, cells, order=order)
+    Lr = bz.transport_residual(m, bz.Grid(2, N, Lv), to_dev(f, "fp32"), precision="fp32")
+    bz.check()
+    want = fvo.transport_residual(om, fin, N, Lv, order=order)
+    _check(Lr.double().cpu().numpy(), want, om, fin, N, Lv, order, fvo, U32, ETA32)
+
+
+def test_mesh_info_and_errors(bz):
+    pts, cells = _tri(12)
+    m = bz.Mesh(pts, cells, order=2)
+    assert m.max_faces == 3 and m.order == 2
+    assert 3 * m.n_cells == 2 * m.n_faces_interior + m.n_faces_boundary
+    lib = bz.load()
+    out = ctypes.c_void_p()
+    xy = np.ascontiguousarray(pts, dtype=np.float64)
+    ptr = np.array([0, 3], dtype=np.int64)
+    bad = np.array([0, 1, len(pts)], dtype=np.int64)              # vertex out of range
+    assert lib.build_fv_mesh(len(pts), xy.ctypes.data_as(ctypes.c_void_p), 1, ptr.ctypes.data_as(ctypes.c_void_p),
+                             bad.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(out)) == bz.EINVAL
+    flat = np.array([0, 1, 2], dtype=np.int64)
+    line = np.ascontiguousarray([[0, 0], [1, 0], [2, 0]], dtype=np.float64)   # zero area
+    assert lib.build_fv_mesh(3, line.ctypes.data_as(ctypes.c_void_p), 1, ptr.ctypes.data_as(ctypes.c_void_p),
+                             flat.ctypes.data_as(ctypes.c_void_p), 2, ctypes.byref(out)) == bz.EINVAL
+    g3 = bz.Grid(3, 8, 8.0)
+    import torch
+    f = torch.zeros((m.n_cells, 512), dtype=torch.float32, device="cuda")
+    with pytest.raises(bz.BzError):
+        bz.transport_residual(m, g3, f, precision="fp32")
+
+
+def test_imex_step_fv_matches_oracle(bz, fvo):
+    """ARS(2,2,2) with transport: the oracle composes the stages, stage l taking
+    the residuals of the stage values 0..l-1 (each computed by oracle/fv.py)."""
+    import oracle
+    N, Lv, dt, eps = 8, 6.0, 2e-3, 5e-2
+    pts, cells = _tri(10)
+    om = fvo.Mesh(pts, cells)
+    f = workloads.mesh_states(om.bary, N, Lv, jump=True)
+    k = oracle.Kernel(2, N, Lv, 0.0)
+    Lres = np.zeros((3,) + f.shape)
+    for l in range(2):
+        _, F, _, _ = k.imex_step(f, dt, eps, Lres=Lres, stages=True)
+        Lres[l] = fvo.transport_residual(om, F[l], N, Lv, order=2)
+    want = k.imex_step(f, dt, eps, Lres=Lres)
+    m = bz.Mesh(pts, cells, order=2)
+    md = bz.Modes(bz.Grid(2, N, Lv), 0.0)
+    got = bz.imex_step_fv(md, m, to_dev(f, "fp64"), dt, eps, precision="fp64")
+    bz.check()
+    assert relerr(got.cpu().numpy(), want) < TOL64
+    # and the fast collision form inside the same step
+    kf = oracle.FastKernel(N, Lv, 8)
+    Lres[:] = 0
+    for l in range(2):
+        _, F, _, _ = kf.imex_step(f, dt, eps, Lres=Lres, stages=True)
+        Lres[l] = fvo.transport_residual(om, F[l], N, Lv, order=2)
+    want_f = kf.imex_step(f, dt, eps, Lres=Lres)
+    got_f = bz.imex_step_fv(bz.FastModes(bz.Grid(2, N, Lv), 8), m, to_dev(f, "fp64"), dt, eps, precision="fp64")
+    bz.check()
+    assert relerr(got_f.cpu().numpy(), want_f) < TOL64
+
+
+def test_full_mesh_fp32_sampled(bz, fvo):
+    """The 19802-triangle mesh with the 32^2 grid (the measured configuration):
+    every cell against the oracle within the FP32 bound."""
+    N, Lv = 32, 10.0
+    pts, cells = workloads.sod_triangulation()
+    om = fvo.Mesh(pts, cells)
+    f = workloads.mesh_states(om.bary, N, Lv, jump=True)
+    fin = as_input(f, "fp32")
+    m = bz.Mesh(pts, cells, order=2)
+    Lr = bz.transport_residual(m, bz.Grid(2, N, Lv), to_dev(f, "fp32"), precision="fp32")
+    bz.check()
+    want = fvo.transport_residual(om, fin, N, Lv, order=2)
+    _check(Lr.double().cpu().numpy(), want, om, fin, N, Lv, 2, fvo, U32, ETA32)
