@@ -186,6 +186,8 @@ def main():
     ap.add_argument("--method", default="direct", choices=["direct", "fast"],
                     help="fast: time the fast spectral form (Maxwell molecules) as the main line instead")
     ap.add_argument("--ndirs", type=int, default=8, help="collision directions of the fast form")
+    ap.add_argument("--sections", default="transport,imex,grouped,fast",
+                    help="comma list of the extra measurements to run (transport, imex, grouped, fast)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -271,11 +273,15 @@ def main():
         value64 = cells * world / (ms64 / 1e3)
 
     extra = {}
-    if not args.no_extra and not fast:
+    sections = set(args.sections.split(",")) if not args.no_extra and not fast else set()
+    if "transport" in sections:
+        extra["transport"] = _transport_measure(bz, workloads, st, check=not args.no_cpu_baseline)
+    if "imex" in sections:
         extra["imex_step"] = _imex_measure(bz, workloads, barrier)
+    if "grouped" in sections:
         extra["grouped"] = _group_measure(bz, workloads, barrier)
-        extra["fast_spectral"] = _fast_measure(bz, f, f_host, st, args.ndirs,
-                                               check=not args.no_cpu_baseline)
+    if "fast" in sections:
+        extra["fast_spectral"] = _fast_measure(bz, f, f_host, st, args.ndirs, check=not args.no_cpu_baseline)
 
     # end to end: pinned host f -> device, collide, device -> pinned host Q
     e2e_val = None
@@ -330,6 +336,84 @@ def _timed(fn, steps, stream):
     e1.record(stream)
     e1.synchronize()
     return e0.elapsed_time(e1) / steps
+
+
+def _transport_measure(bz, workloads, st, check=True):
+    """Transport step of the finite-volume scheme on the 19802-triangle mesh
+    with the 32^2 velocity grid (the explosion-problem states): the residual
+    <L(f^w)>_x (CWENO degree 1 + Rusanov) in FP32 and FP64, its HBM roofline
+    (algorithmic bytes: f read once, L written once), the ARS(2,2,2) step
+    coupled to it (VHS direct sum; Maxwell fast form), and the oracle's rate
+    on a 50x50-lattice mesh."""
+    import numpy as np
+    import torch
+    pts, tri = workloads.sod_triangulation()
+    mesh = bz.Mesh(pts, tri, order=2)
+    P = pts[tri]
+    bary = P.mean(axis=1)
+    g = bz.Grid(2, N_V, L_BOX)
+    fh = workloads.mesh_states(bary, N_V, L_BOX, jump=True)
+    out = {"cells": int(mesh.n_cells), "velocities": N_V * N_V, "order": 2,
+           "mesh": "jittered 100x100 lattice, Delaunay, 19802 triangles",
+           "l2": "a 256 MB buffer is written before every timed call (f alone, 81 MB in FP32, would fit L2)"}
+    hbm = _measured_hbm()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")     # 256 MB > L2, written between calls
+    for prec, dt_, steps in (("fp32", torch.float32, 20), ("fp64", torch.float64, 5)):
+        f = torch.from_numpy(fh).to("cuda", dt_)
+        Lr = torch.empty_like(f)
+        for _ in range(3):
+            bz.transport_residual(mesh, g, f, Lr, precision=prec)
+        bz.check()
+        bz.profile(True)
+        ms = 0.0
+        for _ in range(steps):
+            flush.fill_(1)
+            ms += _timed(lambda: bz.transport_residual(mesh, g, f, Lr, precision=prec), 1, st)
+        ms /= steps
+        prof = bz.profile_read()
+        bz.profile(False)
+        es = 4 if prec == "fp32" else 8
+        alg = 2.0 * f.numel() * es
+        kern = {k: v[1] / max(1, v[0]) for k, v in prof.items()}
+        ent = {"ms_per_call": ms, "cell_velocity_updates_per_s": f.numel() / (ms / 1e3), "kernel_ms": kern,
+               "algorithmic_bytes": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9}
+        if prec == "fp32":
+            ent["roofline"] = {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                               "frac": alg / (ms / 1e3) / 1e9 / hbm,
+                               "note": "two passes: the reconstruction writes 2 gradient values per (cell, velocity) "
+                                       "that the flux pass reads back"}
+        out[prec] = ent
+    # the coupled step
+    hmesh = float(np.sqrt(np.abs(0.5 * ((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) -
+                                        (P[:, 2, 0] - P[:, 0, 0]) * (P[:, 1, 1] - P[:, 0, 1]))).mean()))
+    dtt = 0.5 * hmesh / (math.sqrt(2.0) * L_BOX)
+    f = torch.from_numpy(fh).to("cuda", torch.float32)
+    y = torch.empty_like(f)
+    for name, m in (("vhs_direct", bz.Modes(g, GAMMA)), ("maxwell_fast_A8", bz.FastModes(g, 8))):
+        bz.imex_step_fv(m, mesh, f, dtt, 5e-3, f_out=y, precision="fp32")
+        bz.check()
+        msi = _timed(lambda: bz.imex_step_fv(m, mesh, f, dtt, 5e-3, f_out=y, precision="fp32"), 5, st)
+        out["imex_step_fv_fp32_" + name] = {"ms_per_step": msi, "dt": dtt, "eps": 5e-3,
+                                            "cell_steps_per_s": f.shape[0] / (msi / 1e3)}
+    if check:
+        from oracle import fv
+        p2, t2 = workloads.sod_triangulation(n_side=50)
+        om = fv.Mesh(p2, t2)
+        f2 = workloads.mesh_states(om.bary, N_V, L_BOX, jump=True)
+        t0 = time.perf_counter()
+        fv.transport_residual(om, f2, N_V, L_BOX, order=2)
+        el = time.perf_counter() - t0
+        out["cpu_baseline"] = {"kind": "oracle", "value": f2.size / el, "unit": "cell-velocity updates/s",
+                               "sample": "%d-triangle mesh, 32^2 velocities (numpy, one process)" % len(t2)}
+    return out
+
+
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fp:
+            return float(json.load(fp)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
 
 
 def _imex_measure(bz, workloads, barrier):
@@ -535,6 +619,7 @@ def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, valu
         "imex_step": extra.get("imex_step"),
         "grouped": extra.get("grouped"),
         "fast_spectral": extra.get("fast_spectral"),
+        "transport": extra.get("transport"),
         "e2e": {"value": e2e_val, "unit": "cell-collision evals/s",
                 "h2d_bytes_per_step": int(Q.numel() * 4), "d2h_bytes_per_step": int(Q.numel() * 4)},
         "clocks": clk,

@@ -115,6 +115,7 @@ struct bz_mesh {
     int *d_cen;             // [cell][kFvCentral]
     int *d_nsec;            // [cell] sectors
     int *d_sec;             // [cell][face][2] sector cells
+    int *d_order;           // [cell] processing order: cells sorted along a Morton curve of their barycentres
     void *d_real64;         // one block holding the FvTables<double> arrays
     void *d_real32;         // one block holding the FvTables<float> arrays
     bz::FvTables<double> t64;

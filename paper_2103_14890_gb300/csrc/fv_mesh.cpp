@@ -40,7 +40,7 @@ namespace {
 
 struct HostMesh {
     int64_t n = 0;
-    std::vector<int> nface, nb, ncen, cen, nsec, sec;
+    std::vector<int> nface, nb, ncen, cen, nsec, sec, order;
     std::vector<double> inv_area, h2, fn, off_i, off_j, Rc, Rs;
 };
 
@@ -92,6 +92,7 @@ void fv_mesh_destroy(bz_mesh *m) {
     cudaFree(m->d_cen);
     cudaFree(m->d_nsec);
     cudaFree(m->d_sec);
+    cudaFree(m->d_order);
     cudaFree(m->d_real64);
     cudaFree(m->d_real32);
     free(m);
@@ -276,6 +277,36 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
             h.nsec[i] = ns;
         }
     }
+    // processing order: the kernels take cells along a Morton (Z-order) curve
+    // of the barycentres, so CTAs resident at the same time read neighbouring
+    // rows of f and of the gradients and share them in L2 (the results do not
+    // depend on the order)
+    {
+        double x0 = bx[0], x1 = bx[0], y0 = by[0], y1 = by[0];
+        for (int64_t i = 1; i < n; ++i) {
+            x0 = std::min(x0, bx[i]);
+            x1 = std::max(x1, bx[i]);
+            y0 = std::min(y0, by[i]);
+            y1 = std::max(y1, by[i]);
+        }
+        const double sx = x1 > x0 ? 65535.0 / (x1 - x0) : 0.0, sy = y1 > y0 ? 65535.0 / (y1 - y0) : 0.0;
+        auto spread = [](uint32_t v) {
+            uint64_t x = v & 0xffffu;
+            x = (x | (x << 8)) & 0x00ff00ffu;
+            x = (x | (x << 4)) & 0x0f0f0f0fu;
+            x = (x | (x << 2)) & 0x33333333u;
+            x = (x | (x << 1)) & 0x55555555u;
+            return x;
+        };
+        std::vector<std::pair<uint64_t, int>> key((size_t)n);
+        for (int64_t i = 0; i < n; ++i) {
+            const uint32_t qx = (uint32_t)((bx[i] - x0) * sx), qy = (uint32_t)((by[i] - y0) * sy);
+            key[i] = {spread(qx) | (spread(qy) << 1), (int)i};
+        }
+        std::sort(key.begin(), key.end());
+        h.order.resize(n);
+        for (int64_t i = 0; i < n; ++i) h.order[i] = key[i].second;
+    }
     bz_mesh *m = (bz_mesh *)calloc(1, sizeof(bz_mesh));
     if (!m) return fail(BZ_ENOMEM, "build_fv_mesh: host allocation");
     cudaGetDevice(&m->device);
@@ -294,6 +325,7 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
     if (e == cudaSuccess) e = upload(&m->d_cen, h.cen);
     if (e == cudaSuccess) e = upload(&m->d_nsec, h.nsec);
     if (e == cudaSuccess) e = upload(&m->d_sec, h.sec);
+    if (e == cudaSuccess) e = upload(&m->d_order, h.order);
     double *r64 = nullptr;
     float *r32 = nullptr;
     if (e == cudaSuccess) e = upload(&r64, real);

@@ -3,10 +3,12 @@
 // fluxes, for every cell and every discrete velocity of a 2-D grid.
 //
 // Layout: f, L are [cell][nv] (the collision operator's layout), so one
-// cell's velocities are contiguous.  A block takes 256 velocities of one
-// cell: every table entry of the cell is a warp-uniform load and every f
-// access is one coalesced row segment (neighbour rows come from L2: a 32^2
-// grid of 20k cells holds 81 MB in FP32).
+// cell's velocities are contiguous.  A block takes 1024 velocities of one cell
+// (4 per thread on triangle meshes): every table entry of the cell is a
+// warp-uniform load shared by 4 velocities and every f access is a 16-byte
+// vector of one coalesced row segment (neighbour rows come from L2: a 32^2
+// grid of 20k cells holds 81 MB in FP32).  Cells are taken along a Morton
+// curve of their barycentres (the mesh's order table).
 //
 // Pass 1 (order 2): gradient of the CWENO polynomial per (cell, velocity),
 // stored as G [cell][2][nv].  The central (least-squares) gradient g_opt and
@@ -31,119 +33,282 @@ namespace {
 
 constexpr int kFvThreads = 256;
 
-template <typename T>
-__global__ void __launch_bounds__(kFvThreads)
-fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, const int *__restrict__ ncen,
-                   const int *__restrict__ cen, const int *__restrict__ nsec, const int *__restrict__ sec, int nv) {
-    const int64_t i = blockIdx.x;
-    const int k = blockIdx.y * kFvThreads + threadIdx.x;
-    if (k >= nv) return;
-    const T fi = f[i * nv + k];
-    const int nc = __ldg(ncen + i);
-    T gx = (T)0, gy = (T)0;
-    for (int q = 0; q < nc; ++q) {
-        const int j = __ldg(cen + i * kFvCentral + q);
-        const T d = f[(int64_t)j * nv + k] - fi;
-        gx += __ldg(tb.Rc + (i * 2) * kFvCentral + q) * d;
-        gy += __ldg(tb.Rc + (i * 2 + 1) * kFvCentral + q) * d;
+// VEC consecutive velocities per thread: the cell's table entries are loaded
+// once for all of them and f moves in 16-byte vectors (the row length N^2 is
+// a multiple of 4, and the host checks 16-byte alignment, else VEC = 1).
+template <typename T, int VEC> struct Vec {
+    T v[VEC];
+};
+template <typename T, int VEC>
+__device__ __forceinline__ Vec<T, VEC> ldv(const T *__restrict__ p) {
+    Vec<T, VEC> r;
+    if constexpr (VEC == 4 && sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+    } else if constexpr (VEC == 4 && sizeof(T) == 8) {
+        const double2 q0 = reinterpret_cast<const double2 *>(p)[0], q1 = reinterpret_cast<const double2 *>(p)[1];
+        r.v[0] = q0.x; r.v[1] = q0.y; r.v[2] = q1.x; r.v[3] = q1.y;
+    } else {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) r.v[u] = p[u];
     }
-    const int ns = __ldg(nsec + i);
-    if (ns > 0) {
-        constexpr T kLam0 = (T)0.75, kEps = (T)1e-14;
-        const T lamL = (T)0.25 / (T)ns, h2 = __ldg(tb.h2 + i);
-        T sx[kFvMaxFaces], sy[kFvMaxFaces];
-        T sumx = (T)0, sumy = (T)0;
-        for (int s = 0; s < ns; ++s) {
-            const int a = __ldg(sec + (i * kFvMaxFaces + s) * 2), b = __ldg(sec + (i * kFvMaxFaces + s) * 2 + 1);
-            const T da = f[(int64_t)a * nv + k] - fi, db = f[(int64_t)b * nv + k] - fi;
-            const T *R = tb.Rs + (i * kFvMaxFaces + s) * 4;
-            sx[s] = __ldg(R) * da + __ldg(R + 1) * db;
-            sy[s] = __ldg(R + 2) * da + __ldg(R + 3) * db;
-            sumx += sx[s];
-            sumy += sy[s];
-        }
-        const T g0x = (gx - lamL * sumx) / kLam0, g0y = (gy - lamL * sumy) / kLam0;
-        const T sig0 = h2 * (g0x * g0x + g0y * g0y);
-        T smin = sig0;
-        for (int s = 0; s < ns; ++s) smin = fmin(smin, h2 * (sx[s] * sx[s] + sy[s] * sy[s]));
-        auto weight = [&](T lam, T sig) {
-            T r = (smin + kEps) / (sig + kEps);
-            r = r * r;
-            return lam * (r * r);
-        };
-        T w = weight(kLam0, sig0);
-        T wsum = w, ax = w * g0x, ay = w * g0y;
-        for (int s = 0; s < ns; ++s) {
-            w = weight(lamL, h2 * (sx[s] * sx[s] + sy[s] * sy[s]));
-            wsum += w;
-            ax += w * sx[s];
-            ay += w * sy[s];
-        }
-        gx = ax / wsum;
-        gy = ay / wsum;
+    return r;
+}
+template <typename T, int VEC>
+__device__ __forceinline__ void stv(T *__restrict__ p, const Vec<T, VEC> &r) {
+    if constexpr (VEC == 4 && sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    } else if constexpr (VEC == 4 && sizeof(T) == 8) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(r.v[0], r.v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(r.v[2], r.v[3]);
+    } else {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) p[u] = r.v[u];
     }
-    G[(i * 2) * nv + k] = gx;
-    G[(i * 2 + 1) * nv + k] = gy;
 }
 
-template <typename T, bool kGrad>
+// MAXS / MAXF: compile-time bound on the sectors / faces of a cell (3 for
+// triangle meshes, kFvMaxFaces otherwise).  Every loop over them is unrolled
+// with a predicate, so all neighbour rows of a cell are requested before the
+// first one is used (the kernels are latency-bound otherwise).
+template <typename T, int VEC, int MAXS>
+__global__ void __launch_bounds__(kFvThreads)
+fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, const int *__restrict__ ncen,
+                   const int *__restrict__ cen, const int *__restrict__ nsec, const int *__restrict__ sec,
+                   const int *__restrict__ order, int nv) {
+    const int64_t i = __ldg(order + blockIdx.x);
+    const int k = (blockIdx.y * kFvThreads + threadIdx.x) * VEC;
+    if (k >= nv) return;
+    const Vec<T, VEC> fi = ldv<T, VEC>(f + i * nv + k);
+    const int nc = __ldg(ncen + i), ns = __ldg(nsec + i);
+    // central least-squares gradient
+    T gx[VEC], gy[VEC];
+    {
+        Vec<T, VEC> fj[kFvCentral];
+        T rx[kFvCentral], ry[kFvCentral];
+#pragma unroll
+        for (int q = 0; q < kFvCentral; ++q) {
+            rx[q] = ry[q] = (T)0;
+            fj[q] = fi;
+            if (q < nc) {
+                const int j = __ldg(cen + i * kFvCentral + q);
+                rx[q] = __ldg(tb.Rc + (i * 2) * kFvCentral + q);
+                ry[q] = __ldg(tb.Rc + (i * 2 + 1) * kFvCentral + q);
+                fj[q] = ldv<T, VEC>(f + (int64_t)j * nv + k);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+            gx[u] = gy[u] = (T)0;
+#pragma unroll
+            for (int q = 0; q < kFvCentral; ++q) {
+                const T d = fj[q].v[u] - fi.v[u];
+                gx[u] += rx[q] * d;
+                gy[u] += ry[q] * d;
+            }
+        }
+    }
+    if (ns > 0) {
+        constexpr T kLam0 = (T)0.75, kInvLam0 = (T)(4.0 / 3.0), kEps = (T)1e-14;
+        const T lamL = (T)0.25 / (T)ns, h2 = __ldg(tb.h2 + i);
+        T sx[MAXS][VEC], sy[MAXS][VEC];
+        {
+            Vec<T, VEC> fa[MAXS], fb[MAXS];
+            T R[MAXS][4];
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s) {
+                fa[s] = fi;
+                fb[s] = fi;
+                R[s][0] = R[s][1] = R[s][2] = R[s][3] = (T)0;
+                if (s < ns) {
+                    const int a = __ldg(sec + (i * kFvMaxFaces + s) * 2), b = __ldg(sec + (i * kFvMaxFaces + s) * 2 + 1);
+                    const T *Rp = tb.Rs + (i * kFvMaxFaces + s) * 4;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) R[s][c] = __ldg(Rp + c);
+                    fa[s] = ldv<T, VEC>(f + (int64_t)a * nv + k);
+                    fb[s] = ldv<T, VEC>(f + (int64_t)b * nv + k);
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s)
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) {
+                    const T da = fa[s].v[u] - fi.v[u], db = fb[s].v[u] - fi.v[u];
+                    sx[s][u] = R[s][0] * da + R[s][1] * db;
+                    sy[s][u] = R[s][2] * da + R[s][3] * db;
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+            T sumx = (T)0, sumy = (T)0;
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s)
+                if (s < ns) {
+                    sumx += sx[s][u];
+                    sumy += sy[s][u];
+                }
+            const T g0x = (gx[u] - lamL * sumx) * kInvLam0, g0y = (gy[u] - lamL * sumy) * kInvLam0;
+            const T sig0 = h2 * (g0x * g0x + g0y * g0y);
+            T sig[MAXS];
+            T smin = sig0;
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s) {
+                sig[s] = h2 * (sx[s][u] * sx[s][u] + sy[s][u] * sy[s][u]);
+                if (s < ns) smin = fmin(smin, sig[s]);
+            }
+            const T num = smin + kEps;
+            T r = num / (sig0 + kEps);
+            r = r * r;
+            T w = kLam0 * (r * r);
+            T wsum = w, ax = w * g0x, ay = w * g0y;
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s)
+                if (s < ns) {
+                    r = num / (sig[s] + kEps);
+                    r = r * r;
+                    w = lamL * (r * r);
+                    wsum += w;
+                    ax += w * sx[s][u];
+                    ay += w * sy[s][u];
+                }
+            const T iw = (T)1 / wsum;
+            gx[u] = ax * iw;
+            gy[u] = ay * iw;
+        }
+    }
+    Vec<T, VEC> ox, oy;
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) {
+        ox.v[u] = gx[u];
+        oy.v[u] = gy[u];
+    }
+    stv<T, VEC>(G + (i * 2) * nv + k, ox);
+    stv<T, VEC>(G + (i * 2 + 1) * nv + k, oy);
+}
+
+template <typename T, bool kGrad, int VEC, int MAXF>
 __global__ void __launch_bounds__(kFvThreads)
 fv_flux_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__ L, FvTables<T> tb,
-               const int *__restrict__ nface, const int *__restrict__ nb, int nv, int N, double Lv, double dv) {
-    const int64_t i = blockIdx.x;
-    const int k = blockIdx.y * kFvThreads + threadIdx.x;
+               const int *__restrict__ nface, const int *__restrict__ nb, const int *__restrict__ order, int nv,
+               int N, T Lv, T dv) {
+    const int64_t i = __ldg(order + blockIdx.x);
+    const int k = (blockIdx.y * kFvThreads + threadIdx.x) * VEC;
     if (k >= nv) return;
-    const T v1 = (T)(-Lv + (k / N) * dv), v2 = (T)(-Lv + (k % N) * dv);
-    const T fi = f[i * nv + k];
-    T gxi = (T)0, gyi = (T)0;
-    if (kGrad) {
-        gxi = G[(i * 2) * nv + k];
-        gyi = G[(i * 2 + 1) * nv + k];
-    }
     const int nf = __ldg(nface + i);
-    T acc = (T)0;
-    for (int q = 0; q < nf; ++q) {
-        const int64_t s = i * kFvMaxFaces + q;
-        const int j = __ldg(nb + s);
-        const T vn = v1 * __ldg(tb.fn + 2 * s) + v2 * __ldg(tb.fn + 2 * s + 1);
-        T fl = fi, fr;
-        if (kGrad) fl += gxi * __ldg(tb.off_i + 2 * s) + gyi * __ldg(tb.off_i + 2 * s + 1);
-        if (j >= 0) {
-            fr = f[(int64_t)j * nv + k];
-            if (kGrad)
-                fr += G[((int64_t)j * 2) * nv + k] * __ldg(tb.off_j + 2 * s) +
-                      G[((int64_t)j * 2 + 1) * nv + k] * __ldg(tb.off_j + 2 * s + 1);
-        } else {
-            fr = fl;
-        }
-        acc += (T)0.5 * vn * (fl + fr) - (T)0.5 * fabs(vn) * (fr - fl);
+    const Vec<T, VEC> fi = ldv<T, VEC>(f + i * nv + k);
+    Vec<T, VEC> gxi, gyi;
+    if (kGrad) {
+        gxi = ldv<T, VEC>(G + (i * 2) * nv + k);
+        gyi = ldv<T, VEC>(G + (i * 2 + 1) * nv + k);
     }
-    L[i * nv + k] = acc * __ldg(tb.inv_area + i);
+    // every face's neighbour row first
+    int jn[MAXF];
+    Vec<T, VEC> fj[MAXF], gxj[MAXF], gyj[MAXF];
+#pragma unroll
+    for (int q = 0; q < MAXF; ++q) {
+        jn[q] = q < nf ? __ldg(nb + i * kFvMaxFaces + q) : -1;
+        fj[q] = fi;
+        if (kGrad) {
+            gxj[q] = gxi;
+            gyj[q] = gyi;
+        }
+        if (jn[q] >= 0) {
+            fj[q] = ldv<T, VEC>(f + (int64_t)jn[q] * nv + k);
+            if (kGrad) {
+                gxj[q] = ldv<T, VEC>(G + ((int64_t)jn[q] * 2) * nv + k);
+                gyj[q] = ldv<T, VEC>(G + ((int64_t)jn[q] * 2 + 1) * nv + k);
+            }
+        }
+    }
+    T v1[VEC], v2[VEC], acc[VEC];
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) {
+        v1[u] = -Lv + (T)((k + u) / N) * dv;       // velocities in the working precision
+        v2[u] = -Lv + (T)((k + u) % N) * dv;
+        acc[u] = (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < MAXF; ++q) {
+        if (q >= nf) continue;
+        const int64_t s = i * kFvMaxFaces + q;
+        const T nx = __ldg(tb.fn + 2 * s), ny = __ldg(tb.fn + 2 * s + 1);
+        T oix = (T)0, oiy = (T)0, ojx = (T)0, ojy = (T)0;
+        if (kGrad) {
+            oix = __ldg(tb.off_i + 2 * s);
+            oiy = __ldg(tb.off_i + 2 * s + 1);
+            ojx = __ldg(tb.off_j + 2 * s);
+            ojy = __ldg(tb.off_j + 2 * s + 1);
+        }
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+            const T vn = v1[u] * nx + v2[u] * ny;
+            T fl = fi.v[u];
+            if (kGrad) fl += gxi.v[u] * oix + gyi.v[u] * oiy;
+            T fr = fl;
+            if (jn[q] >= 0) {
+                fr = fj[q].v[u];
+                if (kGrad) fr += gxj[q].v[u] * ojx + gyj[q].v[u] * ojy;
+            }
+            acc[u] += (T)0.5 * vn * (fl + fr) - (T)0.5 * fabs(vn) * (fr - fl);
+        }
+    }
+    const T ia = __ldg(tb.inv_area + i);
+    Vec<T, VEC> o;
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) o.v[u] = acc[u] * ia;
+    stv<T, VEC>(L + i * nv + k, o);
 }
 
 template <typename T> const FvTables<T> &pick(const bz_mesh *m);
 template <> const FvTables<double> &pick<double>(const bz_mesh *m) { return m->t64; }
 template <> const FvTables<float> &pick<float>(const bz_mesh *m) { return m->t32; }
 
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+template <typename T, int VEC, int MAXS>
+void gradient_launch(const bz_mesh *m, int nv, const T *f, T *G, cudaStream_t st) {
+    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / VEC + kFvThreads - 1) / kFvThreads));
+    fv_gradient_kernel<T, VEC, MAXS><<<grid, kFvThreads, 0, st>>>(f, G, pick<T>(m), m->d_ncen, m->d_cen, m->d_nsec,
+                                                                  m->d_sec, m->d_order, nv);
+}
+
+template <typename T, bool kGrad, int VEC, int MAXF>
+void flux_launch(const bz_mesh *m, const GridView &g, const T *f, const T *G, T *L, cudaStream_t st) {
+    const int nv = (int)g.nv;
+    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / VEC + kFvThreads - 1) / kFvThreads));
+    fv_flux_kernel<T, kGrad, VEC, MAXF><<<grid, kFvThreads, 0, st>>>(f, G, L, pick<T>(m), m->d_nface, m->d_nb,
+                                                                     m->d_order, nv, g.N, (T)g.L, (T)g.dv);
+}
+
+// Triangle meshes with 16-byte aligned rows take 4 velocities per thread and
+// unrolled 3-face loops; other meshes one velocity per thread and 8-face loops.
 template <typename T>
 cudaError_t gradient(const bz_mesh *m, const GridView &g, const T *f, T *G, cudaStream_t st) {
     if (m->n_cells <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)m->n_cells, (unsigned)((g.nv + kFvThreads - 1) / kFvThreads));
-    fv_gradient_kernel<T><<<grid, kFvThreads, 0, st>>>(f, G, pick<T>(m), m->d_ncen, m->d_cen, m->d_nsec, m->d_sec,
-                                                       (int)g.nv);
+    const int nv = (int)g.nv;
+    if (m->max_faces <= 3 && nv % 4 == 0 && aligned16(f) && aligned16(G))
+        gradient_launch<T, 4, 3>(m, nv, f, G, st);
+    else if (m->max_faces <= 3)
+        gradient_launch<T, 1, 3>(m, nv, f, G, st);
+    else
+        gradient_launch<T, 1, kFvMaxFaces>(m, nv, f, G, st);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t flux(const bz_mesh *m, const GridView &g, const T *f, const T *G, T *L, cudaStream_t st) {
     if (m->n_cells <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)m->n_cells, (unsigned)((g.nv + kFvThreads - 1) / kFvThreads));
-    if (G)
-        fv_flux_kernel<T, true><<<grid, kFvThreads, 0, st>>>(f, G, L, pick<T>(m), m->d_nface, m->d_nb, (int)g.nv,
-                                                             g.N, g.L, g.dv);
-    else
-        fv_flux_kernel<T, false><<<grid, kFvThreads, 0, st>>>(f, nullptr, L, pick<T>(m), m->d_nface, m->d_nb,
-                                                              (int)g.nv, g.N, g.L, g.dv);
+    const bool tri = m->max_faces <= 3;
+    const bool v4 = tri && g.nv % 4 == 0 && aligned16(f) && aligned16(L) && (!G || aligned16(G));
+    if (G) {
+        if (v4) flux_launch<T, true, 4, 3>(m, g, f, G, L, st);
+        else if (tri) flux_launch<T, true, 1, 3>(m, g, f, G, L, st);
+        else flux_launch<T, true, 1, kFvMaxFaces>(m, g, f, G, L, st);
+    } else {
+        if (v4) flux_launch<T, false, 4, 3>(m, g, f, G, L, st);
+        else if (tri) flux_launch<T, false, 1, 3>(m, g, f, G, L, st);
+        else flux_launch<T, false, 1, kFvMaxFaces>(m, g, f, G, L, st);
+    }
     return cudaGetLastError();
 }
 
