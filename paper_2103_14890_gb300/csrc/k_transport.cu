@@ -72,7 +72,7 @@ __device__ __forceinline__ void stv(T *__restrict__ p, const Vec<T, VEC> &r) {
 // with a predicate, so all neighbour rows of a cell are requested before the
 // first one is used (the kernels are latency-bound otherwise).
 template <typename T, int VEC, int MAXS>
-__global__ void __launch_bounds__(kFvThreads)
+__global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4) ? 4 : 1)
 fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, const int *__restrict__ ncen,
                    const int *__restrict__ cen, const int *__restrict__ nsec, const int *__restrict__ sec,
                    const int *__restrict__ order, int nv) {
@@ -156,15 +156,21 @@ fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, c
                 sig[s] = h2 * (sx[s][u] * sx[s][u] + sy[s][u] * sy[s][u]);
                 if (s < ns) smin = fmin(smin, sig[s]);
             }
+            // weight ratios: FP32 takes the fast division (2 ulp; the weights
+            // are smooth in sigma), FP64 the correctly rounded one
             const T num = smin + kEps;
-            T r = num / (sig0 + kEps);
+            auto ratio = [](T a, T b) {
+                if constexpr (sizeof(T) == 4) return __fdividef(a, b);
+                else return a / b;
+            };
+            T r = ratio(num, sig0 + kEps);
             r = r * r;
             T w = kLam0 * (r * r);
             T wsum = w, ax = w * g0x, ay = w * g0y;
 #pragma unroll
             for (int s = 0; s < MAXS; ++s)
                 if (s < ns) {
-                    r = num / (sig[s] + kEps);
+                    r = ratio(num, sig[s] + kEps);
                     r = r * r;
                     w = lamL * (r * r);
                     wsum += w;
@@ -220,11 +226,14 @@ fv_flux_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__
             }
         }
     }
-    T v1[VEC], v2[VEC], acc[VEC];
+    // velocities in the working precision; the VEC velocities of a thread lie
+    // in one row of the grid (the host takes VEC = 4 only when 4 divides N)
+    const int j1 = k / N, j2 = k - j1 * N;
+    const T v1 = -Lv + (T)j1 * dv;
+    T v2[VEC], acc[VEC];
 #pragma unroll
     for (int u = 0; u < VEC; ++u) {
-        v1[u] = -Lv + (T)((k + u) / N) * dv;       // velocities in the working precision
-        v2[u] = -Lv + (T)((k + u) % N) * dv;
+        v2[u] = -Lv + (T)(j2 + u) * dv;
         acc[u] = (T)0;
     }
 #pragma unroll
@@ -241,7 +250,7 @@ fv_flux_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__
         }
 #pragma unroll
         for (int u = 0; u < VEC; ++u) {
-            const T vn = v1[u] * nx + v2[u] * ny;
+            const T vn = v1 * nx + v2[u] * ny;
             T fl = fi.v[u];
             if (kGrad) fl += gxi.v[u] * oix + gyi.v[u] * oiy;
             T fr = fl;
@@ -299,7 +308,7 @@ template <typename T>
 cudaError_t flux(const bz_mesh *m, const GridView &g, const T *f, const T *G, T *L, cudaStream_t st) {
     if (m->n_cells <= 0) return cudaSuccess;
     const bool tri = m->max_faces <= 3;
-    const bool v4 = tri && g.nv % 4 == 0 && aligned16(f) && aligned16(L) && (!G || aligned16(G));
+    const bool v4 = tri && g.N % 4 == 0 && aligned16(f) && aligned16(L) && (!G || aligned16(G));
     if (G) {
         if (v4) flux_launch<T, true, 4, 3>(m, g, f, G, L, st);
         else if (tri) flux_launch<T, true, 1, 3>(m, g, f, G, L, st);

@@ -138,6 +138,29 @@ def test_transport_fp32_within_bound(bz, fvo, order, jump):
     _check(Lr.double().cpu().numpy(), want, om, fin, N, Lv, order, fvo, U32, ETA32)
 
 
+def test_transport_scalar_paths(bz, fvo):
+    """N = 6 (4 does not divide N: one velocity per thread in the flux pass) and
+    rows that start off a 16-byte boundary (one velocity per thread in both
+    passes) give the oracle's result too."""
+    import torch
+    pts, cells = _tri(12)
+    om = fvo.Mesh(pts, cells)
+    m = bz.Mesh(pts, cells, order=2)
+    for N in (6, 8):
+        Lv = 6.0
+        f = workloads.mesh_states(om.bary, N, Lv, jump=True)
+        want = fvo.transport_residual(om, f, N, Lv, order=2)
+        g = bz.Grid(2, N, Lv)
+        buf = torch.zeros(f.size + 1, dtype=torch.float64, device="cuda")
+        fd = buf[1:].view(f.shape)                        # 8-byte but not 16-byte aligned
+        fd.copy_(torch.from_numpy(f))
+        out = torch.zeros(f.size + 1, dtype=torch.float64, device="cuda")[1:].view(f.shape)
+        for src, dst in ((to_dev(f, "fp64"), None), (fd, out)):
+            Lr = bz.transport_residual(m, g, src, dst, precision="fp64")
+            bz.check()
+            _check(Lr.cpu().numpy(), want, om, f, N, Lv, 2, fvo, U64, ETA64)
+
+
 def test_mesh_info_and_errors(bz):
     pts, cells = _tri(12)
     m = bz.Mesh(pts, cells, order=2)
