@@ -15,7 +15,8 @@ with F the Rusanov flux of the linear flux v f (eq. finite_vol5):
   F = (v.n)(f_L + f_R)/2 - |v.n| (f_R - f_L)/2,
 f_L, f_R the reconstructed values on either side at the face midpoint (the
 midpoint rule is exact for reconstructions of degree <= 1), and a
-transmissive boundary (f_R = f_L on faces without a neighbour).
+transmissive boundary (f_R = f_L on faces without a neighbour) unless the face
+is a wall with full accommodation (transport_residual's `walls`).
 
 Reconstruction (eq. CWENO:Popt, CWENO:P0, CWENO:Prec, eqn.weights) for the
 degree M = 1: with the zero-mean Taylor basis about the barycentre x_b
@@ -83,8 +84,10 @@ class Mesh:
             for q in range(len(c)):
                 owner[(c[q], c[(q + 1) % len(c)])] = i
         self.faces = []          # per cell: list of (neighbour or -1, length, nx, ny, midx, midy)
+        self.face_vertices = []  # per cell: the vertex pair (a, b) of every face
         for i, c in enumerate(self.cells):
             fl = []
+            self.face_vertices.append([(c[q], c[(q + 1) % len(c)]) for q in range(len(c))])
             for q in range(len(c)):
                 a, b = c[q], c[(q + 1) % len(c)]
                 d = self.xy[b] - self.xy[a]
@@ -179,18 +182,37 @@ def reconstruct_gradients(mesh, f, order):
     return g
 
 
-def transport_residual(mesh, f, N, L, order=2):
-    """L_{k,i} of the module docstring for f of shape (n_cells, N*N)."""
+def wall_maxwellian(v1, v2, theta, u1, u2):
+    """Unit-mass 2-D Maxwellian of the wall (eq. MAXB)."""
+    return np.exp(-((v1 - u1) ** 2 + (v2 - u2) ** 2) / (2 * theta)) / (2 * np.pi * theta)
+
+
+def transport_residual(mesh, f, N, L, order=2, walls=None):
+    """L_{k,i} of the module docstring for f of shape (n_cells, N*N).
+
+    walls: optional {frozenset({a, b}): (theta_w, u_w1, u_w2)} for boundary
+    edges with vertices a, b that are walls with full accommodation
+    (eq. BOU with alpha = 1, eq. MAXB, eq. MU): velocities leaving the domain
+    through the face carry the reconstructed inner value f_L, velocities
+    entering it carry mu M_w(v), with mu such that the discrete mass fluxes
+    balance, mu sum_{v.n < 0} M_w |v.n| = sum_{v.n > 0} f_L v.n (n the outer
+    normal; the velocity-cell volume cancels)."""
     f = np.asarray(f, dtype=np.float64)
     v1, v2 = velocity_grid(N, L)
     g = reconstruct_gradients(mesh, f, order)
     out = np.zeros_like(f)
     for i in range(len(f)):
         acc = np.zeros(f.shape[1])
-        for (j, ln, nx, ny, mx, my) in mesh.faces[i]:
+        for q, (j, ln, nx, ny, mx, my) in enumerate(mesh.faces[i]):
             vn = v1 * nx + v2 * ny
             fl = f[i] + g[i, 0] * (mx - mesh.bary[i, 0]) + g[i, 1] * (my - mesh.bary[i, 1])
-            if j < 0:
+            wall = None if walls is None else walls.get(frozenset(mesh.face_vertices[i][q]))
+            if j < 0 and wall is not None:
+                mw = wall_maxwellian(v1, v2, *wall)
+                out_ = vn > 0
+                mu = (fl * vn)[out_].sum() / (mw * -vn)[~out_].sum()
+                fr = np.where(out_, fl, mu * mw)
+            elif j < 0:
                 fr = fl
             else:
                 fr = f[j] + g[j, 0] * (mx - mesh.bary[j, 0]) + g[j, 1] * (my - mesh.bary[j, 1])

@@ -12,7 +12,9 @@ Checked against what geometry and calculus fix, not against the oracle itself:
   - interior fluxes cancel in pairs: sum |P_i| L_i equals the boundary flux;
   - the first-order form reduces to upwinding, written out by hand on one cell;
   - near a jump the nonlinear weights leave far fewer out-of-range face
-    values than the unweighted least-squares gradient.
+    values than the unweighted least-squares gradient;
+  - walls with full accommodation keep a gas at rest at the wall temperature
+    and conserve mass in a closed box.
 """
 import numpy as np
 import pytest
@@ -151,3 +153,48 @@ def test_weno_limits_overshoot_at_a_jump(fv):
 
     n_w, n_ls = count(lambda i: g[i, :, 0]), count(least_squares)
     assert n_ls > 20 and n_w < n_ls / 2
+
+
+def _box_walls(m, theta=1.0, u=(0.0, 0.0)):
+    """Every boundary edge of the mesh a wall at rest (or moving with u)."""
+    walls = {}
+    for i, fl in enumerate(m.faces):
+        for q, fc in enumerate(fl):
+            if fc[0] < 0:
+                walls[frozenset(m.face_vertices[i][q])] = (theta, u[0], u[1])
+    return walls
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_walls_keep_the_wall_equilibrium(fv, order):
+    """A gas at rest at the walls' temperature (any density) is an equilibrium
+    of full accommodation (eq. BOU, eq. MU): the residual vanishes in every cell
+    of a closed box (axis-aligned walls, so the discrete half-range fluxes of
+    the Maxwellian balance up to the grid's e^{-L^2/(2 theta)} tail)."""
+    m = _quad_tri_mesh(fv)
+    N, L, th = 16, 8.0, 0.9
+    v1, v2 = fv.velocity_grid(N, L)
+    rho = 1.7
+    f = np.tile(rho * fv.wall_maxwellian(v1, v2, th, 0.0, 0.0), (len(m.cells), 1))
+    Lr = fv.transport_residual(m, f, N, L, order=order, walls=_box_walls(m, th))
+    scale = np.abs(v1).max() * f.max() / np.sqrt(m.area.min())
+    assert np.abs(Lr).max() < 1e-12 * scale
+    # a gas at another temperature is not at rest with the walls
+    f2 = np.tile(rho * fv.wall_maxwellian(v1, v2, 1.5 * th, 0.0, 0.0), (len(m.cells), 1))
+    Lw = fv.transport_residual(m, f2, N, L, order=order, walls=_box_walls(m, th))
+    assert np.abs(Lw).max() > 1e-3 * scale
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_walls_conserve_mass(fv, order):
+    """Diffuse reflection conserves mass at every wall face: in a closed box the
+    total mass flux sum_i |P_i| sum_k L_ik vanishes for any state, also with
+    moving walls and a triangle mesh whose walls are not axis-aligned."""
+    rng = np.random.default_rng(4)
+    pts, tri = workloads.sod_triangulation(n_side=10, seed=3)
+    m = fv.Mesh(pts, tri)
+    N, L = 8, 6.0
+    f = rng.uniform(0.05, 1.0, (len(m.cells), N * N))
+    Lr = fv.transport_residual(m, f, N, L, order=order, walls=_box_walls(m, 1.2, (0.3, -0.2)))
+    total = (m.area[:, None] * Lr).sum()
+    assert abs(total) < 1e-13 * (m.area[:, None] * np.abs(Lr)).sum()
