@@ -383,6 +383,27 @@ def _transport_measure(bz, workloads, st, check=True):
                                "note": "two passes: the reconstruction writes 2 gradient values per (cell, velocity) "
                                        "that the flux pass reads back"}
         out[prec] = ent
+    # the same residual in a closed box: every boundary edge a wall at rest
+    # with full accommodation (the wall flux pass: one CTA per cell holds all
+    # 1024 velocities for the wall's mass balance)
+    bedges = _boundary_edges(tri)
+    mesh_w = bz.Mesh(pts, tri, order=2)
+    mesh_w.set_walls(bedges, np.tile([[1.0, 0.0, 0.0]], (len(bedges), 1)))
+    f = torch.from_numpy(fh).to("cuda", torch.float32)
+    Lr = torch.empty_like(f)
+    for _ in range(3):
+        bz.transport_residual(mesh_w, g, f, Lr, precision="fp32")
+    bz.check()
+    bz.profile(True)
+    msw = 0.0
+    for _ in range(10):
+        flush.fill_(1)
+        msw += _timed(lambda: bz.transport_residual(mesh_w, g, f, Lr, precision="fp32"), 1, st)
+    msw /= 10
+    profw = bz.profile_read()
+    bz.profile(False)
+    out["fp32_walls"] = {"ms_per_call": msw, "wall_edges": int(len(bedges)),
+                         "kernel_ms": {k: v[1] / max(1, v[0]) for k, v in profw.items()}}
     # the coupled step
     hmesh = float(np.sqrt(np.abs(0.5 * ((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) -
                                         (P[:, 2, 0] - P[:, 0, 0]) * (P[:, 1, 1] - P[:, 0, 1]))).mean()))
@@ -406,6 +427,18 @@ def _transport_measure(bz, workloads, st, check=True):
         out["cpu_baseline"] = {"kind": "oracle", "value": f2.size / el, "unit": "cell-velocity updates/s",
                                "sample": "%d-triangle mesh, 32^2 velocities (numpy, one process)" % len(t2)}
     return out
+
+
+def _boundary_edges(cells):
+    """Vertex pairs of the edges that belong to one cell only."""
+    count = {}
+    for c in cells:
+        c = [int(v) for v in c]
+        for q in range(len(c)):
+            e = frozenset((c[q], c[(q + 1) % len(c)]))
+            count[e] = count.get(e, 0) + 1
+    import numpy as np
+    return np.array([sorted(e) for e, n in count.items() if n == 1], dtype=np.int64)
 
 
 def _measured_hbm():

@@ -259,6 +259,24 @@ int group_collide(const bz_group_item *items, int n_items, int precision, int fl
 int build_fv_mesh(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
                   const int64_t *cell_vertices, int order, bz_mesh **out);
 
+/* fv_mesh_set_walls -- make boundary edges walls with full accommodation
+ * (Sec. 2, eq. BOU with alpha = 1, eq. MAXB, eq. MU): at a wall face the
+ * velocities leaving the domain carry the reconstructed inner value f_L, the
+ * velocities entering it carry mu M_w(v), M_w the unit-mass Maxwellian of the
+ * wall's temperature and velocity, mu such that the discrete mass fluxes
+ * through the face balance, mu sum_{v.n<0} M_w |v.n| = sum_{v.n>0} f_L v.n
+ * (n the outer normal).  Boundary edges that are not walls stay transmissive.
+ * The call replaces the mesh's walls; n_edges = 0 removes them; on an error
+ * the mesh is left without walls.
+ *   edge_vertices : 2 n_edges vertex indices (host), each pair a boundary edge
+ *                   of the mesh in either order
+ *   wall_params   : 3 n_edges values (host): theta_w > 0, u_w1, u_w2
+ * A mesh with walls needs N divisible by 4 and N^2 <= 1024 in
+ * transport_residual and imex_step_fv (BZ_ENOTSUP otherwise): one CTA forms
+ * each cell's mu over all its velocities.
+ * Errors: BZ_EINVAL (NULL mesh, not a boundary edge, theta_w <= 0), BZ_ECUDA. */
+int fv_mesh_set_walls(bz_mesh *mesh, int64_t n_edges, const int64_t *edge_vertices, const double *wall_params);
+
 /* transport_residual -- <L(f^w)>_x of eq. ho for every cell and discrete
  * velocity: L[i][k] = (1/|P_i|) sum over the faces e of P_i of
  * |e| F(f_L, f_R; v_k . n_e), with F the Rusanov flux of v f,
@@ -267,8 +285,11 @@ int build_fv_mesh(int n_vertices, const double *xy, int64_t n_cells, const int64
  * the collision operator).
  *   f, L      : device arrays [n_cells][N^2] (n_cells of the mesh), double for
  *               BZ_FP64, float for BZ_FP32; must not overlap
+ * Boundary faces are transmissive (the outer state equals the inner one)
+ * unless fv_mesh_set_walls made them walls.
  * Scratch (order 2: 2 n_cells N^2 values) comes from the stream-ordered pool.
- * Errors: BZ_EINVAL, BZ_ENOTSUP (3-D grid), BZ_ECUDA. */
+ * Errors: BZ_EINVAL, BZ_ENOTSUP (3-D grid; walls with N not divisible by 4 or
+ * N^2 > 1024), BZ_ECUDA. */
 int transport_residual(const bz_mesh *mesh, const bz_grid *g, int precision, const void *f, void *L,
                        void *stream);
 

@@ -76,6 +76,7 @@ def load(path=None):
             "imex_step_fv": ([c_p, c_p, c_i, c_i, c_d, c_d, c_p, c_p, c_i, c_i, c_p], c_i),
             "bz_mesh_info": ([c_p, ctypes.POINTER(c_i64)], c_i),
             "bz_mesh_destroy": ([c_p], None),
+            "fv_mesh_set_walls": ([c_p, c_i64, c_p, c_p], c_i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -197,6 +198,18 @@ class Mesh:
         info = (ctypes.c_int64 * 5)()
         _check(load().bz_mesh_info(h, info))
         self.n_cells, self.n_faces_interior, self.n_faces_boundary, self.max_faces, self.order = list(info)
+
+    def set_walls(self, edges, params):
+        """Walls with full accommodation on boundary edges (vertex pairs, shape
+        (n, 2)); params (n, 3) = (theta_w, u_w1, u_w2) per edge; an empty list
+        removes every wall."""
+        import numpy as np
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int64).reshape(-1, 2))
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(-1, 3))
+        if len(e) != len(p):
+            raise ValueError("one parameter triple per edge")
+        _check(load().fv_mesh_set_walls(self._h, int(len(e)), e.ctypes.data_as(ctypes.c_void_p),
+                                        p.ctypes.data_as(ctypes.c_void_p)))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

@@ -32,6 +32,7 @@ int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out);
 int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
                    const int64_t *cell_vertices, int order, bz_mesh **out);
 void fv_mesh_destroy(bz_mesh *m);
+int fv_mesh_set_walls(bz_mesh *m, int64_t n_edges, const int64_t *edges, const double *params);
 void modes_destroy(bz_modes *m);
 double beta_host(const bz_modes *m, const int *l, const int *mm);
 double fast_beta_host(const bz_modes *m, int64_t li, int64_t mi);
@@ -325,6 +326,8 @@ size_t transport_scratch_bytes(const bz_mesh *mesh, const bz_grid *g, int precis
 int transport_chain(const bz_mesh *mesh, const bz_grid *g, int precision, const void *f, void *L, cudaStream_t st,
                     void *ext = nullptr) {
     const GridView &v = g->v;
+    if (!fv_walls_supported(mesh, v))
+        return fail(BZ_ENOTSUP, "transport: walls need N divisible by 4 and at most 32^2 velocities");
     Scratch s;
     void *G = nullptr;
     if (mesh->order == 2) {
@@ -820,6 +823,12 @@ int transport_residual(const bz_mesh *mesh, const bz_grid *g, int precision, con
     if (fb < lb + bytes && lb < fb + bytes) return fail(BZ_EINVAL, "transport_residual: f and L overlap");
     DeviceGuard dg(g->device);
     return transport_chain(mesh, g, precision, f, L, static_cast<cudaStream_t>(stream));
+}
+
+int fv_mesh_set_walls(bz_mesh *mesh, int64_t n_edges, const int64_t *edge_vertices, const double *wall_params) {
+    if (!mesh) return fail(BZ_EINVAL, "fv_mesh_set_walls: mesh is NULL");
+    DeviceGuard dg(mesh->device);
+    return bz::fv_mesh_set_walls(mesh, n_edges, edge_vertices, wall_params);
 }
 
 int bz_mesh_info(const bz_mesh *mesh, int64_t out[5]) {

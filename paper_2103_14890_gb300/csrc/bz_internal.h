@@ -116,6 +116,16 @@ struct bz_mesh {
     int *d_nsec;            // [cell] sectors
     int *d_sec;             // [cell][face][2] sector cells
     int *d_order;           // [cell] processing order: cells sorted along a Morton curve of their barycentres
+    // walls with full accommodation (fv_mesh_set_walls): per face the wall
+    // index (-1: none), per wall (theta_w, u_w1, u_w2) in FP64 and FP32
+    int *d_wall;
+    double *d_wall64;
+    float *d_wall32;
+    int64_t n_walls;
+    // host copies for the wall look-up: counter-clockwise vertex lists (CSR)
+    // and the neighbour of every face
+    int64_t *h_ptr, *h_vtx;
+    int *h_nb;
     void *d_real64;         // one block holding the FvTables<double> arrays
     void *d_real32;         // one block holding the FvTables<float> arrays
     bz::FvTables<double> t64;
@@ -229,6 +239,8 @@ cudaError_t launch_fv_gradient_f32(const bz_mesh *mesh, const GridView &g, const
                                    cudaStream_t st);
 cudaError_t launch_fv_flux_f64(const bz_mesh *mesh, const GridView &g, const double *f, const double *G, double *L,
                                cudaStream_t st);
+// walls need one CTA to hold all velocities of a cell
+bool fv_walls_supported(const bz_mesh *mesh, const GridView &g);
 cudaError_t launch_fv_flux_f32(const bz_mesh *mesh, const GridView &g, const float *f, const float *G, float *L,
                                cudaStream_t st);
 

@@ -93,6 +93,12 @@ void fv_mesh_destroy(bz_mesh *m) {
     cudaFree(m->d_nsec);
     cudaFree(m->d_sec);
     cudaFree(m->d_order);
+    cudaFree(m->d_wall);
+    cudaFree(m->d_wall64);
+    cudaFree(m->d_wall32);
+    free(m->h_ptr);
+    free(m->h_vtx);
+    free(m->h_nb);
     cudaFree(m->d_real64);
     cudaFree(m->d_real32);
     free(m);
@@ -338,7 +344,66 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
     }
     m->t64 = carve<double>(m->d_real64, n);
     m->t32 = carve<float>(m->d_real32, n);
+    // host copies for fv_mesh_set_walls
+    m->h_ptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    m->h_vtx = (int64_t *)malloc(sizeof(int64_t) * (size_t)cell_ptr[n]);
+    m->h_nb = (int *)malloc(sizeof(int) * h.nb.size());
+    if (!m->h_ptr || !m->h_vtx || !m->h_nb) {
+        fv_mesh_destroy(m);
+        return fail(BZ_ENOMEM, "build_fv_mesh: host copies");
+    }
+    m->h_ptr[0] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        m->h_ptr[i + 1] = m->h_ptr[i] + (int64_t)cells[i].size();
+        memcpy(m->h_vtx + m->h_ptr[i], cells[i].data(), sizeof(int64_t) * cells[i].size());
+    }
+    memcpy(m->h_nb, h.nb.data(), sizeof(int) * h.nb.size());
     *out = m;
+    return BZ_OK;
+}
+
+// Walls with full accommodation on the boundary edges given by their vertex
+// pairs (either order); n_edges = 0 removes every wall.
+int fv_mesh_set_walls(bz_mesh *m, int64_t n_edges, const int64_t *edges, const double *params) {
+    if (!m) return fail(BZ_EINVAL, "fv_mesh_set_walls: mesh is NULL");
+    if (n_edges < 0 || (n_edges > 0 && (!edges || !params)))
+        return fail(BZ_EINVAL, "fv_mesh_set_walls: bad edge list");
+    cudaFree(m->d_wall);
+    cudaFree(m->d_wall64);
+    cudaFree(m->d_wall32);
+    m->d_wall = nullptr;
+    m->d_wall64 = nullptr;
+    m->d_wall32 = nullptr;
+    m->n_walls = 0;
+    if (n_edges == 0) return BZ_OK;
+    const int64_t n = m->n_cells;
+    std::unordered_map<uint64_t, int64_t> bface;           // unordered vertex pair -> cell * K + face
+    auto key = [](int64_t a, int64_t b) {
+        if (a > b) std::swap(a, b);
+        return ((uint64_t)a << 32) | (uint64_t)b;
+    };
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t a0 = m->h_ptr[i], k = m->h_ptr[i + 1] - a0;
+        for (int64_t q = 0; q < k; ++q)
+            if (m->h_nb[i * kFvMaxFaces + q] < 0)
+                bface[key(m->h_vtx[a0 + q], m->h_vtx[a0 + (q + 1) % k])] = i * kFvMaxFaces + q;
+    }
+    std::vector<int> wall((size_t)n * kFvMaxFaces, -1);
+    std::vector<double> p64((size_t)n_edges * 3);
+    for (int64_t e = 0; e < n_edges; ++e) {
+        auto it = bface.find(key(edges[2 * e], edges[2 * e + 1]));
+        if (it == bface.end()) return fail(BZ_EINVAL, "fv_mesh_set_walls: an edge is not a boundary edge of the mesh");
+        if (!(params[3 * e] > 0)) return fail(BZ_EINVAL, "fv_mesh_set_walls: wall temperature must be > 0");
+        wall[(size_t)it->second] = (int)e;
+        for (int c = 0; c < 3; ++c) p64[3 * e + c] = params[3 * e + c];
+    }
+    std::vector<float> p32(p64.size());
+    for (size_t q = 0; q < p64.size(); ++q) p32[q] = (float)p64[q];
+    cudaError_t err = upload(&m->d_wall, wall);
+    if (err == cudaSuccess) err = upload(&m->d_wall64, p64);
+    if (err == cudaSuccess) err = upload(&m->d_wall32, p32);
+    if (err != cudaSuccess) return cuda_fail(err, "fv_mesh_set_walls: device tables");
+    m->n_walls = n_edges;
     return BZ_OK;
 }
 

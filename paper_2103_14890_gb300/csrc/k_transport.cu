@@ -268,6 +268,136 @@ fv_flux_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__
     stv<T, VEC>(L + i * nv + k, o);
 }
 
+// Flux pass of a mesh with walls (full accommodation, eq. BOU with alpha = 1,
+// eq. MAXB, eq. MU): one CTA holds all nv <= 1024 velocities of its cell, 4
+// per thread, so the wall density mu of a face -- the ratio of the outgoing
+// mass flux sum_{v.n > 0} f_L v.n to the incoming flux of the unit wall
+// Maxwellian sum_{v.n < 0} M_w |v.n| -- is a block reduction (FP64, fixed
+// order).  Velocities entering the domain through the wall carry mu M_w(v),
+// the others the reconstructed inner value; other faces as in fv_flux_kernel.
+template <typename T, bool VLOAD>
+__device__ __forceinline__ Vec<T, 4> ld4(const T *__restrict__ p) {
+    if constexpr (VLOAD) {
+        return ldv<T, 4>(p);
+    } else {
+        Vec<T, 4> r;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) r.v[u] = p[u];
+        return r;
+    }
+}
+
+template <typename T, bool kGrad, int MAXF, bool VLOAD>
+__global__ void __launch_bounds__(kFvThreads)
+fv_flux_wall_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__ L, FvTables<T> tb,
+                    const int *__restrict__ nface, const int *__restrict__ nb, const int *__restrict__ order,
+                    const int *__restrict__ wall, const T *__restrict__ wallp, int nv, int N, T Lv, T dv) {
+    __shared__ double red[2 * (kFvThreads / 32)];
+    const int64_t i = __ldg(order + blockIdx.x);
+    const int kt = threadIdx.x * 4;
+    const bool act = kt < nv;
+    const int k = act ? kt : 0;                  // idle threads read row 0 and store nothing
+    const int nf = __ldg(nface + i);
+    const Vec<T, 4> fi = ld4<T, VLOAD>(f + i * nv + k);
+    Vec<T, 4> gxi, gyi;
+    if (kGrad) {
+        gxi = ld4<T, VLOAD>(G + (i * 2) * nv + k);
+        gyi = ld4<T, VLOAD>(G + (i * 2 + 1) * nv + k);
+    }
+    int jn[MAXF];
+    Vec<T, 4> fj[MAXF], gxj[MAXF], gyj[MAXF];
+#pragma unroll
+    for (int q = 0; q < MAXF; ++q) {
+        jn[q] = q < nf ? __ldg(nb + i * kFvMaxFaces + q) : -1;
+        fj[q] = fi;
+        if (kGrad) {
+            gxj[q] = gxi;
+            gyj[q] = gyi;
+        }
+        if (jn[q] >= 0) {
+            fj[q] = ld4<T, VLOAD>(f + (int64_t)jn[q] * nv + k);
+            if (kGrad) {
+                gxj[q] = ld4<T, VLOAD>(G + ((int64_t)jn[q] * 2) * nv + k);
+                gyj[q] = ld4<T, VLOAD>(G + ((int64_t)jn[q] * 2 + 1) * nv + k);
+            }
+        }
+    }
+    const int j1 = k / N, j2 = k - j1 * N;
+    const T v1 = -Lv + (T)j1 * dv;
+    T v2[4], acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        v2[u] = -Lv + (T)(j2 + u) * dv;
+        acc[u] = (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < MAXF; ++q) {
+        if (q >= nf) continue;                   // uniform over the CTA (one cell)
+        const int64_t s = i * kFvMaxFaces + q;
+        const T nx = __ldg(tb.fn + 2 * s), ny = __ldg(tb.fn + 2 * s + 1);
+        T oix = (T)0, oiy = (T)0, ojx = (T)0, ojy = (T)0;
+        if (kGrad) {
+            oix = __ldg(tb.off_i + 2 * s);
+            oiy = __ldg(tb.off_i + 2 * s + 1);
+            ojx = __ldg(tb.off_j + 2 * s);
+            ojy = __ldg(tb.off_j + 2 * s + 1);
+        }
+        T vn[4], fl[4], fr[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            vn[u] = v1 * nx + v2[u] * ny;
+            fl[u] = fi.v[u];
+            if (kGrad) fl[u] += gxi.v[u] * oix + gyi.v[u] * oiy;
+            fr[u] = fl[u];
+            if (jn[q] >= 0) {
+                fr[u] = fj[q].v[u];
+                if (kGrad) fr[u] += gxj[q].v[u] * ojx + gyj[q].v[u] * ojy;
+            }
+        }
+        const int w = jn[q] < 0 ? __ldg(wall + s) : -1;      // uniform over the CTA
+        if (w >= 0) {
+            const T th = __ldg(wallp + 3 * w), uw1 = __ldg(wallp + 3 * w + 1), uw2 = __ldg(wallp + 3 * w + 2);
+            const T inv2th = (T)0.5 / th, norm = (T)(0.15915494309189535) / th;   // 1 / (2 pi theta)
+            T mw[4];
+            double num = 0.0, den = 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const T d1 = v1 - uw1, d2 = v2[u] - uw2;
+                mw[u] = norm * exp(-(d1 * d1 + d2 * d2) * inv2th);
+                if (act && vn[u] > (T)0) num += (double)(fl[u] * vn[u]);
+                if (act && vn[u] < (T)0) den += (double)(mw[u] * -vn[u]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                num += __shfl_xor_sync(0xffffffffu, num, o);
+                den += __shfl_xor_sync(0xffffffffu, den, o);
+            }
+            __syncthreads();                     // red is reused face after face
+            if ((threadIdx.x & 31) == 0) {
+                red[2 * (threadIdx.x >> 5)] = num;
+                red[2 * (threadIdx.x >> 5) + 1] = den;
+            }
+            __syncthreads();
+            num = den = 0.0;
+#pragma unroll
+            for (int q2 = 0; q2 < kFvThreads / 32; ++q2) {
+                num += red[2 * q2];
+                den += red[2 * q2 + 1];
+            }
+            const T mu = (T)(num / den);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) fr[u] = vn[u] > (T)0 ? fl[u] : mu * mw[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += (T)0.5 * vn[u] * (fl[u] + fr[u]) - (T)0.5 * fabs(vn[u]) * (fr[u] - fl[u]);
+    }
+    if (act) {
+        const T ia = __ldg(tb.inv_area + i);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) L[i * nv + k + u] = acc[u] * ia;
+    }
+}
+
 template <typename T> const FvTables<T> &pick(const bz_mesh *m);
 template <> const FvTables<double> &pick<double>(const bz_mesh *m) { return m->t64; }
 template <> const FvTables<float> &pick<float>(const bz_mesh *m) { return m->t32; }
@@ -304,9 +434,39 @@ cudaError_t gradient(const bz_mesh *m, const GridView &g, const T *f, T *G, cuda
     return cudaGetLastError();
 }
 
+template <typename T, bool kGrad, int MAXF, bool VLOAD>
+void flux_wall_launch(const bz_mesh *m, const GridView &g, const T *f, const T *G, T *L, cudaStream_t st) {
+    const T *wp = static_cast<const T *>(sizeof(T) == 8 ? static_cast<const void *>(m->d_wall64)
+                                                        : static_cast<const void *>(m->d_wall32));
+    fv_flux_wall_kernel<T, kGrad, MAXF, VLOAD><<<(unsigned)m->n_cells, kFvThreads, 0, st>>>(
+        f, G, L, pick<T>(m), m->d_nface, m->d_nb, m->d_order, m->d_wall, wp, (int)g.nv, g.N, (T)g.L, (T)g.dv);
+}
+
+template <typename T>
+cudaError_t flux_walls(const bz_mesh *m, const GridView &g, const T *f, const T *G, T *L, cudaStream_t st) {
+    const bool al = aligned16(f) && aligned16(L) && (!G || aligned16(G));
+    const bool tri = m->max_faces <= 3;
+    if (G) {
+        if (tri && al) flux_wall_launch<T, true, 3, true>(m, g, f, G, L, st);
+        else if (tri) flux_wall_launch<T, true, 3, false>(m, g, f, G, L, st);
+        else if (al) flux_wall_launch<T, true, kFvMaxFaces, true>(m, g, f, G, L, st);
+        else flux_wall_launch<T, true, kFvMaxFaces, false>(m, g, f, G, L, st);
+    } else {
+        if (tri && al) flux_wall_launch<T, false, 3, true>(m, g, f, G, L, st);
+        else if (tri) flux_wall_launch<T, false, 3, false>(m, g, f, G, L, st);
+        else if (al) flux_wall_launch<T, false, kFvMaxFaces, true>(m, g, f, G, L, st);
+        else flux_wall_launch<T, false, kFvMaxFaces, false>(m, g, f, G, L, st);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t flux(const bz_mesh *m, const GridView &g, const T *f, const T *G, T *L, cudaStream_t st) {
     if (m->n_cells <= 0) return cudaSuccess;
+    if (m->n_walls > 0) {
+        if (!fv_walls_supported(m, g)) return cudaErrorInvalidValue;
+        return flux_walls<T>(m, g, f, G, L, st);
+    }
     const bool tri = m->max_faces <= 3;
     const bool v4 = tri && g.N % 4 == 0 && aligned16(f) && aligned16(L) && (!G || aligned16(G));
     if (G) {
@@ -322,6 +482,10 @@ cudaError_t flux(const bz_mesh *m, const GridView &g, const T *f, const T *G, T 
 }
 
 }  // namespace
+
+bool fv_walls_supported(const bz_mesh *m, const GridView &g) {
+    return m->n_walls == 0 || (g.N % 4 == 0 && g.nv <= 4 * kFvThreads);
+}
 
 cudaError_t launch_fv_gradient_f64(const bz_mesh *m, const GridView &g, const double *f, double *G, cudaStream_t st) {
     return gradient<double>(m, g, f, G, st);

@@ -65,8 +65,10 @@ def _mixed():
     return pts, cells
 
 
-def _magnitude(om, f, N, L, order, fvo):
-    """M_ik of the module docstring."""
+def _magnitude(om, f, N, L, order, fvo, walls=None):
+    """M_ik of the module docstring (at a wall face the inner state bounds the
+    outgoing half and mu_mag M_w the incoming one, mu_mag formed from the
+    magnitudes)."""
     v1, v2 = fvo.velocity_grid(N, L)
     af = np.abs(np.asarray(f, dtype=np.float64))
     n = len(om.cells)
@@ -87,22 +89,32 @@ def _magnitude(om, f, N, L, order, fvo):
             G[i] = np.max(cand, axis=0)
     M = np.zeros_like(af)
     for i, fl in enumerate(om.faces):
-        for (j, ln, nx, ny, mx, my) in fl:
+        for q, (j, ln, nx, ny, mx, my) in enumerate(fl):
             avn = ln * (np.abs(v1 * nx) + np.abs(v2 * ny))
             fl_ = af[i] + G[i] * (abs(mx - om.bary[i, 0]) + abs(my - om.bary[i, 1]))
             fr_ = fl_ if j < 0 else af[j] + G[j] * (abs(mx - om.bary[j, 0]) + abs(my - om.bary[j, 1]))
+            wall = None if (walls is None or j >= 0) else walls.get(frozenset(om.face_vertices[i][q]))
+            if wall is not None:
+                vn = v1 * nx + v2 * ny
+                mw = fvo.wall_maxwellian(v1, v2, *wall)
+                mu = (fl_ * np.abs(vn))[vn > 0].sum() / (mw * np.abs(vn))[vn < 0].sum()
+                fr_ = fl_ + mu * mw
             M[i] += avn * (fl_ + fr_)
         M[i] /= om.area[i]
     return M
 
 
-def _check(got, want, om, fin, N, L, order, fvo, u, eta):
-    """err <= 64 (u M(|f|) + eta M(1)): eta is the absolute error of a rounding
+def _check(got, want, om, fin, N, L, order, fvo, u, eta, walls=None):
+    """err <= C (u M(|f|) + eta M(1)): eta is the absolute error of a rounding
     in the subnormal range (2^-150 in FP32), which the tails of f reach; M(1)
-    carries it through the same sums."""
+    carries it through the same sums.  C = 64; with walls, the mass balance of
+    a wall face adds two sums over the N^2 velocities and a division (up to
+    2 log2 N^2 + 8 roundings, in the incoming half of the face state), so
+    C = 64 + 4 log2 N^2 + 16."""
     err = np.abs(got - want)
-    bound = 64 * (u * _magnitude(om, fin, N, L, order, fvo) +
-                  eta * _magnitude(om, np.ones_like(fin), N, L, order, fvo))
+    C = 64 if walls is None else 64 + 4 * np.log2(N * N) + 16
+    bound = C * (u * _magnitude(om, fin, N, L, order, fvo, walls) +
+                 eta * _magnitude(om, np.ones_like(fin), N, L, order, fvo, walls))
     assert (err <= bound).all(), float((err / np.maximum(bound, 1e-300)).max())
 
 
@@ -228,3 +240,73 @@ def test_full_mesh_fp32_sampled(bz, fvo):
     bz.check()
     want = fvo.transport_residual(om, fin, N, Lv, order=2)
     _check(Lr.double().cpu().numpy(), want, om, fin, N, Lv, 2, fvo, U32, ETA32)
+
+
+def _walls(om, rng=None):
+    """Every boundary edge a wall: temperatures and velocities vary by edge."""
+    rng = rng or np.random.default_rng(0)
+    edges, params, walls = [], [], {}
+    for i, fl in enumerate(om.faces):
+        for q, fc in enumerate(fl):
+            if fc[0] < 0:
+                a, b = om.face_vertices[i][q]
+                p = (float(rng.uniform(0.6, 1.4)), float(rng.uniform(-0.3, 0.3)), float(rng.uniform(-0.3, 0.3)))
+                edges.append((a, b))
+                params.append(p)
+                walls[frozenset((a, b))] = p
+    return np.array(edges), np.array(params), walls
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("order", [1, 2])
+def test_walls_match_oracle(bz, fvo, precision, order):
+    N, Lv = 8, 6.0
+    pts, cells = _tri(12)
+    om = fvo.Mesh(pts, cells)
+    edges, params, walls = _walls(om)
+    f = workloads.mesh_states(om.bary, N, Lv, jump=True)
+    fin = as_input(f, precision)
+    m = bz.Mesh(pts, cells, order=order)
+    m.set_walls(edges, params)
+    Lr = bz.transport_residual(m, bz.Grid(2, N, Lv), to_dev(f, precision), precision=precision)
+    bz.check()
+    want = fvo.transport_residual(om, fin, N, Lv, order=order, walls=walls)
+    u, eta = (U64, ETA64) if precision == "fp64" else (U32, ETA32)
+    _check(Lr.double().cpu().numpy(), want, om, fin, N, Lv, order, fvo, u, eta, walls)
+    if precision == "fp64":     # a closed box: no mass crosses the walls
+        tot = (om.area[:, None] * Lr.cpu().numpy()).sum()
+        assert abs(tot) < 1e-12 * (om.area[:, None] * np.abs(want)).sum()
+
+
+def test_walls_imex_step_and_limits(bz, fvo):
+    """The coupled step with walls against the oracle's composed stages; walls
+    removed again give the transmissive result; unsupported grids and edges
+    that are not boundary edges are refused."""
+    import oracle
+    N, Lv, dt, eps = 8, 6.0, 2e-3, 5e-2
+    pts, cells = _tri(10)
+    om = fvo.Mesh(pts, cells)
+    edges, params, walls = _walls(om, np.random.default_rng(5))
+    f = workloads.mesh_states(om.bary, N, Lv, jump=True)
+    k = oracle.Kernel(2, N, Lv, 0.0)
+    Lres = np.zeros((3,) + f.shape)
+    for l in range(2):
+        _, F, _, _ = k.imex_step(f, dt, eps, Lres=Lres, stages=True)
+        Lres[l] = fvo.transport_residual(om, F[l], N, Lv, order=2, walls=walls)
+    want = k.imex_step(f, dt, eps, Lres=Lres)
+    m = bz.Mesh(pts, cells, order=2)
+    m.set_walls(edges, params)
+    got = bz.imex_step_fv(bz.Modes(bz.Grid(2, N, Lv), 0.0), m, to_dev(f, "fp64"), dt, eps, precision="fp64")
+    bz.check()
+    assert relerr(got.cpu().numpy(), want) < TOL64
+    m.set_walls([], [])
+    L0 = bz.transport_residual(m, bz.Grid(2, N, Lv), to_dev(f, "fp64"), precision="fp64").cpu().numpy()
+    _check(L0, fvo.transport_residual(om, f, N, Lv, order=2), om, f, N, Lv, 2, fvo, U64, ETA64)
+    m.set_walls(edges, params)
+    import torch
+    with pytest.raises(bz.BzError):          # 4 does not divide N
+        bz.transport_residual(m, bz.Grid(2, 6, Lv), torch.zeros((m.n_cells, 36), dtype=torch.float64,
+                                                                 device="cuda"), precision="fp64")
+    inner = next((om.face_vertices[i][q] for i, fl in enumerate(om.faces) for q, fc in enumerate(fl) if fc[0] >= 0))
+    with pytest.raises(bz.BzError):
+        m.set_walls([inner], [(1.0, 0.0, 0.0)])
