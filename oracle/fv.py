@@ -58,9 +58,16 @@ R_EXP = 4
 
 class Mesh:
     """Geometry of a polygonal mesh: vertices xy (n_vtx, 2), cells as a list of
-    vertex-index lists (any orientation; stored counter-clockwise)."""
+    vertex-index lists (any orientation; stored counter-clockwise).
 
-    def __init__(self, xy, cells):
+    periodic=(Lx, Ly) makes the mesh periodic in x and/or y (0: not periodic in
+    that direction): vertices whose coordinates agree modulo the periods are
+    one point of the torus.  Neighbour relations then carry a shift s, the
+    translation that takes the neighbour's coordinates into the cell's frame,
+    and every offset to a neighbour's barycentre or face midpoint uses
+    bary_j + s."""
+
+    def __init__(self, xy, cells, periodic=None):
         self.xy = np.asarray(xy, dtype=np.float64)
         self.cells = []
         n = len(cells)
@@ -77,30 +84,66 @@ class Mesh:
             self.area[i] = a
             self.bary[i] = b
             self.h[i] = np.sqrt(((self.xy[c] - b) ** 2).sum(axis=1)).max()
+        # periodic classes of the vertices (the vertex itself without periodicity)
+        self.vclass = np.arange(len(self.xy))
+        self.period = (0.0, 0.0)
+        if periodic is not None and (periodic[0] > 0 or periodic[1] > 0):
+            Lx, Ly = float(periodic[0]), float(periodic[1])
+            self.period = (Lx, Ly)
+            tol = 1e-9 * max(Lx, Ly)
+            reps = {}
+            for v, (x, y) in enumerate(self.xy):
+                kx = round((x % Lx) / tol) % round(Lx / tol) if Lx > 0 else round(x / tol)
+                ky = round((y % Ly) / tol) % round(Ly / tol) if Ly > 0 else round(y / tol)
+                self.vclass[v] = reps.setdefault((kx, ky), v)
         # faces: edge a -> b of a counter-clockwise polygon has the outward
-        # normal (y_b - y_a, -(x_b - x_a)) / |e|; the neighbour owns edge b -> a
+        # normal (y_b - y_a, -(x_b - x_a)) / |e|; the neighbour owns the edge
+        # b -> a (periodic classes), the shift is the difference of the copies
+        # of a
         owner = {}
         for i, c in enumerate(self.cells):
             for q in range(len(c)):
-                owner[(c[q], c[(q + 1) % len(c)])] = i
+                a, b = c[q], c[(q + 1) % len(c)]
+                owner[(self.vclass[a], self.vclass[b])] = (i, a)
         self.faces = []          # per cell: list of (neighbour or -1, length, nx, ny, midx, midy)
         self.face_vertices = []  # per cell: the vertex pair (a, b) of every face
+        self.face_shift = []     # per cell: the neighbour's shift across every face
         for i, c in enumerate(self.cells):
-            fl = []
+            fl, sh = [], []
             self.face_vertices.append([(c[q], c[(q + 1) % len(c)]) for q in range(len(c))])
             for q in range(len(c)):
                 a, b = c[q], c[(q + 1) % len(c)]
                 d = self.xy[b] - self.xy[a]
                 ln = float(np.hypot(d[0], d[1]))
                 mid = 0.5 * (self.xy[a] + self.xy[b])
-                fl.append((owner.get((b, a), -1), ln, d[1] / ln, -d[0] / ln, mid[0], mid[1]))
+                j, shift = -1, np.zeros(2)
+                o = owner.get((self.vclass[b], self.vclass[a]))
+                if o is not None:
+                    j = o[0]
+                    # the neighbour's copy of b (its edge runs b -> a): the
+                    # vertex of the same class on the neighbour's edge
+                    cj = self.cells[j]
+                    wb = next(w for w in cj if self.vclass[w] == self.vclass[b])
+                    shift = self._lattice(self.xy[b] - self.xy[wb])
+                fl.append((j, ln, d[1] / ln, -d[0] / ln, mid[0], mid[1]))
+                sh.append(shift)
             self.faces.append(fl)
-        # vertex -> cells
-        vc = [[] for _ in range(len(self.xy))]
+            self.face_shift.append(sh)
+        # vertex class -> (cell, vertex)
+        vc = {}
         for i, c in enumerate(self.cells):
             for v in c:
-                vc[v].append(i)
+                vc.setdefault(self.vclass[v], []).append((i, v))
         self.vertex_cells = vc
+
+    def _lattice(self, s):
+        """A shift rounded to the nearest multiple of the periods (zero along a
+        direction without periodicity)."""
+        out = np.zeros(2)
+        for d in range(2):
+            if self.period[d] > 0:
+                out[d] = round(s[d] / self.period[d]) * self.period[d]
+        return out
 
     def _shoelace(self, c):
         """Signed area and barycentre of the polygon c, with coordinates taken
@@ -114,35 +157,52 @@ class Mesh:
         return a, b
 
     def vertex_neighbours(self, i):
-        s = set()
+        """{(j, sx, sy)}: cells sharing a (periodic) vertex with cell i, with the
+        shift of j's copy into i's frame; (i, 0, 0) excluded."""
+        out = set()
         for v in self.cells[i]:
-            s.update(self.vertex_cells[v])
-        s.discard(i)
-        return s
+            for (j, w) in self.vertex_cells[self.vclass[v]]:
+                s = self._lattice(self.xy[v] - self.xy[w])
+                out.add((j, float(s[0]), float(s[1])))
+        out.discard((i, 0.0, 0.0))
+        return out
 
-    def central_stencil(self, i, count=5):
+    def central_stencil_shifted(self, i, count=5):
+        """The 5 nearest (cell, shift) images by barycentre distance among the
+        vertex neighbours and their vertex neighbours (ties by index, shift)."""
         cand = set()
         first = self.vertex_neighbours(i)
         cand.update(first)
-        for j in first:
-            cand.update(self.vertex_neighbours(j))
-        cand.discard(i)
-        d = [(float(np.hypot(*(self.bary[j] - self.bary[i]))), j) for j in cand]
+        for (j, sx, sy) in first:
+            for (k, tx, ty) in self.vertex_neighbours(j):
+                cand.add((k, sx + tx, sy + ty))
+        cand.discard((i, 0.0, 0.0))
+        d = [(float(np.hypot(self.bary[j, 0] + sx - self.bary[i, 0], self.bary[j, 1] + sy - self.bary[i, 1])),
+              j, sx, sy) for (j, sx, sy) in cand]
         d.sort()
-        return [j for _, j in d[:count]]
+        return [(j, np.array([sx, sy])) for _, j, sx, sy in d[:count]]
 
-    def sectors(self, i):
+    def central_stencil(self, i, count=5):
+        return [j for j, _ in self.central_stencil_shifted(i, count)]
+
+    def sectors_shifted(self, i):
+        """[(a, s_a, b, s_b)]: consecutive face neighbours with their shifts."""
         fl = self.faces[i]
         out = []
         for q in range(len(fl)):
-            a, b = fl[q][0], fl[(q + 1) % len(fl)][0]
+            q2 = (q + 1) % len(fl)
+            a, b = fl[q][0], fl[q2][0]
             if a < 0 or b < 0:
                 continue
-            A = np.array([self.bary[a] - self.bary[i], self.bary[b] - self.bary[i]])
+            sa, sb = self.face_shift[i][q], self.face_shift[i][q2]
+            A = np.array([self.bary[a] + sa - self.bary[i], self.bary[b] + sb - self.bary[i]])
             if abs(np.linalg.det(A)) <= 1e-12 * float(np.abs(A).max()) ** 2:
                 continue
-            out.append((a, b))
+            out.append((a, sa, b, sb))
         return out
+
+    def sectors(self, i):
+        return [(a, b) for a, _, b, _ in self.sectors_shifted(i)]
 
 
 def velocity_grid(N, L):
@@ -159,18 +219,18 @@ def reconstruct_gradients(mesh, f, order):
     if order == 1:
         return g
     for i in range(n):
-        st = mesh.central_stencil(i)
-        A = np.array([mesh.bary[j] - mesh.bary[i] for j in st])            # (5, 2)
-        d = np.array([f[j] - f[i] for j in st])                             # (5, nv)
+        st = mesh.central_stencil_shifted(i)
+        A = np.array([mesh.bary[j] + s - mesh.bary[i] for j, s in st])     # (5, 2)
+        d = np.array([f[j] - f[i] for j, _ in st])                          # (5, nv)
         g_opt = np.linalg.solve(A.T @ A, A.T @ d)       # normal equations of the least-squares fit
-        secs = mesh.sectors(i)
+        secs = mesh.sectors_shifted(i)
         if not secs:
             g[i] = g_opt
             continue
         lam_l = (1.0 - LAMBDA0) / len(secs)
         gs = []
-        for a, b in secs:
-            A2 = np.array([mesh.bary[a] - mesh.bary[i], mesh.bary[b] - mesh.bary[i]])
+        for a, sa, b, sb in secs:
+            A2 = np.array([mesh.bary[a] + sa - mesh.bary[i], mesh.bary[b] + sb - mesh.bary[i]])
             gs.append(np.linalg.solve(A2, np.array([f[a] - f[i], f[b] - f[i]])))
         g0 = (g_opt - lam_l * sum(gs)) / LAMBDA0
         polys = [g0] + gs
@@ -215,7 +275,8 @@ def transport_residual(mesh, f, N, L, order=2, walls=None):
             elif j < 0:
                 fr = fl
             else:
-                fr = f[j] + g[j, 0] * (mx - mesh.bary[j, 0]) + g[j, 1] * (my - mesh.bary[j, 1])
+                sx, sy = mesh.face_shift[i][q]
+                fr = f[j] + g[j, 0] * (mx - sx - mesh.bary[j, 0]) + g[j, 1] * (my - sy - mesh.bary[j, 1])
             acc += ln * (0.5 * vn * (fl + fr) - 0.5 * np.abs(vn) * (fr - fl))
         out[i] = acc / mesh.area[i]
     return out

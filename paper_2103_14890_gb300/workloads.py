@@ -116,6 +116,56 @@ def sod_triangulation(n_side=100, seed=1004, jitter=0.3):
     return pts, np.ascontiguousarray(tri, dtype=np.int64)
 
 
+def periodic_triangulation(n_side, Lx=10.0, Ly=10.0, seed=1006, jitter=0.25):
+    """Triangulated jittered lattice of the periodic box [0,Lx] x [0,Ly]: the
+    n_side x n_side nodes of the torus are jittered (by up to jitter x spacing)
+    and repeated with the periods, so the left and right (bottom and top)
+    boundaries are translates of each other; every lattice quadrilateral is
+    split along a randomly chosen diagonal.  Returns the vertices
+    ((n_side + 1)^2, 2) and the triangles (2 n_side^2, 3)."""
+    rng = np.random.default_rng(seed)
+    n = n_side
+    hx, hy = Lx / n, Ly / n
+    jx = rng.uniform(-jitter, jitter, (n, n)) * hx
+    jy = rng.uniform(-jitter, jitter, (n, n)) * hy
+    a = np.arange(n + 1)
+    A, B = np.meshgrid(a, a, indexing="ij")
+    X = A * hx + jx[A % n, B % n]
+    Y = B * hy + jy[A % n, B % n]
+    pts = np.stack([X.ravel(), Y.ravel()], axis=1)
+    idx = np.arange((n + 1) ** 2).reshape(n + 1, n + 1)
+    flip = rng.uniform(size=(n, n)) < 0.5
+    tri = []
+    for i in range(n):
+        for j in range(n):
+            p0, p1, p2, p3 = idx[i, j], idx[i + 1, j], idx[i + 1, j + 1], idx[i, j + 1]
+            if flip[i, j]:
+                tri += [(p0, p1, p2), (p0, p2, p3)]
+            else:
+                tri += [(p0, p1, p3), (p1, p2, p3)]
+    return pts, np.asarray(tri, dtype=np.int64)
+
+
+def vortex_states(bary, N, L, t=0.0, Lx=10.0, Ly=10.0, beta=5.0, gamma=2.0):
+    """Maxwellians of the isentropic vortex of Sec. 4.1 (the Euler solution,
+    advected by the mean flow (1, 1) over the periodic box) at the points
+    bary (n, 2) at time t: delta T = -(gamma-1) beta^2/(8 gamma pi^2)
+    e^{1-r^2}, rho = (1 + delta T)^{1/(gamma-1)}, u = (1, 1) + beta/(2 pi)
+    e^{(1-r^2)/2} (-(y-5), x-5), T = 1 + delta T, r measured from the
+    vortex centre (5, 5) + t (1, 1) taken periodically.  Returns
+    (f (n, N^2), rho (n,), T (n,))."""
+    x = (bary[:, 0] - t) % Lx
+    y = (bary[:, 1] - t) % Ly
+    dx, dy = x - 5.0, y - 5.0
+    r2 = dx * dx + dy * dy
+    dT = -(gamma - 1.0) * beta ** 2 / (8.0 * gamma * np.pi ** 2) * np.exp(1.0 - r2)
+    rho = (1.0 + dT) ** (1.0 / (gamma - 1.0))
+    du = beta / (2.0 * np.pi) * np.exp(0.5 * (1.0 - r2))
+    u = np.stack([1.0 - du * dy, 1.0 + du * dx], axis=1)
+    T = 1.0 + dT
+    return _gaussian(2, N, L, rho, u, T), rho, T
+
+
 def sod_mesh(n_side=100, seed=1004, jitter=0.3):
     """Triangle centroids (n_tri, 2) of sod_triangulation and the mesh size
     h = sqrt(mean area)."""

@@ -198,3 +198,45 @@ def test_walls_conserve_mass(fv, order):
     Lr = fv.transport_residual(m, f, N, L, order=order, walls=_box_walls(m, 1.2, (0.3, -0.2)))
     total = (m.area[:, None] * Lr).sum()
     assert abs(total) < 1e-13 * (m.area[:, None] * np.abs(Lr)).sum()
+
+
+def _tile3(pts, tri, Lx, Ly):
+    """3 x 3 copies of a periodic mesh as one plain mesh (shared vertices merged)."""
+    key, xy, cells = {}, [], []
+    tol = 1e-9 * max(Lx, Ly)
+    for ky in (-1, 0, 1):
+        for kx in (-1, 0, 1):
+            vid = []
+            for (x, y) in pts:
+                X, Y = x + kx * Lx, y + ky * Ly
+                k = (round(X / tol), round(Y / tol))
+                if k not in key:
+                    key[k] = len(xy)
+                    xy.append((X, Y))
+                vid.append(key[k])
+            cells += [[vid[v] for v in c] for c in tri]
+    return np.array(xy), cells
+
+
+def test_periodic_mesh_equals_the_tiled_plane(fv):
+    """The periodic residual equals that of the middle copy of a 3 x 3 tiling
+    computed as a plain (non-periodic) mesh: pins the shifts of faces,
+    stencils and sectors against the ordinary code path."""
+    Lx, Ly = 10.0, 6.0
+    pts, tri = workloads.periodic_triangulation(6, Lx, Ly, seed=2)
+    m = fv.Mesh(pts, tri, periodic=(Lx, Ly))
+    assert abs(m.area.sum() - Lx * Ly) < 1e-11
+    assert all(fc[0] >= 0 for fl in m.faces for fc in fl)
+    N, L = 4, 3.0
+    rng = np.random.default_rng(8)
+    f = rng.uniform(0.1, 1.0, (len(m.cells), N * N))
+    xy3, cells3 = _tile3(pts, tri, Lx, Ly)
+    m3 = fv.Mesh(xy3, cells3)
+    f3 = np.tile(f, (9, 1))
+    for order in (1, 2):
+        Lp = fv.transport_residual(m, f, N, L, order=order)
+        L3 = fv.transport_residual(m3, f3, N, L, order=order)
+        mid = L3[4 * len(m.cells):5 * len(m.cells)]
+        assert np.abs(Lp - mid).max() < 1e-12 * np.abs(mid).max()
+        # no boundary: the fluxes cancel in the sum
+        assert abs((m.area[:, None] * Lp).sum()) < 1e-12 * (m.area[:, None] * np.abs(Lp)).sum()
