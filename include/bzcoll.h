@@ -259,6 +259,22 @@ int group_collide(const bz_group_item *items, int n_items, int precision, int fl
 int build_fv_mesh(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
                   const int64_t *cell_vertices, int order, bz_mesh **out);
 
+/* build_fv_mesh_periodic -- build_fv_mesh on a mesh that is periodic with
+ * period Lx in x and/or Ly in y (0: not periodic in that direction), as for
+ * the isentropic vortex of Sec. 4.  Vertices whose coordinates agree modulo
+ * the periods (within 1e-9 max(Lx, Ly)) are one point; a boundary edge whose
+ * periodic image is an edge of another cell pairs with it, and the
+ * neighbour's barycentre enters the face offsets, the least-squares stencil
+ * and the sectors translated by the multiple of the periods that brings it
+ * next to the cell.  Stencil candidates are (cell, translation) pairs, so a
+ * cell can appear in a stencil more than once on a mesh that is a few cells
+ * wide.  The remaining boundary edges stay transmissive.
+ *   Lx, Ly : periods, >= 0 (both 0: the same as build_fv_mesh)
+ * Other arguments and errors as build_fv_mesh; BZ_EINVAL also for negative
+ * or non-finite periods. */
+int build_fv_mesh_periodic(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
+                           const int64_t *cell_vertices, int order, double Lx, double Ly, bz_mesh **out);
+
 /* fv_mesh_set_walls -- make boundary edges walls with full accommodation
  * (Sec. 2, eq. BOU with alpha = 1, eq. MAXB, eq. MU): at a wall face the
  * velocities leaving the domain carry the reconstructed inner value f_L, the

@@ -104,7 +104,11 @@ class Mesh:
         for i, c in enumerate(self.cells):
             for q in range(len(c)):
                 a, b = c[q], c[(q + 1) % len(c)]
-                owner[(self.vclass[a], self.vclass[b])] = (i, a)
+                key = (self.vclass[a], self.vclass[b])
+                if key in owner:         # the pairing of this edge would be ambiguous
+                    raise ValueError("an edge is used twice in the same direction (overlapping cells, "
+                                     "inconsistent orientation, or a period only two cells wide)")
+                owner[key] = (i, a)
         self.faces = []          # per cell: list of (neighbour or -1, length, nx, ny, midx, midy)
         self.face_vertices = []  # per cell: the vertex pair (a, b) of every face
         self.face_shift = []     # per cell: the neighbour's shift across every face

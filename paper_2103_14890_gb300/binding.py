@@ -72,6 +72,7 @@ def load(path=None):
             "build_fast_modes": ([c_p, c_d, c_i, pp], c_i),
             "bz_fast_info": ([c_p, ctypes.POINTER(c_i64)], c_i),
             "build_fv_mesh": ([c_i, c_p, c_i64, c_p, c_p, c_i, pp], c_i),
+            "build_fv_mesh_periodic": ([c_i, c_p, c_i64, c_p, c_p, c_i, c_d, c_d, pp], c_i),
             "transport_residual": ([c_p, c_p, c_i, c_p, c_p, c_p], c_i),
             "imex_step_fv": ([c_p, c_p, c_i, c_i, c_d, c_d, c_p, c_p, c_i, c_i, c_p], c_i),
             "bz_mesh_info": ([c_p, ctypes.POINTER(c_i64)], c_i),
@@ -181,9 +182,11 @@ class FastModes(Modes):
 class Mesh:
     """Finite-volume mesh of the transport step (build_fv_mesh): vertices xy
     (n_vtx, 2) and cells, either an (n_cells, k) integer array or a list of
-    vertex lists; order 1 (first order) or 2 (CWENO of degree 1)."""
+    vertex lists; order 1 (first order) or 2 (CWENO of degree 1); periodic
+    (Lx, Ly) makes it periodic (build_fv_mesh_periodic, 0 for a direction
+    without periodicity)."""
 
-    def __init__(self, xy, cells, order=2):
+    def __init__(self, xy, cells, order=2, periodic=None):
         import numpy as np
         xy = np.ascontiguousarray(xy, dtype=np.float64)
         cells = [list(map(int, c)) for c in cells]
@@ -191,9 +194,12 @@ class Mesh:
         ptr[1:] = np.cumsum([len(c) for c in cells])
         vtx = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.int64) for c in cells]))
         h = ctypes.c_void_p()
-        _check(load().build_fv_mesh(int(len(xy)), xy.ctypes.data_as(ctypes.c_void_p), int(len(cells)),
-                                    ptr.ctypes.data_as(ctypes.c_void_p), vtx.ctypes.data_as(ctypes.c_void_p),
-                                    int(order), ctypes.byref(h)))
+        args = (int(len(xy)), xy.ctypes.data_as(ctypes.c_void_p), int(len(cells)),
+                ptr.ctypes.data_as(ctypes.c_void_p), vtx.ctypes.data_as(ctypes.c_void_p), int(order))
+        if periodic is None:
+            _check(load().build_fv_mesh(*args, ctypes.byref(h)))
+        else:
+            _check(load().build_fv_mesh_periodic(*args, float(periodic[0]), float(periodic[1]), ctypes.byref(h)))
         self._h = h
         info = (ctypes.c_int64 * 5)()
         _check(load().bz_mesh_info(h, info))

@@ -30,7 +30,7 @@ void grid_destroy(bz_grid *g);
 int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **out);
 int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out);
 int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
-                   const int64_t *cell_vertices, int order, bz_mesh **out);
+                   const int64_t *cell_vertices, int order, double Lx, double Ly, bz_mesh **out);
 void fv_mesh_destroy(bz_mesh *m);
 int fv_mesh_set_walls(bz_mesh *m, int64_t n_edges, const int64_t *edges, const double *params);
 void modes_destroy(bz_modes *m);
@@ -808,7 +808,12 @@ int imex_step_fv(const bz_modes *m, const bz_mesh *mesh, int scheme, int model, 
 
 int build_fv_mesh(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
                   const int64_t *cell_vertices, int order, bz_mesh **out) {
-    return fv_mesh_create(n_vertices, xy, n_cells, cell_ptr, cell_vertices, order, out);
+    return fv_mesh_create(n_vertices, xy, n_cells, cell_ptr, cell_vertices, order, 0.0, 0.0, out);
+}
+
+int build_fv_mesh_periodic(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
+                           const int64_t *cell_vertices, int order, double Lx, double Ly, bz_mesh **out) {
+    return fv_mesh_create(n_vertices, xy, n_cells, cell_ptr, cell_vertices, order, Lx, Ly, out);
 }
 
 int transport_residual(const bz_mesh *mesh, const bz_grid *g, int precision, const void *f, void *L, void *stream) {

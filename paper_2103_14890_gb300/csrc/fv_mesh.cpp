@@ -24,10 +24,13 @@
 // The device keeps R_c = (A^T A)^-1 A^T and A_L^-1 per cell; the nonlinear
 // weights are formed per velocity by the gradient kernel.
 #include <math.h>
+
+#include <cmath>
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <unordered_map>
 #include <utility>
 #include <vector>
@@ -105,7 +108,7 @@ void fv_mesh_destroy(bz_mesh *m) {
 }
 
 int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
-                   const int64_t *cell_vertices, int order, bz_mesh **out) {
+                   const int64_t *cell_vertices, int order, double Lx, double Ly, bz_mesh **out) {
     if (!out) return fail(BZ_EINVAL, "build_fv_mesh: out is NULL");
     *out = nullptr;
     if (n_vertices < 3 || !xy) return fail(BZ_EINVAL, "build_fv_mesh: need >= 3 vertices and their coordinates");
@@ -113,6 +116,8 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
         return fail(BZ_EINVAL, "build_fv_mesh: bad cell list");
     if (order != 1 && order != 2) return fail(BZ_EINVAL, "build_fv_mesh: order must be 1 or 2");
     if (cell_ptr[0] != 0) return fail(BZ_EINVAL, "build_fv_mesh: cell_ptr[0] must be 0");
+    if (!(Lx >= 0) || !(Ly >= 0) || !std::isfinite(Lx) || !std::isfinite(Ly))
+        return fail(BZ_EINVAL, "build_fv_mesh: periods must be finite and >= 0");
     const int64_t n = n_cells;
     HostMesh h;
     h.n = n;
@@ -160,14 +165,37 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
         h.h2.push_back(hm * hm);
         cells[i] = std::move(c);
     }
-    // directed edge -> owning cell
-    std::unordered_map<uint64_t, int64_t> owner;
+    // periodic classes: vertices whose coordinates agree modulo the periods
+    // are one point (a vertex is its own class without periodicity); a shift
+    // is kept as integer multiples (kx, ky) of the periods
+    std::vector<int64_t> vclass(n_vertices);
+    for (int v = 0; v < n_vertices; ++v) vclass[v] = v;
+    const double pmax = std::max(Lx, Ly), qtol = 1e-9 * pmax;
+    if (pmax > 0) {
+        std::map<std::pair<int64_t, int64_t>, int64_t> rep;
+        auto wrap = [qtol](double x, double P) -> int64_t {
+            if (P <= 0) return llround(x / qtol);
+            const int64_t per = llround(P / qtol);
+            int64_t k = llround(x / qtol) % per;
+            return k < 0 ? k + per : k;
+        };
+        for (int v = 0; v < n_vertices; ++v) {
+            vclass[v] = rep.emplace(std::make_pair(wrap(xy[2 * v], Lx), wrap(xy[2 * v + 1], Ly)), v).first->second;
+        }
+    }
+    auto lattice = [&](double dx, double dy, int &kx, int &ky) {
+        kx = Lx > 0 ? (int)llround(dx / Lx) : 0;
+        ky = Ly > 0 ? (int)llround(dy / Ly) : 0;
+    };
+    // directed edge (classes) -> owning cell and its copy of the edge's first vertex
+    std::unordered_map<uint64_t, std::pair<int64_t, int64_t>> owner;
     owner.reserve((size_t)(n * 4));
     auto key = [](int64_t a, int64_t b) { return ((uint64_t)a << 32) | (uint64_t)b; };
     for (int64_t i = 0; i < n; ++i) {
         const auto &c = cells[i];
         for (size_t q = 0; q < c.size(); ++q) {
-            if (!owner.emplace(key(c[q], c[(q + 1) % c.size()]), i).second)
+            const int64_t a = c[q], b = c[(q + 1) % c.size()];
+            if (!owner.emplace(key(vclass[a], vclass[b]), std::make_pair(i, a)).second)
                 return fail(BZ_EINVAL, "build_fv_mesh: an edge is used twice in the same direction (overlapping or "
                                        "inconsistently oriented cells)");
         }
@@ -177,6 +205,7 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
     h.fn.assign(n * kFvMaxFaces * 2, 0.0);
     h.off_i.assign(n * kFvMaxFaces * 2, 0.0);
     h.off_j.assign(n * kFvMaxFaces * 2, 0.0);
+    std::vector<double> fsx(n * kFvMaxFaces, 0.0), fsy(n * kFvMaxFaces, 0.0);   // neighbour shifts
     int64_t interior = 0, boundary = 0;
     int maxf = 0;
     for (int64_t i = 0; i < n; ++i) {
@@ -193,12 +222,16 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
             h.fn[2 * s + 1] = -dx;
             h.off_i[2 * s] = mx - bx[i];
             h.off_i[2 * s + 1] = my - by[i];
-            auto it = owner.find(key(b, a));
+            auto it = owner.find(key(vclass[b], vclass[a]));
             if (it != owner.end()) {
-                const int64_t j = it->second;
+                const int64_t j = it->second.first, wb = it->second.second;   // j's copy of b
+                int kx, ky;
+                lattice(xy[2 * b] - xy[2 * wb], xy[2 * b + 1] - xy[2 * wb + 1], kx, ky);
+                fsx[s] = kx * Lx;
+                fsy[s] = ky * Ly;
                 h.nb[s] = (int)j;
-                h.off_j[2 * s] = mx - bx[j];
-                h.off_j[2 * s + 1] = my - by[j];
+                h.off_j[2 * s] = mx - fsx[s] - bx[j];
+                h.off_j[2 * s + 1] = my - fsy[s] - by[j];
                 ++interior;
             } else {
                 ++boundary;
@@ -212,61 +245,87 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
     h.sec.assign(n * kFvMaxFaces * 2, 0);
     h.Rs.assign(n * kFvMaxFaces * 4, 0.0);
     if (order == 2) {
-        // vertex -> cells
-        std::vector<int64_t> vptr(n_vertices + 1, 0), vcell;
+        // vertex class -> (cell, vertex)
+        std::vector<int64_t> vptr(n_vertices + 1, 0);
+        std::vector<std::pair<int64_t, int64_t>> vcell;
         for (int64_t i = 0; i < n; ++i)
-            for (int64_t v : cells[i]) ++vptr[v + 1];
+            for (int64_t v : cells[i]) ++vptr[vclass[v] + 1];
         for (int v = 0; v < n_vertices; ++v) vptr[v + 1] += vptr[v];
-        vcell.assign(vptr[n_vertices], 0);
+        vcell.assign(vptr[n_vertices], {0, 0});
         std::vector<int64_t> fillp(vptr.begin(), vptr.end() - 1);
         for (int64_t i = 0; i < n; ++i)
-            for (int64_t v : cells[i]) vcell[fillp[v]++] = i;
-        auto vertex_neighbours = [&](int64_t i, std::vector<int64_t> &out) {
-            for (int64_t v : cells[i])
-                for (int64_t p = vptr[v]; p < vptr[v + 1]; ++p)
-                    if (vcell[p] != i) out.push_back(vcell[p]);
+            for (int64_t v : cells[i]) vcell[fillp[vclass[v]]++] = {i, v};
+        struct Img {
+            int64_t j;
+            int kx, ky;
+            bool operator<(const Img &o) const {
+                return j != o.j ? j < o.j : kx != o.kx ? kx < o.kx : ky < o.ky;
+            }
+            bool operator==(const Img &o) const { return j == o.j && kx == o.kx && ky == o.ky; }
         };
-        std::vector<int64_t> ring, cand;
-        std::vector<std::pair<double, int64_t>> dist;
+        // cells sharing a (periodic) vertex with cell i, with the shift of
+        // their copy into i's frame, offset by (ox, oy)
+        auto vertex_neighbours = [&](int64_t i, int ox, int oy, std::vector<Img> &out) {
+            for (int64_t v : cells[i])
+                for (int64_t p = vptr[vclass[v]]; p < vptr[vclass[v] + 1]; ++p) {
+                    const int64_t j = vcell[p].first, w = vcell[p].second;
+                    int kx, ky;
+                    lattice(xy[2 * v] - xy[2 * w], xy[2 * v + 1] - xy[2 * w + 1], kx, ky);
+                    out.push_back({j, kx + ox, ky + oy});
+                }
+        };
+        std::vector<Img> ring, cand;
+        struct Cand {
+            double d;
+            Img m;
+            bool operator<(const Cand &o) const {
+                return d != o.d ? d < o.d : o.m.j != m.j ? m.j < o.m.j : m.kx != o.m.kx ? m.kx < o.m.kx : m.ky < o.m.ky;
+            }
+        };
+        std::vector<Cand> dist;
         for (int64_t i = 0; i < n; ++i) {
             ring.clear();
-            vertex_neighbours(i, ring);
+            vertex_neighbours(i, 0, 0, ring);
             cand = ring;
-            for (int64_t j : ring) vertex_neighbours(j, cand);
+            for (const Img &r : ring) vertex_neighbours(r.j, r.kx, r.ky, cand);
             std::sort(cand.begin(), cand.end());
             cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
             dist.clear();
-            for (int64_t j : cand)
-                if (j != i) dist.emplace_back(hypot(bx[j] - bx[i], by[j] - by[i]), j);
+            for (const Img &c : cand) {
+                if (c.j == i && c.kx == 0 && c.ky == 0) continue;
+                dist.push_back({hypot(bx[c.j] + c.kx * Lx - bx[i], by[c.j] + c.ky * Ly - by[i]), c});
+            }
             std::sort(dist.begin(), dist.end());
             const int nc = (int)std::min<size_t>(kFvCentral, dist.size());
             double ata[3] = {0, 0, 0};
+            double axs[kFvCentral], ays[kFvCentral];
             for (int q = 0; q < nc; ++q) {
-                const int64_t j = dist[q].second;
-                h.cen[i * kFvCentral + q] = (int)j;
-                const double ax = bx[j] - bx[i], ay = by[j] - by[i];
-                ata[0] += ax * ax;
-                ata[1] += ax * ay;
-                ata[2] += ay * ay;
+                const Img &c = dist[q].m;
+                h.cen[i * kFvCentral + q] = (int)c.j;
+                axs[q] = bx[c.j] + c.kx * Lx - bx[i];
+                ays[q] = by[c.j] + c.ky * Ly - by[i];
+                ata[0] += axs[q] * axs[q];
+                ata[1] += axs[q] * ays[q];
+                ata[2] += ays[q] * ays[q];
             }
             h.ncen[i] = nc;
             const double det = ata[0] * ata[2] - ata[1] * ata[1];
             if (nc >= 2 && det > 1e-300) {
                 const double i00 = ata[2] / det, i01 = -ata[1] / det, i11 = ata[0] / det;
                 for (int q = 0; q < nc; ++q) {
-                    const int64_t j = dist[q].second;
-                    const double ax = bx[j] - bx[i], ay = by[j] - by[i];
-                    h.Rc[(i * 2 + 0) * kFvCentral + q] = i00 * ax + i01 * ay;
-                    h.Rc[(i * 2 + 1) * kFvCentral + q] = i01 * ax + i11 * ay;
+                    h.Rc[(i * 2 + 0) * kFvCentral + q] = i00 * axs[q] + i01 * ays[q];
+                    h.Rc[(i * 2 + 1) * kFvCentral + q] = i01 * axs[q] + i11 * ays[q];
                 }
             }
             // sectors: consecutive faces with neighbours on both
             const int k = h.nface[i];
             int ns = 0;
             for (int q = 0; q < k; ++q) {
-                const int a = h.nb[i * kFvMaxFaces + q], b = h.nb[i * kFvMaxFaces + (q + 1) % k];
+                const size_t sa = (size_t)i * kFvMaxFaces + q, sb = (size_t)i * kFvMaxFaces + (q + 1) % k;
+                const int a = h.nb[sa], b = h.nb[sb];
                 if (a < 0 || b < 0) continue;
-                const double a0 = bx[a] - bx[i], a1 = by[a] - by[i], b0 = bx[b] - bx[i], b1 = by[b] - by[i];
+                const double a0 = bx[a] + fsx[sa] - bx[i], a1 = by[a] + fsy[sa] - by[i];
+                const double b0 = bx[b] + fsx[sb] - bx[i], b1 = by[b] + fsy[sb] - by[i];
                 const double mxa = std::max(std::max(fabs(a0), fabs(a1)), std::max(fabs(b0), fabs(b1)));
                 const double dt = a0 * b1 - a1 * b0;
                 if (fabs(dt) <= 1e-12 * mxa * mxa) continue;

@@ -75,13 +75,14 @@ def _magnitude(om, f, N, L, order, fvo, walls=None):
     G = np.zeros_like(af)
     if order == 2:
         for i in range(n):
-            st = om.central_stencil(i)
-            A = np.array([om.bary[j] - om.bary[i] for j in st])
+            sts = om.central_stencil_shifted(i)
+            st = [j for j, _ in sts]
+            A = np.array([om.bary[j] + s - om.bary[i] for j, s in sts])
             R = np.abs(np.linalg.inv(A.T @ A) @ A.T)
             gc = (R @ (af[st] + af[i])).max(axis=0)
             gs = []
-            for a, b in om.sectors(i):
-                Rs = np.abs(np.linalg.inv(np.array([om.bary[a] - om.bary[i], om.bary[b] - om.bary[i]])))
+            for a, sa, b, sb in om.sectors_shifted(i):
+                Rs = np.abs(np.linalg.inv(np.array([om.bary[a] + sa - om.bary[i], om.bary[b] + sb - om.bary[i]])))
                 gs.append((Rs @ np.stack([af[a] + af[i], af[b] + af[i]])).max(axis=0))
             cand = [gc] + gs
             if gs:
@@ -92,7 +93,8 @@ def _magnitude(om, f, N, L, order, fvo, walls=None):
         for q, (j, ln, nx, ny, mx, my) in enumerate(fl):
             avn = ln * (np.abs(v1 * nx) + np.abs(v2 * ny))
             fl_ = af[i] + G[i] * (abs(mx - om.bary[i, 0]) + abs(my - om.bary[i, 1]))
-            fr_ = fl_ if j < 0 else af[j] + G[j] * (abs(mx - om.bary[j, 0]) + abs(my - om.bary[j, 1]))
+            sh = om.face_shift[i][q]
+            fr_ = fl_ if j < 0 else af[j] + G[j] * (abs(mx - sh[0] - om.bary[j, 0]) + abs(my - sh[1] - om.bary[j, 1]))
             wall = None if (walls is None or j >= 0) else walls.get(frozenset(om.face_vertices[i][q]))
             if wall is not None:
                 vn = v1 * nx + v2 * ny
@@ -310,3 +312,113 @@ def test_walls_imex_step_and_limits(bz, fvo):
     inner = next((om.face_vertices[i][q] for i, fl in enumerate(om.faces) for q, fc in enumerate(fl) if fc[0] >= 0))
     with pytest.raises(bz.BzError):
         m.set_walls([inner], [(1.0, 0.0, 0.0)])
+
+
+def _periodic(n_side, seed=1006):
+    return workloads.periodic_triangulation(n_side, 10.0, 10.0, seed=seed)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("n_side,per", [(8, (10.0, 10.0)), (8, (10.0, 0.0)), (8, (0.0, 10.0)), (3, (10.0, 10.0))])
+def test_periodic_fp64_matches_oracle(bz, fvo, order, n_side, per):
+    """Periodic in both directions, in one direction (the other boundary
+    transmissive) and a torus 3 cells wide, where a stencil holds several
+    copies of one cell; the isentropic-vortex states."""
+    N, Lv = 8, 8.0
+    pts, tri = _periodic(n_side)
+    om = fvo.Mesh(pts, tri, periodic=per)
+    f, _, _ = workloads.vortex_states(om.bary, N, Lv)
+    m = bz.Mesh(pts, tri, order=order, periodic=per)
+    nb = sum(1 for fl in om.faces for fc in fl if fc[0] < 0)
+    assert m.n_faces_boundary == nb and 3 * m.n_cells == 2 * m.n_faces_interior + nb
+    if per == (10.0, 10.0):
+        assert nb == 0
+    Lr = bz.transport_residual(m, bz.Grid(2, N, Lv), to_dev(f, "fp64"), precision="fp64")
+    bz.check()
+    want = fvo.transport_residual(om, f, N, Lv, order=order)
+    _check(Lr.cpu().numpy(), want, om, f, N, Lv, order, fvo, U64, ETA64)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_periodic_fp32_within_bound(bz, fvo, order):
+    N, Lv = 16, 8.0
+    pts, tri = _periodic(12, seed=11)
+    om = fvo.Mesh(pts, tri, periodic=(10.0, 10.0))
+    f, _, _ = workloads.vortex_states(om.bary, N, Lv, t=3.3)
+    fin = as_input(f, "fp32")
+    m = bz.Mesh(pts, tri, order=order, periodic=(10.0, 10.0))
+    Lr = bz.transport_residual(m, bz.Grid(2, N, Lv), to_dev(f, "fp32"), precision="fp32")
+    bz.check()
+    want = fvo.transport_residual(om, fin, N, Lv, order=order)
+    _check(Lr.double().cpu().numpy(), want, om, fin, N, Lv, order, fvo, U32, ETA32)
+
+
+def test_periodic_conserves_mass_at_scale(bz, fvo):
+    """On the torus no mass leaves the box: sum_i |P_i| L_ik vanishes for every
+    velocity up to rounding, bounded by the same sums of magnitudes as one
+    element (64 x 64 periodic triangulation, 8192 cells, 30^2 grid, both
+    precisions); every cell against the oracle at that size."""
+    N, Lv = 30, 10.0
+    pts, tri = _periodic(64)
+    m = bz.Mesh(pts, tri, order=2, periodic=(10.0, 10.0))
+    om = fvo.Mesh(pts, tri, periodic=(10.0, 10.0))
+    f, _, _ = workloads.vortex_states(om.bary, N, Lv)
+    for precision, u, eta in (("fp64", U64, ETA64), ("fp32", U32, ETA32)):
+        fin = as_input(f, precision)
+        Lr = bz.transport_residual(m, bz.Grid(2, N, Lv), to_dev(f, precision), precision=precision)
+        bz.check()
+        got = Lr.double().cpu().numpy()
+        bound = 64 * (u * _magnitude(om, fin, N, Lv, 2, fvo) + eta * _magnitude(om, np.ones_like(fin), N, Lv, 2, fvo))
+        assert (np.abs(om.area @ got) <= om.area @ bound).all()
+        _check(got, fvo.transport_residual(om, fin, N, Lv, order=2), om, fin, N, Lv, 2, fvo, u, eta)
+
+
+def test_periodic_imex_step_fv_matches_oracle(bz, fvo):
+    import oracle
+    N, Lv, dt, eps = 8, 8.0, 2e-3, 1e-3
+    pts, tri = _periodic(6)
+    om = fvo.Mesh(pts, tri, periodic=(10.0, 10.0))
+    f, _, _ = workloads.vortex_states(om.bary, N, Lv)
+    k = oracle.Kernel(2, N, Lv, 0.0)
+    Lres = np.zeros((3,) + f.shape)
+    for l in range(2):
+        _, F, _, _ = k.imex_step(f, dt, eps, Lres=Lres, stages=True)
+        Lres[l] = fvo.transport_residual(om, F[l], N, Lv, order=2)
+    want = k.imex_step(f, dt, eps, Lres=Lres)
+    m = bz.Mesh(pts, tri, order=2, periodic=(10.0, 10.0))
+    got = bz.imex_step_fv(bz.Modes(bz.Grid(2, N, Lv), 0.0), m, to_dev(f, "fp64"), dt, eps, precision="fp64")
+    bz.check()
+    assert relerr(got.cpu().numpy(), want) < TOL64
+
+
+def test_periodic_mesh_errors(bz):
+    pts, tri = _periodic(4)
+    lib = bz.load()
+    out = ctypes.c_void_p()
+    xy = np.ascontiguousarray(pts, dtype=np.float64)
+    ptr = np.ascontiguousarray(np.arange(0, 3 * len(tri) + 1, 3), dtype=np.int64)
+    vtx = np.ascontiguousarray(np.asarray(tri, dtype=np.int64).ravel())
+    args = (len(pts), xy.ctypes.data_as(ctypes.c_void_p), len(tri), ptr.ctypes.data_as(ctypes.c_void_p),
+            vtx.ctypes.data_as(ctypes.c_void_p), 2)
+    for Lx, Ly in ((-1.0, 10.0), (10.0, float("inf")), (float("nan"), 0.0)):
+        assert lib.build_fv_mesh_periodic(*args, Lx, Ly, ctypes.byref(out)) == bz.EINVAL
+    p2, t2 = _periodic(2)          # 2 cells wide: two edges join the same pair of periodic vertices
+    with pytest.raises(bz.BzError):
+        bz.Mesh(p2, t2, order=2, periodic=(10.0, 10.0))
+    m = bz.Mesh(pts, tri, order=2, periodic=(0.0, 0.0))      # no period: the plain mesh
+    assert m.n_faces_boundary == 16
+
+
+def test_isentropic_vortex_second_order(bz):
+    """Sec. 4.1, Table conv_0: the fluid limit (eps = 1e-6) of the full scheme
+    on periodic triangulations with h = 0.39, 0.20, 0.13 (the paper's three
+    coarsest sizes), 30^2 velocities on [-10,10]^2, t_f = 0.1: the density
+    and temperature errors fall at second order or better, as in the paper's
+    order-2 column (2.5, 2.1 for the density in L1)."""
+    from paper_2103_14890_gb300 import convergence
+    modes = bz.Modes(bz.Grid(2, 30, 10.0), 0.0)
+    rows = [convergence.vortex_run(n, modes=modes) for n in (18, 36, 54)]
+    for key in ("rho_L1", "rho_L2", "T_L1", "T_L2"):
+        o = convergence.orders(rows, key)
+        assert min(o) > 1.7, (key, o, rows)
+    assert rows[0]["rho_L1"] < 0.1

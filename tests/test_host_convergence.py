@@ -1,0 +1,34 @@
+"""Host arithmetic of the vortex study (moments, geometry, time step) against
+closed forms; the march itself runs on the GPU (test_gpu_transport.py)."""
+import math
+
+import numpy as np
+
+from paper_2103_14890_gb300 import convergence, workloads
+
+
+def test_moments_of_vortex_maxwellians():
+    """The sampled Maxwellians of the vortex carry its density and temperature
+    (rectangle rule on a periodic-like grid: exponentially accurate for a
+    Gaussian well inside [-10,10]^2)."""
+    pts, tri = workloads.periodic_triangulation(6)
+    _, bary, _ = convergence.mesh_geometry(pts, tri)
+    f, rho, T = workloads.vortex_states(bary, 30, 10.0)
+    r, t = convergence.moments(f, 30, 10.0)
+    assert np.abs(r - rho).max() < 1e-10 and np.abs(t - T).max() < 1e-10
+    assert T.min() < 0.9 and rho.min() < 0.9         # the vortex core is resolved
+
+
+def test_geometry_and_time_step():
+    pts, tri = workloads.periodic_triangulation(10, jitter=0.0)
+    area, bary, per = convergence.mesh_geometry(pts, tri)
+    assert abs(area.sum() - 100.0) < 1e-9                      # the box [0,10]^2
+    assert np.allclose(per, 1.0 * (2 + math.sqrt(2)))          # right triangles with legs 1
+    assert (bary > 0).all() and (bary < 10).all()
+    dt = convergence.time_step(area, per, 30, 10.0, 0.4)
+    assert abs(dt - 0.4 * (0.5 / (2 + math.sqrt(2))) / (10 * math.sqrt(2))) < 1e-15
+
+
+def test_orders():
+    rows = [{"h": 0.4, "e": 1.6e-2}, {"h": 0.2, "e": 4e-3}, {"h": 0.1, "e": 1e-3}]
+    assert np.allclose(convergence.orders(rows, "e"), [2.0, 2.0])

@@ -240,3 +240,16 @@ def test_periodic_mesh_equals_the_tiled_plane(fv):
         assert np.abs(Lp - mid).max() < 1e-12 * np.abs(mid).max()
         # no boundary: the fluxes cancel in the sum
         assert abs((m.area[:, None] * Lp).sum()) < 1e-12 * (m.area[:, None] * np.abs(Lp)).sum()
+
+
+def test_ambiguous_pairing_is_refused(fv):
+    """A period two cells wide makes two edges join the same pair of periodic
+    vertices in the same direction, and the same edge given twice (duplicated
+    cell) does too: the face pairing is undefined and the mesh is refused."""
+    p2, t2 = workloads.periodic_triangulation(2, 10.0, 10.0, seed=3)
+    with pytest.raises(ValueError):
+        fv.Mesh(p2, t2, periodic=(10.0, 10.0))
+    fv.Mesh(p2, t2)                              # without the periods it is a plain mesh
+    pts = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    with pytest.raises(ValueError):
+        fv.Mesh(pts, [[0, 1, 2], [0, 1, 2]])
