@@ -174,9 +174,10 @@ int collide_batch_host(const bz_modes *m, int precision, int flags, const void *
 
 /* imex_stage_local -- stage l (1-based) of the penalised IMEX Runge-Kutta step
  * of Sec. 3.4 (eq. Bref2: Q = G_P + Q_BGK with G_P explicit and the BGK
- * operator nu (M - f), nu = rho, implicit), cell by cell:
+ * operator nu (M - f) implicit; nu = rho for BZ_BGK, nu = c rho for
+ * BZ_BOLTZMANN with c set by bz_modes_set_penalty, 1 by default), cell by cell:
  *   R_l = f^n + dt sum_{m<l} [ At_lm (G_m/eps - L_m) + A_lm P_m/eps ]
- *   U_l = moments(R_l), nu_l = rho_l, M_l = Maxwellian(U_l)       (FP64)
+ *   U_l = moments(R_l), nu_l = (c) rho_l, M_l = Maxwellian(U_l)   (FP64)
  *   F_l = (R_l + dt A_ll (nu_l/eps) M_l) / (1 + dt A_ll nu_l/eps)
  *   P_l = nu_l (M_l - F_l),  G_l = Q(F_l) - P_l  (G_l = 0 for BZ_BGK or when no
  *   later stage uses it).
@@ -196,6 +197,20 @@ int imex_stage_local(const bz_modes *m, int scheme, int stage, int model, double
                      double eps, const void *f_n, void *F, void *G, void *P,
                      const void *L_res, int64_t n_cells, int precision, int flags,
                      void *stream);
+
+/* bz_modes_set_penalty -- the penalty rate of the Boltzmann model in the IMEX
+ * stages, nu = c rho (Sec. 3.4, eq. Bref2 leaves nu open; the default c = 1).
+ * Near the fluid limit the explicit part G_P / eps acts on the distance to
+ * equilibrium, and with ARS(2,2,2) that distance is multiplied per step by
+ * g(K) = ((1 - d) K^2 + (d - 1 + gamma) K) / gamma, K = 1 + lambda / nu over
+ * the spectrum lambda of the linearised Q (gamma = 1 - 1/sqrt 2, d = 1 -
+ * 1/(2 gamma)); |g| > 1 for complex K near 0.41, which the spectral Q of
+ * Maxwell molecules reaches with c = 1 (eigenvalues down to about -1.03 rho
+ * with imaginary parts up to 0.24 rho).  c = 3 keeps K in [0.65, 1] and the
+ * step stable.  The BGK model keeps nu = rho (its collision frequency).
+ * Changing c drops the CUDA graphs captured by imex_step for these modes.
+ * Errors: BZ_EINVAL (NULL modes, c not finite or <= 0). */
+int bz_modes_set_penalty(bz_modes *m, double c);
 
 /* imex_step -- all stages of one IMEX step (the schemes are stiffly accurate,
  * so f^{n+1} is the last stage value): f_out = step(f_n).  Stage buffers are

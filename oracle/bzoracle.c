@@ -165,6 +165,7 @@ static int default_nodes(const orc_grid *g) {
  * the same number because F(a,b) is formed symmetrically. */
 int orc_kernel_init(orc_kernel *k, const orc_grid *g, double gamma, double b0, int nq) {
     memset(k, 0, sizeof *k);
+    k->penalty = 1.0;
     k->g = *g;
     k->gamma = gamma;
     k->b0 = (b0 > 0) ? b0 : (g->dim == 2 ? 1.0 / (2.0 * M_PI) : 1.0 / (4.0 * M_PI));
@@ -239,6 +240,7 @@ static double carleman_phi(double xi) {
 int orc_fast_kernel_init(orc_kernel *k, const orc_grid *g, double b0, int ndirs) {
     if (!k || !g || g->dim != 2 || ndirs < 1) return -1;
     memset(k, 0, sizeof *k);
+    k->penalty = 1.0;
     k->g = *g;
     k->gamma = 0.0;
     k->b0 = (b0 > 0) ? b0 : 1.0 / (2.0 * M_PI);
@@ -586,10 +588,12 @@ static int tableau(int scheme, int *s, double At[MAXS][MAXS], double A[MAXS][MAX
 }
 
 /* Penalised IMEX step of Sec. 3.4 (eq. Bref2 and the scheme after it) for one
- * cell, with the cell-centred BGK operator nu (M - F), nu = rho, implicit and
- * G = Q - nu (M - F) explicit.  Stage l:
+ * cell, with the cell-centred BGK operator nu (M - F) implicit and
+ * G = Q - nu (M - F) explicit.  The paper leaves the penalty rate nu open:
+ * nu = rho for the BGK model (its collision frequency) and nu = c rho for the
+ * Boltzmann model, c = k->penalty (1 unless set).  Stage l:
  *   R_l = f^n + dt sum_{m<l} [ At_lm (G_m/eps - L_m) + A_lm P_m/eps ]
- *   U_l = moments(R_l), nu_l = rho_l, M_l = M[U_l]
+ *   U_l = moments(R_l), nu_l = rho_l (times c for Boltzmann), M_l = M[U_l]
  *   F_l = (R_l + dt A_ll (nu_l/eps) M_l) / (1 + dt A_ll nu_l/eps)
  *   P_l = nu_l (M_l - F_l),   G_l = Q(F_l) - P_l  (Boltzmann) or 0 (BGK).
  * G enters with a plus sign, consistent with eq. Bref2.  The stage moments are
@@ -616,7 +620,7 @@ static void imex_one(const orc_kernel *k, int s, double At[MAXS][MAXS], double A
         double U[5];
         orc_moments(g, R, U);
         orc_maxwellian(g, U, Mx);
-        double nu = U[0];
+        double nu = (model == 0) ? k->penalty * U[0] : U[0];
         double c = dt * A[l][l] * nu / eps;
         (void)d;
         for (int64_t j = 0; j < nv; ++j) {

@@ -59,6 +59,7 @@ typedef struct {
     int ndirs;        /* A, number of collision directions; 0 for eq. KM */
     double *alpha;    /* [ndirs][nm]: alpha_p(k)  */
     double *alphap;   /* [ndirs][nm]: alpha'_p(k) */
+    double penalty;   /* c of the Boltzmann model's penalty rate nu = c rho (1 after init) */
 } orc_kernel;
 
 int    orc_grid_init(orc_grid *g, int dim, int N, double L);

@@ -31,7 +31,7 @@ class _Grid(ctypes.Structure):
 class _Kernel(ctypes.Structure):
     _fields_ = [("g", _Grid), ("gamma", _d), ("b0", _d), ("nq", _i), ("arows", _i),
                 ("amax2", _i), ("F", ctypes.POINTER(_d)), ("ndirs", _i),
-                ("alpha", ctypes.POINTER(_d)), ("alphap", ctypes.POINTER(_d))]
+                ("alpha", ctypes.POINTER(_d)), ("alphap", ctypes.POINTER(_d)), ("penalty", _d)]
 
 
 def build(force=False):
@@ -221,9 +221,11 @@ class Kernel:
         return out.reshape((self.N,) * self.dim)
 
     def imex_step(self, f_n, dt, eps, scheme="ars222", model="boltzmann", Lres=None,
-                  conserve=False, stages=False):
+                  conserve=False, stages=False, penalty=1.0):
         """One penalised IMEX step.  f_n: (ncells, N^d).  Lres: (stages, ncells, N^d)
-        or None.  With stages=True also returns (F, G, P) per stage."""
+        or None.  With stages=True also returns (F, G, P) per stage.  penalty:
+        c of the Boltzmann model's penalty rate nu = c rho."""
+        self._k.penalty = float(penalty)
         f = np.ascontiguousarray(np.asarray(f_n, dtype=np.float64).reshape(-1, self.nv))
         nc = f.shape[0]
         ns = STAGES[scheme]

@@ -62,6 +62,7 @@ def load(path=None):
             "bz_last_error": ([], ctypes.c_char_p),
             "bz_modes_info": ([c_p, ctypes.POINTER(c_i64)], c_i),
             "bz_modes_beta": ([c_p, c_p], c_i),
+            "bz_modes_set_penalty": ([c_p, c_d], c_i),
             "bz_grid_destroy": ([c_p], None),
             "bz_modes_destroy": ([c_p], None),
             "bz_profile": ([c_i], c_i),
@@ -147,6 +148,7 @@ class Modes:
         self._h = h
         self.grid = grid              # keep the grid alive
         self.gamma = gamma
+        self.penalty = 1.0
         fi = (ctypes.c_int64 * 4)()
         _check(load().bz_fast_info(h, fi))
         self.method, self.ndirs, self.pad, self.fast_cells = list(fi)
@@ -159,6 +161,12 @@ class Modes:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.bz_modes_destroy(self._h)
             self._h = None
+
+    def set_penalty(self, c):
+        """Penalty rate nu = c rho of the Boltzmann model in the IMEX stages
+        (bz_modes_set_penalty)."""
+        _check(load().bz_modes_set_penalty(self._h, float(c)))
+        self.penalty = float(c)
 
     def beta_table(self):
         import numpy as np

@@ -380,6 +380,7 @@ int run_stage(const bz_modes *m, const Tableau &t, int l, int model, double dt, 
     c.all = t.A[l][l];
     c.dt = dt;
     c.eps = eps;
+    c.nuf = (model == BZ_BOLTZMANN) ? m->penalty : 1.0;
     const int64_t stride = n * v.nv;
     const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
     cudaError_t e;
@@ -977,6 +978,16 @@ int bz_fast_info(const bz_modes *m, int64_t out[4]) {
     out[1] = m->method == 1 ? m->ndirs : 0;
     out[2] = m->method == 1 ? fast_pad_length(m->g->v.N) : 0;
     out[3] = m->method == 1 ? fast_cells_per_cta(m->g->v.N) : 0;
+    return BZ_OK;
+}
+
+int bz_modes_set_penalty(bz_modes *m, double c) {
+    if (!m) return fail(BZ_EINVAL, "bz_modes_set_penalty: NULL modes");
+    if (!(c > 0.0) || !std::isfinite(c)) return fail(BZ_EINVAL, "bz_modes_set_penalty: c must be finite and > 0");
+    if (c != m->penalty) {
+        purge_graphs(m);          // captured steps hold the old rate
+        m->penalty = c;
+    }
     return BZ_OK;
 }
 

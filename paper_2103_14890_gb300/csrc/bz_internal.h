@@ -72,6 +72,7 @@ struct bz_modes {
     int64_t pairs_sym;   // unordered pairs per cell (algorithmic unit)
     int tile_dft;        // 1: the tile FFT kernels of k_dft32.cu serve this grid
     double scale;        // s^(d + gamma)
+    double penalty;      // c of the Boltzmann model's penalty rate nu = c rho (IMEX stages)
     // fast spectral (Carleman) form, k_fast.cu: method 1 replaces the mode sum
     // of eq. CF1 by nconv + 1 FFT convolutions with the direction factors
     // [(nconv + 1)][M][M] complex: (c_p alpha_p + i alpha'_p)(k), then
@@ -219,6 +220,7 @@ struct StageCoef {
     double at[5], a[5];        // At[l][m], A[l][m] for m < l
     double all;                // A[l][l]
     double dt, eps;
+    double nuf;                // penalty rate nu = nuf * rho
 };
 cudaError_t launch_imex_stage_f64(const GridView &g, const StageCoef &c, const double *fn,
                                   double *F, const double *G, double *P, const double *Lres,

@@ -215,6 +215,7 @@ int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **o
     bz_modes *m = (bz_modes *)calloc(1, sizeof(bz_modes));
     if (!m) return fail(BZ_ENOMEM, "build_kernel_modes: host allocation");
     m->g = g;
+    m->penalty = 1.0;
     m->gamma = gamma;
     m->b0 = (b0 > 0.0) ? b0 : (v.dim == 2 ? 1.0 / (2.0 * M_PI) : 1.0 / (4.0 * M_PI));
     m->nq = nq > 0 ? nq : auto_nodes(v);
@@ -282,6 +283,7 @@ int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out) {
     bz_modes *m = (bz_modes *)calloc(1, sizeof(bz_modes));
     if (!m) return fail(BZ_ENOMEM, "build_fast_modes: host allocation");
     m->g = g;
+    m->penalty = 1.0;
     m->gamma = 0.0;
     m->b0 = (b0 > 0.0) ? b0 : 1.0 / (2.0 * M_PI);
     m->scale = pow(v.s, 2.0);

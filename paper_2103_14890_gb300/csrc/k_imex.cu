@@ -5,8 +5,9 @@
 //   R_l = f^n + dt sum_{m<l} [ At_lm (G_m/eps - L_m) + A_lm P_m/eps ]
 //   U_l = (rho, rho u, E) = discrete moments of R_l                (FP64)
 //   M_l = rho (2 pi theta)^(-d/2) exp(-|v - u|^2 / (2 theta))     (parameters FP64)
-//   F_l = (R_l + c M_l) / (1 + c),   c = dt A_ll rho / eps
-//   P_l = rho (M_l - F_l)
+//   F_l = (R_l + c M_l) / (1 + c),   c = dt A_ll nu / eps
+//   P_l = nu (M_l - F_l),   nu = nuf rho (nuf = 1 for BGK, the modes' penalty
+//   factor for the Boltzmann model)
 // G_l = Q(F_l) - P_l is formed by the inverse-DFT epilogue of the collision
 // chain that follows this kernel.
 #include "bz_device.cuh"
@@ -64,8 +65,9 @@ __global__ void __launch_bounds__(kThreads) imex_stage_kernel(GridView g, StageC
     const double theta = (2.0 * E / rho - u2) / g.dim;
     const double pref = rho * pow(2.0 * M_PI * theta, -0.5 * g.dim);
     const double inv2t = 0.5 / theta;
-    const double cc = c.dt * c.all * rho / c.eps;
-    const T cT = (T)cc, denom = (T)(1.0 / (1.0 + cc)), rhoT = (T)rho;
+    const double nu = c.nuf * rho;
+    const double cc = c.dt * c.all * nu / c.eps;
+    const T cT = (T)cc, denom = (T)(1.0 / (1.0 + cc)), nuT = (T)nu;
     T *Fo = F + base;
     T *Po = P + (int64_t)c.stage * stride + base;
     for (int64_t i = threadIdx.x; i < g.nv; i += blockDim.x) {
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(kThreads) imex_stage_kernel(GridView g, StageC
             Mx = (T)pref * expf((float)(-r2 * inv2t));   // exponent in FP64, exp in the state precision
         T Fi = (R[i] + cT * Mx) * denom;
         Fo[i] = Fi;
-        Po[i] = rhoT * (Mx - Fi);
+        Po[i] = nuT * (Mx - Fi);
     }
 }
 
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kStageCells * 32) imex_stage2d_kernel(GridView
                                                                        const T *__restrict__ Lres, int64_t stride,
                                                                        int64_t n) {
     __shared__ double part[kStageCells][4][33];   // per-lane moment partials (pitch 33: no bank conflicts)
-    __shared__ double par[kStageCells][8];        // rho, u1, u2, inv2t, pref, c, 1/(1+c)
+    __shared__ double par[kStageCells][8];        // nu, u1, u2, inv2t, pref, c, 1/(1+c)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t cell = (int64_t)blockIdx.x * kStageCells + wib;
     const bool live = cell < n;
@@ -181,8 +183,8 @@ __global__ void __launch_bounds__(kStageCells * 32) imex_stage2d_kernel(GridView
         const double u1 = w * part[cc][1][32] / rho, u2 = w * part[cc][2][32] / rho;
         const double E = 0.5 * w * part[cc][3][32];
         const double theta = (2.0 * E / rho - (u1 * u1 + u2 * u2)) / 2.0;
-        const double cst = c.dt * c.all * rho / c.eps;
-        par[cc][0] = rho;
+        const double cst = c.dt * c.all * c.nuf * rho / c.eps;
+        par[cc][0] = c.nuf * rho;          // penalty rate nu
         par[cc][1] = u1;
         par[cc][2] = u2;
         par[cc][3] = 0.5 / theta;
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(kStageCells * 32) imex_stage2d_kernel(GridView
     const T i2t = (T)par[wib][3];
     const T fcol = (T)par[wib][4] * exp(-d2 * d2 * i2t);
     const T frow_l = exp(-d1 * d1 * i2t);
-    const T cT = (T)par[wib][5], denom = (T)par[wib][6], rhoT = (T)par[wib][0];
+    const T cT = (T)par[wib][5], denom = (T)par[wib][6], nuT = (T)par[wib][0];
     T *Fo = F + base;
     T *Po = P + (int64_t)c.stage * stride + base;
 #pragma unroll
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(kStageCells * 32) imex_stage2d_kernel(GridView
         const T Fi = (R[j] + cT * Mx) * denom;
         if (on) {
             Fo[j * N] = Fi;
-            Po[j * N] = rhoT * (Mx - Fi);
+            Po[j * N] = nuT * (Mx - Fi);
         }
     }
 }

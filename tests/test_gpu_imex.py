@@ -111,3 +111,45 @@ def test_sod_mesh_step_sampled(bz):
     k = oracle.Kernel(2, N, L, 1.0)
     want = k.imex_step(as_input(f[idx], "fp32"), dt, 5e-3)
     assert relerr(got[idx], want) < 1e-6
+
+
+def test_penalty_factor_matches_oracle_and_drops_graphs(bz):
+    """nu = c rho with c = 3 for the Boltzmann model (bz_modes_set_penalty):
+    FP64 stages and step against the oracle with the same c; a step captured in
+    a CUDA graph before the change is not replayed with the old rate; the BGK
+    model ignores c."""
+    import oracle
+    import torch
+    N, L, n = 16, 8.0, 24
+    f = workloads.bi_maxwellian(n, 2, N, L, seed=35, noise=0.05)
+    k = oracle.Kernel(2, N, L, 0.0)
+    dt, eps = 0.01, 2e-3
+    m = bz.Modes(bz.Grid(2, N, L), 0.0)
+    fd = to_dev(f, "fp64")
+    s = torch.cuda.Stream()
+    out = torch.empty_like(fd)
+    scale = np.abs(f).max()
+    for c in (1.0, 3.0, 1.0):
+        m.set_penalty(c)
+        want = k.imex_step(f, dt, eps, conserve=True, penalty=c)
+        with torch.cuda.stream(s):
+            for _ in range(2):                       # capture, then a replay
+                out.fill_(float("nan"))
+                bz.imex_step(m, fd, dt, eps, f_out=out, conserve=True, precision="fp64", stream=s)
+                bz.check(s)
+                assert np.abs(out.cpu().numpy() - want).max() < 1e-12 * (1 + dt * c / eps) * scale, c
+    m.set_penalty(3.0)
+    _, Fr, Gr, Pr = k.imex_step(f, dt, eps, penalty=3.0, stages=True)
+    F = torch.zeros((3, n, N * N), dtype=torch.float64, device="cuda")
+    G = torch.zeros_like(F)
+    P = torch.zeros_like(F)
+    for l in (1, 2, 3):
+        bz.imex_stage_local(m, l, fd, F, G, P, dt, eps, precision="fp64")
+    bz.check()
+    for a, b in ((F, Fr), (G, Gr), (P, Pr)):
+        assert np.abs(a.cpu().numpy() - b).max() < 1e-12 * (1 + dt * 3 / eps) * max(scale, np.abs(b).max())
+    bgk = bz.imex_step(m, fd, dt, eps, model="bgk", precision="fp64").cpu().numpy()
+    assert np.abs(bgk - k.imex_step(f, dt, eps, model="bgk")).max() < 1e-12 * (1 + dt / eps) * scale
+    for bad in (0.0, -1.0, float("inf"), float("nan")):
+        with pytest.raises(bz.BzError):
+            m.set_penalty(bad)

@@ -29,6 +29,12 @@ def test_geometry_and_time_step():
     assert abs(dt - 0.4 * (0.5 / (2 + math.sqrt(2))) / (10 * math.sqrt(2))) < 1e-15
 
 
-def test_orders():
+def test_orders_and_errors():
     rows = [{"h": 0.4, "e": 1.6e-2}, {"h": 0.2, "e": 4e-3}, {"h": 0.1, "e": 1e-3}]
     assert np.allclose(convergence.orders(rows, "e"), [2.0, 2.0])
+    rows = [{"dt": 1e-3, "e": 8e-6}, {"dt": 5e-4, "e": 1e-6}]
+    assert np.allclose(convergence.orders(rows, "e", by="dt"), [3.0])
+    e = convergence.errors(np.array([2.0, 3.0]), np.array([1.0, 1.5]), np.array([1.0, 1.0]),
+                           np.array([1.0, 1.0]), np.array([0.5, 1.0]))
+    assert np.isclose(e["rho_L1"], 1.5) and np.isclose(e["rho_L2"], np.sqrt(0.75))
+    assert np.isclose(e["T_L1"], 1.0) and np.isclose(e["T_L2"], np.sqrt(0.5))
