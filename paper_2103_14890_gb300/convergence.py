@@ -1,9 +1,10 @@
 """Isentropic-vortex convergence studies of Sec. 4.1 (Tables conv_0,
 conv_1e-3, conv_1e-2 and conv_1): the full scheme of Sec. 3.4 (CWENO
 transport of Sec. 3.2 with the penalised IMEX stages and the spectral
-collision operator) on periodic triangulations of the box [0,10]^2, 30^2
-velocities on [-10,10]^2, every time step on the device through imex_step_fv;
-the host forms only the moments of the final states and the norms.
+collision operator) on periodic triangulations or Voronoi tessellations of
+the box [0,10]^2, 30^2 velocities on [-10,10]^2, every time step on the
+device through imex_step_fv; the host forms only the moments of the final
+states and the norms.
 
 - Space-time study (eps -> 0, Table conv_0): errors against the exact
   solution of the Euler equations, the vortex advected by the mean flow
@@ -35,13 +36,29 @@ BOX = 10.0
 
 
 def mesh_geometry(pts, cells):
-    """Areas, barycentres and perimeters of triangles (n, 3) given
-    counter-clockwise or clockwise."""
-    P = np.asarray(pts, dtype=np.float64)[np.asarray(cells)]
-    e1, e2 = P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]
-    area = 0.5 * np.abs(e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
-    per = sum(np.hypot(*(P[:, (q + 1) % 3] - P[:, q]).T) for q in range(3))
-    return area, P.mean(axis=1), per
+    """Areas, barycentres and perimeters of polygons given counter-clockwise
+    or clockwise (an (n, k) array or a list of vertex lists)."""
+    pts = np.asarray(pts, dtype=np.float64)
+    area, bary, per = np.zeros(len(cells)), np.zeros((len(cells), 2)), np.zeros(len(cells))
+    for i, c in enumerate(cells):
+        P = pts[list(c)] - pts[c[0]]
+        x, y = P[:, 0], P[:, 1]
+        xn, yn = np.roll(x, -1), np.roll(y, -1)
+        cr = x * yn - xn * y
+        a = 0.5 * cr.sum()
+        area[i] = abs(a)
+        bary[i] = pts[c[0]] + np.array([((x + xn) * cr).sum(), ((y + yn) * cr).sum()]) / (6.0 * a)
+        per[i] = np.hypot(xn - x, yn - y).sum()
+    return area, bary, per
+
+
+def vortex_mesh(n, kind="tri", seed=None):
+    """The periodic meshes of the study: kind "tri", an n x n jittered
+    triangulation (2 n^2 cells); kind "voronoi", a Voronoi tessellation with
+    n cells (the polygonal meshes of Table conv_0)."""
+    if kind == "tri":
+        return workloads.periodic_triangulation(n, BOX, BOX, seed=1006 if seed is None else seed)
+    return workloads.periodic_voronoi(n, BOX, BOX, seed=1007 if seed is None else seed)
 
 
 def moments(f, N, L):
@@ -73,15 +90,15 @@ def errors(area, rho, T, rho_ref, T_ref):
             "T_L1": float((area * np.abs(dT)).sum()), "T_L2": float(np.sqrt((area * dT * dT).sum()))}
 
 
-def vortex_march(n_side, N=30, L=10.0, t_final=0.1, eps=1e-8, model="bgk", steps=None, cfl=0.4, order=2,
-                 precision="fp64", scheme="ars222", seed=1006, modes=None, conserve=True, penalty=1.0):
-    """March the vortex to t_final on the periodic n_side x n_side
-    triangulation with `steps` steps (default: the CFL step).  Returns
-    (moments (rho, T) of the final state, area, barycentres, steps)."""
+def vortex_march(n, N=30, L=10.0, t_final=0.1, eps=1e-8, model="bgk", steps=None, cfl=0.4, order=2,
+                 precision="fp64", scheme="ars222", seed=None, modes=None, conserve=True, penalty=1.0, mesh="tri"):
+    """March the vortex to t_final on the periodic mesh vortex_mesh(n, mesh)
+    with `steps` steps (default: the CFL step).  Returns (moments (rho, T) of
+    the final state, area, barycentres, steps)."""
     import torch
-    pts, tri = workloads.periodic_triangulation(n_side, BOX, BOX, seed=seed)
+    pts, tri = vortex_mesh(n, mesh, seed)
     area, bary, per = mesh_geometry(pts, tri)
-    mesh = bz.Mesh(pts, tri, order=order, periodic=(BOX, BOX))
+    fvm = bz.Mesh(pts, tri, order=order, periodic=(BOX, BOX))
     if modes is None:
         modes = bz.Modes(bz.Grid(2, N, L), 0.0)
     modes.set_penalty(penalty)
@@ -93,28 +110,30 @@ def vortex_march(n_side, N=30, L=10.0, t_final=0.1, eps=1e-8, model="bgk", steps
     a = torch.from_numpy(f0).to(device="cuda", dtype=ty).contiguous()
     b = torch.empty_like(a)
     for _ in range(steps):
-        bz.imex_step_fv(modes, mesh, a, dt, eps, f_out=b, scheme=scheme, model=model, precision=precision,
+        bz.imex_step_fv(modes, fvm, a, dt, eps, f_out=b, scheme=scheme, model=model, precision=precision,
                         conserve=conserve)
         a, b = b, a
     bz.check()
     return moments(a.double().cpu().numpy(), N, L), area, bary, steps
 
 
-def space_study(sides=(18, 36, 54, 72), N=30, L=10.0, t_final=0.1, eps=1e-8, model="bgk", **kw):
-    """Table conv_0: one row per mesh, errors against the exact vortex."""
+def space_study(sizes=(18, 36, 54, 72), N=30, L=10.0, t_final=0.1, eps=1e-8, model="bgk", **kw):
+    """Table conv_0: one row per mesh (vortex_mesh(n, kw["mesh"]) for n in
+    sizes), errors against the exact vortex."""
     rows = []
-    for n in sides:
+    for n in sizes:
         (rho, T), area, bary, steps = vortex_march(n, N, L, t_final, eps, model, **kw)
         _, rho_x, T_x = workloads.vortex_states(bary, N, L, t_final, BOX, BOX)
-        rows.append({"n_side": n, "cells": len(area), "h": float(np.sqrt(area).mean()), "steps": steps,
-                     "dt": t_final / steps, **errors(area, rho, T, rho_x, T_x)})
+        rows.append({"n": n, "mesh": kw.get("mesh", "tri"), "cells": len(area), "h": float(np.sqrt(area).mean()),
+                     "steps": steps, "dt": t_final / steps, **errors(area, rho, T, rho_x, T_x)})
     return rows
 
 
 def time_study(eps, n_side=21, N=30, L=10.0, t_final=9e-3, dts=(1.8e-3, 9e-4, 4.5e-4, 2.25e-4), refine=32,
                model="boltzmann", **kw):
-    """Tables conv_1e-3 to conv_1: one row per time step on one mesh, errors
-    against the run with a step `refine` times smaller than the smallest."""
+    """Tables conv_1e-3 to conv_1: one row per time step on one mesh
+    (vortex_mesh(n_side, kw["mesh"])), errors against the run with a step
+    `refine` times smaller than the smallest."""
     modes = kw.pop("modes", None) or bz.Modes(bz.Grid(2, N, L), 0.0)
     ref_steps = int(round(t_final / (min(dts) / refine)))
     (rho_r, T_r), area, _, _ = vortex_march(n_side, N, L, t_final, eps, model, steps=ref_steps, modes=modes, **kw)
@@ -139,7 +158,9 @@ def main(argv=None):
     import json
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--study", choices=["space", "time"], default="space")
-    ap.add_argument("--sides", type=int, nargs="+", default=[18, 36, 54, 72])
+    ap.add_argument("--sizes", type=int, nargs="+", default=None,
+                    help="triangulation sides (default 18 36 54 72) or Voronoi cell counts (678 2603 5739 10203)")
+    ap.add_argument("--mesh", choices=["tri", "voronoi"], default="tri")
     ap.add_argument("--eps", type=float, nargs="+", default=None)
     ap.add_argument("--model", choices=["bgk", "boltzmann"], default=None)
     ap.add_argument("--order", type=int, default=2)
@@ -147,11 +168,12 @@ def main(argv=None):
     ap.add_argument("--penalty", type=float, default=1.0)
     a = ap.parse_args(argv)
     modes = bz.Modes(bz.Grid(2, 30, 10.0), 0.0)
-    kw = dict(order=a.order, precision=a.precision, penalty=a.penalty, modes=modes)
+    kw = dict(order=a.order, precision=a.precision, penalty=a.penalty, modes=modes, mesh=a.mesh)
     keys = ("rho_L1", "rho_L2", "T_L1", "T_L2")
     if a.study == "space":
         for eps in a.eps or [1e-8]:
-            rows = space_study(a.sides, eps=eps, model=a.model or "bgk", **kw)
+            sizes = a.sizes or ([18, 36, 54, 72] if a.mesh == "tri" else [678, 2603, 5739, 10203])
+            rows = space_study(sizes, eps=eps, model=a.model or "bgk", **kw)
             for r in rows:
                 print(json.dumps(r), flush=True)
             print(json.dumps({"orders": {k: orders(rows, k) for k in keys}}), flush=True)

@@ -146,6 +146,58 @@ def periodic_triangulation(n_side, Lx=10.0, Ly=10.0, seed=1006, jitter=0.25):
     return pts, np.asarray(tri, dtype=np.int64)
 
 
+def periodic_voronoi(n_cells, Lx=10.0, Ly=10.0, seed=1007, lloyd=6, max_vertices=8):
+    """Voronoi tessellation of the periodic box [0,Lx] x [0,Ly] (the polygonal
+    meshes of Sec. 4.1): n_cells seeded random generators, moved `lloyd`
+    times to the centroids of their cells (Lloyd's iteration, which makes the
+    cells close to hexagons; continued until no cell has more than
+    max_vertices vertices), the diagram computed on the 3 x 3 tiling of the
+    box and the cells of the middle copy kept.  A vertex that lies outside
+    the box is the periodic image of one used by a cell on the other side;
+    the mesh joins them through the periods.  Returns the vertices (m, 2) and
+    the cells (lists of vertex indices, counter-clockwise)."""
+    from scipy.spatial import Voronoi
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(0.0, 1.0, (n_cells, 2)) * [Lx, Ly]
+    shifts = np.array([(a * Lx, b * Ly) for a in (-1, 0, 1) for b in (-1, 0, 1)])
+    mid = 4                                                  # index of the (0, 0) shift
+
+    def diagram(p):
+        vor = Voronoi(np.concatenate([p + s for s in shifts]))
+        cells = []
+        for c in range(mid * n_cells, (mid + 1) * n_cells):
+            reg = vor.regions[vor.point_region[c]]
+            assert reg and -1 not in reg
+            cells.append(reg)
+        return vor.vertices, cells
+
+    def centroid(P):
+        x, y = P[:, 0], P[:, 1]
+        xn, yn = np.roll(x, -1), np.roll(y, -1)
+        cr = x * yn - xn * y
+        a = 0.5 * cr.sum()
+        return np.array([((x + xn) * cr).sum(), ((y + yn) * cr).sum()]) / (6.0 * a)
+
+    it = 0
+    while True:
+        V, cells = diagram(p)
+        if it >= lloyd and max(len(c) for c in cells) <= max_vertices:
+            break
+        if it >= lloyd + 60:
+            raise ValueError("Voronoi cells with more than %d vertices remain; try another seed" % max_vertices)
+        p = np.array([centroid(V[c]) for c in cells]) % [Lx, Ly]
+        it += 1
+    used = sorted({v for c in cells for v in c})
+    remap = {v: i for i, v in enumerate(used)}
+    out = []
+    for c in cells:
+        P = V[c]
+        x, y = P[:, 0], P[:, 1]
+        ccw = (x * np.roll(y, -1) - np.roll(x, -1) * y).sum() > 0
+        out.append([remap[v] for v in (c if ccw else c[::-1])])
+    return V[used], out
+
+
 def vortex_states(bary, N, L, t=0.0, Lx=10.0, Ly=10.0, beta=5.0, gamma=2.0):
     """Maxwellians of the isentropic vortex of Sec. 4.1 (the Euler solution,
     advected by the mean flow (1, 1) over the periodic box) at the points

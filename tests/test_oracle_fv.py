@@ -218,12 +218,17 @@ def _tile3(pts, tri, Lx, Ly):
     return np.array(xy), cells
 
 
-def test_periodic_mesh_equals_the_tiled_plane(fv):
+@pytest.mark.parametrize("kind", ["triangles", "voronoi"])
+def test_periodic_mesh_equals_the_tiled_plane(fv, kind):
     """The periodic residual equals that of the middle copy of a 3 x 3 tiling
     computed as a plain (non-periodic) mesh: pins the shifts of faces,
-    stencils and sectors against the ordinary code path."""
+    stencils and sectors against the ordinary code path (triangles, and the
+    polygons of a periodic Voronoi tessellation)."""
     Lx, Ly = 10.0, 6.0
-    pts, tri = workloads.periodic_triangulation(6, Lx, Ly, seed=2)
+    if kind == "triangles":
+        pts, tri = workloads.periodic_triangulation(6, Lx, Ly, seed=2)
+    else:
+        pts, tri = workloads.periodic_voronoi(40, Lx, Ly, seed=3)
     m = fv.Mesh(pts, tri, periodic=(Lx, Ly))
     assert abs(m.area.sum() - Lx * Ly) < 1e-11
     assert all(fc[0] >= 0 for fl in m.faces for fc in fl)
