@@ -35,6 +35,23 @@ fbar_i + g . (x_b,j - x_b,i).  Hence
     sigma_s = h_i^2 |g_s|^2.
 For M = 0, f^w = fbar (first order).
 
+Degree M = 2 (order=3, the third-order scheme of Sec. 4.1's O3 columns): the
+zero-mean Taylor basis about x_b scaled by h (eq. Dubiner_phi_spatial),
+  phi = (xi, eta, xi^2 - <xi^2>_i, xi eta - <xi eta>_i, eta^2 - <eta^2>_i),
+  xi = (x - x_b,i)/h_i, eta = (y - y_b,i)/h_i, <.>_i the mean over P_i,
+p = fbar_i + sum_l c_l phi_l.  Cell means of quadratics are exact: the polygon
+is split into the fan of triangles from its first vertex and each triangle's
+three edge midpoints, with a third of its area each, integrate quadratics
+exactly.
+  - p_opt: least squares over the cell and its 11 nearest cells
+    (n_e = 2 M(M) = 12), rows = the means of phi over P_j;
+  - p^L: the degree-1 sector polynomials above (coefficients (h g, 0, 0, 0));
+  - p^0 = (p_opt - sum_L lambda_L p^L) / lambda_0;
+  - sigma_s = (1/|P_i|) int_{P_i} (h^2 |grad p|^2 + h^4 (p_xx^2 + p_xy^2 +
+    p_yy^2)) dx, the same indicator (h^2 |g|^2) for the linear polynomials;
+  - the face integrals use the 2-point Gauss-Legendre rule on every edge
+    (exact for the cubic v.n p along a straight edge).
+
 Readings of points the paper leaves open (each listed in the design notes):
   - central stencil: the 5 cells nearest to P_i by barycentre distance
     among the cells that share a vertex with P_i or with one of its
@@ -246,13 +263,110 @@ def reconstruct_gradients(mesh, f, order):
     return g
 
 
+GAUSS2 = (0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0))   # 2-point Gauss-Legendre on [0, 1]
+
+
+def _quadratic_means(P, xb, h):
+    """Means over the polygon with vertices P (k, 2), taken in order, of
+    (xi, eta, xi^2, xi eta, eta^2), xi = (x - xb_x)/h, eta = (y - xb_y)/h."""
+    Q = (np.asarray(P, dtype=np.float64) - xb) / h
+    tot, area = np.zeros(5), 0.0
+    for t in range(1, len(Q) - 1):
+        a, b, c = Q[0], Q[t], Q[t + 1]
+        at = 0.5 * ((b[0] - a[0]) * (c[1] - a[1]) - (c[0] - a[0]) * (b[1] - a[1]))
+        for m in (0.5 * (a + b), 0.5 * (b + c), 0.5 * (c + a)):
+            tot += (at / 3.0) * np.array([m[0], m[1], m[0] * m[0], m[0] * m[1], m[1] * m[1]])
+        area += at
+    return tot / area
+
+
+def quadratic_basis(mesh, i):
+    """(x_b, h, mu): the expansion point, the scale and the means over P_i of
+    (xi, eta, xi^2, xi eta, eta^2) (the first two vanish: x_b is the centroid)."""
+    xb, h = mesh.bary[i], mesh.h[i]
+    return xb, h, _quadratic_means(mesh.xy[mesh.cells[i]], xb, h)
+
+
+def quadratic_phi(x, xb, h, mu):
+    """The zero-mean basis (xi, eta, xi^2 - mu_20, xi eta - mu_11, eta^2 - mu_02) at x."""
+    xi, eta = (x[0] - xb[0]) / h, (x[1] - xb[1]) / h
+    return np.array([xi, eta, xi * xi - mu[2], xi * eta - mu[3], eta * eta - mu[4]])
+
+
+def quadratic_indicator(c, mu):
+    """sigma of the module docstring for coefficients c (5, nv): the cell mean
+    of (d/dxi p)^2 + (d/deta p)^2 plus the squares of the second derivatives."""
+    c1, c2, c3, c4, c5 = c
+    return (c1 * c1 + c2 * c2
+            + 4 * c3 * c3 * mu[2] + 4 * c3 * c4 * mu[3] + c4 * c4 * mu[4]
+            + c4 * c4 * mu[2] + 4 * c4 * c5 * mu[3] + 4 * c5 * c5 * mu[4]
+            + 4 * c3 * c3 + c4 * c4 + 4 * c5 * c5)
+
+
+def reconstruct_quadratic(mesh, f, weights="nonlinear"):
+    """CWENO coefficients C (n_cells, 5, nv) of degree 2 in the basis of
+    quadratic_phi; weights="linear" returns p_opt (for the exactness pins)."""
+    f = np.asarray(f, dtype=np.float64)
+    n, nv = f.shape
+    C = np.zeros((n, 5, nv))
+    for i in range(n):
+        xb, h, mu = quadratic_basis(mesh, i)
+        sub = np.array([0.0, 0.0, mu[2], mu[3], mu[4]])
+        st = mesh.central_stencil_shifted(i, count=11)
+        A = np.array([_quadratic_means(mesh.xy[mesh.cells[j]] + s, xb, h) - sub for j, s in st])
+        d = np.array([f[j] - f[i] for j, _ in st])
+        c_opt = np.linalg.solve(A.T @ A, A.T @ d)
+        secs = mesh.sectors_shifted(i)
+        if weights == "linear" or not secs:
+            C[i] = c_opt
+            continue
+        lam_l = (1.0 - LAMBDA0) / len(secs)
+        polys = []
+        for a, sa, b, sb in secs:
+            A2 = np.array([(mesh.bary[a] + sa - xb) / h, (mesh.bary[b] + sb - xb) / h])
+            cs = np.zeros((5, nv))
+            cs[:2] = np.linalg.solve(A2, np.array([f[a] - f[i], f[b] - f[i]]))
+            polys.append(cs)
+        c0 = (c_opt - lam_l * sum(polys)) / LAMBDA0
+        allp = [c0] + polys
+        lams = [LAMBDA0] + [lam_l] * len(polys)
+        wt = [lm / (quadratic_indicator(cc, mu) + EPS) ** R_EXP for lm, cc in zip(lams, allp)]
+        tot = sum(wt)
+        C[i] = sum((w / tot) * cc for w, cc in zip(wt, allp))
+    return C
+
+
+def _residual_quadratic(mesh, f, N, L, weights):
+    """L_{k,i} with the degree-2 reconstruction and 2 Gauss points per face."""
+    v1, v2 = velocity_grid(N, L)
+    C = reconstruct_quadratic(mesh, f, weights)
+    basis = [quadratic_basis(mesh, i) for i in range(len(f))]
+    out = np.zeros_like(f)
+    for i, c in enumerate(mesh.cells):
+        acc = np.zeros(f.shape[1])
+        for q, (j, ln, nx, ny, mx, my) in enumerate(mesh.faces[i]):
+            vn = v1 * nx + v2 * ny
+            xa, xe = mesh.xy[c[q]], mesh.xy[c[(q + 1) % len(c)]]
+            for t in GAUSS2:
+                x = xa + t * (xe - xa)
+                fl = f[i] + quadratic_phi(x, *basis[i]) @ C[i]
+                if j < 0:
+                    fr = fl
+                else:
+                    fr = f[j] + quadratic_phi(x - mesh.face_shift[i][q], *basis[j]) @ C[j]
+                acc += 0.5 * ln * (0.5 * vn * (fl + fr) - 0.5 * np.abs(vn) * (fr - fl))
+        out[i] = acc / mesh.area[i]
+    return out
+
+
 def wall_maxwellian(v1, v2, theta, u1, u2):
     """Unit-mass 2-D Maxwellian of the wall (eq. MAXB)."""
     return np.exp(-((v1 - u1) ** 2 + (v2 - u2) ** 2) / (2 * theta)) / (2 * np.pi * theta)
 
 
-def transport_residual(mesh, f, N, L, order=2, walls=None):
-    """L_{k,i} of the module docstring for f of shape (n_cells, N*N).
+def transport_residual(mesh, f, N, L, order=2, walls=None, weights="nonlinear"):
+    """L_{k,i} of the module docstring for f of shape (n_cells, N*N); order 1,
+    2 (degree 0, 1) or 3 (degree 2; weights="linear" keeps p_opt).
 
     walls: optional {frozenset({a, b}): (theta_w, u_w1, u_w2)} for boundary
     edges with vertices a, b that are walls with full accommodation
@@ -262,6 +376,10 @@ def transport_residual(mesh, f, N, L, order=2, walls=None):
     balance, mu sum_{v.n < 0} M_w |v.n| = sum_{v.n > 0} f_L v.n (n the outer
     normal; the velocity-cell volume cancels)."""
     f = np.asarray(f, dtype=np.float64)
+    if order == 3:
+        if walls:
+            raise NotImplementedError("walls are built for orders 1 and 2")
+        return _residual_quadratic(mesh, f, N, L, weights)
     v1, v2 = velocity_grid(N, L)
     g = reconstruct_gradients(mesh, f, order)
     out = np.zeros_like(f)

@@ -14,7 +14,13 @@ Checked against what geometry and calculus fix, not against the oracle itself:
   - near a jump the nonlinear weights leave far fewer out-of-range face
     values than the unweighted least-squares gradient;
   - walls with full accommodation keep a gas at rest at the wall temperature
-    and conserve mass in a closed box.
+    and conserve mass in a closed box;
+  - degree 2 (order 3): cell averages of a quadratic field, integrated by
+    Green's theorem (not by the oracle's triangle rule), are reconstructed
+    exactly by p_opt, so the residual is v . grad q at the barycentre (the
+    mean of a linear function) in every cell; with the nonlinear weights
+    every linear field is still exact; a periodic mesh equals the tiled
+    plane; near a jump the weights cut the overshoots of p_opt.
 """
 import numpy as np
 import pytest
@@ -88,7 +94,7 @@ def test_linear_field_gives_exact_divergence(fv, mesh, which):
     assert np.abs(Lr - want).max() < 1e-9 * np.abs(want).max()
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_constant_field_has_zero_residual(fv, mesh, order):
     f = np.full((len(mesh.cells), 16), 0.37)
     assert np.abs(fv.transport_residual(mesh, f, 4, 2.0, order=order)).max() < 1e-12
@@ -238,7 +244,7 @@ def test_periodic_mesh_equals_the_tiled_plane(fv, kind):
     xy3, cells3 = _tile3(pts, tri, Lx, Ly)
     m3 = fv.Mesh(xy3, cells3)
     f3 = np.tile(f, (9, 1))
-    for order in (1, 2):
+    for order in (1, 2, 3):
         Lp = fv.transport_residual(m, f, N, L, order=order)
         L3 = fv.transport_residual(m3, f3, N, L, order=order)
         mid = L3[4 * len(m.cells):5 * len(m.cells)]
@@ -258,3 +264,78 @@ def test_ambiguous_pairing_is_refused(fv):
     pts = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
     with pytest.raises(ValueError):
         fv.Mesh(pts, [[0, 1, 2], [0, 1, 2]])
+
+
+def _green_means(P):
+    """Means of (1, x, y, x^2, x y, y^2) over the polygon P (k, 2), counter-
+    clockwise, from Green's theorem (vertex sums of the boundary integrals)."""
+    x, y = P[:, 0], P[:, 1]
+    xn, yn = np.roll(x, -1), np.roll(y, -1)
+    c = x * yn - xn * y
+    a = c.sum() / 2
+    mx = ((x + xn) * c).sum() / 6
+    my = ((y + yn) * c).sum() / 6
+    mxx = ((x * x + x * xn + xn * xn) * c).sum() / 12
+    myy = ((y * y + y * yn + yn * yn) * c).sum() / 12
+    mxy = ((x * yn + 2 * x * y + 2 * xn * yn + xn * y) * c).sum() / 24
+    return np.array([a, mx, my, mxx, mxy, myy]) / a
+
+
+def _quadratic_meshes(fv):
+    pts, tri = workloads.sod_triangulation(n_side=10, seed=11)
+    vp, vc = workloads.periodic_voronoi(50, 1.0, 1.0, seed=4)      # used as a plain (bounded) mesh
+    return {"tri": fv.Mesh(pts, tri), "voronoi": fv.Mesh(vp, vc), "mixed": _quad_tri_mesh(fv)}
+
+
+@pytest.mark.parametrize("which", ["tri", "voronoi", "mixed"])
+def test_quadratic_field_exact_with_optimal_polynomial(fv, which):
+    m = _quadratic_meshes(fv)[which]
+    N, L = 4, 2.0
+    v1, v2 = fv.velocity_grid(N, L)
+    rng = np.random.default_rng(5)
+    # q_k(x, y) = a_k + b_k x + c_k y + d_k x^2 + e_k x y + g_k y^2, one per velocity
+    co = rng.uniform(-1, 1, (6, N * N))
+    means = np.array([_green_means(m.xy[c]) for c in m.cells])          # (n, 6)
+    f = means @ co
+    Lr = fv.transport_residual(m, f, N, L, order=3, weights="linear")
+    x, y = m.bary[:, :1], m.bary[:, 1:]
+    qx = co[1] + 2 * co[3] * x + co[4] * y
+    qy = co[2] + co[4] * x + 2 * co[5] * y
+    want = v1 * qx + v2 * qy
+    assert np.abs(Lr - want).max() < 1e-9 * np.abs(want).max()
+    # the degree-1 reconstruction is not exact for them
+    assert np.abs(fv.transport_residual(m, f, N, L, order=2) - want).max() > 1e-4 * np.abs(want).max()
+
+
+def test_linear_field_exact_with_weights_degree2(fv, mesh):
+    N, L = 8, 3.0
+    v1, v2 = fv.velocity_grid(N, L)
+    a = np.linspace(0.5, 1.5, N * N)
+    b = np.stack([np.linspace(-2, 1, N * N), np.linspace(0.3, -0.7, N * N)])
+    f = a[None, :] + mesh.bary[:, :1] * b[0][None, :] + mesh.bary[:, 1:] * b[1][None, :]
+    Lr = fv.transport_residual(mesh, f, N, L, order=3)
+    want = (v1 * b[0] + v2 * b[1])[None, :]
+    assert np.abs(Lr - want).max() < 1e-9 * np.abs(want).max()
+
+
+def test_degree2_weights_cut_overshoots(fv):
+    """Near the jump the nonlinear weights leave fewer out-of-range face values
+    (at the Gauss points) than the optimal polynomial alone."""
+    pts, tri = workloads.sod_triangulation(n_side=20, seed=9)
+    m = fv.Mesh(pts, tri)
+    f = np.where(m.bary[:, 0] < 0.5, 1.0, 0.125)[:, None] * np.ones((1, 2))
+
+    def count(C):
+        n = 0
+        for i, c in enumerate(m.cells):
+            basis = fv.quadratic_basis(m, i)
+            for q in range(len(c)):
+                xa, xe = m.xy[c[q]], m.xy[c[(q + 1) % len(c)]]
+                for t in fv.GAUSS2:
+                    val = f[i, 0] + fv.quadratic_phi(xa + t * (xe - xa), *basis) @ C[i, :, 0]
+                    n += max(val - 1.0, 0.125 - val) > 0.05 * 0.875
+        return n
+
+    n_w = count(fv.reconstruct_quadratic(m, f))
+    n_opt = count(fv.reconstruct_quadratic(m, f, weights="linear"))
+    assert n_opt > 40 and n_w < n_opt / 2, (n_w, n_opt)
