@@ -261,16 +261,24 @@ int group_collide(const bz_group_item *items, int n_items, int precision, int fl
  * with one of its vertex neighbours), one sector polynomial per pair of
  * consecutive faces with neighbours on both, linear weights 3/4 (central) and
  * 1/4 shared by the sectors, smoothness h^2 |grad p|^2 (h: largest
- * barycentre-to-vertex distance), eps = 1e-14, r = 4.  The tables are built
- * in FP64 on the host and uploaded to the current device in FP64 and FP32.
+ * barycentre-to-vertex distance), eps = 1e-14, r = 4.  order 3: CWENO of
+ * degree 2 (the third-order scheme): the optimal quadratic by least squares
+ * over the cell and its 11 nearest cells in the zero-mean Taylor basis about
+ * the barycentre scaled by h (eq. Dubiner_phi_spatial; cell means of the
+ * basis exact for quadratics), the same degree-1 sectors and weights with
+ * the indicator extended by the squared scaled second derivatives, and the
+ * fluxes at the two Gauss-Legendre points of every face.  The tables are
+ * built in FP64 on the host and uploaded to the current device in FP64 and
+ * FP32.
  *   n_vertices, xy     : vertices, xy[2 v] = x, xy[2 v + 1] = y (host)
  *   n_cells            : cells, 1 .. 2^30
  *   cell_ptr           : n_cells + 1 offsets into cell_vertices, cell_ptr[0] = 0
  *   cell_vertices      : vertex indices of every cell (3 to 8 per cell)
- *   order              : 1 or 2
+ *   order              : 1, 2 or 3
  *   out                : receives the handle (release with bz_mesh_destroy)
- * Errors: BZ_EINVAL (bad sizes or indices, degenerate or overlapping cells),
- * BZ_ENOMEM, BZ_ECUDA. */
+ * Errors: BZ_EINVAL (bad sizes or indices, degenerate or overlapping cells; for
+ * order 3 a neighbourhood that does not determine a quadratic), BZ_ENOMEM,
+ * BZ_ECUDA. */
 int build_fv_mesh(int n_vertices, const double *xy, int64_t n_cells, const int64_t *cell_ptr,
                   const int64_t *cell_vertices, int order, bz_mesh **out);
 
@@ -305,7 +313,8 @@ int build_fv_mesh_periodic(int n_vertices, const double *xy, int64_t n_cells, co
  * A mesh with walls needs N divisible by 4 and N^2 <= 1024 in
  * transport_residual and imex_step_fv (BZ_ENOTSUP otherwise): one CTA forms
  * each cell's mu over all its velocities.
- * Errors: BZ_EINVAL (NULL mesh, not a boundary edge, theta_w <= 0), BZ_ECUDA. */
+ * Errors: BZ_EINVAL (NULL mesh, not a boundary edge, theta_w <= 0), BZ_ENOTSUP
+ * (an order-3 mesh: the wall flux is built for orders 1 and 2), BZ_ECUDA. */
 int fv_mesh_set_walls(bz_mesh *mesh, int64_t n_edges, const int64_t *edge_vertices, const double *wall_params);
 
 /* transport_residual -- <L(f^w)>_x of eq. ho for every cell and discrete
@@ -318,7 +327,8 @@ int fv_mesh_set_walls(bz_mesh *mesh, int64_t n_edges, const int64_t *edge_vertic
  *               BZ_FP64, float for BZ_FP32; must not overlap
  * Boundary faces are transmissive (the outer state equals the inner one)
  * unless fv_mesh_set_walls made them walls.
- * Scratch (order 2: 2 n_cells N^2 values) comes from the stream-ordered pool.
+ * Scratch (order 2: 2 n_cells N^2 values, order 3: 5 n_cells N^2) comes from
+ * the stream-ordered pool.
  * Errors: BZ_EINVAL, BZ_ENOTSUP (3-D grid; walls with N not divisible by 4 or
  * N^2 > 1024), BZ_ECUDA. */
 int transport_residual(const bz_mesh *mesh, const bz_grid *g, int precision, const void *f, void *L,

@@ -190,7 +190,8 @@ class FastModes(Modes):
 class Mesh:
     """Finite-volume mesh of the transport step (build_fv_mesh): vertices xy
     (n_vtx, 2) and cells, either an (n_cells, k) integer array or a list of
-    vertex lists; order 1 (first order) or 2 (CWENO of degree 1); periodic
+    vertex lists; order 1 (first order), 2 (CWENO of degree 1) or 3 (CWENO
+    of degree 2, two Gauss points per face); periodic
     (Lx, Ly) makes it periodic (build_fv_mesh_periodic, 0 for a direction
     without periodicity)."""
 

@@ -163,12 +163,15 @@ def main(argv=None):
     ap.add_argument("--mesh", choices=["tri", "voronoi"], default="tri")
     ap.add_argument("--eps", type=float, nargs="+", default=None)
     ap.add_argument("--model", choices=["bgk", "boltzmann"], default=None)
-    ap.add_argument("--order", type=int, default=2)
+    ap.add_argument("--order", type=int, default=2, help="1, 2 or 3 (CWENO of degree 0, 1, 2)")
+    ap.add_argument("--scheme", choices=["ars222", "bpr343", "euler"], default=None,
+                    help="IMEX scheme (default: bpr343 with --order 3, else ars222)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--penalty", type=float, default=1.0)
     a = ap.parse_args(argv)
     modes = bz.Modes(bz.Grid(2, 30, 10.0), 0.0)
-    kw = dict(order=a.order, precision=a.precision, penalty=a.penalty, modes=modes, mesh=a.mesh)
+    kw = dict(order=a.order, precision=a.precision, penalty=a.penalty, modes=modes, mesh=a.mesh,
+              scheme=a.scheme or ("bpr343" if a.order == 3 else "ars222"))
     keys = ("rho_L1", "rho_L2", "T_L1", "T_L2")
     if a.study == "space":
         for eps in a.eps or [1e-8]:

@@ -319,8 +319,9 @@ int collide_chain(const bz_modes *m, int precision, int flags, const void *f, vo
 // Transport residual L [cell][nv] of f over the mesh: CWENO gradients into
 // scratch (`ext` if given: transport_scratch_bytes), then the fluxes.
 size_t transport_scratch_bytes(const bz_mesh *mesh, const bz_grid *g, int precision) {
-    if (mesh->order != 2) return 0;
-    return (size_t)2 * mesh->n_cells * g->v.nv * (precision == BZ_FP64 ? sizeof(double) : sizeof(float));
+    if (mesh->order == 1) return 0;
+    const size_t per = mesh->order == 3 ? (size_t)kFvCoef3 : 2;     // coefficients per (cell, velocity)
+    return per * mesh->n_cells * g->v.nv * (precision == BZ_FP64 ? sizeof(double) : sizeof(float));
 }
 
 int transport_chain(const bz_mesh *mesh, const bz_grid *g, int precision, const void *f, void *L, cudaStream_t st,
@@ -329,6 +330,28 @@ int transport_chain(const bz_mesh *mesh, const bz_grid *g, int precision, const 
     if (!fv_walls_supported(mesh, v))
         return fail(BZ_ENOTSUP, "transport: walls need N divisible by 4 and at most 32^2 velocities");
     Scratch s;
+    if (mesh->order == 3) {
+        if (!ext) BZ_TRY(s.alloc(transport_scratch_bytes(mesh, g, precision), st), "transport: scratch");
+        void *C = ext ? ext : s.p;
+        if (precision == BZ_FP64) {
+            BZ_LAUNCH("fv_coef3_f64", st,
+                      launch_fv_coef3_f64(mesh, v, static_cast<const double *>(f), static_cast<double *>(C), st),
+                      "transport: reconstruction");
+            BZ_LAUNCH("fv_flux3_f64", st,
+                      launch_fv_flux3_f64(mesh, v, static_cast<const double *>(f), static_cast<const double *>(C),
+                                          static_cast<double *>(L), st),
+                      "transport: fluxes");
+        } else {
+            BZ_LAUNCH("fv_coef3_f32", st,
+                      launch_fv_coef3_f32(mesh, v, static_cast<const float *>(f), static_cast<float *>(C), st),
+                      "transport: reconstruction");
+            BZ_LAUNCH("fv_flux3_f32", st,
+                      launch_fv_flux3_f32(mesh, v, static_cast<const float *>(f), static_cast<const float *>(C),
+                                          static_cast<float *>(L), st),
+                      "transport: fluxes");
+        }
+        return BZ_OK;
+    }
     void *G = nullptr;
     if (mesh->order == 2) {
         if (!ext) BZ_TRY(s.alloc(transport_scratch_bytes(mesh, g, precision), st), "transport: scratch");

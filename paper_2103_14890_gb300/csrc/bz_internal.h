@@ -93,6 +93,8 @@ namespace bz {
 // [cell][slot] layout, FP64 and FP32 copies of the real-valued ones.
 constexpr int kFvMaxFaces = 8;
 constexpr int kFvCentral = 5;       // central stencil: the cell and its 5 nearest cells (2 x 3 cells)
+constexpr int kFvCentral3 = 11;     // degree 2: the cell and its 11 nearest cells (2 x 6 cells)
+constexpr int kFvCoef3 = 5;         // degree 2: coefficients of xi, eta, xi^2, xi eta, eta^2
 
 template <typename T> struct FvTables {
     const T *inv_area;      // [cell]
@@ -101,13 +103,22 @@ template <typename T> struct FvTables {
     const T *off_i;         // [cell][face][2]  x_face - x_b,i
     const T *off_j;         // [cell][face][2]  x_face - x_b,j (neighbour side)
     const T *Rc;            // [cell][2][kFvCentral] least-squares gradient rows
-    const T *Rs;            // [cell][face][4]  sector inverses (row-major 2 x 2)
+    const T *Rs;            // [cell][face][4]  sector inverses (row-major 2 x 2); degree 2: in the
+                            //                   scaled coordinates (x - x_b) / h
+};
+// Degree-2 reconstruction (order 3): zero-mean scaled Taylor basis
+// phi = (xi, eta, xi^2 - mu20, xi eta - mu11, eta^2 - mu02), xi = (x - x_b)/h.
+template <typename T> struct FvTables3 {
+    const T *mu;            // [cell][3]  cell means of xi^2, xi eta, eta^2
+    const T *Rc;            // [cell][5][kFvCentral3] least-squares coefficient rows
+    const T *phi_i;         // [cell][face][2 Gauss points][5] basis of the cell at the face's Gauss points
+    const T *phi_j;         // [cell][face][2][5] the neighbour's basis at the same points
 };
 }  // namespace bz
 
 struct bz_mesh {
     int device;
-    int order;              // 1: piecewise constant, 2: CWENO with degree-1 polynomials
+    int order;              // 1: piecewise constant, 2: CWENO of degree 1, 3: CWENO of degree 2
     int64_t n_cells, n_faces_interior, n_faces_boundary;
     int max_faces;
     int *d_nface;           // [cell] faces
@@ -131,6 +142,12 @@ struct bz_mesh {
     void *d_real32;         // one block holding the FvTables<float> arrays
     bz::FvTables<double> t64;
     bz::FvTables<float> t32;
+    // order 3 only
+    int *d_ncen3;           // [cell] central stencil size (<= kFvCentral3)
+    int *d_cen3;            // [cell][kFvCentral3]
+    void *d_real3_64, *d_real3_32;
+    bz::FvTables3<double> u64;
+    bz::FvTables3<float> u32;
 };
 
 namespace bz {
@@ -243,6 +260,15 @@ cudaError_t launch_fv_flux_f64(const bz_mesh *mesh, const GridView &g, const dou
                                cudaStream_t st);
 // walls need one CTA to hold all velocities of a cell
 bool fv_walls_supported(const bz_mesh *mesh, const GridView &g);
+// order 3: coefficients C [cell][5][nv] of the degree-2 CWENO polynomial, then
+// the fluxes at two Gauss points per face
+cudaError_t launch_fv_coef3_f64(const bz_mesh *mesh, const GridView &g, const double *f, double *C,
+                                cudaStream_t st);
+cudaError_t launch_fv_coef3_f32(const bz_mesh *mesh, const GridView &g, const float *f, float *C, cudaStream_t st);
+cudaError_t launch_fv_flux3_f64(const bz_mesh *mesh, const GridView &g, const double *f, const double *C,
+                                double *L, cudaStream_t st);
+cudaError_t launch_fv_flux3_f32(const bz_mesh *mesh, const GridView &g, const float *f, const float *C, float *L,
+                                cudaStream_t st);
 cudaError_t launch_fv_flux_f32(const bz_mesh *mesh, const GridView &g, const float *f, const float *G, float *L,
                                cudaStream_t st);
 

@@ -45,7 +45,80 @@ struct HostMesh {
     int64_t n = 0;
     std::vector<int> nface, nb, ncen, cen, nsec, sec, order;
     std::vector<double> inv_area, h2, fn, off_i, off_j, Rc, Rs;
+    // order 3
+    std::vector<int> ncen3, cen3;
+    std::vector<double> mu, Rc3, phi_i, phi_j;
 };
+
+constexpr int64_t kReal3PerCell = 3 + kFvCoef3 * kFvCentral3 + 2 * kFvMaxFaces * 2 * kFvCoef3;
+
+template <typename T>
+FvTables3<T> carve3(void *base, int64_t n) {
+    T *p = static_cast<T *>(base);
+    FvTables3<T> t;
+    t.mu = p; p += n * 3;
+    t.Rc = p; p += n * kFvCoef3 * kFvCentral3;
+    t.phi_i = p; p += n * kFvMaxFaces * 2 * kFvCoef3;
+    t.phi_j = p;
+    return t;
+}
+
+// Means over a polygon (vertices px, py in order, translated by (sx, sy)) of
+// xi, eta, xi^2, xi eta, eta^2 with xi = (x - x0)/hh, eta = (y - y0)/hh: the
+// fan of triangles from the first vertex, each integrated exactly for
+// quadratics by its three edge midpoints (a third of the area each).
+void quad_means(const std::vector<int64_t> &c, const double *xy, double sx, double sy, double x0, double y0,
+                double hh, double out[5]) {
+    double acc[5] = {0, 0, 0, 0, 0}, area = 0.0;
+    auto X = [&](int64_t v) { return (xy[2 * v] + sx - x0) / hh; };
+    auto Y = [&](int64_t v) { return (xy[2 * v + 1] + sy - y0) / hh; };
+    const double ax = X(c[0]), ay = Y(c[0]);
+    for (size_t t = 1; t + 1 < c.size(); ++t) {
+        const double bx = X(c[t]), by = Y(c[t]), cx = X(c[t + 1]), cy = Y(c[t + 1]);
+        const double at = 0.5 * ((bx - ax) * (cy - ay) - (cx - ax) * (by - ay));
+        const double mx[3] = {0.5 * (ax + bx), 0.5 * (bx + cx), 0.5 * (cx + ax)};
+        const double my[3] = {0.5 * (ay + by), 0.5 * (by + cy), 0.5 * (cy + ay)};
+        for (int q = 0; q < 3; ++q) {
+            const double w = at / 3.0;
+            acc[0] += w * mx[q];
+            acc[1] += w * my[q];
+            acc[2] += w * mx[q] * mx[q];
+            acc[3] += w * mx[q] * my[q];
+            acc[4] += w * my[q] * my[q];
+        }
+        area += at;
+    }
+    for (int l = 0; l < 5; ++l) out[l] = acc[l] / area;
+}
+
+// Solve the symmetric positive definite 5 x 5 system M X = B (B: 5 x nc,
+// row-major, overwritten with X) by Gaussian elimination with partial
+// pivoting.  Returns false when a pivot falls below tol times the largest
+// diagonal entry (the stencil does not determine a quadratic).
+bool solve5(double M[5][5], double *B, int nc, double tol) {
+    double dmax = 0.0;
+    for (int r = 0; r < 5; ++r) dmax = std::max(dmax, fabs(M[r][r]));
+    for (int col = 0; col < 5; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 5; ++r)
+            if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+        if (!(fabs(M[piv][col]) > tol * dmax)) return false;
+        if (piv != col) {
+            for (int q = 0; q < 5; ++q) std::swap(M[piv][q], M[col][q]);
+            for (int q = 0; q < nc; ++q) std::swap(B[piv * nc + q], B[col * nc + q]);
+        }
+        for (int r = 0; r < 5; ++r) {
+            if (r == col) continue;
+            const double fct = M[r][col] / M[col][col];
+            if (fct == 0.0) continue;
+            for (int q = col; q < 5; ++q) M[r][q] -= fct * M[col][q];
+            for (int q = 0; q < nc; ++q) B[r * nc + q] -= fct * B[col * nc + q];
+        }
+    }
+    for (int r = 0; r < 5; ++r)
+        for (int q = 0; q < nc; ++q) B[r * nc + q] /= M[r][r];
+    return true;
+}
 
 template <typename T>
 FvTables<T> carve(void *base, int64_t n) {
@@ -104,6 +177,10 @@ void fv_mesh_destroy(bz_mesh *m) {
     free(m->h_nb);
     cudaFree(m->d_real64);
     cudaFree(m->d_real32);
+    cudaFree(m->d_ncen3);
+    cudaFree(m->d_cen3);
+    cudaFree(m->d_real3_64);
+    cudaFree(m->d_real3_32);
     free(m);
 }
 
@@ -114,7 +191,7 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
     if (n_vertices < 3 || !xy) return fail(BZ_EINVAL, "build_fv_mesh: need >= 3 vertices and their coordinates");
     if (n_cells < 1 || n_cells > (int64_t)1 << 30 || !cell_ptr || !cell_vertices)
         return fail(BZ_EINVAL, "build_fv_mesh: bad cell list");
-    if (order != 1 && order != 2) return fail(BZ_EINVAL, "build_fv_mesh: order must be 1 or 2");
+    if (order < 1 || order > 3) return fail(BZ_EINVAL, "build_fv_mesh: order must be 1, 2 or 3");
     if (cell_ptr[0] != 0) return fail(BZ_EINVAL, "build_fv_mesh: cell_ptr[0] must be 0");
     if (!(Lx >= 0) || !(Ly >= 0) || !std::isfinite(Lx) || !std::isfinite(Ly))
         return fail(BZ_EINVAL, "build_fv_mesh: periods must be finite and >= 0");
@@ -244,7 +321,23 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
     h.nsec.assign(n, 0);
     h.sec.assign(n * kFvMaxFaces * 2, 0);
     h.Rs.assign(n * kFvMaxFaces * 4, 0.0);
-    if (order == 2) {
+    if (order == 3) {
+        h.ncen3.assign(n, 0);
+        h.cen3.assign(n * kFvCentral3, 0);
+        h.mu.assign(n * 3, 0.0);
+        h.Rc3.assign(n * kFvCoef3 * kFvCentral3, 0.0);
+        h.phi_i.assign(n * kFvMaxFaces * 2 * kFvCoef3, 0.0);
+        h.phi_j.assign(n * kFvMaxFaces * 2 * kFvCoef3, 0.0);
+        for (int64_t i = 0; i < n; ++i) {
+            double q[5];
+            quad_means(cells[i], xy, 0.0, 0.0, bx[i], by[i], sqrt(h.h2[i]), q);
+            h.mu[3 * i] = q[2];
+            h.mu[3 * i + 1] = q[3];
+            h.mu[3 * i + 2] = q[4];
+        }
+    }
+    if (order >= 2) {
+        const int ncen_max = order == 3 ? kFvCentral3 : kFvCentral;
         // vertex class -> (cell, vertex)
         std::vector<int64_t> vptr(n_vertices + 1, 0);
         std::vector<std::pair<int64_t, int64_t>> vcell;
@@ -296,6 +389,37 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
                 dist.push_back({hypot(bx[c.j] + c.kx * Lx - bx[i], by[c.j] + c.ky * Ly - by[i]), c});
             }
             std::sort(dist.begin(), dist.end());
+            const double hi = sqrt(h.h2[i]);
+            if (order == 3) {
+                // least squares for the 5 coefficients of the zero-mean scaled
+                // Taylor basis over the cell's 11 nearest cells (row q: the
+                // basis' means over cell q, translated into this cell's frame)
+                const int nc = (int)std::min<size_t>(kFvCentral3, dist.size());
+                double A[kFvCentral3][5];
+                for (int q = 0; q < nc; ++q) {
+                    const Img &c = dist[q].m;
+                    h.cen3[i * kFvCentral3 + q] = (int)c.j;
+                    quad_means(cells[c.j], xy, c.kx * Lx, c.ky * Ly, bx[i], by[i], hi, A[q]);
+                    A[q][2] -= h.mu[3 * i];
+                    A[q][3] -= h.mu[3 * i + 1];
+                    A[q][4] -= h.mu[3 * i + 2];
+                }
+                h.ncen3[i] = nc;
+                double M[5][5], B[5 * kFvCentral3];
+                for (int r = 0; r < 5; ++r) {
+                    for (int col = 0; col < 5; ++col) {
+                        double sum = 0.0;
+                        for (int q = 0; q < nc; ++q) sum += A[q][r] * A[q][col];
+                        M[r][col] = sum;
+                    }
+                    for (int q = 0; q < nc; ++q) B[r * nc + q] = A[q][r];
+                }
+                if (nc < 5 || !solve5(M, B, nc, 1e-12))
+                    return fail(BZ_EINVAL, "build_fv_mesh: order 3 needs a cell neighbourhood that determines a "
+                                           "quadratic (mesh too small or degenerate)");
+                for (int r = 0; r < 5; ++r)
+                    for (int q = 0; q < nc; ++q) h.Rc3[((size_t)i * kFvCoef3 + r) * kFvCentral3 + q] = B[r * nc + q];
+            }
             const int nc = (int)std::min<size_t>(kFvCentral, dist.size());
             double ata[3] = {0, 0, 0};
             double axs[kFvCentral], ays[kFvCentral];
@@ -329,17 +453,48 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
                 const double mxa = std::max(std::max(fabs(a0), fabs(a1)), std::max(fabs(b0), fabs(b1)));
                 const double dt = a0 * b1 - a1 * b0;
                 if (fabs(dt) <= 1e-12 * mxa * mxa) continue;
-                // A = [[a0, a1], [b0, b1]] (rows: offsets), g = A^-1 (d_a, d_b)
+                // A = [[a0, a1], [b0, b1]] (rows: offsets), g = A^-1 (d_a, d_b);
+                // degree 2 takes the coefficients of xi = (x - x_b)/h: h g
+                const double sc = order == 3 ? hi : 1.0;
                 double *R = &h.Rs[((size_t)i * kFvMaxFaces + ns) * 4];
-                R[0] = b1 / dt;
-                R[1] = -a1 / dt;
-                R[2] = -b0 / dt;
-                R[3] = a0 / dt;
+                R[0] = sc * b1 / dt;
+                R[1] = -sc * a1 / dt;
+                R[2] = -sc * b0 / dt;
+                R[3] = sc * a0 / dt;
                 h.sec[((size_t)i * kFvMaxFaces + ns) * 2] = a;
                 h.sec[((size_t)i * kFvMaxFaces + ns) * 2 + 1] = b;
                 ++ns;
             }
             h.nsec[i] = ns;
+        }
+    }
+    if (order == 3) {
+        // the basis of the cell and of its neighbour at the face's two
+        // Gauss-Legendre points x_a + t (x_b - x_a), t = 1/2 -+ 1/(2 sqrt 3)
+        const double tg[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
+        auto basis = [&](int64_t c, double x, double y, double *out) {
+            const double hc = sqrt(h.h2[c]);
+            const double xi = (x - bx[c]) / hc, eta = (y - by[c]) / hc;
+            out[0] = xi;
+            out[1] = eta;
+            out[2] = xi * xi - h.mu[3 * c];
+            out[3] = xi * eta - h.mu[3 * c + 1];
+            out[4] = eta * eta - h.mu[3 * c + 2];
+        };
+        for (int64_t i = 0; i < n; ++i) {
+            const auto &c = cells[i];
+            const int k = (int)c.size();
+            for (int q = 0; q < k; ++q) {
+                const int64_t a = c[q], b = c[(q + 1) % k];
+                const size_t sidx = (size_t)i * kFvMaxFaces + q;
+                for (int g = 0; g < 2; ++g) {
+                    const double x = xy[2 * a] + tg[g] * (xy[2 * b] - xy[2 * a]);
+                    const double y = xy[2 * a + 1] + tg[g] * (xy[2 * b + 1] - xy[2 * a + 1]);
+                    basis(i, x, y, &h.phi_i[(sidx * 2 + g) * kFvCoef3]);
+                    const int j = h.nb[sidx];
+                    if (j >= 0) basis(j, x - fsx[sidx], y - fsy[sidx], &h.phi_j[(sidx * 2 + g) * kFvCoef3]);
+                }
+            }
         }
     }
     // processing order: the kernels take cells along a Morton (Z-order) curve
@@ -403,6 +558,30 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
     }
     m->t64 = carve<double>(m->d_real64, n);
     m->t32 = carve<float>(m->d_real32, n);
+    if (order == 3) {
+        std::vector<double> r3((size_t)(n * kReal3PerCell));
+        double *p3 = r3.data();
+        for (const std::vector<double> *v : {&h.mu, &h.Rc3, &h.phi_i, &h.phi_j}) {
+            memcpy(p3, v->data(), sizeof(double) * v->size());
+            p3 += v->size();
+        }
+        std::vector<float> r3f(r3.size());
+        for (size_t q = 0; q < r3.size(); ++q) r3f[q] = (float)r3[q];
+        double *d3 = nullptr;
+        float *d3f = nullptr;
+        e = upload(&m->d_ncen3, h.ncen3);
+        if (e == cudaSuccess) e = upload(&m->d_cen3, h.cen3);
+        if (e == cudaSuccess) e = upload(&d3, r3);
+        m->d_real3_64 = d3;
+        if (e == cudaSuccess) e = upload(&d3f, r3f);
+        m->d_real3_32 = d3f;
+        if (e != cudaSuccess) {
+            fv_mesh_destroy(m);
+            return cuda_fail(e, "build_fv_mesh: degree-2 tables");
+        }
+        m->u64 = carve3<double>(m->d_real3_64, n);
+        m->u32 = carve3<float>(m->d_real3_32, n);
+    }
     // host copies for fv_mesh_set_walls
     m->h_ptr = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
     m->h_vtx = (int64_t *)malloc(sizeof(int64_t) * (size_t)cell_ptr[n]);
@@ -425,6 +604,7 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
 // pairs (either order); n_edges = 0 removes every wall.
 int fv_mesh_set_walls(bz_mesh *m, int64_t n_edges, const int64_t *edges, const double *params) {
     if (!m) return fail(BZ_EINVAL, "fv_mesh_set_walls: mesh is NULL");
+    if (m->order == 3 && n_edges > 0) return fail(BZ_ENOTSUP, "fv_mesh_set_walls: walls are built for orders 1 and 2");
     if (n_edges < 0 || (n_edges > 0 && (!edges || !params)))
         return fail(BZ_EINVAL, "fv_mesh_set_walls: bad edge list");
     cudaFree(m->d_wall);

@@ -398,9 +398,188 @@ fv_flux_wall_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restr
     }
 }
 
+
+// ---- degree 2 (order 3) -----------------------------------------------------
+// Coefficients of the CWENO polynomial of degree 2 per (cell, velocity) in the
+// zero-mean scaled Taylor basis phi = (xi, eta, xi^2 - mu20, xi eta - mu11,
+// eta^2 - mu02), xi = (x - x_b)/h: p_opt from the least-squares rows over the
+// cell's 11 nearest cells, the degree-1 sector polynomials (coefficients of
+// xi and eta only), p_0 = (p_opt - lambda_L sum_L p_L) / lambda_0, and the
+// weights lambda_s / (sigma_s + eps)^4 in the same ratio form as degree 1,
+// sigma_s the cell mean of |h grad p|^2 plus the squared scaled second
+// derivatives (for the linear sectors: |h grad p|^2).  One velocity per
+// thread; C is [cell][5][nv].
+template <typename T, int MAXS>
+__global__ void __launch_bounds__(kFvThreads)
+fv_coef3_kernel(const T *__restrict__ f, T *__restrict__ C, FvTables<T> tb, FvTables3<T> t3,
+                const int *__restrict__ ncen, const int *__restrict__ cen, const int *__restrict__ nsec,
+                const int *__restrict__ sec, const int *__restrict__ order, int nv) {
+    const int64_t i = __ldg(order + blockIdx.x);
+    const int k = blockIdx.y * kFvThreads + threadIdx.x;
+    if (k >= nv) return;
+    const T fi = f[i * nv + k];
+    T c[kFvCoef3];
+#pragma unroll
+    for (int l = 0; l < kFvCoef3; ++l) c[l] = (T)0;
+    const int nc = __ldg(ncen + i);
+    const T *Rc = t3.Rc + i * kFvCoef3 * kFvCentral3;
+#pragma unroll
+    for (int q = 0; q < kFvCentral3; ++q) {
+        if (q < nc) {
+            const int j = __ldg(cen + i * kFvCentral3 + q);
+            const T d = f[(int64_t)j * nv + k] - fi;
+#pragma unroll
+            for (int l = 0; l < kFvCoef3; ++l) c[l] += __ldg(Rc + l * kFvCentral3 + q) * d;
+        }
+    }
+    const int ns = __ldg(nsec + i);
+    if (ns > 0) {
+        constexpr T kInvLam0 = (T)(4.0 / 3.0), kLam0 = (T)0.75, kEps = (T)1e-14;
+        const T lamL = (T)0.25 / (T)ns;
+        T sx[MAXS], sy[MAXS], sumx = (T)0, sumy = (T)0;
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s) {
+            sx[s] = sy[s] = (T)0;
+            if (s < ns) {
+                const int a = __ldg(sec + (i * kFvMaxFaces + s) * 2), b = __ldg(sec + (i * kFvMaxFaces + s) * 2 + 1);
+                const T *R = tb.Rs + (i * kFvMaxFaces + s) * 4;
+                const T da = f[(int64_t)a * nv + k] - fi, db = f[(int64_t)b * nv + k] - fi;
+                sx[s] = __ldg(R) * da + __ldg(R + 1) * db;
+                sy[s] = __ldg(R + 2) * da + __ldg(R + 3) * db;
+                sumx += sx[s];
+                sumy += sy[s];
+            }
+        }
+        T p0[kFvCoef3];
+        p0[0] = (c[0] - lamL * sumx) * kInvLam0;
+        p0[1] = (c[1] - lamL * sumy) * kInvLam0;
+#pragma unroll
+        for (int l = 2; l < kFvCoef3; ++l) p0[l] = c[l] * kInvLam0;
+        const T m20 = __ldg(t3.mu + 3 * i), m11 = __ldg(t3.mu + 3 * i + 1), m02 = __ldg(t3.mu + 3 * i + 2);
+        const T sig0 = p0[0] * p0[0] + p0[1] * p0[1] + (T)4 * p0[2] * p0[2] * m20 + (T)4 * p0[2] * p0[3] * m11 +
+                       p0[3] * p0[3] * m02 + p0[3] * p0[3] * m20 + (T)4 * p0[3] * p0[4] * m11 +
+                       (T)4 * p0[4] * p0[4] * m02 + (T)4 * p0[2] * p0[2] + p0[3] * p0[3] + (T)4 * p0[4] * p0[4];
+        T sig[MAXS], smin = sig0;
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s) {
+            sig[s] = sx[s] * sx[s] + sy[s] * sy[s];
+            if (s < ns) smin = fmin(smin, sig[s]);
+        }
+        const T num = smin + kEps;
+        auto ratio = [](T a, T b) {
+            if constexpr (sizeof(T) == 4) return __fdividef(a, b);
+            else return a / b;
+        };
+        T r = ratio(num, sig0 + kEps);
+        r = r * r;
+        T w = kLam0 * (r * r);
+        T wsum = w, acc[kFvCoef3];
+#pragma unroll
+        for (int l = 0; l < kFvCoef3; ++l) acc[l] = w * p0[l];
+#pragma unroll
+        for (int s = 0; s < MAXS; ++s)
+            if (s < ns) {
+                r = ratio(num, sig[s] + kEps);
+                r = r * r;
+                w = lamL * (r * r);
+                wsum += w;
+                acc[0] += w * sx[s];
+                acc[1] += w * sy[s];
+            }
+        const T iw = (T)1 / wsum;
+#pragma unroll
+        for (int l = 0; l < kFvCoef3; ++l) c[l] = acc[l] * iw;
+    }
+#pragma unroll
+    for (int l = 0; l < kFvCoef3; ++l) C[(i * kFvCoef3 + l) * nv + k] = c[l];
+}
+
+// Flux pass of degree 2: the reconstruction on both sides at the face's two
+// Gauss-Legendre points (weights 1/2), the Rusanov flux at each; transmissive
+// boundary faces take f_R = f_L.  One velocity per thread.
+template <typename T, int MAXF>
+__global__ void __launch_bounds__(kFvThreads)
+fv_flux3_kernel(const T *__restrict__ f, const T *__restrict__ C, T *__restrict__ L, FvTables<T> tb,
+                FvTables3<T> t3, const int *__restrict__ nface, const int *__restrict__ nb,
+                const int *__restrict__ order, int nv, int N, T Lv, T dv) {
+    const int64_t i = __ldg(order + blockIdx.x);
+    const int k = blockIdx.y * kFvThreads + threadIdx.x;
+    if (k >= nv) return;
+    const int nf = __ldg(nface + i);
+    const T fi = f[i * nv + k];
+    T ci[kFvCoef3];
+#pragma unroll
+    for (int l = 0; l < kFvCoef3; ++l) ci[l] = C[(i * kFvCoef3 + l) * nv + k];
+    const int j1 = k / N, j2 = k - j1 * N;
+    const T v1 = -Lv + (T)j1 * dv, v2 = -Lv + (T)j2 * dv;
+    T acc = (T)0;
+#pragma unroll
+    for (int q = 0; q < MAXF; ++q) {
+        if (q >= nf) continue;
+        const int64_t s = i * kFvMaxFaces + q;
+        const T vn = v1 * __ldg(tb.fn + 2 * s) + v2 * __ldg(tb.fn + 2 * s + 1);
+        const int jn = __ldg(nb + s);
+        T fj = (T)0, cj[kFvCoef3];
+#pragma unroll
+        for (int l = 0; l < kFvCoef3; ++l) cj[l] = (T)0;
+        if (jn >= 0) {
+            fj = f[(int64_t)jn * nv + k];
+#pragma unroll
+            for (int l = 0; l < kFvCoef3; ++l) cj[l] = C[((int64_t)jn * kFvCoef3 + l) * nv + k];
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const T *pi = t3.phi_i + (s * 2 + g) * kFvCoef3;
+            T fl = fi;
+#pragma unroll
+            for (int l = 0; l < kFvCoef3; ++l) fl += ci[l] * __ldg(pi + l);
+            T fr = fl;
+            if (jn >= 0) {
+                const T *pj = t3.phi_j + (s * 2 + g) * kFvCoef3;
+                fr = fj;
+#pragma unroll
+                for (int l = 0; l < kFvCoef3; ++l) fr += cj[l] * __ldg(pj + l);
+            }
+            acc += (T)0.25 * (vn * (fl + fr) - fabs(vn) * (fr - fl));
+        }
+    }
+    L[i * nv + k] = acc * __ldg(tb.inv_area + i);
+}
+
 template <typename T> const FvTables<T> &pick(const bz_mesh *m);
 template <> const FvTables<double> &pick<double>(const bz_mesh *m) { return m->t64; }
 template <> const FvTables<float> &pick<float>(const bz_mesh *m) { return m->t32; }
+template <typename T> const FvTables3<T> &pick3(const bz_mesh *m);
+template <> const FvTables3<double> &pick3<double>(const bz_mesh *m) { return m->u64; }
+template <> const FvTables3<float> &pick3<float>(const bz_mesh *m) { return m->u32; }
+
+template <typename T>
+cudaError_t coef3(const bz_mesh *m, const GridView &g, const T *f, T *C, cudaStream_t st) {
+    if (m->n_cells <= 0) return cudaSuccess;
+    const int nv = (int)g.nv;
+    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv + kFvThreads - 1) / kFvThreads));
+    if (m->max_faces <= 3)
+        fv_coef3_kernel<T, 3><<<grid, kFvThreads, 0, st>>>(f, C, pick<T>(m), pick3<T>(m), m->d_ncen3, m->d_cen3,
+                                                            m->d_nsec, m->d_sec, m->d_order, nv);
+    else
+        fv_coef3_kernel<T, kFvMaxFaces><<<grid, kFvThreads, 0, st>>>(f, C, pick<T>(m), pick3<T>(m), m->d_ncen3,
+                                                                      m->d_cen3, m->d_nsec, m->d_sec, m->d_order, nv);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t flux3(const bz_mesh *m, const GridView &g, const T *f, const T *C, T *L, cudaStream_t st) {
+    if (m->n_cells <= 0) return cudaSuccess;
+    const int nv = (int)g.nv;
+    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv + kFvThreads - 1) / kFvThreads));
+    if (m->max_faces <= 3)
+        fv_flux3_kernel<T, 3><<<grid, kFvThreads, 0, st>>>(f, C, L, pick<T>(m), pick3<T>(m), m->d_nface, m->d_nb,
+                                                            m->d_order, nv, g.N, (T)g.L, (T)g.dv);
+    else
+        fv_flux3_kernel<T, kFvMaxFaces><<<grid, kFvThreads, 0, st>>>(f, C, L, pick<T>(m), pick3<T>(m), m->d_nface,
+                                                                      m->d_nb, m->d_order, nv, g.N, (T)g.L, (T)g.dv);
+    return cudaGetLastError();
+}
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
@@ -500,6 +679,21 @@ cudaError_t launch_fv_flux_f64(const bz_mesh *m, const GridView &g, const double
 cudaError_t launch_fv_flux_f32(const bz_mesh *m, const GridView &g, const float *f, const float *G, float *L,
                                cudaStream_t st) {
     return flux<float>(m, g, f, G, L, st);
+}
+
+cudaError_t launch_fv_coef3_f64(const bz_mesh *m, const GridView &g, const double *f, double *C, cudaStream_t st) {
+    return coef3<double>(m, g, f, C, st);
+}
+cudaError_t launch_fv_coef3_f32(const bz_mesh *m, const GridView &g, const float *f, float *C, cudaStream_t st) {
+    return coef3<float>(m, g, f, C, st);
+}
+cudaError_t launch_fv_flux3_f64(const bz_mesh *m, const GridView &g, const double *f, const double *C, double *L,
+                                cudaStream_t st) {
+    return flux3<double>(m, g, f, C, L, st);
+}
+cudaError_t launch_fv_flux3_f32(const bz_mesh *m, const GridView &g, const float *f, const float *C, float *L,
+                                cudaStream_t st) {
+    return flux3<float>(m, g, f, C, L, st);
 }
 
 }  // namespace bz

@@ -486,3 +486,131 @@ def test_periodic_voronoi_matches_oracle(bz, fvo, order):
     got = bz.imex_step_fv(bz.Modes(bz.Grid(2, N, Lv), 0.0), m, to_dev(f, "fp64"), 2e-3, 5e-2, precision="fp64")
     bz.check()
     assert relerr(got.cpu().numpy(), want) < TOL64
+
+
+def _magnitude3(om, f, N, L, fvo):
+    """M_ik of the module docstring for the degree-2 reconstruction: each
+    coefficient bounded by the largest magnitude any CWENO polynomial of the
+    cell can give it (|R| applied to |f_j| + |f_i|; the weighted combination
+    is convex), the face values at the Gauss points by |f_i| + sum_l G_l
+    |phi_l|."""
+    v1, v2 = fvo.velocity_grid(N, L)
+    af = np.abs(np.asarray(f, dtype=np.float64))
+    n = len(om.cells)
+    G = np.zeros((n, 5, af.shape[1]))
+    basis = [fvo.quadratic_basis(om, i) for i in range(n)]
+    for i in range(n):
+        xb, h, mu = basis[i]
+        sub = np.array([0.0, 0.0, mu[2], mu[3], mu[4]])
+        st = om.central_stencil_shifted(i, count=11)
+        A = np.array([fvo._quadratic_means(om.xy[om.cells[j]] + s, xb, h) - sub for j, s in st])
+        R = np.abs(np.linalg.solve(A.T @ A, A.T))
+        gc = R @ (af[[j for j, _ in st]] + af[i])
+        polys = []
+        for a, sa, b, sb in om.sectors_shifted(i):
+            Rs = np.abs(np.linalg.inv(np.array([(om.bary[a] + sa - xb) / h, (om.bary[b] + sb - xb) / h])))
+            p = np.zeros_like(gc)
+            p[:2] = Rs @ np.stack([af[a] + af[i], af[b] + af[i]])
+            polys.append(p)
+        cand = [gc] + polys
+        if polys:
+            cand.append((gc + 0.25 * sum(polys) / len(polys)) / 0.75)
+        G[i] = np.max(cand, axis=0)
+    M = np.zeros_like(af)
+    for i, c in enumerate(om.cells):
+        for q, (j, ln, nx, ny, mx, my) in enumerate(om.faces[i]):
+            avn = ln * ((np.abs(v1) + 0.25 * L) * abs(nx) + (np.abs(v2) + 0.25 * L) * abs(ny))
+            xa, xe = om.xy[c[q]], om.xy[c[(q + 1) % len(c)]]
+            for t in fvo.GAUSS2:
+                x = xa + t * (xe - xa)
+                fl_ = af[i] + np.abs(fvo.quadratic_phi(x, *basis[i])) @ G[i]
+                fr_ = fl_ if j < 0 else af[j] + np.abs(fvo.quadratic_phi(x - om.face_shift[i][q], *basis[j])) @ G[j]
+                M[i] += 0.5 * avn * (fl_ + fr_)
+        M[i] /= om.area[i]
+    return M
+
+
+def _check3(got, want, om, fin, N, L, fvo, u, eta):
+    err = np.abs(got - want)
+    bound = 64 * (u * _magnitude3(om, fin, N, L, fvo) + eta * _magnitude3(om, np.ones_like(fin), N, L, fvo))
+    assert np.isfinite(got).all()
+    assert (err <= bound).all(), float((err / np.maximum(bound, 1e-300)).max())
+
+
+def _order3_meshes():
+    pts, tri = _tri(12)
+    vp, vc = workloads.periodic_voronoi(60, seed=12)
+    pp, pt = _periodic(8)
+    return {"tri": (pts, tri, None), "mixed": _mixed() + (None,), "voronoi_periodic": (vp, vc, (10.0, 10.0)),
+            "tri_periodic": (pp, pt, (10.0, 10.0))}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["tri", "mixed", "voronoi_periodic", "tri_periodic"])
+def test_order3_matches_oracle(bz, fvo, kind, precision):
+    """CWENO of degree 2 with two Gauss points per face (the third-order
+    scheme) against the oracle on triangles, a mixed mesh and periodic
+    triangle and Voronoi meshes, within the running-error bound."""
+    import torch
+    pts, cells, per = _order3_meshes()[kind]
+    N, Lv = 8, 8.0
+    om = fvo.Mesh(pts, cells, periodic=per)
+    if per is None:
+        f = workloads.mesh_states(om.bary, N, Lv, jump=True)
+    else:
+        f, _, _ = workloads.vortex_states(om.bary, N, Lv, t=0.7)
+    fin = as_input(f, precision)
+    m = bz.Mesh(pts, cells, order=3, periodic=per)
+    assert m.order == 3
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    out = torch.full(f.shape, float("nan"), dtype=dt, device="cuda")
+    Lr = bz.transport_residual(m, bz.Grid(2, N, Lv), to_dev(f, precision), out, precision=precision)
+    bz.check()
+    want = fvo.transport_residual(om, fin, N, Lv, order=3)
+    u, eta = (U64, ETA64) if precision == "fp64" else (U32, ETA32)
+    _check3(Lr.double().cpu().numpy(), want, om, fin, N, Lv, fvo, u, eta)
+
+
+def test_order3_imex_step_and_limits(bz, fvo):
+    """BPR(3,4,3) with the degree-2 transport (the paper's third-order
+    scheme) against the oracle's composed stages; walls are refused on an
+    order-3 mesh."""
+    import oracle
+    N, Lv, dt, eps = 8, 6.0, 2e-3, 5e-2
+    pts, cells = _tri(10)
+    om = fvo.Mesh(pts, cells)
+    f = workloads.mesh_states(om.bary, N, Lv, jump=True)
+    k = oracle.Kernel(2, N, Lv, 0.0)
+    s = bz.STAGES["bpr343"]
+    Lres = np.zeros((s,) + f.shape)
+    for l in range(s - 1):
+        _, F, _, _ = k.imex_step(f, dt, eps, scheme="bpr343", Lres=Lres, stages=True)
+        Lres[l] = fvo.transport_residual(om, F[l], N, Lv, order=3)
+    want = k.imex_step(f, dt, eps, scheme="bpr343", Lres=Lres)
+    m = bz.Mesh(pts, cells, order=3)
+    got = bz.imex_step_fv(bz.Modes(bz.Grid(2, N, Lv), 0.0), m, to_dev(f, "fp64"), dt, eps, scheme="bpr343",
+                          precision="fp64")
+    bz.check()
+    assert relerr(got.cpu().numpy(), want) < TOL64
+    with pytest.raises(bz.BzError):
+        m.set_walls(_boundary_edges_of(om)[:1], [(1.0, 0.0, 0.0)])
+
+
+def _boundary_edges_of(om):
+    return [om.face_vertices[i][q] for i, fl in enumerate(om.faces) for q, fc in enumerate(fl) if fc[0] < 0]
+
+
+def test_isentropic_vortex_third_order(bz):
+    """The third-order scheme (CWENO of degree 2, BPR(3,4,3)): Table conv_1e-2's
+    O3 column, third order in time for the density (the paper prints 2.9, 2.9;
+    errors 5.1e-8, 6.8e-9, 8.8e-10), and the space-time limit on Voronoi
+    meshes, faster than the second-order scheme on the finer pair."""
+    from paper_2103_14890_gb300 import convergence
+    modes = bz.Modes(bz.Grid(2, 30, 10.0), 0.0)
+    rows = convergence.time_study(1e-2, order=3, scheme="bpr343", modes=modes)
+    o = convergence.orders(rows, "rho_L1", by="dt")
+    assert min(o) > 2.8, (o, rows)
+    assert 5e-9 < rows[1]["rho_L1"] < 1e-7 and 5e-11 < rows[3]["rho_L1"] < 2e-9, rows
+    sp = convergence.space_study((2603, 5739), modes=modes, order=3, scheme="bpr343", mesh="voronoi")
+    o3 = convergence.orders(sp, "rho_L1")[0]
+    assert o3 > 2.3 and sp[-1]["rho_L1"] < 7e-3, (o3, sp)
