@@ -404,6 +404,36 @@ def _transport_measure(bz, workloads, st, check=True):
     bz.profile(False)
     out["fp32_walls"] = {"ms_per_call": msw, "wall_edges": int(len(bedges)),
                          "kernel_ms": {k: v[1] / max(1, v[0]) for k, v in profw.items()}}
+
+    def timed_residual(m, f, Lr, reps):
+        for _ in range(3):
+            bz.transport_residual(m, g, f, Lr, precision="fp32")
+        bz.check()
+        bz.profile(True)
+        ms = 0.0
+        for _ in range(reps):
+            flush.fill_(1)
+            ms += _timed(lambda: bz.transport_residual(m, g, f, Lr, precision="fp32"), 1, st)
+        prof = bz.profile_read()
+        bz.profile(False)
+        return ms / reps, {k: v[1] / max(1, v[0]) for k, v in prof.items()}
+
+    # the third-order residual (CWENO of degree 2, two Gauss points per face)
+    f = torch.from_numpy(fh).to("cuda", torch.float32)
+    Lr = torch.empty_like(f)
+    ms3, k3 = timed_residual(bz.Mesh(pts, tri, order=3), f, Lr, 10)
+    out["fp32_order3"] = {"ms_per_call": ms3, "kernel_ms": k3,
+                          "cell_velocity_updates_per_s": f.numel() / (ms3 / 1e3),
+                          "note": "5 coefficients per (cell, velocity) written and read back; one velocity per thread"}
+    # a periodic Voronoi mesh (the polygonal cells of the vortex study), orders 2 and 3
+    vp, vc = workloads.periodic_voronoi(2603)
+    vbary = np.array([np.asarray(vp)[c].mean(axis=0) for c in vc])
+    fv_ = torch.from_numpy(workloads.mesh_states(vbary / 10.0, N_V, L_BOX, jump=True)).to("cuda", torch.float32)
+    Lv = torch.empty_like(fv_)
+    for order in (2, 3):
+        msv, kv = timed_residual(bz.Mesh(vp, vc, order=order, periodic=(10.0, 10.0)), fv_, Lv, 10)
+        out["fp32_voronoi_order%d" % order] = {"ms_per_call": msv, "kernel_ms": kv, "cells": len(vc),
+                                              "cell_velocity_updates_per_s": fv_.numel() / (msv / 1e3)}
     # the coupled step
     hmesh = float(np.sqrt(np.abs(0.5 * ((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1]) -
                                         (P[:, 2, 0] - P[:, 0, 0]) * (P[:, 1, 1] - P[:, 0, 1]))).mean()))
