@@ -407,144 +407,189 @@ fv_flux_wall_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restr
 // xi and eta only), p_0 = (p_opt - lambda_L sum_L p_L) / lambda_0, and the
 // weights lambda_s / (sigma_s + eps)^4 in the same ratio form as degree 1,
 // sigma_s the cell mean of |h grad p|^2 plus the squared scaled second
-// derivatives (for the linear sectors: |h grad p|^2).  One velocity per
-// thread; C is [cell][5][nv].
-template <typename T, int MAXS>
+// derivatives (for the linear sectors: |h grad p|^2).  VEC velocities per
+// thread (4 on triangle meshes with aligned rows: the table entries, uniform
+// over the CTA, are then loaded once per 4 velocities); C is [cell][5][nv].
+template <typename T, int VEC, int MAXS>
 __global__ void __launch_bounds__(kFvThreads)
 fv_coef3_kernel(const T *__restrict__ f, T *__restrict__ C, FvTables<T> tb, FvTables3<T> t3,
                 const int *__restrict__ ncen, const int *__restrict__ cen, const int *__restrict__ nsec,
                 const int *__restrict__ sec, const int *__restrict__ order, int nv) {
     const int64_t i = __ldg(order + blockIdx.x);
-    const int k = blockIdx.y * kFvThreads + threadIdx.x;
+    const int k = (blockIdx.y * kFvThreads + threadIdx.x) * VEC;
     if (k >= nv) return;
-    const T fi = f[i * nv + k];
-    T c[kFvCoef3];
+    const Vec<T, VEC> fi = ldv<T, VEC>(f + i * nv + k);
+    T c[kFvCoef3][VEC];
 #pragma unroll
-    for (int l = 0; l < kFvCoef3; ++l) c[l] = (T)0;
+    for (int l = 0; l < kFvCoef3; ++l)
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) c[l][u] = (T)0;
     const int nc = __ldg(ncen + i);
     const T *Rc = t3.Rc + i * kFvCoef3 * kFvCentral3;
 #pragma unroll
     for (int q = 0; q < kFvCentral3; ++q) {
         if (q < nc) {
             const int j = __ldg(cen + i * kFvCentral3 + q);
-            const T d = f[(int64_t)j * nv + k] - fi;
+            const Vec<T, VEC> fj = ldv<T, VEC>(f + (int64_t)j * nv + k);
 #pragma unroll
-            for (int l = 0; l < kFvCoef3; ++l) c[l] += __ldg(Rc + l * kFvCentral3 + q) * d;
+            for (int l = 0; l < kFvCoef3; ++l) {
+                const T r = __ldg(Rc + l * kFvCentral3 + q);
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) c[l][u] += r * (fj.v[u] - fi.v[u]);
+            }
         }
     }
     const int ns = __ldg(nsec + i);
     if (ns > 0) {
         constexpr T kInvLam0 = (T)(4.0 / 3.0), kLam0 = (T)0.75, kEps = (T)1e-14;
         const T lamL = (T)0.25 / (T)ns;
-        T sx[MAXS], sy[MAXS], sumx = (T)0, sumy = (T)0;
+        T sx[MAXS][VEC], sy[MAXS][VEC];
 #pragma unroll
         for (int s = 0; s < MAXS; ++s) {
-            sx[s] = sy[s] = (T)0;
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) sx[s][u] = sy[s][u] = (T)0;
             if (s < ns) {
                 const int a = __ldg(sec + (i * kFvMaxFaces + s) * 2), b = __ldg(sec + (i * kFvMaxFaces + s) * 2 + 1);
                 const T *R = tb.Rs + (i * kFvMaxFaces + s) * 4;
-                const T da = f[(int64_t)a * nv + k] - fi, db = f[(int64_t)b * nv + k] - fi;
-                sx[s] = __ldg(R) * da + __ldg(R + 1) * db;
-                sy[s] = __ldg(R + 2) * da + __ldg(R + 3) * db;
-                sumx += sx[s];
-                sumy += sy[s];
+                const T r0 = __ldg(R), r1 = __ldg(R + 1), r2 = __ldg(R + 2), r3 = __ldg(R + 3);
+                const Vec<T, VEC> fa = ldv<T, VEC>(f + (int64_t)a * nv + k), fb = ldv<T, VEC>(f + (int64_t)b * nv + k);
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) {
+                    const T da = fa.v[u] - fi.v[u], db = fb.v[u] - fi.v[u];
+                    sx[s][u] = r0 * da + r1 * db;
+                    sy[s][u] = r2 * da + r3 * db;
+                }
             }
         }
-        T p0[kFvCoef3];
-        p0[0] = (c[0] - lamL * sumx) * kInvLam0;
-        p0[1] = (c[1] - lamL * sumy) * kInvLam0;
-#pragma unroll
-        for (int l = 2; l < kFvCoef3; ++l) p0[l] = c[l] * kInvLam0;
         const T m20 = __ldg(t3.mu + 3 * i), m11 = __ldg(t3.mu + 3 * i + 1), m02 = __ldg(t3.mu + 3 * i + 2);
-        const T sig0 = p0[0] * p0[0] + p0[1] * p0[1] + (T)4 * p0[2] * p0[2] * m20 + (T)4 * p0[2] * p0[3] * m11 +
-                       p0[3] * p0[3] * m02 + p0[3] * p0[3] * m20 + (T)4 * p0[3] * p0[4] * m11 +
-                       (T)4 * p0[4] * p0[4] * m02 + (T)4 * p0[2] * p0[2] + p0[3] * p0[3] + (T)4 * p0[4] * p0[4];
-        T sig[MAXS], smin = sig0;
-#pragma unroll
-        for (int s = 0; s < MAXS; ++s) {
-            sig[s] = sx[s] * sx[s] + sy[s] * sy[s];
-            if (s < ns) smin = fmin(smin, sig[s]);
-        }
-        const T num = smin + kEps;
         auto ratio = [](T a, T b) {
             if constexpr (sizeof(T) == 4) return __fdividef(a, b);
             else return a / b;
         };
-        T r = ratio(num, sig0 + kEps);
-        r = r * r;
-        T w = kLam0 * (r * r);
-        T wsum = w, acc[kFvCoef3];
 #pragma unroll
-        for (int l = 0; l < kFvCoef3; ++l) acc[l] = w * p0[l];
+        for (int u = 0; u < VEC; ++u) {
+            T sumx = (T)0, sumy = (T)0;
 #pragma unroll
-        for (int s = 0; s < MAXS; ++s)
-            if (s < ns) {
-                r = ratio(num, sig[s] + kEps);
-                r = r * r;
-                w = lamL * (r * r);
-                wsum += w;
-                acc[0] += w * sx[s];
-                acc[1] += w * sy[s];
+            for (int s = 0; s < MAXS; ++s) {
+                sumx += sx[s][u];
+                sumy += sy[s][u];
             }
-        const T iw = (T)1 / wsum;
+            T p0[kFvCoef3];
+            p0[0] = (c[0][u] - lamL * sumx) * kInvLam0;
+            p0[1] = (c[1][u] - lamL * sumy) * kInvLam0;
 #pragma unroll
-        for (int l = 0; l < kFvCoef3; ++l) c[l] = acc[l] * iw;
+            for (int l = 2; l < kFvCoef3; ++l) p0[l] = c[l][u] * kInvLam0;
+            const T sig0 = p0[0] * p0[0] + p0[1] * p0[1] + (T)4 * p0[2] * p0[2] * m20 + (T)4 * p0[2] * p0[3] * m11 +
+                           p0[3] * p0[3] * m02 + p0[3] * p0[3] * m20 + (T)4 * p0[3] * p0[4] * m11 +
+                           (T)4 * p0[4] * p0[4] * m02 + (T)4 * p0[2] * p0[2] + p0[3] * p0[3] + (T)4 * p0[4] * p0[4];
+            T sig[MAXS], smin = sig0;
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s) {
+                sig[s] = sx[s][u] * sx[s][u] + sy[s][u] * sy[s][u];
+                if (s < ns) smin = fmin(smin, sig[s]);
+            }
+            const T num = smin + kEps;
+            T r = ratio(num, sig0 + kEps);
+            r = r * r;
+            T w = kLam0 * (r * r);
+            T wsum = w, acc[kFvCoef3];
+#pragma unroll
+            for (int l = 0; l < kFvCoef3; ++l) acc[l] = w * p0[l];
+#pragma unroll
+            for (int s = 0; s < MAXS; ++s)
+                if (s < ns) {
+                    r = ratio(num, sig[s] + kEps);
+                    r = r * r;
+                    w = lamL * (r * r);
+                    wsum += w;
+                    acc[0] += w * sx[s][u];
+                    acc[1] += w * sy[s][u];
+                }
+            const T iw = (T)1 / wsum;
+#pragma unroll
+            for (int l = 0; l < kFvCoef3; ++l) c[l][u] = acc[l] * iw;
+        }
     }
 #pragma unroll
-    for (int l = 0; l < kFvCoef3; ++l) C[(i * kFvCoef3 + l) * nv + k] = c[l];
+    for (int l = 0; l < kFvCoef3; ++l) {
+        Vec<T, VEC> o;
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) o.v[u] = c[l][u];
+        stv<T, VEC>(C + (i * kFvCoef3 + l) * nv + k, o);
+    }
 }
 
 // Flux pass of degree 2: the reconstruction on both sides at the face's two
 // Gauss-Legendre points (weights 1/2), the Rusanov flux at each; transmissive
-// boundary faces take f_R = f_L.  One velocity per thread.
-template <typename T, int MAXF>
+// boundary faces take f_R = f_L.  VEC velocities of one grid row per thread
+// (the host takes VEC = 4 only when 4 divides N).
+template <typename T, int VEC, int MAXF>
 __global__ void __launch_bounds__(kFvThreads)
 fv_flux3_kernel(const T *__restrict__ f, const T *__restrict__ C, T *__restrict__ L, FvTables<T> tb,
                 FvTables3<T> t3, const int *__restrict__ nface, const int *__restrict__ nb,
                 const int *__restrict__ order, int nv, int N, T Lv, T dv) {
     const int64_t i = __ldg(order + blockIdx.x);
-    const int k = blockIdx.y * kFvThreads + threadIdx.x;
+    const int k = (blockIdx.y * kFvThreads + threadIdx.x) * VEC;
     if (k >= nv) return;
     const int nf = __ldg(nface + i);
-    const T fi = f[i * nv + k];
-    T ci[kFvCoef3];
+    const Vec<T, VEC> fi = ldv<T, VEC>(f + i * nv + k);
+    Vec<T, VEC> ci[kFvCoef3];
 #pragma unroll
-    for (int l = 0; l < kFvCoef3; ++l) ci[l] = C[(i * kFvCoef3 + l) * nv + k];
+    for (int l = 0; l < kFvCoef3; ++l) ci[l] = ldv<T, VEC>(C + (i * kFvCoef3 + l) * nv + k);
     const int j1 = k / N, j2 = k - j1 * N;
-    const T v1 = -Lv + (T)j1 * dv, v2 = -Lv + (T)j2 * dv;
-    T acc = (T)0;
+    const T v1 = -Lv + (T)j1 * dv;
+    T v2[VEC], acc[VEC];
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) {
+        v2[u] = -Lv + (T)(j2 + u) * dv;
+        acc[u] = (T)0;
+    }
 #pragma unroll
     for (int q = 0; q < MAXF; ++q) {
         if (q >= nf) continue;
         const int64_t s = i * kFvMaxFaces + q;
-        const T vn = v1 * __ldg(tb.fn + 2 * s) + v2 * __ldg(tb.fn + 2 * s + 1);
+        const T nx = __ldg(tb.fn + 2 * s), ny = __ldg(tb.fn + 2 * s + 1);
         const int jn = __ldg(nb + s);
-        T fj = (T)0, cj[kFvCoef3];
+        Vec<T, VEC> fj = fi, cj[kFvCoef3];
 #pragma unroll
-        for (int l = 0; l < kFvCoef3; ++l) cj[l] = (T)0;
+        for (int l = 0; l < kFvCoef3; ++l) cj[l] = ci[l];
         if (jn >= 0) {
-            fj = f[(int64_t)jn * nv + k];
+            fj = ldv<T, VEC>(f + (int64_t)jn * nv + k);
 #pragma unroll
-            for (int l = 0; l < kFvCoef3; ++l) cj[l] = C[((int64_t)jn * kFvCoef3 + l) * nv + k];
+            for (int l = 0; l < kFvCoef3; ++l) cj[l] = ldv<T, VEC>(C + ((int64_t)jn * kFvCoef3 + l) * nv + k);
         }
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
-            const T *pi = t3.phi_i + (s * 2 + g) * kFvCoef3;
-            T fl = fi;
+            T pi[kFvCoef3], pj[kFvCoef3];
 #pragma unroll
-            for (int l = 0; l < kFvCoef3; ++l) fl += ci[l] * __ldg(pi + l);
-            T fr = fl;
-            if (jn >= 0) {
-                const T *pj = t3.phi_j + (s * 2 + g) * kFvCoef3;
-                fr = fj;
-#pragma unroll
-                for (int l = 0; l < kFvCoef3; ++l) fr += cj[l] * __ldg(pj + l);
+            for (int l = 0; l < kFvCoef3; ++l) {
+                pi[l] = __ldg(t3.phi_i + (s * 2 + g) * kFvCoef3 + l);
+                pj[l] = jn >= 0 ? __ldg(t3.phi_j + (s * 2 + g) * kFvCoef3 + l) : (T)0;
             }
-            acc += (T)0.25 * (vn * (fl + fr) - fabs(vn) * (fr - fl));
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) {
+                T fl = fi.v[u];
+#pragma unroll
+                for (int l = 0; l < kFvCoef3; ++l) fl += ci[l].v[u] * pi[l];
+                T fr = fl;
+                if (jn >= 0) {
+                    fr = fj.v[u];
+#pragma unroll
+                    for (int l = 0; l < kFvCoef3; ++l) fr += cj[l].v[u] * pj[l];
+                }
+                const T vn = v1 * nx + v2[u] * ny;
+                acc[u] += (T)0.25 * (vn * (fl + fr) - fabs(vn) * (fr - fl));
+            }
         }
     }
-    L[i * nv + k] = acc * __ldg(tb.inv_area + i);
+    const T ia = __ldg(tb.inv_area + i);
+    Vec<T, VEC> o;
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) o.v[u] = acc[u] * ia;
+    stv<T, VEC>(L + i * nv + k, o);
 }
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 template <typename T> const FvTables<T> &pick(const bz_mesh *m);
 template <> const FvTables<double> &pick<double>(const bz_mesh *m) { return m->t64; }
@@ -557,13 +602,19 @@ template <typename T>
 cudaError_t coef3(const bz_mesh *m, const GridView &g, const T *f, T *C, cudaStream_t st) {
     if (m->n_cells <= 0) return cudaSuccess;
     const int nv = (int)g.nv;
-    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv + kFvThreads - 1) / kFvThreads));
-    if (m->max_faces <= 3)
-        fv_coef3_kernel<T, 3><<<grid, kFvThreads, 0, st>>>(f, C, pick<T>(m), pick3<T>(m), m->d_ncen3, m->d_cen3,
-                                                            m->d_nsec, m->d_sec, m->d_order, nv);
+    const bool v4 = m->max_faces <= 3 && nv % 4 == 0 && aligned16(f) && aligned16(C);
+    const int vec = v4 ? 4 : 1;
+    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / vec + kFvThreads - 1) / kFvThreads));
+    if (v4)
+        fv_coef3_kernel<T, 4, 3><<<grid, kFvThreads, 0, st>>>(f, C, pick<T>(m), pick3<T>(m), m->d_ncen3, m->d_cen3,
+                                                               m->d_nsec, m->d_sec, m->d_order, nv);
+    else if (m->max_faces <= 3)
+        fv_coef3_kernel<T, 1, 3><<<grid, kFvThreads, 0, st>>>(f, C, pick<T>(m), pick3<T>(m), m->d_ncen3, m->d_cen3,
+                                                               m->d_nsec, m->d_sec, m->d_order, nv);
     else
-        fv_coef3_kernel<T, kFvMaxFaces><<<grid, kFvThreads, 0, st>>>(f, C, pick<T>(m), pick3<T>(m), m->d_ncen3,
-                                                                      m->d_cen3, m->d_nsec, m->d_sec, m->d_order, nv);
+        fv_coef3_kernel<T, 1, kFvMaxFaces><<<grid, kFvThreads, 0, st>>>(f, C, pick<T>(m), pick3<T>(m), m->d_ncen3,
+                                                                         m->d_cen3, m->d_nsec, m->d_sec, m->d_order,
+                                                                         nv);
     return cudaGetLastError();
 }
 
@@ -571,17 +622,21 @@ template <typename T>
 cudaError_t flux3(const bz_mesh *m, const GridView &g, const T *f, const T *C, T *L, cudaStream_t st) {
     if (m->n_cells <= 0) return cudaSuccess;
     const int nv = (int)g.nv;
-    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv + kFvThreads - 1) / kFvThreads));
-    if (m->max_faces <= 3)
-        fv_flux3_kernel<T, 3><<<grid, kFvThreads, 0, st>>>(f, C, L, pick<T>(m), pick3<T>(m), m->d_nface, m->d_nb,
-                                                            m->d_order, nv, g.N, (T)g.L, (T)g.dv);
+    const bool v4 = m->max_faces <= 3 && g.N % 4 == 0 && aligned16(f) && aligned16(C) && aligned16(L);
+    const int vec = v4 ? 4 : 1;
+    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / vec + kFvThreads - 1) / kFvThreads));
+    if (v4)
+        fv_flux3_kernel<T, 4, 3><<<grid, kFvThreads, 0, st>>>(f, C, L, pick<T>(m), pick3<T>(m), m->d_nface, m->d_nb,
+                                                               m->d_order, nv, g.N, (T)g.L, (T)g.dv);
+    else if (m->max_faces <= 3)
+        fv_flux3_kernel<T, 1, 3><<<grid, kFvThreads, 0, st>>>(f, C, L, pick<T>(m), pick3<T>(m), m->d_nface, m->d_nb,
+                                                               m->d_order, nv, g.N, (T)g.L, (T)g.dv);
     else
-        fv_flux3_kernel<T, kFvMaxFaces><<<grid, kFvThreads, 0, st>>>(f, C, L, pick<T>(m), pick3<T>(m), m->d_nface,
-                                                                      m->d_nb, m->d_order, nv, g.N, (T)g.L, (T)g.dv);
+        fv_flux3_kernel<T, 1, kFvMaxFaces><<<grid, kFvThreads, 0, st>>>(f, C, L, pick<T>(m), pick3<T>(m),
+                                                                         m->d_nface, m->d_nb, m->d_order, nv, g.N,
+                                                                         (T)g.L, (T)g.dv);
     return cudaGetLastError();
 }
-
-bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 template <typename T, int VEC, int MAXS>
 void gradient_launch(const bz_mesh *m, int nv, const T *f, T *G, cudaStream_t st) {

@@ -614,3 +614,25 @@ def test_isentropic_vortex_third_order(bz):
     sp = convergence.space_study((2603, 5739), modes=modes, order=3, scheme="bpr343", mesh="voronoi")
     o3 = convergence.orders(sp, "rho_L1")[0]
     assert o3 > 2.3 and sp[-1]["rho_L1"] < 7e-3, (o3, sp)
+
+
+def test_order3_scalar_paths(bz, fvo):
+    """Degree 2 with one velocity per thread on a triangle mesh: N = 6 (4 does
+    not divide N) and rows that start off a 16-byte boundary."""
+    import torch
+    pts, cells = _tri(10)
+    om = fvo.Mesh(pts, cells)
+    m = bz.Mesh(pts, cells, order=3)
+    for N in (6, 8):
+        Lv = 6.0
+        f = workloads.mesh_states(om.bary, N, Lv, jump=True)
+        want = fvo.transport_residual(om, f, N, Lv, order=3)
+        g = bz.Grid(2, N, Lv)
+        buf = torch.zeros(f.size + 1, dtype=torch.float64, device="cuda")
+        fd = buf[1:].view(f.shape)
+        fd.copy_(torch.from_numpy(f))
+        out = torch.full((f.size + 1,), float("nan"), dtype=torch.float64, device="cuda")[1:].view(f.shape)
+        for src, dst in ((to_dev(f, "fp64"), None), (fd, out)):
+            Lr = bz.transport_residual(m, g, src, dst, precision="fp64")
+            bz.check()
+            _check3(Lr.cpu().numpy(), want, om, f, N, Lv, fvo, U64, ETA64)
