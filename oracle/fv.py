@@ -336,8 +336,11 @@ def reconstruct_quadratic(mesh, f, weights="nonlinear"):
     return C
 
 
-def _residual_quadratic(mesh, f, N, L, weights):
-    """L_{k,i} with the degree-2 reconstruction and 2 Gauss points per face."""
+def _residual_quadratic(mesh, f, N, L, weights, walls=None):
+    """L_{k,i} with the degree-2 reconstruction and 2 Gauss points per face; at
+    a wall face the mass balance of eq. MU holds at each Gauss point (the
+    point value of the outgoing flux against the wall Maxwellian's incoming
+    one)."""
     v1, v2 = velocity_grid(N, L)
     C = reconstruct_quadratic(mesh, f, weights)
     basis = [quadratic_basis(mesh, i) for i in range(len(f))]
@@ -347,10 +350,16 @@ def _residual_quadratic(mesh, f, N, L, weights):
         for q, (j, ln, nx, ny, mx, my) in enumerate(mesh.faces[i]):
             vn = v1 * nx + v2 * ny
             xa, xe = mesh.xy[c[q]], mesh.xy[c[(q + 1) % len(c)]]
+            wall = None if walls is None else walls.get(frozenset(mesh.face_vertices[i][q]))
             for t in GAUSS2:
                 x = xa + t * (xe - xa)
                 fl = f[i] + quadratic_phi(x, *basis[i]) @ C[i]
-                if j < 0:
+                if j < 0 and wall is not None:
+                    mw = wall_maxwellian(v1, v2, *wall)
+                    out_ = vn > 0
+                    mu = (fl * vn)[out_].sum() / (mw * -vn)[~out_].sum()
+                    fr = np.where(out_, fl, mu * mw)
+                elif j < 0:
                     fr = fl
                 else:
                     fr = f[j] + quadratic_phi(x - mesh.face_shift[i][q], *basis[j]) @ C[j]
@@ -377,9 +386,7 @@ def transport_residual(mesh, f, N, L, order=2, walls=None, weights="nonlinear"):
     normal; the velocity-cell volume cancels)."""
     f = np.asarray(f, dtype=np.float64)
     if order == 3:
-        if walls:
-            raise NotImplementedError("walls are built for orders 1 and 2")
-        return _residual_quadratic(mesh, f, N, L, weights)
+        return _residual_quadratic(mesh, f, N, L, weights, walls)
     v1, v2 = velocity_grid(N, L)
     g = reconstruct_gradients(mesh, f, order)
     out = np.zeros_like(f)

@@ -171,7 +171,7 @@ def _box_walls(m, theta=1.0, u=(0.0, 0.0)):
     return walls
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_walls_keep_the_wall_equilibrium(fv, order):
     """A gas at rest at the walls' temperature (any density) is an equilibrium
     of full accommodation (eq. BOU, eq. MU): the residual vanishes in every cell
@@ -191,7 +191,7 @@ def test_walls_keep_the_wall_equilibrium(fv, order):
     assert np.abs(Lw).max() > 1e-3 * scale
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_walls_conserve_mass(fv, order):
     """Diffuse reflection conserves mass at every wall face: in a closed box the
     total mass flux sum_i |P_i| sum_k L_ik vanishes for any state, also with
