@@ -313,8 +313,8 @@ int build_fv_mesh_periodic(int n_vertices, const double *xy, int64_t n_cells, co
  * A mesh with walls needs N divisible by 4 and N^2 <= 1024 in
  * transport_residual and imex_step_fv (BZ_ENOTSUP otherwise): one CTA forms
  * each cell's mu over all its velocities.
- * Errors: BZ_EINVAL (NULL mesh, not a boundary edge, theta_w <= 0), BZ_ENOTSUP
- * (an order-3 mesh: the wall flux is built for orders 1 and 2), BZ_ECUDA. */
+ * On an order-3 mesh the balance holds at each of the face's two Gauss points.
+ * Errors: BZ_EINVAL (NULL mesh, not a boundary edge, theta_w <= 0), BZ_ECUDA. */
 int fv_mesh_set_walls(bz_mesh *mesh, int64_t n_edges, const int64_t *edge_vertices, const double *wall_params);
 
 /* transport_residual -- <L(f^w)>_x of eq. ho for every cell and discrete

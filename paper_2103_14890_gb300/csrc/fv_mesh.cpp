@@ -604,7 +604,6 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
 // pairs (either order); n_edges = 0 removes every wall.
 int fv_mesh_set_walls(bz_mesh *m, int64_t n_edges, const int64_t *edges, const double *params) {
     if (!m) return fail(BZ_EINVAL, "fv_mesh_set_walls: mesh is NULL");
-    if (m->order == 3 && n_edges > 0) return fail(BZ_ENOTSUP, "fv_mesh_set_walls: walls are built for orders 1 and 2");
     if (n_edges < 0 || (n_edges > 0 && (!edges || !params)))
         return fail(BZ_EINVAL, "fv_mesh_set_walls: bad edge list");
     cudaFree(m->d_wall);

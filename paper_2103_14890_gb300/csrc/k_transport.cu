@@ -589,6 +589,132 @@ fv_flux3_kernel(const T *__restrict__ f, const T *__restrict__ C, T *__restrict_
     stv<T, VEC>(L + i * nv + k, o);
 }
 
+
+// Flux pass of degree 2 on a mesh with walls: as fv_flux_wall_kernel (one CTA
+// per cell, 4 velocities per thread, nv <= 1024), with the reconstruction at
+// the two Gauss points of every face; at a wall face the mass balance of
+// eq. MU holds at each Gauss point, so one block reduction forms the two
+// outgoing fluxes and the wall Maxwellian's incoming flux together.
+template <typename T, int MAXF, bool VLOAD>
+__global__ void __launch_bounds__(kFvThreads)
+fv_flux3_wall_kernel(const T *__restrict__ f, const T *__restrict__ C, T *__restrict__ L, FvTables<T> tb,
+                     FvTables3<T> t3, const int *__restrict__ nface, const int *__restrict__ nb,
+                     const int *__restrict__ order, const int *__restrict__ wall, const T *__restrict__ wallp, int nv,
+                     int N, T Lv, T dv) {
+    __shared__ double red[3 * (kFvThreads / 32)];
+    const int64_t i = __ldg(order + blockIdx.x);
+    const int kt = threadIdx.x * 4;
+    const bool act = kt < nv;
+    const int k = act ? kt : 0;                  // idle threads read row 0 and store nothing
+    const int nf = __ldg(nface + i);
+    const Vec<T, 4> fi = ld4<T, VLOAD>(f + i * nv + k);
+    Vec<T, 4> ci[kFvCoef3];
+#pragma unroll
+    for (int l = 0; l < kFvCoef3; ++l) ci[l] = ld4<T, VLOAD>(C + (i * kFvCoef3 + l) * nv + k);
+    const int j1 = k / N, j2 = k - j1 * N;
+    const T v1 = -Lv + (T)j1 * dv;
+    T v2[4], acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        v2[u] = -Lv + (T)(j2 + u) * dv;
+        acc[u] = (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < MAXF; ++q) {
+        if (q >= nf) continue;                   // uniform over the CTA (one cell)
+        const int64_t s = i * kFvMaxFaces + q;
+        const T nx = __ldg(tb.fn + 2 * s), ny = __ldg(tb.fn + 2 * s + 1);
+        const int jn = __ldg(nb + s);
+        Vec<T, 4> fj = fi, cj[kFvCoef3];
+#pragma unroll
+        for (int l = 0; l < kFvCoef3; ++l) cj[l] = ci[l];
+        if (jn >= 0) {
+            fj = ld4<T, VLOAD>(f + (int64_t)jn * nv + k);
+#pragma unroll
+            for (int l = 0; l < kFvCoef3; ++l) cj[l] = ld4<T, VLOAD>(C + ((int64_t)jn * kFvCoef3 + l) * nv + k);
+        }
+        T vn[4], fl[2][4], fr[2][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) vn[u] = v1 * nx + v2[u] * ny;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            T pi[kFvCoef3], pj[kFvCoef3];
+#pragma unroll
+            for (int l = 0; l < kFvCoef3; ++l) {
+                pi[l] = __ldg(t3.phi_i + (s * 2 + g) * kFvCoef3 + l);
+                pj[l] = jn >= 0 ? __ldg(t3.phi_j + (s * 2 + g) * kFvCoef3 + l) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                T a = fi.v[u];
+#pragma unroll
+                for (int l = 0; l < kFvCoef3; ++l) a += ci[l].v[u] * pi[l];
+                fl[g][u] = a;
+                T b = a;
+                if (jn >= 0) {
+                    b = fj.v[u];
+#pragma unroll
+                    for (int l = 0; l < kFvCoef3; ++l) b += cj[l].v[u] * pj[l];
+                }
+                fr[g][u] = b;
+            }
+        }
+        const int w = jn < 0 ? __ldg(wall + s) : -1;         // uniform over the CTA
+        if (w >= 0) {
+            const T th = __ldg(wallp + 3 * w), uw1 = __ldg(wallp + 3 * w + 1), uw2 = __ldg(wallp + 3 * w + 2);
+            const T inv2th = (T)0.5 / th, norm = (T)(0.15915494309189535) / th;   // 1 / (2 pi theta)
+            T mw[4];
+            double num0 = 0.0, num1 = 0.0, den = 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const T d1 = v1 - uw1, d2 = v2[u] - uw2;
+                mw[u] = norm * exp(-(d1 * d1 + d2 * d2) * inv2th);
+                if (act && vn[u] > (T)0) {
+                    num0 += (double)(fl[0][u] * vn[u]);
+                    num1 += (double)(fl[1][u] * vn[u]);
+                }
+                if (act && vn[u] < (T)0) den += (double)(mw[u] * -vn[u]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                num0 += __shfl_xor_sync(0xffffffffu, num0, o);
+                num1 += __shfl_xor_sync(0xffffffffu, num1, o);
+                den += __shfl_xor_sync(0xffffffffu, den, o);
+            }
+            __syncthreads();                     // red is reused face after face
+            if ((threadIdx.x & 31) == 0) {
+                red[3 * (threadIdx.x >> 5)] = num0;
+                red[3 * (threadIdx.x >> 5) + 1] = num1;
+                red[3 * (threadIdx.x >> 5) + 2] = den;
+            }
+            __syncthreads();
+            num0 = num1 = den = 0.0;
+#pragma unroll
+            for (int q2 = 0; q2 < kFvThreads / 32; ++q2) {
+                num0 += red[3 * q2];
+                num1 += red[3 * q2 + 1];
+                den += red[3 * q2 + 2];
+            }
+            const T mu0 = (T)(num0 / den), mu1 = (T)(num1 / den);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                fr[0][u] = vn[u] > (T)0 ? fl[0][u] : mu0 * mw[u];
+                fr[1][u] = vn[u] > (T)0 ? fl[1][u] : mu1 * mw[u];
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                acc[u] += (T)0.25 * (vn[u] * (fl[g][u] + fr[g][u]) - fabs(vn[u]) * (fr[g][u] - fl[g][u]));
+    }
+    if (act) {
+        const T ia = __ldg(tb.inv_area + i);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) L[i * nv + k + u] = acc[u] * ia;
+    }
+}
+
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 
 template <typename T> const FvTables<T> &pick(const bz_mesh *m);
@@ -622,6 +748,30 @@ template <typename T>
 cudaError_t flux3(const bz_mesh *m, const GridView &g, const T *f, const T *C, T *L, cudaStream_t st) {
     if (m->n_cells <= 0) return cudaSuccess;
     const int nv = (int)g.nv;
+    if (m->n_walls > 0) {
+        if (!fv_walls_supported(m, g)) return cudaErrorInvalidValue;
+        const T *wp = static_cast<const T *>(sizeof(T) == 8 ? static_cast<const void *>(m->d_wall64)
+                                                            : static_cast<const void *>(m->d_wall32));
+        const bool al = aligned16(f) && aligned16(C) && aligned16(L);
+        const unsigned grid = (unsigned)m->n_cells;
+        if (m->max_faces <= 3 && al)
+            fv_flux3_wall_kernel<T, 3, true><<<grid, kFvThreads, 0, st>>>(f, C, L, pick<T>(m), pick3<T>(m), m->d_nface,
+                                                                          m->d_nb, m->d_order, m->d_wall, wp, nv, g.N,
+                                                                          (T)g.L, (T)g.dv);
+        else if (m->max_faces <= 3)
+            fv_flux3_wall_kernel<T, 3, false><<<grid, kFvThreads, 0, st>>>(f, C, L, pick<T>(m), pick3<T>(m),
+                                                                           m->d_nface, m->d_nb, m->d_order, m->d_wall,
+                                                                           wp, nv, g.N, (T)g.L, (T)g.dv);
+        else if (al)
+            fv_flux3_wall_kernel<T, kFvMaxFaces, true><<<grid, kFvThreads, 0, st>>>(
+                f, C, L, pick<T>(m), pick3<T>(m), m->d_nface, m->d_nb, m->d_order, m->d_wall, wp, nv, g.N, (T)g.L,
+                (T)g.dv);
+        else
+            fv_flux3_wall_kernel<T, kFvMaxFaces, false><<<grid, kFvThreads, 0, st>>>(
+                f, C, L, pick<T>(m), pick3<T>(m), m->d_nface, m->d_nb, m->d_order, m->d_wall, wp, nv, g.N, (T)g.L,
+                (T)g.dv);
+        return cudaGetLastError();
+    }
     const bool v4 = m->max_faces <= 3 && g.N % 4 == 0 && aligned16(f) && aligned16(C) && aligned16(L);
     const int vec = v4 ? 4 : 1;
     const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / vec + kFvThreads - 1) / kFvThreads));

@@ -488,7 +488,7 @@ def test_periodic_voronoi_matches_oracle(bz, fvo, order):
     assert relerr(got.cpu().numpy(), want) < TOL64
 
 
-def _magnitude3(om, f, N, L, fvo):
+def _magnitude3(om, f, N, L, fvo, walls=None):
     """M_ik of the module docstring for the degree-2 reconstruction: each
     coefficient bounded by the largest magnitude any CWENO polynomial of the
     cell can give it (|R| applied to |f_j| + |f_i|; the weighted combination
@@ -521,18 +521,26 @@ def _magnitude3(om, f, N, L, fvo):
         for q, (j, ln, nx, ny, mx, my) in enumerate(om.faces[i]):
             avn = ln * ((np.abs(v1) + 0.25 * L) * abs(nx) + (np.abs(v2) + 0.25 * L) * abs(ny))
             xa, xe = om.xy[c[q]], om.xy[c[(q + 1) % len(c)]]
+            wall = None if (walls is None or j >= 0) else walls.get(frozenset(om.face_vertices[i][q]))
             for t in fvo.GAUSS2:
                 x = xa + t * (xe - xa)
                 fl_ = af[i] + np.abs(fvo.quadratic_phi(x, *basis[i])) @ G[i]
                 fr_ = fl_ if j < 0 else af[j] + np.abs(fvo.quadratic_phi(x - om.face_shift[i][q], *basis[j])) @ G[j]
+                if wall is not None:
+                    vn = v1 * nx + v2 * ny
+                    mw = fvo.wall_maxwellian(v1, v2, *wall)
+                    fr_ = fl_ + (fl_ * np.abs(vn))[vn > 0].sum() / (mw * np.abs(vn))[vn < 0].sum() * mw
                 M[i] += 0.5 * avn * (fl_ + fr_)
         M[i] /= om.area[i]
     return M
 
 
-def _check3(got, want, om, fin, N, L, fvo, u, eta):
+def _check3(got, want, om, fin, N, L, fvo, u, eta, walls=None):
+    """As _check (the wall constant included) with the degree-2 magnitudes."""
     err = np.abs(got - want)
-    bound = 64 * (u * _magnitude3(om, fin, N, L, fvo) + eta * _magnitude3(om, np.ones_like(fin), N, L, fvo))
+    C = 64 if walls is None else 64 + 4 * np.log2(N * N) + 16
+    bound = C * (u * _magnitude3(om, fin, N, L, fvo, walls) +
+                 eta * _magnitude3(om, np.ones_like(fin), N, L, fvo, walls))
     assert np.isfinite(got).all()
     assert (err <= bound).all(), float((err / np.maximum(bound, 1e-300)).max())
 
@@ -573,8 +581,7 @@ def test_order3_matches_oracle(bz, fvo, kind, precision):
 
 def test_order3_imex_step_and_limits(bz, fvo):
     """BPR(3,4,3) with the degree-2 transport (the paper's third-order
-    scheme) against the oracle's composed stages; walls are refused on an
-    order-3 mesh."""
+    scheme) against the oracle's composed stages."""
     import oracle
     N, Lv, dt, eps = 8, 6.0, 2e-3, 5e-2
     pts, cells = _tri(10)
@@ -592,12 +599,42 @@ def test_order3_imex_step_and_limits(bz, fvo):
                           precision="fp64")
     bz.check()
     assert relerr(got.cpu().numpy(), want) < TOL64
-    with pytest.raises(bz.BzError):
-        m.set_walls(_boundary_edges_of(om)[:1], [(1.0, 0.0, 0.0)])
 
 
-def _boundary_edges_of(om):
-    return [om.face_vertices[i][q] for i, fl in enumerate(om.faces) for q, fc in enumerate(fl) if fc[0] < 0]
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["tri", "mixed"])
+def test_order3_walls_match_oracle(bz, fvo, kind, precision):
+    """Walls with full accommodation on an order-3 mesh (the balance of
+    eq. MU at each Gauss point): the residual against the oracle, mass
+    conservation in the closed box, and the coupled BPR(3,4,3) step."""
+    N, Lv = 8, 6.0
+    pts, cells = _tri(12) if kind == "tri" else _mixed()
+    om = fvo.Mesh(pts, cells)
+    edges, params, walls = _walls(om)
+    f = workloads.mesh_states(om.bary, N, Lv, jump=True)
+    fin = as_input(f, precision)
+    m = bz.Mesh(pts, cells, order=3)
+    m.set_walls(edges, params)
+    Lr = bz.transport_residual(m, bz.Grid(2, N, Lv), to_dev(f, precision), precision=precision)
+    bz.check()
+    want = fvo.transport_residual(om, fin, N, Lv, order=3, walls=walls)
+    u, eta = (U64, ETA64) if precision == "fp64" else (U32, ETA32)
+    _check3(Lr.double().cpu().numpy(), want, om, fin, N, Lv, fvo, u, eta, walls)
+    if precision == "fp64":
+        tot = (om.area[:, None] * Lr.cpu().numpy()).sum()
+        assert abs(tot) < 1e-12 * (om.area[:, None] * np.abs(want)).sum()
+        import oracle
+        k = oracle.Kernel(2, N, Lv, 0.0)
+        s = bz.STAGES["bpr343"]
+        Lres = np.zeros((s,) + f.shape)
+        for l in range(s - 1):
+            _, F, _, _ = k.imex_step(f, 2e-3, 5e-2, scheme="bpr343", Lres=Lres, stages=True)
+            Lres[l] = fvo.transport_residual(om, F[l], N, Lv, order=3, walls=walls)
+        want_s = k.imex_step(f, 2e-3, 5e-2, scheme="bpr343", Lres=Lres)
+        got = bz.imex_step_fv(bz.Modes(bz.Grid(2, N, Lv), 0.0), m, to_dev(f, "fp64"), 2e-3, 5e-2,
+                              scheme="bpr343", precision="fp64")
+        bz.check()
+        assert relerr(got.cpu().numpy(), want_s) < TOL64
 
 
 def test_isentropic_vortex_third_order(bz):
