@@ -72,7 +72,7 @@ __device__ __forceinline__ void stv(T *__restrict__ p, const Vec<T, VEC> &r) {
 // with a predicate, so all neighbour rows of a cell are requested before the
 // first one is used (the kernels are latency-bound otherwise).
 template <typename T, int VEC, int MAXS>
-__global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4 && MAXS <= 3) ? 4 : 1)
+__global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4) ? 4 : 1)
 fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, const int *__restrict__ ncen,
                    const int *__restrict__ cen, const int *__restrict__ nsec, const int *__restrict__ sec,
                    const int *__restrict__ order, int nv) {
@@ -728,9 +728,8 @@ template <typename T>
 cudaError_t coef3(const bz_mesh *m, const GridView &g, const T *f, T *C, cudaStream_t st) {
     if (m->n_cells <= 0) return cudaSuccess;
     const int nv = (int)g.nv;
-    const bool al = nv % 4 == 0 && aligned16(f) && aligned16(C);
-    const bool v4 = m->max_faces <= 3 && al, p4 = m->max_faces > 3 && al && sizeof(T) == 4;
-    const int vec = (v4 || p4) ? 4 : 1;
+    const bool v4 = m->max_faces <= 3 && nv % 4 == 0 && aligned16(f) && aligned16(C);
+    const int vec = v4 ? 4 : 1;
     const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / vec + kFvThreads - 1) / kFvThreads));
     if (v4)
         fv_coef3_kernel<T, 4, 3><<<grid, kFvThreads, 0, st>>>(f, C, pick<T>(m), pick3<T>(m), m->d_ncen3, m->d_cen3,
@@ -738,12 +737,7 @@ cudaError_t coef3(const bz_mesh *m, const GridView &g, const T *f, T *C, cudaStr
     else if (m->max_faces <= 3)
         fv_coef3_kernel<T, 1, 3><<<grid, kFvThreads, 0, st>>>(f, C, pick<T>(m), pick3<T>(m), m->d_ncen3, m->d_cen3,
                                                                m->d_nsec, m->d_sec, m->d_order, nv);
-    else if (p4) {
-        if constexpr (sizeof(T) == 4)
-            fv_coef3_kernel<T, 4, kFvMaxFaces><<<grid, kFvThreads, 0, st>>>(f, C, pick<T>(m), pick3<T>(m),
-                                                                             m->d_ncen3, m->d_cen3, m->d_nsec,
-                                                                             m->d_sec, m->d_order, nv);
-    } else
+    else
         fv_coef3_kernel<T, 1, kFvMaxFaces><<<grid, kFvThreads, 0, st>>>(f, C, pick<T>(m), pick3<T>(m), m->d_ncen3,
                                                                          m->d_cen3, m->d_nsec, m->d_sec, m->d_order,
                                                                          nv);
@@ -779,6 +773,8 @@ cudaError_t flux3(const bz_mesh *m, const GridView &g, const T *f, const T *C, T
         return cudaGetLastError();
     }
     const bool al = g.N % 4 == 0 && aligned16(f) && aligned16(C) && aligned16(L);
+    // polygons in FP32 also take 4 velocities per thread here (measured: 0.082 -> 0.064 ms on a
+    // 2603-cell Voronoi mesh; the reconstruction passes lose occupancy to registers and keep 1)
     const bool v4 = m->max_faces <= 3 && al, p4 = m->max_faces > 3 && al && sizeof(T) == 4;
     const int vec = (v4 || p4) ? 4 : 1;
     const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / vec + kFvThreads - 1) / kFvThreads));
@@ -821,17 +817,12 @@ template <typename T>
 cudaError_t gradient(const bz_mesh *m, const GridView &g, const T *f, T *G, cudaStream_t st) {
     if (m->n_cells <= 0) return cudaSuccess;
     const int nv = (int)g.nv;
-    const bool al = nv % 4 == 0 && aligned16(f) && aligned16(G);
-    if (m->max_faces <= 3 && al)
+    if (m->max_faces <= 3 && nv % 4 == 0 && aligned16(f) && aligned16(G))
         gradient_launch<T, 4, 3>(m, nv, f, G, st);
     else if (m->max_faces <= 3)
         gradient_launch<T, 1, 3>(m, nv, f, G, st);
-    else if constexpr (sizeof(T) == 4) {             // polygons, FP32: 4 velocities per thread
-        if (al) gradient_launch<T, 4, kFvMaxFaces>(m, nv, f, G, st);
-        else gradient_launch<T, 1, kFvMaxFaces>(m, nv, f, G, st);
-    } else {
+    else
         gradient_launch<T, 1, kFvMaxFaces>(m, nv, f, G, st);
-    }
     return cudaGetLastError();
 }
 
@@ -869,26 +860,15 @@ cudaError_t flux(const bz_mesh *m, const GridView &g, const T *f, const T *G, T 
         return flux_walls<T>(m, g, f, G, L, st);
     }
     const bool tri = m->max_faces <= 3;
-    const bool al = g.N % 4 == 0 && aligned16(f) && aligned16(L) && (!G || aligned16(G));
-    const bool v4 = tri && al, p4 = !tri && al && sizeof(T) == 4;   // p4: polygons, FP32
+    const bool v4 = tri && g.N % 4 == 0 && aligned16(f) && aligned16(L) && (!G || aligned16(G));
     if (G) {
         if (v4) flux_launch<T, true, 4, 3>(m, g, f, G, L, st);
         else if (tri) flux_launch<T, true, 1, 3>(m, g, f, G, L, st);
-        else if constexpr (sizeof(T) == 4) {
-            if (p4) flux_launch<T, true, 4, kFvMaxFaces>(m, g, f, G, L, st);
-            else flux_launch<T, true, 1, kFvMaxFaces>(m, g, f, G, L, st);
-        } else {
-            flux_launch<T, true, 1, kFvMaxFaces>(m, g, f, G, L, st);
-        }
+        else flux_launch<T, true, 1, kFvMaxFaces>(m, g, f, G, L, st);
     } else {
         if (v4) flux_launch<T, false, 4, 3>(m, g, f, G, L, st);
         else if (tri) flux_launch<T, false, 1, 3>(m, g, f, G, L, st);
-        else if constexpr (sizeof(T) == 4) {
-            if (p4) flux_launch<T, false, 4, kFvMaxFaces>(m, g, f, G, L, st);
-            else flux_launch<T, false, 1, kFvMaxFaces>(m, g, f, G, L, st);
-        } else {
-            flux_launch<T, false, 1, kFvMaxFaces>(m, g, f, G, L, st);
-        }
+        else flux_launch<T, false, 1, kFvMaxFaces>(m, g, f, G, L, st);
     }
     return cudaGetLastError();
 }
