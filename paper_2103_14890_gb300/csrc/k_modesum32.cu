@@ -57,17 +57,14 @@ namespace bz {
 namespace {
 
 // Kernel variants: outputs per thread R along k_2, warps per CTA, cells per
-// CTA, and pk = 1 for the packed form (below).  Variant ids reported by
-// bz_modes_info are index + 1.
+// CTA.  Variant ids reported by bz_modes_info are index + 1.
 struct Variant {
-    int R, warps, cells, pk;
+    int R, warps, cells;
 };
 constexpr int kNumVariants = kModesumVariants;   // FP32 variants (timed by the autotuner)
-// entries 0..5: the FP32 variants (4 and 5 packed); entry 6: an FP64-only
-// layout (2 outputs per thread, 8 warps, 8-cell tiles) for grids whose FP64
-// spectrum needs it
-constexpr Variant kVariants[kNumVariants + 1] = {{8, 16, 32, 0}, {4, 32, 32, 0}, {4, 16, 16, 0}, {4, 16, 8, 0},
-                                                 {4, 16, 32, 1}, {4, 24, 32, 1}, {2, 8, 8, 0}};
+// entries 0..3: the FP32 variants; entry 4: an FP64-only layout (2 outputs per
+// thread, 8 warps, 8-cell tiles) for grids whose FP64 spectrum needs it
+constexpr Variant kVariants[kNumVariants + 1] = {{8, 16, 32}, {4, 32, 32}, {4, 16, 16}, {4, 16, 8}, {2, 8, 8}};
 constexpr int kTaskInts = 12;   // ints per task record
 
 constexpr int kPad = 8;         // zero guard columns before the first and after the last row
@@ -190,97 +187,7 @@ __device__ __forceinline__ void row_pass(const typename C2<T>::type *__restrict_
     if (blk < nblk) block_pass<T, RR, CS, WS, 0, DIR>(win, mp, lp, wrow + blk * RR * WS, acc);
 }
 
-// ---- packed form (FP32) ------------------------------------------------------
-// The same sum with two-lane FP32 instructions (fma.rn.f32x2 / mul.rn.f32x2,
-// one instruction for both halves of a complex value): per (l_2 step, output)
-//   p = (x_l, x_l) * (b_x, b_y) + (-+y_l, +-y_l) * (b_y, b_x)     (= f-hat_l b, or conj(f-hat_l) b)
-//   acc += (w, w) * p
-// three instructions instead of six; the weight stream stores every weight
-// twice (w, w) and the window keeps each f-hat_m also with its halves
-// swapped.  The kernel is issue-bound, so fewer instructions per pair is the
-// gain; the FMA work is the same.
-typedef unsigned long long u64;
-__device__ __forceinline__ u64 pk2(float a, float b) {
-    u64 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk2(u64 v, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
-    u64 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-    u64 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ u64 swap2(u64 v) {
-    float a, b;
-    upk2(v, a, b);
-    return pk2(b, a);
-}
-
-template <int RR, int CS, int WS, int PH, int DIR>
-__device__ __forceinline__ void block_pass_pk(u64 (&win)[2 * RR], u64 (&wsw)[2 * RR], const u64 *__restrict__ mp,
-                                              const u64 *__restrict__ lp, const u64 *__restrict__ wb,
-                                              u64 (&acc)[RR]) {
-#pragma unroll
-    for (int j = 0; j < RR; ++j) {
-        const u64 b = mp[j * CS];
-        win[(j + PH * RR) & (2 * RR - 1)] = b;
-        wsw[(j + PH * RR) & (2 * RR - 1)] = swap2(b);
-    }
-#pragma unroll
-    for (int s = 0; s < RR; ++s) {
-        float fx, fy;
-        upk2(lp[s * DIR * CS], fx, fy);
-        const u64 flx = pk2(fx, fx);
-        const u64 fly = DIR > 0 ? pk2(-fy, fy) : pk2(fy, -fy);
-        u64 wv[RR];
-#pragma unroll
-        for (int q = 0; q < RR; q += 2) {
-            const ulonglong2 w2 = *reinterpret_cast<const ulonglong2 *>(wb + s * WS + q);
-            wv[q] = w2.x;
-            wv[q + 1] = w2.y;
-        }
-#pragma unroll
-        for (int r = 0; r < RR; ++r) {
-            const int slot = (r - s + RR - 1 + PH * RR) & (2 * RR - 1);
-            u64 p = mul2(flx, win[slot]);
-            p = fma2(fly, wsw[slot], p);
-            acc[r] = fma2(wv[r], p, acc[r]);
-        }
-    }
-}
-
-template <int RR, int CS, int WS, int DIR>
-__device__ __forceinline__ void row_pass_pk(const u64 *__restrict__ rowl, const u64 *__restrict__ rowm,
-                                            const u64 *__restrict__ wrow, int nblk, int l2lo, int mbase0,
-                                            u64 (&acc)[RR]) {
-    u64 win[2 * RR], wsw[2 * RR];
-    const u64 *mp = rowm + mbase0 * CS;
-    const u64 *lp = rowl + DIR * l2lo * CS;
-#pragma unroll
-    for (int j = RR; j < 2 * RR - 1; ++j) {
-        win[j] = mp[j * CS];
-        wsw[j] = swap2(win[j]);
-    }
-    int blk = 0;
-    for (; blk + 1 < nblk; blk += 2) {
-        block_pass_pk<RR, CS, WS, 0, DIR>(win, wsw, mp, lp, wrow + blk * RR * WS, acc);
-        block_pass_pk<RR, CS, WS, 1, DIR>(win, wsw, mp - RR * CS, lp + RR * DIR * CS, wrow + (blk + 1) * RR * WS,
-                                          acc);
-        mp -= 2 * RR * CS;
-        lp += 2 * RR * DIR * CS;
-    }
-    if (blk < nblk) block_pass_pk<RR, CS, WS, 0, DIR>(win, wsw, mp, lp, wrow + blk * RR * WS, acc);
-}
-
-template <typename T, int RR, int WARPS, int CELLS, bool PK = false>
+template <typename T, int RR, int WARPS, int CELLS>
 __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Group gd) {
     using V2 = typename C2<T>::type;
     constexpr int G = 32 / CELLS;     // lane groups splitting a task's outputs
@@ -327,12 +234,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
         const int rowf = tk.rowf;                         // elements per row pair
         const T *wsrc = W + tk.woff;
         V2 hi[RR], lo[RR], acc[RR];
-        u64 pacc[RR];                                     // packed form: (x, y) of acc in one register pair
 #pragma unroll
-        for (int r = 0; r < RR; ++r) {
-            hi[r] = lo[r] = acc[r] = cmk<V2>(0, 0);
-            pacc[r] = 0ull;
-        }
+        for (int r = 0; r < RR; ++r) hi[r] = lo[r] = acc[r] = cmk<V2>(0, 0);
         const int k20 = tk.k20 + grp * RR;                // this thread's first output column
         const int mbase0 = k20 - tk.l2lo - (RR - 1);
         stage_row(wbuf0, wsrc, rowf * (int)sizeof(T), lane);
@@ -348,34 +251,15 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
             // row header: element offsets of the rows of l and m, and the
             // direction of l (-1: f-hat_l = conj(f-hat_{-l}), row of -l read backwards)
             const int4 hd = *reinterpret_cast<const int4 *>(wcur);
-            if constexpr (PK) {
-                static_assert(sizeof(T) == 4, "the packed form is FP32");
-                const u64 *rl = reinterpret_cast<const u64 *>(F0 + hd.x), *rm = reinterpret_cast<const u64 *>(F0 + hd.y);
-                const u64 *wr = reinterpret_cast<const u64 *>(wcur + HEAD) + grp * RR;
-                if (hd.z > 0)
-                    row_pass_pk<RR, CELLS, RT, 1>(rl, rm, wr, tk.nblk * G, tk.l2lo, mbase0, pacc);
-                else
-                    row_pass_pk<RR, CELLS, RT, -1>(rl, rm, wr, tk.nblk * G, tk.l2lo, mbase0, pacc);
-            } else {
-                if (hd.z > 0)
-                    row_pass<T, RR, CELLS, RT, 1>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G, tk.l2lo,
-                                                  mbase0, acc);
-                else
-                    row_pass<T, RR, CELLS, RT, -1>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G,
-                                                   tk.l2lo, mbase0, acc);
-            }
+            if (hd.z > 0)
+                row_pass<T, RR, CELLS, RT, 1>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G, tk.l2lo,
+                                              mbase0, acc);
+            else
+                row_pass<T, RR, CELLS, RT, -1>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G,
+                                               tk.l2lo, mbase0, acc);
             __syncwarp();
             // fold the row sums (<= 4 rows) into (hi, lo)
             if ((i & 3) == 3 || i + 1 == tk.nrows) {
-                if constexpr (PK) {
-#pragma unroll
-                    for (int r = 0; r < RR; ++r) {
-                        float ax, ay;
-                        upk2(pacc[r], ax, ay);
-                        acc[r] = cmk<V2>(ax, ay);
-                        pacc[r] = 0ull;
-                    }
-                }
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
                     T s, e;
@@ -478,8 +362,7 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                 t.nblk = nblk;
                 t.woff = (int)W.size();
                 t.rfirst = std::max(0, prev_end + 1 - k20);
-                const int dup = kVariants[v].pk ? 2 : 1;        // the packed form stores every weight twice
-                t.rowf = HEAD + npad * R * dup;
+                t.rowf = HEAD + npad * R;
                 t.pad0 = t.pad1 = t.pad2 = t.pad3 = 0;
                 prev_end = k2last;
                 for (const Pair &p : pairs) {
@@ -512,7 +395,7 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                                 w = beta_host(m, l, mm);
                                 if (p.l[0] < p.m[0]) w += beta_host(m, mm, l);
                             }
-                            for (int q = 0; q < dup; ++q) W.push_back((T)w);
+                            W.push_back((T)w);
                         }
                     }
                 }
@@ -565,12 +448,12 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
 
 bool modesum32_available(const bz_modes *m) { return m->d_W32 != nullptr; }
 
-template <typename T, int RR, int WARPS, int CELLS, bool PK = false>
+template <typename T, int RR, int WARPS, int CELLS>
 static cudaError_t launch_instance(const Mode32Group &gd, size_t sm, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(modesum32_kernel<T, RR, WARPS, CELLS, PK>,
+    cudaError_t e = cudaFuncSetAttribute(modesum32_kernel<T, RR, WARPS, CELLS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    modesum32_kernel<T, RR, WARPS, CELLS, PK><<<(unsigned)gd.tile_start[gd.nitems], WARPS * 32, sm, st>>>(gd);
+    modesum32_kernel<T, RR, WARPS, CELLS><<<(unsigned)gd.tile_start[gd.nitems], WARPS * 32, sm, st>>>(gd);
     return cudaGetLastError();
 }
 
@@ -580,8 +463,6 @@ static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStr
         case 1: return launch_instance<float, 4, 32, 32>(gd, sm, st);
         case 2: return launch_instance<float, 4, 16, 16>(gd, sm, st);
         case 3: return launch_instance<float, 4, 16, 8>(gd, sm, st);
-        case 4: return launch_instance<float, 4, 16, 32, true>(gd, sm, st);
-        case 5: return launch_instance<float, 4, 24, 32, true>(gd, sm, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -620,8 +501,8 @@ static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, 
 
 // FP64 form: the same kernel on double spectra and weights, on 16-cell tiles
 // (variant entry 2) or, where the double spectrum of 16 cells does not fit
-// shared memory (48^2), on 8-cell tiles (the last entry); no last-wave split.
-constexpr int kFp64Variants[2] = {2, kNumVariants};
+// shared memory (48^2), on 8-cell tiles (entry 4); no last-wave split.
+constexpr int kFp64Variants[2] = {2, 4};
 
 bool modesum64_available(const bz_modes *m) { return m->w64 != nullptr; }
 
