@@ -524,7 +524,7 @@ fv_coef3_kernel(const T *__restrict__ f, T *__restrict__ C, FvTables<T> tb, FvTa
 // boundary faces take f_R = f_L.  VEC velocities of one grid row per thread
 // (the host takes VEC = 4 only when 4 divides N).
 template <typename T, int VEC, int MAXF>
-__global__ void __launch_bounds__(kFvThreads)
+__global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4 && MAXF <= 3) ? 3 : 1)
 fv_flux3_kernel(const T *__restrict__ f, const T *__restrict__ C, T *__restrict__ L, FvTables<T> tb,
                 FvTables3<T> t3, const int *__restrict__ nface, const int *__restrict__ nb,
                 const int *__restrict__ order, int nv, int N, T Lv, T dv) {
