@@ -49,10 +49,13 @@ def test_host_side_argument_errors(lib):
     assert lib.bz_fast_info(None, (ctypes.c_int64 * 4)()) == b.EINVAL
     assert lib.build_fv_mesh(0, None, 1, None, None, 2, ctypes.byref(out)) == b.EINVAL
     assert lib.build_fv_mesh_periodic(0, None, 1, None, None, 2, 10.0, 10.0, ctypes.byref(out)) == b.EINVAL
+    assert lib.bz_modes_set_penalty(None, 3.0) == b.EINVAL
     xy = (ctypes.c_double * 6)(0, 0, 1, 0, 0, 1)
     ptr = (ctypes.c_int64 * 2)(0, 3)
     vtx = (ctypes.c_int64 * 3)(0, 1, 2)
     assert lib.build_fv_mesh_periodic(3, xy, 1, ptr, vtx, 2, -1.0, 0.0, ctypes.byref(out)) == b.EINVAL
+    for order in (0, 4):                                     # orders 1, 2, 3 only
+        assert lib.build_fv_mesh(3, xy, 1, ptr, vtx, order, ctypes.byref(out)) == b.EINVAL
     assert lib.transport_residual(None, None, 1, None, None, None) == b.EINVAL
     assert lib.bz_mesh_info(None, (ctypes.c_int64 * 5)()) == b.EINVAL
     assert lib.imex_step_fv(None, None, 0, 0, 0.1, 1.0, None, None, 1, 0, None) == b.EINVAL
