@@ -52,7 +52,7 @@ exactly.
   - the face integrals use the 2-point Gauss-Legendre rule on every edge
     (exact for the cubic v.n p along a straight edge).
 
-Readings of points the paper leaves open (each listed in the design notes):
+Readings of points the paper leaves open:
   - central stencil: the 5 cells nearest to P_i by barycentre distance
     among the cells that share a vertex with P_i or with one of its
     vertex neighbours (ties by cell index);
