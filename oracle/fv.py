@@ -232,8 +232,9 @@ def velocity_grid(N, L):
     return V1.ravel(), V2.ravel()
 
 
-def reconstruct_gradients(mesh, f, order):
-    """CWENO gradient g (n_cells, 2, nv) of f^w in every cell; zero for order 1."""
+def reconstruct_gradients(mesh, f, order, weights="nonlinear"):
+    """CWENO gradient g (n_cells, 2, nv) of f^w in every cell; zero for order 1;
+    weights="linear" returns the optimal (least-squares) gradient."""
     f = np.asarray(f, dtype=np.float64)
     n, nv = f.shape
     g = np.zeros((n, 2, nv))
@@ -245,7 +246,7 @@ def reconstruct_gradients(mesh, f, order):
         d = np.array([f[j] - f[i] for j, _ in st])                          # (5, nv)
         g_opt = np.linalg.solve(A.T @ A, A.T @ d)       # normal equations of the least-squares fit
         secs = mesh.sectors_shifted(i)
-        if not secs:
+        if weights == "linear" or not secs:
             g[i] = g_opt
             continue
         lam_l = (1.0 - LAMBDA0) / len(secs)
@@ -375,7 +376,7 @@ def wall_maxwellian(v1, v2, theta, u1, u2):
 
 def transport_residual(mesh, f, N, L, order=2, walls=None, weights="nonlinear"):
     """L_{k,i} of the module docstring for f of shape (n_cells, N*N); order 1,
-    2 (degree 0, 1) or 3 (degree 2; weights="linear" keeps p_opt).
+    2 (degree 0, 1) or 3 (degree 2); weights="linear" keeps p_opt (for pins).
 
     walls: optional {frozenset({a, b}): (theta_w, u_w1, u_w2)} for boundary
     edges with vertices a, b that are walls with full accommodation
@@ -388,7 +389,7 @@ def transport_residual(mesh, f, N, L, order=2, walls=None, weights="nonlinear"):
     if order == 3:
         return _residual_quadratic(mesh, f, N, L, weights, walls)
     v1, v2 = velocity_grid(N, L)
-    g = reconstruct_gradients(mesh, f, order)
+    g = reconstruct_gradients(mesh, f, order, weights)
     out = np.zeros_like(f)
     for i in range(len(f)):
         acc = np.zeros(f.shape[1])

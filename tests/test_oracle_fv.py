@@ -339,3 +339,67 @@ def test_degree2_weights_cut_overshoots(fv):
     n_w = count(fv.reconstruct_quadratic(m, f))
     n_opt = count(fv.reconstruct_quadratic(m, f, weights="linear"))
     assert n_opt > 40 and n_w < n_opt / 2, (n_w, n_opt)
+
+
+def _tri_quadrature_means(P, fn, levels=3):
+    """Mean of fn over the polygon P (counter-clockwise), by splitting its fan
+    triangles `levels` times into four and applying the 3-point interior rule
+    (points at (2/3, 1/6, 1/6), exact for quadratics) on each piece."""
+    tris = [(P[0], P[t], P[t + 1]) for t in range(1, len(P) - 1)]
+    for _ in range(levels):
+        nxt = []
+        for a, b, c in tris:
+            ab, bc, ca = (a + b) / 2, (b + c) / 2, (c + a) / 2
+            nxt += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]
+        tris = nxt
+    tot, area = 0.0, 0.0
+    for a, b, c in tris:
+        at = 0.5 * ((b[0] - a[0]) * (c[1] - a[1]) - (c[0] - a[0]) * (b[1] - a[1]))
+        for w in ((2 / 3, 1 / 6, 1 / 6), (1 / 6, 2 / 3, 1 / 6), (1 / 6, 1 / 6, 2 / 3)):
+            x = w[0] * a + w[1] * b + w[2] * c
+            tot = tot + at / 3 * fn(x[0], x[1])
+        area += at
+    return tot / area
+
+
+def test_residual_truncation_error_rates(fv):
+    """On a smooth periodic field the residual with the optimal polynomial
+    approximates the cell mean of v . grad f with an error of O(h) for degree 1
+    and O(h^2) for degree 2 (a face value off by O(h^{M+1}) over faces of
+    length h, divided by |P| ~ h^2).  Cell means by a refined triangle
+    quadrature, independent of the oracle's; periodic triangulations with 8,
+    16 and 32 nodes a side; the 2 x 2 velocity grid on [-1, 1) gives the
+    velocities (-1, -1), (-1, 0), (0, -1), (0, 0).  With the nonlinear weights
+    (eps = 1e-14, r = 4) degree 2 still beats degree 1, but the weights pull it
+    off p_opt near the field's smooth extrema (measured rates 1.1 and 1.7)."""
+    k = 2 * np.pi / 10.0
+
+    def fx(x, y):
+        return 2.0 + np.sin(k * x) * np.cos(k * y) + 0.5 * np.cos(k * (x + 2 * y))
+
+    def grad(x, y):
+        return np.array([k * np.cos(k * x) * np.cos(k * y) - 0.5 * k * np.sin(k * (x + 2 * y)),
+                         -k * np.sin(k * x) * np.sin(k * y) - k * np.sin(k * (x + 2 * y))])
+
+    v1, v2 = fv.velocity_grid(2, 1.0)
+    errs, hs = {}, []
+    for n in (8, 16, 32):
+        pts, tri = workloads.periodic_triangulation(n, 10.0, 10.0, seed=5, jitter=0.1)
+        m = fv.Mesh(pts, tri, periodic=(10.0, 10.0))
+        fbar = np.array([_tri_quadrature_means(m.xy[c], fx) for c in m.cells])
+        gbar = np.array([_tri_quadrature_means(m.xy[c], grad) for c in m.cells])     # (n, 2)
+        want = gbar[:, :1] * v1[None, :] + gbar[:, 1:] * v2[None, :]
+        f = np.tile(fbar[:, None], (1, 4))
+        hs.append(np.sqrt(m.area).mean())
+        for order in (2, 3):
+            for w in ("linear", "nonlinear"):
+                Lr = fv.transport_residual(m, f, 2, 1.0, order=order, weights=w)
+                errs.setdefault((order, w), []).append(np.abs(Lr - want).mean())
+
+    def rate(key):
+        e = errs[key]
+        return np.log(e[1] / e[2]) / np.log(hs[1] / hs[2])
+
+    assert 0.8 < rate((2, "linear")) < 1.3 and 1.85 < rate((3, "linear")) < 2.4, errs
+    assert errs[(3, "linear")][2] < errs[(2, "linear")][2] / 5
+    assert errs[(3, "nonlinear")][2] < errs[(2, "nonlinear")][2], errs
