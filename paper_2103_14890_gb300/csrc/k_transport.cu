@@ -193,7 +193,7 @@ fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, c
 }
 
 template <typename T, bool kGrad, int VEC, int MAXF>
-__global__ void __launch_bounds__(kFvThreads)
+__global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4 && MAXF <= 3) ? 4 : 1)
 fv_flux_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__ L, FvTables<T> tb,
                const int *__restrict__ nface, const int *__restrict__ nb, const int *__restrict__ order, int nv,
                int N, T Lv, T dv) {
