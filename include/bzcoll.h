@@ -396,31 +396,38 @@ int bz_profile_read(char *names, int names_bytes, double *total_ms, int64_t *lau
                     int max_kernels);
 
 /* collide_batch_noalloc -- the same operator as collide_batch, for callers
- * that cannot allocate device memory: code running inside a CUDA stream
- * capture whose graph may not contain allocation nodes, hosts that have handed
- * their whole device-memory budget to their own allocator, or loops that must
- * not meet an allocation failure or its latency part-way through.  The paper
- * has no counterpart; this is a deployment convenience of the library.
+ * that cannot allocate device memory: applications whose device memory is
+ * owned by another allocator (a framework's caching allocator, or a host
+ * program that reserved the whole device up front), where an allocation by
+ * this library would fail or eat into that budget, and real-time loops that
+ * must not meet an allocation's latency or an allocation failure part-way
+ * through a run.  The paper has no counterpart; this is a deployment
+ * convenience of the library.
  *
- * The call requests no device memory: the Fourier scratch of the cells lives
- * in one file-scope __device__ array of 32 MiB, which every GPU that loads the
- * library holds until the process exits.  That bounds the batch: with S =
- * 32 MiB, at most floor(S / (2 * 32 * H * c)) * 32 cells per call, H = half-
- * spectrum modes (bz_modes_info out[4]), c = 8 bytes (BZ_FP32) or 16 (BZ_FP64)
- * -- 4224 cells of a 32x32 grid in FP32, 2112 in FP64.  Larger n_cells are
- * rejected with BZ_EINVAL and a message giving the limit.
+ * The call requests no device memory and launches exactly the kernels of
+ * collide_batch (same results, bit for bit): the Fourier scratch of the cells
+ * lives in one file-scope __device__ array of 32 MiB, which every GPU that
+ * loads the library holds until the process exits.  That bounds the batch:
+ * with S = 32 MiB, at most floor(S / (2 * 32 * H * c)) * 32 cells per call,
+ * H = half-spectrum modes (bz_modes_info out[4]), c = 8 bytes (BZ_FP32) or 16
+ * (BZ_FP64) -- 4224 cells of a 32x32 grid in FP32, 2112 in FP64, 1856 of a
+ * 48x48 grid in FP32.  Larger n_cells are rejected with BZ_EINVAL and a
+ * message giving the limit.
  *   precision : BZ_FP32 or BZ_FP64
  *   flags     : 0 or BZ_CONSERVE (BZ_CHECK_INPUT is not accepted: its error
  *               word would be allocated on first use)
  *   f, Q, n_cells, stream : as for collide_batch; the device that owns the
  *               modes handle must be current.
  * Every call shares the one array and the array keeps the last call's
- * contents; nothing in it needs to start at zero (each value a call reads was
+ * contents; nothing in it needs to start at zero (each value a call uses was
  * written earlier by the same call).  Calls that overlap on the GPU (on
  * different streams, or from several host threads without ordering) race on
- * the array and produce wrong results: order them.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture that should contain these calls.
+ * the array and produce wrong results: order them.  Set-up: the first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and keeps it for the life of the process; make that
+ * first call before any stream capture begins, and do not call
+ * cudaDeviceReset on a device after its first call (the kept address would be
+ * stale).
  * Errors: BZ_EINVAL (arguments, size limit, wrong current device), BZ_ECUDA. */
 int collide_batch_noalloc(const bz_modes *m, int precision, int flags, const void *f, void *Q,
                           int64_t n_cells, void *stream);

@@ -308,6 +308,19 @@ void orc_beta_table(const orc_kernel *k, double *beta) {
     }
 }
 
+/* beta-hat for a list of (l, m) pairs given by flat mode indices: the
+ * weights of the terms of eq. CF1 (all pairs the truncated sum visits have
+ * l + m in K_h, which the radial cache covers). */
+void orc_beta_pairs(const orc_kernel *k, int64_t n, const int64_t *li, const int64_t *mi, double *out) {
+    const orc_grid *g = &k->g;
+    for (int64_t p = 0; p < n; ++p) {
+        int l[3], m[3];
+        mode_index(g, li[p], l);
+        mode_index(g, mi[p], m);
+        out[p] = orc_beta(k, l, m);
+    }
+}
+
 /* ---------------------------------------------------------- transforms --- */
 
 /* 1-D exponentials E[k+h][j] = e^{-i k u_j} with u_j = -pi + 2 pi j / N,

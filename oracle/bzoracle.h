@@ -88,6 +88,8 @@ double orc_Bhat(const orc_kernel *k, const int *l, const int *m);
 double orc_beta(const orc_kernel *k, const int *l, const int *m);
 /* Full table beta[lidx * nm + midx] (nm^2 doubles) for small grids. */
 void   orc_beta_table(const orc_kernel *k, double *beta);
+/* beta-hat(l, m) for n pairs of flat mode indices li[p], mi[p] */
+void   orc_beta_pairs(const orc_kernel *k, int64_t n, const int64_t *li, const int64_t *mi, double *out);
 
 /* Steps of one collision evaluation (one cell). */
 void   orc_dft_forward(const orc_grid *g, const double *f, double *fhat);

@@ -66,6 +66,7 @@ def load():
     lib.orc_beta.argtypes = [P(_Kernel), _p, _p]
     lib.orc_beta.restype = _d
     lib.orc_beta_table.argtypes = [P(_Kernel), _p]
+    lib.orc_beta_pairs.argtypes = [P(_Kernel), _i64, _p, _p, _p]
     lib.orc_dft_forward.argtypes = [P(_Grid), _p, _p]
     lib.orc_mode_sum.argtypes = [P(_Kernel), _p, _p]
     lib.orc_dft_inverse.argtypes = [P(_Grid), _p, _d, _p]
@@ -163,6 +164,14 @@ class Kernel:
         t = np.zeros((self.nm, self.nm))
         load().orc_beta_table(ctypes.byref(self._k), _ptr(t))
         return t
+
+    def beta_pairs(self, li, mi):
+        """beta-hat(l, m) for arrays of flat mode indices (row-major, k_i + h)."""
+        li = np.ascontiguousarray(li, dtype=np.int64)
+        mi = np.ascontiguousarray(mi, dtype=np.int64)
+        out = np.zeros(li.shape[0])
+        load().orc_beta_pairs(ctypes.byref(self._k), li.shape[0], _ptr(li), _ptr(mi), _ptr(out))
+        return out
 
     # transforms ---------------------------------------------------------
     def dft_forward(self, f):

@@ -566,6 +566,19 @@ int64_t host_chunk_cells(int dev) {
 
 }  // namespace
 
+// collide_chain on caller-provided Fourier scratch of collide_scratch_bytes()
+// bytes (the allocation-free entry point, noalloc.cu): the same kernels and
+// launches as collide_batch, no allocation.
+size_t collide_scratch_size(const bz_modes *m, int precision, int64_t n) {
+    return collide_scratch_bytes(m, precision, n);
+}
+
+int collide_on_scratch(const bz_modes *m, int precision, int flags, const void *f, void *Q, int64_t n,
+                       void *scratch, cudaStream_t st) {
+    if (!scratch) return fail(BZ_EINVAL, "collide: scratch is NULL");
+    return collide_chain(m, precision, flags, f, Q, nullptr, n, st, scratch);
+}
+
 int *device_error_word() {
     int dev = current_device();
     if (dev < 0 || dev >= kMaxDevices) return nullptr;

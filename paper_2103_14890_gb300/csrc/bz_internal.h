@@ -275,4 +275,11 @@ cudaError_t launch_fv_flux_f32(const bz_mesh *mesh, const GridView &g, const flo
 // Device error word of the current device (allocated on first use; api.cu).
 int *device_error_word();
 
+// One collision evaluation (forward DFT, mode sum, inverse DFT; the launches of
+// collide_batch) with the Fourier scratch at `scratch`, which must hold
+// collide_scratch_size() bytes; requests no device memory (api.cu).
+size_t collide_scratch_size(const bz_modes *m, int precision, int64_t n);
+int collide_on_scratch(const bz_modes *m, int precision, int flags, const void *f, void *Q, int64_t n,
+                       void *scratch, cudaStream_t st);
+
 }  // namespace bz

@@ -1,19 +1,30 @@
 """Parity of the CUDA collision operator with the FP64 oracle (C ABI calls).
 
-Plain FP64 form: <= 1e-12 relative L2 against the oracle.  FP32 form: the
-error bound derived for FP32 arithmetic under gain/loss cancellation (see the
-tolerances below), against the oracle on the same FP32-rounded input.
+Plain FP64 form: <= 1e-12 relative L2 against the oracle, and element by
+element.  FP32 form, against the oracle on the same FP32-rounded input:
+  * on the shifted-Maxwellian workload (Mach 0-3) the target of the mixed
+    form, rel-L2 <= 1e-6 over all cells and velocities (TARGET32);
+  * in every FP32 case, every cell within the bounds derived from the
+    rounding count (gpu_util.fp32_cell_bounds): its L2 error and each
+    element's error against u times the cell's absolute mode sum, which a
+    localised defect (a wrong weight row, a wrong mode, a wrong cell of a
+    ragged tile) exceeds by orders of magnitude;
+  * TOL32 = 1e-5 rel-L2 only where the inputs carry 5 % point noise or 48^2 /
+    3-D grids: there the FP32 floor itself (FP32 spectra, products and
+    accumulation under the gain/loss cancellation) is 1e-6 to 4e-6, above the
+    target; the FP32X2 form is the one that meets 1e-6 there.
 """
 import numpy as np
 import pytest
 
 from paper_2103_14890_gb300 import workloads
-from gpu_util import as_input, bz_module, relerr, to_dev
+from gpu_util import AbsModeSum, as_input, bz_module, check_fp32_cells, relerr, to_dev
 
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
 TOL32 = 1e-5
+TARGET32 = 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -79,8 +90,11 @@ def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, dim, N, variant):
     fin = as_input(f, "fp32")
     Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32")
     bz.check()
-    Qr = oracle_k(dim, N, L, 1.0).collide(fin)
-    assert relerr(Q.double().cpu().numpy(), Qr) < TOL32
+    k = oracle_k(dim, N, L, 1.0)
+    Qr = k.collide(fin)
+    Qg = Q.double().cpu().numpy()
+    assert relerr(Qg, Qr) < TOL32
+    check_fp32_cells(k, fin, Qg, Qr, what="variant %d N=%d d=%d" % (variant, N, dim))
 
 
 def test_last_wave_split_is_exact(bz, monkeypatch):
@@ -118,8 +132,11 @@ def test_fp32_3d_16_grid_8_cell_tiles(bz, oracle_k, n):
     fin = as_input(f, "fp32")
     Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32")
     bz.check()
-    Qr = oracle_k(3, N, L, 1.0).collide(fin)
-    assert relerr(Q.double().cpu().numpy(), Qr) < TOL32
+    k = oracle_k(3, N, L, 1.0)
+    Qr = k.collide(fin)
+    Qg = Q.double().cpu().numpy()
+    assert relerr(Qg, Qr) < TOL32
+    check_fp32_cells(k, fin, Qg, Qr, what="16^3 n=%d" % n)
 
 
 @pytest.mark.parametrize("n", [1, 16, 17, 45])
@@ -133,8 +150,11 @@ def test_fp32_48_grid_16_cell_tiles(bz, oracle_k, n):
     fin = as_input(f, "fp32")
     Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32")
     bz.check()
-    Qr = oracle_k(2, N, L, 1.0).collide(fin)
-    assert relerr(Q.double().cpu().numpy(), Qr) < TOL32
+    k = oracle_k(2, N, L, 1.0)
+    Qr = k.collide(fin)
+    Qg = Q.double().cpu().numpy()
+    assert relerr(Qg, Qr) < TOL32
+    check_fp32_cells(k, fin, Qg, Qr, what="48^2 n=%d" % n)
 
 
 def test_fp64_small_config_matches_oracle(bz, oracle_k):
@@ -206,22 +226,33 @@ def test_fp64_three_dimensional(bz, oracle_k):
 
 @pytest.mark.parametrize("seed,kind", [(1003, "shifted"), (1002, "noise")])
 def test_fp32_matches_oracle(bz, oracle_k, seed, kind):
+    """70 cells (2 full tiles and a ragged tail) of the benchmark's workload
+    (shifted Maxwellians, Mach 0-3): the mixed form's 1e-6 target.  The 5 %
+    noise inputs of the 4096-cell configuration sit above it in FP32 (below
+    target: their FP32 floor is ~2.5e-6) and are held to the per-cell bounds
+    and TOL32."""
     if kind == "shifted":
         f = workloads.shifted_maxwellians(70, 2, 32, 10.0, seed=seed)
     else:
         f = workloads.bi_maxwellian(70, 2, 32, 10.0, seed=seed, noise=0.05)
     Q = _gpu_collide(bz, 2, 32, 10.0, 1.0, f, "fp32")
-    Qr = oracle_k(2, 32, 10.0, 1.0).collide(as_input(f, "fp32"))
+    fin = as_input(f, "fp32")
+    k = oracle_k(2, 32, 10.0, 1.0)
+    Qr = k.collide(fin)
     err = relerr(Q, Qr)
     print("fp32 %s rel-L2 %.3e" % (kind, err))
-    assert err < TOL32
+    assert err < (TARGET32 if kind == "shifted" else TOL32)
+    check_fp32_cells(k, fin, Q, Qr, what="fp32 " + kind)
 
 
 def test_fp32_three_dimensional(bz, oracle_k):
     f = workloads.bi_maxwellian(33, 3, 8, 8.0, seed=12)
     Q = _gpu_collide(bz, 3, 8, 8.0, 1.0, f, "fp32")
-    Qr = oracle_k(3, 8, 8.0, 1.0).collide(as_input(f, "fp32"))
+    fin = as_input(f, "fp32")
+    k = oracle_k(3, 8, 8.0, 1.0)
+    Qr = k.collide(fin)
     assert relerr(Q, Qr) < TOL32
+    check_fp32_cells(k, fin, Q, Qr, what="fp32 3-D 8^3")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -291,21 +322,32 @@ def test_deterministic_and_mass_conserving(bz, precision, N):
 
 def test_full_size_fp32_sampled(bz, oracle_k):
     """65536 cells, 32^2, VHS, shifted Maxwellians (Mach 0-3): the launch the
-    benchmark times; sampled cells against the oracle."""
+    benchmark times.  4096 sampled cells (every 16th, and both ends of the
+    batch) against the oracle at the 1e-6 target; 256 of them also against
+    the per-cell bounds."""
     n = 65536
     f = workloads.shifted_maxwellians(n, 2, 32, 10.0, seed=1003).astype(np.float32)
     Q = _gpu_collide(bz, 2, 32, 10.0, 1.0, f, "fp32")
-    idx = np.array([0, 1, 31, 32, 4097, 30000, 65503, 65535])
-    Qr = oracle_k(2, 32, 10.0, 1.0).collide(f[idx].astype(np.float64))
-    assert relerr(Q[idx], Qr) < TOL32
     assert np.isfinite(Q).all()
+    idx = np.unique(np.concatenate([np.arange(0, n, 16), [1, 31, 32, 65503, 65535]]))
+    k = oracle_k(2, 32, 10.0, 1.0)
+    Qr = k.collide(f[idx].astype(np.float64))
+    err = relerr(Q[idx], Qr)
+    print("full-size fp32 rel-L2 over %d cells: %.3e" % (len(idx), err))
+    assert err < TARGET32
+    sub = np.arange(0, len(idx), len(idx) // 256)
+    check_fp32_cells(k, f[idx[sub]].astype(np.float64), Q[idx[sub]], Qr[sub], what="full-size fp32")
 
 
-def test_full_size_fp64_sampled(bz, oracle_k):
-    """4096 cells, 32^2, VHS, bi-Maxwellian with 5% noise (plain form)."""
+def test_full_size_fp64_every_cell(bz, oracle_k):
+    """4096 cells, 32^2, VHS, bi-Maxwellian with 5% noise (plain form): every
+    cell against the oracle, element by element."""
     n = 4096
     f = workloads.bi_maxwellian(n, 2, 32, 10.0, seed=1002, noise=0.05)
     Q = _gpu_collide(bz, 2, 32, 10.0, 1.0, f, "fp64")
-    idx = np.array([0, 33, 2047, 4064, 4095])
-    Qr = oracle_k(2, 32, 10.0, 1.0).collide(f[idx])
-    assert relerr(Q[idx], Qr) < TOL64
+    Qr = oracle_k(2, 32, 10.0, 1.0).collide(f)
+    assert relerr(Q, Qr) < TOL64
+    cellmax = np.abs(Qr).max(axis=1, keepdims=True)
+    worst = (np.abs(Q - Qr) / cellmax).max()
+    print("fp64 config 2: rel-L2 %.3e, worst element / cell max %.3e" % (relerr(Q, Qr), worst))
+    assert worst < TOL64

@@ -149,6 +149,77 @@ def test_conservation_fix(oracle_mod):
         assert np.abs(k.conserve(qc) - qc).max() < 1e-13 * np.abs(q).max()
 
 
+def test_conservation_fix_is_the_orthogonal_projection(oracle_mod):
+    """Reading of the conservation fix: the smallest L2 change of Q that zeroes
+    the discrete moments of 1, v, |v|^2.  That is the orthogonal projection onto
+    the complement of span{1, v_1, v_2, |v|^2}: the change Q - Q_c lies in that
+    span (a least-squares fit onto it leaves only rounding), and no other change
+    with zero moments is smaller.  A projection weighted by anything but a
+    constant (an oblique one) also zeroes the moments but fails the first
+    check."""
+    k = oracle_mod.Kernel(2, 32, 10.0, 1.0)
+    f = workloads.bi_maxwellian(3, 2, 32, 10.0, seed=21, noise=0.05)
+    Q = k.collide(f, conserve=False)
+    Qc = k.collide(f, conserve=True)
+    v = k.velocities()
+    V1, V2 = np.meshgrid(v, v, indexing="ij")
+    C = np.stack([np.ones(V1.size), V1.ravel(), V2.ravel(), (V1 ** 2 + V2 ** 2).ravel()], axis=1)
+    rng = np.random.default_rng(4)
+    for q, qc in zip(Q, Qc):
+        dq = q - qc
+        coef, *_ = np.linalg.lstsq(C, dq, rcond=None)
+        assert np.linalg.norm(dq - C @ coef) < 1e-12 * np.linalg.norm(dq)
+        # any other zero-moment correction q - z (z + another span element
+        # moved off the span) is larger: perturb by vectors orthogonal to the span
+        for _ in range(3):
+            r = rng.normal(size=q.size)
+            r -= C @ np.linalg.lstsq(C, r, rcond=None)[0]
+            r *= 1e-3 * np.linalg.norm(dq) / np.linalg.norm(r)
+            assert np.abs(C.T @ (qc + r)).max() < 1e-10 * np.abs(q).sum() * 200
+            assert np.linalg.norm(q - (qc + r)) > np.linalg.norm(dq)
+    # an oblique projection with weights w(v) = 1 + |v|^2 / 100 zeroes the
+    # moments too, but moves Q off the span: the first check rejects it
+    wv = 1 + (V1 ** 2 + V2 ** 2).ravel() / 100
+    q = Q[0]
+    Cw = C * wv[:, None]
+    y = np.linalg.solve(C.T @ Cw, C.T @ q)
+    qo = q - Cw @ y
+    assert np.abs(C.T @ qo).max() < 1e-10 * np.abs(q).sum() * 200
+    dq = q - qo
+    coef, *_ = np.linalg.lstsq(C, dq, rcond=None)
+    assert np.linalg.norm(dq - C @ coef) > 1e-3 * np.linalg.norm(dq)
+
+
+def test_abs_mode_sum_error_scale(oracle_mod):
+    """The error scale of the GPU parity tests (tests/gpu_util.AbsModeSum):
+    A_k = sum_{l+m=k} |beta(l,m)| |f-hat_l| |f-hat_m|.  It bounds |Q-hat_k| (the
+    triangle inequality on eq. CF1), is quadratic in f, and one output equals a
+    brute-force loop over the pairs with the oracle's beta(l, m)."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from gpu_util import AbsModeSum
+    N = 6
+    k = oracle_mod.Kernel(2, N, 5.0, 1.0)
+    f = workloads.bi_maxwellian(2, 2, N, 5.0, seed=7, noise=0.05)
+    A = AbsModeSum(k)(f)
+    for c in range(2):
+        fh = k.dft_forward(f[c])
+        qh = k.mode_sum(fh).ravel()
+        assert (A[c] >= np.abs(qh) * (1 - 1e-12)).all()
+        assert A[c].max() > 2 * np.abs(qh).max()           # gain and loss cancel in Q-hat
+        kk = (1, -1)
+        h = k.h
+        brute = 0.0
+        for l1 in range(-h, h + 1):
+            for l2 in range(-h, h + 1):
+                m = (kk[0] - l1, kk[1] - l2)
+                if max(abs(m[0]), abs(m[1])) > h:
+                    continue
+                brute += abs(k.beta((l1, l2), m)) * abs(fh[l1 + h, l2 + h]) * abs(fh[m[0] + h, m[1] + h])
+        assert abs(A[c].reshape(k.M, k.M)[kk[0] + h, kk[1] + h] - brute) < 1e-13 * brute
+    assert np.allclose(AbsModeSum(k)(3 * f), 9 * A, rtol=1e-13)
+
+
 def _bkw(r2, t):
     S = 1 - math.exp(-t / 8) / 2
     return np.exp(-r2 / (2 * S)) / (2 * math.pi * S ** 2) * (2 * S - 1 + (1 - S) / (2 * S) * r2)
