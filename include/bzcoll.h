@@ -58,9 +58,22 @@ extern "C" {
  *   BZ_FP64   : every step in FP64 (the plain form).
  *   BZ_FP32   : DFTs and the mode sum in FP32 with compensated accumulation
  *               of the mode sum; moments, Maxwellian and the conservation
- *               fix in FP64. */
+ *               fix in FP64.
+ *   BZ_FP32X2 : FP32 arrays in and out (as BZ_FP32); the forward DFT in FP64,
+ *               the mode sum of eq. CF1 in double-float arithmetic on the FP32
+ *               pipe (spectra and weights as FP32 high and low parts, every
+ *               product split exactly by FMA, every running sum by TwoSum:
+ *               the compensated dot product of Ogita, Rump and Oishi), Q-hat
+ *               rounded to FP32, the inverse DFT and the IMEX stage arithmetic
+ *               as BZ_FP32.  Its error against the FP64 operator is the FP32
+ *               rounding of the result and of the inverse DFT, independent of
+ *               the gain/loss cancellation that bounds BZ_FP32.  Served for
+ *               the direct sum (build_kernel_modes) on 2-D grids with N <= 48
+ *               and 3-D grids with N <= 16; other handles return BZ_ENOTSUP.
+ *               Not accepted by collide_batch_noalloc or transport_residual. */
 #define BZ_FP64    0
 #define BZ_FP32    1
+#define BZ_FP32X2  2
 
 /* flags */
 #define BZ_CONSERVE     1  /* project Q so its discrete moments of 1, v, |v|^2 vanish */

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libbzcoll.so")
 HEADER = os.path.join(ROOT, "include", "bzcoll.h")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTSUP, ETIMEOUT, ENONFINITE = 0, -1, -2, -3, -4, -5, -6
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "fp32x2": 2}
 CONSERVE, CHECK_INPUT = 1, 2
 SCHEME = {"ars222": 0, "bpr343": 1, "euler": 2}
 STAGES = {"ars222": 3, "bpr343": 5, "euler": 2}

@@ -190,8 +190,11 @@ bool tableau(int scheme, Tableau &t) {
 
 int check_modes(const bz_modes *m, int precision, const char *who) {
     if (!m || !m->g) return fail(BZ_EINVAL, std::string(who) + ": modes handle is NULL");
-    if (precision != BZ_FP64 && precision != BZ_FP32)
+    if (precision != BZ_FP64 && precision != BZ_FP32 && precision != BZ_FP32X2)
         return fail(BZ_EINVAL, std::string(who) + ": unknown precision");
+    if (precision == BZ_FP32X2 && (m->method != 0 || !modesum_x2_available(m)))
+        return fail(BZ_ENOTSUP, std::string(who) + ": the FP32X2 form serves the direct sum on 2-D grids with "
+                                                    "N <= 48 and 3-D grids with N <= 16");
     return BZ_OK;
 }
 
@@ -201,7 +204,16 @@ int check_modes(const bz_modes *m, int precision, const char *who) {
 int phase_forward(const bz_modes *m, int precision, const void *f, void *fh, int64_t n, cudaStream_t st) {
     const bz_grid *g = m->g;
     const GridView &v = g->v;
-    if (precision == BZ_FP64 && m->tile_dft) {
+    if (precision == BZ_FP32X2 && m->tile_dft) {
+        BZ_LAUNCH("dft_forward_x2", st,
+                  launch_dft64_forward_tile_f32in(v, static_cast<const float *>(f), static_cast<double2 *>(fh), n, st),
+                  "collide: forward DFT");
+    } else if (precision == BZ_FP32X2) {
+        BZ_LAUNCH("dft_forward_x2_generic", st,
+                  launch_dft_forward_f64_f32in(v, g->d_E64, static_cast<const float *>(f), static_cast<double2 *>(fh),
+                                               n, st),
+                  "collide: forward DFT");
+    } else if (precision == BZ_FP64 && m->tile_dft) {
         BZ_LAUNCH("dft_forward_f64", st,
                   launch_dft64_forward_tile(v, static_cast<const double *>(f), static_cast<double2 *>(fh), n, st),
                   "collide: forward DFT");
@@ -223,7 +235,11 @@ int phase_forward(const bz_modes *m, int precision, const void *f, void *fh, int
 
 int phase_modesum(const bz_modes *m, int precision, const void *fh, void *qh, int64_t n, cudaStream_t st) {
     const GridView &v = m->g->v;
-    if (m->method == 1 && precision == BZ_FP64) {
+    if (precision == BZ_FP32X2) {
+        BZ_LAUNCH("modesum_x2", st,
+                  launch_modesum_x2(m, static_cast<const double2 *>(fh), static_cast<float2 *>(qh), n, st),
+                  "collide: mode sum");
+    } else if (m->method == 1 && precision == BZ_FP64) {
         BZ_LAUNCH("fast_f64", st,
                   launch_fast_f64(m, static_cast<const double2 *>(fh), static_cast<double2 *>(qh), n, st),
                   "collide: fast spectral convolutions");
@@ -295,11 +311,19 @@ int phase_inverse(const bz_modes *m, int precision, int flags, const void *qh, v
     return BZ_OK;
 }
 
-// Bytes of Fourier scratch one collision evaluation over n cells needs.
+// Fourier scratch of one collision evaluation over n cells: the forward
+// spectra (FP64 for the FP64 and FP32X2 forms, FP32 otherwise) followed by the
+// mode sums (FP64 for the FP64 form, FP32 otherwise), both in the tiled layout.
+size_t spectrum_bytes(const bz_modes *m, int precision, int64_t n) {
+    const int64_t ntile = (n + kTile - 1) / kTile;
+    const size_t celem = (size_t)ntile * m->g->v.nhalf * kTile;
+    return celem * (precision == BZ_FP32 ? sizeof(float2) : sizeof(double2));
+}
+
 size_t collide_scratch_bytes(const bz_modes *m, int precision, int64_t n) {
     const int64_t ntile = (n + kTile - 1) / kTile;
     const size_t celem = (size_t)ntile * m->g->v.nhalf * kTile;
-    return 2 * celem * (precision == BZ_FP64 ? sizeof(double2) : sizeof(float2));
+    return spectrum_bytes(m, precision, n) + celem * (precision == BZ_FP64 ? sizeof(double2) : sizeof(float2));
 }
 
 // Q (or G = Q - P when P != nullptr) of n cells: forward DFT, mode sum, inverse DFT.
@@ -309,7 +333,7 @@ int collide_chain(const bz_modes *m, int precision, int flags, const void *f, vo
     const size_t bytes = collide_scratch_bytes(m, precision, n);
     Scratch s;
     if (!ext) BZ_TRY(s.alloc(bytes, st), "collide: scratch");
-    char *fh = static_cast<char *>(ext ? ext : s.p), *qh = fh + bytes / 2;
+    char *fh = static_cast<char *>(ext ? ext : s.p), *qh = fh + spectrum_bytes(m, precision, n);
     int rc = phase_forward(m, precision, f, fh, n, st);
     if (!rc) rc = phase_modesum(m, precision, fh, qh, n, st);
     if (!rc) rc = phase_inverse(m, precision, flags, qh, Q, P, n, st);
@@ -887,7 +911,8 @@ void bz_mesh_destroy(bz_mesh *mesh) { fv_mesh_destroy(mesh); }
 
 int group_collide(const bz_group_item *items, int n_items, int precision, int flags, void *stream) {
     if (!items || n_items < 0 || n_items > 1024) return fail(BZ_EINVAL, "group_collide: bad item list");
-    if (precision != BZ_FP64 && precision != BZ_FP32) return fail(BZ_EINVAL, "group_collide: precision");
+    if (precision != BZ_FP64 && precision != BZ_FP32 && precision != BZ_FP32X2)
+        return fail(BZ_EINVAL, "group_collide: precision");
     if (flags & ~(BZ_CONSERVE | BZ_CHECK_INPUT)) return fail(BZ_EINVAL, "group_collide: unknown flag");
     if (n_items == 0) return BZ_OK;
     int dev = -1;
@@ -898,6 +923,8 @@ int group_collide(const bz_group_item *items, int n_items, int precision, int fl
         if (it.n_cells < 0) return fail(BZ_EINVAL, "group_collide: n_cells < 0");
         if (it.n_cells > 0 && (!it.f || !it.Q)) return fail(BZ_EINVAL, "group_collide: NULL buffer");
         if (it.modes->g->device != dev) return fail(BZ_EINVAL, "group_collide: items must live on the current device");
+        int rc0 = check_modes(it.modes, precision, "group_collide");
+        if (rc0) return rc0;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // longest first: per-cell work (pairs of the symmetric sum) decides the order
@@ -917,7 +944,7 @@ int group_collide(const bz_group_item *items, int n_items, int precision, int fl
     char *base = static_cast<char *>(s.p);
     auto fh_of = [&](size_t q) { return base + off[q]; };
     auto qh_of = [&](size_t q) {
-        return base + off[q] + collide_scratch_bytes(items[order[q]].modes, precision, items[order[q]].n_cells) / 2;
+        return base + off[q] + spectrum_bytes(items[order[q]].modes, precision, items[order[q]].n_cells);
     };
     int rc;
     for (size_t q = 0; q < order.size(); ++q) {

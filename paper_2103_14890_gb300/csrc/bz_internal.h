@@ -65,6 +65,8 @@ struct bz_modes {
     int *task64;
     int rowmax64;
     int variant64;        // layout of the FP64 tables (entry of the variant list), -1 if none
+    float *wx2;           // FP32X2 weight stream: the FP64 stream's layout and task table, each
+                          // step's weights as FP32 (hi, lo) parts; null if unused
     int modesum_variant;  // variant id reported to callers (index + 1; 0: generic kernel)
     float *d_W32;
     int w32_rowmax;       // largest staged weight row (floats)
@@ -159,6 +161,9 @@ cudaError_t launch_dft_forward_f64(const GridView &g, const double2 *E, const do
                                    double2 *fhat, int64_t n, cudaStream_t st);
 cudaError_t launch_dft_forward_f32(const GridView &g, const float2 *E, const float *f,
                                    float2 *fhat, int64_t n, cudaStream_t st);
+// FP64 transform of FP32 input (the FP32X2 form's forward DFT).
+cudaError_t launch_dft_forward_f64_f32in(const GridView &g, const double2 *E, const float *f,
+                                         double2 *fhat, int64_t n, cudaStream_t st);
 
 // Inverse Gram matrix of the collision invariants, passed by value to kernels.
 struct Cinv {
@@ -186,6 +191,8 @@ cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *Qhat, flo
                                       const double *cinv, const InvEpilogue &ep, cudaStream_t st);
 cudaError_t launch_dft64_forward_tile(const GridView &g, const double *f, double2 *fhat, int64_t n,
                                       cudaStream_t st);
+cudaError_t launch_dft64_forward_tile_f32in(const GridView &g, const float *f, double2 *fhat, int64_t n,
+                                            cudaStream_t st);
 cudaError_t launch_dft64_inverse_tile(const GridView &g, const double2 *Qhat, double *Q, int64_t n, double scale,
                                       const double *cinv, const InvEpilogue &ep, cudaStream_t st);
 
@@ -211,6 +218,10 @@ bool modesum64_available(const bz_modes *m);
 cudaError_t launch_modesum64(const bz_modes *m, const double2 *fhat, double2 *Qhat, int64_t n, cudaStream_t st);
 cudaError_t launch_modesum32_part(const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n,
                                   cudaStream_t st);
+// FP32X2 (double-float) mode sum on the FP64 tables: FP64 spectra in, Q-hat
+// rounded to FP32 out (k_modesum32.cu).
+bool modesum_x2_available(const bz_modes *m);
+cudaError_t launch_modesum_x2(const bz_modes *m, const double2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st);
 cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *const *fhat, float2 *const *Qhat,
                                    const int64_t *n, int count, cudaStream_t st);
 

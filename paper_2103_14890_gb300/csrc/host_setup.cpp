@@ -355,6 +355,7 @@ void modes_destroy(bz_modes *m) {
     cudaFree(m->d_F64);
     cudaFree(m->d_F32);
     cudaFree(m->w64);
+    cudaFree(m->wx2);
     cudaFree(m->task64);
     for (int v = 0; v < kModesumVariants; ++v) {
         cudaFree(m->var_W[v]);

@@ -33,9 +33,9 @@ template <typename T> size_t inv_smem(const GridView &g) {
     return q + sizeof(V) * ((size_t)H * M * M + (size_t)H * M * N + (size_t)H * N * N);
 }
 
-template <typename T>
+template <typename T, typename TI = T>
 __global__ void __launch_bounds__(kThreads) dft_forward_kernel(GridView g, const typename C2<T>::type *__restrict__ E,
-                                                               const T *__restrict__ f,
+                                                               const TI *__restrict__ f,
                                                                typename C2<T>::type *__restrict__ fhat) {
     using V = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -43,8 +43,8 @@ __global__ void __launch_bounds__(kThreads) dft_forward_kernel(GridView g, const
     const int N = g.N, M = g.M, h = g.h, H = h + 1;
     const T invN = (T)1 / (T)N;
     T *fs = reinterpret_cast<T *>(smem_raw);
-    const T *fc = f + cell * g.nv;
-    for (int64_t i = threadIdx.x; i < g.nv; i += blockDim.x) fs[i] = fc[i];
+    const TI *fc = f + cell * g.nv;
+    for (int64_t i = threadIdx.x; i < g.nv; i += blockDim.x) fs[i] = (T)fc[i];
     __syncthreads();
     if (g.dim == 2) {
         V *A = reinterpret_cast<V *>(fs + N * N);          // A[k1][j2], k1 = 0..h
@@ -217,14 +217,15 @@ __global__ void __launch_bounds__(kThreads) dft_inverse_kernel(GridView g, const
     }
 }
 
-template <typename T>
-cudaError_t forward(const GridView &g, const typename C2<T>::type *E, const T *f,
+template <typename T, typename TI = T>
+cudaError_t forward(const GridView &g, const typename C2<T>::type *E, const TI *f,
                     typename C2<T>::type *fhat, int64_t n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     size_t sm = fwd_smem<T>(g);
-    cudaError_t e = cudaFuncSetAttribute(dft_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e =
+        cudaFuncSetAttribute(dft_forward_kernel<T, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    dft_forward_kernel<T><<<(unsigned)n, kThreads, sm, st>>>(g, E, f, fhat);
+    dft_forward_kernel<T, TI><<<(unsigned)n, kThreads, sm, st>>>(g, E, f, fhat);
     return cudaGetLastError();
 }
 
@@ -252,6 +253,10 @@ cudaError_t launch_dft_forward_f64(const GridView &g, const double2 *E, const do
 cudaError_t launch_dft_forward_f32(const GridView &g, const float2 *E, const float *f, float2 *fhat,
                                    int64_t n, cudaStream_t st) {
     return forward<float>(g, E, f, fhat, n, st);
+}
+cudaError_t launch_dft_forward_f64_f32in(const GridView &g, const double2 *E, const float *f, double2 *fhat,
+                                         int64_t n, cudaStream_t st) {
+    return forward<double, float>(g, E, f, fhat, n, st);
 }
 cudaError_t launch_dft_inverse_f64(const GridView &g, const double2 *E, const double2 *Qhat, double *Q,
                                    int64_t n, double scale, const double *cinv, const InvEpilogue &ep,

@@ -102,9 +102,9 @@ __device__ __forceinline__ void inv32_epilogue(T (&q)[N], int64_t cell, int lane
 // One CTA handles C cells (C = 32: a whole 32-cell tile of the Fourier layout,
 // or C = 16: half of one, so that two CTAs fit an SM and one's memory traffic
 // overlaps the other's arithmetic) with 16 C threads.
-template <typename T, int N, int C>
+template <typename T, int N, int C, typename TI = T>
 __global__ void __launch_bounds__(C * 16)
-fft_fwd32_kernel(const T *__restrict__ f, typename C2<T>::type *__restrict__ fhat, int64_t n) {
+fft_fwd32_kernel(const TI *__restrict__ f, typename C2<T>::type *__restrict__ fhat, int64_t n) {
     using V2 = typename C2<T>::type;
     using S = T;
     constexpr int H = N / 2, M = N - 1, NV = N * N, LH = ilog2(H), LN = ilog2(N);
@@ -120,12 +120,12 @@ fft_fwd32_kernel(const T *__restrict__ f, typename C2<T>::type *__restrict__ fha
         for (int c = warp; c < C; c += NW) {
             const int64_t g = tile * 32 + sub + c;
             const bool ok = g < n;
-            const S *fc = f + g * NV + lane;
+            const TI *fc = f + g * NV + lane;
             V2 z[H];
 #pragma unroll
             for (int p = 0; p < H; ++p) {
-                const S x0 = ok ? __ldg(fc + (2 * p) * N) : (S)0.;
-                const S x1 = ok ? __ldg(fc + (2 * p + 1) * N) : (S)0.;
+                const S x0 = ok ? (S)__ldg(fc + (2 * p) * N) : (S)0.;
+                const S x1 = ok ? (S)__ldg(fc + (2 * p + 1) * N) : (S)0.;
                 z[bitrev(p, LH)] = cmk<V2>(x0, x1);   // packed even / odd samples
             }
             fft_dit<H, -1>(z);
@@ -254,9 +254,9 @@ fft_inv32_kernel(const typename C2<T>::type *__restrict__ Qhat, T *__restrict__ 
 
 template <int N> constexpr int threads_per_cell() { return N <= 32 ? 32 : 64; }
 
-template <typename T, int N, int C>
+template <typename T, int N, int C, typename TI = T>
 __global__ void __launch_bounds__(C * threads_per_cell<N>())
-fftg_fwd_kernel(const T *__restrict__ f, typename C2<T>::type *__restrict__ fhat, int64_t n) {
+fftg_fwd_kernel(const TI *__restrict__ f, typename C2<T>::type *__restrict__ fhat, int64_t n) {
     using V2 = typename C2<T>::type;
     using S = T;
     constexpr int H = N / 2, M = N - 1, NV = N * N, P = C + 1, NT = C * threads_per_cell<N>();
@@ -270,11 +270,11 @@ fftg_fwd_kernel(const T *__restrict__ f, typename C2<T>::type *__restrict__ fhat
         const int c = t / N, j2 = t % N;
         const int64_t g = tile * 32 + sub + c;
         const bool ok = g < n;
-        const S *fc = f + g * NV + j2;
+        const TI *fc = f + g * NV + j2;
         V2 z[H];
 #pragma unroll
         for (int p = 0; p < H; ++p)
-            z[p] = cmk<V2>(ok ? __ldg(fc + (2 * p) * N) : (S)0., ok ? __ldg(fc + (2 * p + 1) * N) : (S)0.);
+            z[p] = cmk<V2>(ok ? (S)__ldg(fc + (2 * p) * N) : (S)0., ok ? (S)__ldg(fc + (2 * p + 1) * N) : (S)0.);
         fft_nat<H, -1>(z);
 #pragma unroll
         for (int k = 0; k < H; ++k) {
@@ -471,21 +471,23 @@ template <typename T, int N> constexpr int fft_cells() {
 // The inverse keeps 128 registers per thread; 8-cell CTAs let four share an SM.
 template <typename T, int N> constexpr int ifft_cells() { return (N == 16 || N == 32) ? 8 : fft_cells<T, N>(); }
 
-template <typename T, int N>
-cudaError_t fwd_tile(const T *f, typename C2<T>::type *fhat, int64_t n, cudaStream_t st) {
+template <typename T, int N, typename TI = T>
+cudaError_t fwd_tile(const TI *f, typename C2<T>::type *fhat, int64_t n, cudaStream_t st) {
     constexpr int C = fft_cells<T, N>();
     const unsigned grid = (unsigned)(((n + 31) / 32) * (32 / C));
     cudaError_t e;
     if constexpr (N == 16 || N == 32) {
         const size_t sm = fft_smem<T, N, C>();
-        e = cudaFuncSetAttribute(fft_fwd32_kernel<T, N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaFuncSetAttribute(fft_fwd32_kernel<T, N, C, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
         if (e != cudaSuccess) return e;
-        fft_fwd32_kernel<T, N, C><<<grid, C * 16, sm, st>>>(f, fhat, n);
+        fft_fwd32_kernel<T, N, C, TI><<<grid, C * 16, sm, st>>>(f, fhat, n);
     } else {
         const size_t sm = fftg_smem<T, N, C>();
-        e = cudaFuncSetAttribute(fftg_fwd_kernel<T, N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaFuncSetAttribute(fftg_fwd_kernel<T, N, C, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
         if (e != cudaSuccess) return e;
-        fftg_fwd_kernel<T, N, C><<<grid, C * threads_per_cell<N>(), sm, st>>>(f, fhat, n);
+        fftg_fwd_kernel<T, N, C, TI><<<grid, C * threads_per_cell<N>(), sm, st>>>(f, fhat, n);
     }
     return cudaGetLastError();
 }
@@ -512,14 +514,14 @@ cudaError_t inv_tile(const GridView &g, const typename C2<T>::type *Qhat, T *Q, 
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t fwd_any(const GridView &g, const T *f, typename C2<T>::type *fhat, int64_t n, cudaStream_t st) {
+template <typename T, typename TI = T>
+cudaError_t fwd_any(const GridView &g, const TI *f, typename C2<T>::type *fhat, int64_t n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     switch (g.N) {
-        case 16: return fwd_tile<T, 16>(f, fhat, n, st);
-        case 24: return fwd_tile<T, 24>(f, fhat, n, st);
-        case 32: return fwd_tile<T, 32>(f, fhat, n, st);
-        case 48: return fwd_tile<T, 48>(f, fhat, n, st);
+        case 16: return fwd_tile<T, 16, TI>(f, fhat, n, st);
+        case 24: return fwd_tile<T, 24, TI>(f, fhat, n, st);
+        case 32: return fwd_tile<T, 32, TI>(f, fhat, n, st);
+        case 48: return fwd_tile<T, 48, TI>(f, fhat, n, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -559,6 +561,10 @@ cudaError_t launch_dft32_forward_tile(const GridView &g, const float *f, float2 
 cudaError_t launch_dft64_forward_tile(const GridView &g, const double *f, double2 *fhat, int64_t n,
                                       cudaStream_t st) {
     return fwd_any<double>(g, f, fhat, n, st);
+}
+cudaError_t launch_dft64_forward_tile_f32in(const GridView &g, const float *f, double2 *fhat, int64_t n,
+                                            cudaStream_t st) {
+    return fwd_any<double, float>(g, f, fhat, n, st);
 }
 cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *Qhat, float *Q, int64_t n, double scale,
                                       const double *cinv, const InvEpilogue &ep, cudaStream_t st) {

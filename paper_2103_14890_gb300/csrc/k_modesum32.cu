@@ -62,9 +62,11 @@ struct Variant {
     int R, warps, cells;
 };
 constexpr int kNumVariants = kModesumVariants;   // FP32 variants (timed by the autotuner)
-// entries 0..3: the FP32 variants; entry 4: an FP64-only layout (2 outputs per
-// thread, 8 warps, 8-cell tiles) for grids whose FP64 spectrum needs it
-constexpr Variant kVariants[kNumVariants + 1] = {{8, 16, 32}, {4, 32, 32}, {4, 16, 16}, {4, 16, 8}, {2, 8, 8}};
+// entries 0..3: the FP32 variants; entries 4, 5: layouts of the FP64 and FP32X2
+// forms only (2 outputs per thread, 8 warps, 8- and 4-cell tiles) for grids
+// whose 16-byte-per-value spectrum needs them (48^2, 16^3)
+constexpr Variant kVariants[kNumVariants + 2] = {{8, 16, 32}, {4, 32, 32}, {4, 16, 16},
+                                                 {4, 16, 8},  {2, 8, 8},   {2, 8, 4}};
 constexpr int kTaskInts = 12;   // ints per task record
 
 constexpr int kPad = 8;         // zero guard columns before the first and after the last row
@@ -286,6 +288,234 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
     }
 }
 
+// ---- FP32X2 form: double-float arithmetic on the FP32 pipe ------------------
+// Every value is an unevaluated sum hi + lo of two FP32 numbers (|lo| <= u |hi|).
+// For each term w f-hat_l f-hat_m of eq. CF1 the product X = w f-hat_l is
+// formed exactly in its high part (TwoProd: fmaf(a, b, -fl(a b)) is the exact
+// rounding error of a b) with the low parts of w and f-hat_l added to its
+// error; each of the four real products X b of the complex product is split
+// exactly the same way, its high part enters the running sum by TwoSum (exact
+// error), and every error and the cross terms with the low part of b
+// accumulate in a second FP32 sum.  This is the compensated dot product
+// ("Dot2") of Ogita, Rump and Oishi (2005), accurate as if computed in twice
+// the working precision; the operations are pinned with __fmul_rn / __fadd_rn
+// so the compiler cannot fuse them into FMAs that would break the exact splits.
+struct X2Acc {
+    float sx, sy;     // running sums of the high parts (real, imaginary)
+    float cx, cy;     // accumulated errors and low-order terms
+};
+
+__device__ __forceinline__ void x2_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// acc += w a b with w = wh + wl (real), a = ah + al (conjugated for DIR < 0),
+// b = bh + bl.
+template <int DIR>
+__device__ __forceinline__ void x2_term(X2Acc &acc, float wh, float wl, float2 ah, float2 al, float2 bh,
+                                        float2 bl) {
+    // X = w a: high parts exact products, errors plus the low-part terms
+    const float xx = __fmul_rn(wh, ah.x);
+    float ex = fmaf(wh, ah.x, -xx);
+    ex = fmaf(wl, ah.x, ex);
+    ex = fmaf(wh, al.x, ex);
+    const float xy = __fmul_rn(wh, ah.y);
+    float ey = fmaf(wh, ah.y, -xy);
+    ey = fmaf(wl, ah.y, ey);
+    ey = fmaf(wh, al.y, ey);
+    // with xi the imaginary part of X after the optional conjugation, yn = -xi:
+    // re(X b) = xx bx + yn by, im(X b) = xx by - yn bx
+    const float yn = DIR > 0 ? -xy : xy;
+    const float en = DIR > 0 ? -ey : ey;
+    float p, q, s, d, c;
+    // real part
+    p = __fmul_rn(xx, bh.x);
+    q = fmaf(xx, bh.x, -p);
+    x2_two_sum(acc.sx, p, s, d);
+    acc.sx = s;
+    c = __fadd_rn(q, d);
+    p = __fmul_rn(yn, bh.y);
+    q = fmaf(yn, bh.y, -p);
+    x2_two_sum(acc.sx, p, s, d);
+    acc.sx = s;
+    c = __fadd_rn(c, __fadd_rn(q, d));
+    acc.cx = __fadd_rn(acc.cx, c);
+    acc.cx = fmaf(ex, bh.x, acc.cx);
+    acc.cx = fmaf(en, bh.y, acc.cx);
+    acc.cx = fmaf(xx, bl.x, acc.cx);
+    acc.cx = fmaf(yn, bl.y, acc.cx);
+    // imaginary part
+    p = __fmul_rn(xx, bh.y);
+    q = fmaf(xx, bh.y, -p);
+    x2_two_sum(acc.sy, p, s, d);
+    acc.sy = s;
+    c = __fadd_rn(q, d);
+    p = __fmul_rn(-yn, bh.x);
+    q = fmaf(-yn, bh.x, -p);
+    x2_two_sum(acc.sy, p, s, d);
+    acc.sy = s;
+    c = __fadd_rn(c, __fadd_rn(q, d));
+    acc.cy = __fadd_rn(acc.cy, c);
+    acc.cy = fmaf(ex, bh.y, acc.cy);
+    acc.cy = fmaf(-en, bh.x, acc.cy);
+    acc.cy = fmaf(xx, bl.y, acc.cy);
+    acc.cy = fmaf(-yn, bl.x, acc.cy);
+}
+
+// RR consecutive FP32 weights (RR = 4: 16-byte aligned, RR = 2: 8-byte aligned).
+template <int RR> __device__ __forceinline__ void load_wx(float *wv, const float *p) {
+    if constexpr (RR == 4) {
+        const float4 w4 = *reinterpret_cast<const float4 *>(p);
+        wv[0] = w4.x;
+        wv[1] = w4.y;
+        wv[2] = w4.z;
+        wv[3] = w4.w;
+    } else {
+        static_assert(RR == 2, "FP32X2 blocks hold 2 or 4 outputs per thread");
+        const float2 w2 = *reinterpret_cast<const float2 *>(p);
+        wv[0] = w2.x;
+        wv[1] = w2.y;
+    }
+}
+
+// One block of RR l_2 steps of the FP32X2 form: the window scheme of
+// block_pass, with the high and low parts of each spectrum value LO elements
+// apart in shared memory and the weights of step s at wb + s * 2 RT (high
+// parts) and wb + s * 2 RT + RT (low parts).
+template <int RR, int CS, int RT, int PH, int DIR>
+__device__ __forceinline__ void block_pass_x2(float2 (&wh)[2 * RR], float2 (&wl)[2 * RR],
+                                              const float2 *__restrict__ mp, const float2 *__restrict__ lp, int LO,
+                                              const float *__restrict__ wb, X2Acc (&acc)[RR]) {
+#pragma unroll
+    for (int j = 0; j < RR; ++j) {
+        wh[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
+        wl[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS + LO];
+    }
+#pragma unroll
+    for (int s = 0; s < RR; ++s) {
+        const float2 ah = lp[s * DIR * CS], al = lp[s * DIR * CS + LO];
+        float whi[RR], wlo[RR];
+        load_wx<RR>(whi, wb + s * 2 * RT);
+        load_wx<RR>(wlo, wb + s * 2 * RT + RT);
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+            const int q = (r - s + RR - 1 + PH * RR) & (2 * RR - 1);
+            x2_term<DIR>(acc[r], whi[r], wlo[r], ah, al, wh[q], wl[q]);
+        }
+    }
+}
+
+template <int RR, int CS, int RT, int DIR>
+__device__ __forceinline__ void row_pass_x2(const float2 *__restrict__ rowl, const float2 *__restrict__ rowm, int LO,
+                                            const float *__restrict__ wrow, int nblk, int l2lo, int mbase0,
+                                            X2Acc (&acc)[RR]) {
+    float2 wh[2 * RR], wl[2 * RR];
+    const float2 *mp = rowm + mbase0 * CS;
+    const float2 *lp = rowl + DIR * l2lo * CS;
+#pragma unroll
+    for (int j = RR; j < 2 * RR - 1; ++j) {
+        wh[j] = mp[j * CS];
+        wl[j] = mp[j * CS + LO];
+    }
+    int blk = 0;
+    for (; blk + 1 < nblk; blk += 2) {
+        block_pass_x2<RR, CS, RT, 0, DIR>(wh, wl, mp, lp, LO, wrow + blk * RR * 2 * RT, acc);
+        block_pass_x2<RR, CS, RT, 1, DIR>(wh, wl, mp - RR * CS, lp + RR * DIR * CS, LO,
+                                          wrow + (blk + 1) * RR * 2 * RT, acc);
+        mp -= 2 * RR * CS;
+        lp += 2 * RR * DIR * CS;
+    }
+    if (blk < nblk) block_pass_x2<RR, CS, RT, 0, DIR>(wh, wl, mp, lp, LO, wrow + blk * RR * 2 * RT, acc);
+}
+
+// The FP32X2 mode sum: the task structure and shared-memory layout of
+// modesum32_kernel on the FP64 tables (same tasks, same row pairs; a weight's
+// 8 bytes hold its FP32 high and low parts).  Input: FP64 spectra in the tiled
+// layout, split into FP32 high and low parts while they are staged; output:
+// Q-hat rounded to FP32 (hi + lo), tiled layout.
+template <int RR, int WARPS, int CELLS>
+__global__ void __launch_bounds__(WARPS * 32, 1)
+modesum_x2_kernel(const double2 *__restrict__ fhat, float2 *__restrict__ Qhat, const float *__restrict__ W,
+                  const int *__restrict__ tasks, int h, int M, int nhalf, int wrow_max, int64_t n) {
+    constexpr int G = 32 / CELLS;
+    constexpr int RT = RR * G;
+    constexpr int HEADF = kRowHeadBytes / (int)sizeof(float);
+    extern __shared__ __align__(16) uint4 smem16[];
+    const int64_t tile = (int64_t)blockIdx.x / G;
+    const int sub = (int)(blockIdx.x % G);
+    const int rows = nhalf + 2 * kPad;
+    float2 *Fh = reinterpret_cast<float2 *>(smem16);              // [rows][CELLS] high parts
+    float2 *Fl = Fh + (size_t)rows * CELLS;                       // [rows][CELLS] low parts
+    float *wsm = reinterpret_cast<float *>(Fl + (size_t)rows * CELLS);   // [warps][2][2 wrow_max]
+    const int LO = rows * CELLS;
+    {
+        const double2 *src = fhat + tile * (int64_t)nhalf * 32 + sub * CELLS;
+        for (int i = threadIdx.x; i < rows * CELLS; i += blockDim.x) {
+            const int row = i / CELLS - kPad, c = i % CELLS;
+            float2 hv = make_float2(0.f, 0.f), lv = make_float2(0.f, 0.f);
+            if (row >= 0 && row < nhalf) {
+                const double2 x = src[(int64_t)row * 32 + c];
+                hv.x = __double2float_rn(x.x);
+                hv.y = __double2float_rn(x.y);
+                lv.x = __double2float_rn(x.x - (double)hv.x);
+                lv.y = __double2float_rn(x.y - (double)hv.y);
+            }
+            Fh[i] = hv;
+            Fl[i] = lv;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cell = lane % CELLS, grp = lane / CELLS;
+    float *wbuf0 = wsm + (size_t)warp * 4 * wrow_max;             // wrow_max counts 8-byte slots
+    float *wbuf1 = wbuf0 + 2 * wrow_max;
+    const int tbeg = tasks[warp], tend = tasks[warp + 1];
+    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS + 1);
+    const float2 *F0 = Fh + (size_t)(kPad + h) * CELLS + cell;
+
+    for (int t = tbeg; t < tend; ++t) {
+        const TaskRec tk = trec[t];
+        const int rowb = tk.rowf * 8;                      // bytes per row pair
+        const float *wsrc = W + 2 * (size_t)tk.woff;
+        X2Acc acc[RR];
+#pragma unroll
+        for (int r = 0; r < RR; ++r) acc[r] = X2Acc{0.f, 0.f, 0.f, 0.f};
+        const int k20 = tk.k20 + grp * RR;
+        const int mbase0 = k20 - tk.l2lo - (RR - 1);
+        stage_row(wbuf0, wsrc, rowb, lane);
+        for (int i = 0; i < tk.nrows; ++i) {
+            const float *wcur = (i & 1) ? wbuf1 : wbuf0;
+            if (i + 1 < tk.nrows) {
+                stage_row((i & 1) ? wbuf0 : wbuf1, wsrc + (size_t)(i + 1) * 2 * tk.rowf, rowb, lane);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            const int4 hd = *reinterpret_cast<const int4 *>(wcur);
+            if (hd.z > 0)
+                row_pass_x2<RR, CELLS, RT, 1>(F0 + hd.x, F0 + hd.y, LO, wcur + HEADF + grp * RR, tk.nblk * G,
+                                              tk.l2lo, mbase0, acc);
+            else
+                row_pass_x2<RR, CELLS, RT, -1>(F0 + hd.x, F0 + hd.y, LO, wcur + HEADF + grp * RR, tk.nblk * G,
+                                               tk.l2lo, mbase0, acc);
+            __syncwarp();
+        }
+        const int64_t c = tile * 32 + sub * CELLS + cell;
+        if (c < n) {
+            float2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.orow * M * 32 + sub * CELLS + cell;
+#pragma unroll
+            for (int r = 0; r < RR; ++r) {
+                const int k2 = k20 + r;
+                if (grp * RR + r >= tk.rfirst && k2 <= h)
+                    out[(k2 + h) * 32] = make_float2(__fadd_rn(acc[r].sx, acc[r].cx), __fadd_rn(acc[r].sy, acc[r].cy));
+            }
+        }
+    }
+}
+
 template <typename T> size_t smem_bytes(const GridView &g, int wrow_max, int v) {
     return 2 * sizeof(T) * (size_t)(g.nhalf + 2 * kPad) * kVariants[v].cells +
            sizeof(T) * (size_t)kVariants[v].warps * 2 * wrow_max;
@@ -298,9 +528,13 @@ double beta_host(const bz_modes *m, const int *l, const int *mm);
 
 // Weight stream (with row-pair headers) and task table of one variant, with
 // weights of type T; false if the grid is not covered by this variant (another
-// variant or the generic kernel serves it).
+// variant or the generic kernel serves it).  With T = double and outX2 set, a
+// second stream of the same byte layout for the FP32X2 form: the RT doubles of
+// each l_2 step become RT FP32 high parts followed by RT FP32 low parts
+// (hi = fl32(w), lo = fl32(w - hi)), headers copied as they are.
 template <typename T>
-static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, int *outRowmax) {
+static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, int *outRowmax,
+                          float **outX2 = nullptr) {
     constexpr int HEAD = kRowHeadBytes / (int)sizeof(T);
     const int R = kVariants[v].R * (32 / kVariants[v].cells);   // outputs per task (RT)
     const int kWarps = kVariants[v].warps;
@@ -314,6 +548,9 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
     const int lo_col = -h - kPad, hi_col = h + kPad;         // addressable columns
     std::vector<TaskRec> tasks;
     std::vector<T> W;
+    std::vector<float> X2;                                  // FP32X2 stream (T = double only)
+    const bool want_x2 = outX2 != nullptr && sizeof(T) == 8;
+    std::vector<double> stepw(R);
     std::vector<double> cost;
     const int nmid = (d == 3) ? M : 1;                      // values of the middle index (3-D)
     struct Pair { int l[2], m[2]; };                         // leading indices of l and m
@@ -377,6 +614,11 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                     T hw[HEAD];
                     std::memcpy(hw, head, sizeof head);
                     for (int q = 0; q < HEAD; ++q) W.push_back(hw[q]);
+                    if (want_x2) {
+                        float hf[4];
+                        std::memcpy(hf, head, sizeof head);
+                        for (int q = 0; q < 4; ++q) X2.push_back(hf[q]);
+                    }
                     for (int j = 0; j < npad; ++j) {
                         const int lz = l2lo + j;
                         for (int r = 0; r < R; ++r) {
@@ -396,6 +638,11 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                                 if (p.l[0] < p.m[0]) w += beta_host(m, mm, l);
                             }
                             W.push_back((T)w);
+                            stepw[r] = w;
+                        }
+                        if (want_x2) {
+                            for (int r = 0; r < R; ++r) X2.push_back((float)stepw[r]);
+                            for (int r = 0; r < R; ++r) X2.push_back((float)(stepw[r] - (double)(float)stepw[r]));
                         }
                     }
                 }
@@ -430,19 +677,26 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
     if (smem_bytes<T>(gv, wrow_max, v) > 227 * 1024) return false;   // does not fit
     T *dW = nullptr;
     int *dT = nullptr;
+    float *dX = nullptr;
     cudaError_t e = cudaMalloc(&dW, sizeof(T) * W.size());
     if (e == cudaSuccess) e = cudaMalloc(&dT, sizeof(int) * tab.size());
     if (e == cudaSuccess) e = cudaMemcpy(dW, W.data(), sizeof(T) * W.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dT, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && want_x2) {
+        e = cudaMalloc(&dX, sizeof(float) * X2.size());
+        if (e == cudaSuccess) e = cudaMemcpy(dX, X2.data(), sizeof(float) * X2.size(), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaFree(dW);
         cudaFree(dT);
+        cudaFree(dX);
         rc = cuda_fail(e, "build_kernel_modes: weight stream");
         return false;
     }
     *outW = dW;
     *outT = dT;
     *outRowmax = wrow_max;
+    if (want_x2) *outX2 = dX;
     return true;
 }
 
@@ -501,8 +755,9 @@ static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, 
 
 // FP64 form: the same kernel on double spectra and weights, on 16-cell tiles
 // (variant entry 2) or, where the double spectrum of 16 cells does not fit
-// shared memory (48^2), on 8-cell tiles (entry 4); no last-wave split.
-constexpr int kFp64Variants[2] = {2, 4};
+// shared memory, on 8- or 4-cell tiles (entries 4, 5: 48^2, 16^3); no
+// last-wave split.  The FP32X2 form runs on the same layout.
+constexpr int kFp64Variants[3] = {2, 4, 5};
 
 bool modesum64_available(const bz_modes *m) { return m->w64 != nullptr; }
 
@@ -517,7 +772,34 @@ cudaError_t launch_modesum64(const bz_modes *m, const double2 *fhat, double2 *Qh
     gd.tile_start[1] = ctas_for(m->variant64, n);
     const size_t sm = smem_bytes<double>(m->g->v, m->rowmax64, m->variant64);
     if (m->variant64 == 2) return launch_instance<double, 4, 16, 16>(gd, sm, st);
-    return launch_instance<double, 2, 8, 8>(gd, sm, st);
+    if (m->variant64 == 4) return launch_instance<double, 2, 8, 8>(gd, sm, st);
+    return launch_instance<double, 2, 8, 4>(gd, sm, st);
+}
+
+// FP32X2 form on the FP64 layout (variant entries 2, 4, 5).
+bool modesum_x2_available(const bz_modes *m) { return m->wx2 != nullptr && m->variant64 >= 0; }
+
+template <int RR, int WARPS, int CELLS>
+static cudaError_t launch_x2_instance(const bz_modes *m, const double2 *fhat, float2 *Qhat, int64_t n, size_t sm,
+                                      cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(modesum_x2_kernel<RR, WARPS, CELLS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const GridView &gv = m->g->v;
+    modesum_x2_kernel<RR, WARPS, CELLS><<<(unsigned)ctas_for(m->variant64, n), WARPS * 32, sm, st>>>(
+        fhat, Qhat, m->wx2, m->task64, gv.h, gv.M, (int)gv.nhalf, m->rowmax64, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_modesum_x2(const bz_modes *m, const double2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (!modesum_x2_available(m)) return cudaErrorInvalidValue;
+    // the FP64 layout's shared memory: spectra of 16 bytes per value (hi, lo
+    // parts of FP32 instead of one double) and weight rows of 8-byte slots
+    const size_t sm = smem_bytes<double>(m->g->v, m->rowmax64, m->variant64);
+    if (m->variant64 == 2) return launch_x2_instance<4, 16, 16>(m, fhat, Qhat, n, sm, st);
+    if (m->variant64 == 4) return launch_x2_instance<2, 8, 8>(m, fhat, Qhat, n, sm, st);
+    return launch_x2_instance<2, 8, 4>(m, fhat, Qhat, n, sm, st);
 }
 
 static int sm_count();
@@ -707,8 +989,9 @@ int modes_build_fp32_tables(bz_modes *m) {
     m->task64 = nullptr;
     m->rowmax64 = 0;
     m->variant64 = -1;
-    for (int q = 0; q < 2 && m->variant64 < 0; ++q) {
-        if (build_variant<double>(m, kFp64Variants[q], rc, &m->w64, &m->task64, &m->rowmax64))
+    m->wx2 = nullptr;
+    for (int q = 0; q < 3 && m->variant64 < 0; ++q) {
+        if (build_variant<double>(m, kFp64Variants[q], rc, &m->w64, &m->task64, &m->rowmax64, &m->wx2))
             m->variant64 = kFp64Variants[q];
         if (rc) return rc;
     }
