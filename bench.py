@@ -186,8 +186,8 @@ def main():
     ap.add_argument("--method", default="direct", choices=["direct", "fast"],
                     help="fast: time the fast spectral form (Maxwell molecules) as the main line instead")
     ap.add_argument("--ndirs", type=int, default=8, help="collision directions of the fast form")
-    ap.add_argument("--sections", default="transport,imex,grouped,fast",
-                    help="comma list of the extra measurements to run (transport, imex, grouped, fast)")
+    ap.add_argument("--sections", default="forms,transport,imex,grouped,fast",
+                    help="comma list of the extra measurements to run (forms, transport, imex, grouped, fast)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -276,10 +276,12 @@ def main():
     sections = set(args.sections.split(",")) if not args.no_extra and not fast else set()
     if "transport" in sections:
         extra["transport"] = _transport_measure(bz, workloads, st, check=not args.no_cpu_baseline)
+    if "forms" in sections:
+        extra["precision_forms"] = _forms_measure(bz, workloads, st, f, f_host, check=not args.no_cpu_baseline)
     if "imex" in sections:
-        extra["imex_step"] = _imex_measure(bz, workloads, barrier)
+        extra["imex_step"] = _imex_measure(bz, workloads, barrier, check=not args.no_cpu_baseline)
     if "grouped" in sections:
-        extra["grouped"] = _group_measure(bz, workloads, barrier)
+        extra["grouped"] = _group_measure(bz, workloads, barrier, check=not args.no_cpu_baseline)
     if "fast" in sections:
         extra["fast_spectral"] = _fast_measure(bz, f, f_host, st, args.ndirs, check=not args.no_cpu_baseline)
 
@@ -487,10 +489,11 @@ def _measured_hbm():
         return 6800.0
 
 
-def _imex_measure(bz, workloads, barrier):
+def _imex_measure(bz, workloads, barrier, check=True):
     """One ARS(2,2,2) step on the ~19.6k-cell triangulated Sod-like mesh
-    (32x32 grid on [-10,10]^2, VHS, eps = 5e-3, dt = h / (2 max|v|)), FP32 and
-    FP64, the step captured as a CUDA graph (non-default stream)."""
+    (32x32 grid on [-10,10]^2, VHS, eps = 5e-3, dt = h / (2 max|v|)), FP32,
+    FP32X2 and FP64, the step captured as a CUDA graph (non-default stream);
+    f^{n+1} against the oracle's step on 256 cells spread over the mesh."""
     import math
     import torch
     f, hmesh = workloads.sod_cells(32, 10.0)
@@ -498,26 +501,95 @@ def _imex_measure(bz, workloads, barrier):
     m = bz.Modes(bz.Grid(2, 32, 10.0), 1.0)
     s = torch.cuda.Stream()
     out = {}
+    import numpy as np
+    fin = f.astype(np.float32).astype(np.float64)
+    idx = np.unique(np.linspace(0, f.shape[0] - 1, 256).astype(np.int64))
+    want = None
+    if check:
+        import oracle
+        want = oracle.Kernel(2, 32, 10.0, 1.0).imex_step(fin[idx], dt, 5e-3)
     with torch.cuda.stream(s):
-        for prec, steps in (("fp32", 10), ("fp64", 1)):
-            x = torch.from_numpy(f).to("cuda", torch.float32 if prec == "fp32" else torch.float64)
+        for prec, steps in (("fp32", 10), ("fp32x2", 3), ("fp64", 1)):
+            x = torch.from_numpy(fin).to("cuda", torch.float64 if prec == "fp64" else torch.float32)
             y = torch.empty_like(x)
             for _ in range(2):
                 bz.imex_step(m, x, dt, 5e-3, f_out=y, precision=prec, stream=s)
             bz.check(s)
             ms = _timed(lambda: bz.imex_step(m, x, dt, 5e-3, f_out=y, precision=prec, stream=s), steps, s)
             out[prec] = {"ms_per_step": ms, "cell_collision_evals_per_s": 2 * x.shape[0] / (ms / 1e3)}
+            if want is not None:
+                got = y[torch_index(idx)].double().cpu().numpy()
+                out[prec]["rel_l2_fnp1_vs_oracle"] = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+    out["oracle_cells"] = int(len(idx))
     out["cells"] = int(f.shape[0])
     out["workload"] = "ARS(2,2,2) step, %d-cell Delaunay mesh, 32x32 grid, VHS, eps=5e-3, dt=%.3g, CUDA graph" % (
         f.shape[0], dt)
     return out
 
 
-def _group_measure(bz, workloads, barrier):
+def _oracle_err(k, f_in, got, idx=None):
+    """rel-L2 of got against the FP64 oracle on the rows idx (all rows if None)."""
+    import numpy as np
+    if idx is None:
+        idx = np.arange(f_in.shape[0])
+    Qr = k.collide(f_in[idx])
+    return float(np.linalg.norm(got[idx] - Qr) / np.linalg.norm(Qr)), len(idx)
+
+
+def _forms_measure(bz, workloads, st, f3, f3_host, check=True):
+    """The three precision forms on the small and noisy configurations and the
+    FP32X2 form on the benchmark workload: throughput and rel-L2 against the
+    FP64 oracle (FP32-rounded inputs, the same values the device sees).
+      config 1: 64 cells, 16^2 on [-8,8]^2, Maxwell molecules, bi-Maxwellians
+      config 2: 4096 cells, 32^2 on [-10,10]^2, VHS, bi-Maxwellians x (1 + 5 % noise)
+      config 3: the benchmark workload (65536 cells), FP32X2 only; its FP32 and
+                FP64 numbers are the main line and fp64_form"""
+    import numpy as np
+    import oracle
+    import torch
+    out = {}
+    cfgs = (("config1", 2, 16, 8.0, 0.0, workloads.bi_maxwellian(64, 2, 16, 8.0, seed=1001), 50),
+            ("config2", 2, 32, 10.0, 1.0, workloads.bi_maxwellian(4096, 2, 32, 10.0, seed=1002, noise=0.05), 5))
+    for name, d, N, L, gam, f, reps in cfgs:
+        m = bz.Modes(bz.Grid(d, N, L), gam)
+        fin = f.astype(np.float32).astype(np.float64)
+        k = oracle.Kernel(d, N, L, gam) if check else None
+        res = {"cells": f.shape[0], "grid": "%d^%d on [-%g,%g]^%d" % (N, d, L, L, d), "gamma": gam}
+        for prec in ("fp32", "fp32x2", "fp64"):
+            x = torch.from_numpy(fin).to("cuda", torch.float64 if prec == "fp64" else torch.float32)
+            Q = torch.empty_like(x)
+            bz.collide_batch(m, x, Q, precision=prec, stream=st)
+            bz.check(st)
+            ms = _timed(lambda: bz.collide_batch(m, x, Q, precision=prec, stream=st), reps, st)
+            r = {"ms": ms, "cell_collision_evals_per_s": f.shape[0] / (ms / 1e3)}
+            if check:
+                r["rel_l2_vs_oracle"], r["oracle_cells"] = _oracle_err(k, fin, Q.double().cpu().numpy())
+            res[prec] = r
+        out[name] = res
+    m = bz.Modes(bz.Grid(2, N_V, L_BOX), GAMMA)
+    Q = torch.empty_like(f3)
+    bz.collide_batch(m, f3, Q, precision="fp32x2", stream=st)
+    bz.check(st)
+    ms = _timed(lambda: bz.collide_batch(m, f3, Q, precision="fp32x2", stream=st), 3, st)
+    r = {"ms": ms, "cell_collision_evals_per_s": f3.shape[0] / (ms / 1e3)}
+    if check:
+        idx = np.unique(np.linspace(0, f3.shape[0] - 1, 2048).astype(np.int64))
+        k = oracle.Kernel(2, N_V, L_BOX, GAMMA)
+        r["rel_l2_vs_oracle"], r["oracle_cells"] = _oracle_err(k, f3_host.astype(np.float64), Q.double().cpu().numpy(),
+                                                               idx)
+    out["config3_fp32x2"] = r
+    out["note"] = ("fp32x2: FP64 forward DFT, double-float (compensated) mode sum on the FP32 pipe, FP32 inverse "
+                   "DFT; FP32 arrays in and out")
+    return out
+
+
+def _group_measure(bz, workloads, barrier, check=True):
     """Heterogeneous batch in one group_collide call: 8 instances with cell
     counts log-uniform in [1e3, 5e4] and N in {16, 24, 32, 48}, plus two 3-D
-    16^3 instances of 1000 cells; FP32 form timed against the FP64 form on the
-    same inputs (rel-L2 of FP32 against FP64 over all cells)."""
+    16^3 instances of 1000 cells; the FP32, FP32X2 and FP64 forms on the same
+    FP32-rounded inputs, each against the FP64 oracle on 32 cells of every
+    instance (and FP32 against FP64 over all cells)."""
+    import numpy as np
     import torch
     items = workloads.grouped_instances()
     grids = {}
@@ -533,11 +605,11 @@ def _group_measure(bz, workloads, barrier):
     out = {"cells": total, "instances": [(it["dim"], it["N"], it["n_cells"]) for it in items],
            "variants": {"%dd N=%d" % k: m.modesum_variant for k, m in grids.items()}}
     results = {}
-    for prec in ("fp32", "fp64"):
-        dt = torch.float32 if prec == "fp32" else torch.float64
+    for prec in ("fp32", "fp32x2", "fp64"):
+        dt = torch.float64 if prec == "fp64" else torch.float32
         entries = []
         for it, f in zip(items, hosts):
-            x = torch.from_numpy(f).to("cuda", dt)
+            x = torch.from_numpy(f.astype(np.float32)).to("cuda", dt)
             entries.append((grids[(it["dim"], it["N"])], x, torch.empty_like(x)))
         bz.group_collide(entries, precision=prec)
         bz.check()
@@ -545,6 +617,30 @@ def _group_measure(bz, workloads, barrier):
         out[prec] = {"ms_per_call": ms, "cell_collision_evals_per_s": total / (ms / 1e3)}
         results[prec] = [Q for (_, _, Q) in entries]
         del entries
+    if check:
+        # every instance against the FP64 oracle on 32 cells spread over it
+        import oracle
+        per = []
+        for prec in ("fp32", "fp32x2", "fp64"):
+            num = den = 0.0
+            worst = 0.0
+            for i, (it, f) in enumerate(zip(items, hosts)):
+                k = oracle.Kernel(it["dim"], it["N"], it["L"], 1.0)
+                idx = np.unique(np.linspace(0, it["n_cells"] - 1, 32).astype(np.int64))
+                fin = f[idx].astype(np.float32).astype(np.float64)
+                Qr = k.collide(fin)
+                got = results[prec][i][torch_index(idx)].double().cpu().numpy()
+                e2, q2 = float(((got - Qr) ** 2).sum()), float((Qr ** 2).sum())
+                num += e2
+                den += q2
+                worst = max(worst, (e2 / q2) ** 0.5)
+                if prec == "fp32x2":
+                    per.append({"dim": it["dim"], "N": it["N"], "rel_l2_fp32x2": (e2 / q2) ** 0.5})
+            out[prec]["rel_l2_vs_oracle"] = (num / den) ** 0.5
+            out[prec]["worst_instance_rel_l2_vs_oracle"] = worst
+        out["oracle_cells_per_instance"] = 32
+        out["fp32x2_per_instance"] = per
+        out["speedup_fp32x2_over_fp64"] = out["fp64"]["ms_per_call"] / out["fp32x2"]["ms_per_call"]
     # FP32 form against the FP64 GPU form on every cell of every instance
     num = den = 0.0
     for a, b in zip(results["fp32"], results["fp64"]):
@@ -689,6 +785,7 @@ def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, valu
         "gpu_launches": gpu_launches,
         "imex_step": extra.get("imex_step"),
         "grouped": extra.get("grouped"),
+        "precision_forms": extra.get("precision_forms"),
         "fast_spectral": extra.get("fast_spectral"),
         "transport": extra.get("transport"),
         "e2e": {"value": e2e_val, "unit": "cell-collision evals/s",
