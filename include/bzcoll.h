@@ -109,12 +109,12 @@ int init_velocity_grid(int dim, int n_per_dim, double half_width_L, bz_grid **ou
  * beta-hat(l,m) = B-hat(l,m) - B-hat(m,m) of the mode sum; uploads FP64 and
  * FP32 copies (plus the symmetrised weight tiles of the FP32 kernels).
  * For 2-D grids with N <= 48 the register-blocked FP32 mode-sum kernel has
- * three variants (see bz_modes_info); the first build for a (dim, N, SM count)
+ * several variants (see bz_modes_info); the first build for a (dim, N, SM count)
  * times those that fit the grid on the current device (a few ms, zero spectra)
  * and keeps the fastest.  The choice is cached in the process and, if the
  * environment variable BZ_TUNE_CACHE names a writable file, appended there as
  * lines "dim N sms variant" and read back by later processes.
- * BZ_MODESUM_VARIANT=1, 2, 3 or 4 fixes the variant without timing (ignored
+ * BZ_MODESUM_VARIANT=1, 2, 3, 4 or 5 fixes the variant without timing (ignored
  * if that variant does not fit the grid).  With a 32-cell variant chosen by
  * timing, collide calls run the whole waves of CTAs on it and the last partial
  * wave on the 16-cell variant (a second launch); a fixed variant runs every
@@ -377,8 +377,10 @@ const char *bz_last_error(void);
  * per cell by the symmetric FP32 kernel (algorithmic work unit), out[7] =
  * register-blocked FP32 mode-sum variant in use: 1 = 8 outputs per thread,
  * 16 warps, 32-cell tiles; 2 = 4 outputs per thread, 32 warps, 32-cell tiles;
- * 3 = 4 outputs per thread, 16 warps, 16-cell tiles; 0 = FP32 mode sums run
- * on the generic kernel (3-D grids, 2-D grids with N > 48). */
+ * 3 = 4 outputs per thread, 16 warps, 16-cell tiles; 4 = 4 outputs per
+ * thread, 16 warps, 8-cell tiles (3-D 16^3); 5 = two cells per thread in
+ * FP32x2 register pairs, 4 outputs per thread, 16 warps, 32-cell tiles;
+ * 0 = FP32 mode sums run on the generic kernel (2-D grids with N > 48). */
 int bz_modes_info(const bz_modes *m, int64_t out[8]);
 
 /* bz_fast_info -- out[0] = method of a modes handle (0: eq. KM / eq. CF1

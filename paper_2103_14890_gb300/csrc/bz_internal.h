@@ -42,7 +42,7 @@ struct bz_grid {
     double cinv[25];
 };
 
-constexpr int kModesumVariants = 4;   // register-blocked FP32 mode-sum kernel variants
+constexpr int kModesumVariants = 5;   // register-blocked FP32 mode-sum kernel variants
 
 struct bz_modes {
     const bz_grid *g;

@@ -57,16 +57,23 @@ namespace bz {
 namespace {
 
 // Kernel variants: outputs per thread R along k_2, warps per CTA, cells per
-// CTA.  Variant ids reported by bz_modes_info are index + 1.
+// CTA, cells per thread (pack: 1, or 2 for the packed two-cell kernel, whose
+// lanes hold cells c and c + 16 of a 32-cell tile in FP32x2 register pairs).
+// Variant ids reported by bz_modes_info are index + 1.
 struct Variant {
-    int R, warps, cells;
+    int R, warps, cells, pack;
 };
 constexpr int kNumVariants = kModesumVariants;   // FP32 variants (timed by the autotuner)
-// entries 0..3: the FP32 variants; entries 4, 5: layouts of the FP64 and FP32X2
+// entries 0..4: the FP32 variants; entries 5, 6: layouts of the FP64 and FP32X2
 // forms only (2 outputs per thread, 8 warps, 8- and 4-cell tiles) for grids
 // whose 16-byte-per-value spectrum needs them (48^2, 16^3)
-constexpr Variant kVariants[kNumVariants + 2] = {{8, 16, 32}, {4, 32, 32}, {4, 16, 16},
-                                                 {4, 16, 8},  {2, 8, 8},   {2, 8, 4}};
+constexpr Variant kVariants[kNumVariants + 2] = {{8, 16, 32, 1}, {4, 32, 32, 1}, {4, 16, 16, 1}, {4, 16, 8, 1},
+                                                 {4, 16, 32, 2}, {2, 8, 8, 1},   {2, 8, 4, 1}};
+constexpr int kPackedVariant = 4;
+
+// lane groups splitting a task's outputs, and outputs per task (RT)
+constexpr int variant_groups(int v) { return 32 / kVariants[v].cells * kVariants[v].pack; }
+constexpr int variant_rt(int v) { return kVariants[v].R * variant_groups(v); }
 constexpr int kTaskInts = 12;   // ints per task record
 
 constexpr int kPad = 8;         // zero guard columns before the first and after the last row
@@ -283,6 +290,182 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
                 const int k2 = k20 + r;
                 if (grp * RR + r >= tk.rfirst && k2 <= h)
                     out[(k2 + h) * 32] = cmk<V2>(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
+            }
+        }
+    }
+}
+
+// ---- packed two-cell form ------------------------------------------------------
+// The same sums with two cells per thread: lane p of a lane group holds cells
+// p and p + 16 of the 32-cell tile, every spectrum entry in shared memory is
+// one float4 (re_p, re_{p+16}, im_p, im_{p+16}), and every product and
+// accumulation is one FP32x2 instruction (__fmul2_rn / __ffma2_rn: two
+// independent IEEE FP32 operations, the same results as two scalar ones).
+// Each weight is stored twice, (w, w), so it is an FP32x2 operand as loaded.
+// The real part of w f-hat_l f-hat_m is kept as two sums, A = sum w a_re b_re
+// and B = sum w a_im b_im (re = A - B at each fold), so no operand needs a
+// negation; for l_1 < 0 the conjugate f-hat_l is formed once per l_2 step.
+// The two lane groups of a warp split a task's 2 R outputs as in the 16-cell
+// variant.
+struct P2Acc {
+    float2 a, b, c;       // sum w re re, sum w im im, sum w (re im + im re)
+};
+
+template <int RR, int PH, int DIR>
+__device__ __forceinline__ void block_pass_p2(float4 (&win)[2 * RR], const float4 *__restrict__ mp,
+                                              const float4 *__restrict__ lp, const float *__restrict__ wb,
+                                              P2Acc (&acc)[RR]) {
+    constexpr int CS = 16, RT = 2 * RR;
+#pragma unroll
+    for (int j = 0; j < RR; ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
+#pragma unroll
+    for (int s = 0; s < RR; ++s) {
+        const float4 av = lp[s * DIR * CS];
+        const float2 ar = make_float2(av.x, av.y);
+        const float2 ai = DIR > 0 ? make_float2(av.z, av.w) : make_float2(-av.z, -av.w);
+        float2 w2[RR];
+#pragma unroll
+        for (int q = 0; q < RR; q += 2) {
+            const float4 w4 = *reinterpret_cast<const float4 *>(wb + s * 2 * RT + 2 * q);
+            w2[q] = make_float2(w4.x, w4.y);
+            w2[q + 1] = make_float2(w4.z, w4.w);
+        }
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+            const float4 bv = win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)];
+            const float2 br = make_float2(bv.x, bv.y), bi = make_float2(bv.z, bv.w);
+            const float2 tx = __fmul2_rn(w2[r], ar), ty = __fmul2_rn(w2[r], ai);
+            acc[r].a = __ffma2_rn(tx, br, acc[r].a);
+            acc[r].b = __ffma2_rn(ty, bi, acc[r].b);
+            acc[r].c = __ffma2_rn(tx, bi, acc[r].c);
+            acc[r].c = __ffma2_rn(ty, br, acc[r].c);
+        }
+    }
+}
+
+template <int RR, int DIR>
+__device__ __forceinline__ void row_pass_p2(const float4 *__restrict__ rowl, const float4 *__restrict__ rowm,
+                                            const float *__restrict__ wrow, int nblk, int l2lo, int mbase0,
+                                            P2Acc (&acc)[RR]) {
+    constexpr int CS = 16, RT = 2 * RR;
+    float4 win[2 * RR];
+    const float4 *mp = rowm + mbase0 * CS;
+    const float4 *lp = rowl + DIR * l2lo * CS;
+#pragma unroll
+    for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * CS];
+    int blk = 0;
+    for (; blk + 1 < nblk; blk += 2) {
+        block_pass_p2<RR, 0, DIR>(win, mp, lp, wrow + blk * RR * 2 * RT, acc);
+        block_pass_p2<RR, 1, DIR>(win, mp - RR * CS, lp + RR * DIR * CS, wrow + (blk + 1) * RR * 2 * RT, acc);
+        mp -= 2 * RR * CS;
+        lp += 2 * RR * DIR * CS;
+    }
+    if (blk < nblk) block_pass_p2<RR, 0, DIR>(win, mp, lp, wrow + blk * RR * 2 * RT, acc);
+}
+
+// TwoSum on both lanes of an FP32x2 pair (each lane exact as the scalar form).
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e) {
+    s = __fadd2_rn(a, b);
+    const float2 bb = __fadd2_rn(s, make_float2(-a.x, -a.y));
+    const float2 t = __fadd2_rn(s, make_float2(-bb.x, -bb.y));
+    e = __fadd2_rn(__fadd2_rn(a, make_float2(-t.x, -t.y)), __fadd2_rn(b, make_float2(-bb.x, -bb.y)));
+}
+
+template <int RR, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) modesum_p2_kernel(const Mode32Group gd) {
+    constexpr int G = 2, CS = 16;
+    constexpr int HEADF = kRowHeadBytes / (int)sizeof(float);
+    extern __shared__ __align__(16) uint4 smem16[];
+    int it = 0;
+    while (it + 1 < gd.nitems && (int64_t)blockIdx.x >= gd.tile_start[it + 1]) ++it;
+    const Mode32Item &ip = gd.item[it];
+    const float2 *__restrict__ fhat = static_cast<const float2 *>(ip.fhat);
+    float2 *__restrict__ Qhat = static_cast<float2 *>(ip.Qhat);
+    const float *__restrict__ W = static_cast<const float *>(ip.W);
+    const int *__restrict__ tasks = ip.tasks;
+    const int h = ip.h, M = ip.M, nhalf = ip.nhalf, wrow_max = ip.wrow_max;
+    const int64_t n = ip.n;
+    const int64_t tile = (int64_t)blockIdx.x - gd.tile_start[it];
+    float4 *Fs = reinterpret_cast<float4 *>(smem16);                        // [kPad + nhalf + kPad][16]
+    float *wsm = reinterpret_cast<float *>(Fs + (size_t)(nhalf + 2 * kPad) * CS);   // [warps][2][wrow_max]
+    {
+        // the tile's half spectrum as cell pairs (c, c + 16); zero guard rows
+        const float2 *src = fhat + tile * (int64_t)nhalf * 32;
+        const int rows = nhalf + 2 * kPad;
+        for (int i = threadIdx.x; i < rows * CS; i += blockDim.x) {
+            const int row = i / CS - kPad, pr = i % CS;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row >= 0 && row < nhalf) {
+                const float2 x = src[(int64_t)row * 32 + pr], y = src[(int64_t)row * 32 + pr + 16];
+                v = make_float4(x.x, y.x, x.y, y.y);
+            }
+            Fs[i] = v;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pr = lane % CS, grp = lane / CS;
+    float *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
+    float *wbuf1 = wbuf0 + wrow_max;
+    const int tbeg = tasks[warp], tend = tasks[warp + 1];
+    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS + 1);
+    const float4 *F0 = Fs + (size_t)(kPad + h) * CS + pr;
+
+    for (int t = tbeg; t < tend; ++t) {
+        const TaskRec tk = trec[t];
+        const int rowf = tk.rowf;
+        const float *wsrc = W + tk.woff;
+        float2 hre[RR], lre[RR], him[RR], lim[RR];
+        P2Acc acc[RR];
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+            hre[r] = lre[r] = him[r] = lim[r] = make_float2(0.f, 0.f);
+            acc[r].a = acc[r].b = acc[r].c = make_float2(0.f, 0.f);
+        }
+        const int k20 = tk.k20 + grp * RR;
+        const int mbase0 = k20 - tk.l2lo - (RR - 1);
+        stage_row(wbuf0, wsrc, rowf * (int)sizeof(float), lane);
+        for (int i = 0; i < tk.nrows; ++i) {
+            const float *wcur = (i & 1) ? wbuf1 : wbuf0;
+            if (i + 1 < tk.nrows) {
+                stage_row((i & 1) ? wbuf0 : wbuf1, wsrc + (size_t)(i + 1) * rowf, rowf * (int)sizeof(float), lane);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            const int4 hd = *reinterpret_cast<const int4 *>(wcur);
+            if (hd.z > 0)
+                row_pass_p2<RR, 1>(F0 + hd.x, F0 + hd.y, wcur + HEADF + 2 * grp * RR, tk.nblk * G, tk.l2lo, mbase0,
+                                   acc);
+            else
+                row_pass_p2<RR, -1>(F0 + hd.x, F0 + hd.y, wcur + HEADF + 2 * grp * RR, tk.nblk * G, tk.l2lo, mbase0,
+                                    acc);
+            __syncwarp();
+            if ((i & 3) == 3 || i + 1 == tk.nrows) {
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const float2 re = __fadd2_rn(acc[r].a, make_float2(-acc[r].b.x, -acc[r].b.y));
+                    float2 sm, e;
+                    two_sum2(hre[r], re, sm, e);
+                    hre[r] = sm;
+                    lre[r] = __fadd2_rn(lre[r], e);
+                    two_sum2(him[r], acc[r].c, sm, e);
+                    him[r] = sm;
+                    lim[r] = __fadd2_rn(lim[r], e);
+                    acc[r].a = acc[r].b = acc[r].c = make_float2(0.f, 0.f);
+                }
+            }
+        }
+        const int64_t c0 = tile * 32 + pr, c1 = c0 + 16;
+        float2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.orow * M * 32 + pr;
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+            const int k2 = k20 + r;
+            if (grp * RR + r >= tk.rfirst && k2 <= h) {
+                const float2 re = __fadd2_rn(hre[r], lre[r]), im = __fadd2_rn(him[r], lim[r]);
+                if (c0 < n) out[(k2 + h) * 32] = make_float2(re.x, im.x);
+                if (c1 < n) out[(k2 + h) * 32 + 16] = make_float2(re.y, im.y);
             }
         }
     }
@@ -536,8 +719,9 @@ template <typename T>
 static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, int *outRowmax,
                           float **outX2 = nullptr) {
     constexpr int HEAD = kRowHeadBytes / (int)sizeof(T);
-    const int R = kVariants[v].R * (32 / kVariants[v].cells);   // outputs per task (RT)
+    const int R = variant_rt(v);                                // outputs per task (RT)
     const int kWarps = kVariants[v].warps;
+    const int pack = kVariants[v].pack;                         // 2: each weight stored twice (w, w)
     rc = BZ_OK;
     const GridView &gv = m->g->v;
     const int d = gv.dim, h = gv.h, M = gv.M;
@@ -599,7 +783,7 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                 t.nblk = nblk;
                 t.woff = (int)W.size();
                 t.rfirst = std::max(0, prev_end + 1 - k20);
-                t.rowf = HEAD + npad * R;
+                t.rowf = HEAD + npad * R * pack;
                 t.pad0 = t.pad1 = t.pad2 = t.pad3 = 0;
                 prev_end = k2last;
                 for (const Pair &p : pairs) {
@@ -608,7 +792,7 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                     const int a1 = neg ? -p.l[0] : p.l[0], a2 = neg ? -p.l[1] : p.l[1];
                     const int lrow = (d == 3) ? a1 * M + (a2 + h) : a1;
                     const int mrow = (d == 3) ? p.m[0] * M + (p.m[1] + h) : p.m[0];
-                    const int cs = kVariants[v].cells;
+                    const int cs = kVariants[v].cells / pack;   // shared-memory entries per mode
                     const int head[4] = {lrow * M * cs, mrow * M * cs, neg ? -1 : 1, 0};
                     static_assert(sizeof head == kRowHeadBytes, "16-byte row header");
                     T hw[HEAD];
@@ -638,6 +822,7 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                                 if (p.l[0] < p.m[0]) w += beta_host(m, mm, l);
                             }
                             W.push_back((T)w);
+                            if (pack == 2) W.push_back((T)w);
                             stepw[r] = w;
                         }
                         if (want_x2) {
@@ -717,6 +902,13 @@ static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStr
         case 1: return launch_instance<float, 4, 32, 32>(gd, sm, st);
         case 2: return launch_instance<float, 4, 16, 16>(gd, sm, st);
         case 3: return launch_instance<float, 4, 16, 8>(gd, sm, st);
+        case 4: {
+            cudaError_t e = cudaFuncSetAttribute(modesum_p2_kernel<4, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sm);
+            if (e != cudaSuccess) return e;
+            modesum_p2_kernel<4, 16><<<(unsigned)gd.tile_start[gd.nitems], 16 * 32, sm, st>>>(gd);
+            return cudaGetLastError();
+        }
         default: return cudaErrorInvalidValue;
     }
 }
@@ -737,7 +929,7 @@ static void fill_item(Mode32Item &it, const bz_modes *m, const void *W, const in
 
 // CTAs of an instance of n cells: one per CELLS cells of each 32-cell tile.
 static int64_t ctas_for(int v, int64_t n) {
-    const int G = 32 / kVariants[v].cells;
+    const int G = 32 / kVariants[v].cells;      // CTAs per 32-cell tile
     return ((n + 31) / 32) * G;
 }
 
@@ -755,9 +947,9 @@ static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, 
 
 // FP64 form: the same kernel on double spectra and weights, on 16-cell tiles
 // (variant entry 2) or, where the double spectrum of 16 cells does not fit
-// shared memory, on 8- or 4-cell tiles (entries 4, 5: 48^2, 16^3); no
+// shared memory, on 8- or 4-cell tiles (entries 5, 6: 48^2, 16^3); no
 // last-wave split.  The FP32X2 form runs on the same layout.
-constexpr int kFp64Variants[3] = {2, 4, 5};
+constexpr int kFp64Variants[3] = {2, 5, 6};
 
 bool modesum64_available(const bz_modes *m) { return m->w64 != nullptr; }
 
@@ -772,7 +964,7 @@ cudaError_t launch_modesum64(const bz_modes *m, const double2 *fhat, double2 *Qh
     gd.tile_start[1] = ctas_for(m->variant64, n);
     const size_t sm = smem_bytes<double>(m->g->v, m->rowmax64, m->variant64);
     if (m->variant64 == 2) return launch_instance<double, 4, 16, 16>(gd, sm, st);
-    if (m->variant64 == 4) return launch_instance<double, 2, 8, 8>(gd, sm, st);
+    if (m->variant64 == 5) return launch_instance<double, 2, 8, 8>(gd, sm, st);
     return launch_instance<double, 2, 8, 4>(gd, sm, st);
 }
 
@@ -798,7 +990,7 @@ cudaError_t launch_modesum_x2(const bz_modes *m, const double2 *fhat, float2 *Qh
     // parts of FP32 instead of one double) and weight rows of 8-byte slots
     const size_t sm = smem_bytes<double>(m->g->v, m->rowmax64, m->variant64);
     if (m->variant64 == 2) return launch_x2_instance<4, 16, 16>(m, fhat, Qhat, n, sm, st);
-    if (m->variant64 == 4) return launch_x2_instance<2, 8, 8>(m, fhat, Qhat, n, sm, st);
+    if (m->variant64 == 5) return launch_x2_instance<2, 8, 8>(m, fhat, Qhat, n, sm, st);
     return launch_x2_instance<2, 8, 4>(m, fhat, Qhat, n, sm, st);
 }
 

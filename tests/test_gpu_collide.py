@@ -70,15 +70,15 @@ def test_fast_kernels_selected(bz):
     and the 3-D grids up to 16^3 (a silent fall back to the generic kernel would
     hide a table-building bug)."""
     for N in (16, 24, 32):
-        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant in (1, 2, 3), N
+        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant in (1, 2, 3, 5), N
     assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_variant == 3    # only 16-cell tiles fit
     assert bz.Modes(bz.Grid(3, 16, 10.0), 1.0).modesum_variant == 4    # 8-cell tiles, 3-D rows
-    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant in (1, 2, 3)   # 16-wide blocks overhang a 7-mode row
+    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant in (1, 2, 3, 5)   # 16-wide blocks overhang a 7-mode row
     assert bz.Modes(bz.Grid(2, 64, 10.0), 1.0).modesum_variant == 0
 
 
-@pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3)]
-                         + [(2, 16, 4), (3, 8, 1), (3, 8, 2), (3, 8, 3)])
+@pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3, 5)]
+                         + [(2, 16, 4), (3, 8, 1), (3, 8, 2), (3, 8, 3), (3, 8, 5)])
 def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, dim, N, variant):
     """Every register-blocked variant (fixed through BZ_MODESUM_VARIANT, bypassing
     the autotuner) against the oracle: 70 cells = 2 full tiles and a ragged tail."""
@@ -107,7 +107,7 @@ def test_last_wave_split_is_exact(bz, monkeypatch):
     n = sms * 32 + 70
     f = workloads.bi_maxwellian(n, 2, N, L, seed=1500)
     m = bz.Modes(bz.Grid(2, N, L), 1.0)
-    if m.modesum_variant not in (1, 2):
+    if m.modesum_variant not in (1, 2, 5):
         pytest.skip("timed variant is not a 32-cell one")
     Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32").cpu().numpy()
     monkeypatch.setenv("BZ_MODESUM_VARIANT", str(m.modesum_variant))
