@@ -159,3 +159,59 @@ def test_penalty_factor_matches_oracle_and_drops_graphs(bz):
     for bad in (0.0, -1.0, float("inf"), float("nan")):
         with pytest.raises(bz.BzError):
             m.set_penalty(bad)
+
+
+@pytest.mark.parametrize("N", [16, 32])
+@pytest.mark.parametrize("scheme", ["ars222", "euler"])
+@pytest.mark.parametrize("conserve,with_L", [(False, False), (True, True)])
+def test_fused_step_equals_stage_chain(bz, N, scheme, conserve, with_L):
+    """The FP32 step on 16^2 / 32^2 grids runs on the fused stage kernels
+    (inverse DFT, G, the next stage's update and the forward DFT in one
+    launch); the same arithmetic in the same order as the per-stage chain of
+    imex_stage_local, so f^{n+1} must equal the chain's last stage value bit
+    for bit, on the legacy stream (direct launches), in a captured graph and its
+    replay; 70 cells (a ragged tile)."""
+    import torch
+    L, n = 10.0, 70
+    f = to_dev(workloads.bi_maxwellian(n, 2, N, L, seed=40 + N, noise=0.05), "fp32")
+    s = bz.STAGES[scheme]
+    Lres = None
+    if with_L:
+        rng = np.random.default_rng(N)
+        Lres = to_dev(0.01 * rng.normal(size=(s, n, N * N)), "fp32")
+    m = bz.Modes(bz.Grid(2, N, L), 1.0)
+    dt, eps = 2.5e-4, 5e-3
+    F = torch.zeros((s, n, N * N), dtype=torch.float32, device="cuda")
+    G = torch.zeros_like(F)
+    P = torch.zeros_like(F)
+    for l in range(1, s + 1):
+        bz.imex_stage_local(m, l, f, F, G, P, dt, eps, scheme=scheme, L_res=Lres, conserve=conserve, precision="fp32")
+    bz.check()
+    want = F[s - 1].cpu().numpy()
+    got = bz.imex_step(m, f, dt, eps, scheme=scheme, L_res=Lres, conserve=conserve, precision="fp32")
+    bz.check()
+    assert np.array_equal(got.cpu().numpy(), want)
+    st = torch.cuda.Stream()
+    out = torch.full_like(f, float("nan"))
+    with torch.cuda.stream(st):
+        for _ in range(2):              # capture, then a replay
+            bz.imex_step(m, f, dt, eps, f_out=out, scheme=scheme, L_res=Lres, conserve=conserve, precision="fp32",
+                         stream=st)
+            bz.check(st)
+            assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_fused_step_fast_form(bz):
+    """The fused step with the fast (Carleman) operator equals its stage chain."""
+    import torch
+    N, L, n = 32, 10.0, 40
+    f = to_dev(workloads.bi_maxwellian(n, 2, N, L, seed=48), "fp32")
+    m = bz.FastModes(bz.Grid(2, N, L), 8)
+    F = torch.zeros((3, n, N * N), dtype=torch.float32, device="cuda")
+    G = torch.zeros_like(F)
+    P = torch.zeros_like(F)
+    for l in (1, 2, 3):
+        bz.imex_stage_local(m, l, f, F, G, P, 2.5e-4, 5e-3, precision="fp32")
+    got = bz.imex_step(m, f, 2.5e-4, 5e-3, precision="fp32")
+    bz.check()
+    assert np.array_equal(got.cpu().numpy(), F[2].cpu().numpy())
