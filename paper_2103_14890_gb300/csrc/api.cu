@@ -454,73 +454,6 @@ int run_stage(const bz_modes *m, const Tableau &t, int l, int model, double dt, 
     return BZ_OK;
 }
 
-// Coefficients of stage l (row l of the tableaux) for the stage kernels.
-StageCoef stage_coef(const bz_modes *m, const Tableau &t, int l, int model, double dt, double eps) {
-    StageCoef c;
-    memset(&c, 0, sizeof c);
-    c.stage = l;
-    c.nprev = l;
-    for (int q = 0; q < l; ++q) {
-        c.at[q] = t.At[l][q];
-        c.a[q] = t.A[l][q];
-    }
-    c.all = t.A[l][l];
-    c.dt = dt;
-    c.eps = eps;
-    c.nuf = (model == BZ_BOLTZMANN) ? m->penalty : 1.0;
-    return c;
-}
-
-// The fused stage kernels serve the FP32 Boltzmann step on 2-D 16^2 / 32^2
-// grids when every stage but the last feeds a later one through G.
-bool fused_step_ok(const bz_modes *m, const Tableau &t, int model, int precision) {
-    if (precision != BZ_FP32 || model != BZ_BOLTZMANN || !m->tile_dft || !imex_fused_supported(m->g->v)) return false;
-    for (int l = 0; l + 1 < t.s; ++l) {
-        bool need = false;
-        for (int q = l + 1; q < t.s; ++q)
-            if (t.At[q][l] != 0.0) need = true;
-        if (!need) return false;
-    }
-    return true;
-}
-
-// One step on the fused kernels: stage 0's update with the forward DFT of F_0,
-// then per stage l the mode sum of F_l and one kernel that forms G_l, the
-// update of stage l + 1 and the forward DFT of F_{l+1} (the last one stores
-// f^{n+1} instead).  Scratch as step_sequence.
-int step_sequence_fused(const bz_modes *m, const Tableau &t, double dt, double eps, const void *f_n, void *f_out,
-                        const void *L_res, int64_t n, int flags, cudaStream_t st, void *scratch) {
-    const GridView &v = m->g->v;
-    const int64_t stride = n * v.nv;
-    float *G = static_cast<float *>(scratch);
-    float *P = G + (size_t)t.s * stride;
-    char *coll = reinterpret_cast<char *>(P + (size_t)(t.s + 1) * stride);   // after P and the stage buffer
-    float2 *fh = reinterpret_cast<float2 *>(coll);
-    float2 *qh = reinterpret_cast<float2 *>(coll + spectrum_bytes(m, BZ_FP32, n));
-    const float *fn = static_cast<const float *>(f_n);
-    const float *Lr = static_cast<const float *>(L_res);
-    const int conserve = (flags & BZ_CONSERVE) ? 1 : 0;
-    const StageCoef c0 = stage_coef(m, t, 0, BZ_BOLTZMANN, dt, eps);
-    BZ_LAUNCH("imex_fused_f32", st,
-              launch_imex_fused_f32(v, c0, -1, false, true, 0, conserve, m->scale, m->g->cinv, nullptr, fn, G, P, Lr,
-                                    nullptr, fh, n, st),
-              "imex_step: stage 0");
-    for (int l = 0; l + 1 < t.s; ++l) {
-        int rc = phase_modesum(m, BZ_FP32, fh, qh, n, st);
-        if (rc) return rc;
-        const StageCoef c = stage_coef(m, t, l + 1, BZ_BOLTZMANN, dt, eps);
-        const bool last = l + 2 == t.s;
-        int store_G = 0;
-        for (int q = l + 2; q < t.s; ++q)
-            if (t.At[q][l] != 0.0) store_G = 1;
-        BZ_LAUNCH("imex_fused_f32", st,
-                  launch_imex_fused_f32(v, c, l, true, !last, store_G, conserve, m->scale, m->g->cinv, qh, fn, G, P,
-                                        Lr, last ? static_cast<float *>(f_out) : nullptr, fh, n, st),
-                  "imex_step: fused stage");
-    }
-    return BZ_OK;
-}
-
 // ---- CUDA-graph cache of imex_step ----
 // One captured graph per distinct argument set (pointers, sizes, dt, eps,
 // scheme, model, precision, flags); each entry owns its scratch, allocated
@@ -571,8 +504,6 @@ int step_sequence(const bz_modes *m, const Tableau &t, int model, double dt, dou
                   void *scratch) {
     const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
     const int64_t stride = n * m->g->v.nv;
-    if (fused_step_ok(m, t, model, precision))
-        return step_sequence_fused(m, t, dt, eps, f_n, f_out, L_res, n, flags, st, scratch);
     char *G = static_cast<char *>(scratch);
     char *P = G + (size_t)t.s * stride * es;
     char *Fbuf = P + (size_t)t.s * stride * es;

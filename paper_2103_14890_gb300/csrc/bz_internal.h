@@ -250,17 +250,6 @@ struct StageCoef {
     double dt, eps;
     double nuf;                // penalty rate nu = nuf * rho
 };
-// Fused IMEX stage (k_dft32.cu), FP32, 2-D N in {16, 32}: optionally the
-// inverse DFT of Q-hat(F_l) and G_l = Q - P_l (stored if store_G), the
-// update of stage c.stage = l + 1 (or of stage 0 when !inv) with F and
-// P_{c.stage}, then optionally the forward DFT of F into fhat; without fwd the
-// stage value F is stored to Fout.  c.nprev counts the stages whose G, P, L
-// enter R; with inv, stage l's G comes from the inverse DFT.
-bool imex_fused_supported(const GridView &g);
-cudaError_t launch_imex_fused_f32(const GridView &g, const StageCoef &c, int l, bool inv, bool fwd, int store_G,
-                                  int conserve, double scale, const double *cinv, const float2 *Qhat,
-                                  const float *fn, float *G, float *P, const float *Lres, float *Fout,
-                                  float2 *fhat, int64_t n, cudaStream_t st);
 cudaError_t launch_imex_stage_f64(const GridView &g, const StageCoef &c, const double *fn,
                                   double *F, const double *G, double *P, const double *Lres,
                                   int64_t stride, int64_t n, cudaStream_t st);

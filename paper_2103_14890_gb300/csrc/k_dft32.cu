@@ -541,348 +541,6 @@ cudaError_t inv_any(const GridView &g, const typename C2<T>::type *Qhat, T *Q, i
     }
 }
 
-// ---------------------------------------------------------------------------
-// Fused IMEX stage kernel (Sec. 3.4, the penalised scheme after eq. Bref2):
-// for C = 8 cells per CTA (8 warps, warp w owns cell w, lane = column j2), in
-// one launch
-//   1. (DO_INV) the inverse DFT of Q-hat(F_l) (the two passes of
-//      fft_inv32_kernel, with the optional conservation projection) and
-//      G_l = Q(F_l) - P_l, kept in registers and stored only if a stage after
-//      l + 1 reads it;
-//   2. the explicit part of stage l + 1,
-//      R = f^n + dt sum_{m <= l} [At (G_m / eps - L_m) + A P_m / eps],
-//      with G_l from registers and the earlier G_m, P_m, L_m from memory;
-//   3. the moments of R (FP32 TwoSum partials per column, FP64 across the
-//      columns), the Maxwellian parameters in FP64, the separable Maxwellian
-//      M, F = (R + c M) / (1 + c) and P_{l+1} = nu (M - F) (the implicit BGK
-//      solve of stage l + 1), as imex_stage2d_kernel computes them;
-//   4. (DO_FWD) the forward DFT of F_{l+1} (the two passes of
-//      fft_fwd32_kernel) into the tiled spectrum for the next mode sum; the
-//      last stage stores F (= f^{n+1}, the tableaux are stiffly accurate)
-//      instead.
-// F_{l+1} and G_l never leave the chip unless a later stage needs them.
-struct FusedStageArgs {
-    const float2 *Qhat;     // mode sums of F_l (DO_INV)
-    const float *fn;        // f^n
-    float *G;               // [stages][n][NV] stage values G_m
-    float *P;               // [stages][n][NV] penalty terms P_m
-    const float *Lres;      // [stages][n][NV] transport residuals or null
-    float *Fout;            // last stage: F (f^{n+1})
-    float2 *fhat;           // DO_FWD: spectrum of F_{l+1}
-    int64_t stride, n;
-    int l;                  // stage whose mode sums arrive (DO_INV)
-    int store_G;            // write G_l (a stage after l + 1 reads it)
-    int conserve;
-    float scale;            // s^(d + gamma)
-    double L, dv;
-    Cinv cinv;
-    StageCoef c;            // coefficients of stage l + 1 (c.nprev = l + 1, or 1 for stage 0... see launcher)
-};
-
-constexpr int kFusedCells = 8;
-
-template <int N, bool DO_INV, bool DO_FWD>
-__global__ void __launch_bounds__(kFusedCells * 32, 2) imex_fused32_kernel(const FusedStageArgs a) {
-    using V2 = float2;
-    using S = float;
-    constexpr int C = kFusedCells, H = N / 2, M = N - 1, LH = ilog2(H), LN = ilog2(N), NV = N * N;
-    constexpr int P = C + 1, NROW = C * H;          // (cell, row) units of the row passes
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V2 *Bs = reinterpret_cast<V2 *>(smem_raw);                          // [H][N][P]
-    double *part = reinterpret_cast<double *>(Bs + H * N * P);           // [C][4][33]
-    double *par = part + C * 4 * 33;                                     // [C][8]
-    const int64_t tile = blockIdx.x / (32 / C);
-    const int sub = (int)(blockIdx.x % (32 / C)) * C;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool col = lane < N;
-    const S dt = (S)a.c.dt, ieps = (S)(1.0 / a.c.eps);
-
-    // ---- 1a. inverse DFT, pass 1: thread = (cell, row k1) ----
-    if constexpr (DO_INV) {
-        const int cell = threadIdx.x % C;
-        const V2 *qt = a.Qhat + tile * (int64_t)(H * M) * 32 + sub + cell;
-#pragma unroll 1
-        for (int t = threadIdx.x; t < NROW; t += C * 32) {
-            const int k1 = t / C;
-            V2 v[N];
-            v[bitrev(H, LN)] = cmk<V2>((S)0., (S)0.);
-#pragma unroll
-            for (int kk = 0; kk < M; ++kk) {
-                const int k2 = kk - (H - 1);
-                const V2 q = qt[(k1 * M + kk) * 32];
-                v[bitrev(k2 & (N - 1), LN)] = (k2 & 1) ? cmk<V2>(-q.x, -q.y) : q;
-            }
-            fft_dit<N, +1>(v);
-            const S sc = (k1 & 1) ? -a.scale : a.scale;
-#pragma unroll
-            for (int j = 0; j < N; ++j) Bs[(k1 * N + j) * P + cell] = cmk<V2>(v[j].x * sc, v[j].y * sc);
-        }
-        __syncthreads();
-    }
-
-    // ---- 1b, 2. this warp's cell: Q column, G_l, R column, moment partials ----
-    S r[N];
-    {
-        const int c = warp;
-        const int64_t cell = tile * 32 + sub + c;
-        const bool live = cell < a.n && col;
-        const int64_t base = (cell < a.n ? cell : 0) * NV + (col ? lane : 0);
-#pragma unroll
-        for (int j = 0; j < N; ++j) r[j] = live ? a.fn[base + j * N] : (S)0.;
-        for (int m = 0; m < a.c.nprev; ++m) {
-            if (DO_INV && m == a.l) continue;       // stage l's terms come from registers below
-            const S ca = dt * (S)a.c.at[m] * ieps, cb = dt * (S)a.c.a[m] * ieps, cl = dt * (S)a.c.at[m];
-            if (ca == (S)0. && cb == (S)0.) continue;
-            const int64_t o = (int64_t)m * a.stride + base;
-            if (live) {
-#pragma unroll
-                for (int j = 0; j < N; ++j) {
-                    S t = r[j];
-                    if (ca != (S)0.) t = fma(ca, a.G[o + j * N], t);
-                    if (cb != (S)0.) t = fma(cb, a.P[o + j * N], t);
-                    if (a.Lres && cl != (S)0.) t = fma(-cl, a.Lres[o + j * N], t);
-                    r[j] = t;
-                }
-            }
-        }
-        if constexpr (DO_INV) {
-            // pass 2 of the inverse DFT for this column: Hermitian-to-real over k1
-            S q[N];
-            if (col) {
-                V2 x[H + 1];
-#pragma unroll
-                for (int k = 0; k < H; ++k) x[k] = Bs[(k * N + lane) * P + c];
-                x[0].y = (S)0.;
-                x[H] = cmk<V2>((S)0., (S)0.);
-                V2 z[H];
-#pragma unroll
-                for (int k = 0; k < H; ++k) {
-                    const V2 xk = x[k], xc = cmk<V2>(x[H - k].x, -x[H - k].y);
-                    S ex, ey, ox, oy;
-                    if (k == 0) {
-                        ex = xk.x; ey = xk.y; ox = xk.x; oy = xk.y;
-                    } else {
-                        ex = xk.x + xc.x;
-                        ey = xk.y + xc.y;
-                        const S dx = xk.x - xc.x, dy = xk.y - xc.y;
-                        const V2 w = tw32<V2>(k * (32 / N));
-                        ox = dx * w.x + dy * w.y;
-                        oy = dy * w.x - dx * w.y;
-                    }
-                    z[bitrev(k, LH)] = cmk<V2>(ex - oy, ey + ox);
-                }
-                fft_dit<H, +1>(z);
-#pragma unroll
-                for (int p = 0; p < H; ++p) {
-                    q[2 * p] = z[p].x;
-                    q[2 * p + 1] = z[p].y;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < N; ++j) q[j] = (S)0.;
-            }
-            if (a.conserve) {
-                // smallest L2 change of Q that zeroes its moments of 1, v, |v|^2
-                const S v2c = (S)(-a.L + lane * a.dv);
-                double mom[4];
-                {
-                    S s0 = 0, e0 = 0, s1 = 0, e1 = 0, s3 = 0, e3 = 0;
-#pragma unroll
-                    for (int j = 0; j < N; ++j) {
-                        const S v1 = (S)(-a.L + j * a.dv);
-                        const S t0 = col ? q[j] : (S)0.;
-                        S sx, bb;
-                        sx = s0 + t0; bb = sx - s0; e0 += (s0 - (sx - bb)) + (t0 - bb); s0 = sx;
-                        const S t1 = v1 * t0;
-                        sx = s1 + t1; bb = sx - s1; e1 += (s1 - (sx - bb)) + (t1 - bb); s1 = sx;
-                        const S t3 = v1 * v1 * t0;
-                        sx = s3 + t3; bb = sx - s3; e3 += (s3 - (sx - bb)) + (t3 - bb); s3 = sx;
-                    }
-                    const double S0 = (double)s0 + e0, S1 = (double)s1 + e1, S3 = (double)s3 + e3;
-                    const double vv = col ? (double)(-a.L + lane * a.dv) : 0.0;
-                    mom[0] = S0;
-                    mom[1] = S1;
-                    mom[2] = vv * S0;
-                    mom[3] = S3 + vv * vv * S0;
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) mom[k] += __shfl_xor_sync(0xffffffffu, mom[k], o);
-                double xs[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    double t = 0.0;
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) t += a.cinv.v[e * 4 + f] * mom[f];
-                    xs[e] = t;
-                }
-                const S x0 = (S)xs[0], x1 = (S)xs[1], x2 = (S)xs[2], x3 = (S)xs[3];
-#pragma unroll
-                for (int j = 0; j < N; ++j) {
-                    const S v1 = (S)(-a.L + j * a.dv);
-                    q[j] -= x0 + x1 * v1 + x2 * v2c + x3 * (v1 * v1 + v2c * v2c);
-                }
-            }
-            // G_l = Q - P_l, and its terms (with P_l's and L_l's) in R
-            const S ca = dt * (S)a.c.at[a.l] * ieps, cb = dt * (S)a.c.a[a.l] * ieps, cl = dt * (S)a.c.at[a.l];
-            const int64_t o = (int64_t)a.l * a.stride + base;
-            if (live) {
-#pragma unroll
-                for (int j = 0; j < N; ++j) {
-                    const S pl = a.P[o + j * N];
-                    const S gl = q[j] - pl;
-                    if (a.store_G) a.G[o + j * N] = gl;
-                    S t = fma(ca, gl, r[j]);
-                    t = fma(cb, pl, t);
-                    if (a.Lres) t = fma(-cl, a.Lres[o + j * N], t);
-                    r[j] = t;
-                }
-            }
-        }
-        // this column's moment partials of R
-        {
-            S s0 = 0, e0 = 0, s1 = 0, e1 = 0, s3 = 0, e3 = 0;
-            const S Lf = (S)a.L, dvf = (S)a.dv;
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                const S v1 = fma((S)j, dvf, -Lf);
-                const S t0 = live ? r[j] : (S)0.;
-                S sx, bb;
-                sx = s0 + t0; bb = sx - s0; e0 += (s0 - (sx - bb)) + (t0 - bb); s0 = sx;
-                const S t1 = v1 * t0;
-                sx = s1 + t1; bb = sx - s1; e1 += (s1 - (sx - bb)) + (t1 - bb); s1 = sx;
-                const S t3 = v1 * v1 * t0;
-                sx = s3 + t3; bb = sx - s3; e3 += (s3 - (sx - bb)) + (t3 - bb); s3 = sx;
-            }
-            const double vv = -a.L + lane * a.dv;
-            const double S0 = (double)s0 + (double)e0, S1 = (double)s1 + (double)e1, S3 = (double)s3 + (double)e3;
-            part[(c * 4 + 0) * 33 + lane] = S0;
-            part[(c * 4 + 1) * 33 + lane] = S1;
-            part[(c * 4 + 2) * 33 + lane] = vv * S0;
-            part[(c * 4 + 3) * 33 + lane] = S3 + vv * vv * S0;
-        }
-    }
-    __syncthreads();
-    // ---- 3. moments over the 32 columns (four threads per cell and moment) ----
-    if (threadIdx.x < C * 16) {
-        const int cc = threadIdx.x >> 4, q = (threadIdx.x >> 2) & 3, pp = threadIdx.x & 3;
-        double tot = 0.0;
-#pragma unroll
-        for (int l = 0; l < 8; ++l) tot += part[(cc * 4 + q) * 33 + pp * 8 + l];
-        tot += __shfl_xor_sync(0xffffffffu, tot, 1);
-        tot += __shfl_xor_sync(0xffffffffu, tot, 2);
-        if (pp == 0) part[(cc * 4 + q) * 33 + 32] = tot;
-    }
-    __syncthreads();
-    if (threadIdx.x < C) {
-        const int cc = threadIdx.x;
-        const double w = a.dv * a.dv;
-        const double rho = w * part[(cc * 4 + 0) * 33 + 32];
-        const double u1 = w * part[(cc * 4 + 1) * 33 + 32] / rho, u2 = w * part[(cc * 4 + 2) * 33 + 32] / rho;
-        const double E = 0.5 * w * part[(cc * 4 + 3) * 33 + 32];
-        const double theta = (2.0 * E / rho - (u1 * u1 + u2 * u2)) / 2.0;
-        const double cst = a.c.dt * a.c.all * a.c.nuf * rho / a.c.eps;
-        par[cc * 8 + 0] = a.c.nuf * rho;
-        par[cc * 8 + 1] = u1;
-        par[cc * 8 + 2] = u2;
-        par[cc * 8 + 3] = 0.5 / theta;
-        par[cc * 8 + 4] = rho / (2.0 * M_PI * theta);
-        par[cc * 8 + 5] = cst;
-        par[cc * 8 + 6] = 1.0 / (1.0 + cst);
-    }
-    __syncthreads();
-    // ---- 3b. Maxwellian, implicit solve, P_{l+1}; 4. forward DFT pass 1 or the final store ----
-    const double vl = -a.L + lane * a.dv;
-    {
-        const int c = warp;
-        const int64_t cell = tile * 32 + sub + c;
-        const bool live = cell < a.n && col;
-        const int64_t base = (cell < a.n ? cell : 0) * NV + (col ? lane : 0);
-        const double *pc = par + c * 8;
-        const S d2 = (S)(vl - pc[2]), d1 = (S)(vl - pc[1]);
-        const S i2t = (S)pc[3];
-        const S fcol = (S)pc[4] * expf(-d2 * d2 * i2t);
-        const S frow_l = expf(-d1 * d1 * i2t);
-        const S cT = (S)pc[5], denom = (S)pc[6], nuT = (S)pc[0];
-        S F[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const S frow = __shfl_sync(0xffffffffu, frow_l, j);
-            const S Mx = fcol * frow;
-            F[j] = (r[j] + cT * Mx) * denom;
-            if (live) a.P[(int64_t)a.c.stage * a.stride + base + j * N] = nuT * (Mx - F[j]);
-        }
-        if constexpr (!DO_FWD) {
-            if (live)
-#pragma unroll
-                for (int j = 0; j < N; ++j) a.Fout[base + j * N] = F[j];
-        } else {
-            if (col) {
-                V2 z[H];
-#pragma unroll
-                for (int p = 0; p < H; ++p) z[bitrev(p, LH)] = cmk<V2>(live ? F[2 * p] : (S)0., live ? F[2 * p + 1] : (S)0.);
-                fft_dit<H, -1>(z);
-#pragma unroll
-                for (int k = 0; k < H; ++k) {
-                    const V2 zk = z[k], zc = z[(H - k) % H];
-                    const S ex = (S)0.5 * (zk.x + zc.x), ey = (S)0.5 * (zk.y - zc.y);
-                    const S ox = (S)0.5 * (zk.y + zc.y), oy = -(S)0.5 * (zk.x - zc.x);
-                    const V2 w = tw32<V2>(k * (32 / N));
-                    const S xr = ex + (w.x * ox - w.y * oy);
-                    const S xi = ey + (w.x * oy + w.y * ox);
-                    const S sc = (k & 1) ? -(S)1. / N : (S)1. / N;
-                    Bs[(k * N + lane) * P + c] = cmk<V2>(xr * sc, xi * sc);
-                }
-            }
-        }
-    }
-    if constexpr (DO_FWD) {
-        __syncthreads();
-        // ---- 4b. forward DFT pass 2: thread = (cell, row k1) ----
-        const int cell = threadIdx.x % C;
-        const int64_t gc = tile * 32 + sub + cell;
-#pragma unroll 1
-        for (int t = threadIdx.x; t < NROW; t += C * 32) {
-            const int k1 = t / C;
-            V2 v[N];
-#pragma unroll
-            for (int j = 0; j < N; ++j) v[bitrev(j, LN)] = Bs[(k1 * N + j) * P + cell];
-            fft_dit<N, -1>(v);
-            if (gc < a.n) {
-                V2 *out = a.fhat + tile * (int64_t)(H * M) * 32 + (int64_t)k1 * M * 32 + sub + cell;
-#pragma unroll
-                for (int kk = 0; kk < M; ++kk) {
-                    const int k2 = kk - (H - 1);
-                    const S sc = (k2 & 1) ? -(S)1. / N : (S)1. / N;
-                    const V2 vv = v[k2 & (N - 1)];
-                    out[kk * 32] = cmk<V2>(vv.x * sc, vv.y * sc);
-                }
-            }
-        }
-    }
-}
-
-template <int N, bool DO_INV, bool DO_FWD>
-cudaError_t launch_fused(const FusedStageArgs &a, cudaStream_t st) {
-    constexpr int C = kFusedCells;
-    const size_t sm = sizeof(float2) * (size_t)(N / 2) * N * (C + 1) + sizeof(double) * (C * 4 * 33 + C * 8);
-    cudaError_t e =
-        cudaFuncSetAttribute(imex_fused32_kernel<N, DO_INV, DO_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)(((a.n + 31) / 32) * (32 / C));
-    imex_fused32_kernel<N, DO_INV, DO_FWD><<<grid, C * 32, sm, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int N>
-cudaError_t launch_fused_n(const FusedStageArgs &a, bool inv, bool fwd, cudaStream_t st) {
-    if (inv && fwd) return launch_fused<N, true, true>(a, st);
-    if (inv) return launch_fused<N, true, false>(a, st);
-    if (fwd) return launch_fused<N, false, true>(a, st);
-    return launch_fused<N, false, false>(a, st);
-}
-
 }  // namespace
 
 bool dft32_tile_supported(const GridView &g) {
@@ -908,36 +566,6 @@ cudaError_t launch_dft64_forward_tile_f32in(const GridView &g, const float *f, d
                                             cudaStream_t st) {
     return fwd_any<double, float>(g, f, fhat, n, st);
 }
-bool imex_fused_supported(const GridView &g) { return g.dim == 2 && (g.N == 16 || g.N == 32); }
-
-cudaError_t launch_imex_fused_f32(const GridView &g, const StageCoef &c, int l, bool inv, bool fwd, int store_G,
-                                  int conserve, double scale, const double *cinv, const float2 *Qhat,
-                                  const float *fn, float *G, float *P, const float *Lres, float *Fout,
-                                  float2 *fhat, int64_t n, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    FusedStageArgs a;
-    a.Qhat = Qhat;
-    a.fn = fn;
-    a.G = G;
-    a.P = P;
-    a.Lres = Lres;
-    a.Fout = Fout;
-    a.fhat = fhat;
-    a.stride = n * g.nv;
-    a.n = n;
-    a.l = l;
-    a.store_G = store_G;
-    a.conserve = conserve;
-    a.scale = (float)scale;
-    a.L = g.L;
-    a.dv = g.dv;
-    for (int i = 0; i < 25; ++i) a.cinv.v[i] = cinv[i];
-    a.c = c;
-    if (g.N == 16) return launch_fused_n<16>(a, inv, fwd, st);
-    if (g.N == 32) return launch_fused_n<32>(a, inv, fwd, st);
-    return cudaErrorInvalidValue;
-}
-
 cudaError_t launch_dft32_inverse_tile(const GridView &g, const float2 *Qhat, float *Q, int64_t n, double scale,
                                       const double *cinv, const InvEpilogue &ep, cudaStream_t st) {
     return inv_any<float>(g, Qhat, Q, n, scale, cinv, ep, st);

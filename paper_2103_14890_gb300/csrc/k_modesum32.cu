@@ -302,13 +302,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
 // accumulation is one FP32x2 instruction (__fmul2_rn / __ffma2_rn: two
 // independent IEEE FP32 operations, the same results as two scalar ones).
 // Each weight is stored twice, (w, w), so it is an FP32x2 operand as loaded.
-// The real part of w f-hat_l f-hat_m is kept as two sums, A = sum w a_re b_re
-// and B = sum w a_im b_im (re = A - B at each fold), so no operand needs a
-// negation; for l_1 < 0 the conjugate f-hat_l is formed once per l_2 step.
-// The two lane groups of a warp split a task's 2 R outputs as in the 16-cell
-// variant.
+// Every lane performs exactly the operations of the scalar kernels, in the
+// same order (tx = w a_re, ty = w a_im, re += tx b_re then += (-ty) b_im, im
+// += tx b_im then += ty b_re, with the signs of a conjugated f-hat_l for
+// l_1 < 0), so its results equal theirs bit for bit and the variants can
+// share one batch (whole waves on one, the last wave on another).  The two
+// lane groups of a warp split a task's 2 R outputs as in the 16-cell variant.
 struct P2Acc {
-    float2 a, b, c;       // sum w re re, sum w im im, sum w (re im + im re)
+    float2 re, im;
 };
 
 template <int RR, int PH, int DIR>
@@ -322,7 +323,7 @@ __device__ __forceinline__ void block_pass_p2(float4 (&win)[2 * RR], const float
     for (int s = 0; s < RR; ++s) {
         const float4 av = lp[s * DIR * CS];
         const float2 ar = make_float2(av.x, av.y);
-        const float2 ai = DIR > 0 ? make_float2(av.z, av.w) : make_float2(-av.z, -av.w);
+        const float2 ai = make_float2(av.z, av.w), an = make_float2(-av.z, -av.w);
         float2 w2[RR];
 #pragma unroll
         for (int q = 0; q < RR; q += 2) {
@@ -334,11 +335,12 @@ __device__ __forceinline__ void block_pass_p2(float4 (&win)[2 * RR], const float
         for (int r = 0; r < RR; ++r) {
             const float4 bv = win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)];
             const float2 br = make_float2(bv.x, bv.y), bi = make_float2(bv.z, bv.w);
-            const float2 tx = __fmul2_rn(w2[r], ar), ty = __fmul2_rn(w2[r], ai);
-            acc[r].a = __ffma2_rn(tx, br, acc[r].a);
-            acc[r].b = __ffma2_rn(ty, bi, acc[r].b);
-            acc[r].c = __ffma2_rn(tx, bi, acc[r].c);
-            acc[r].c = __ffma2_rn(ty, br, acc[r].c);
+            const float2 tx = __fmul2_rn(w2[r], ar);
+            const float2 ty = __fmul2_rn(w2[r], ai), tn = __fmul2_rn(w2[r], an);   // w a_im, -(w a_im)
+            acc[r].re = __ffma2_rn(tx, br, acc[r].re);
+            acc[r].re = __ffma2_rn(DIR > 0 ? tn : ty, bi, acc[r].re);
+            acc[r].im = __ffma2_rn(tx, bi, acc[r].im);
+            acc[r].im = __ffma2_rn(DIR > 0 ? ty : tn, br, acc[r].im);
         }
     }
 }
@@ -420,7 +422,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_p2_kernel(const Mode32G
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
             hre[r] = lre[r] = him[r] = lim[r] = make_float2(0.f, 0.f);
-            acc[r].a = acc[r].b = acc[r].c = make_float2(0.f, 0.f);
+            acc[r].re = acc[r].im = make_float2(0.f, 0.f);
         }
         const int k20 = tk.k20 + grp * RR;
         const int mbase0 = k20 - tk.l2lo - (RR - 1);
@@ -445,15 +447,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_p2_kernel(const Mode32G
             if ((i & 3) == 3 || i + 1 == tk.nrows) {
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
-                    const float2 re = __fadd2_rn(acc[r].a, make_float2(-acc[r].b.x, -acc[r].b.y));
                     float2 sm, e;
-                    two_sum2(hre[r], re, sm, e);
+                    two_sum2(hre[r], acc[r].re, sm, e);
                     hre[r] = sm;
                     lre[r] = __fadd2_rn(lre[r], e);
-                    two_sum2(him[r], acc[r].c, sm, e);
+                    two_sum2(him[r], acc[r].im, sm, e);
                     him[r] = sm;
                     lim[r] = __fadd2_rn(lim[r], e);
-                    acc[r].a = acc[r].b = acc[r].c = make_float2(0.f, 0.f);
+                    acc[r].re = acc[r].im = make_float2(0.f, 0.f);
                 }
             }
         }

@@ -164,13 +164,11 @@ def test_penalty_factor_matches_oracle_and_drops_graphs(bz):
 @pytest.mark.parametrize("N", [16, 32])
 @pytest.mark.parametrize("scheme", ["ars222", "euler"])
 @pytest.mark.parametrize("conserve,with_L", [(False, False), (True, True)])
-def test_fused_step_equals_stage_chain(bz, N, scheme, conserve, with_L):
-    """The FP32 step on 16^2 / 32^2 grids runs on the fused stage kernels
-    (inverse DFT, G, the next stage's update and the forward DFT in one
-    launch); the same arithmetic in the same order as the per-stage chain of
-    imex_stage_local, so f^{n+1} must equal the chain's last stage value bit
-    for bit, on the legacy stream (direct launches), in a captured graph and its
-    replay; 70 cells (a ragged tile)."""
+def test_step_equals_stage_chain(bz, N, scheme, conserve, with_L):
+    """imex_step (FP32, 16^2 / 32^2) runs the arithmetic of the per-stage chain
+    of imex_stage_local in the same order, so f^{n+1} must equal the chain's
+    last stage value bit for bit: on the legacy stream (direct launches), in a
+    captured graph and its replay; 70 cells (a ragged tile)."""
     import torch
     L, n = 10.0, 70
     f = to_dev(workloads.bi_maxwellian(n, 2, N, L, seed=40 + N, noise=0.05), "fp32")
@@ -201,8 +199,8 @@ def test_fused_step_equals_stage_chain(bz, N, scheme, conserve, with_L):
             assert np.array_equal(out.cpu().numpy(), want)
 
 
-def test_fused_step_fast_form(bz):
-    """The fused step with the fast (Carleman) operator equals its stage chain."""
+def test_step_fast_form_equals_stage_chain(bz):
+    """The step with the fast (Carleman) operator equals its stage chain."""
     import torch
     N, L, n = 32, 10.0, 40
     f = to_dev(workloads.bi_maxwellian(n, 2, N, L, seed=48), "fp32")
