@@ -257,19 +257,11 @@ int phase_modesum(const bz_modes *m, int precision, const void *fh, void *qh, in
                                              static_cast<double2 *>(qh), n, st),
                   "collide: mode sum");
     } else if (modesum32_available(m)) {
-        // whole waves on the selected variant, the last partial wave on the
-        // 16-cell variant when it fits (one launch each)
-        int tv = -1;
-        const int64_t nm = modesum32_split(m, n, &tv);
-        const float2 *f2 = static_cast<const float2 *>(fh);
-        float2 *q2 = static_cast<float2 *>(qh);
-        if (nm > 0)
-            BZ_LAUNCH("modesum_f32", st, launch_modesum32_part(m, m->variant, f2, q2, nm, st), "collide: mode sum");
-        if (tv >= 0 && n > nm) {
-            const size_t off = (size_t)(nm / 32) * v.nhalf * 32;
-            BZ_LAUNCH("modesum_f32_tail", st, launch_modesum32_part(m, tv, f2 + off, q2 + off, n - nm, st),
-                      "collide: mode sum (last wave)");
-        }
+        // whole waves on the selected variant, the last partial wave split
+        // (one launch), or on the 16-cell variant (a second launch)
+        BZ_LAUNCH("modesum_f32", st,
+                  launch_modesum32(m, static_cast<const float2 *>(fh), static_cast<float2 *>(qh), n, st),
+                  "collide: mode sum");
     } else {
         BZ_LAUNCH("modesum_f32_generic", st,
                   launch_modesum_generic_f32(v, m->d_F32, m->bcols, static_cast<const float2 *>(fh),

@@ -43,6 +43,7 @@ struct bz_grid {
 };
 
 constexpr int kModesumVariants = 5;   // register-blocked FP32 mode-sum kernel variants
+constexpr int kSplitTables = 3;       // task tables for a tile split over 2, 4, 8 CTAs
 
 struct bz_modes {
     const bz_grid *g;
@@ -58,6 +59,7 @@ struct bz_modes {
     // in use (null if the generic kernel serves this grid)
     float *var_W[kModesumVariants];
     int *var_task[kModesumVariants];
+    int *var_task_split[kModesumVariants][kSplitTables];   // 32-cell variants: tile split over 2, 4, 8 CTAs
     int var_rowmax[kModesumVariants];
     int variant;          // index of the selected variant
     int variant_fixed;    // 1: chosen by BZ_MODESUM_VARIANT (no last-wave split)
@@ -202,9 +204,10 @@ struct Mode32Item {
     const void *fhat;     // float2 or double2 spectra, tiled layout
     void *Qhat;
     const void *W;        // weight stream of the kernel's scalar type
-    const int *tasks;
+    const int *tasks;     // task table for WARPS x split warps
     int h, M, nhalf, wrow_max;
     int64_t n;
+    int split;            // CTAs per tile (1, or 2, 4, 8 for a last partial wave)
 };
 struct Mode32Group {
     int nitems;
@@ -213,7 +216,7 @@ struct Mode32Group {
 };
 bool modesum32_available(const bz_modes *m);
 cudaError_t launch_modesum32(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st);
-int64_t modesum32_split(const bz_modes *m, int64_t n, int *tail_v);
+int64_t modesum32_split(const bz_modes *m, int64_t n, int *tail_v, int *tail_split);
 bool modesum64_available(const bz_modes *m);
 cudaError_t launch_modesum64(const bz_modes *m, const double2 *fhat, double2 *Qhat, int64_t n, cudaStream_t st);
 cudaError_t launch_modesum32_part(const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n,

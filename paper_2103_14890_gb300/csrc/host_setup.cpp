@@ -360,6 +360,7 @@ void modes_destroy(bz_modes *m) {
     for (int v = 0; v < kModesumVariants; ++v) {
         cudaFree(m->var_W[v]);
         cudaFree(m->var_task[v]);
+        for (int k = 0; k < kSplitTables; ++k) cudaFree(m->var_task_split[v][k]);
     }
     free(m->h_F);
     free(m);

@@ -213,7 +213,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
     const int *__restrict__ tasks = ip.tasks;
     const int h = ip.h, M = ip.M, nhalf = ip.nhalf, wrow_max = ip.wrow_max;
     const int64_t n = ip.n;
-    const int64_t cta = (int64_t)blockIdx.x - gd.tile_start[it];
+    // a tile may be split over ip.split CTAs, each taking one part of the
+    // task table (the last partial wave of a launch)
+    const int64_t cta0 = (int64_t)blockIdx.x - gd.tile_start[it];
+    const int part = (int)(cta0 % ip.split);
+    const int64_t cta = cta0 / ip.split;
     const int64_t tile = cta / G;                                    // 32-cell tile of the scratch layout
     const int sub = (int)(cta % G);                                  // which CELLS-cell part of it
     V2 *Fs = reinterpret_cast<V2 *>(smem16);                         // [kPad + nhalf + kPad][CELLS]
@@ -234,8 +238,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
     const int cell = lane % CELLS, grp = lane / CELLS;
     T *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
     T *wbuf1 = wbuf0 + wrow_max;
-    const int tbeg = tasks[warp], tend = tasks[warp + 1];
-    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS + 1);
+    const int vw = part * WARPS + warp;                              // task list of this warp
+    const int tbeg = tasks[vw], tend = tasks[vw + 1];
+    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS * ip.split + 1);
     const V2 *F0 = Fs + (size_t)(kPad + h) * CELLS + cell;          // (row 0, column 0) of this cell
 
     for (int t = tbeg; t < tend; ++t) {
@@ -387,7 +392,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_p2_kernel(const Mode32G
     const int *__restrict__ tasks = ip.tasks;
     const int h = ip.h, M = ip.M, nhalf = ip.nhalf, wrow_max = ip.wrow_max;
     const int64_t n = ip.n;
-    const int64_t tile = (int64_t)blockIdx.x - gd.tile_start[it];
+    const int64_t cta0 = (int64_t)blockIdx.x - gd.tile_start[it];
+    const int part = (int)(cta0 % ip.split);
+    const int64_t tile = cta0 / ip.split;
     float4 *Fs = reinterpret_cast<float4 *>(smem16);                        // [kPad + nhalf + kPad][16]
     float *wsm = reinterpret_cast<float *>(Fs + (size_t)(nhalf + 2 * kPad) * CS);   // [warps][2][wrow_max]
     {
@@ -409,8 +416,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_p2_kernel(const Mode32G
     const int pr = lane % CS, grp = lane / CS;
     float *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
     float *wbuf1 = wbuf0 + wrow_max;
-    const int tbeg = tasks[warp], tend = tasks[warp + 1];
-    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS + 1);
+    const int vw = part * WARPS + warp;
+    const int tbeg = tasks[vw], tend = tasks[vw + 1];
+    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS * ip.split + 1);
     const float4 *F0 = Fs + (size_t)(kPad + h) * CS + pr;
 
     for (int t = tbeg; t < tend; ++t) {
@@ -718,7 +726,7 @@ double beta_host(const bz_modes *m, const int *l, const int *mm);
 // (hi = fl32(w), lo = fl32(w - hi)), headers copied as they are.
 template <typename T>
 static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, int *outRowmax,
-                          float **outX2 = nullptr) {
+                          float **outX2 = nullptr, int **outSplit = nullptr) {
     constexpr int HEAD = kRowHeadBytes / (int)sizeof(T);
     const int R = variant_rt(v);                                // outputs per task (RT)
     const int kWarps = kVariants[v].warps;
@@ -837,27 +845,32 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
             }
         }
     }
-    // longest-processing-time-first assignment of tasks to the warps of a CTA
-    std::vector<int> order(tasks.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    std::vector<double> load(kWarps, 0.0);
-    std::vector<std::vector<int>> per(kWarps);
-    for (int i : order) {
-        int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        load[w] += cost[i];
-        per[w].push_back(i);
-    }
-    std::vector<int> tab(kWarps + 1 + tasks.size() * kTaskInts);
-    int pos = 0;
-    for (int w = 0; w < kWarps; ++w) {
-        tab[w] = pos;
-        for (int i : per[w]) {
-            std::memcpy(&tab[kWarps + 1 + (size_t)pos * kTaskInts], &tasks[i], sizeof(TaskRec));
-            ++pos;
+    // longest-processing-time-first assignment of tasks to nw warps: the
+    // offsets of each warp's list, then the task records
+    auto make_table = [&](int nw) {
+        std::vector<int> order(tasks.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        std::vector<double> load(nw, 0.0);
+        std::vector<std::vector<int>> per(nw);
+        for (int i : order) {
+            int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            load[w] += cost[i];
+            per[w].push_back(i);
         }
-    }
-    tab[kWarps] = pos;
+        std::vector<int> t(nw + 1 + tasks.size() * kTaskInts);
+        int pos = 0;
+        for (int w = 0; w < nw; ++w) {
+            t[w] = pos;
+            for (int i : per[w]) {
+                std::memcpy(&t[nw + 1 + (size_t)pos * kTaskInts], &tasks[i], sizeof(TaskRec));
+                ++pos;
+            }
+        }
+        t[nw] = pos;
+        return t;
+    };
+    const std::vector<int> tab = make_table(kWarps);
     int wrow_max = 0;
     for (auto &t : tasks) wrow_max = std::max(wrow_max, t.rowf);   // staging buffer: one row pair
     if (smem_bytes<T>(gv, wrow_max, v) > 227 * 1024) return false;   // does not fit
@@ -878,6 +891,23 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
         cudaFree(dX);
         rc = cuda_fail(e, "build_kernel_modes: weight stream");
         return false;
+    }
+    // tables for one tile split over S = 2, 4, 8 CTAs (S x kWarps warps; the
+    // last partial wave of a launch of a 32-cell variant)
+    if (outSplit) {
+        for (int k = 0; k < kSplitTables && e == cudaSuccess; ++k) {
+            const std::vector<int> ts = make_table(kWarps << (k + 1));
+            e = cudaMalloc(&outSplit[k], sizeof(int) * ts.size());
+            if (e == cudaSuccess) e = cudaMemcpy(outSplit[k], ts.data(), sizeof(int) * ts.size(), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) {
+            for (int k = 0; k < kSplitTables; ++k) cudaFree(outSplit[k]), outSplit[k] = nullptr;
+            cudaFree(dW);
+            cudaFree(dT);
+            cudaFree(dX);
+            rc = cuda_fail(e, "build_kernel_modes: split task tables");
+            return false;
+        }
     }
     *outW = dW;
     *outT = dT;
@@ -915,7 +945,8 @@ static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStr
 }
 
 static void fill_item(Mode32Item &it, const bz_modes *m, const void *W, const int *tasks, int rowmax,
-                      const void *fhat, void *Qhat, int64_t n) {
+                      const void *fhat, void *Qhat, int64_t n, int split = 1) {
+    it.split = split;
     const GridView &gv = m->g->v;
     it.fhat = fhat;
     it.Qhat = Qhat;
@@ -997,36 +1028,76 @@ cudaError_t launch_modesum_x2(const bz_modes *m, const double2 *fhat, float2 *Qh
 
 static int sm_count();
 
-// A launch over n cells ends with a partial wave of 32-cell CTAs; the SMs that
-// run one CTA fewer idle meanwhile.  When the 16-cell variant fits the grid,
-// the whole waves run on the selected variant and the remaining tiles on the
-// 16-cell one (twice the CTAs, each half as long).  Returns the cells of the
-// main part and sets *tail_v to the tail's variant (-1: no split).
-int64_t modesum32_split(const bz_modes *m, int64_t n, int *tail_v) {
+// A launch over n cells ends with a partial wave of tiles; the SMs that run
+// one tile fewer idle meanwhile.  With a 32-cell variant chosen by timing,
+// the whole waves run one tile per CTA and the T remaining tiles are split
+// over S = 2, 4 or 8 CTAs each (each CTA takes one part of the tile's tasks),
+// S the largest with T S <= SM count; when no such S exists (T > SMs / 2)
+// and the 16-cell variant fits the grid, the remaining tiles run on it (twice
+// the CTAs, each half as long).  Every output is computed by one task in
+// either case, with the same arithmetic, so the results do not depend on the
+// split.  Returns the cells of the main part; *tail_v is the tail's variant
+// (-1: no tail) and *tail_split its split.
+int64_t modesum32_split(const bz_modes *m, int64_t n, int *tail_v, int *tail_split) {
     *tail_v = -1;
-    if (m->variant_fixed || kVariants[m->variant].cells != 32 || !m->var_W[2]) return n;
+    *tail_split = 1;
+    if (m->variant_fixed || kVariants[m->variant].cells != 32) return n;
     const int64_t sms = sm_count();
     const int64_t ntiles = (n + 31) / 32, full = (ntiles / sms) * sms;
-    if (full == ntiles) return n;
+    const int64_t T = ntiles - full;
+    if (T == 0) return n;
+    for (int k = kSplitTables - 1; k >= 0; --k) {
+        const int S = 2 << k;
+        if (T * S <= sms && m->var_task_split[m->variant][k]) {
+            *tail_v = m->variant;
+            *tail_split = S;
+            return full * 32;
+        }
+    }
+    if (!m->var_W[2]) return n;
     *tail_v = 2;
     return full * 32;
+}
+
+// One launch for the whole batch: the main part (one tile per CTA) and the
+// last partial wave (split tiles, or the 16-cell variant) as two items.
+cudaError_t launch_modesum32(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int tv = -1, ts = 1;
+    const int64_t nm = modesum32_split(m, n, &tv, &ts);
+    const int v = m->variant;
+    if (tv >= 0 && tv != v) {
+        // tail on another variant: two launches (different kernels)
+        cudaError_t e = nm > 0 ? launch_variant(m, v, fhat, Qhat, nm, st) : cudaSuccess;
+        const size_t off = (size_t)(nm / 32) * m->g->v.nhalf * 32;
+        if (e == cudaSuccess) e = launch_variant(m, tv, fhat + off, Qhat + off, n - nm, st);
+        return e;
+    }
+    Mode32Group gd;
+    memset(&gd, 0, sizeof gd);
+    gd.tile_start[0] = 0;
+    int k = 0;
+    if (nm > 0) {
+        fill_item(gd.item[k], m, m->var_W[v], m->var_task[v], m->var_rowmax[v], fhat, Qhat, nm);
+        gd.tile_start[k + 1] = gd.tile_start[k] + ctas_for(v, nm);
+        ++k;
+    }
+    if (tv >= 0 && n > nm) {
+        const size_t off = (size_t)(nm / 32) * m->g->v.nhalf * 32;
+        int lg = 0;
+        while ((2 << lg) != ts) ++lg;
+        fill_item(gd.item[k], m, m->var_W[v], m->var_task_split[v][lg], m->var_rowmax[v], fhat + off, Qhat + off,
+                  n - nm, ts);
+        gd.tile_start[k + 1] = gd.tile_start[k] + ctas_for(v, n - nm) * ts;
+        ++k;
+    }
+    gd.nitems = k;
+    return launch_group(gd, v, smem_bytes<float>(m->g->v, m->var_rowmax[v], v), st);
 }
 
 cudaError_t launch_modesum32_part(const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n,
                                   cudaStream_t st) {
     return launch_variant(m, v, fhat, Qhat, n, st);
-}
-
-cudaError_t launch_modesum32(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
-    int tv = -1;
-    const int64_t nm = modesum32_split(m, n, &tv);
-    cudaError_t e = cudaSuccess;
-    if (nm > 0) e = launch_variant(m, m->variant, fhat, Qhat, nm, st);
-    if (e == cudaSuccess && tv >= 0 && n > nm) {
-        const size_t off = (size_t)(nm / 32) * m->g->v.nhalf * 32;   // whole 32-cell tiles
-        e = launch_variant(m, tv, fhat + off, Qhat + off, n - nm, st);
-    }
-    return e;
 }
 
 // Heterogeneous instances in one launch; all items must use the same kernel
@@ -1171,7 +1242,9 @@ int modes_build_fp32_tables(bz_modes *m) {
         m->var_task[v] = nullptr;
         m->var_rowmax[v] = 0;
         void *w = nullptr;
-        if (build_variant<float>(m, v, rc, &w, &m->var_task[v], &m->var_rowmax[v])) {
+        for (int k = 0; k < kSplitTables; ++k) m->var_task_split[v][k] = nullptr;
+        int **split = kVariants[v].cells == 32 ? m->var_task_split[v] : nullptr;
+        if (build_variant<float>(m, v, rc, &w, &m->var_task[v], &m->var_rowmax[v], nullptr, split)) {
             m->var_W[v] = static_cast<float *>(w);
             any = true;
         }

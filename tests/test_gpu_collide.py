@@ -97,14 +97,17 @@ def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, dim, N, variant):
     check_fp32_cells(k, fin, Qg, Qr, what="variant %d N=%d d=%d" % (variant, N, dim))
 
 
-def test_last_wave_split_is_exact(bz, monkeypatch):
-    """With a timed 32-cell variant, whole waves of CTAs run on it and the last
-    partial wave on the 16-cell variant: every cell must equal a run of the
-    corresponding variant alone (cells are independent)."""
+@pytest.mark.parametrize("extra", [70, 30 * 32 + 5, 50 * 32, 100 * 32 - 1])
+def test_last_wave_split_is_exact(bz, monkeypatch, extra):
+    """With a timed 32-cell variant, whole waves of CTAs run one tile each and
+    the tiles of the last partial wave are split over 8, 4 or 2 CTAs (3, 31,
+    50 extra tiles) or, beyond half the SMs (100 extra tiles), run on the
+    16-cell variant: every cell must equal a run of a fixed variant (cells are
+    independent and every variant performs the same operations per output)."""
     import torch
     N, L = 32, 10.0
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    n = sms * 32 + 70
+    n = sms * 32 + extra
     f = workloads.bi_maxwellian(n, 2, N, L, seed=1500)
     m = bz.Modes(bz.Grid(2, N, L), 1.0)
     if m.modesum_variant not in (1, 2, 5):
