@@ -404,9 +404,12 @@ int check_input(int precision, const void *f, int64_t count, cudaStream_t st) {
 }
 
 // One IMEX stage: F_l, P_l by the stage kernel, then G_l = Q(F_l) - P_l.
+// in_step: called by step_sequence (library scratch): stage 0's F (= f^n
+// exactly when A_00 = 0) is not written and the collision reads f^n, and the
+// last stage's G, which no stage reads, is not zeroed.
 int run_stage(const bz_modes *m, const Tableau &t, int l, int model, double dt, double eps, const void *f_n,
               void *F_l, void *G, void *P, const void *L_res, int64_t n, int precision, int flags,
-              cudaStream_t st, void *ext = nullptr) {
+              cudaStream_t st, void *ext = nullptr, bool in_step = false) {
     const GridView &v = m->g->v;
     StageCoef c;
     memset(&c, 0, sizeof c);
@@ -420,6 +423,8 @@ int run_stage(const bz_modes *m, const Tableau &t, int l, int model, double dt, 
     c.dt = dt;
     c.eps = eps;
     c.nuf = (model == BZ_BOLTZMANN) ? m->penalty : 1.0;
+    const bool f0 = in_step && l == 0 && c.all == 0.0;     // F_0 = f^n
+    c.store_F = f0 ? 0 : 1;
     const int64_t stride = n * v.nv;
     const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
     cudaError_t e;
@@ -440,7 +445,9 @@ int run_stage(const bz_modes *m, const Tableau &t, int l, int model, double dt, 
         if (t.At[q][l] != 0.0) needG = true;
     char *Gl = static_cast<char *>(G) + (size_t)l * stride * es;
     const char *Pl = static_cast<const char *>(P) + (size_t)l * stride * es;
-    if (model == BZ_BOLTZMANN && needG) return collide_chain(m, precision, flags, F_l, Gl, Pl, n, st, ext);
+    if (model == BZ_BOLTZMANN && needG)
+        return collide_chain(m, precision, flags, f0 ? f_n : F_l, Gl, Pl, n, st, ext);
+    if (in_step && l == t.s - 1) return BZ_OK;
     e = launch_fill_zero(Gl, (int64_t)(stride * es), st);
     if (e != cudaSuccess) return cuda_fail(e, "imex stage: zero G");
     return BZ_OK;
@@ -502,7 +509,7 @@ int step_sequence(const bz_modes *m, const Tableau &t, int model, double dt, dou
     char *coll = Fbuf + (size_t)stride * es;
     for (int l = 0; l < t.s; ++l) {
         void *F_l = (l == t.s - 1) ? f_out : static_cast<void *>(Fbuf);
-        int rc = run_stage(m, t, l, model, dt, eps, f_n, F_l, G, P, L_res, n, precision, flags, st, coll);
+        int rc = run_stage(m, t, l, model, dt, eps, f_n, F_l, G, P, L_res, n, precision, flags, st, coll, true);
         if (rc) return rc;
     }
     return BZ_OK;

@@ -252,6 +252,7 @@ struct StageCoef {
     double all;                // A[l][l]
     double dt, eps;
     double nuf;                // penalty rate nu = nuf * rho
+    int store_F;               // 0: F_l equals f^n exactly (stage 0 of a step) and is not written
 };
 cudaError_t launch_imex_stage_f64(const GridView &g, const StageCoef &c, const double *fn,
                                   double *F, const double *G, double *P, const double *Lres,

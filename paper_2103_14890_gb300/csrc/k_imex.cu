@@ -35,7 +35,9 @@ __global__ void __launch_bounds__(kThreads) imex_stage_kernel(GridView g, StageC
     double mom[5] = {0, 0, 0, 0, 0};
     for (int64_t i = threadIdx.x; i < g.nv; i += blockDim.x) {
         T r = fn[base + i];
-        for (int m = 0; m < c.nprev; ++m) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            if (m >= c.nprev) break;
             const int64_t o = (int64_t)m * stride + base + i;
             T gm = G[o] * ieps;
             if (Lres) gm -= Lres[o];
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) imex_stage_kernel(GridView g, StageC
         else
             Mx = (T)pref * expf((float)(-r2 * inv2t));   // exponent in FP64, exp in the state precision
         T Fi = (R[i] + cT * Mx) * denom;
-        Fo[i] = Fi;
+        if (c.store_F) Fo[i] = Fi;
         Po[i] = nuT * (Mx - Fi);
     }
 }
@@ -131,7 +133,9 @@ __global__ void __launch_bounds__(kStageCells * 32) imex_stage2d_kernel(GridView
     T R[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) R[j] = on ? fn[base + j * N] : (T)0;
-    for (int m = 0; m < c.nprev; ++m) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {              // compile-time index into the coefficient arrays
+        if (m >= c.nprev) break;
         const T ca = dt * (T)c.at[m] * ieps, cb = dt * (T)c.a[m] * ieps, cl = dt * (T)c.at[m];
         const int64_t o = (int64_t)m * stride + base;
         if (on) {
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(kStageCells * 32) imex_stage2d_kernel(GridView
         const T Mx = fcol * frow;
         const T Fi = (R[j] + cT * Mx) * denom;
         if (on) {
-            Fo[j * N] = Fi;
+            if (c.store_F) Fo[j * N] = Fi;
             Po[j * N] = nuT * (Mx - Fi);
         }
     }
