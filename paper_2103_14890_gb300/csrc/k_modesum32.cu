@@ -172,6 +172,62 @@ __device__ __forceinline__ void block_pass(typename C2<T>::type (&win)[2 * RR],
     }
 }
 
+// block_pass with the read direction of f-hat_l at run time: dcs = +/-CS
+// (elements between consecutive l_2), sgn = +/-1 multiplies the value's
+// imaginary part (f-hat_l = conj of the value read for l_1 < 0).  The
+// products are those of block_pass<.., +1> on the conjugated value, which are
+// exactly those of block_pass<.., -1> on the value read (negation is exact),
+// so the results equal the specialised bodies' bit for bit with half the code
+// (the R = 8 kernel's four specialised bodies overflow the instruction cache).
+template <typename T, int RR, int CS, int WS, int PH>
+__device__ __forceinline__ void block_pass_rt(typename C2<T>::type (&win)[2 * RR],
+                                              const typename C2<T>::type *__restrict__ mp,
+                                              const typename C2<T>::type *__restrict__ lp, int dcs, T sgn,
+                                              const T *__restrict__ wb, typename C2<T>::type (&acc)[RR]) {
+    using V2 = typename C2<T>::type;
+#pragma unroll
+    for (int j = 0; j < RR; ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
+#pragma unroll
+    for (int s = 0; s < RR; ++s) {
+        V2 fl = lp[s * dcs];
+        fl.y *= sgn;
+        T wv[RR];
+#pragma unroll
+        for (int q = 0; q < RR; q += 4) load_w4(wv + q, wb + s * WS + q);
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+            const V2 b = win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)];
+            const T tx = wv[r] * fl.x, ty = wv[r] * fl.y;
+            acc[r].x = fma(tx, b.x, acc[r].x);
+            acc[r].x = fma(-ty, b.y, acc[r].x);
+            acc[r].y = fma(tx, b.y, acc[r].y);
+            acc[r].y = fma(ty, b.x, acc[r].y);
+        }
+    }
+}
+
+template <typename T, int RR, int CS, int WS>
+__device__ __forceinline__ void row_pass_rt(const typename C2<T>::type *__restrict__ rowl,
+                                            const typename C2<T>::type *__restrict__ rowm, const T *__restrict__ wrow,
+                                            int nblk, int l2lo, int mbase0, int dir, typename C2<T>::type (&acc)[RR]) {
+    using V2 = typename C2<T>::type;
+    V2 win[2 * RR];
+    const int dcs = dir * CS;
+    const T sgn = (T)dir;
+    const V2 *mp = rowm + mbase0 * CS;
+    const V2 *lp = rowl + l2lo * dcs;
+#pragma unroll
+    for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * CS];
+    int blk = 0;
+    for (; blk + 1 < nblk; blk += 2) {
+        block_pass_rt<T, RR, CS, WS, 0>(win, mp, lp, dcs, sgn, wrow + blk * RR * WS, acc);
+        block_pass_rt<T, RR, CS, WS, 1>(win, mp - RR * CS, lp + RR * dcs, dcs, sgn, wrow + (blk + 1) * RR * WS, acc);
+        mp -= 2 * RR * CS;
+        lp += 2 * RR * dcs;
+    }
+    if (blk < nblk) block_pass_rt<T, RR, CS, WS, 0>(win, mp, lp, dcs, sgn, wrow + blk * RR * WS, acc);
+}
+
 // One row pair of a task for this thread's R outputs:
 // acc[r] += sum_l2 w(l2, r) f-hat_l(l2) f-hat_m(k2_0 + r - l2).
 // rowl / rowm point at column 0 of the rows of l (or -l) and m (this thread's
@@ -196,7 +252,7 @@ __device__ __forceinline__ void row_pass(const typename C2<T>::type *__restrict_
     if (blk < nblk) block_pass<T, RR, CS, WS, 0, DIR>(win, mp, lp, wrow + blk * RR * WS, acc);
 }
 
-template <typename T, int RR, int WARPS, int CELLS>
+template <typename T, int RR, int WARPS, int CELLS, bool RTDIR = false>
 __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Group gd) {
     using V2 = typename C2<T>::type;
     constexpr int G = 32 / CELLS;     // lane groups splitting a task's outputs
@@ -265,7 +321,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
             // row header: element offsets of the rows of l and m, and the
             // direction of l (-1: f-hat_l = conj(f-hat_{-l}), row of -l read backwards)
             const int4 hd = *reinterpret_cast<const int4 *>(wcur);
-            if (hd.z > 0)
+            if constexpr (RTDIR)
+                row_pass_rt<T, RR, CELLS, RT>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G, tk.l2lo,
+                                              mbase0, hd.z > 0 ? 1 : -1, acc);
+            else if (hd.z > 0)
                 row_pass<T, RR, CELLS, RT, 1>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G, tk.l2lo,
                                               mbase0, acc);
             else
@@ -918,18 +977,18 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
 
 bool modesum32_available(const bz_modes *m) { return m->d_W32 != nullptr; }
 
-template <typename T, int RR, int WARPS, int CELLS>
+template <typename T, int RR, int WARPS, int CELLS, bool RTDIR = false>
 static cudaError_t launch_instance(const Mode32Group &gd, size_t sm, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(modesum32_kernel<T, RR, WARPS, CELLS>,
+    cudaError_t e = cudaFuncSetAttribute(modesum32_kernel<T, RR, WARPS, CELLS, RTDIR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    modesum32_kernel<T, RR, WARPS, CELLS><<<(unsigned)gd.tile_start[gd.nitems], WARPS * 32, sm, st>>>(gd);
+    modesum32_kernel<T, RR, WARPS, CELLS, RTDIR><<<(unsigned)gd.tile_start[gd.nitems], WARPS * 32, sm, st>>>(gd);
     return cudaGetLastError();
 }
 
 static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStream_t st) {
     switch (v) {
-        case 0: return launch_instance<float, 8, 16, 32>(gd, sm, st);
+        case 0: return launch_instance<float, 8, 16, 32, true>(gd, sm, st);
         case 1: return launch_instance<float, 4, 32, 32>(gd, sm, st);
         case 2: return launch_instance<float, 4, 16, 16>(gd, sm, st);
         case 3: return launch_instance<float, 4, 16, 8>(gd, sm, st);
