@@ -186,6 +186,8 @@ def main():
     ap.add_argument("--method", default="direct", choices=["direct", "fast"],
                     help="fast: time the fast spectral form (Maxwell molecules) as the main line instead")
     ap.add_argument("--ndirs", type=int, default=8, help="collision directions of the fast form")
+    ap.add_argument("--form", default="fp32", choices=["fp32", "fp32x2"],
+                    help="precision form of the timed line (fp32x2: the double-float mode sum)")
     ap.add_argument("--sections", default="forms,transport,imex,grouped,fast",
                     help="comma list of the extra measurements to run (forms, transport, imex, grouped, fast)")
     args = ap.parse_args()
@@ -217,8 +219,10 @@ def main():
             tdist.barrier()
         torch.cuda.synchronize()
 
+    form = args.form
+
     def step():
-        bz.collide_batch(modes, f, Q, precision="fp32")
+        bz.collide_batch(modes, f, Q, precision=form)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -246,12 +250,15 @@ def main():
     value = cells * world / (ms / 1e3)
 
     # dominant kernel: the mode sum (or the fast form's convolutions)
-    ms_name = "fast_f32" if fast else "modesum_f32" if "modesum_f32" in prof else "modesum_f32_generic"
+    ms_name = "fast_f32" if fast else "modesum_x2" if form == "fp32x2" else \
+        "modesum_f32" if "modesum_f32" in prof else "modesum_f32_generic"
     launches, ktot = prof.get(ms_name, (0, float("nan")))
     k_ms = ktot / max(1, launches)
     if "modesum_f32_tail" in prof:          # the last partial wave runs as a second launch
         tl, tt = prof["modesum_f32_tail"]
         k_ms += tt / max(1, tl)
+    # the X2 form's unit of work is the same pair count (its extra instructions
+    # are the precision, not more pairs)
     flops_launch = (fast_flops_per_cell(N_V, args.ndirs) if fast else 10.0 * modes.pairs_sym) * cells
     achieved = flops_launch / (k_ms / 1e3) / 1e12
     gpu_launches = sum(c for c, _ in prof.values())
@@ -308,11 +315,11 @@ def _e2e(args, bz, modes, f_host, f, barrier, st, e0, e1, cells, world):
     fh = torch.from_numpy(f_host).pin_memory()
     qh = torch.empty_like(fh).pin_memory()
     for _ in range(2):
-        bz.collide_batch_host(modes, fh, qh, precision="fp32", stream=st)
+        bz.collide_batch_host(modes, fh, qh, precision=args.form, stream=st)
     barrier()
     e0.record(st)
     for _ in range(args.steps):
-        bz.collide_batch_host(modes, fh, qh, precision="fp32", stream=st)
+        bz.collide_batch_host(modes, fh, qh, precision=args.form, stream=st)
     e1.record(st)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
@@ -768,10 +775,10 @@ def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, valu
                    "cells_per_gpu": cells, "N_v": N_V * N_V, "L": L_BOX,
                    "kernel": ("Maxwell molecules (gamma=0, b0=1/(2pi)), fast form, %d directions" % args.ndirs
                               if args.method == "fast" else "VHS hard spheres (gamma=1, b0=1/(2pi))"),
-                   "precision_form": "fp32",
+                   "precision_form": args.form,
                    "l2": "inputs and outputs (268 MB each) exceed L2: no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "rel_l2_err": {"fp32_vs_oracle": err32, "fp64_vs_oracle": err64, "fp32_loss_scaled": loss32,
+        "rel_l2_err": {"form": args.form, "fp32_vs_oracle": err32, "fp64_vs_oracle": err64, "fp32_loss_scaled": loss32,
                        "oracle_cells": nchk, "fp32_vs_fp64_gpu_all_cells": err32_vs64},
         "fp64_form": {"value": value64, "unit": "cell-collision evals/s", "ms_per_step": ms64,
                       "speedup_fp32_over_fp64": value / value64} if Q64 is not None else None,
@@ -780,7 +787,9 @@ def _report(args, bz, modes, f_host, Q, Q64, cells, world, ms, value, ms64, valu
                      "traffic": MODESUM_TRAFFIC_65536 if cells == CELLS and args.method == "direct" else None,
                      "kernel": ms_name,
                      "kernel_ms": k_ms, "flops_per_launch": flops_launch,
-                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" + (
+                         "; fp32x2 counts the same 10 flops per pair, its double-float arithmetic executes ~54 FP32 "
+                         "instructions per pair" if args.form == "fp32x2" else "")},
         "kernel_times_ms": {k2: v[1] / max(1, v[0]) for k2, v in prof.items()},
         "gpu_launches": gpu_launches,
         "imex_step": extra.get("imex_step"),
