@@ -634,11 +634,16 @@ template <int RR> __device__ __forceinline__ void load_wx(float *wv, const float
 // One block of RR l_2 steps of the FP32X2 form: the window scheme of
 // block_pass, with the high and low parts of each spectrum value LO elements
 // apart in shared memory and the weights of step s at wb + s * 2 RT (high
-// parts) and wb + s * 2 RT + RT (low parts).
-template <int RR, int CS, int RT, int PH, int DIR>
-__device__ __forceinline__ void block_pass_x2(float2 (&wh)[2 * RR], float2 (&wl)[2 * RR],
-                                              const float2 *__restrict__ mp, const float2 *__restrict__ lp, int LO,
-                                              const float *__restrict__ wb, X2Acc (&acc)[RR]) {
+// parts) and wb + s * 2 RT + RT (low parts).  The read direction of f-hat_l is
+// chosen at run time (dcs = +/-CS, sgn = +/-1 on the imaginary parts):
+// x2_term<+1> on the conjugated value performs exactly the
+// operations of x2_term<-1> on the value read, each negated (rounding is
+// symmetric), so the results are those of direction-specialised bodies with
+// half the code (four specialised bodies overflow the instruction cache).
+template <int RR, int CS, int RT, int PH>
+__device__ __forceinline__ void block_pass_x2_rt(float2 (&wh)[2 * RR], float2 (&wl)[2 * RR],
+                                                 const float2 *__restrict__ mp, const float2 *__restrict__ lp, int dcs,
+                                                 float sgn, int LO, const float *__restrict__ wb, X2Acc (&acc)[RR]) {
 #pragma unroll
     for (int j = 0; j < RR; ++j) {
         wh[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
@@ -646,25 +651,29 @@ __device__ __forceinline__ void block_pass_x2(float2 (&wh)[2 * RR], float2 (&wl)
     }
 #pragma unroll
     for (int s = 0; s < RR; ++s) {
-        const float2 ah = lp[s * DIR * CS], al = lp[s * DIR * CS + LO];
+        float2 ah = lp[s * dcs], al = lp[s * dcs + LO];
+        ah.y *= sgn;
+        al.y *= sgn;
         float whi[RR], wlo[RR];
         load_wx<RR>(whi, wb + s * 2 * RT);
         load_wx<RR>(wlo, wb + s * 2 * RT + RT);
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
             const int q = (r - s + RR - 1 + PH * RR) & (2 * RR - 1);
-            x2_term<DIR>(acc[r], whi[r], wlo[r], ah, al, wh[q], wl[q]);
+            x2_term<1>(acc[r], whi[r], wlo[r], ah, al, wh[q], wl[q]);
         }
     }
 }
 
-template <int RR, int CS, int RT, int DIR>
+template <int RR, int CS, int RT>
 __device__ __forceinline__ void row_pass_x2(const float2 *__restrict__ rowl, const float2 *__restrict__ rowm, int LO,
-                                            const float *__restrict__ wrow, int nblk, int l2lo, int mbase0,
+                                            const float *__restrict__ wrow, int nblk, int l2lo, int mbase0, int dir,
                                             X2Acc (&acc)[RR]) {
     float2 wh[2 * RR], wl[2 * RR];
+    const int dcs = dir * CS;
+    const float sgn = (float)dir;
     const float2 *mp = rowm + mbase0 * CS;
-    const float2 *lp = rowl + DIR * l2lo * CS;
+    const float2 *lp = rowl + l2lo * dcs;
 #pragma unroll
     for (int j = RR; j < 2 * RR - 1; ++j) {
         wh[j] = mp[j * CS];
@@ -672,13 +681,13 @@ __device__ __forceinline__ void row_pass_x2(const float2 *__restrict__ rowl, con
     }
     int blk = 0;
     for (; blk + 1 < nblk; blk += 2) {
-        block_pass_x2<RR, CS, RT, 0, DIR>(wh, wl, mp, lp, LO, wrow + blk * RR * 2 * RT, acc);
-        block_pass_x2<RR, CS, RT, 1, DIR>(wh, wl, mp - RR * CS, lp + RR * DIR * CS, LO,
-                                          wrow + (blk + 1) * RR * 2 * RT, acc);
+        block_pass_x2_rt<RR, CS, RT, 0>(wh, wl, mp, lp, dcs, sgn, LO, wrow + blk * RR * 2 * RT, acc);
+        block_pass_x2_rt<RR, CS, RT, 1>(wh, wl, mp - RR * CS, lp + RR * dcs, dcs, sgn, LO,
+                                        wrow + (blk + 1) * RR * 2 * RT, acc);
         mp -= 2 * RR * CS;
-        lp += 2 * RR * DIR * CS;
+        lp += 2 * RR * dcs;
     }
-    if (blk < nblk) block_pass_x2<RR, CS, RT, 0, DIR>(wh, wl, mp, lp, LO, wrow + blk * RR * 2 * RT, acc);
+    if (blk < nblk) block_pass_x2_rt<RR, CS, RT, 0>(wh, wl, mp, lp, dcs, sgn, LO, wrow + blk * RR * 2 * RT, acc);
 }
 
 // The FP32X2 mode sum: the task structure and shared-memory layout of
@@ -746,12 +755,8 @@ modesum_x2_kernel(const double2 *__restrict__ fhat, float2 *__restrict__ Qhat, c
             }
             __syncwarp();
             const int4 hd = *reinterpret_cast<const int4 *>(wcur);
-            if (hd.z > 0)
-                row_pass_x2<RR, CELLS, RT, 1>(F0 + hd.x, F0 + hd.y, LO, wcur + HEADF + grp * RR, tk.nblk * G,
-                                              tk.l2lo, mbase0, acc);
-            else
-                row_pass_x2<RR, CELLS, RT, -1>(F0 + hd.x, F0 + hd.y, LO, wcur + HEADF + grp * RR, tk.nblk * G,
-                                               tk.l2lo, mbase0, acc);
+            row_pass_x2<RR, CELLS, RT>(F0 + hd.x, F0 + hd.y, LO, wcur + HEADF + grp * RR, tk.nblk * G, tk.l2lo,
+                                       mbase0, hd.z > 0 ? 1 : -1, acc);
             __syncwarp();
         }
         const int64_t c = tile * 32 + sub * CELLS + cell;
