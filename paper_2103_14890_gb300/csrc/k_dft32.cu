@@ -29,8 +29,10 @@ __device__ __forceinline__ void inv32_epilogue(T (&q)[N], int64_t cell, int lane
                                                double L, double dv, int64_t n) {
     using S = T;
     constexpr int NV = N * N;
-    const S v2 = (S)(-L + lane * dv);          // velocity of column j2
     if (conserve) {
+        // the column's velocity, formed here only: FP64 operations cost 64
+        // FP32 ones on this GPU and the common path needs none
+        const S v2 = (S)(-L + lane * dv);
         // moments of Q over the cell: FP32 partials along j1 with a TwoSum
         // error term, combined in FP64 across the lanes; then the projection
         // Q -= phi . (C C^T)^{-1} (C Q) with phi = (1, v1, v2, |v|^2)
@@ -322,8 +324,8 @@ __device__ __forceinline__ void invg_epilogue(T (&q)[N], int64_t cell, int j2, c
     using S = T;
     constexpr int NV = N * N;
     const bool col = j2 < N;
-    const S v2 = (S)(-L + j2 * dv);
     if (conserve) {
+        const S v2 = (S)(-L + j2 * dv);        // formed only where used (FP64 is 1/64 rate)
         double mom[4];
         {
             S s0 = (S)0., e0 = (S)0., s1 = (S)0., e1 = (S)0., s3 = (S)0., e3 = (S)0.;
