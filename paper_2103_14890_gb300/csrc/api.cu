@@ -678,7 +678,27 @@ int collide_batch_host(const bz_modes *m, int precision, int flags, const void *
     const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
     const size_t cell_bytes = (size_t)m->g->v.nv * es;
     const int64_t chunk = std::min(n_cells, host_chunk_cells(m->g->device));
-    const int64_t nchunks = (n_cells + chunk - 1) / chunk;
+    // chunk boundaries: one mode-sum wave each, except that the first and the
+    // last chunk of a long batch are a quarter wave, so the copy that fills
+    // the pipeline and the one that drains it are short (a quarter-wave mode
+    // sum splits its tiles over four CTAs and takes about a quarter of a wave)
+    std::vector<int64_t> bnd{0};
+    {
+        const int64_t q = std::max<int64_t>(32, (chunk / 4 + 31) / 32 * 32);
+        int64_t at = 0;
+        if (n_cells > 2 * chunk) {
+            at = q;
+            bnd.push_back(at);
+        }
+        while (n_cells - at > chunk) {
+            const int64_t rest = n_cells - at;
+            const int64_t step = (rest <= chunk + q && rest > q && n_cells > 2 * chunk) ? rest - q : chunk;
+            at += step;
+            bnd.push_back(at);
+        }
+        if (bnd.back() != n_cells) bnd.push_back(n_cells);
+    }
+    const int64_t nchunks = (int64_t)bnd.size() - 1;
     cudaStream_t cp[2];
     if ((rc = copy_streams(m->g->device, cp))) return rc;
     cudaStream_t s_in = cp[0], s_out = cp[1];
@@ -708,7 +728,7 @@ int collide_batch_host(const bz_modes *m, int precision, int flags, const void *
         BZ_TRY(cudaStreamWaitEvent(s_out, ready, 0), "collide_batch_host: wait");
         for (int64_t c = 0; c < nchunks; ++c) {
             const int i = (int)(c & 1);
-            const int64_t off = c * chunk, nc = std::min(chunk, n_cells - off);
+            const int64_t off = bnd[c], nc = bnd[c + 1] - bnd[c];
             const size_t bytes = (size_t)nc * cell_bytes;
             if (c >= 2) BZ_TRY(cudaStreamWaitEvent(s_in, done[i], 0), "collide_batch_host: wait");
             BZ_TRY(cudaMemcpyAsync(fd[i], static_cast<const char *>(f_host) + (size_t)off * cell_bytes, bytes,
