@@ -412,6 +412,30 @@ int bz_profile(int enable);
 int bz_profile_read(char *names, int names_bytes, double *total_ms, int64_t *launches,
                     int max_kernels);
 
+/* bz_inject_alloc_failure -- host-side fault injection for tests of the error
+ * paths (no GPU fault is involved).  after >= 0 arms a countdown: the
+ * library's next `after` device allocations succeed and the one after them
+ * fails as if the device were out of memory (the allocation is not attempted),
+ * after which injection is off again; after < 0 turns it off.  Counted
+ * allocations: the per-call scratch of every entry point (stream-ordered
+ * pool), imex_step's graph scratch, the device tables of init_velocity_grid,
+ * build_kernel_modes, build_fast_modes, build_fv_mesh(_periodic) and
+ * fv_mesh_set_walls, the autotuner's timing batch and the device error word
+ * of BZ_CHECK_INPUT / bz_check.  The entry point that meets the failure
+ * returns BZ_ENOMEM, releases what it had taken (bz_alloc_stats returns to
+ * its earlier values once the stream has completed), writes no handle, and
+ * leaves every existing handle usable.  The countdown is process-wide: arm it
+ * only while no other thread calls the library.  Returns BZ_OK. */
+int bz_inject_alloc_failure(int64_t after);
+
+/* bz_alloc_stats -- live_blocks (process-wide): device blocks the library
+ * holds outside its pools (tables of live handles, cached graph scratch,
+ * device error words, FFT tables excluded: those are __constant__ data);
+ * pool_used_bytes: bytes currently allocated from the library's
+ * stream-ordered pools on all devices (zero between calls once their streams
+ * have completed).  Either pointer may be NULL.  Errors: BZ_ECUDA. */
+int bz_alloc_stats(int64_t *live_blocks, uint64_t *pool_used_bytes);
+
 /* collide_batch_noalloc -- the same operator as collide_batch, for callers
  * that cannot allocate device memory: applications whose device memory is
  * owned by another allocator (a framework's caching allocator, or a host

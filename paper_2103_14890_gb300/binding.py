@@ -79,6 +79,8 @@ def load(path=None):
             "bz_mesh_info": ([c_p, ctypes.POINTER(c_i64)], c_i),
             "bz_mesh_destroy": ([c_p], None),
             "fv_mesh_set_walls": ([c_p, c_i64, c_p, c_p], c_i),
+            "bz_inject_alloc_failure": ([c_i64], c_i),
+            "bz_alloc_stats": ([c_p, c_p], c_i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -385,6 +387,21 @@ def check(stream=None):
 def profile(enable):
     """Turn per-kernel CUDA-event timing inside the library on or off (clears it)."""
     _check(load().bz_profile(1 if enable else 0))
+
+
+def inject_alloc_failure(after):
+    """Test hook: the library's next `after` device allocations succeed and the
+    one after them fails with BZ_ENOMEM (host side); None or < 0 turns it off."""
+    _check(load().bz_inject_alloc_failure(-1 if after is None else int(after)))
+
+
+def alloc_stats():
+    """(device blocks the library holds outside its pools, bytes in use in its
+    stream-ordered pools)."""
+    live = ctypes.c_int64()
+    used = ctypes.c_uint64()
+    _check(load().bz_alloc_stats(ctypes.byref(live), ctypes.byref(used)))
+    return int(live.value), int(used.value)
 
 
 def profile_read(max_kernels=32):

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -23,6 +24,31 @@ int fail(int code, const std::string &msg) {
 int cuda_fail(cudaError_t e, const char *what) {
     t_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return e == cudaErrorMemoryAllocation ? BZ_ENOMEM : BZ_ECUDA;
+}
+
+// Host-side allocation failure injection: -1 = off, k >= 0 = the next k
+// allocations succeed and the one after fails (then off again).
+static std::atomic<int64_t> g_fail_after{-1};
+static std::atomic<int64_t> g_live_blocks{0};
+
+bool alloc_fault_due() {
+    int64_t v = g_fail_after.load(std::memory_order_relaxed);
+    while (v >= 0)
+        if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+    return false;
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (alloc_fault_due()) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) *p = nullptr;
+    else if (*p) g_live_blocks.fetch_add(1);
+    return e;
+}
+
+void dev_free(void *p) {
+    if (p && cudaFree(p) == cudaSuccess) g_live_blocks.fetch_sub(1);
 }
 
 int grid_create(int dim, int N, double L, bz_grid **out);
@@ -74,6 +100,7 @@ struct Scratch {
     cudaError_t alloc(size_t bytes, cudaStream_t s) {
         st = s;
         if (bytes == 0) return cudaSuccess;
+        if (alloc_fault_due()) return cudaErrorMemoryAllocation;
         cudaMemPool_t pool = pool_for(current_device());
         if (!pool) return cudaErrorMemoryAllocation;
         return cudaMallocFromPoolAsync(&p, bytes, pool, s);
@@ -482,7 +509,7 @@ uint64_t g_graph_clock = 0;
 
 void drop_graph(StepGraph &e) {
     cudaGraphExecDestroy(e.exec);
-    cudaFree(e.scratch);
+    dev_free(e.scratch);
 }
 
 void purge_graphs(const bz_modes *m) {
@@ -608,9 +635,9 @@ int *device_error_word() {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_err_word[dev]) {
         int *p = nullptr;
-        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (dev_malloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
         if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) {
-            cudaFree(p);
+            dev_free(p);
             return nullptr;
         }
         g_err_word[dev] = p;
@@ -830,12 +857,12 @@ int imex_step(const bz_modes *m, int scheme, int model, double dt, double eps, c
     ne.stamp = ++g_graph_clock;
     ne.scratch = nullptr;
     ne.exec = nullptr;
-    cudaError_t e = cudaMalloc(&ne.scratch, step_scratch_bytes(m, t, n_cells, precision));
+    cudaError_t e = dev_malloc(&ne.scratch, step_scratch_bytes(m, t, n_cells, precision));
     if (e != cudaSuccess) return cuda_fail(e, "imex_step: graph scratch");
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
-        cudaFree(ne.scratch);
+        dev_free(ne.scratch);
         return cuda_fail(e, "imex_step: begin capture");
     }
     t_capturing = true;
@@ -845,7 +872,7 @@ int imex_step(const bz_modes *m, int scheme, int model, double dt, double eps, c
     if (rc == BZ_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ne.exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (rc != BZ_OK || e != cudaSuccess) {
-        cudaFree(ne.scratch);
+        dev_free(ne.scratch);
         return rc != BZ_OK ? rc : cuda_fail(e, "imex_step: capture");
     }
     if (g_graphs.size() >= kMaxGraphs) {
@@ -1143,6 +1170,27 @@ int bz_profile_read(char *names, int names_bytes, double *total_ms, int64_t *lau
         launches[i] = cnt[i];
     }
     return n;
+}
+
+int bz_inject_alloc_failure(int64_t after) {
+    g_fail_after.store(after < 0 ? -1 : after);
+    return BZ_OK;
+}
+
+int bz_alloc_stats(int64_t *live_blocks, uint64_t *pool_used_bytes) {
+    if (live_blocks) *live_blocks = g_live_blocks.load();
+    if (!pool_used_bytes) return BZ_OK;
+    uint64_t total = 0;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int d = 0; d < kMaxDevices; ++d) {
+        if (!g_pool_ok[d]) continue;
+        uint64_t used = 0;
+        cudaError_t e = cudaMemPoolGetAttribute(g_pool[d], cudaMemPoolAttrUsedMemCurrent, &used);
+        if (e != cudaSuccess) return cuda_fail(e, "bz_alloc_stats: pool attribute");
+        total += used;
+    }
+    *pool_used_bytes = total;
+    return BZ_OK;
 }
 
 void bz_grid_destroy(bz_grid *g) { grid_destroy(g); }

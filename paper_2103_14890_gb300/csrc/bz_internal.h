@@ -18,6 +18,19 @@ constexpr int kTile = 32;          // cells per tile in the Fourier scratch layo
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 
+// Device memory the library holds beyond one call (grid, kernel and mesh
+// tables, the autotuner's batch, cached graph scratch, the error word).  Every
+// such block goes through dev_malloc / dev_free, which count the live blocks;
+// alloc_fault_due() consumes one step of the host-side failure countdown that
+// bz_inject_alloc_failure arms (true: fail this allocation without calling
+// CUDA).  The per-call pool scratch draws on the same countdown.
+cudaError_t dev_malloc(void **p, size_t bytes);
+template <typename X> cudaError_t dev_malloc(X **p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+void dev_free(void *p);
+bool alloc_fault_due();
+
 // Device error word (one per device context), latched by kernels.
 enum DeviceError : int { kDevOk = 0, kDevNonFinite = 1, kDevTimeout = 2 };
 

@@ -153,7 +153,7 @@ void fill_real(const HostMesh &h, std::vector<double> &out) {
 }
 
 template <typename X> cudaError_t upload(X **d, const std::vector<X> &v) {
-    cudaError_t e = cudaMalloc(d, sizeof(X) * v.size());
+    cudaError_t e = dev_malloc(d, sizeof(X) * v.size());
     if (e == cudaSuccess) e = cudaMemcpy(*d, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice);
     return e;
 }
@@ -162,25 +162,25 @@ template <typename X> cudaError_t upload(X **d, const std::vector<X> &v) {
 
 void fv_mesh_destroy(bz_mesh *m) {
     if (!m) return;
-    cudaFree(m->d_nface);
-    cudaFree(m->d_nb);
-    cudaFree(m->d_ncen);
-    cudaFree(m->d_cen);
-    cudaFree(m->d_nsec);
-    cudaFree(m->d_sec);
-    cudaFree(m->d_order);
-    cudaFree(m->d_wall);
-    cudaFree(m->d_wall64);
-    cudaFree(m->d_wall32);
+    dev_free(m->d_nface);
+    dev_free(m->d_nb);
+    dev_free(m->d_ncen);
+    dev_free(m->d_cen);
+    dev_free(m->d_nsec);
+    dev_free(m->d_sec);
+    dev_free(m->d_order);
+    dev_free(m->d_wall);
+    dev_free(m->d_wall64);
+    dev_free(m->d_wall32);
     free(m->h_ptr);
     free(m->h_vtx);
     free(m->h_nb);
-    cudaFree(m->d_real64);
-    cudaFree(m->d_real32);
-    cudaFree(m->d_ncen3);
-    cudaFree(m->d_cen3);
-    cudaFree(m->d_real3_64);
-    cudaFree(m->d_real3_32);
+    dev_free(m->d_real64);
+    dev_free(m->d_real32);
+    dev_free(m->d_ncen3);
+    dev_free(m->d_cen3);
+    dev_free(m->d_real3_64);
+    dev_free(m->d_real3_32);
     free(m);
 }
 
@@ -606,9 +606,9 @@ int fv_mesh_set_walls(bz_mesh *m, int64_t n_edges, const int64_t *edges, const d
     if (!m) return fail(BZ_EINVAL, "fv_mesh_set_walls: mesh is NULL");
     if (n_edges < 0 || (n_edges > 0 && (!edges || !params)))
         return fail(BZ_EINVAL, "fv_mesh_set_walls: bad edge list");
-    cudaFree(m->d_wall);
-    cudaFree(m->d_wall64);
-    cudaFree(m->d_wall32);
+    dev_free(m->d_wall);
+    dev_free(m->d_wall64);
+    dev_free(m->d_wall32);
     m->d_wall = nullptr;
     m->d_wall64 = nullptr;
     m->d_wall32 = nullptr;
@@ -640,7 +640,15 @@ int fv_mesh_set_walls(bz_mesh *m, int64_t n_edges, const int64_t *edges, const d
     cudaError_t err = upload(&m->d_wall, wall);
     if (err == cudaSuccess) err = upload(&m->d_wall64, p64);
     if (err == cudaSuccess) err = upload(&m->d_wall32, p32);
-    if (err != cudaSuccess) return cuda_fail(err, "fv_mesh_set_walls: device tables");
+    if (err != cudaSuccess) {
+        dev_free(m->d_wall);
+        dev_free(m->d_wall64);
+        dev_free(m->d_wall32);
+        m->d_wall = nullptr;
+        m->d_wall64 = nullptr;
+        m->d_wall32 = nullptr;
+        return cuda_fail(err, "fv_mesh_set_walls: device tables");
+    }
     m->n_walls = n_edges;
     return BZ_OK;
 }

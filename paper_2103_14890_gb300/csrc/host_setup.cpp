@@ -137,15 +137,15 @@ int grid_create(int dim, int N, double L, bz_grid **out) {
             E32[(size_t)(k + v.h) * N + j] = make_float2((float)e.x, (float)e.y);
         }
     }
-    cudaError_t e = cudaMalloc(&g->d_E64, sizeof(double2) * E64.size());
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_E32, sizeof(float2) * E32.size());
+    cudaError_t e = dev_malloc(&g->d_E64, sizeof(double2) * E64.size());
+    if (e == cudaSuccess) e = dev_malloc(&g->d_E32, sizeof(float2) * E32.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(g->d_E64, E64.data(), sizeof(double2) * E64.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(g->d_E32, E32.data(), sizeof(float2) * E32.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(g->d_E64);
-        cudaFree(g->d_E32);
+        dev_free(g->d_E64);
+        dev_free(g->d_E32);
         free(g);
         return cuda_fail(e, "init_velocity_grid: device tables");
     }
@@ -196,8 +196,8 @@ int grid_create(int dim, int N, double L, bz_grid **out) {
 
 void grid_destroy(bz_grid *g) {
     if (!g) return;
-    cudaFree(g->d_E64);
-    cudaFree(g->d_E32);
+    dev_free(g->d_E64);
+    dev_free(g->d_E32);
     free(g);
 }
 
@@ -230,13 +230,13 @@ int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **o
     memcpy(m->h_F, F.data(), sizeof(double) * nF);
     std::vector<float> F32(nF);
     for (size_t i = 0; i < nF; ++i) F32[i] = (float)F[i];
-    cudaError_t e = cudaMalloc(&m->d_F64, sizeof(double) * nF);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_F32, sizeof(float) * nF);
+    cudaError_t e = dev_malloc(&m->d_F64, sizeof(double) * nF);
+    if (e == cudaSuccess) e = dev_malloc(&m->d_F32, sizeof(float) * nF);
     if (e == cudaSuccess) e = cudaMemcpy(m->d_F64, F.data(), sizeof(double) * nF, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->d_F32, F32.data(), sizeof(float) * nF, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(m->d_F64);
-        cudaFree(m->d_F32);
+        dev_free(m->d_F64);
+        dev_free(m->d_F32);
         free(m->h_F);
         free(m);
         return cuda_fail(e, "build_kernel_modes: device tables");
@@ -248,10 +248,7 @@ int modes_create(const bz_grid *g, double gamma, double b0, int nq, bz_modes **o
         m->tile_dft = rc == BZ_OK;
     }
     if (rc != BZ_OK) {
-        cudaFree(m->d_F64);
-        cudaFree(m->d_F32);
-        free(m->h_F);
-        free(m);
+        modes_destroy(m);        // also the variant tables built before the failure
         return rc;
     }
     *out = m;
@@ -325,9 +322,9 @@ int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out) {
     cudaError_t e = m->h_fast ? cudaSuccess : cudaErrorMemoryAllocation;
     if (e == cudaSuccess) {
         memcpy(m->h_fast, cf.data(), sizeof(double) * cf.size());
-        e = cudaMalloc(&m->d_fast64, sizeof(double) * cf.size());
+        e = dev_malloc(&m->d_fast64, sizeof(double) * cf.size());
     }
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_fast32, sizeof(float) * cf.size());
+    if (e == cudaSuccess) e = dev_malloc(&m->d_fast32, sizeof(float) * cf.size());
     if (e == cudaSuccess) e = cudaMemcpy(m->d_fast64, cf.data(), sizeof(double) * cf.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->d_fast32, cf32.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -349,18 +346,18 @@ int fast_modes_create(const bz_grid *g, double b0, int ndirs, bz_modes **out) {
 
 void modes_destroy(bz_modes *m) {
     if (!m) return;
-    cudaFree(m->d_fast64);
-    cudaFree(m->d_fast32);
+    dev_free(m->d_fast64);
+    dev_free(m->d_fast32);
     free(m->h_fast);
-    cudaFree(m->d_F64);
-    cudaFree(m->d_F32);
-    cudaFree(m->w64);
-    cudaFree(m->wx2);
-    cudaFree(m->task64);
+    dev_free(m->d_F64);
+    dev_free(m->d_F32);
+    dev_free(m->w64);
+    dev_free(m->wx2);
+    dev_free(m->task64);
     for (int v = 0; v < kModesumVariants; ++v) {
-        cudaFree(m->var_W[v]);
-        cudaFree(m->var_task[v]);
-        for (int k = 0; k < kSplitTables; ++k) cudaFree(m->var_task_split[v][k]);
+        dev_free(m->var_W[v]);
+        dev_free(m->var_task[v]);
+        for (int k = 0; k < kSplitTables; ++k) dev_free(m->var_task_split[v][k]);
     }
     free(m->h_F);
     free(m);

@@ -69,7 +69,6 @@ constexpr int kNumVariants = kModesumVariants;   // FP32 variants (timed by the 
 // whose 16-byte-per-value spectrum needs them (48^2, 16^3)
 constexpr Variant kVariants[kNumVariants + 2] = {{8, 16, 32, 1}, {4, 32, 32, 1}, {4, 16, 16, 1}, {4, 16, 8, 1},
                                                  {4, 16, 32, 2}, {2, 8, 8, 1},   {2, 8, 4, 1}};
-constexpr int kPackedVariant = 4;
 
 // lane groups splitting a task's outputs, and outputs per task (RT)
 constexpr int variant_groups(int v) { return 32 / kVariants[v].cells * kVariants[v].pack; }
@@ -941,18 +940,18 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
     T *dW = nullptr;
     int *dT = nullptr;
     float *dX = nullptr;
-    cudaError_t e = cudaMalloc(&dW, sizeof(T) * W.size());
-    if (e == cudaSuccess) e = cudaMalloc(&dT, sizeof(int) * tab.size());
+    cudaError_t e = dev_malloc(&dW, sizeof(T) * W.size());
+    if (e == cudaSuccess) e = dev_malloc(&dT, sizeof(int) * tab.size());
     if (e == cudaSuccess) e = cudaMemcpy(dW, W.data(), sizeof(T) * W.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dT, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && want_x2) {
-        e = cudaMalloc(&dX, sizeof(float) * X2.size());
+        e = dev_malloc(&dX, sizeof(float) * X2.size());
         if (e == cudaSuccess) e = cudaMemcpy(dX, X2.data(), sizeof(float) * X2.size(), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
-        cudaFree(dW);
-        cudaFree(dT);
-        cudaFree(dX);
+        dev_free(dW);
+        dev_free(dT);
+        dev_free(dX);
         rc = cuda_fail(e, "build_kernel_modes: weight stream");
         return false;
     }
@@ -961,14 +960,14 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
     if (outSplit) {
         for (int k = 0; k < kSplitTables && e == cudaSuccess; ++k) {
             const std::vector<int> ts = make_table(kWarps << (k + 1));
-            e = cudaMalloc(&outSplit[k], sizeof(int) * ts.size());
+            e = dev_malloc(&outSplit[k], sizeof(int) * ts.size());
             if (e == cudaSuccess) e = cudaMemcpy(outSplit[k], ts.data(), sizeof(int) * ts.size(), cudaMemcpyHostToDevice);
         }
         if (e != cudaSuccess) {
-            for (int k = 0; k < kSplitTables; ++k) cudaFree(outSplit[k]), outSplit[k] = nullptr;
-            cudaFree(dW);
-            cudaFree(dT);
-            cudaFree(dX);
+            for (int k = 0; k < kSplitTables; ++k) dev_free(outSplit[k]), outSplit[k] = nullptr;
+            dev_free(dW);
+            dev_free(dT);
+            dev_free(dX);
             rc = cuda_fail(e, "build_kernel_modes: split task tables");
             return false;
         }
@@ -1254,7 +1253,7 @@ static int autotune(bz_modes *m, int &rc) {
     const int64_t n = (int64_t)6 * sms * 32;
     const size_t bytes = 2 * sizeof(float2) * (size_t)((n + 31) / 32) * gv.nhalf * 32;
     void *buf = nullptr;
-    cudaError_t e = cudaMalloc(&buf, bytes);
+    cudaError_t e = dev_malloc(&buf, bytes);
     if (e == cudaSuccess) e = cudaMemset(buf, 0, bytes);
     cudaEvent_t a = nullptr, b = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&a);
@@ -1283,7 +1282,7 @@ static int autotune(bz_modes *m, int &rc) {
         if (best[avail[q]] < best[pick]) pick = avail[q];
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
-    cudaFree(buf);
+    dev_free(buf);
     if (e != cudaSuccess) {
         rc = cuda_fail(e, "build_kernel_modes: autotune");
         return avail[0];

@@ -70,3 +70,16 @@ def test_missing_library_fails_loudly(tmp_path):
             b.load(str(tmp_path / "absent.so"))
     finally:
         b._lib = saved
+
+
+def test_alloc_injection_hook_host_side(lib):
+    """The fault-injection hook and the allocation counters answer on the
+    host: arming and disarming return BZ_OK; with no handle alive and no pool
+    created the library holds nothing."""
+    from paper_2103_14890_gb300 import binding as b
+    assert lib.bz_inject_alloc_failure(3) == b.OK
+    assert lib.bz_inject_alloc_failure(-1) == b.OK
+    live, used = ctypes.c_int64(-7), ctypes.c_uint64(7)
+    assert lib.bz_alloc_stats(ctypes.byref(live), ctypes.byref(used)) == b.OK
+    assert live.value == 0 and used.value == 0
+    assert lib.bz_alloc_stats(None, None) == b.OK
