@@ -58,21 +58,28 @@ namespace {
 
 // Kernel variants: outputs per thread R along k_2, warps per CTA, cells per
 // CTA, cells per thread (pack: 1, or 2 for the packed two-cell kernel, whose
-// lanes hold cells c and c + 16 of a 32-cell tile in FP32x2 register pairs).
-// Variant ids reported by bz_modes_info are index + 1.
+// lanes hold cells c and c + 16 of a 32-cell tile in FP32x2 register pairs),
+// wdup: each weight stored twice (w, w) as an FP32x2 operand, pq: the FP32x2
+// form with one cell per lane (modesum_pq_kernel).  Variant ids reported by
+// bz_modes_info are index + 1.
 struct Variant {
-    int R, warps, cells, pack;
+    int R, warps, cells, pack, wdup, pq;
 };
 constexpr int kNumVariants = kModesumVariants;   // FP32 variants (timed by the autotuner)
-// entries 0..4: the FP32 variants; entries 5, 6: layouts of the FP64 and FP32X2
+// entries 0..6: the FP32 variants; entries 7, 8: layouts of the FP64 and FP32X2
 // forms only (2 outputs per thread, 8 warps, 8- and 4-cell tiles) for grids
 // whose 16-byte-per-value spectrum needs them (48^2, 16^3)
-constexpr Variant kVariants[kNumVariants + 2] = {{8, 16, 32, 1}, {4, 32, 32, 1}, {4, 16, 16, 1}, {4, 16, 8, 1},
-                                                 {4, 16, 32, 2}, {2, 8, 8, 1},   {2, 8, 4, 1}};
+constexpr Variant kVariants[kNumVariants + 2] = {
+    {8, 16, 32, 1, 0, 0}, {4, 32, 32, 1, 0, 0}, {4, 16, 16, 1, 0, 0}, {4, 16, 8, 1, 0, 0},
+    {4, 16, 32, 2, 1, 0}, {8, 12, 32, 1, 0, 1}, {8, 16, 32, 1, 0, 1}, {2, 8, 8, 1, 0, 0}, {2, 8, 4, 1, 0, 0}};
 
 // lane groups splitting a task's outputs, and outputs per task (RT)
 constexpr int variant_groups(int v) { return 32 / kVariants[v].cells * kVariants[v].pack; }
 constexpr int variant_rt(int v) { return kVariants[v].R * variant_groups(v); }
+// Whether an FP32 variant's tables compute k_2 < 0 on the reflected spectrum
+// (every output block of k_2 >= 0 fits within the row: R T <= h + 1); all
+// variants that do sum each output in one order, as do all that do not.
+constexpr bool variant_reflects(int v, int h) { return kVariants[v].pack == 1 && variant_rt(v) <= h + 1; }
 constexpr int kTaskInts = 12;   // ints per task record
 
 constexpr int kPad = 8;         // zero guard columns before the first and after the last row
@@ -80,7 +87,8 @@ constexpr int kRowHeadBytes = 16;   // row-pair header in front of each weight r
 
 struct TaskRec {
     int orow, k20, nrows, l2lo, nblk, woff, rfirst;   // rfirst: first r (of RT) this task stores
-    int rowf, pad0, pad1, pad2, pad3;                 // rowf: elements per row pair (header + weights)
+    int rowf, flags, crow, pad2, pad3;                // rowf: elements per row pair (header + weights);
+                                                      // flags: kTask*; crow: row of the conjugate outputs
 };
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -123,40 +131,54 @@ __device__ __forceinline__ void load_w4(double *wv, const double *p) {
     wv[3] = b.y;
 }
 
-// One block of R l_2 steps.  The window of f-hat_m values lives in a 2R-slot
+// One block of RR l_2 steps.  The window of f-hat_m values lives in a 2RR-slot
 // register array used under two alternating namings (PH = 0, 1): logical slot
-// j is physical slot (j + PH R) mod 2R, so moving the window by R between
-// blocks costs no register moves.  Columns are CS elements apart; f-hat_l is
-// read at lp, lp + DIR CS, ...: for DIR = -1 (l_1 < 0) the row is that of -l_1
-// read backwards and f-hat_l = conj of the value read, which only flips the
-// signs of two FMA operands.  The weights of step s are wb[s * WS + r].  Four
-// instances of this body exist per variant (PH x DIR); one row uses two.
-template <typename T, int RR, int CS, int WS, int PH, int DIR>
-__device__ __forceinline__ void block_pass(typename C2<T>::type (&win)[2 * RR],
+// j is physical slot (j + PH RR) mod 2RR, so moving the window by RR between
+// blocks costs no register moves; logical slot j of a block holds the column
+// mp + j CS, and output r at step s reads logical slot r - s + RR - 1.
+// f-hat_l is read at lp, lp + D, lp + 2 D, ... with D = DIR CS: for DIR = -1
+// (l_1 < 0) the row is that of -l_1 read backwards and f-hat_l = conj of the
+// value read, which only flips the signs of two FMA operands.  DIR = 0 takes
+// the direction at run time (D = dcs, sgn = +/-1 multiplies the value's
+// imaginary part): the products are those of DIR = +1 on the conjugated value,
+// which are exactly those of DIR = -1 on the value read (negation is exact), so
+// the results equal the specialised bodies' bit for bit with half the code.
+// The weights of step s are wb[s * WS + r].
+//
+// RAMP: the first block of a task whose steps start one before the lowest l_2
+// of its first output (l2lo = k2_0 - h - 1, outputs k2_0 + r >= 0): pair
+// (s, r) lies in K_h exactly when s > r, so only those pairs are evaluated
+// (the others have zero weights and would add exact zeros), and the window
+// slots it needs are only the RR - 1 it loads itself.
+template <typename T, int RR, int CS, int WS, int PH, int DIR, bool RAMP>
+__device__ __forceinline__ void block_body(typename C2<T>::type (&win)[2 * RR],
                                            const typename C2<T>::type *__restrict__ mp,
-                                           const typename C2<T>::type *__restrict__ lp, const T *__restrict__ wb,
-                                           typename C2<T>::type (&acc)[RR]) {
+                                           const typename C2<T>::type *__restrict__ lp, int dcs, T sgn,
+                                           const T *__restrict__ wb, typename C2<T>::type (&acc)[RR]) {
     using V2 = typename C2<T>::type;
 #pragma unroll
-    for (int j = 0; j < RR; ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
+    for (int j = 0; j < (RAMP ? RR - 1 : RR); ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
 #pragma unroll
-    for (int s = 0; s < RR; ++s) {
-        const V2 fl = lp[s * DIR * CS];
+    for (int s = RAMP ? 1 : 0; s < RR; ++s) {
+        V2 fl = (DIR == 0) ? lp[s * dcs] : lp[s * DIR * CS];
+        if (DIR == 0) fl.y *= sgn;
         T wv[RR];
         if constexpr (RR % 4 == 0) {
 #pragma unroll
-            for (int q = 0; q < RR; q += 4) load_w4(wv + q, wb + s * WS + q);
+            for (int q = 0; q < RR; q += 4)
+                if (!RAMP || q < s) load_w4(wv + q, wb + s * WS + q);
         } else {
-            static_assert(RR == 2 && sizeof(T) == 8, "two-output blocks are used by the FP64 form only");
+            static_assert(RR == 2 && sizeof(T) == 8 && !RAMP, "two-output blocks are used by the FP64 form only");
             const double2 w2 = *reinterpret_cast<const double2 *>(wb + s * WS);
             wv[0] = w2.x;
             wv[1] = w2.y;
         }
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
+            if (RAMP && r >= s) continue;
             const V2 b = win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)];
             const T tx = wv[r] * fl.x, ty = wv[r] * fl.y;       // weight * value read
-            if (DIR > 0) {                                      // acc += w f-hat_l b
+            if (DIR >= 0) {                                     // acc += w f-hat_l b
                 acc[r].x = fma(tx, b.x, acc[r].x);
                 acc[r].x = fma(-ty, b.y, acc[r].x);
                 acc[r].y = fma(tx, b.y, acc[r].y);
@@ -171,92 +193,93 @@ __device__ __forceinline__ void block_pass(typename C2<T>::type (&win)[2 * RR],
     }
 }
 
-// block_pass with the read direction of f-hat_l at run time: dcs = +/-CS
-// (elements between consecutive l_2), sgn = +/-1 multiplies the value's
-// imaginary part (f-hat_l = conj of the value read for l_1 < 0).  The
-// products are those of block_pass<.., +1> on the conjugated value, which are
-// exactly those of block_pass<.., -1> on the value read (negation is exact),
-// so the results equal the specialised bodies' bit for bit with half the code
-// (the R = 8 kernel's four specialised bodies overflow the instruction cache).
-template <typename T, int RR, int CS, int WS, int PH>
-__device__ __forceinline__ void block_pass_rt(typename C2<T>::type (&win)[2 * RR],
-                                              const typename C2<T>::type *__restrict__ mp,
-                                              const typename C2<T>::type *__restrict__ lp, int dcs, T sgn,
-                                              const T *__restrict__ wb, typename C2<T>::type (&acc)[RR]) {
-    using V2 = typename C2<T>::type;
-#pragma unroll
-    for (int j = 0; j < RR; ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
-#pragma unroll
-    for (int s = 0; s < RR; ++s) {
-        V2 fl = lp[s * dcs];
-        fl.y *= sgn;
-        T wv[RR];
-#pragma unroll
-        for (int q = 0; q < RR; q += 4) load_w4(wv + q, wb + s * WS + q);
-#pragma unroll
-        for (int r = 0; r < RR; ++r) {
-            const V2 b = win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)];
-            const T tx = wv[r] * fl.x, ty = wv[r] * fl.y;
-            acc[r].x = fma(tx, b.x, acc[r].x);
-            acc[r].x = fma(-ty, b.y, acc[r].x);
-            acc[r].y = fma(tx, b.y, acc[r].y);
-            acc[r].y = fma(ty, b.x, acc[r].y);
-        }
-    }
-}
-
-template <typename T, int RR, int CS, int WS>
-__device__ __forceinline__ void row_pass_rt(const typename C2<T>::type *__restrict__ rowl,
-                                            const typename C2<T>::type *__restrict__ rowm, const T *__restrict__ wrow,
-                                            int nblk, int l2lo, int mbase0, int dir, typename C2<T>::type (&acc)[RR]) {
+// One row pair of a task for this thread's RR outputs:
+// acc[r] += sum_l2 w(l2, r) f-hat_l(l2) f-hat_m(k2_0 + r - l2) over nblk
+// blocks of RR steps from l2lo.  rowl / rowm point at column 0 of the rows of
+// l (or -l) and m (this thread's cell); wrow at this thread's first weight of
+// the row.  The blocks run as pairs (PH 0, PH 1) and a last PH 0; with ramp
+// (RAMPS only) the first block is the ramp body.
+template <typename T, int RR, int CS, int WS, int DIR, bool RAMPS>
+__device__ __forceinline__ void row_pass(const typename C2<T>::type *__restrict__ rowl,
+                                         const typename C2<T>::type *__restrict__ rowm, const T *__restrict__ wrow,
+                                         int nblk, int l2lo, int mbase0, int dir, bool ramp,
+                                         typename C2<T>::type (&acc)[RR]) {
     using V2 = typename C2<T>::type;
     V2 win[2 * RR];
-    const int dcs = dir * CS;
+    const int dcs = (DIR == 0 ? dir : DIR) * CS;
     const T sgn = (T)dir;
     const V2 *mp = rowm + mbase0 * CS;
     const V2 *lp = rowl + l2lo * dcs;
-#pragma unroll
-    for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * CS];
     int blk = 0;
+    bool ramped = false;
+    if constexpr (RAMPS) {
+        if (ramp) {
+            // the ramp block under the PH 1 naming leaves the window exactly
+            // as the preload below does for a first block under PH 0
+            block_body<T, RR, CS, WS, 1, DIR, true>(win, mp, lp, dcs, sgn, wrow, acc);
+            mp -= RR * CS;
+            lp += RR * dcs;
+            blk = 1;
+            ramped = true;
+        }
+    }
+    if (!ramped) {
+#pragma unroll
+        for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * CS];
+    }
     for (; blk + 1 < nblk; blk += 2) {
-        block_pass_rt<T, RR, CS, WS, 0>(win, mp, lp, dcs, sgn, wrow + blk * RR * WS, acc);
-        block_pass_rt<T, RR, CS, WS, 1>(win, mp - RR * CS, lp + RR * dcs, dcs, sgn, wrow + (blk + 1) * RR * WS, acc);
+        block_body<T, RR, CS, WS, 0, DIR, false>(win, mp, lp, dcs, sgn, wrow + blk * RR * WS, acc);
+        block_body<T, RR, CS, WS, 1, DIR, false>(win, mp - RR * CS, lp + RR * dcs, dcs, sgn,
+                                                 wrow + (blk + 1) * RR * WS, acc);
         mp -= 2 * RR * CS;
         lp += 2 * RR * dcs;
     }
-    if (blk < nblk) block_pass_rt<T, RR, CS, WS, 0>(win, mp, lp, dcs, sgn, wrow + blk * RR * WS, acc);
+    if (blk < nblk) block_body<T, RR, CS, WS, 0, DIR, false>(win, mp, lp, dcs, sgn, wrow + blk * RR * WS, acc);
 }
 
-// One row pair of a task for this thread's R outputs:
-// acc[r] += sum_l2 w(l2, r) f-hat_l(l2) f-hat_m(k2_0 + r - l2).
-// rowl / rowm point at column 0 of the rows of l (or -l) and m (this thread's
-// cell); wrow at this thread's first weight of the row.
-template <typename T, int RR, int CS, int WS, int DIR>
-__device__ __forceinline__ void row_pass(const typename C2<T>::type *__restrict__ rowl,
-                                         const typename C2<T>::type *__restrict__ rowm, const T *__restrict__ wrow,
-                                         int nblk, int l2lo, int mbase0, typename C2<T>::type (&acc)[RR]) {
-    using V2 = typename C2<T>::type;
-    V2 win[2 * RR];
-    const V2 *mp = rowm + mbase0 * CS;
-    const V2 *lp = rowl + DIR * l2lo * CS;
-#pragma unroll
-    for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * CS];
-    int blk = 0;
-    for (; blk + 1 < nblk; blk += 2) {
-        block_pass<T, RR, CS, WS, 0, DIR>(win, mp, lp, wrow + blk * RR * WS, acc);
-        block_pass<T, RR, CS, WS, 1, DIR>(win, mp - RR * CS, lp + RR * DIR * CS, wrow + (blk + 1) * RR * WS, acc);
-        mp -= 2 * RR * CS;
-        lp += 2 * RR * DIR * CS;
+// Copy this CTA's cells of the tile's half spectrum into shared memory
+// ([kPad + nhalf + kPad][CELLS], zero guards), or with every row's columns
+// reversed (rev: mode (row, c) <- (row, -c), the spectrum of f reflected in
+// the last velocity axis).
+template <typename V2, int CELLS>
+__device__ __forceinline__ void stage_spectrum(uint4 *smem16, const V2 *fhat, int64_t tile, int sub, int nhalf,
+                                               int M, bool rev) {
+    constexpr int VEC = 16 / (int)sizeof(V2);                    // cells per 16-byte vector
+    constexpr int Q4 = CELLS / VEC, ROW = 32 / VEC;              // vectors per mode: this CTA, whole tile
+    const uint4 *src = reinterpret_cast<const uint4 *>(fhat + tile * (int64_t)nhalf * 32) + sub * Q4;
+    const int body = nhalf * Q4, guard = kPad * Q4;
+    for (int i = threadIdx.x; i < body + 2 * guard; i += blockDim.x) {
+        const int b = i - guard;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (b >= 0 && b < body) {
+            int mode = b / Q4;
+            if (rev) {
+                const int row = mode / M;
+                mode = row * M + (M - 1) - (mode - row * M);
+            }
+            v = src[mode * ROW + (b % Q4)];
+        }
+        smem16[i] = v;
     }
-    if (blk < nblk) block_pass<T, RR, CS, WS, 0, DIR>(win, mp, lp, wrow + blk * RR * WS, acc);
 }
 
+// Task flags (TaskRec.flags)
+constexpr int kTaskRamp = 1;     // first block is the ramp (l2lo = k2_0 - h - 1)
+constexpr int kTaskRefl = 2;     // runs on the reflected spectrum; stores output k_2 at column -k_2
+constexpr int kTaskConj = 4;     // k_1 = 0 row: also stores conj(Q-hat) at (row crow, column -k_2), k_2 > 0
+
+// The task table: 2 W + 1 offsets (W = warps x split), then the records.
+// Warp w's phase-0 tasks are [off[w], off[w + 1]) and its phase-1 tasks
+// [off[W + w], off[W + w + 1]); phase 1 (tasks flagged kTaskRefl) runs after
+// the CTA has restaged its spectrum reversed.  Tables without reflected
+// tasks have an empty phase 1.
 template <typename T, int RR, int WARPS, int CELLS, bool RTDIR = false>
 __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Group gd) {
     using V2 = typename C2<T>::type;
     constexpr int G = 32 / CELLS;     // lane groups splitting a task's outputs
     constexpr int RT = RR * G;        // outputs per task
     constexpr int HEAD = kRowHeadBytes / (int)sizeof(T);
+    constexpr bool RAMPS = (G == 1);  // ramped tasks need every lane on the same outputs
     extern __shared__ __align__(16) uint4 smem16[];
     // this CTA's instance and tile (instances are ordered longest-first)
     int it = 0;
@@ -277,30 +300,45 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
     const int sub = (int)(cta % G);                                  // which CELLS-cell part of it
     V2 *Fs = reinterpret_cast<V2 *>(smem16);                         // [kPad + nhalf + kPad][CELLS]
     T *wsm = reinterpret_cast<T *>(Fs + (size_t)(nhalf + 2 * kPad) * CELLS);   // [warps][2][wrow_max]
-    {
-        // copy this CTA's cells of the tile's half spectrum, zero the guards
-        constexpr int VEC = 16 / (int)sizeof(V2);                    // cells per 16-byte vector
-        constexpr int Q4 = CELLS / VEC, ROW = 32 / VEC;              // vectors per mode: this CTA, whole tile
-        const uint4 *src = reinterpret_cast<const uint4 *>(fhat + tile * (int64_t)nhalf * 32) + sub * Q4;
-        const int body = nhalf * Q4, guard = kPad * Q4;
-        for (int i = threadIdx.x; i < body + 2 * guard; i += blockDim.x) {
-            const int b = i - guard;
-            smem16[i] = (b >= 0 && b < body) ? src[(b / Q4) * ROW + (b % Q4)] : make_uint4(0u, 0u, 0u, 0u);
-        }
-    }
+    stage_spectrum<V2, CELLS>(smem16, fhat, tile, sub, nhalf, M, false);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cell = lane % CELLS, grp = lane / CELLS;
     T *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
     T *wbuf1 = wbuf0 + wrow_max;
-    const int vw = part * WARPS + warp;                              // task list of this warp
-    const int tbeg = tasks[vw], tend = tasks[vw + 1];
-    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS * ip.split + 1);
+    const int NW = WARPS * ip.split;                                 // task lists of the table
+    int t = tasks[part * WARPS + warp], tend = tasks[part * WARPS + warp + 1];
+    bool phase1 = false;
+    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + 2 * NW + 1);
     const V2 *F0 = Fs + (size_t)(kPad + h) * CELLS + cell;          // (row 0, column 0) of this cell
+    const bool valid = tile * 32 + sub * CELLS + cell < n;          // this lane's cell exists
+    V2 *const qt = Qhat + tile * (int64_t)nhalf * 32 + sub * CELLS + cell;   // its (row 0, column -h)
 
-    for (int t = tbeg; t < tend; ++t) {
-        const TaskRec tk = trec[t];
+    for (;;) {
+        if (t >= tend) {
+            // phase 1 (the same for the whole CTA: one table) after a restage;
+            // the item's fields are read again from the parameters here rather
+            // than kept in registers through the task loop
+            if (phase1) break;
+            const Mode32Item &iq = gd.item[it];
+            const int *tq = iq.tasks;
+            const int nw = WARPS * iq.split;
+            if (tq[2 * nw] == tq[nw]) break;
+            __syncthreads();                                         // every warp is done with the spectrum
+            const int64_t c1 = (int64_t)blockIdx.x - gd.tile_start[it];
+            const int64_t ct = c1 / iq.split;
+            stage_spectrum<V2, CELLS>(smem16, static_cast<const V2 *>(iq.fhat), ct / G, (int)(ct % G), iq.nhalf,
+                                      iq.M, true);
+            __syncthreads();
+            const int w1 = (int)(c1 % iq.split) * WARPS + (int)(threadIdx.x >> 5);
+            t = tq[nw + w1];
+            tend = tq[nw + w1 + 1];
+            phase1 = true;
+            continue;
+        }
+        const TaskRec tk = trec[t++];
         const int rowf = tk.rowf;                         // elements per row pair
+        const bool ramp = RAMPS && (tk.flags & kTaskRamp) != 0;
         const T *wsrc = W + tk.woff;
         V2 hi[RR], lo[RR], acc[RR];
 #pragma unroll
@@ -320,15 +358,16 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
             // row header: element offsets of the rows of l and m, and the
             // direction of l (-1: f-hat_l = conj(f-hat_{-l}), row of -l read backwards)
             const int4 hd = *reinterpret_cast<const int4 *>(wcur);
+            const int dir = hd.z > 0 ? 1 : -1;
             if constexpr (RTDIR)
-                row_pass_rt<T, RR, CELLS, RT>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G, tk.l2lo,
-                                              mbase0, hd.z > 0 ? 1 : -1, acc);
-            else if (hd.z > 0)
-                row_pass<T, RR, CELLS, RT, 1>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G, tk.l2lo,
-                                              mbase0, acc);
+                row_pass<T, RR, CELLS, RT, 0, RAMPS>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G,
+                                                     tk.l2lo, mbase0, dir, ramp, acc);
+            else if (dir > 0)
+                row_pass<T, RR, CELLS, RT, 1, RAMPS>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G,
+                                                     tk.l2lo, mbase0, dir, ramp, acc);
             else
-                row_pass<T, RR, CELLS, RT, -1>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G,
-                                               tk.l2lo, mbase0, acc);
+                row_pass<T, RR, CELLS, RT, -1, RAMPS>(F0 + hd.x, F0 + hd.y, wcur + HEAD + grp * RR, tk.nblk * G,
+                                                      tk.l2lo, mbase0, dir, ramp, acc);
             __syncwarp();
             // fold the row sums (<= 4 rows) into (hi, lo)
             if ((i & 3) == 3 || i + 1 == tk.nrows) {
@@ -345,14 +384,22 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum32_kernel(const Mode32Gr
                 }
             }
         }
-        const int64_t c = tile * 32 + sub * CELLS + cell;
-        if (c < n) {
-            V2 *out = Qhat + tile * (int64_t)nhalf * 32 + (int64_t)tk.orow * M * 32 + sub * CELLS + cell;
+        if (valid) {
+            // the record's output fields are read again here (volatile: not
+            // kept in registers through the row loop)
+            const volatile TaskRec *tv = trec + (t - 1);
+            const int orow = tv->orow, rfirst = tv->rfirst, flags = tv->flags, crow = tv->crow;
+            const int k2o = tv->k20 + grp * RR;
+            V2 *out = qt + (int64_t)orow * M * 32;
+            const bool refl = (flags & kTaskRefl) != 0, cj = (flags & kTaskConj) != 0;
 #pragma unroll
             for (int r = 0; r < RR; ++r) {
-                const int k2 = k20 + r;
-                if (grp * RR + r >= tk.rfirst && k2 <= h)
-                    out[(k2 + h) * 32] = cmk<V2>(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
+                const int k2 = k2o + r;
+                if (grp * RR + r >= rfirst && k2 <= h) {
+                    const V2 q = cmk<V2>(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
+                    out[(refl ? h - k2 : k2 + h) * 32] = q;
+                    if (cj && k2 > 0) qt[((int64_t)crow * M + h - k2) * 32] = cmk<V2>(q.x, -q.y);
+                }
             }
         }
     }
@@ -476,7 +523,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_p2_kernel(const Mode32G
     float *wbuf1 = wbuf0 + wrow_max;
     const int vw = part * WARPS + warp;
     const int tbeg = tasks[vw], tend = tasks[vw + 1];
-    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS * ip.split + 1);
+    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + 2 * WARPS * ip.split + 1);
     const float4 *F0 = Fs + (size_t)(kPad + h) * CS + pr;
 
     for (int t = tbeg; t < tend; ++t) {
@@ -533,6 +580,185 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_p2_kernel(const Mode32G
                 const float2 re = __fadd2_rn(hre[r], lre[r]), im = __fadd2_rn(him[r], lim[r]);
                 if (c0 < n) out[(k2 + h) * 32] = make_float2(re.x, im.x);
                 if (c1 < n) out[(k2 + h) * 32 + 16] = make_float2(re.y, im.y);
+            }
+        }
+    }
+}
+
+// ---- FP32x2 form with one cell per lane ----------------------------------------
+// The sums of modesum32_kernel (tiles of 32 cells, one cell per lane, RR
+// outputs per thread, reflected and ramped task tables) with the complex
+// product w f-hat_l b (b = f-hat_m from the window) split as
+//   U = w b                 (one FP32x2 multiply: (w b_x, w b_y)),
+//   P += U f_x, Q += U f_y  (two FP32x2 FMAs; f = f-hat_l, f_y negated for a
+//                            conjugated value),
+// so that Re = P_x - Q_y and Im = P_y + Q_x.  Three FP32x2 instructions per
+// pair in place of six scalar ones, the same six FP32 operations: the kernel
+// is bounded by the FMA pipe rather than by instruction issue.  The weights
+// are read as in the scalar kernels (16 bytes = four outputs' weights; a
+// broadcast 16-byte shared-memory load takes two wavefronts, so a stream of
+// (w, w) pairs would make shared memory the bound).  P and Q are folded into the (hi, lo) pair of each output every
+// four rows as (P_x - Q_y, P_y + Q_x); the sums differ in rounding from the
+// scalar kernels', so the last partial wave of a batch stays on this kernel.
+template <int RR, int WS, int PH, bool RAMP>
+__device__ __forceinline__ void block_pq(float2 (&win)[2 * RR], const float2 *__restrict__ mp,
+                                         const float2 *__restrict__ lp, int dcs, float sgn,
+                                         const float *__restrict__ wb, float2 (&P)[RR], float2 (&Q)[RR]) {
+    constexpr int CS = 32;
+#pragma unroll
+    for (int j = 0; j < (RAMP ? RR - 1 : RR); ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
+#pragma unroll
+    for (int s = RAMP ? 1 : 0; s < RR; ++s) {
+        const float2 fl = lp[s * dcs];
+        const float fy = fl.y * sgn;
+        const float2 fxx = make_float2(fl.x, fl.x), fyy = make_float2(fy, fy);
+#pragma unroll
+        for (int q = 0; q < RR; q += 4) {
+            if (RAMP && q >= s) continue;                       // outputs q .. q + 3 all before the ramp
+            float wv[4];
+            load_w4(wv, wb + s * WS + q);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int r = q + e;
+                if (RAMP && r >= s) continue;
+                const float2 u = __fmul2_rn(make_float2(wv[e], wv[e]), win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)]);
+                P[r] = __ffma2_rn(u, fxx, P[r]);
+                Q[r] = __ffma2_rn(u, fyy, Q[r]);
+            }
+        }
+    }
+}
+
+// One row pair (as row_pass): the ramp block under the PH 1 naming, or the
+// preload, then pairs of blocks (PH 0, PH 1) and a last PH 0.
+template <int RR, int WS>
+__device__ __forceinline__ void row_pass_pq(const float2 *__restrict__ rowl, const float2 *__restrict__ rowm,
+                                            const float *__restrict__ wrow, int nblk, int l2lo, int mbase0,
+                                            int dir, bool ramp, float2 (&P)[RR], float2 (&Q)[RR]) {
+    constexpr int CS = 32;
+    float2 win[2 * RR];
+    const int dcs = dir * CS;
+    const float sgn = (float)dir;
+    const float2 *mp = rowm + mbase0 * CS;
+    const float2 *lp = rowl + l2lo * dcs;
+    int blk = 0;
+    if (ramp) {
+        block_pq<RR, WS, 1, true>(win, mp, lp, dcs, sgn, wrow, P, Q);
+        mp -= RR * CS;
+        lp += RR * dcs;
+        blk = 1;
+    } else {
+#pragma unroll
+        for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * CS];
+    }
+    for (; blk + 1 < nblk; blk += 2) {
+        block_pq<RR, WS, 0, false>(win, mp, lp, dcs, sgn, wrow + blk * RR * WS, P, Q);
+        block_pq<RR, WS, 1, false>(win, mp - RR * CS, lp + RR * dcs, dcs, sgn, wrow + (blk + 1) * RR * WS, P, Q);
+        mp -= 2 * RR * CS;
+        lp += 2 * RR * dcs;
+    }
+    if (blk < nblk) block_pq<RR, WS, 0, false>(win, mp, lp, dcs, sgn, wrow + blk * RR * WS, P, Q);
+}
+
+template <int RR, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) modesum_pq_kernel(const Mode32Group gd) {
+    constexpr int CELLS = 32;
+    constexpr int WS = RR;                       // floats per l_2 step
+    constexpr int HEAD = kRowHeadBytes / (int)sizeof(float);
+    extern __shared__ __align__(16) uint4 smem16[];
+    int it = 0;
+    while (it + 1 < gd.nitems && (int64_t)blockIdx.x >= gd.tile_start[it + 1]) ++it;
+    const Mode32Item &ip = gd.item[it];
+    const float2 *__restrict__ fhat = static_cast<const float2 *>(ip.fhat);
+    float2 *__restrict__ Qhat = static_cast<float2 *>(ip.Qhat);
+    const float *__restrict__ W = static_cast<const float *>(ip.W);
+    const int *__restrict__ tasks = ip.tasks;
+    const int h = ip.h, M = ip.M, nhalf = ip.nhalf, wrow_max = ip.wrow_max;
+    const int64_t cta0 = (int64_t)blockIdx.x - gd.tile_start[it];
+    const int part = (int)(cta0 % ip.split);
+    const int64_t tile = cta0 / ip.split;
+    float2 *Fs = reinterpret_cast<float2 *>(smem16);                 // [kPad + nhalf + kPad][32]
+    float *wsm = reinterpret_cast<float *>(Fs + (size_t)(nhalf + 2 * kPad) * CELLS);
+    stage_spectrum<float2, CELLS>(smem16, fhat, tile, 0, nhalf, M, false);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
+    float *wbuf1 = wbuf0 + wrow_max;
+    const int NW = WARPS * ip.split;
+    int t = tasks[part * WARPS + warp], tend = tasks[part * WARPS + warp + 1];
+    bool phase1 = false;
+    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + 2 * NW + 1);
+    const float2 *F0 = Fs + (size_t)(kPad + h) * CELLS + lane;
+    const bool valid = tile * 32 + lane < ip.n;
+    float2 *const qt = Qhat + tile * (int64_t)nhalf * 32 + lane;
+
+    for (;;) {
+        if (t >= tend) {
+            if (phase1) break;
+            const Mode32Item &iq = gd.item[it];
+            const int *tq = iq.tasks;
+            const int nw = WARPS * iq.split;
+            if (tq[2 * nw] == tq[nw]) break;
+            __syncthreads();
+            const int64_t c1 = (int64_t)blockIdx.x - gd.tile_start[it];
+            stage_spectrum<float2, CELLS>(smem16, static_cast<const float2 *>(iq.fhat), c1 / iq.split, 0, iq.nhalf,
+                                          iq.M, true);
+            __syncthreads();
+            const int w1 = (int)(c1 % iq.split) * WARPS + (int)(threadIdx.x >> 5);
+            t = tq[nw + w1];
+            tend = tq[nw + w1 + 1];
+            phase1 = true;
+            continue;
+        }
+        const TaskRec tk = trec[t++];
+        const int rowf = tk.rowf;
+        const bool ramp = (tk.flags & kTaskRamp) != 0;
+        const float *wsrc = W + tk.woff;
+        float2 hi[RR], lo[RR], P[RR], Q[RR];
+#pragma unroll
+        for (int r = 0; r < RR; ++r) hi[r] = lo[r] = P[r] = Q[r] = make_float2(0.f, 0.f);
+        const int mbase0 = tk.k20 - tk.l2lo - (RR - 1);
+        stage_row(wbuf0, wsrc, rowf * (int)sizeof(float), lane);
+        for (int i = 0; i < tk.nrows; ++i) {
+            const float *wcur = (i & 1) ? wbuf1 : wbuf0;
+            if (i + 1 < tk.nrows) {
+                stage_row((i & 1) ? wbuf0 : wbuf1, wsrc + (size_t)(i + 1) * rowf, rowf * (int)sizeof(float), lane);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            const int4 hd = *reinterpret_cast<const int4 *>(wcur);
+            row_pass_pq<RR, WS>(F0 + hd.x, F0 + hd.y, wcur + HEAD, tk.nblk, tk.l2lo, mbase0, hd.z > 0 ? 1 : -1, ramp,
+                                P, Q);
+            __syncwarp();
+            if ((i & 3) == 3 || i + 1 == tk.nrows) {
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const float ax = P[r].x - Q[r].y, ay = P[r].y + Q[r].x;
+                    float sx, ex, sy, ey;
+                    two_sum(hi[r].x, ax, sx, ex);
+                    two_sum(hi[r].y, ay, sy, ey);
+                    hi[r] = make_float2(sx, sy);
+                    lo[r].x += ex;
+                    lo[r].y += ey;
+                    P[r] = Q[r] = make_float2(0.f, 0.f);
+                }
+            }
+        }
+        if (valid) {
+            const volatile TaskRec *tv = trec + (t - 1);
+            const int orow = tv->orow, rfirst = tv->rfirst, flags = tv->flags, crow = tv->crow, k20 = tv->k20;
+            float2 *out = qt + (int64_t)orow * M * 32;
+            const bool refl = (flags & kTaskRefl) != 0, cj = (flags & kTaskConj) != 0;
+#pragma unroll
+            for (int r = 0; r < RR; ++r) {
+                const int k2 = k20 + r;
+                if (r >= rfirst && k2 <= h) {
+                    const float2 q = make_float2(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
+                    out[(refl ? h - k2 : k2 + h) * 32] = q;
+                    if (cj && k2 > 0) qt[((int64_t)crow * M + h - k2) * 32] = make_float2(q.x, -q.y);
+                }
             }
         }
     }
@@ -731,7 +957,7 @@ modesum_x2_kernel(const double2 *__restrict__ fhat, float2 *__restrict__ Qhat, c
     float *wbuf0 = wsm + (size_t)warp * 4 * wrow_max;             // wrow_max counts 8-byte slots
     float *wbuf1 = wbuf0 + 2 * wrow_max;
     const int tbeg = tasks[warp], tend = tasks[warp + 1];
-    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + WARPS + 1);
+    const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + 2 * WARPS + 1);
     const float2 *F0 = Fh + (size_t)(kPad + h) * CELLS + cell;
 
     for (int t = tbeg; t < tend; ++t) {
@@ -793,7 +1019,7 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
     constexpr int HEAD = kRowHeadBytes / (int)sizeof(T);
     const int R = variant_rt(v);                                // outputs per task (RT)
     const int kWarps = kVariants[v].warps;
-    const int pack = kVariants[v].pack;                         // 2: each weight stored twice (w, w)
+    const int pack = kVariants[v].pack;                         // cells per lane
     rc = BZ_OK;
     const GridView &gv = m->g->v;
     const int d = gv.dim, h = gv.h, M = gv.M;
@@ -808,6 +1034,15 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
     const bool want_x2 = outX2 != nullptr && sizeof(T) == 8;
     std::vector<double> stepw(R);
     std::vector<double> cost;
+    std::vector<int> phase;                                 // 1: runs on the reflected spectrum
+    // reflect: the FP32 variants with one cell per lane whose output blocks
+    // fit the row compute k_2 < 0 as k_2 > 0 of the spectrum reflected in the
+    // last axis (beta-hat is invariant under that reflection); ramped: with
+    // one lane group and R dividing h + 1, every task starts with the ramp
+    // block and no step is padding
+    const int G = 32 / kVariants[v].cells;
+    const bool reflect = sizeof(T) == 4 && variant_reflects(v, h);
+    const bool ramped = reflect && G == 1 && (h + 1) % R == 0;
     const int nmid = (d == 3) ? M : 1;                      // values of the middle index (3-D)
     struct Pair { int l[2], m[2]; };                         // leading indices of l and m
     for (int k1 = 0; k1 <= h; ++k1) {
@@ -824,29 +1059,47 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                         pairs.push_back({{l1, l2}, {m1, k2 - l2}});
                 }
             }
+            // blocks of R consecutive last-axis outputs.  reflect: the blocks
+            // start at 0, R, 2R, ... and cover k_2 >= 0; each is run a second
+            // time on the reflected spectrum for k_2 <= 0 (same weights), except
+            // in the k_1 = 0 row, whose k_2 < 0 outputs are the conjugates of its
+            // k_2 > 0 ones.  Otherwise they tile [-h, h], the last one ending at
+            // h (it may overlap the previous block, whose outputs it then does
+            // not store) and a block wider than the row starting at -h.
+            std::vector<int> starts;
+            if (reflect) {
+                for (int k = 0; k <= h; k += R) starts.push_back(k);
+            } else {
+                for (int b = 0; b < nb; ++b) starts.push_back(std::max(-h, std::min(-h + R * b, h - R + 1)));
+            }
             int prev_end = -h - 1;
-            for (int b = 0; b < nb; ++b) {
-                // blocks of R consecutive last-axis outputs; the last one ends at h
-                // (it may overlap the previous block, whose outputs it then does
-                // not store); a block wider than the row starts at -h
-                const int k20 = std::max(-h, std::min(-h + R * b, h - R + 1));
+            for (const int k20 : starts) {
                 const int k2last = k20 + R - 1;
-                const int lo = std::max(-h, k20 - h), hi = std::min(h, k2last + h);
-                const int len = hi - lo + 1;
-                const int nblk = (len + R - 1) / R;
-                const int npad = nblk * R;
-                // place the padded range [l2lo, l2lo + npad - 1] so that every f-hat_l
-                // column and every window column k - l lies within kPad of [-h, h]
-                int l2lo = 0;
-                bool placed = false;
-                for (int cand = lo - (npad - len); cand <= lo && !placed; ++cand) {
-                    const int last = cand + npad - 1;
-                    if (cand < lo_col || last > hi_col) continue;
-                    if (k20 - last < lo_col || k2last - cand > hi_col) continue;
-                    l2lo = cand;
-                    placed = true;
+                int l2lo = 0, nblk = 0, npad = 0;
+                if (ramped) {
+                    // one step before the lowest l_2 of output k20, through h:
+                    // 2h + 2 - k20 steps, a multiple of R when R divides h + 1
+                    l2lo = k20 - h - 1;
+                    npad = 2 * h + 2 - k20;
+                    nblk = npad / R;
+                } else {
+                    const int lo = std::max(-h, k20 - h), hi = std::min(h, k2last + h);
+                    const int len = hi - lo + 1;
+                    nblk = (len + R - 1) / R;
+                    npad = nblk * R;
+                    // place the padded range [l2lo, l2lo + npad - 1] so that every
+                    // f-hat_l column and every window column k - l lies within kPad
+                    // of [-h, h]
+                    bool placed = false;
+                    for (int cand = lo - (npad - len); cand <= lo && !placed; ++cand) {
+                        const int last = cand + npad - 1;
+                        if (cand < lo_col || last > hi_col) continue;
+                        if (k20 - last < lo_col || k2last - cand > hi_col) continue;
+                        l2lo = cand;
+                        placed = true;
+                    }
+                    if (!placed) return false;
                 }
-                if (!placed) return false;
                 TaskRec t;
                 t.orow = orow;
                 t.k20 = k20;
@@ -854,9 +1107,11 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                 t.l2lo = l2lo;
                 t.nblk = nblk;
                 t.woff = (int)W.size();
-                t.rfirst = std::max(0, prev_end + 1 - k20);
-                t.rowf = HEAD + npad * R * pack;
-                t.pad0 = t.pad1 = t.pad2 = t.pad3 = 0;
+                t.rfirst = reflect ? 0 : std::max(0, prev_end + 1 - k20);
+                t.rowf = HEAD + npad * R * (kVariants[v].wdup ? 2 : 1);
+                t.flags = (ramped ? kTaskRamp : 0) | (reflect && k1 == 0 ? kTaskConj : 0);
+                t.crow = (d == 3) ? (M - 1 - i2) : 0;        // k_1 = 0: row of -k (middle index -k_2)
+                t.pad2 = t.pad3 = 0;
                 prev_end = k2last;
                 for (const Pair &p : pairs) {
                     // row of l (that of -l read backwards when l_1 < 0) and row of m
@@ -894,7 +1149,7 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                                 if (p.l[0] < p.m[0]) w += beta_host(m, mm, l);
                             }
                             W.push_back((T)w);
-                            if (pack == 2) W.push_back((T)w);
+                            if (kVariants[v].wdup) W.push_back((T)w);
                             stepw[r] = w;
                         }
                         if (want_x2) {
@@ -903,34 +1158,48 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                         }
                     }
                 }
+                // evaluated pairs (a ramp skips R (R + 1) / 2 of each row pair's)
+                const double c = (double)t.nrows * ((double)npad * R - (ramped ? R * (R + 1) / 2 : 0) + 2.0 * npad);
                 tasks.push_back(t);
-                cost.push_back((double)t.nrows * npad);
+                cost.push_back(c);
+                phase.push_back(0);
+                if (reflect && k1 > 0) {
+                    TaskRec tr = t;                      // the same weights on the reflected spectrum
+                    tr.flags = (t.flags & kTaskRamp) | kTaskRefl;
+                    tr.rfirst = (k20 == 0) ? 1 : 0;      // k_2 = 0 is the unreflected task's
+                    tasks.push_back(tr);
+                    cost.push_back(c);
+                    phase.push_back(1);
+                }
             }
         }
     }
     // longest-processing-time-first assignment of tasks to nw warps: the
     // offsets of each warp's list, then the task records
     auto make_table = [&](int nw) {
-        std::vector<int> order(tasks.size());
-        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-        std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-        std::vector<double> load(nw, 0.0);
-        std::vector<std::vector<int>> per(nw);
-        for (int i : order) {
-            int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-            load[w] += cost[i];
-            per[w].push_back(i);
+        std::vector<std::vector<int>> per(2 * nw);
+        for (int ph = 0; ph < 2; ++ph) {
+            std::vector<int> order;
+            for (size_t i = 0; i < tasks.size(); ++i)
+                if (phase[i] == ph) order.push_back((int)i);
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+            std::vector<double> load(nw, 0.0);
+            for (int i : order) {
+                int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                load[w] += cost[i];
+                per[ph * nw + w].push_back(i);
+            }
         }
-        std::vector<int> t(nw + 1 + tasks.size() * kTaskInts);
+        std::vector<int> t(2 * nw + 1 + tasks.size() * kTaskInts);
         int pos = 0;
-        for (int w = 0; w < nw; ++w) {
-            t[w] = pos;
-            for (int i : per[w]) {
-                std::memcpy(&t[nw + 1 + (size_t)pos * kTaskInts], &tasks[i], sizeof(TaskRec));
+        for (int q = 0; q < 2 * nw; ++q) {
+            t[q] = pos;
+            for (int i : per[q]) {
+                std::memcpy(&t[2 * nw + 1 + (size_t)pos * kTaskInts], &tasks[i], sizeof(TaskRec));
                 ++pos;
             }
         }
-        t[nw] = pos;
+        t[2 * nw] = pos;
         return t;
     };
     const std::vector<int> tab = make_table(kWarps);
@@ -990,6 +1259,15 @@ static cudaError_t launch_instance(const Mode32Group &gd, size_t sm, cudaStream_
     return cudaGetLastError();
 }
 
+template <int RR, int WARPS>
+static cudaError_t launch_pq(const Mode32Group &gd, size_t sm, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(modesum_pq_kernel<RR, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    modesum_pq_kernel<RR, WARPS><<<(unsigned)gd.tile_start[gd.nitems], WARPS * 32, sm, st>>>(gd);
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStream_t st) {
     switch (v) {
         case 0: return launch_instance<float, 8, 16, 32, true>(gd, sm, st);
@@ -1003,6 +1281,8 @@ static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStr
             modesum_p2_kernel<4, 16><<<(unsigned)gd.tile_start[gd.nitems], 16 * 32, sm, st>>>(gd);
             return cudaGetLastError();
         }
+        case 5: return launch_pq<8, 12>(gd, sm, st);
+        case 6: return launch_pq<8, 16>(gd, sm, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1042,9 +1322,9 @@ static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, 
 
 // FP64 form: the same kernel on double spectra and weights, on 16-cell tiles
 // (variant entry 2) or, where the double spectrum of 16 cells does not fit
-// shared memory, on 8- or 4-cell tiles (entries 5, 6: 48^2, 16^3); no
+// shared memory, on 8- or 4-cell tiles (entries 7, 8: 48^2, 16^3); no
 // last-wave split.  The FP32X2 form runs on the same layout.
-constexpr int kFp64Variants[3] = {2, 5, 6};
+constexpr int kFp64Variants[3] = {2, 7, 8};
 
 bool modesum64_available(const bz_modes *m) { return m->w64 != nullptr; }
 
@@ -1058,12 +1338,13 @@ cudaError_t launch_modesum64(const bz_modes *m, const double2 *fhat, double2 *Qh
     gd.tile_start[0] = 0;
     gd.tile_start[1] = ctas_for(m->variant64, n);
     const size_t sm = smem_bytes<double>(m->g->v, m->rowmax64, m->variant64);
-    if (m->variant64 == 2) return launch_instance<double, 4, 16, 16>(gd, sm, st);
-    if (m->variant64 == 5) return launch_instance<double, 2, 8, 8>(gd, sm, st);
-    return launch_instance<double, 2, 8, 4>(gd, sm, st);
+    if (m->variant64 == kFp64Variants[0]) return launch_instance<double, 4, 16, 16>(gd, sm, st);
+    if (m->variant64 == kFp64Variants[1]) return launch_instance<double, 2, 8, 8>(gd, sm, st);
+    if (m->variant64 == kFp64Variants[2]) return launch_instance<double, 2, 8, 4>(gd, sm, st);
+    return cudaErrorInvalidValue;
 }
 
-// FP32X2 form on the FP64 layout (variant entries 2, 4, 5).
+// FP32X2 form on the FP64 layout (the entries of kFp64Variants).
 bool modesum_x2_available(const bz_modes *m) { return m->wx2 != nullptr && m->variant64 >= 0; }
 
 template <int RR, int WARPS, int CELLS>
@@ -1084,9 +1365,10 @@ cudaError_t launch_modesum_x2(const bz_modes *m, const double2 *fhat, float2 *Qh
     // the FP64 layout's shared memory: spectra of 16 bytes per value (hi, lo
     // parts of FP32 instead of one double) and weight rows of 8-byte slots
     const size_t sm = smem_bytes<double>(m->g->v, m->rowmax64, m->variant64);
-    if (m->variant64 == 2) return launch_x2_instance<4, 16, 16>(m, fhat, Qhat, n, sm, st);
-    if (m->variant64 == 5) return launch_x2_instance<2, 8, 8>(m, fhat, Qhat, n, sm, st);
-    return launch_x2_instance<2, 8, 4>(m, fhat, Qhat, n, sm, st);
+    if (m->variant64 == kFp64Variants[0]) return launch_x2_instance<4, 16, 16>(m, fhat, Qhat, n, sm, st);
+    if (m->variant64 == kFp64Variants[1]) return launch_x2_instance<2, 8, 8>(m, fhat, Qhat, n, sm, st);
+    if (m->variant64 == kFp64Variants[2]) return launch_x2_instance<2, 8, 4>(m, fhat, Qhat, n, sm, st);
+    return cudaErrorInvalidValue;
 }
 
 static int sm_count();
@@ -1098,8 +1380,9 @@ static int sm_count();
 // S the largest with T S <= SM count; when no such S exists (T > SMs / 2)
 // and the 16-cell variant fits the grid, the remaining tiles run on it (twice
 // the CTAs, each half as long).  Every output is computed by one task in
-// either case, with the same arithmetic, so the results do not depend on the
-// split.  Returns the cells of the main part; *tail_v is the tail's variant
+// either case, with the same arithmetic (the one-cell-per-lane variants sum
+// each output over the same terms in the same order), so the results do not
+// depend on the split.  Returns the cells of the main part; *tail_v is the tail's variant
 // (-1: no tail) and *tail_split its split.
 int64_t modesum32_split(const bz_modes *m, int64_t n, int *tail_v, int *tail_split) {
     *tail_v = -1;
@@ -1117,7 +1400,10 @@ int64_t modesum32_split(const bz_modes *m, int64_t n, int *tail_v, int *tail_spl
             return full * 32;
         }
     }
-    if (!m->var_W[2]) return n;
+    // the 16-cell variant, if it sums every output in the order of this one
+    if (!m->var_W[2] || kVariants[m->variant].pq ||
+        variant_reflects(2, m->g->v.h) != variant_reflects(m->variant, m->g->v.h))
+        return n;
     *tail_v = 2;
     return full * 32;
 }

@@ -70,15 +70,15 @@ def test_fast_kernels_selected(bz):
     and the 3-D grids up to 16^3 (a silent fall back to the generic kernel would
     hide a table-building bug)."""
     for N in (16, 24, 32):
-        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant in (1, 2, 3, 5), N
+        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7), N
     assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_variant == 3    # only 16-cell tiles fit
     assert bz.Modes(bz.Grid(3, 16, 10.0), 1.0).modesum_variant == 4    # 8-cell tiles, 3-D rows
-    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant in (1, 2, 3, 5)   # 16-wide blocks overhang a 7-mode row
+    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7)   # 16-wide blocks overhang a 7-mode row
     assert bz.Modes(bz.Grid(2, 64, 10.0), 1.0).modesum_variant == 0
 
 
-@pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3, 5)]
-                         + [(2, 16, 4), (3, 8, 1), (3, 8, 2), (3, 8, 3), (3, 8, 5)])
+@pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3, 5, 6, 7)]
+                         + [(2, 16, 4), (3, 8, 1), (3, 8, 2), (3, 8, 3), (3, 8, 5), (3, 8, 6), (3, 8, 7)])
 def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, dim, N, variant):
     """Every register-blocked variant (fixed through BZ_MODESUM_VARIANT, bypassing
     the autotuner) against the oracle: 70 cells = 2 full tiles and a ragged tail."""
@@ -102,20 +102,22 @@ def test_last_wave_split_is_exact(bz, monkeypatch, extra):
     """With a timed 32-cell variant, whole waves of CTAs run one tile each and
     the tiles of the last partial wave are split over 8, 4 or 2 CTAs (3, 31,
     50 extra tiles) or, beyond half the SMs (100 extra tiles), run on the
-    16-cell variant: every cell must equal a run of a fixed variant (cells are
-    independent and every variant performs the same operations per output)."""
+    16-cell variant when that one sums every output in the same order (the
+    scalar one-cell-per-lane variants), else as a plain partial wave: every
+    cell must equal a run of a fixed variant (cells are independent)."""
     import torch
     N, L = 32, 10.0
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     n = sms * 32 + extra
     f = workloads.bi_maxwellian(n, 2, N, L, seed=1500)
     m = bz.Modes(bz.Grid(2, N, L), 1.0)
-    if m.modesum_variant not in (1, 2, 5):
+    if m.modesum_variant not in (1, 2, 5, 6, 7):
         pytest.skip("timed variant is not a 32-cell one")
     Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32").cpu().numpy()
     monkeypatch.setenv("BZ_MODESUM_VARIANT", str(m.modesum_variant))
     m_main = bz.Modes(bz.Grid(2, N, L), 1.0)
-    monkeypatch.setenv("BZ_MODESUM_VARIANT", "3")
+    own_class = m.modesum_variant in (5, 6, 7)       # packed forms: the tail stays on them
+    monkeypatch.setenv("BZ_MODESUM_VARIANT", str(m.modesum_variant) if own_class else "3")
     m_tail = bz.Modes(bz.Grid(2, N, L), 1.0)
     Qa = bz.collide_batch(m_main, to_dev(f[:sms * 32], "fp32"), precision="fp32").cpu().numpy()
     Qb = bz.collide_batch(m_tail, to_dev(f[sms * 32:], "fp32"), precision="fp32").cpu().numpy()
