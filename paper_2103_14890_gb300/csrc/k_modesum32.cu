@@ -265,7 +265,7 @@ __device__ __forceinline__ void stage_spectrum(uint4 *smem16, const V2 *fhat, in
 
 // Task flags (TaskRec.flags)
 constexpr int kTaskRamp = 1;     // first block is the ramp (l2lo = k2_0 - h - 1)
-constexpr int kTaskRefl = 2;     // runs on the reflected spectrum; stores output k_2 at column -k_2
+constexpr int kTaskRefl = 2;     // reflected block: on the reflected spectrum (restaged, or read mirrored); output k_2 at column -k_2
 constexpr int kTaskConj = 4;     // k_1 = 0 row: also stores conj(Q-hat) at (row crow, column -k_2), k_2 > 0
 
 // The task table: 2 W + 1 offsets (W = warps x split), then the records.
@@ -601,12 +601,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_p2_kernel(const Mode32G
 // four rows as (P_x - Q_y, P_y + Q_x); the sums differ in rounding from the
 // scalar kernels', so the last partial wave of a batch stays on this kernel.
 template <int RR, int WS, int PH, bool RAMP>
-__device__ __forceinline__ void block_pq(float2 (&win)[2 * RR], const float2 *__restrict__ mp,
+__device__ __forceinline__ void block_pq(float2 (&win)[2 * RR], const float2 *__restrict__ mp, int mcs,
                                          const float2 *__restrict__ lp, int dcs, float sgn,
                                          const float *__restrict__ wb, float2 (&P)[RR], float2 (&Q)[RR]) {
-    constexpr int CS = 32;
 #pragma unroll
-    for (int j = 0; j < (RAMP ? RR - 1 : RR); ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * CS];
+    for (int j = 0; j < (RAMP ? RR - 1 : RR); ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * mcs];
 #pragma unroll
     for (int s = RAMP ? 1 : 0; s < RR; ++s) {
         const float2 fl = lp[s * dcs];
@@ -630,34 +629,38 @@ __device__ __forceinline__ void block_pq(float2 (&win)[2 * RR], const float2 *__
 }
 
 // One row pair (as row_pass): the ramp block under the PH 1 naming, or the
-// preload, then pairs of blocks (PH 0, PH 1) and a last PH 0.
+// preload, then pairs of blocks (PH 0, PH 1) and a last PH 0.  mirror: the
+// task of a reflected output block, read from the unreflected spectrum: every
+// column index is negated, so f-hat_l and the window run the other way.
 template <int RR, int WS>
 __device__ __forceinline__ void row_pass_pq(const float2 *__restrict__ rowl, const float2 *__restrict__ rowm,
                                             const float *__restrict__ wrow, int nblk, int l2lo, int mbase0,
-                                            int dir, bool ramp, float2 (&P)[RR], float2 (&Q)[RR]) {
+                                            int dir, bool ramp, bool mirror, float2 (&P)[RR], float2 (&Q)[RR]) {
     constexpr int CS = 32;
     float2 win[2 * RR];
-    const int dcs = dir * CS;
+    const int dcs = (mirror ? -dir : dir) * CS;          // between consecutive l_2
+    const int mcs = mirror ? -CS : CS;                   // between consecutive window columns
     const float sgn = (float)dir;
-    const float2 *mp = rowm + mbase0 * CS;
+    const float2 *mp = rowm + mbase0 * mcs;
     const float2 *lp = rowl + l2lo * dcs;
     int blk = 0;
     if (ramp) {
-        block_pq<RR, WS, 1, true>(win, mp, lp, dcs, sgn, wrow, P, Q);
-        mp -= RR * CS;
+        block_pq<RR, WS, 1, true>(win, mp, mcs, lp, dcs, sgn, wrow, P, Q);
+        mp -= RR * mcs;
         lp += RR * dcs;
         blk = 1;
     } else {
 #pragma unroll
-        for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * CS];
+        for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * mcs];
     }
     for (; blk + 1 < nblk; blk += 2) {
-        block_pq<RR, WS, 0, false>(win, mp, lp, dcs, sgn, wrow + blk * RR * WS, P, Q);
-        block_pq<RR, WS, 1, false>(win, mp - RR * CS, lp + RR * dcs, dcs, sgn, wrow + (blk + 1) * RR * WS, P, Q);
-        mp -= 2 * RR * CS;
+        block_pq<RR, WS, 0, false>(win, mp, mcs, lp, dcs, sgn, wrow + blk * RR * WS, P, Q);
+        block_pq<RR, WS, 1, false>(win, mp - RR * mcs, mcs, lp + RR * dcs, dcs, sgn, wrow + (blk + 1) * RR * WS, P,
+                                   Q);
+        mp -= 2 * RR * mcs;
         lp += 2 * RR * dcs;
     }
-    if (blk < nblk) block_pq<RR, WS, 0, false>(win, mp, lp, dcs, sgn, wrow + blk * RR * WS, P, Q);
+    if (blk < nblk) block_pq<RR, WS, 0, false>(win, mp, mcs, lp, dcs, sgn, wrow + blk * RR * WS, P, Q);
 }
 
 template <int RR, int WARPS>
@@ -684,35 +687,17 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_pq_kernel(const Mode32G
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
     float *wbuf1 = wbuf0 + wrow_max;
-    const int NW = WARPS * ip.split;
+    const int NW = WARPS * ip.split;                 // one phase: every task reads this spectrum
     int t = tasks[part * WARPS + warp], tend = tasks[part * WARPS + warp + 1];
-    bool phase1 = false;
     const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + 2 * NW + 1);
     const float2 *F0 = Fs + (size_t)(kPad + h) * CELLS + lane;
     const bool valid = tile * 32 + lane < ip.n;
     float2 *const qt = Qhat + tile * (int64_t)nhalf * 32 + lane;
 
-    for (;;) {
-        if (t >= tend) {
-            if (phase1) break;
-            const Mode32Item &iq = gd.item[it];
-            const int *tq = iq.tasks;
-            const int nw = WARPS * iq.split;
-            if (tq[2 * nw] == tq[nw]) break;
-            __syncthreads();
-            const int64_t c1 = (int64_t)blockIdx.x - gd.tile_start[it];
-            stage_spectrum<float2, CELLS>(smem16, static_cast<const float2 *>(iq.fhat), c1 / iq.split, 0, iq.nhalf,
-                                          iq.M, true);
-            __syncthreads();
-            const int w1 = (int)(c1 % iq.split) * WARPS + (int)(threadIdx.x >> 5);
-            t = tq[nw + w1];
-            tend = tq[nw + w1 + 1];
-            phase1 = true;
-            continue;
-        }
+    for (; t < tend;) {
         const TaskRec tk = trec[t++];
         const int rowf = tk.rowf;
-        const bool ramp = (tk.flags & kTaskRamp) != 0;
+        const bool ramp = (tk.flags & kTaskRamp) != 0, mirror = (tk.flags & kTaskRefl) != 0;
         const float *wsrc = W + tk.woff;
         float2 hi[RR], lo[RR], P[RR], Q[RR];
 #pragma unroll
@@ -730,7 +715,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_pq_kernel(const Mode32G
             __syncwarp();
             const int4 hd = *reinterpret_cast<const int4 *>(wcur);
             row_pass_pq<RR, WS>(F0 + hd.x, F0 + hd.y, wcur + HEAD, tk.nblk, tk.l2lo, mbase0, hd.z > 0 ? 1 : -1, ramp,
-                                P, Q);
+                                mirror, P, Q);
             __syncwarp();
             if ((i & 3) == 3 || i + 1 == tk.nrows) {
 #pragma unroll
@@ -1169,7 +1154,7 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                     tr.rfirst = (k20 == 0) ? 1 : 0;      // k_2 = 0 is the unreflected task's
                     tasks.push_back(tr);
                     cost.push_back(c);
-                    phase.push_back(1);
+                    phase.push_back(kVariants[v].pq ? 0 : 1);   // the FP32x2 kernel reads it mirrored
                 }
             }
         }
