@@ -244,14 +244,19 @@ int imex_step(const bz_modes *m, int scheme, int model, double dt, double eps,
 
 /* group_collide -- one collision evaluation for several independent instances
  * (each its own grid N / dimension / kernel and cell batch) in one call.  The
- * forward DFTs run per instance; the FP32 mode sums of all instances served by
- * the register-blocked kernel (2-D N <= 48, 3-D N <= 16) share one launch per
- * kernel variant (up to 16 instances per launch), scheduled longest-first by
- * per-cell work; other instances (and the FP64 form) use one launch each; then
- * the inverse DFTs.  Results equal collide_batch on each instance.
+ * FP32 mode sums of all instances served by the register-blocked kernel
+ * (2-D N <= 48, 3-D N <= 16) share one launch per kernel variant (up to 16
+ * instances per launch, longest first by per-cell work); other instances
+ * (and the FP64 and FP32X2 forms) use one launch each.  The instances of one
+ * variant, with their forward and inverse DFTs, form a lane; the lanes run on
+ * up to four library-owned streams forked from `stream` (longest lane first)
+ * and joined back to it, so that one lane's partial waves overlap the others'
+ * work.  The call is asynchronous on `stream` like collide_batch: the results
+ * are complete once `stream` has completed.  Results equal collide_batch on
+ * each instance.
  *   items     : n_items descriptors; item.modes must belong to the current
  *               device; item.f / item.Q are device arrays [n_cells][N^d]
- *   precision : BZ_FP32 or BZ_FP64 (all items alike)
+ *   precision : BZ_FP32, BZ_FP32X2 or BZ_FP64 (all items alike)
  *   flags     : BZ_CONSERVE | BZ_CHECK_INPUT, applied to every item
  * Errors: as collide_batch. */
 typedef struct bz_group_item {

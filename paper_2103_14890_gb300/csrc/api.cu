@@ -606,6 +606,24 @@ int copy_streams(int dev, cudaStream_t out[2]) {
     return BZ_OK;
 }
 
+// Streams of group_collide's lanes per device (non-blocking, created on first use).
+constexpr int kGroupStreams = 4;
+cudaStream_t g_group_streams[kMaxDevices][kGroupStreams];
+bool g_group_ok[kMaxDevices];
+
+int group_streams(int dev, cudaStream_t out[kGroupStreams]) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_group_ok[dev]) {
+        for (int i = 0; i < kGroupStreams; ++i) {
+            cudaError_t e = cudaStreamCreateWithFlags(&g_group_streams[dev][i], cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "group_collide: stream");
+        }
+        g_group_ok[dev] = true;
+    }
+    for (int i = 0; i < kGroupStreams; ++i) out[i] = g_group_streams[dev][i];
+    return BZ_OK;
+}
+
 // Cells per pipeline stage of collide_batch_host: one wave of 32-cell CTAs of
 // the mode-sum kernel (one per SM), so that no chunk leaves SMs idle at its end.
 int64_t host_chunk_cells(int dev) {
@@ -993,57 +1011,118 @@ int group_collide(const bz_group_item *items, int n_items, int precision, int fl
         return base + off[q] + spectrum_bytes(items[order[q]].modes, precision, items[order[q]].n_cells);
     };
     int rc;
-    for (size_t q = 0; q < order.size(); ++q) {
-        const bz_group_item &it = items[order[q]];
-        if (flags & BZ_CHECK_INPUT) {
+    if (flags & BZ_CHECK_INPUT) {
+        for (size_t q = 0; q < order.size(); ++q) {
+            const bz_group_item &it = items[order[q]];
             rc = check_input(precision, it.f, it.n_cells * it.modes->g->v.nv, st);
             if (rc) return rc;
         }
-        rc = phase_forward(it.modes, precision, it.f, fh_of(q), it.n_cells, st);
-        if (rc) return rc;
     }
-    // one launch of the register-blocked kernel for up to kMaxGroup FP32 2-D
-    // instances at a time; the others run the generic kernel one by one
-    std::vector<const bz_modes *> gm;
-    std::vector<const float2 *> gf;
-    std::vector<float2 *> gq;
-    std::vector<int64_t> gn;
-    auto flush = [&]() -> int {
-        if (gm.empty()) return BZ_OK;
-        BZ_LAUNCH("modesum_f32_group", st,
-                  launch_modesum32_group(gm.data(), gf.data(), gq.data(), gn.data(), (int)gm.size(), st),
-                  "group_collide: grouped mode sum");
-        gm.clear();
-        gf.clear();
-        gq.clear();
-        gn.clear();
+    // Lanes: the FP32 instances on one register-blocked variant form one lane
+    // (one grouped mode-sum launch for up to kMaxGroup of them); every other
+    // instance is a lane of its own.  Each lane runs its forward transforms,
+    // mode sum and inverse transforms in order on one of the library's group
+    // streams, forked from the caller's stream and joined back to it, so that
+    // the last partial wave of one lane's launches overlaps the others' work.
+    struct Lane {
+        std::vector<size_t> qs;
+        double work = 0.0;
+        bool grouped = false;
+    };
+    std::vector<Lane> lanes;
+    std::vector<int> lane_of_var(kModesumVariants, -1);
+    for (size_t q = 0; q < order.size(); ++q) {
+        const bz_group_item &it = items[order[q]];
+        const double w = (double)it.modes->pairs_sym * (double)it.n_cells;
+        if (precision == BZ_FP32 && modesum32_available(it.modes)) {
+            int &l = lane_of_var[it.modes->variant];
+            if (l < 0) {
+                l = (int)lanes.size();
+                lanes.emplace_back();
+                lanes.back().grouped = true;
+            }
+            lanes[l].qs.push_back(q);
+            lanes[l].work += w;
+        } else {
+            lanes.emplace_back();
+            lanes.back().qs.push_back(q);
+            lanes.back().work = w;
+        }
+    }
+    auto run_lane = [&](const Lane &ln, cudaStream_t ls) -> int {
+        int r;
+        for (size_t q : ln.qs) {
+            const bz_group_item &it = items[order[q]];
+            if ((r = phase_forward(it.modes, precision, it.f, fh_of(q), it.n_cells, ls))) return r;
+        }
+        if (ln.grouped) {
+            for (size_t a = 0; a < ln.qs.size(); a += kMaxGroup) {
+                std::vector<const bz_modes *> gm;
+                std::vector<const float2 *> gf;
+                std::vector<float2 *> gq;
+                std::vector<int64_t> gn;
+                for (size_t b = a; b < ln.qs.size() && b < a + kMaxGroup; ++b) {
+                    const bz_group_item &it = items[order[ln.qs[b]]];
+                    gm.push_back(it.modes);
+                    gf.push_back(reinterpret_cast<const float2 *>(fh_of(ln.qs[b])));
+                    gq.push_back(reinterpret_cast<float2 *>(qh_of(ln.qs[b])));
+                    gn.push_back(it.n_cells);
+                }
+                BZ_LAUNCH("modesum_f32_group", ls,
+                          launch_modesum32_group(gm.data(), gf.data(), gq.data(), gn.data(), (int)gm.size(), ls),
+                          "group_collide: grouped mode sum");
+            }
+        } else {
+            const bz_group_item &it = items[order[ln.qs[0]]];
+            if ((r = phase_modesum(it.modes, precision, fh_of(ln.qs[0]), qh_of(ln.qs[0]), it.n_cells, ls))) return r;
+        }
+        for (size_t q : ln.qs) {
+            const bz_group_item &it = items[order[q]];
+            if ((r = phase_inverse(it.modes, precision, flags, qh_of(q), it.Q, nullptr, it.n_cells, ls))) return r;
+        }
         return BZ_OK;
     };
-    // one grouped launch per kernel variant (items keep the longest-first order)
-    for (int var = 0; var < kModesumVariants; ++var) {
-        for (size_t q = 0; q < order.size(); ++q) {
-            const bz_group_item &it = items[order[q]];
-            if (precision != BZ_FP32 || !modesum32_available(it.modes) || it.modes->variant != var) continue;
-            gm.push_back(it.modes);
-            gf.push_back(reinterpret_cast<const float2 *>(fh_of(q)));
-            gq.push_back(reinterpret_cast<float2 *>(qh_of(q)));
-            gn.push_back(it.n_cells);
-            if ((int)gm.size() == kMaxGroup && (rc = flush())) return rc;
+    if (lanes.size() == 1) return run_lane(lanes[0], st);
+    // longest lane first onto the least loaded stream
+    cudaStream_t gs[kGroupStreams];
+    if ((rc = group_streams(dev, gs))) return rc;
+    std::vector<int> lorder(lanes.size());
+    for (size_t i = 0; i < lanes.size(); ++i) lorder[i] = (int)i;
+    std::stable_sort(lorder.begin(), lorder.end(), [&](int a, int b) { return lanes[a].work > lanes[b].work; });
+    const int K = (int)std::min<size_t>(kGroupStreams, lanes.size());
+    std::vector<double> load(K, 0.0);
+    std::vector<int> lane_stream(lanes.size(), 0);
+    for (int l : lorder) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[k] += lanes[l].work;
+        lane_stream[l] = k;
+    }
+    cudaEvent_t ev[kGroupStreams + 1] = {};
+    for (int k = 0; k <= K; ++k) {
+        cudaError_t e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (int q = 0; q < k; ++q) cudaEventDestroy(ev[q]);
+            return cuda_fail(e, "group_collide: events");
         }
-        if ((rc = flush())) return rc;
     }
-    for (size_t q = 0; q < order.size(); ++q) {
-        const bz_group_item &it = items[order[q]];
-        if (precision == BZ_FP32 && modesum32_available(it.modes)) continue;
-        rc = phase_modesum(it.modes, precision, fh_of(q), qh_of(q), it.n_cells, st);
-        if (rc) return rc;
+    // fork: every stream starts after the caller's stream (scratch allocated,
+    // inputs written); join: the caller's stream continues after all of them,
+    // also after an error part-way (the scratch returns to the pool on it)
+    rc = BZ_OK;
+    cudaError_t e = cudaEventRecord(ev[K], st);
+    for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(gs[k], ev[K], 0);
+    if (e != cudaSuccess) rc = cuda_fail(e, "group_collide: fork");
+    for (int l : lorder) {
+        if (rc) break;
+        rc = run_lane(lanes[l], gs[lane_stream[l]]);
     }
-    for (size_t q = 0; q < order.size(); ++q) {
-        const bz_group_item &it = items[order[q]];
-        rc = phase_inverse(it.modes, precision, flags, qh_of(q), it.Q, nullptr, it.n_cells, st);
-        if (rc) return rc;
+    for (int k = 0; k < K; ++k) {
+        e = cudaEventRecord(ev[k], gs[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev[k], 0);
+        if (e != cudaSuccess && !rc) rc = cuda_fail(e, "group_collide: join");
     }
-    return BZ_OK;
+    for (int k = 0; k <= K; ++k) cudaEventDestroy(ev[k]);
+    return rc;
 }
 
 int bz_check(void *stream) {

@@ -60,21 +60,23 @@ namespace {
 // CTA, cells per thread (pack: 1, or 2 for the packed two-cell kernel, whose
 // lanes hold cells c and c + 16 of a 32-cell tile in FP32x2 register pairs),
 // wdup: each weight stored twice (w, w) as an FP32x2 operand, pq: the FP32x2
-// form with one cell per lane (modesum_pq_kernel).  Variant ids reported by
-// bz_modes_info are index + 1.
+// form with one cell per lane (modesum_pq_kernel), orient: 2 when the two
+// halves of a warp hold the same cells and run each task plain and mirrored
+// (paired orientations).  Variant ids reported by bz_modes_info are index + 1.
 struct Variant {
-    int R, warps, cells, pack, wdup, pq;
+    int R, warps, cells, pack, wdup, pq, orient;
 };
 constexpr int kNumVariants = kModesumVariants;   // FP32 variants (timed by the autotuner)
-// entries 0..6: the FP32 variants; entries 7, 8: layouts of the FP64 and FP32X2
+// entries 0..7: the FP32 variants; entries 8, 9: layouts of the FP64 and FP32X2
 // forms only (2 outputs per thread, 8 warps, 8- and 4-cell tiles) for grids
 // whose 16-byte-per-value spectrum needs them (48^2, 16^3)
 constexpr Variant kVariants[kNumVariants + 2] = {
-    {8, 16, 32, 1, 0, 0}, {4, 32, 32, 1, 0, 0}, {4, 16, 16, 1, 0, 0}, {4, 16, 8, 1, 0, 0},
-    {4, 16, 32, 2, 1, 0}, {8, 12, 32, 1, 0, 1}, {8, 16, 32, 1, 0, 1}, {2, 8, 8, 1, 0, 0}, {2, 8, 4, 1, 0, 0}};
+    {8, 16, 32, 1, 0, 0, 1}, {4, 32, 32, 1, 0, 0, 1}, {4, 16, 16, 1, 0, 0, 1}, {4, 16, 8, 1, 0, 0, 1},
+    {4, 16, 32, 2, 1, 0, 1}, {8, 12, 32, 1, 0, 1, 1}, {8, 16, 32, 1, 0, 1, 1}, {8, 16, 16, 1, 0, 1, 2},
+    {2, 8, 8, 1, 0, 0, 1},   {2, 8, 4, 1, 0, 0, 1}};
 
 // lane groups splitting a task's outputs, and outputs per task (RT)
-constexpr int variant_groups(int v) { return 32 / kVariants[v].cells * kVariants[v].pack; }
+constexpr int variant_groups(int v) { return 32 / kVariants[v].cells * kVariants[v].pack / kVariants[v].orient; }
 constexpr int variant_rt(int v) { return kVariants[v].R * variant_groups(v); }
 // Whether an FP32 variant's tables compute k_2 < 0 on the reflected spectrum
 // (every output block of k_2 >= 0 fits within the row: R T <= h + 1); all
@@ -632,11 +634,10 @@ __device__ __forceinline__ void block_pq(float2 (&win)[2 * RR], const float2 *__
 // preload, then pairs of blocks (PH 0, PH 1) and a last PH 0.  mirror: the
 // task of a reflected output block, read from the unreflected spectrum: every
 // column index is negated, so f-hat_l and the window run the other way.
-template <int RR, int WS>
+template <int RR, int WS, int CS>
 __device__ __forceinline__ void row_pass_pq(const float2 *__restrict__ rowl, const float2 *__restrict__ rowm,
                                             const float *__restrict__ wrow, int nblk, int l2lo, int mbase0,
                                             int dir, bool ramp, bool mirror, float2 (&P)[RR], float2 (&Q)[RR]) {
-    constexpr int CS = 32;
     float2 win[2 * RR];
     const int dcs = (mirror ? -dir : dir) * CS;          // between consecutive l_2
     const int mcs = mirror ? -CS : CS;                   // between consecutive window columns
@@ -663,9 +664,17 @@ __device__ __forceinline__ void row_pass_pq(const float2 *__restrict__ rowl, con
     if (blk < nblk) block_pq<RR, WS, 0, false>(win, mp, mcs, lp, dcs, sgn, wrow + blk * RR * WS, P, Q);
 }
 
-template <int RR, int WARPS>
+// CELLS = 32: one cell per lane; reflected blocks are separate tasks (read
+// mirrored).  CELLS = 16 (paired orientations, for grids whose 32-cell
+// spectrum does not fit shared memory): lanes c and c + 16 hold cell c, the
+// upper half running every task mirrored, i.e. the task's reflected twin with
+// the same weights and control flow, so all lanes take the same outputs and
+// the ramp applies; the table holds no reflected tasks and k_2 = 0 is the
+// lower half's.
+template <int RR, int WARPS, int CELLS>
 __global__ void __launch_bounds__(WARPS * 32, 1) modesum_pq_kernel(const Mode32Group gd) {
-    constexpr int CELLS = 32;
+    constexpr bool PAIRED = (CELLS == 16);
+    constexpr int G = 32 / CELLS;                // CTAs per 32-cell tile
     constexpr int WS = RR;                       // floats per l_2 step
     constexpr int HEAD = kRowHeadBytes / (int)sizeof(float);
     extern __shared__ __align__(16) uint4 smem16[];
@@ -679,25 +688,29 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_pq_kernel(const Mode32G
     const int h = ip.h, M = ip.M, nhalf = ip.nhalf, wrow_max = ip.wrow_max;
     const int64_t cta0 = (int64_t)blockIdx.x - gd.tile_start[it];
     const int part = (int)(cta0 % ip.split);
-    const int64_t tile = cta0 / ip.split;
-    float2 *Fs = reinterpret_cast<float2 *>(smem16);                 // [kPad + nhalf + kPad][32]
+    const int64_t cta = cta0 / ip.split;
+    const int64_t tile = cta / G;
+    const int sub = (int)(cta % G);
+    float2 *Fs = reinterpret_cast<float2 *>(smem16);                 // [kPad + nhalf + kPad][CELLS]
     float *wsm = reinterpret_cast<float *>(Fs + (size_t)(nhalf + 2 * kPad) * CELLS);
-    stage_spectrum<float2, CELLS>(smem16, fhat, tile, 0, nhalf, M, false);
+    stage_spectrum<float2, CELLS>(smem16, fhat, tile, sub, nhalf, M, false);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cell = lane % CELLS;
+    const bool upper = PAIRED && lane >= CELLS;                      // runs every task mirrored
     float *wbuf0 = wsm + (size_t)warp * 2 * wrow_max;
     float *wbuf1 = wbuf0 + wrow_max;
     const int NW = WARPS * ip.split;                 // one phase: every task reads this spectrum
     int t = tasks[part * WARPS + warp], tend = tasks[part * WARPS + warp + 1];
     const TaskRec *trec = reinterpret_cast<const TaskRec *>(tasks + 2 * NW + 1);
-    const float2 *F0 = Fs + (size_t)(kPad + h) * CELLS + lane;
-    const bool valid = tile * 32 + lane < ip.n;
-    float2 *const qt = Qhat + tile * (int64_t)nhalf * 32 + lane;
+    const float2 *F0 = Fs + (size_t)(kPad + h) * CELLS + cell;
+    const bool valid = tile * 32 + sub * CELLS + cell < ip.n;
+    float2 *const qt = Qhat + tile * (int64_t)nhalf * 32 + sub * CELLS + cell;
 
     for (; t < tend;) {
         const TaskRec tk = trec[t++];
         const int rowf = tk.rowf;
-        const bool ramp = (tk.flags & kTaskRamp) != 0, mirror = (tk.flags & kTaskRefl) != 0;
+        const bool ramp = (tk.flags & kTaskRamp) != 0, mirror = ((tk.flags & kTaskRefl) != 0) != upper;
         const float *wsrc = W + tk.woff;
         float2 hi[RR], lo[RR], P[RR], Q[RR];
 #pragma unroll
@@ -714,8 +727,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_pq_kernel(const Mode32G
             }
             __syncwarp();
             const int4 hd = *reinterpret_cast<const int4 *>(wcur);
-            row_pass_pq<RR, WS>(F0 + hd.x, F0 + hd.y, wcur + HEAD, tk.nblk, tk.l2lo, mbase0, hd.z > 0 ? 1 : -1, ramp,
-                                mirror, P, Q);
+            row_pass_pq<RR, WS, CELLS>(F0 + hd.x, F0 + hd.y, wcur + HEAD, tk.nblk, tk.l2lo, mbase0,
+                                       hd.z > 0 ? 1 : -1, ramp, mirror, P, Q);
             __syncwarp();
             if ((i & 3) == 3 || i + 1 == tk.nrows) {
 #pragma unroll
@@ -735,11 +748,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_pq_kernel(const Mode32G
             const volatile TaskRec *tv = trec + (t - 1);
             const int orow = tv->orow, rfirst = tv->rfirst, flags = tv->flags, crow = tv->crow, k20 = tv->k20;
             float2 *out = qt + (int64_t)orow * M * 32;
-            const bool refl = (flags & kTaskRefl) != 0, cj = (flags & kTaskConj) != 0;
+            const bool refl = ((flags & kTaskRefl) != 0) != upper, cj = (flags & kTaskConj) != 0;
 #pragma unroll
             for (int r = 0; r < RR; ++r) {
                 const int k2 = k20 + r;
-                if (r >= rfirst && k2 <= h) {
+                if (r >= rfirst && k2 <= h && !(upper && k2 == 0)) {
                     const float2 q = make_float2(hi[r].x + lo[r].x, hi[r].y + lo[r].y);
                     out[(refl ? h - k2 : k2 + h) * 32] = q;
                     if (cj && k2 > 0) qt[((int64_t)crow * M + h - k2) * 32] = make_float2(q.x, -q.y);
@@ -1025,9 +1038,10 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
     // last axis (beta-hat is invariant under that reflection); ramped: with
     // one lane group and R dividing h + 1, every task starts with the ramp
     // block and no step is padding
-    const int G = 32 / kVariants[v].cells;
+    const int G = variant_groups(v);
     const bool reflect = sizeof(T) == 4 && variant_reflects(v, h);
     const bool ramped = reflect && G == 1 && (h + 1) % R == 0;
+    const bool twins = reflect && kVariants[v].orient == 1;   // paired orientations need no reflected tasks
     const int nmid = (d == 3) ? M : 1;                      // values of the middle index (3-D)
     struct Pair { int l[2], m[2]; };                         // leading indices of l and m
     for (int k1 = 0; k1 <= h; ++k1) {
@@ -1094,7 +1108,7 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                 t.woff = (int)W.size();
                 t.rfirst = reflect ? 0 : std::max(0, prev_end + 1 - k20);
                 t.rowf = HEAD + npad * R * (kVariants[v].wdup ? 2 : 1);
-                t.flags = (ramped ? kTaskRamp : 0) | (reflect && k1 == 0 ? kTaskConj : 0);
+                t.flags = (ramped ? kTaskRamp : 0) | (twins && k1 == 0 ? kTaskConj : 0);
                 t.crow = (d == 3) ? (M - 1 - i2) : 0;        // k_1 = 0: row of -k (middle index -k_2)
                 t.pad2 = t.pad3 = 0;
                 prev_end = k2last;
@@ -1148,7 +1162,7 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
                 tasks.push_back(t);
                 cost.push_back(c);
                 phase.push_back(0);
-                if (reflect && k1 > 0) {
+                if (twins && k1 > 0) {
                     TaskRec tr = t;                      // the same weights on the reflected spectrum
                     tr.flags = (t.flags & kTaskRamp) | kTaskRefl;
                     tr.rfirst = (k20 == 0) ? 1 : 0;      // k_2 = 0 is the unreflected task's
@@ -1244,12 +1258,12 @@ static cudaError_t launch_instance(const Mode32Group &gd, size_t sm, cudaStream_
     return cudaGetLastError();
 }
 
-template <int RR, int WARPS>
+template <int RR, int WARPS, int CELLS>
 static cudaError_t launch_pq(const Mode32Group &gd, size_t sm, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(modesum_pq_kernel<RR, WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(modesum_pq_kernel<RR, WARPS, CELLS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    modesum_pq_kernel<RR, WARPS><<<(unsigned)gd.tile_start[gd.nitems], WARPS * 32, sm, st>>>(gd);
+    modesum_pq_kernel<RR, WARPS, CELLS><<<(unsigned)gd.tile_start[gd.nitems], WARPS * 32, sm, st>>>(gd);
     return cudaGetLastError();
 }
 
@@ -1266,8 +1280,9 @@ static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStr
             modesum_p2_kernel<4, 16><<<(unsigned)gd.tile_start[gd.nitems], 16 * 32, sm, st>>>(gd);
             return cudaGetLastError();
         }
-        case 5: return launch_pq<8, 12>(gd, sm, st);
-        case 6: return launch_pq<8, 16>(gd, sm, st);
+        case 5: return launch_pq<8, 12, 32>(gd, sm, st);
+        case 6: return launch_pq<8, 16, 32>(gd, sm, st);
+        case 7: return launch_pq<8, 16, 16>(gd, sm, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1307,9 +1322,9 @@ static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, 
 
 // FP64 form: the same kernel on double spectra and weights, on 16-cell tiles
 // (variant entry 2) or, where the double spectrum of 16 cells does not fit
-// shared memory, on 8- or 4-cell tiles (entries 7, 8: 48^2, 16^3); no
+// shared memory, on 8- or 4-cell tiles (entries 8, 9: 48^2, 16^3); no
 // last-wave split.  The FP32X2 form runs on the same layout.
-constexpr int kFp64Variants[3] = {2, 7, 8};
+constexpr int kFp64Variants[3] = {2, 8, 9};
 
 bool modesum64_available(const bz_modes *m) { return m->w64 != nullptr; }
 

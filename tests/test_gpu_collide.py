@@ -70,15 +70,16 @@ def test_fast_kernels_selected(bz):
     and the 3-D grids up to 16^3 (a silent fall back to the generic kernel would
     hide a table-building bug)."""
     for N in (16, 24, 32):
-        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7), N
-    assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_variant == 3    # only 16-cell tiles fit
+        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7, 8), N
+    assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_variant in (3, 8)    # only 16-cell tiles fit
     assert bz.Modes(bz.Grid(3, 16, 10.0), 1.0).modesum_variant == 4    # 8-cell tiles, 3-D rows
-    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7)   # 16-wide blocks overhang a 7-mode row
+    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7, 8)   # 16-wide blocks overhang a 7-mode row
     assert bz.Modes(bz.Grid(2, 64, 10.0), 1.0).modesum_variant == 0
 
 
-@pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3, 5, 6, 7)]
-                         + [(2, 16, 4), (3, 8, 1), (3, 8, 2), (3, 8, 3), (3, 8, 5), (3, 8, 6), (3, 8, 7)])
+@pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3, 5, 6, 7, 8)]
+                         + [(2, 16, 4), (3, 8, 1), (3, 8, 2), (3, 8, 3), (3, 8, 5), (3, 8, 6), (3, 8, 7), (3, 8, 8),
+                            (2, 48, 3), (2, 48, 8)])
 def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, dim, N, variant):
     """Every register-blocked variant (fixed through BZ_MODESUM_VARIANT, bypassing
     the autotuner) against the oracle: 70 cells = 2 full tiles and a ragged tail."""
@@ -111,12 +112,12 @@ def test_last_wave_split_is_exact(bz, monkeypatch, extra):
     n = sms * 32 + extra
     f = workloads.bi_maxwellian(n, 2, N, L, seed=1500)
     m = bz.Modes(bz.Grid(2, N, L), 1.0)
-    if m.modesum_variant not in (1, 2, 5, 6, 7):
+    if m.modesum_variant not in (1, 2, 5, 6, 7):     # 32-cell variants
         pytest.skip("timed variant is not a 32-cell one")
     Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32").cpu().numpy()
     monkeypatch.setenv("BZ_MODESUM_VARIANT", str(m.modesum_variant))
     m_main = bz.Modes(bz.Grid(2, N, L), 1.0)
-    own_class = m.modesum_variant in (5, 6, 7)       # packed forms: the tail stays on them
+    own_class = m.modesum_variant in (5, 6, 7, 8)    # packed forms: the tail stays on them
     monkeypatch.setenv("BZ_MODESUM_VARIANT", str(m.modesum_variant) if own_class else "3")
     m_tail = bz.Modes(bz.Grid(2, N, L), 1.0)
     Qa = bz.collide_batch(m_main, to_dev(f[:sms * 32], "fp32"), precision="fp32").cpu().numpy()
@@ -146,11 +147,12 @@ def test_fp32_3d_16_grid_8_cell_tiles(bz, oracle_k, n):
 
 @pytest.mark.parametrize("n", [1, 16, 17, 45])
 def test_fp32_48_grid_16_cell_tiles(bz, oracle_k, n):
-    """48^2 grid on [-10,10]^2 (16-cell tiles): single cell, exactly one CTA,
-    one past it, and a ragged 32-cell tile pair, against the oracle."""
+    """48^2 grid on [-10,10]^2 (16-cell tiles, the timed variant): single cell,
+    exactly one CTA, one past it, and a ragged 32-cell tile pair, against the
+    oracle."""
     N, L = 48, 10.0
     m = bz.Modes(bz.Grid(2, N, L), 1.0)
-    assert m.modesum_variant == 3
+    assert m.modesum_variant in (3, 8)
     f = workloads.bi_maxwellian(n, 2, N, L, seed=1200 + n)
     fin = as_input(f, "fp32")
     Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32")
