@@ -20,6 +20,15 @@ template <typename V> __device__ __forceinline__ V tw32(int k);
 template <> __device__ __forceinline__ float2 tw32<float2>(int k) { return c_w32[k]; }
 template <> __device__ __forceinline__ double2 tw32<double2>(int k) { return c_w32d[k]; }
 
+// Complex sums and differences: one FP32x2 instruction for float2 (two IEEE
+// FP32 additions, the results of the scalar form), two scalar ones otherwise.
+template <typename V> __device__ __forceinline__ V c_add(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V c_sub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+template <> __device__ __forceinline__ float2 c_add<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 c_sub<float2>(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+
 constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 constexpr int bitrev(int i, int bits) {
     int r = 0;
@@ -52,8 +61,8 @@ __device__ __forceinline__ void fft_dit(V (&a)[L]) {
                     t = cmk<V2>(b.x * w.x - b.y * wy, b.x * wy + b.y * w.x);
                 }
                 const V2 u = a[g + j];
-                a[g + j] = cmk<V2>(u.x + t.x, u.y + t.y);
-                a[g + j + m] = cmk<V2>(u.x - t.x, u.y - t.y);
+                a[g + j] = c_add(u, t);
+                a[g + j + m] = c_sub(u, t);
             }
         }
     }
@@ -106,12 +115,12 @@ __device__ __forceinline__ void fft_nat(V (&a)[L]) {
 #pragma unroll
         for (int n2 = 0; n2 < Q; ++n2) {
             const V2 p = a[n2], q = a[Q + n2], r = a[2 * Q + n2];
-            const S sx = q.x + r.x, sy = q.y + r.y, dx = q.x - r.x, dy = q.y - r.y;
-            y0[n2] = cmk<V2>(p.x + sx, p.y + sy);
-            const S mx = p.x - (S)0.5 * sx, my = p.y - (S)0.5 * sy;
+            const V2 sq = c_add(q, r), dq = c_sub(q, r);
+            y0[n2] = c_add(p, sq);
+            const V2 mq = cmk<V2>(p.x - (S)0.5 * sq.x, p.y - (S)0.5 * sq.y);
             // -i (sqrt3/2) d for the forward transform, +i (sqrt3/2) d for the inverse
-            const S ix = SIGN < 0 ? kS3 * dy : -kS3 * dy, iy = SIGN < 0 ? -kS3 * dx : kS3 * dx;
-            V2 u1 = cmk<V2>(mx + ix, my + iy), u2 = cmk<V2>(mx - ix, my - iy);
+            const V2 iq = SIGN < 0 ? cmk<V2>(kS3 * dq.y, -kS3 * dq.x) : cmk<V2>(-kS3 * dq.y, kS3 * dq.x);
+            V2 u1 = c_add(mq, iq), u2 = c_sub(mq, iq);
             if (n2 > 0) {
                 const V w1 = twl<L, V>(n2), w2 = twl<L, V>(2 * n2);
                 const S w1y = SIGN < 0 ? w1.y : -w1.y, w2y = SIGN < 0 ? w2.y : -w2.y;

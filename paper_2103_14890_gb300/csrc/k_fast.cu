@@ -23,8 +23,8 @@
 // pass B, one thread per (cell, j2) transforms Y along k1 and accumulates the
 // product into g (shared; each thread owns its column of g for the whole
 // call).  Then pass C (thread per (cell, j2)) transforms g along j1 for
-// k1 = 0..h, and pass D (thread per (cell, k1)) along j2, scales by P^-2 and
-// stores Q-hat.  Every shared-memory array keeps the cell index fastest, so
+// k1 = 0..h, and pass D (three threads per (cell, k1), one per residue class
+// of the output index) along j2, scales by P^-2 and stores Q-hat.  Every shared-memory array keeps the cell index fastest, so
 // consecutive threads touch consecutive words.
 //
 // Two other organisations were measured on a GB300 and were slower at A = 8
@@ -64,11 +64,21 @@ template <typename T, int N> struct FastShape {
     static constexpr int nY = nYa > nYb ? nYa : nYb;           // complex
     static constexpr int nF = (H + 1) * M * C;                 // complex
     static constexpr int nG = P * P * C;                       // real
+    static constexpr int nCF = (H + 1) * M;                    // complex: one direction's rows k1 >= 0
 };
 
 template <typename T, int N> constexpr size_t fast_smem() {
     using Sh = FastShape<T, N>;
-    return 2 * sizeof(T) * (size_t)(Sh::nY + Sh::nF) + sizeof(T) * (size_t)Sh::nG;
+    return 2 * sizeof(T) * (size_t)(Sh::nY + Sh::nF + Sh::nCF) + sizeof(T) * (size_t)Sh::nG;
+}
+
+// Asynchronous copy of one 8- or 16-byte value into shared memory.
+template <int BYTES> __device__ __forceinline__ void cp_async_val(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
 }
 
 template <typename T, int N>
@@ -83,42 +93,55 @@ fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>:
     V2 *Y = reinterpret_cast<V2 *>(smem_raw);     // pass A/B: [P][M][C]; pass C/D: [H+1][TS]
     V2 *F = Y + Sh::nY;                           // half spectrum [H+1][M][C]
     S *G = reinterpret_cast<S *>(F + Sh::nF);     // products [P][P][C]
+    V2 *CF = reinterpret_cast<V2 *>(G + Sh::nG);  // direction factors of one direction, rows k1 = 0..H
     const int tid = threadIdx.x;
     const int64_t cell0 = (int64_t)blockIdx.x * C;
-
+    // the factors are even in k, so rows k1 >= 0 serve every row; each
+    // direction's are copied in while the previous direction's pass B runs
+    auto stage_cf = [&](int p) {
+        const V2 *src = coef + ((size_t)p * M + H) * M;
+        for (int i = tid; i < Sh::nCF; i += Sh::NT) cp_async_val<(int)sizeof(V2)>(CF + i, src + i);
+    };
+    stage_cf(0);
     for (int i = tid; i < Sh::nF; i += Sh::NT) {
         const int c = i % C, mode = i / C;
         const int64_t cell = cell0 + c;
         F[i] = cell < n ? fh[tiled_index(cell, mode, nhalf)] : cmk<V2>((S)0., (S)0.);
     }
+    cp_async_commit_wait_all();
     __syncthreads();
 
     const int c = tid % C, col = tid / C;
     for (int p = 0; p <= nconv; ++p) {            // p == nconv: the loss term
         // pass A: (cell c, row k1): along k2, sum_k2 w(k) f-hat(k) e^{+2 pi i j2 k2 / P}
         if (tid < C * M) {
-            const int k1 = col - H;
-            const V2 *crow = coef + ((size_t)p * M + (k1 + H)) * M;
+            const int k1 = col - H, a1 = k1 > 0 ? k1 : -k1;
+            const V2 *frow = F + (a1 * M + H) * C + c;    // row |k1| at column 0
+            const V2 *crow = CF + a1 * M + H;
             V2 a[P];
 #pragma unroll
             for (int j = 0; j < P; ++j) a[j] = cmk<V2>((S)0., (S)0.);
+            if (k1 > 0) {
 #pragma unroll
-            for (int k2 = -H; k2 <= H; ++k2) {
-                V2 fv;
-                if (k1 >= 0) {
-                    fv = F[(k1 * M + k2 + H) * C + c];
-                } else {                          // f-hat(k) = conj f-hat(-k)
-                    const V2 t = F[(-k1 * M - k2 + H) * C + c];
-                    fv = cmk<V2>(t.x, -t.y);
+                for (int k2 = -H; k2 <= H; ++k2) {
+                    const V2 fv = frow[k2 * C], w = crow[k2];
+                    a[(k2 + P) % P] = cmk<V2>(w.x * fv.x - w.y * fv.y, w.x * fv.y + w.y * fv.x);
                 }
-                const V2 w = __ldg(crow + k2 + H);
-                a[(k2 + P) % P] = cmk<V2>(w.x * fv.x - w.y * fv.y, w.x * fv.y + w.y * fv.x);
+            } else {
+                // f-hat(k) = conj f-hat(-k) and w(k) = w(-k): row -k1 read backwards
+#pragma unroll
+                for (int k2 = -H; k2 <= H; ++k2) {
+                    const V2 t = frow[-k2 * C], w = crow[-k2];
+                    const V2 fv = cmk<V2>(t.x, -t.y);
+                    a[(k2 + P) % P] = cmk<V2>(w.x * fv.x - w.y * fv.y, w.x * fv.y + w.y * fv.x);
+                }
             }
             fft_nat<P, +1>(a);
 #pragma unroll
             for (int j2 = 0; j2 < P; ++j2) Y[(j2 * M + k1 + H) * C + c] = a[j2];
         }
         __syncthreads();
+        if (p < nconv) stage_cf(p + 1);           // pass A is done with this direction's factors
         // pass B: (cell c, column j2): along k1, then g += Re * Im (gain) or -= (loss)
         {
             const int j2 = col;
@@ -140,6 +163,7 @@ fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>:
                 for (int j1 = 0; j1 < P; ++j1) g[j1 * P * C] = fma(-b[j1].x, b[j1].y, g[j1 * P * C]);
             }
         }
+        cp_async_commit_wait_all();
         __syncthreads();
     }
 
@@ -164,20 +188,54 @@ fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>:
         }
     }
     __syncthreads();
-    // pass D: (cell c, row k1 >= 0): along j2, keep k2 in [-h, h], scale P^-2
-    if (tid < C * (H + 1)) {
-        const int k1 = col;
-        V2 a[P];
+    // pass D: (cell, row k1 >= 0, residue r): the length-P transform along j2,
+    // keep k2 in [-h, h], scale P^-2.  P = 3Q, split over three threads by the
+    // residue r of the output index (3 k' + r): thread r forms the r-th output
+    // of the 3-point DFTs over (n, n + Q, n + 2Q) times the twiddle of its
+    // class and finishes with one Q-point transform (the first stage of the
+    // mixed-radix fft_nat, spread over three threads instead of one).
+    {
+        static_assert(P % 3 == 0, "pass D splits P = 3Q");
+        constexpr int Q = P / 3, ROWS = C * (H + 1);
+        static_assert(3 * ROWS <= Sh::NT, "three threads per output row");
+        if (tid < 3 * ROWS) {
+            const int r = tid / ROWS, rest = tid % ROWS;
+            const int cd = rest % C, k1 = rest / C;
+            const V2 *yr = Y + k1 * TS + cd;
+            constexpr S kS3 = (S)0.866025403784438647;   // sqrt(3) / 2
+            V2 y[Q];
 #pragma unroll
-        for (int j2 = 0; j2 < P; ++j2) a[j2] = Y[k1 * TS + j2 * C + c];
-        fft_nat<P, -1>(a);
-        const int64_t cell = cell0 + c;
-        if (cell < n) {
-            const S sc = (S)(1.0 / ((double)P * (double)P));
+            for (int n2 = 0; n2 < Q; ++n2) {
+                const V2 a0 = yr[n2 * C], a1 = yr[(Q + n2) * C], a2 = yr[(2 * Q + n2) * C];
+                const S sx = a1.x + a2.x, sy = a1.y + a2.y;
+                if (r == 0) {
+                    y[n2] = cmk<V2>(a0.x + sx, a0.y + sy);
+                } else {
+                    // e^{-2 pi i r / 3}: the forward transform's 3-point DFT
+                    const S mx = a0.x - (S)0.5 * sx, my = a0.y - (S)0.5 * sy;
+                    const S dx = a1.x - a2.x, dy = a1.y - a2.y;
+                    const S ix = kS3 * dy, iy = -kS3 * dx;
+                    V2 u = r == 1 ? cmk<V2>(mx + ix, my + iy) : cmk<V2>(mx - ix, my - iy);
+                    if (n2 > 0) {
+                        const V2 w = twl<P, V2>(r * n2);
+                        u = cmk<V2>(u.x * w.x - u.y * w.y, u.x * w.y + u.y * w.x);
+                    }
+                    y[n2] = u;
+                }
+            }
+            fft_nat<Q, -1>(y);
+            const int64_t cell = cell0 + cd;
+            if (cell < n) {
+                const S sc = (S)(1.0 / ((double)P * (double)P));
 #pragma unroll
-            for (int k2 = -H; k2 <= H; ++k2) {
-                const V2 v = a[(k2 + P) % P];
-                qh[tiled_index(cell, (int64_t)k1 * M + k2 + H, nhalf)] = cmk<V2>(v.x * sc, v.y * sc);
+                for (int kq = 0; kq < Q; ++kq) {
+                    const int idx = 3 * kq + r;
+                    const int k2 = idx <= H ? idx : idx - P;
+                    if (k2 >= -H && k2 <= H) {
+                        const V2 v = y[kq];
+                        qh[tiled_index(cell, (int64_t)k1 * M + k2 + H, nhalf)] = cmk<V2>(v.x * sc, v.y * sc);
+                    }
+                }
             }
         }
     }
