@@ -55,7 +55,7 @@ struct bz_grid {
     double cinv[25];
 };
 
-constexpr int kModesumVariants = 8;   // register-blocked FP32 mode-sum kernel variants
+constexpr int kModesumVariants = 10;   // register-blocked FP32 mode-sum kernel variants
 constexpr int kSplitTables = 3;       // task tables for a tile split over 2, 4, 8 CTAs
 
 struct bz_modes {

@@ -67,13 +67,13 @@ struct Variant {
     int R, warps, cells, pack, wdup, pq, orient;
 };
 constexpr int kNumVariants = kModesumVariants;   // FP32 variants (timed by the autotuner)
-// entries 0..7: the FP32 variants; entries 8, 9: layouts of the FP64 and FP32X2
+// entries 0..9: the FP32 variants; entries 10, 11: layouts of the FP64 and FP32X2
 // forms only (2 outputs per thread, 8 warps, 8- and 4-cell tiles) for grids
 // whose 16-byte-per-value spectrum needs them (48^2, 16^3)
 constexpr Variant kVariants[kNumVariants + 2] = {
     {8, 16, 32, 1, 0, 0, 1}, {4, 32, 32, 1, 0, 0, 1}, {4, 16, 16, 1, 0, 0, 1}, {4, 16, 8, 1, 0, 0, 1},
     {4, 16, 32, 2, 1, 0, 1}, {8, 12, 32, 1, 0, 1, 1}, {8, 16, 32, 1, 0, 1, 1}, {8, 16, 16, 1, 0, 1, 2},
-    {2, 8, 8, 1, 0, 0, 1},   {2, 8, 4, 1, 0, 0, 1}};
+    {8, 8, 16, 1, 0, 1, 2},  {8, 4, 16, 1, 0, 1, 2},  {2, 8, 8, 1, 0, 0, 1},   {2, 8, 4, 1, 0, 0, 1}};
 
 // lane groups splitting a task's outputs, and outputs per task (RT)
 constexpr int variant_groups(int v) { return 32 / kVariants[v].cells * kVariants[v].pack / kVariants[v].orient; }
@@ -672,7 +672,7 @@ __device__ __forceinline__ void row_pass_pq(const float2 *__restrict__ rowl, con
 // the ramp applies; the table holds no reflected tasks and k_2 = 0 is the
 // lower half's.
 template <int RR, int WARPS, int CELLS>
-__global__ void __launch_bounds__(WARPS * 32, 1) modesum_pq_kernel(const Mode32Group gd) {
+__global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 3 : WARPS <= 8 ? 2 : 1) modesum_pq_kernel(const Mode32Group gd) {
     constexpr bool PAIRED = (CELLS == 16);
     constexpr int G = 32 / CELLS;                // CTAs per 32-cell tile
     constexpr int WS = RR;                       // floats per l_2 step
@@ -1283,6 +1283,8 @@ static cudaError_t launch_group(const Mode32Group &gd, int v, size_t sm, cudaStr
         case 5: return launch_pq<8, 12, 32>(gd, sm, st);
         case 6: return launch_pq<8, 16, 32>(gd, sm, st);
         case 7: return launch_pq<8, 16, 16>(gd, sm, st);
+        case 8: return launch_pq<8, 8, 16>(gd, sm, st);
+        case 9: return launch_pq<8, 4, 16>(gd, sm, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1322,9 +1324,9 @@ static cudaError_t launch_variant(const bz_modes *m, int v, const float2 *fhat, 
 
 // FP64 form: the same kernel on double spectra and weights, on 16-cell tiles
 // (variant entry 2) or, where the double spectrum of 16 cells does not fit
-// shared memory, on 8- or 4-cell tiles (entries 8, 9: 48^2, 16^3); no
+// shared memory, on 8- or 4-cell tiles (entries 10, 11: 48^2, 16^3); no
 // last-wave split.  The FP32X2 form runs on the same layout.
-constexpr int kFp64Variants[3] = {2, 8, 9};
+constexpr int kFp64Variants[3] = {2, 10, 11};
 
 bool modesum64_available(const bz_modes *m) { return m->w64 != nullptr; }
 

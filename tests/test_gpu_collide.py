@@ -70,16 +70,16 @@ def test_fast_kernels_selected(bz):
     and the 3-D grids up to 16^3 (a silent fall back to the generic kernel would
     hide a table-building bug)."""
     for N in (16, 24, 32):
-        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7, 8), N
-    assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_variant in (3, 8)    # only 16-cell tiles fit
+        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7, 8, 9), N
+    assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_variant in (3, 8, 9)    # only 16-cell tiles fit
     assert bz.Modes(bz.Grid(3, 16, 10.0), 1.0).modesum_variant == 4    # 8-cell tiles, 3-D rows
-    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7, 8)   # 16-wide blocks overhang a 7-mode row
+    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7, 8, 9)   # 16-wide blocks overhang a 7-mode row
     assert bz.Modes(bz.Grid(2, 64, 10.0), 1.0).modesum_variant == 0
 
 
-@pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3, 5, 6, 7, 8)]
+@pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3, 5, 6, 7, 8, 9)]
                          + [(2, 16, 4), (3, 8, 1), (3, 8, 2), (3, 8, 3), (3, 8, 5), (3, 8, 6), (3, 8, 7), (3, 8, 8),
-                            (2, 48, 3), (2, 48, 8)])
+                            (3, 8, 9), (2, 48, 3), (2, 48, 8), (2, 48, 9)])
 def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, dim, N, variant):
     """Every register-blocked variant (fixed through BZ_MODESUM_VARIANT, bypassing
     the autotuner) against the oracle: 70 cells = 2 full tiles and a ragged tail."""
@@ -98,33 +98,56 @@ def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, dim, N, variant):
     check_fp32_cells(k, fin, Qg, Qr, what="variant %d N=%d d=%d" % (variant, N, dim))
 
 
+_SPLIT_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2103_14890_gb300 import binding as bz, workloads
+variant, extra = int(sys.argv[2]), int(sys.argv[3])
+N, L = 32, 10.0
+sms = torch.cuda.get_device_properties(0).multi_processor_count
+n = sms * 32 + extra
+f = workloads.bi_maxwellian(n, 2, N, L, seed=1500)
+m = bz.Modes(bz.Grid(2, N, L), 1.0)            # the cached choice: timed path, split allowed
+assert m.modesum_variant == variant, m.modesum_variant
+Q = bz.collide_batch(m, torch.tensor(f, dtype=torch.float32, device="cuda")).cpu().numpy()
+import os
+os.environ["BZ_MODESUM_VARIANT"] = str(variant)
+m_main = bz.Modes(bz.Grid(2, N, L), 1.0)
+os.environ["BZ_MODESUM_VARIANT"] = sys.argv[4]
+m_tail = bz.Modes(bz.Grid(2, N, L), 1.0)
+Qa = bz.collide_batch(m_main, torch.tensor(f[:sms * 32], dtype=torch.float32, device="cuda")).cpu().numpy()
+Qb = bz.collide_batch(m_tail, torch.tensor(f[sms * 32:], dtype=torch.float32, device="cuda")).cpu().numpy()
+bz.check()
+assert np.array_equal(Q[:sms * 32], Qa)
+assert np.array_equal(Q[sms * 32:], Qb)
+print("ok")
+"""
+
+
+@pytest.mark.parametrize("variant", [1, 7])
 @pytest.mark.parametrize("extra", [70, 30 * 32 + 5, 50 * 32, 100 * 32 - 1])
-def test_last_wave_split_is_exact(bz, monkeypatch, extra):
-    """With a timed 32-cell variant, whole waves of CTAs run one tile each and
-    the tiles of the last partial wave are split over 8, 4 or 2 CTAs (3, 31,
-    50 extra tiles) or, beyond half the SMs (100 extra tiles), run on the
-    16-cell variant when that one sums every output in the same order (the
-    scalar one-cell-per-lane variants), else as a plain partial wave: every
-    cell must equal a run of a fixed variant (cells are independent)."""
+def test_last_wave_split_is_exact(tmp_path, variant, extra):
+    """A 32-cell variant chosen as the autotuner would (through the tune cache,
+    in a fresh process): whole waves of CTAs run one tile each and the tiles of
+    the last partial wave are split over 8, 4 or 2 CTAs (3, 31, 50 extra
+    tiles) or, beyond half the SMs (100 extra tiles), run on the 16-cell
+    variant when that one sums every output in the same order (the scalar
+    one-cell-per-lane variants), else as a plain partial wave: every cell must
+    equal a run of a fixed variant (cells are independent)."""
+    import os
+    import subprocess
+    import sys
     import torch
-    N, L = 32, 10.0
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    n = sms * 32 + extra
-    f = workloads.bi_maxwellian(n, 2, N, L, seed=1500)
-    m = bz.Modes(bz.Grid(2, N, L), 1.0)
-    if m.modesum_variant not in (1, 2, 5, 6, 7):     # 32-cell variants
-        pytest.skip("timed variant is not a 32-cell one")
-    Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32").cpu().numpy()
-    monkeypatch.setenv("BZ_MODESUM_VARIANT", str(m.modesum_variant))
-    m_main = bz.Modes(bz.Grid(2, N, L), 1.0)
-    own_class = m.modesum_variant in (5, 6, 7, 8)    # packed forms: the tail stays on them
-    monkeypatch.setenv("BZ_MODESUM_VARIANT", str(m.modesum_variant) if own_class else "3")
-    m_tail = bz.Modes(bz.Grid(2, N, L), 1.0)
-    Qa = bz.collide_batch(m_main, to_dev(f[:sms * 32], "fp32"), precision="fp32").cpu().numpy()
-    Qb = bz.collide_batch(m_tail, to_dev(f[sms * 32:], "fp32"), precision="fp32").cpu().numpy()
-    bz.check()
-    assert np.array_equal(Q[:sms * 32], Qa)
-    assert np.array_equal(Q[sms * 32:], Qb)
+    cache = tmp_path / "tune.txt"
+    cache.write_text("2 32 %d %d\n" % (sms, variant))
+    tail = str(variant) if variant == 7 or extra < 100 * 32 - 1 else "3"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, BZ_TUNE_CACHE=str(cache))
+    env.pop("BZ_MODESUM_VARIANT", None)
+    r = subprocess.run([sys.executable, "-c", _SPLIT_CHILD, root, str(variant), str(extra), tail], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
 
 
 @pytest.mark.parametrize("n", [1, 8, 13])
@@ -152,7 +175,7 @@ def test_fp32_48_grid_16_cell_tiles(bz, oracle_k, n):
     oracle."""
     N, L = 48, 10.0
     m = bz.Modes(bz.Grid(2, N, L), 1.0)
-    assert m.modesum_variant in (3, 8)
+    assert m.modesum_variant in (3, 8, 9)
     f = workloads.bi_maxwellian(n, 2, N, L, seed=1200 + n)
     fin = as_input(f, "fp32")
     Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32")
