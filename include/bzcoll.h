@@ -173,7 +173,9 @@ int collide_batch(const bz_modes *m, int precision, int flags, const void *f, vo
  *   f_host, Q_host : host arrays [n_cells][N^d], float64 for BZ_FP64, float32
  *                    for BZ_FP32; caller-owned, must not overlap
  *   other arguments: as collide_batch
- * The batch moves in chunks of 32 x (SM count) cells (4864 on a 152-SM GPU;
+ * The batch moves in chunks of one full wave of the handle's mode-sum kernel
+ * (SM count x the cells one SM holds: 7296 cells for the 32x32 grid's
+ * three 16-cell CTAs per SM on a 152-SM GPU, 32 x SM count for the fast form;
  * the first and the last chunk of a batch longer than two chunks are a
  * quarter of that, to shorten the copies that fill and drain the pipeline)
  * through two device slots taken from the library's pool: the copy of chunk c+1 to the device, the collision of

@@ -624,12 +624,14 @@ int group_streams(int dev, cudaStream_t out[kGroupStreams]) {
     return BZ_OK;
 }
 
-// Cells per pipeline stage of collide_batch_host: one wave of 32-cell CTAs of
-// the mode-sum kernel (one per SM), so that no chunk leaves SMs idle at its end.
-int64_t host_chunk_cells(int dev) {
+// Cells per pipeline stage of collide_batch_host: one full wave of the
+// handle's mode-sum kernel (every SM holding as many CTAs as fit), so that no
+// chunk leaves SMs idle at its end.
+int64_t host_chunk_cells(const bz_modes *m) {
     int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 128;
-    return (int64_t)sms * 32;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->g->device) != cudaSuccess || sms <= 0)
+        sms = 128;
+    return (int64_t)sms * modesum32_wave_cells_per_sm(m);
 }
 
 }  // namespace
@@ -722,7 +724,7 @@ int collide_batch_host(const bz_modes *m, int precision, int flags, const void *
         return fail(BZ_EINVAL, "collide_batch_host: not available inside a stream capture");
     const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
     const size_t cell_bytes = (size_t)m->g->v.nv * es;
-    const int64_t chunk = std::min(n_cells, host_chunk_cells(m->g->device));
+    const int64_t chunk = std::min(n_cells, host_chunk_cells(m));
     // chunk boundaries: one mode-sum wave each, except that the first and the
     // last chunk of a long batch are a quarter wave, so the copy that fills
     // the pipeline and the one that drains it are short (a quarter-wave mode

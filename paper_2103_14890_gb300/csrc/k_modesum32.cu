@@ -613,20 +613,22 @@ __device__ __forceinline__ void block_pq(float2 (&win)[2 * RR], const float2 *__
         const float2 fl = lp[s * dcs];
         const float fy = fl.y * sgn;
         const float2 fxx = make_float2(fl.x, fl.x), fyy = make_float2(fy, fy);
+        // all products U first, then the P and then the Q updates: no FMA
+        // waits on the multiply issued just before it
+        float wv[RR];
 #pragma unroll
-        for (int q = 0; q < RR; q += 4) {
-            if (RAMP && q >= s) continue;                       // outputs q .. q + 3 all before the ramp
-            float wv[4];
-            load_w4(wv, wb + s * WS + q);
+        for (int q = 0; q < RR; q += 4)
+            if (!RAMP || q < s) load_w4(wv + q, wb + s * WS + q);   // outputs q .. q + 3 before the ramp
+        float2 u[RR];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int r = q + e;
-                if (RAMP && r >= s) continue;
-                const float2 u = __fmul2_rn(make_float2(wv[e], wv[e]), win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)]);
-                P[r] = __ffma2_rn(u, fxx, P[r]);
-                Q[r] = __ffma2_rn(u, fyy, Q[r]);
-            }
-        }
+        for (int r = 0; r < RR; ++r)
+            if (!RAMP || r < s) u[r] = __fmul2_rn(make_float2(wv[r], wv[r]), win[(r - s + RR - 1 + PH * RR) & (2 * RR - 1)]);
+#pragma unroll
+        for (int r = 0; r < RR; ++r)
+            if (!RAMP || r < s) P[r] = __ffma2_rn(u[r], fxx, P[r]);
+#pragma unroll
+        for (int r = 0; r < RR; ++r)
+            if (!RAMP || r < s) Q[r] = __ffma2_rn(u[r], fyy, Q[r]);
     }
 }
 
@@ -1408,6 +1410,18 @@ int64_t modesum32_split(const bz_modes *m, int64_t n, int *tail_v, int *tail_spl
         return n;
     *tail_v = 2;
     return full * 32;
+}
+
+// CTAs per SM of a variant's kernel (its launch bounds: the FP32x2 kernels
+// with 8 or 4 warps are built for 2 or 3 resident CTAs).
+static int variant_ctas_per_sm(int v) {
+    if (!kVariants[v].pq) return 1;
+    return kVariants[v].warps <= 4 ? 3 : kVariants[v].warps <= 8 ? 2 : 1;
+}
+
+int modesum32_wave_cells_per_sm(const bz_modes *m) {
+    if (m->method != 0 || !modesum32_available(m)) return 32;
+    return variant_ctas_per_sm(m->variant) * kVariants[m->variant].cells;
 }
 
 // One launch for the whole batch: the main part (one tile per CTA) and the

@@ -15,10 +15,12 @@ def bz():
     return bz_module()
 
 
-@pytest.mark.parametrize("n", [1, 4864, 20000])
+@pytest.mark.parametrize("n", [1, 4864, 7296, 20000, 40000])
 def test_host_pinned_equals_device(bz, n):
-    """On a 152-SM GPU a chunk is 4864 cells: one exact chunk, and 20000 cells =
-    four full chunks and a ragged fifth."""
+    """A chunk is one full wave of the grid's mode-sum kernel (4864 cells for a
+    one-CTA-per-SM 32-cell kernel on 152 SMs, 7296 for three 16-cell CTAs per
+    SM): one cell, one exact chunk of either size, and batches of several
+    chunks with quarter-size first and last chunks and a ragged one."""
     import torch
     N, L = 16, 8.0
     m = bz.Modes(bz.Grid(2, N, L), 1.0)
