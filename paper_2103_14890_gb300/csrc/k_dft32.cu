@@ -26,13 +26,14 @@ namespace {
 template <typename T, int N>
 __device__ __forceinline__ void inv32_epilogue(T (&q)[N], int64_t cell, int lane, const Cinv &cinv,
                                                int conserve, const T *__restrict__ P, T *__restrict__ Q,
-                                               double L, double dv, int64_t n) {
+                                               T L, T dv, int64_t n) {
     using S = T;
     constexpr int NV = N * N;
     if (conserve) {
-        // the column's velocity, formed here only: FP64 operations cost 64
-        // FP32 ones on this GPU and the common path needs none
-        const S v2 = (S)(-L + lane * dv);
+        // velocities in the working precision (L and dv arrive as T): in FP64
+        // the compiler hoisted their 32 conversions out of this branch into
+        // the common path, where FP64 at 1/64 of the FP32 rate bound the kernel
+        const S v2 = -L + (S)lane * dv;
         // moments of Q over the cell: FP32 partials along j1 with a TwoSum
         // error term, combined in FP64 across the lanes; then the projection
         // Q -= phi . (C C^T)^{-1} (C Q) with phi = (1, v1, v2, |v|^2)
@@ -41,7 +42,7 @@ __device__ __forceinline__ void inv32_epilogue(T (&q)[N], int64_t cell, int lane
             S s0 = (S)0., e0 = (S)0., s1 = (S)0., e1 = (S)0., s3 = (S)0., e3 = (S)0.;
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                const S v1 = (S)(-L + j * dv);
+                const S v1 = -L + (S)j * dv;
                 const S t0 = lane < N ? q[j] : (S)0.;
                 S s, bb;
                 s = s0 + t0; bb = s - s0; e0 += (s0 - (s - bb)) + (t0 - bb); s0 = s;
@@ -72,7 +73,7 @@ __device__ __forceinline__ void inv32_epilogue(T (&q)[N], int64_t cell, int lane
         const S x0 = (S)x[0], x1 = (S)x[1], x2 = (S)x[2], x3 = (S)x[3];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            const S v1 = (S)(-L + j * dv);
+            const S v1 = -L + (S)j * dv;
             q[j] -= x0 + x1 * v1 + x2 * v2 + x3 * (v1 * v1 + v2 * v2);
         }
     }
@@ -172,7 +173,7 @@ fft_fwd32_kernel(const TI *__restrict__ f, typename C2<T>::type *__restrict__ fh
 template <typename T, int N, int C>
 __global__ void __launch_bounds__(C * 16)
 fft_inv32_kernel(const typename C2<T>::type *__restrict__ Qhat, T *__restrict__ Q, T scale, Cinv cinv,
-                 int conserve, const T *__restrict__ P_, double L, double dv, int64_t n) {
+                 int conserve, const T *__restrict__ P_, T L, T dv, int64_t n) {
     using V2 = typename C2<T>::type;
     using S = T;
     constexpr int H = N / 2, M = N - 1, LH = ilog2(H), LN = ilog2(N);
@@ -319,19 +320,19 @@ fftg_fwd_kernel(const TI *__restrict__ f, typename C2<T>::type *__restrict__ fha
 template <typename T, int N, int TPC>
 __device__ __forceinline__ void invg_epilogue(T (&q)[N], int64_t cell, int j2, const Cinv &cinv,
                                               int conserve, const T *__restrict__ P,
-                                              T *__restrict__ Q, double L, double dv, int64_t n,
+                                              T *__restrict__ Q, T L, T dv, int64_t n,
                                               double *red) {
     using S = T;
     constexpr int NV = N * N;
     const bool col = j2 < N;
     if (conserve) {
-        const S v2 = (S)(-L + j2 * dv);        // formed only where used (FP64 is 1/64 rate)
+        const S v2 = -L + (S)j2 * dv;          // working precision (FP64 is 1/64 of the FP32 rate)
         double mom[4];
         {
             S s0 = (S)0., e0 = (S)0., s1 = (S)0., e1 = (S)0., s3 = (S)0., e3 = (S)0.;
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-                const S v1 = (S)(-L + j * dv);
+                const S v1 = -L + (S)j * dv;
                 const S t0 = col ? q[j] : (S)0.;
                 S s, bb;
                 s = s0 + t0; bb = s - s0; e0 += (s0 - (s - bb)) + (t0 - bb); s0 = s;
@@ -378,7 +379,7 @@ __device__ __forceinline__ void invg_epilogue(T (&q)[N], int64_t cell, int j2, c
         const S x0 = (S)x[0], x1 = (S)x[1], x2 = (S)x[2], x3 = (S)x[3];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            const S v1 = (S)(-L + j * dv);
+            const S v1 = -L + (S)j * dv;
             q[j] -= x0 + x1 * v1 + x2 * v2 + x3 * (v1 * v1 + v2 * v2);
         }
     }
@@ -393,7 +394,7 @@ __device__ __forceinline__ void invg_epilogue(T (&q)[N], int64_t cell, int j2, c
 template <typename T, int N, int C>
 __global__ void __launch_bounds__(C * threads_per_cell<N>())
 fftg_inv_kernel(const typename C2<T>::type *__restrict__ Qhat, T *__restrict__ Q, T scale, Cinv cinv,
-                int conserve, const T *__restrict__ P_, double L, double dv, int64_t n) {
+                int conserve, const T *__restrict__ P_, T L, T dv, int64_t n) {
     using V2 = typename C2<T>::type;
     using S = T;
     constexpr int H = N / 2, M = N - 1, P = C + 1, TPC = threads_per_cell<N>(), NT = C * TPC;
@@ -505,13 +506,14 @@ cudaError_t inv_tile(const GridView &g, const typename C2<T>::type *Qhat, T *Q, 
         const size_t sm = fft_smem<T, N, C>();
         e = cudaFuncSetAttribute(fft_inv32_kernel<T, N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        fft_inv32_kernel<T, N, C><<<grid, C * 16, sm, st>>>(Qhat, Q, (T)scale, ci, ep.conserve, P, g.L, g.dv, n);
+        fft_inv32_kernel<T, N, C><<<grid, C * 16, sm, st>>>(Qhat, Q, (T)scale, ci, ep.conserve, P, (T)g.L, (T)g.dv,
+                                                             n);
     } else {
         const size_t sm = fftg_smem<T, N, C>();
         e = cudaFuncSetAttribute(fftg_inv_kernel<T, N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         fftg_inv_kernel<T, N, C><<<grid, C * threads_per_cell<N>(), sm, st>>>(Qhat, Q, (T)scale, ci, ep.conserve,
-                                                                             P, g.L, g.dv, n);
+                                                                             P, (T)g.L, (T)g.dv, n);
     }
     return cudaGetLastError();
 }

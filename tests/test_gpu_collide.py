@@ -70,16 +70,16 @@ def test_fast_kernels_selected(bz):
     and the 3-D grids up to 16^3 (a silent fall back to the generic kernel would
     hide a table-building bug)."""
     for N in (16, 24, 32):
-        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7, 8, 9), N
-    assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_variant in (3, 8, 9)    # only 16-cell tiles fit
+        assert bz.Modes(bz.Grid(2, N, 10.0), 1.0).modesum_variant >= 1, N
+    assert bz.Modes(bz.Grid(2, 48, 10.0), 1.0).modesum_variant in (3, 8, 9, 10)    # only 16-cell tiles fit
     assert bz.Modes(bz.Grid(3, 16, 10.0), 1.0).modesum_variant == 4    # 8-cell tiles, 3-D rows
-    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant in (1, 2, 3, 5, 6, 7, 8, 9)   # 16-wide blocks overhang a 7-mode row
+    assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant >= 1   # 16-wide blocks overhang a 7-mode row
     assert bz.Modes(bz.Grid(2, 64, 10.0), 1.0).modesum_variant == 0
 
 
-@pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3, 5, 6, 7, 8, 9)]
+@pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3, 5, 6, 7, 8, 9, 10)]
                          + [(2, 16, 4), (3, 8, 1), (3, 8, 2), (3, 8, 3), (3, 8, 5), (3, 8, 6), (3, 8, 7), (3, 8, 8),
-                            (3, 8, 9), (2, 48, 3), (2, 48, 8), (2, 48, 9)])
+                            (3, 8, 9), (3, 8, 10), (2, 48, 3), (2, 48, 8), (2, 48, 9), (2, 48, 10)])
 def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, dim, N, variant):
     """Every register-blocked variant (fixed through BZ_MODESUM_VARIANT, bypassing
     the autotuner) against the oracle: 70 cells = 2 full tiles and a ragged tail."""
@@ -175,7 +175,7 @@ def test_fp32_48_grid_16_cell_tiles(bz, oracle_k, n):
     oracle."""
     N, L = 48, 10.0
     m = bz.Modes(bz.Grid(2, N, L), 1.0)
-    assert m.modesum_variant in (3, 8, 9)
+    assert m.modesum_variant in (3, 8, 9, 10)
     f = workloads.bi_maxwellian(n, 2, N, L, seed=1200 + n)
     fin = as_input(f, "fp32")
     Q = bz.collide_batch(m, to_dev(f, "fp32"), precision="fp32")

@@ -46,7 +46,8 @@ def test_group_collide_mixed_variants(bz, monkeypatch):
                                         (2, 48, 3, 21), (2, 24, 3, 40), (3, 16, 4, 11), (2, 16, 4, 9),
                                         (2, 32, 5, 45), (2, 24, 5, 70), (2, 32, 6, 45), (2, 24, 6, 70),
                                         (2, 16, 6, 33), (2, 32, 7, 40), (3, 8, 7, 20), (2, 48, 8, 21),
-                                        (2, 32, 8, 40), (2, 32, 9, 37), (2, 48, 9, 19)]):
+                                        (2, 32, 8, 40), (2, 32, 9, 37), (2, 48, 9, 19), (2, 32, 10, 39),
+                                        (2, 48, 10, 23), (2, 16, 10, 41)]):
         monkeypatch.setenv("BZ_MODESUM_VARIANT", str(var))
         m = bz.Modes(bz.Grid(d, N, 10.0), 1.0)
         assert m.modesum_variant == var
