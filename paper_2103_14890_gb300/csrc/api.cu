@@ -726,20 +726,23 @@ int collide_batch_host(const bz_modes *m, int precision, int flags, const void *
     const size_t cell_bytes = (size_t)m->g->v.nv * es;
     const int64_t chunk = std::min(n_cells, host_chunk_cells(m));
     // chunk boundaries: one mode-sum wave each, except that the first and the
-    // last chunk of a long batch are a quarter wave, so the copy that fills
-    // the pipeline and the one that drains it are short (a quarter-wave mode
-    // sum splits its tiles over four CTAs and takes about a quarter of a wave)
+    // last chunk of a long batch are a quarter wave where a quarter wave runs
+    // in about a quarter of the time (the 32-cell kernels split a partial
+    // wave's tiles over four CTAs; the fast form's wave holds four CTAs per
+    // SM), so the copy that fills the pipeline and the one that drains it are
+    // short; kernels that hold several CTAs per SM take full waves throughout
     std::vector<int64_t> bnd{0};
     {
+        const bool quarters = m->method != 0 || (precision == BZ_FP32 && modesum32_tail_splits(m));
         const int64_t q = std::max<int64_t>(32, (chunk / 4 + 31) / 32 * 32);
         int64_t at = 0;
-        if (n_cells > 2 * chunk) {
+        if (quarters && n_cells > 2 * chunk) {
             at = q;
             bnd.push_back(at);
         }
         while (n_cells - at > chunk) {
             const int64_t rest = n_cells - at;
-            const int64_t step = (rest <= chunk + q && rest > q && n_cells > 2 * chunk) ? rest - q : chunk;
+            const int64_t step = (quarters && rest <= chunk + q && rest > q && n_cells > 2 * chunk) ? rest - q : chunk;
             at += step;
             bnd.push_back(at);
         }

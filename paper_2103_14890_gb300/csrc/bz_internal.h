@@ -233,6 +233,9 @@ int64_t modesum32_split(const bz_modes *m, int64_t n, int *tail_v, int *tail_spl
 // Cells one SM holds at a time in the handle's FP32 mode-sum kernel (CTAs per
 // SM x cells per CTA; 32 where the register-blocked kernels do not serve it).
 int modesum32_wave_cells_per_sm(const bz_modes *m);
+// Whether the handle's FP32 mode sum splits the tiles of a partial wave over
+// several CTAs (32-cell variants chosen by timing).
+bool modesum32_tail_splits(const bz_modes *m);
 bool modesum64_available(const bz_modes *m);
 cudaError_t launch_modesum64(const bz_modes *m, const double2 *fhat, double2 *Qhat, int64_t n, cudaStream_t st);
 cudaError_t launch_modesum32_part(const bz_modes *m, int v, const float2 *fhat, float2 *Qhat, int64_t n,

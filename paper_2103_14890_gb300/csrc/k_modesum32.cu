@@ -1419,6 +1419,11 @@ static int variant_ctas_per_sm(int v) {
     return kVariants[v].warps <= 4 ? 3 : kVariants[v].warps <= 8 ? 2 : 1;
 }
 
+bool modesum32_tail_splits(const bz_modes *m) {
+    return m->method == 0 && modesum32_available(m) && !m->variant_fixed && kVariants[m->variant].cells == 32 &&
+           m->var_task_split[m->variant][0] != nullptr;
+}
+
 int modesum32_wave_cells_per_sm(const bz_modes *m) {
     if (m->method != 0 || !modesum32_available(m)) return 32;
     return variant_ctas_per_sm(m->variant) * kVariants[m->variant].cells;
