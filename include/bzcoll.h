@@ -176,9 +176,7 @@ int collide_batch(const bz_modes *m, int precision, int flags, const void *f, vo
  * The batch moves in chunks of one full wave of the handle's mode-sum kernel
  * (SM count x the cells one SM holds: 7296 cells for the 32x32 grid's
  * three 16-cell CTAs per SM on a 152-SM GPU, 32 x SM count for the fast form;
- * where a quarter wave runs in about a quarter of the time (the 32-cell
- * kernels, which split a partial wave's tiles over several CTAs, and the fast
- * form), the first and the last chunk of a batch longer than two chunks are a
+ * the first and the last chunk of a batch longer than two chunks are a
  * quarter of that, to shorten the copies that fill and drain the pipeline)
  * through two device slots taken from the library's pool: the copy of chunk c+1 to the device, the collision of
  * chunk c on `stream` and the copy of chunk c-1 back run concurrently (two

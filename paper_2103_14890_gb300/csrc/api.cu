@@ -728,12 +728,14 @@ int collide_batch_host(const bz_modes *m, int precision, int flags, const void *
     // chunk boundaries: one mode-sum wave each, except that the first and the
     // last chunk of a long batch are a quarter wave where a quarter wave runs
     // in about a quarter of the time (the 32-cell kernels split a partial
-    // wave's tiles over four CTAs; the fast form's wave holds four CTAs per
-    // SM), so the copy that fills the pipeline and the one that drains it are
-    // short; kernels that hold several CTAs per SM take full waves throughout
+    // wave's tiles over four CTAs; kernels with several CTAs per SM run a chunk
+    // on their one-CTA sibling, three short waves; the fast form's wave holds
+    // four CTAs per SM), so the copy that fills the pipeline and the one that
+    // drains it are short
     std::vector<int64_t> bnd{0};
     {
-        const bool quarters = m->method != 0 || (precision == BZ_FP32 && modesum32_tail_splits(m));
+        const bool quarters = m->method != 0 || (precision == BZ_FP32 && (modesum32_tail_splits(m) ||
+                                                                           modesum32_small_batches_fast(m)));
         const int64_t q = std::max<int64_t>(32, (chunk / 4 + 31) / 32 * 32);
         int64_t at = 0;
         if (quarters && n_cells > 2 * chunk) {

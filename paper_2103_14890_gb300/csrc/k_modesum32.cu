@@ -1424,6 +1424,28 @@ bool modesum32_tail_splits(const bz_modes *m) {
            m->var_task_split[m->variant][0] != nullptr;
 }
 
+// A variant that holds several CTAs per SM loses about a sixth of a wave when a
+// launch is a single wave (all CTAs stage their spectra at once and the SMs
+// empty unevenly at the end).  Its sibling with one 16-warp CTA per SM runs
+// the same tasks in the same order (bit-identical results) and has no such
+// loss, so launches of up to one and a half waves take the sibling.
+static int small_batch_variant(const bz_modes *m, int64_t n) {
+    const int v = m->variant;
+    if (m->variant_fixed || variant_ctas_per_sm(v) == 1) return v;
+    if (n > (int64_t)sm_count() * variant_ctas_per_sm(v) * kVariants[v].cells * 3 / 2) return v;
+    for (int s = 0; s < kNumVariants; ++s) {
+        const Variant &a = kVariants[s], &b = kVariants[v];
+        if (s != v && m->var_W[s] && variant_ctas_per_sm(s) == 1 && a.R == b.R && a.cells == b.cells &&
+            a.pack == b.pack && a.wdup == b.wdup && a.pq == b.pq && a.orient == b.orient)
+            return s;
+    }
+    return v;
+}
+
+bool modesum32_small_batches_fast(const bz_modes *m) {
+    return m->method == 0 && modesum32_available(m) && small_batch_variant(m, 1) != m->variant;
+}
+
 int modesum32_wave_cells_per_sm(const bz_modes *m) {
     if (m->method != 0 || !modesum32_available(m)) return 32;
     return variant_ctas_per_sm(m->variant) * kVariants[m->variant].cells;
@@ -1433,6 +1455,8 @@ int modesum32_wave_cells_per_sm(const bz_modes *m) {
 // last partial wave (split tiles, or the 16-cell variant) as two items.
 cudaError_t launch_modesum32(const bz_modes *m, const float2 *fhat, float2 *Qhat, int64_t n, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
+    const int sv = small_batch_variant(m, n);
+    if (sv != m->variant) return launch_variant(m, sv, fhat, Qhat, n, st);
     int tv = -1, ts = 1;
     const int64_t nm = modesum32_split(m, n, &tv, &ts);
     const int v = m->variant;
