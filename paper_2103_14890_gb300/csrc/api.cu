@@ -624,6 +624,31 @@ int group_streams(int dev, cudaStream_t out[kGroupStreams]) {
     return BZ_OK;
 }
 
+// Compute streams of collide_batch_host per device (non-blocking, created on
+// first use): forward and inverse transforms at the greatest priority, the
+// mode sums of even and odd chunks at the least, so that a chunk's inverse
+// transform takes the SMs the moment its mode sum ends, ahead of the CTAs of
+// the next chunk's mode sum, which fill the SMs the previous one frees.
+constexpr int kHostStreams = 4;    // forward, inverse, mode sum (even chunks), mode sum (odd chunks)
+cudaStream_t g_host_streams[kMaxDevices][kHostStreams];
+bool g_host_ok[kMaxDevices];
+
+int host_streams(int dev, cudaStream_t out[kHostStreams]) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_host_ok[dev]) {
+        int lo = 0, hi = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e != cudaSuccess) return cuda_fail(e, "collide_batch_host: stream priorities");
+        for (int i = 0; i < kHostStreams; ++i) {
+            e = cudaStreamCreateWithPriority(&g_host_streams[dev][i], cudaStreamNonBlocking, i < 2 ? hi : lo);
+            if (e != cudaSuccess) return cuda_fail(e, "collide_batch_host: compute stream");
+        }
+        g_host_ok[dev] = true;
+    }
+    for (int i = 0; i < kHostStreams; ++i) out[i] = g_host_streams[dev][i];
+    return BZ_OK;
+}
+
 // Cells per pipeline stage of collide_batch_host: one full wave of the
 // handle's mode-sum kernel (every SM holding as many CTAs as fit), so that no
 // chunk leaves SMs idle at its end.
@@ -631,6 +656,8 @@ int64_t host_chunk_cells(const bz_modes *m) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->g->device) != cudaSuccess || sms <= 0)
         sms = 128;
+    // two waves where a short launch would run on the one-CTA sibling: the
+    // overlapping chunks keep the faster several-CTA kernel busy
     return (int64_t)sms * modesum32_wave_cells_per_sm(m);
 }
 
@@ -725,99 +752,121 @@ int collide_batch_host(const bz_modes *m, int precision, int flags, const void *
     const size_t es = (precision == BZ_FP64) ? sizeof(double) : sizeof(float);
     const size_t cell_bytes = (size_t)m->g->v.nv * es;
     const int64_t chunk = std::min(n_cells, host_chunk_cells(m));
-    // chunk boundaries: one mode-sum wave each, except that the first and the
-    // last chunk of a long batch are a quarter wave where a quarter wave runs
-    // in about a quarter of the time (the 32-cell kernels split a partial
-    // wave's tiles over four CTAs; kernels with several CTAs per SM run a chunk
-    // on their one-CTA sibling, three short waves; the fast form's wave holds
-    // four CTAs per SM), so the copy that fills the pipeline and the one that
+    // chunk boundaries: one mode-sum wave each, except that where a short
+    // chunk runs in proportion to its size (the 32-cell kernels split a partial
+    // wave's tiles over several CTAs; kernels with several CTAs per SM run a
+    // short chunk on their one-CTA sibling; the fast form's wave holds four
+    // CTAs per SM) a long batch starts and ends with chunks of 1/8, 1/4 and 1/2
+    // of a wave, so that the copy that fills the pipeline and the one that
     // drains it are short
     std::vector<int64_t> bnd{0};
     {
-        const bool quarters = m->method != 0 || (precision == BZ_FP32 && (modesum32_tail_splits(m) ||
+        const bool ramped = m->method != 0 || (precision == BZ_FP32 && (modesum32_tail_splits(m) ||
                                                                            modesum32_small_batches_fast(m)));
-        const int64_t q = std::max<int64_t>(32, (chunk / 4 + 31) / 32 * 32);
-        int64_t at = 0;
-        if (quarters && n_cells > 2 * chunk) {
-            at = q;
-            bnd.push_back(at);
-        }
-        while (n_cells - at > chunk) {
-            const int64_t rest = n_cells - at;
-            const int64_t step = (quarters && rest <= chunk + q && rest > q && n_cells > 2 * chunk) ? rest - q : chunk;
-            at += step;
-            bnd.push_back(at);
+        auto part = [&](int d) { return std::max<int64_t>(32, (chunk / d + 31) / 32 * 32); };
+        const int64_t ramp = part(8) + part(4) + part(2);
+        if (ramped && n_cells > 2 * ramp + chunk) {
+            int64_t at = 0;
+            for (int d : {8, 4, 2}) bnd.push_back(at += part(d));
+            const int64_t mid_end = n_cells - ramp;
+            while (mid_end - at > chunk) bnd.push_back(at += chunk);
+            bnd.push_back(at = mid_end);
+            for (int d : {2, 4}) bnd.push_back(at += part(d));
+        } else {
+            int64_t at = 0;
+            while (n_cells - at > chunk) bnd.push_back(at += chunk);
         }
         if (bnd.back() != n_cells) bnd.push_back(n_cells);
     }
     const int64_t nchunks = (int64_t)bnd.size() - 1;
-    cudaStream_t cp[2];
+    cudaStream_t cp[2], hs[kHostStreams];
     if ((rc = copy_streams(m->g->device, cp))) return rc;
-    cudaStream_t s_in = cp[0], s_out = cp[1];
-    // two device slots of (f, Q) chunks, from the pool on the caller's stream
+    if ((rc = host_streams(m->g->device, hs))) return rc;
+    cudaStream_t s_in = cp[0], s_out = cp[1], s_fwd = hs[0], s_inv = hs[1], s_ms[2] = {hs[2], hs[3]};
+    // two device slots, each an (f, Q) chunk pair and the chunk's Fourier
+    // scratch, from the pool on the caller's stream
+    const size_t sbytes = (collide_scratch_bytes(m, precision, chunk) + 255) / 256 * 256;
+    const size_t fbytes = (chunk * cell_bytes + 255) / 256 * 256;
     Scratch buf;
-    BZ_TRY(buf.alloc(4 * chunk * cell_bytes, st), "collide_batch_host: chunk buffers");
-    char *fd[2], *qd[2];
+    BZ_TRY(buf.alloc(2 * (2 * fbytes + sbytes), st), "collide_batch_host: chunk buffers");
+    char *fd[2], *qd[2], *fh[2], *qh[2];
     for (int i = 0; i < 2; ++i) {
-        fd[i] = static_cast<char *>(buf.p) + (size_t)(2 * i) * chunk * cell_bytes;
-        qd[i] = static_cast<char *>(buf.p) + (size_t)(2 * i + 1) * chunk * cell_bytes;
+        char *b = static_cast<char *>(buf.p) + (size_t)i * (2 * fbytes + sbytes);
+        fd[i] = b;
+        qd[i] = b + fbytes;
+        fh[i] = b + 2 * fbytes;
+        qh[i] = fh[i] + spectrum_bytes(m, precision, chunk);
     }
-    // events: ready (buffers allocated), in[i] (f chunk copied), done[i]
-    // (collision of slot i finished: f slot free, Q slot ready), out[i] (Q
-    // slot copied back: free)
-    cudaEvent_t ev[7] = {};
-    for (int i = 0; i < 7; ++i) {
+    // events per slot: in (f copied), fw (forward transform done: f slot
+    // free), ms (mode sum done: spectrum free), done (inverse done: Q ready,
+    // Q-hat free), out (Q copied back: Q slot free); ready (buffers allocated)
+    // and one end event per compute stream
+    constexpr int kEv = 1 + 5 * 2 + kHostStreams;
+    cudaEvent_t ev[kEv] = {};
+    for (int i = 0; i < kEv; ++i) {
         cudaError_t e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
         if (e != cudaSuccess) {
             for (int q = 0; q < i; ++q) cudaEventDestroy(ev[q]);
             return cuda_fail(e, "collide_batch_host: events");
         }
     }
-    cudaEvent_t ready = ev[0], in[2] = {ev[1], ev[2]}, done[2] = {ev[3], ev[4]}, out[2] = {ev[5], ev[6]};
+    cudaEvent_t ready = ev[0], *in = ev + 1, *fw = ev + 3, *ms = ev + 5, *done = ev + 7, *out = ev + 9,
+                *fin = ev + 11;
     auto run = [&]() -> int {
         BZ_TRY(cudaEventRecord(ready, st), "collide_batch_host: record");
-        BZ_TRY(cudaStreamWaitEvent(s_in, ready, 0), "collide_batch_host: wait");
-        BZ_TRY(cudaStreamWaitEvent(s_out, ready, 0), "collide_batch_host: wait");
+        for (cudaStream_t x : {s_in, s_out, s_fwd, s_inv, s_ms[0], s_ms[1]})
+            BZ_TRY(cudaStreamWaitEvent(x, ready, 0), "collide_batch_host: wait");
         for (int64_t c = 0; c < nchunks; ++c) {
             const int i = (int)(c & 1);
             const int64_t off = bnd[c], nc = bnd[c + 1] - bnd[c];
             const size_t bytes = (size_t)nc * cell_bytes;
-            if (c >= 2) BZ_TRY(cudaStreamWaitEvent(s_in, done[i], 0), "collide_batch_host: wait");
+            int r2;
+            // host -> device once the slot's f has been transformed (chunk c - 2)
+            if (c >= 2) BZ_TRY(cudaStreamWaitEvent(s_in, fw[i], 0), "collide_batch_host: wait");
             BZ_TRY(cudaMemcpyAsync(fd[i], static_cast<const char *>(f_host) + (size_t)off * cell_bytes, bytes,
                                    cudaMemcpyHostToDevice, s_in),
                    "collide_batch_host: host to device copy");
             BZ_TRY(cudaEventRecord(in[i], s_in), "collide_batch_host: record");
-            BZ_TRY(cudaStreamWaitEvent(st, in[i], 0), "collide_batch_host: wait");
-            if (c >= 2) BZ_TRY(cudaStreamWaitEvent(st, out[i], 0), "collide_batch_host: wait");
+            // forward transform once the slot's spectrum is free (mode sum of c - 2)
+            BZ_TRY(cudaStreamWaitEvent(s_fwd, in[i], 0), "collide_batch_host: wait");
+            if (c >= 2) BZ_TRY(cudaStreamWaitEvent(s_fwd, ms[i], 0), "collide_batch_host: wait");
             if (flags & BZ_CHECK_INPUT) {
-                int r2 = check_input(precision, fd[i], nc * m->g->v.nv, st);
-                if (r2) return r2;
+                if ((r2 = check_input(precision, fd[i], nc * m->g->v.nv, s_fwd))) return r2;
             }
-            int r2 = collide_chain(m, precision, flags, fd[i], qd[i], nullptr, nc, st);
-            if (r2) return r2;
-            BZ_TRY(cudaEventRecord(done[i], st), "collide_batch_host: record");
+            if ((r2 = phase_forward(m, precision, fd[i], fh[i], nc, s_fwd))) return r2;
+            BZ_TRY(cudaEventRecord(fw[i], s_fwd), "collide_batch_host: record");
+            // mode sum once Q-hat of c - 2 has been inverse-transformed
+            BZ_TRY(cudaStreamWaitEvent(s_ms[i], fw[i], 0), "collide_batch_host: wait");
+            if (c >= 2) BZ_TRY(cudaStreamWaitEvent(s_ms[i], done[i], 0), "collide_batch_host: wait");
+            if ((r2 = phase_modesum(m, precision, fh[i], qh[i], nc, s_ms[i]))) return r2;
+            BZ_TRY(cudaEventRecord(ms[i], s_ms[i]), "collide_batch_host: record");
+            // inverse transform once Q of c - 2 has been copied back
+            BZ_TRY(cudaStreamWaitEvent(s_inv, ms[i], 0), "collide_batch_host: wait");
+            if (c >= 2) BZ_TRY(cudaStreamWaitEvent(s_inv, out[i], 0), "collide_batch_host: wait");
+            if ((r2 = phase_inverse(m, precision, flags, qh[i], qd[i], nullptr, nc, s_inv))) return r2;
+            BZ_TRY(cudaEventRecord(done[i], s_inv), "collide_batch_host: record");
             BZ_TRY(cudaStreamWaitEvent(s_out, done[i], 0), "collide_batch_host: wait");
             BZ_TRY(cudaMemcpyAsync(static_cast<char *>(Q_host) + (size_t)off * cell_bytes, qd[i], bytes,
                                    cudaMemcpyDeviceToHost, s_out),
                    "collide_batch_host: device to host copy");
             BZ_TRY(cudaEventRecord(out[i], s_out), "collide_batch_host: record");
         }
-        // the caller's stream completes after the last copies back; then the
-        // chunk buffers return to the pool in its order
-        for (int i = 0; i < 2 && i < nchunks; ++i) BZ_TRY(cudaStreamWaitEvent(st, out[i], 0), "collide_batch_host: wait");
         return BZ_OK;
     };
     rc = run();
-    if (rc) {
-        // an error part-way: let the caller's stream wait for the copies already
-        // queued on the copy streams, so the chunk buffers are not returned to
-        // the pool while a copy still uses them
-        for (int i = 0; i < 2; ++i) {
-            cudaStream_t cs2 = i ? s_out : s_in;
-            if (cudaEventRecord(ev[5 + i], cs2) == cudaSuccess) cudaStreamWaitEvent(st, ev[5 + i], 0);
+    // the caller's stream continues after every stream of the pipeline (also
+    // after an error part-way), so that the slots return to the pool only when
+    // nothing uses them
+    {
+        cudaStream_t all[kHostStreams + 2] = {s_fwd, s_inv, s_ms[0], s_ms[1], s_in, s_out};
+        for (int k = 0; k < kHostStreams + 2; ++k) {
+            cudaEvent_t e = k < kHostStreams ? fin[k] : (k == kHostStreams ? in[0] : out[0]);
+            cudaError_t x = cudaEventRecord(e, all[k]);
+            if (x == cudaSuccess) x = cudaStreamWaitEvent(st, e, 0);
+            if (x != cudaSuccess && !rc) rc = cuda_fail(x, "collide_batch_host: join");
         }
     }
-    for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < kEv; ++i) cudaEventDestroy(ev[i]);
     return rc;
 }
 
