@@ -176,11 +176,15 @@ int collide_batch(const bz_modes *m, int precision, int flags, const void *f, vo
  * The batch moves in chunks of one full wave of the handle's mode-sum kernel
  * (SM count x the cells one SM holds: 7296 cells for the 32x32 grid's
  * three 16-cell CTAs per SM on a 152-SM GPU, 32 x SM count for the fast form;
- * the first and the last chunk of a batch longer than two chunks are a
- * quarter of that, to shorten the copies that fill and drain the pipeline)
- * through two device slots taken from the library's pool: the copy of chunk c+1 to the device, the collision of
- * chunk c on `stream` and the copy of chunk c-1 back run concurrently (two
- * library-owned copy streams, ordered by events).  Asynchronous like the other
+ * a long batch starts and ends with chunks of 1/8, 1/4 and 1/2 of that, so
+ * that the copies that fill and drain the pipeline are short) through two
+ * device slots taken from the library's pool in one allocation.  The copies
+ * run on two library-owned copy streams; each chunk's forward transform,
+ * mode sum and inverse transform run on library-owned streams (the transforms
+ * at the greatest stream priority, the mode sums of even and odd chunks on
+ * two streams of the least), so that one chunk's mode sum overlaps the
+ * previous one's end; all are ordered by events and forked from and joined
+ * back to `stream`.  Asynchronous like the other
  * calls: Q_host is complete once `stream` has completed (bz_check(stream) or
  * cudaStreamSynchronize).  The copies overlap only if the host buffers are
  * page-locked (cudaHostAlloc / cudaHostRegister); pageable buffers give the
