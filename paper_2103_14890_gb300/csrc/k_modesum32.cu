@@ -735,13 +735,12 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 3 : WARPS <= 8 ? 2 : 
             if ((i & 3) == 3 || i + 1 == tk.nrows) {
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
-                    const float ax = P[r].x - Q[r].y, ay = P[r].y + Q[r].x;
-                    float sx, ex, sy, ey;
-                    two_sum(hi[r].x, ax, sx, ex);
-                    two_sum(hi[r].y, ay, sy, ey);
-                    hi[r] = make_float2(sx, sy);
-                    lo[r].x += ex;
-                    lo[r].y += ey;
+                    // (re, im) TwoSum as FP32x2 operations: the scalar ones, pairwise
+                    const float2 a = make_float2(P[r].x - Q[r].y, P[r].y + Q[r].x);
+                    float2 sm, e;
+                    two_sum2(hi[r], a, sm, e);
+                    hi[r] = sm;
+                    lo[r] = __fadd2_rn(lo[r], e);
                     P[r] = Q[r] = make_float2(0.f, 0.f);
                 }
             }
