@@ -602,16 +602,16 @@ __global__ void __launch_bounds__(WARPS * 32, 1) modesum_p2_kernel(const Mode32G
 // (w, w) pairs would make shared memory the bound).  P and Q are folded into the (hi, lo) pair of each output every
 // four rows as (P_x - Q_y, P_y + Q_x); the sums differ in rounding from the
 // scalar kernels', so the last partial wave of a batch stays on this kernel.
-template <int RR, int WS, int PH, bool RAMP>
+template <int RR, int WS, int PH, bool RAMP, int DIR>
 __device__ __forceinline__ void block_pq(float2 (&win)[2 * RR], const float2 *__restrict__ mp, int mcs,
-                                         const float2 *__restrict__ lp, int dcs, float sgn,
+                                         const float2 *__restrict__ lp, int dcs,
                                          const float *__restrict__ wb, float2 (&P)[RR], float2 (&Q)[RR]) {
 #pragma unroll
     for (int j = 0; j < (RAMP ? RR - 1 : RR); ++j) win[(j + PH * RR) & (2 * RR - 1)] = mp[j * mcs];
 #pragma unroll
     for (int s = RAMP ? 1 : 0; s < RR; ++s) {
         const float2 fl = lp[s * dcs];
-        const float fy = fl.y * sgn;
+        const float fy = DIR > 0 ? fl.y : -fl.y;       // f-hat_l conjugated for DIR < 0
         const float2 fxx = make_float2(fl.x, fl.x), fyy = make_float2(fy, fy);
         // all products U first, then the P and then the Q updates: no FMA
         // waits on the multiply issued just before it
@@ -636,19 +636,18 @@ __device__ __forceinline__ void block_pq(float2 (&win)[2 * RR], const float2 *__
 // preload, then pairs of blocks (PH 0, PH 1) and a last PH 0.  mirror: the
 // task of a reflected output block, read from the unreflected spectrum: every
 // column index is negated, so f-hat_l and the window run the other way.
-template <int RR, int WS, int CS>
+template <int RR, int WS, int CS, int DIR>
 __device__ __forceinline__ void row_pass_pq(const float2 *__restrict__ rowl, const float2 *__restrict__ rowm,
                                             const float *__restrict__ wrow, int nblk, int l2lo, int mbase0,
-                                            int dir, bool ramp, bool mirror, float2 (&P)[RR], float2 (&Q)[RR]) {
+                                            bool ramp, bool mirror, float2 (&P)[RR], float2 (&Q)[RR]) {
     float2 win[2 * RR];
-    const int dcs = (mirror ? -dir : dir) * CS;          // between consecutive l_2
+    const int dcs = (mirror ? -DIR : DIR) * CS;          // between consecutive l_2
     const int mcs = mirror ? -CS : CS;                   // between consecutive window columns
-    const float sgn = (float)dir;
     const float2 *mp = rowm + mbase0 * mcs;
     const float2 *lp = rowl + l2lo * dcs;
     int blk = 0;
     if (ramp) {
-        block_pq<RR, WS, 1, true>(win, mp, mcs, lp, dcs, sgn, wrow, P, Q);
+        block_pq<RR, WS, 1, true, DIR>(win, mp, mcs, lp, dcs, wrow, P, Q);
         mp -= RR * mcs;
         lp += RR * dcs;
         blk = 1;
@@ -657,13 +656,13 @@ __device__ __forceinline__ void row_pass_pq(const float2 *__restrict__ rowl, con
         for (int j = RR; j < 2 * RR - 1; ++j) win[j] = mp[j * mcs];
     }
     for (; blk + 1 < nblk; blk += 2) {
-        block_pq<RR, WS, 0, false>(win, mp, mcs, lp, dcs, sgn, wrow + blk * RR * WS, P, Q);
-        block_pq<RR, WS, 1, false>(win, mp - RR * mcs, mcs, lp + RR * dcs, dcs, sgn, wrow + (blk + 1) * RR * WS, P,
-                                   Q);
+        block_pq<RR, WS, 0, false, DIR>(win, mp, mcs, lp, dcs, wrow + blk * RR * WS, P, Q);
+        block_pq<RR, WS, 1, false, DIR>(win, mp - RR * mcs, mcs, lp + RR * dcs, dcs, wrow + (blk + 1) * RR * WS, P,
+                                        Q);
         mp -= 2 * RR * mcs;
         lp += 2 * RR * dcs;
     }
-    if (blk < nblk) block_pq<RR, WS, 0, false>(win, mp, mcs, lp, dcs, sgn, wrow + blk * RR * WS, P, Q);
+    if (blk < nblk) block_pq<RR, WS, 0, false, DIR>(win, mp, mcs, lp, dcs, wrow + blk * RR * WS, P, Q);
 }
 
 // CELLS = 32: one cell per lane; reflected blocks are separate tasks (read
@@ -729,8 +728,12 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 3 : WARPS <= 8 ? 2 : 
             }
             __syncwarp();
             const int4 hd = *reinterpret_cast<const int4 *>(wcur);
-            row_pass_pq<RR, WS, CELLS>(F0 + hd.x, F0 + hd.y, wcur + HEAD, tk.nblk, tk.l2lo, mbase0,
-                                       hd.z > 0 ? 1 : -1, ramp, mirror, P, Q);
+            if (hd.z > 0)
+                row_pass_pq<RR, WS, CELLS, 1>(F0 + hd.x, F0 + hd.y, wcur + HEAD, tk.nblk, tk.l2lo, mbase0, ramp,
+                                              mirror, P, Q);
+            else
+                row_pass_pq<RR, WS, CELLS, -1>(F0 + hd.x, F0 + hd.y, wcur + HEAD, tk.nblk, tk.l2lo, mbase0, ramp,
+                                               mirror, P, Q);
             __syncwarp();
             if ((i & 3) == 3 || i + 1 == tk.nrows) {
 #pragma unroll
@@ -1523,7 +1526,7 @@ cudaError_t launch_modesum32_group(const bz_modes *const *ms, const float2 *cons
 // ---- autotuner ------------------------------------------------------------
 // Times every buildable variant once per (dimension, N, SM count) on a
 // synthetic batch (zero spectra: the kernel's cost does not depend on the
-// values) of two 32-cell tiles per SM and keeps the fastest.  Results are
+// values) of twelve 32-cell tiles per SM and keeps the fastest.  Results are
 // cached for the process and, when BZ_TUNE_CACHE names a file, in that file as
 // lines "dim N sms variant" (variant = index + 1).
 static std::mutex g_tune_mu;
@@ -1578,9 +1581,10 @@ static int autotune(bz_modes *m, int &rc) {
     if (it != g_tune.end())
         for (int q = 0; q < na; ++q)
             if (avail[q] == it->second) return avail[q];
-    // six 32-cell tiles per SM (several waves, so the tail does not decide);
-    // two rounds over the variants, best of three launches each
-    const int64_t n = (int64_t)6 * sms * 32;
+    // twelve 32-cell tiles per SM (several waves of every variant, so that
+    // neither the tail nor a single wave decides); two rounds over the
+    // variants, best of three launches each
+    const int64_t n = (int64_t)12 * sms * 32;
     const size_t bytes = 2 * sizeof(float2) * (size_t)((n + 31) / 32) * gv.nhalf * 32;
     void *buf = nullptr;
     cudaError_t e = dev_malloc(&buf, bytes);
