@@ -236,8 +236,8 @@ int modesum32_wave_cells_per_sm(const bz_modes *m);
 // Whether the handle's FP32 mode sum splits the tiles of a partial wave over
 // several CTAs (32-cell variants chosen by timing).
 bool modesum32_tail_splits(const bz_modes *m);
-// Whether batches of up to one and a half waves run on a one-CTA-per-SM
-// sibling of the handle's variant (bit-identical results, no single-wave loss).
+// Whether batches of at most half a wave run on a one-CTA-per-SM sibling of
+// the handle's variant (bit-identical results).
 bool modesum32_small_batches_fast(const bz_modes *m);
 bool modesum64_available(const bz_modes *m);
 cudaError_t launch_modesum64(const bz_modes *m, const double2 *fhat, double2 *Qhat, int64_t n, cudaStream_t st);

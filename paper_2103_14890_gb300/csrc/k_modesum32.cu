@@ -1426,15 +1426,15 @@ bool modesum32_tail_splits(const bz_modes *m) {
            m->var_task_split[m->variant][0] != nullptr;
 }
 
-// A variant that holds several CTAs per SM loses about a sixth of a wave when a
-// launch is a single wave (all CTAs stage their spectra at once and the SMs
-// empty unevenly at the end).  Its sibling with one 16-warp CTA per SM runs
-// the same tasks in the same order (bit-identical results) and has no such
-// loss, so launches of up to one and a half waves take the sibling.
+// A variant that holds several CTAs per SM fills only part of each SM in a
+// launch of less than half a wave (and a lone wave loses about a sixth: all
+// CTAs stage their spectra at once and the SMs empty unevenly).  Its sibling
+// with one 16-warp CTA per SM runs the same tasks in the same order
+// (bit-identical results), so launches of at most half a wave take it.
 static int small_batch_variant(const bz_modes *m, int64_t n) {
     const int v = m->variant;
     if (m->variant_fixed || variant_ctas_per_sm(v) == 1) return v;
-    if (n > (int64_t)sm_count() * variant_ctas_per_sm(v) * kVariants[v].cells * 3 / 2) return v;
+    if (n > (int64_t)sm_count() * variant_ctas_per_sm(v) * kVariants[v].cells / 2) return v;
     for (int s = 0; s < kNumVariants; ++s) {
         const Variant &a = kVariants[s], &b = kVariants[v];
         if (s != v && m->var_W[s] && variant_ctas_per_sm(s) == 1 && a.R == b.R && a.cells == b.cells &&
