@@ -142,6 +142,46 @@ __device__ __forceinline__ void fft_nat(V (&a)[L]) {
     }
 }
 
+// fft_nat of length L = 3Q for input whose middle third a[Q .. 2Q-1] is zero
+// (a spectrum of modes |k| < L/3 zero-padded to L: the indices k and L - |k|
+// occupy the first and last thirds only).  The first stage's 3-point DFTs
+// then take two inputs: the sums with the zero third are left out.
+template <int L, int SIGN, typename V>
+__device__ __forceinline__ void fft_nat_mid0(V (&a)[L]) {
+    using S = decltype(V::x);
+    using V2 = V;
+    static_assert(L % 3 == 0 && (L <= 48 || L == 72), "length 3 * 2^p <= 48 or 72");
+    constexpr int Q = L / 3;
+    constexpr S kS3 = (S)0.866025403784438647;    // sqrt(3) / 2
+    V2 y0[Q], y1[Q], y2[Q];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) {
+        const V2 p = a[n2], r = a[2 * Q + n2];
+        y0[n2] = c_add(p, r);
+        const V2 mq = cmk<V2>(p.x - (S)0.5 * r.x, p.y - (S)0.5 * r.y);
+        // the 3-point DFT's +/- i (sqrt3/2)(q - r) with q = 0
+        const V2 iq = SIGN < 0 ? cmk<V2>(-kS3 * r.y, kS3 * r.x) : cmk<V2>(kS3 * r.y, -kS3 * r.x);
+        V2 u1 = c_add(mq, iq), u2 = c_sub(mq, iq);
+        if (n2 > 0) {
+            const V w1 = twl<L, V>(n2), w2 = twl<L, V>(2 * n2);
+            const S w1y = SIGN < 0 ? w1.y : -w1.y, w2y = SIGN < 0 ? w2.y : -w2.y;
+            u1 = cmk<V2>(u1.x * w1.x - u1.y * w1y, u1.x * w1y + u1.y * w1.x);
+            u2 = cmk<V2>(u2.x * w2.x - u2.y * w2y, u2.x * w2y + u2.y * w2.x);
+        }
+        y1[n2] = u1;
+        y2[n2] = u2;
+    }
+    fft_nat<Q, SIGN>(y0);
+    fft_nat<Q, SIGN>(y1);
+    fft_nat<Q, SIGN>(y2);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) {
+        a[3 * k2] = y0[k2];
+        a[3 * k2 + 1] = y1[k2];
+        a[3 * k2 + 2] = y2[k2];
+    }
+}
+
 // e^{-2 pi i k / N} for N in {16, 24, 32, 48}
 template <int N, typename V> __device__ __forceinline__ V tw(int k) {
     if constexpr (N == 16 || N == 32) return tw32<V>(k * (32 / N));

@@ -89,6 +89,7 @@ fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>:
     using S = T;
     using Sh = FastShape<T, N>;
     constexpr int H = Sh::H, M = Sh::M, P = Sh::P, C = Sh::C, TS = Sh::TS;
+    static_assert(3 * H < P && P % 3 == 0, "the padded modes fill the middle third of every transform");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2 *Y = reinterpret_cast<V2 *>(smem_raw);     // pass A/B: [P][M][C]; pass C/D: [H+1][TS]
     V2 *F = Y + Sh::nY;                           // half spectrum [H+1][M][C]
@@ -136,7 +137,7 @@ fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>:
                     a[(k2 + P) % P] = cmk<V2>(w.x * fv.x - w.y * fv.y, w.x * fv.y + w.y * fv.x);
                 }
             }
-            fft_nat<P, +1>(a);
+            fft_nat_mid0<P, +1>(a);            // k2 in [-H, H]: the middle third is padding
 #pragma unroll
             for (int j2 = 0; j2 < P; ++j2) Y[(j2 * M + k1 + H) * C + c] = a[j2];
         }
@@ -150,7 +151,7 @@ fast_collide_kernel(const typename C2<T>::type *__restrict__ fh, typename C2<T>:
             for (int j = 0; j < P; ++j) b[j] = cmk<V2>((S)0., (S)0.);
 #pragma unroll
             for (int k1 = -H; k1 <= H; ++k1) b[(k1 + P) % P] = Y[(j2 * M + k1 + H) * C + c];
-            fft_nat<P, +1>(b);
+            fft_nat_mid0<P, +1>(b);            // k1 in [-H, H]: the middle third is padding
             S *g = G + j2 * C + c;
             if (p == 0) {
 #pragma unroll
