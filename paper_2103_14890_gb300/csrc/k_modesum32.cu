@@ -1046,6 +1046,9 @@ static bool build_variant(bz_modes *m, int v, int &rc, void **outW, int **outT, 
     const bool reflect = sizeof(T) == 4 && variant_reflects(v, h);
     const bool ramped = reflect && G == 1 && (h + 1) % R == 0;
     const bool twins = reflect && kVariants[v].orient == 1;   // paired orientations need no reflected tasks
+    // paired orientations compute k_2 < 0 in the mirrored half of every task:
+    // only with blocks of k_2 >= 0 (else both halves would write one output)
+    if (kVariants[v].orient == 2 && !reflect) return false;
     const int nmid = (d == 3) ? M : 1;                      // values of the middle index (3-D)
     struct Pair { int l[2], m[2]; };                         // leading indices of l and m
     for (int k1 = 0; k1 <= h; ++k1) {

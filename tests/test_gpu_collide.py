@@ -78,8 +78,8 @@ def test_fast_kernels_selected(bz):
 
 
 @pytest.mark.parametrize("dim,N,variant", [(2, N, v) for N in (16, 24, 32) for v in (1, 2, 3, 5, 6, 7, 8, 9, 10)]
-                         + [(2, 16, 4), (3, 8, 1), (3, 8, 2), (3, 8, 3), (3, 8, 5), (3, 8, 6), (3, 8, 7), (3, 8, 8),
-                            (3, 8, 9), (3, 8, 10), (2, 48, 3), (2, 48, 8), (2, 48, 9), (2, 48, 10)])
+                         + [(2, 16, 4), (3, 8, 1), (3, 8, 2), (3, 8, 3), (3, 8, 5), (3, 8, 6), (3, 8, 7),
+                            (2, 48, 3), (2, 48, 8), (2, 48, 9), (2, 48, 10)])
 def test_fp32_each_kernel_variant(bz, oracle_k, monkeypatch, dim, N, variant):
     """Every register-blocked variant (fixed through BZ_MODESUM_VARIANT, bypassing
     the autotuner) against the oracle: 70 cells = 2 full tiles and a ragged tail."""
@@ -122,6 +122,17 @@ assert np.array_equal(Q[:sms * 32], Qa)
 assert np.array_equal(Q[sms * 32:], Qb)
 print("ok")
 """
+
+
+def test_paired_variants_need_half_row_blocks(bz, monkeypatch):
+    """The paired-orientation variants (8, 9, 10) compute k_2 < 0 in the
+    mirrored half of each task, which needs output blocks of k_2 >= 0 only
+    (8 outputs <= h + 1): on 8^3 (h = 3) they are not built and a request for
+    one falls back to the autotuner's choice."""
+    for v in (8, 9, 10):
+        monkeypatch.setenv("BZ_MODESUM_VARIANT", str(v))
+        assert bz.Modes(bz.Grid(3, 8, 8.0), 1.0).modesum_variant not in (8, 9, 10)
+        assert bz.Modes(bz.Grid(2, 16, 8.0), 1.0).modesum_variant == v
 
 
 @pytest.mark.parametrize("variant", [1, 7])
