@@ -112,6 +112,7 @@ constexpr int kFvMaxFaces = 8;
 constexpr int kFvCentral = 5;       // central stencil: the cell and its 5 nearest cells (2 x 3 cells)
 constexpr int kFvCentral3 = 11;     // degree 2: the cell and its 11 nearest cells (2 x 6 cells)
 constexpr int kFvCoef3 = 5;         // degree 2: coefficients of xi, eta, xi^2, xi eta, eta^2
+constexpr int kFvRegularTri = 0x100;  // flag in ncen: a triangle whose stencil starts with its 3 face neighbours
 
 template <typename T> struct FvTables {
     const T *inv_area;      // [cell]
@@ -140,7 +141,8 @@ struct bz_mesh {
     int max_faces;
     int *d_nface;           // [cell] faces
     int *d_nb;              // [cell][face] neighbour, -1 boundary
-    int *d_ncen;            // [cell] central stencil size (<= kFvCentral)
+    int *d_ncen;            // [cell] central stencil size (<= kFvCentral), | kFvRegularTri for a triangle
+                            // whose stencil starts with its face neighbours, sector s on faces s, s+1
     int *d_cen;             // [cell][kFvCentral]
     int *d_nsec;            // [cell] sectors
     int *d_sec;             // [cell][face][2] sector cells

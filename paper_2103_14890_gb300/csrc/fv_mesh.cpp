@@ -466,6 +466,46 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
                 ++ns;
             }
             h.nsec[i] = ns;
+            // A triangle with three sectors whose face neighbours all lie in
+            // its central stencil (nearly every interior cell of a triangle
+            // mesh): the stencil is reordered to start with the face
+            // neighbours in face order and the cell is flagged, so that the
+            // FP32 reconstruction loads every neighbour row once for the
+            // central and the sector gradients (sector s joins faces s and
+            // s + 1 mod 3).
+            if (k == 3 && ns == 3 && nc == kFvCentral) {
+                int perm[kFvCentral];
+                bool used[kFvCentral] = {};
+                bool ok = true;
+                for (int q = 0; q < 3 && ok; ++q) {
+                    const int j = h.nb[(size_t)i * kFvMaxFaces + q];
+                    int hit = -1;
+                    for (int t = 0; t < nc && hit < 0; ++t)
+                        if (!used[t] && h.cen[i * kFvCentral + t] == j) hit = t;
+                    ok = hit >= 0;
+                    if (ok) {
+                        used[hit] = true;
+                        perm[q] = hit;
+                    }
+                }
+                if (ok) {
+                    for (int t = 0, p = 3; t < nc; ++t)
+                        if (!used[t]) perm[p++] = t;
+                    int c0[kFvCentral];
+                    double r0[2][kFvCentral];
+                    for (int t = 0; t < nc; ++t) {
+                        c0[t] = h.cen[i * kFvCentral + t];
+                        r0[0][t] = h.Rc[(i * 2 + 0) * kFvCentral + t];
+                        r0[1][t] = h.Rc[(i * 2 + 1) * kFvCentral + t];
+                    }
+                    for (int t = 0; t < nc; ++t) {
+                        h.cen[i * kFvCentral + t] = c0[perm[t]];
+                        h.Rc[(i * 2 + 0) * kFvCentral + t] = r0[0][perm[t]];
+                        h.Rc[(i * 2 + 1) * kFvCentral + t] = r0[1][perm[t]];
+                    }
+                    h.ncen[i] = nc | kFvRegularTri;
+                }
+            }
         }
     }
     if (order == 3) {

@@ -67,6 +67,110 @@ __device__ __forceinline__ void stv(T *__restrict__ p, const Vec<T, VEC> &r) {
     }
 }
 
+// FP32x2 arithmetic on pairs of velocities: one FADD2 / FMUL2 / FFMA2 rounds
+// each lane as its scalar instruction does.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 lo2(const float4 &a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(const float4 &a) { return make_float2(a.z, a.w); }
+// approximate reciprocal (1 ulp; the argument is a normal number here)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp_approx(a.x), rcp_approx(a.y)); }
+
+// CWENO gradient of one pair of velocities of a flagged triangle (kFvRegularTri):
+// d[q] = fbar_{cen q} - fbar_i, the face neighbours in d[0..2]; sector s
+// joins faces s and s + 1 mod 3.  The steps are those of the generic kernel
+// below (central gradient, sector gradients, g_0, smoothness, weights as
+// lambda_s ((sigma_min + eps) / (sigma_s + eps))^4, normalised sum).
+__device__ __forceinline__ void cweno_pair_tri(const float2 (&d)[kFvCentral], const float (&rx)[kFvCentral],
+                                               const float (&ry)[kFvCentral], const float4 (&R)[3], float h2,
+                                               float2 &gx_out, float2 &gy_out) {
+    constexpr float kLam0 = 0.75f, kInvLam0 = (float)(4.0 / 3.0), kEps = 1e-14f;
+    const float lamL = 0.25f / 3.0f;
+    float2 gx = mul2(dup2(rx[0]), d[0]), gy = mul2(dup2(ry[0]), d[0]);
+#pragma unroll
+    for (int q = 1; q < kFvCentral; ++q) {
+        gx = fma2(dup2(rx[q]), d[q], gx);
+        gy = fma2(dup2(ry[q]), d[q], gy);
+    }
+    float2 sx[3], sy[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const float2 da = d[s], db = d[(s + 1) % 3];
+        sx[s] = fma2(dup2(R[s].x), da, mul2(dup2(R[s].y), db));
+        sy[s] = fma2(dup2(R[s].z), da, mul2(dup2(R[s].w), db));
+    }
+    const float2 sumx = add2(add2(sx[0], sx[1]), sx[2]), sumy = add2(add2(sy[0], sy[1]), sy[2]);
+    const float2 g0x = mul2(fma2(dup2(-lamL), sumx, gx), dup2(kInvLam0));
+    const float2 g0y = mul2(fma2(dup2(-lamL), sumy, gy), dup2(kInvLam0));
+    const float2 H = dup2(h2), E = dup2(kEps);
+    const float2 sig0 = mul2(H, fma2(g0x, g0x, mul2(g0y, g0y)));
+    float2 sig[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) sig[s] = mul2(H, fma2(sx[s], sx[s], mul2(sy[s], sy[s])));
+    const float2 smin = make_float2(fminf(fminf(sig0.x, sig[0].x), fminf(sig[1].x, sig[2].x)),
+                                    fminf(fminf(sig0.y, sig[0].y), fminf(sig[1].y, sig[2].y)));
+    const float2 num = add2(smin, E);
+    float2 r = mul2(num, rcp2(add2(sig0, E)));
+    r = mul2(r, r);
+    float2 w = mul2(dup2(kLam0), mul2(r, r));
+    float2 wsum = w, ax = mul2(w, g0x), ay = mul2(w, g0y);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        r = mul2(num, rcp2(add2(sig[s], E)));
+        r = mul2(r, r);
+        w = mul2(dup2(lamL), mul2(r, r));
+        wsum = add2(wsum, w);
+        ax = fma2(w, sx[s], ax);
+        ay = fma2(w, sy[s], ay);
+    }
+    const float2 iw = rcp2(wsum);
+    gx_out = mul2(ax, iw);
+    gy_out = mul2(ay, iw);
+}
+
+// Gradient of the 4 velocities k..k+3 of a flagged triangle in FP32x2: six
+// rows of f (the cell and its stencil, the face neighbours first), each
+// loaded once.
+__device__ __forceinline__ void gradient_tri_x2(const float *__restrict__ f, float *__restrict__ G,
+                                                const FvTables<float> &tb, const int *__restrict__ cen, int64_t i,
+                                                int k, int nv, const float4 fi) {
+    float4 fr[kFvCentral];
+#pragma unroll
+    for (int q = 0; q < kFvCentral; ++q) {
+        const int j = __ldg(cen + i * kFvCentral + q);
+        fr[q] = *reinterpret_cast<const float4 *>(f + (int64_t)j * nv + k);
+    }
+    float rx[kFvCentral], ry[kFvCentral];
+#pragma unroll
+    for (int q = 0; q < kFvCentral; ++q) {
+        rx[q] = __ldg(tb.Rc + (i * 2) * kFvCentral + q);
+        ry[q] = __ldg(tb.Rc + (i * 2 + 1) * kFvCentral + q);
+    }
+    float4 R[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) R[s] = __ldg(reinterpret_cast<const float4 *>(tb.Rs + (i * kFvMaxFaces + s) * 4));
+    const float h2 = __ldg(tb.h2 + i);
+    float2 gx[2], gy[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const float2 nf = neg2(p == 0 ? lo2(fi) : hi2(fi));
+        float2 d[kFvCentral];
+#pragma unroll
+        for (int q = 0; q < kFvCentral; ++q) d[q] = add2(p == 0 ? lo2(fr[q]) : hi2(fr[q]), nf);
+        cweno_pair_tri(d, rx, ry, R, h2, gx[p], gy[p]);
+    }
+    *reinterpret_cast<float4 *>(G + (i * 2) * nv + k) = make_float4(gx[0].x, gx[0].y, gx[1].x, gx[1].y);
+    *reinterpret_cast<float4 *>(G + (i * 2 + 1) * nv + k) = make_float4(gy[0].x, gy[0].y, gy[1].x, gy[1].y);
+}
+
 // MAXS / MAXF: compile-time bound on the sectors / faces of a cell (3 for
 // triangle meshes, kFvMaxFaces otherwise).  Every loop over them is unrolled
 // with a predicate, so all neighbour rows of a cell are requested before the
@@ -80,7 +184,14 @@ fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, c
     const int k = (blockIdx.y * kFvThreads + threadIdx.x) * VEC;
     if (k >= nv) return;
     const Vec<T, VEC> fi = ldv<T, VEC>(f + i * nv + k);
-    const int nc = __ldg(ncen + i), ns = __ldg(nsec + i);
+    const int ncf = __ldg(ncen + i);
+    if constexpr (sizeof(T) == 4 && VEC == 4 && MAXS == 3) {
+        if (ncf & kFvRegularTri) {      // uniform over the block: one cell per block
+            gradient_tri_x2(f, G, tb, cen, i, k, nv, make_float4(fi.v[0], fi.v[1], fi.v[2], fi.v[3]));
+            return;
+        }
+    }
+    const int nc = ncf & (kFvRegularTri - 1), ns = __ldg(nsec + i);
     // central least-squares gradient
     T gx[VEC], gy[VEC];
     {
@@ -248,17 +359,44 @@ fv_flux_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__
             ojx = __ldg(tb.off_j + 2 * s);
             ojy = __ldg(tb.off_j + 2 * s + 1);
         }
+        if constexpr (sizeof(T) == 4 && VEC == 4) {
+            // the same face flux on pairs of velocities in FP32x2
+            const float2 v1nx = dup2(v1 * nx), hf = dup2(0.5f);
 #pragma unroll
-        for (int u = 0; u < VEC; ++u) {
-            const T vn = v1 * nx + v2[u] * ny;
-            T fl = fi.v[u];
-            if (kGrad) fl += gxi.v[u] * oix + gyi.v[u] * oiy;
-            T fr = fl;
-            if (jn[q] >= 0) {
-                fr = fj[q].v[u];
-                if (kGrad) fr += gxj[q].v[u] * ojx + gyj[q].v[u] * ojy;
+            for (int p = 0; p < 2; ++p) {
+                const int u = 2 * p;
+                const float2 vn = fma2(make_float2(v2[u], v2[u + 1]), dup2(ny), v1nx);
+                float2 fl = make_float2(fi.v[u], fi.v[u + 1]);
+                if (kGrad)
+                    fl = fma2(make_float2(gyi.v[u], gyi.v[u + 1]), dup2(oiy),
+                              fma2(make_float2(gxi.v[u], gxi.v[u + 1]), dup2(oix), fl));
+                float2 fr = fl;
+                if (jn[q] >= 0) {
+                    fr = make_float2(fj[q].v[u], fj[q].v[u + 1]);
+                    if (kGrad)
+                        fr = fma2(make_float2(gyj[q].v[u], gyj[q].v[u + 1]), dup2(ojy),
+                                  fma2(make_float2(gxj[q].v[u], gxj[q].v[u + 1]), dup2(ojx), fr));
+                }
+                const float2 h = mul2(hf, vn), nah = make_float2(-fabsf(h.x), -fabsf(h.y));
+                float2 a = make_float2(acc[u], acc[u + 1]);
+                a = fma2(h, add2(fl, fr), a);
+                a = fma2(nah, add2(fr, neg2(fl)), a);
+                acc[u] = a.x;
+                acc[u + 1] = a.y;
             }
-            acc[u] += (T)0.5 * vn * (fl + fr) - (T)0.5 * fabs(vn) * (fr - fl);
+        } else {
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) {
+                const T vn = v1 * nx + v2[u] * ny;
+                T fl = fi.v[u];
+                if (kGrad) fl += gxi.v[u] * oix + gyi.v[u] * oiy;
+                T fr = fl;
+                if (jn[q] >= 0) {
+                    fr = fj[q].v[u];
+                    if (kGrad) fr += gxj[q].v[u] * ojx + gyj[q].v[u] * ojy;
+                }
+                acc[u] += (T)0.5 * vn * (fl + fr) - (T)0.5 * fabs(vn) * (fr - fl);
+            }
         }
     }
     const T ia = __ldg(tb.inv_area + i);
