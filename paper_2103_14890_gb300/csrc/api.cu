@@ -363,7 +363,9 @@ int collide_chain(const bz_modes *m, int precision, int flags, const void *f, vo
 // scratch (`ext` if given: transport_scratch_bytes), then the fluxes.
 size_t transport_scratch_bytes(const bz_mesh *mesh, const bz_grid *g, int precision) {
     if (mesh->order == 1) return 0;
-    const size_t per = mesh->order == 3 ? (size_t)kFvCoef3 : 2;     // coefficients per (cell, velocity)
+    // values per (cell, velocity): 5 coefficients, 3 face values (FP32 triangles without walls) or 2 gradients
+    const bool faces = precision == BZ_FP32 && mesh->max_faces <= 3 && mesh->n_walls == 0;
+    const size_t per = mesh->order == 3 ? (size_t)kFvCoef3 : faces ? 3 : 2;
     return per * mesh->n_cells * g->v.nv * (precision == BZ_FP64 ? sizeof(double) : sizeof(float));
 }
 
@@ -399,6 +401,15 @@ int transport_chain(const bz_mesh *mesh, const bz_grid *g, int precision, const 
     if (mesh->order == 2) {
         if (!ext) BZ_TRY(s.alloc(transport_scratch_bytes(mesh, g, precision), st), "transport: scratch");
         G = ext ? ext : s.p;
+        if (precision == BZ_FP32 && fv_face_mode(mesh, v, f, L, G)) {
+            BZ_LAUNCH("fv_gradient_f32", st,
+                      launch_fv_faces_f32(mesh, v, static_cast<const float *>(f), static_cast<float *>(G), st),
+                      "transport: reconstruction");
+            BZ_LAUNCH("fv_flux_f32", st,
+                      launch_fv_flux_faces_f32(mesh, v, static_cast<const float *>(G), static_cast<float *>(L), st),
+                      "transport: fluxes");
+            return BZ_OK;
+        }
         if (precision == BZ_FP64)
             BZ_LAUNCH("fv_gradient_f64", st,
                       launch_fv_gradient_f64(mesh, v, static_cast<const double *>(f), static_cast<double *>(G), st),

@@ -141,6 +141,7 @@ struct bz_mesh {
     int max_faces;
     int *d_nface;           // [cell] faces
     int *d_nb;              // [cell][face] neighbour, -1 boundary
+    int *d_nbq;             // [cell][face] the neighbour's index of the same face, -1 boundary
     int *d_ncen;            // [cell] central stencil size (<= kFvCentral), | kFvRegularTri for a triangle
                             // whose stencil starts with its face neighbours, sector s on faces s, s+1
     int *d_cen;             // [cell][kFvCentral]
@@ -299,6 +300,14 @@ cudaError_t launch_fv_flux_f64(const bz_mesh *mesh, const GridView &g, const dou
                                cudaStream_t st);
 // walls need one CTA to hold all velocities of a cell
 bool fv_walls_supported(const bz_mesh *mesh, const GridView &g);
+// FP32 triangle meshes without walls (N divisible by 4, 16-byte aligned rows):
+// the reconstruction writes each cell's values at its three face midpoints,
+// FV [cell][3][nv], and the flux pass reads those of the cell and of its
+// neighbours (the neighbour's face index from the mesh's nbq table).
+bool fv_face_mode(const bz_mesh *mesh, const GridView &g, const void *f, const void *L, const void *FV);
+cudaError_t launch_fv_faces_f32(const bz_mesh *mesh, const GridView &g, const float *f, float *FV, cudaStream_t st);
+cudaError_t launch_fv_flux_faces_f32(const bz_mesh *mesh, const GridView &g, const float *FV, float *L,
+                                     cudaStream_t st);
 // order 3: coefficients C [cell][5][nv] of the degree-2 CWENO polynomial, then
 // the fluxes at two Gauss points per face
 cudaError_t launch_fv_coef3_f64(const bz_mesh *mesh, const GridView &g, const double *f, double *C,

@@ -43,7 +43,7 @@ namespace {
 
 struct HostMesh {
     int64_t n = 0;
-    std::vector<int> nface, nb, ncen, cen, nsec, sec, order;
+    std::vector<int> nface, nb, nbq, ncen, cen, nsec, sec, order;
     std::vector<double> inv_area, h2, fn, off_i, off_j, Rc, Rs;
     // order 3
     std::vector<int> ncen3, cen3;
@@ -164,6 +164,7 @@ void fv_mesh_destroy(bz_mesh *m) {
     if (!m) return;
     dev_free(m->d_nface);
     dev_free(m->d_nb);
+    dev_free(m->d_nbq);
     dev_free(m->d_ncen);
     dev_free(m->d_cen);
     dev_free(m->d_nsec);
@@ -279,6 +280,7 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
     }
     h.nface.assign(n, 0);
     h.nb.assign(n * kFvMaxFaces, -1);
+    h.nbq.assign(n * kFvMaxFaces, -1);
     h.fn.assign(n * kFvMaxFaces * 2, 0.0);
     h.off_i.assign(n * kFvMaxFaces * 2, 0.0);
     h.off_j.assign(n * kFvMaxFaces * 2, 0.0);
@@ -307,6 +309,8 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
                 fsx[s] = kx * Lx;
                 fsy[s] = ky * Ly;
                 h.nb[s] = (int)j;
+                for (size_t t = 0; t < cells[j].size(); ++t)     // j's face starting at its copy of b
+                    if (cells[j][t] == wb) h.nbq[s] = (int)t;
                 h.off_j[2 * s] = mx - fsx[s] - bx[j];
                 h.off_j[2 * s + 1] = my - fsy[s] - by[j];
                 ++interior;
@@ -581,6 +585,7 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
     for (size_t q = 0; q < real.size(); ++q) real32[q] = (float)real[q];
     cudaError_t e = upload(&m->d_nface, h.nface);
     if (e == cudaSuccess) e = upload(&m->d_nb, h.nb);
+    if (e == cudaSuccess) e = upload(&m->d_nbq, h.nbq);
     if (e == cudaSuccess) e = upload(&m->d_ncen, h.ncen);
     if (e == cudaSuccess) e = upload(&m->d_cen, h.cen);
     if (e == cudaSuccess) e = upload(&m->d_nsec, h.nsec);

@@ -138,7 +138,10 @@ __device__ __forceinline__ void cweno_pair_tri(const float2 (&d)[kFvCentral], co
 
 // Gradient of the 4 velocities k..k+3 of a flagged triangle in FP32x2: six
 // rows of f (the cell and its stencil, the face neighbours first), each
-// loaded once.
+// loaded once.  FACE: the output is the reconstruction's value at the three
+// face midpoints, f_i + g . (x_f - x_b,i), rows [cell][face][nv], in place of
+// the gradient rows [cell][2][nv].
+template <bool FACE>
 __device__ __forceinline__ void gradient_tri_x2(const float *__restrict__ f, float *__restrict__ G,
                                                 const FvTables<float> &tb, const int *__restrict__ cen, int64_t i,
                                                 int k, int nv, const float4 fi) {
@@ -167,15 +170,26 @@ __device__ __forceinline__ void gradient_tri_x2(const float *__restrict__ f, flo
         for (int q = 0; q < kFvCentral; ++q) d[q] = add2(p == 0 ? lo2(fr[q]) : hi2(fr[q]), nf);
         cweno_pair_tri(d, rx, ry, R, h2, gx[p], gy[p]);
     }
-    *reinterpret_cast<float4 *>(G + (i * 2) * nv + k) = make_float4(gx[0].x, gx[0].y, gx[1].x, gx[1].y);
-    *reinterpret_cast<float4 *>(G + (i * 2 + 1) * nv + k) = make_float4(gy[0].x, gy[0].y, gy[1].x, gy[1].y);
+    if constexpr (FACE) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float2 ox = dup2(__ldg(tb.off_i + 2 * (i * kFvMaxFaces + q)));
+            const float2 oy = dup2(__ldg(tb.off_i + 2 * (i * kFvMaxFaces + q) + 1));
+            const float2 a = fma2(gy[0], oy, fma2(gx[0], ox, lo2(fi)));
+            const float2 b = fma2(gy[1], oy, fma2(gx[1], ox, hi2(fi)));
+            *reinterpret_cast<float4 *>(G + (i * 3 + q) * nv + k) = make_float4(a.x, a.y, b.x, b.y);
+        }
+    } else {
+        *reinterpret_cast<float4 *>(G + (i * 2) * nv + k) = make_float4(gx[0].x, gx[0].y, gx[1].x, gx[1].y);
+        *reinterpret_cast<float4 *>(G + (i * 2 + 1) * nv + k) = make_float4(gy[0].x, gy[0].y, gy[1].x, gy[1].y);
+    }
 }
 
 // MAXS / MAXF: compile-time bound on the sectors / faces of a cell (3 for
 // triangle meshes, kFvMaxFaces otherwise).  Every loop over them is unrolled
 // with a predicate, so all neighbour rows of a cell are requested before the
 // first one is used (the kernels are latency-bound otherwise).
-template <typename T, int VEC, int MAXS>
+template <typename T, int VEC, int MAXS, bool FACE = false>
 __global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4) ? 4 : 1)
 fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, const int *__restrict__ ncen,
                    const int *__restrict__ cen, const int *__restrict__ nsec, const int *__restrict__ sec,
@@ -187,7 +201,7 @@ fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, c
     const int ncf = __ldg(ncen + i);
     if constexpr (sizeof(T) == 4 && VEC == 4 && MAXS == 3) {
         if (ncf & kFvRegularTri) {      // uniform over the block: one cell per block
-            gradient_tri_x2(f, G, tb, cen, i, k, nv, make_float4(fi.v[0], fi.v[1], fi.v[2], fi.v[3]));
+            gradient_tri_x2<FACE>(f, G, tb, cen, i, k, nv, make_float4(fi.v[0], fi.v[1], fi.v[2], fi.v[3]));
             return;
         }
     }
@@ -293,14 +307,26 @@ fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, c
             gy[u] = ay * iw;
         }
     }
-    Vec<T, VEC> ox, oy;
+    if constexpr (FACE) {
+        static_assert(MAXS == 3, "face values: triangle meshes");
 #pragma unroll
-    for (int u = 0; u < VEC; ++u) {
-        ox.v[u] = gx[u];
-        oy.v[u] = gy[u];
+        for (int q = 0; q < 3; ++q) {
+            const T ofx = __ldg(tb.off_i + 2 * (i * kFvMaxFaces + q)), ofy = __ldg(tb.off_i + 2 * (i * kFvMaxFaces + q) + 1);
+            Vec<T, VEC> o;
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) o.v[u] = fi.v[u] + gx[u] * ofx + gy[u] * ofy;
+            stv<T, VEC>(G + (i * 3 + q) * nv + k, o);
+        }
+    } else {
+        Vec<T, VEC> ox, oy;
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+            ox.v[u] = gx[u];
+            oy.v[u] = gy[u];
+        }
+        stv<T, VEC>(G + (i * 2) * nv + k, ox);
+        stv<T, VEC>(G + (i * 2 + 1) * nv + k, oy);
     }
-    stv<T, VEC>(G + (i * 2) * nv + k, ox);
-    stv<T, VEC>(G + (i * 2 + 1) * nv + k, oy);
 }
 
 template <typename T, bool kGrad, int VEC, int MAXF>
@@ -404,6 +430,59 @@ fv_flux_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__
 #pragma unroll
     for (int u = 0; u < VEC; ++u) o.v[u] = acc[u] * ia;
     stv<T, VEC>(L + i * nv + k, o);
+}
+
+// Flux pass over the face values of a triangle mesh without walls (FP32,
+// 4 velocities per thread): f_L is the cell's own value at face q, f_R the
+// neighbour's value at the same face (its face nbq), or f_L on a boundary
+// face; six row loads per thread in place of the twelve rows of f and of the
+// gradients.
+__global__ void __launch_bounds__(kFvThreads, 5)
+fv_flux_faces_kernel(const float *__restrict__ FV, float *__restrict__ L, FvTables<float> tb,
+                     const int *__restrict__ nb, const int *__restrict__ nbq, const int *__restrict__ order, int nv,
+                     int N, float Lv, float dv) {
+    const int64_t i = __ldg(order + blockIdx.x);
+    const int k = (blockIdx.y * kFvThreads + threadIdx.x) * 4;
+    if (k >= nv) return;
+    float4 fl[3], fr[3];
+    int jn[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        fl[q] = *reinterpret_cast<const float4 *>(FV + (i * 3 + q) * nv + k);
+        jn[q] = __ldg(nb + i * kFvMaxFaces + q);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        fr[q] = fl[q];
+        if (jn[q] >= 0) {
+            const int qn = __ldg(nbq + i * kFvMaxFaces + q);
+            fr[q] = *reinterpret_cast<const float4 *>(FV + ((int64_t)jn[q] * 3 + qn) * nv + k);
+        }
+    }
+    const int j1 = k / N, j2 = k - j1 * N;
+    const float v1 = -Lv + (float)j1 * dv;
+    float2 v2[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) v2[p] = make_float2(-Lv + (float)(j2 + 2 * p) * dv, -Lv + (float)(j2 + 2 * p + 1) * dv);
+    float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    const float2 hf = dup2(0.5f);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int64_t s = i * kFvMaxFaces + q;
+        const float nx = __ldg(tb.fn + 2 * s), ny = __ldg(tb.fn + 2 * s + 1);
+        const float2 v1nx = dup2(v1 * nx);
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float2 a = p == 0 ? lo2(fl[q]) : hi2(fl[q]), b = p == 0 ? lo2(fr[q]) : hi2(fr[q]);
+            const float2 vn = fma2(v2[p], dup2(ny), v1nx);
+            const float2 h = mul2(hf, vn), nah = make_float2(-fabsf(h.x), -fabsf(h.y));
+            acc[p] = fma2(h, add2(a, b), acc[p]);
+            acc[p] = fma2(nah, add2(b, neg2(a)), acc[p]);
+        }
+    }
+    const float2 ia = dup2(__ldg(tb.inv_area + i));
+    const float2 o0 = mul2(acc[0], ia), o1 = mul2(acc[1], ia);
+    *reinterpret_cast<float4 *>(L + i * nv + k) = make_float4(o0.x, o0.y, o1.x, o1.y);
 }
 
 // Flux pass of a mesh with walls (full accommodation, eq. BOU with alpha = 1,
@@ -1012,6 +1091,30 @@ cudaError_t flux(const bz_mesh *m, const GridView &g, const T *f, const T *G, T 
 }
 
 }  // namespace
+
+bool fv_face_mode(const bz_mesh *m, const GridView &g, const void *f, const void *L, const void *FV) {
+    return m->order == 2 && m->max_faces <= 3 && m->n_walls == 0 && g.N % 4 == 0 && aligned16(f) && aligned16(L) &&
+           aligned16(FV);
+}
+
+cudaError_t launch_fv_faces_f32(const bz_mesh *m, const GridView &g, const float *f, float *FV, cudaStream_t st) {
+    if (m->n_cells <= 0) return cudaSuccess;
+    const int nv = (int)g.nv;
+    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / 4 + kFvThreads - 1) / kFvThreads));
+    fv_gradient_kernel<float, 4, 3, true><<<grid, kFvThreads, 0, st>>>(f, FV, m->t32, m->d_ncen, m->d_cen, m->d_nsec,
+                                                                      m->d_sec, m->d_order, nv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fv_flux_faces_f32(const bz_mesh *m, const GridView &g, const float *FV, float *L,
+                                     cudaStream_t st) {
+    if (m->n_cells <= 0) return cudaSuccess;
+    const int nv = (int)g.nv;
+    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / 4 + kFvThreads - 1) / kFvThreads));
+    fv_flux_faces_kernel<<<grid, kFvThreads, 0, st>>>(FV, L, m->t32, m->d_nb, m->d_nbq, m->d_order, nv, g.N,
+                                                      (float)g.L, (float)g.dv);
+    return cudaGetLastError();
+}
 
 bool fv_walls_supported(const bz_mesh *m, const GridView &g) {
     return m->n_walls == 0 || (g.N % 4 == 0 && g.nv <= 4 * kFvThreads);
