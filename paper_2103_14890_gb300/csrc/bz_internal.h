@@ -141,7 +141,12 @@ struct bz_mesh {
     int max_faces;
     int *d_nface;           // [cell] faces
     int *d_nb;              // [cell][face] neighbour, -1 boundary
-    int *d_nbq;             // [cell][face] the neighbour's index of the same face, -1 boundary
+    // triangle meshes (max_faces <= 3): per position p of the processing order
+    // three int4 {i, ncen[i], nsec[i], qbits}, {cen[i][0..3]}, {cen[i][4], nb[i][0..2]}
+    // with i = order[p] and qbits holding, in 2 bits per face, the index of
+    // the same face in the neighbour; one level of loads gives a block all its
+    // indices
+    int4 *d_tripos;
     int *d_ncen;            // [cell] central stencil size (<= kFvCentral), | kFvRegularTri for a triangle
                             // whose stencil starts with its face neighbours, sector s on faces s, s+1
     int *d_cen;             // [cell][kFvCentral]
@@ -303,7 +308,7 @@ bool fv_walls_supported(const bz_mesh *mesh, const GridView &g);
 // FP32 triangle meshes without walls (N divisible by 4, 16-byte aligned rows):
 // the reconstruction writes each cell's values at its three face midpoints,
 // FV [cell][3][nv], and the flux pass reads those of the cell and of its
-// neighbours (the neighbour's face index from the mesh's nbq table).
+// neighbours (indices from the position records d_tripos).
 bool fv_face_mode(const bz_mesh *mesh, const GridView &g, const void *f, const void *L, const void *FV);
 cudaError_t launch_fv_faces_f32(const bz_mesh *mesh, const GridView &g, const float *f, float *FV, cudaStream_t st);
 cudaError_t launch_fv_flux_faces_f32(const bz_mesh *mesh, const GridView &g, const float *FV, float *L,

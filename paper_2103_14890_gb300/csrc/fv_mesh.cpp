@@ -164,7 +164,7 @@ void fv_mesh_destroy(bz_mesh *m) {
     if (!m) return;
     dev_free(m->d_nface);
     dev_free(m->d_nb);
-    dev_free(m->d_nbq);
+    dev_free(m->d_tripos);
     dev_free(m->d_ncen);
     dev_free(m->d_cen);
     dev_free(m->d_nsec);
@@ -585,12 +585,26 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
     for (size_t q = 0; q < real.size(); ++q) real32[q] = (float)real[q];
     cudaError_t e = upload(&m->d_nface, h.nface);
     if (e == cudaSuccess) e = upload(&m->d_nb, h.nb);
-    if (e == cudaSuccess) e = upload(&m->d_nbq, h.nbq);
     if (e == cudaSuccess) e = upload(&m->d_ncen, h.ncen);
     if (e == cudaSuccess) e = upload(&m->d_cen, h.cen);
     if (e == cudaSuccess) e = upload(&m->d_nsec, h.nsec);
     if (e == cudaSuccess) e = upload(&m->d_sec, h.sec);
     if (e == cudaSuccess) e = upload(&m->d_order, h.order);
+    if (e == cudaSuccess && maxf <= 3) {
+        std::vector<int4> tp((size_t)n * 3);
+        for (int64_t p = 0; p < n; ++p) {
+            const int i = h.order[p];
+            const int *nb = &h.nb[(size_t)i * kFvMaxFaces], *nq = &h.nbq[(size_t)i * kFvMaxFaces];
+            const int *c = &h.cen[(size_t)i * kFvCentral];
+            int qbits = 0;
+            for (int q = 0; q < 3; ++q)
+                if (nb[q] >= 0) qbits |= nq[q] << (2 * q);
+            tp[3 * p] = make_int4(i, h.ncen[i], h.nsec[i], qbits);
+            tp[3 * p + 1] = make_int4(c[0], c[1], c[2], c[3]);
+            tp[3 * p + 2] = make_int4(c[4], nb[0], nb[1], nb[2]);
+        }
+        e = upload(&m->d_tripos, tp);
+    }
     double *r64 = nullptr;
     float *r32 = nullptr;
     if (e == cudaSuccess) e = upload(&r64, real);

@@ -11,7 +11,8 @@
 // curve of their barycentres (the mesh's order table).
 //
 // Pass 1 (order 2): gradient of the CWENO polynomial per (cell, velocity),
-// stored as G [cell][2][nv].  The central (least-squares) gradient g_opt and
+// stored as G [cell][2][nv] (FP32 triangle meshes without walls: the values at
+// the three face midpoints, FV [cell][3][nv]).  The central (least-squares) gradient g_opt and
 // the sector gradients g_L are linear in the averages (tables R_c, R_s of
 // fv_mesh.cpp); the central polynomial's gradient is g_0 = (g_opt - sum_L
 // lambda_L g_L) / lambda_0 (eq. CWENO:P0, lambda_0 = 3/4, lambda_L = 1/4 /
@@ -19,6 +20,10 @@
 // to lambda_s / (sigma_s + eps)^4 with eps = 1e-14 (eqn.weights), formed
 // as lambda_s ((sigma_min + eps) / (sigma_s + eps))^4 so that no power
 // underflows in FP32.
+//
+// The flux passes take the cells in the reverse of the reconstruction's
+// order, so that they start on the rows the reconstruction wrote last, which
+// are still in L2.
 //
 // Pass 2: per face, f_L = fbar_i + g_i . (x_f - x_b,i), f_R the same from the
 // neighbour (f_L on a boundary face: transmissive), Rusanov flux of v f:
@@ -143,14 +148,11 @@ __device__ __forceinline__ void cweno_pair_tri(const float2 (&d)[kFvCentral], co
 // the gradient rows [cell][2][nv].
 template <bool FACE>
 __device__ __forceinline__ void gradient_tri_x2(const float *__restrict__ f, float *__restrict__ G,
-                                                const FvTables<float> &tb, const int *__restrict__ cen, int64_t i,
+                                                const FvTables<float> &tb, const int (&jc)[kFvCentral], int64_t i,
                                                 int k, int nv, const float4 fi) {
     float4 fr[kFvCentral];
 #pragma unroll
-    for (int q = 0; q < kFvCentral; ++q) {
-        const int j = __ldg(cen + i * kFvCentral + q);
-        fr[q] = *reinterpret_cast<const float4 *>(f + (int64_t)j * nv + k);
-    }
+    for (int q = 0; q < kFvCentral; ++q) fr[q] = *reinterpret_cast<const float4 *>(f + (int64_t)jc[q] * nv + k);
     float rx[kFvCentral], ry[kFvCentral];
 #pragma unroll
     for (int q = 0; q < kFvCentral; ++q) {
@@ -193,15 +195,31 @@ template <typename T, int VEC, int MAXS, bool FACE = false>
 __global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4) ? 4 : 1)
 fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, const int *__restrict__ ncen,
                    const int *__restrict__ cen, const int *__restrict__ nsec, const int *__restrict__ sec,
-                   const int *__restrict__ order, int nv) {
-    const int64_t i = __ldg(order + blockIdx.x);
+                   const int *__restrict__ order, const int4 *__restrict__ tripos, int nv) {
+    int64_t i;
+    int ncf;
+    int jc[kFvCentral];
+    if constexpr (FACE) {
+        // the block's indices in one level of loads (position record of a triangle mesh)
+        const int4 r0 = __ldg(tripos + 3 * blockIdx.x), r1 = __ldg(tripos + 3 * blockIdx.x + 1);
+        const int4 r2 = __ldg(tripos + 3 * blockIdx.x + 2);
+        i = r0.x;
+        ncf = r0.y;
+        jc[0] = r1.x; jc[1] = r1.y; jc[2] = r1.z; jc[3] = r1.w; jc[4] = r2.x;
+    } else {
+        i = __ldg(order + blockIdx.x);
+        ncf = __ldg(ncen + i);
+    }
     const int k = (blockIdx.y * kFvThreads + threadIdx.x) * VEC;
     if (k >= nv) return;
     const Vec<T, VEC> fi = ldv<T, VEC>(f + i * nv + k);
-    const int ncf = __ldg(ncen + i);
     if constexpr (sizeof(T) == 4 && VEC == 4 && MAXS == 3) {
         if (ncf & kFvRegularTri) {      // uniform over the block: one cell per block
-            gradient_tri_x2<FACE>(f, G, tb, cen, i, k, nv, make_float4(fi.v[0], fi.v[1], fi.v[2], fi.v[3]));
+            if constexpr (!FACE) {
+#pragma unroll
+                for (int q = 0; q < kFvCentral; ++q) jc[q] = __ldg(cen + i * kFvCentral + q);
+            }
+            gradient_tri_x2<FACE>(f, G, tb, jc, i, k, nv, make_float4(fi.v[0], fi.v[1], fi.v[2], fi.v[3]));
             return;
         }
     }
@@ -334,7 +352,7 @@ __global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4 && MAX
 fv_flux_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__ L, FvTables<T> tb,
                const int *__restrict__ nface, const int *__restrict__ nb, const int *__restrict__ order, int nv,
                int N, T Lv, T dv) {
-    const int64_t i = __ldg(order + blockIdx.x);
+    const int64_t i = __ldg(order + (gridDim.x - 1 - blockIdx.x));
     const int k = (blockIdx.y * kFvThreads + threadIdx.x) * VEC;
     if (k >= nv) return;
     const int nf = __ldg(nface + i);
@@ -434,28 +452,26 @@ fv_flux_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__
 
 // Flux pass over the face values of a triangle mesh without walls (FP32,
 // 4 velocities per thread): f_L is the cell's own value at face q, f_R the
-// neighbour's value at the same face (its face nbq), or f_L on a boundary
-// face; six row loads per thread in place of the twelve rows of f and of the
-// gradients.
+// neighbour's value at the same face (its face index from the position
+// record), or f_L on a boundary face; six row loads per thread in place of
+// the twelve rows of f and of the gradients.
 __global__ void __launch_bounds__(kFvThreads, 5)
 fv_flux_faces_kernel(const float *__restrict__ FV, float *__restrict__ L, FvTables<float> tb,
-                     const int *__restrict__ nb, const int *__restrict__ nbq, const int *__restrict__ order, int nv,
-                     int N, float Lv, float dv) {
-    const int64_t i = __ldg(order + blockIdx.x);
+                     const int4 *__restrict__ tripos, int nv, int N, float Lv, float dv) {
+    const int64_t p = gridDim.x - 1 - blockIdx.x;
+    const int4 r0 = __ldg(tripos + 3 * p), r2 = __ldg(tripos + 3 * p + 2);
+    const int64_t i = r0.x;
+    const int jn[3] = {r2.y, r2.z, r2.w};
     const int k = (blockIdx.y * kFvThreads + threadIdx.x) * 4;
     if (k >= nv) return;
     float4 fl[3], fr[3];
-    int jn[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        fl[q] = *reinterpret_cast<const float4 *>(FV + (i * 3 + q) * nv + k);
-        jn[q] = __ldg(nb + i * kFvMaxFaces + q);
-    }
+    for (int q = 0; q < 3; ++q) fl[q] = *reinterpret_cast<const float4 *>(FV + (i * 3 + q) * nv + k);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         fr[q] = fl[q];
         if (jn[q] >= 0) {
-            const int qn = __ldg(nbq + i * kFvMaxFaces + q);
+            const int qn = (r0.w >> (2 * q)) & 3;
             fr[q] = *reinterpret_cast<const float4 *>(FV + ((int64_t)jn[q] * 3 + qn) * nv + k);
         }
     }
@@ -510,7 +526,7 @@ fv_flux_wall_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restr
                     const int *__restrict__ nface, const int *__restrict__ nb, const int *__restrict__ order,
                     const int *__restrict__ wall, const T *__restrict__ wallp, int nv, int N, T Lv, T dv) {
     __shared__ double red[2 * (kFvThreads / 32)];
-    const int64_t i = __ldg(order + blockIdx.x);
+    const int64_t i = __ldg(order + (gridDim.x - 1 - blockIdx.x));
     const int kt = threadIdx.x * 4;
     const bool act = kt < nv;
     const int k = act ? kt : 0;                  // idle threads read row 0 and store nothing
@@ -745,7 +761,7 @@ __global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4 && MAX
 fv_flux3_kernel(const T *__restrict__ f, const T *__restrict__ C, T *__restrict__ L, FvTables<T> tb,
                 FvTables3<T> t3, const int *__restrict__ nface, const int *__restrict__ nb,
                 const int *__restrict__ order, int nv, int N, T Lv, T dv) {
-    const int64_t i = __ldg(order + blockIdx.x);
+    const int64_t i = __ldg(order + (gridDim.x - 1 - blockIdx.x));
     const int k = (blockIdx.y * kFvThreads + threadIdx.x) * VEC;
     if (k >= nv) return;
     const int nf = __ldg(nface + i);
@@ -819,7 +835,7 @@ fv_flux3_wall_kernel(const T *__restrict__ f, const T *__restrict__ C, T *__rest
                      const int *__restrict__ order, const int *__restrict__ wall, const T *__restrict__ wallp, int nv,
                      int N, T Lv, T dv) {
     __shared__ double red[3 * (kFvThreads / 32)];
-    const int64_t i = __ldg(order + blockIdx.x);
+    const int64_t i = __ldg(order + (gridDim.x - 1 - blockIdx.x));
     const int kt = threadIdx.x * 4;
     const bool act = kt < nv;
     const int k = act ? kt : 0;                  // idle threads read row 0 and store nothing
@@ -1017,7 +1033,7 @@ template <typename T, int VEC, int MAXS>
 void gradient_launch(const bz_mesh *m, int nv, const T *f, T *G, cudaStream_t st) {
     const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / VEC + kFvThreads - 1) / kFvThreads));
     fv_gradient_kernel<T, VEC, MAXS><<<grid, kFvThreads, 0, st>>>(f, G, pick<T>(m), m->d_ncen, m->d_cen, m->d_nsec,
-                                                                  m->d_sec, m->d_order, nv);
+                                                                  m->d_sec, m->d_order, m->d_tripos, nv);
 }
 
 template <typename T, bool kGrad, int VEC, int MAXF>
@@ -1093,7 +1109,8 @@ cudaError_t flux(const bz_mesh *m, const GridView &g, const T *f, const T *G, T 
 }  // namespace
 
 bool fv_face_mode(const bz_mesh *m, const GridView &g, const void *f, const void *L, const void *FV) {
-    return m->order == 2 && m->max_faces <= 3 && m->n_walls == 0 && g.N % 4 == 0 && aligned16(f) && aligned16(L) &&
+    return m->order == 2 && m->max_faces <= 3 && m->d_tripos && m->n_walls == 0 && g.N % 4 == 0 && aligned16(f) &&
+           aligned16(L) &&
            aligned16(FV);
 }
 
@@ -1102,7 +1119,7 @@ cudaError_t launch_fv_faces_f32(const bz_mesh *m, const GridView &g, const float
     const int nv = (int)g.nv;
     const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / 4 + kFvThreads - 1) / kFvThreads));
     fv_gradient_kernel<float, 4, 3, true><<<grid, kFvThreads, 0, st>>>(f, FV, m->t32, m->d_ncen, m->d_cen, m->d_nsec,
-                                                                      m->d_sec, m->d_order, nv);
+                                                                      m->d_sec, m->d_order, m->d_tripos, nv);
     return cudaGetLastError();
 }
 
@@ -1111,8 +1128,7 @@ cudaError_t launch_fv_flux_faces_f32(const bz_mesh *m, const GridView &g, const 
     if (m->n_cells <= 0) return cudaSuccess;
     const int nv = (int)g.nv;
     const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / 4 + kFvThreads - 1) / kFvThreads));
-    fv_flux_faces_kernel<<<grid, kFvThreads, 0, st>>>(FV, L, m->t32, m->d_nb, m->d_nbq, m->d_order, nv, g.N,
-                                                      (float)g.L, (float)g.dv);
+    fv_flux_faces_kernel<<<grid, kFvThreads, 0, st>>>(FV, L, m->t32, m->d_tripos, nv, g.N, (float)g.L, (float)g.dv);
     return cudaGetLastError();
 }
 
