@@ -389,8 +389,9 @@ def _transport_measure(bz, workloads, st, check=True):
         if prec == "fp32":
             ent["roofline"] = {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                                "frac": alg / (ms / 1e3) / 1e9 / hbm,
-                               "note": "two passes: the reconstruction writes 2 gradient values per (cell, velocity) "
-                                       "that the flux pass reads back"}
+                               "note": "two passes: the reconstruction writes the values at the 3 face midpoints per "
+                                       "(cell, velocity), which the flux pass reads back (0.65 GB of DRAM traffic "
+                                       "per call at the least)"}
         out[prec] = ent
     # the same residual in a closed box: every boundary edge a wall at rest
     # with full accommodation (the wall flux pass: one CTA per cell holds all

@@ -598,7 +598,7 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
             const int *c = &h.cen[(size_t)i * kFvCentral];
             int qbits = 0;
             for (int q = 0; q < 3; ++q)
-                if (nb[q] >= 0) qbits |= nq[q] << (2 * q);
+                if (nb[q] >= 0) qbits |= (nq[q] & 3) << (2 * q);
             tp[3 * p] = make_int4(i, h.ncen[i], h.nsec[i], qbits);
             tp[3 * p + 1] = make_int4(c[0], c[1], c[2], c[3]);
             tp[3 * p + 2] = make_int4(c[4], nb[0], nb[1], nb[2]);

@@ -29,6 +29,11 @@
 // neighbour (f_L on a boundary face: transmissive), Rusanov flux of v f:
 // |e| F = (v.|e|n)(f_L + f_R)/2 - |v.|e|n| (f_R - f_L)/2, summed and scaled
 // by 1/|P_i|.  The face midpoint rule is exact for degree-1 reconstructions.
+#include <stdlib.h>
+
+#include <algorithm>
+#include <atomic>
+
 #include "bz_device.cuh"
 #include "bz_internal.h"
 
@@ -147,12 +152,9 @@ __device__ __forceinline__ void cweno_pair_tri(const float2 (&d)[kFvCentral], co
 // face midpoints, f_i + g . (x_f - x_b,i), rows [cell][face][nv], in place of
 // the gradient rows [cell][2][nv].
 template <bool FACE>
-__device__ __forceinline__ void gradient_tri_x2(const float *__restrict__ f, float *__restrict__ G,
-                                                const FvTables<float> &tb, const int (&jc)[kFvCentral], int64_t i,
-                                                int k, int nv, const float4 fi) {
-    float4 fr[kFvCentral];
-#pragma unroll
-    for (int q = 0; q < kFvCentral; ++q) fr[q] = *reinterpret_cast<const float4 *>(f + (int64_t)jc[q] * nv + k);
+__device__ __forceinline__ void tri_x2_rows(float *__restrict__ G, const FvTables<float> &tb,
+                                            const float4 (&fr)[kFvCentral], int64_t i, int k, int nv,
+                                            const float4 fi) {
     float rx[kFvCentral], ry[kFvCentral];
 #pragma unroll
     for (int q = 0; q < kFvCentral; ++q) {
@@ -187,42 +189,24 @@ __device__ __forceinline__ void gradient_tri_x2(const float *__restrict__ f, flo
     }
 }
 
-// MAXS / MAXF: compile-time bound on the sectors / faces of a cell (3 for
-// triangle meshes, kFvMaxFaces otherwise).  Every loop over them is unrolled
-// with a predicate, so all neighbour rows of a cell are requested before the
-// first one is used (the kernels are latency-bound otherwise).
-template <typename T, int VEC, int MAXS, bool FACE = false>
-__global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4) ? 4 : 1)
-fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, const int *__restrict__ ncen,
-                   const int *__restrict__ cen, const int *__restrict__ nsec, const int *__restrict__ sec,
-                   const int *__restrict__ order, const int4 *__restrict__ tripos, int nv) {
-    int64_t i;
-    int ncf;
-    int jc[kFvCentral];
-    if constexpr (FACE) {
-        // the block's indices in one level of loads (position record of a triangle mesh)
-        const int4 r0 = __ldg(tripos + 3 * blockIdx.x), r1 = __ldg(tripos + 3 * blockIdx.x + 1);
-        const int4 r2 = __ldg(tripos + 3 * blockIdx.x + 2);
-        i = r0.x;
-        ncf = r0.y;
-        jc[0] = r1.x; jc[1] = r1.y; jc[2] = r1.z; jc[3] = r1.w; jc[4] = r2.x;
-    } else {
-        i = __ldg(order + blockIdx.x);
-        ncf = __ldg(ncen + i);
-    }
-    const int k = (blockIdx.y * kFvThreads + threadIdx.x) * VEC;
-    if (k >= nv) return;
-    const Vec<T, VEC> fi = ldv<T, VEC>(f + i * nv + k);
-    if constexpr (sizeof(T) == 4 && VEC == 4 && MAXS == 3) {
-        if (ncf & kFvRegularTri) {      // uniform over the block: one cell per block
-            if constexpr (!FACE) {
+template <bool FACE>
+__device__ __forceinline__ void gradient_tri_x2(const float *__restrict__ f, float *__restrict__ G,
+                                                const FvTables<float> &tb, const int (&jc)[kFvCentral], int64_t i,
+                                                int k, int nv, const float4 fi) {
+    float4 fr[kFvCentral];
 #pragma unroll
-                for (int q = 0; q < kFvCentral; ++q) jc[q] = __ldg(cen + i * kFvCentral + q);
-            }
-            gradient_tri_x2<FACE>(f, G, tb, jc, i, k, nv, make_float4(fi.v[0], fi.v[1], fi.v[2], fi.v[3]));
-            return;
-        }
-    }
+    for (int q = 0; q < kFvCentral; ++q) fr[q] = *reinterpret_cast<const float4 *>(f + (int64_t)jc[q] * nv + k);
+    tri_x2_rows<FACE>(G, tb, fr, i, k, nv, fi);
+}
+
+// Reconstruction of cell i for the VEC velocities k.. of a thread (any
+// polygon; MAXS bounds its sectors): gradients, or with FACE the values at
+// the three face midpoints of a triangle.
+template <typename T, int VEC, int MAXS, bool FACE>
+__device__ __forceinline__ void gradient_generic(const T *__restrict__ f, T *__restrict__ G, const FvTables<T> &tb,
+                                                 const int *__restrict__ cen, const int *__restrict__ nsec,
+                                                 const int *__restrict__ sec, int64_t i, int ncf, int k, int nv,
+                                                 const Vec<T, VEC> &fi) {
     const int nc = ncf & (kFvRegularTri - 1), ns = __ldg(nsec + i);
     // central least-squares gradient
     T gx[VEC], gy[VEC];
@@ -347,6 +331,32 @@ fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, c
     }
 }
 
+// MAXS / MAXF: compile-time bound on the sectors / faces of a cell (3 for
+// triangle meshes, kFvMaxFaces otherwise).  Every loop over them is unrolled
+// with a predicate, so all neighbour rows of a cell are requested before the
+// first one is used (the kernels are latency-bound otherwise).
+template <typename T, int VEC, int MAXS>
+__global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4) ? 4 : 1)
+fv_gradient_kernel(const T *__restrict__ f, T *__restrict__ G, FvTables<T> tb, const int *__restrict__ ncen,
+                   const int *__restrict__ cen, const int *__restrict__ nsec, const int *__restrict__ sec,
+                   const int *__restrict__ order, int nv) {
+    const int64_t i = __ldg(order + blockIdx.x);
+    const int ncf = __ldg(ncen + i);
+    const int k = (blockIdx.y * kFvThreads + threadIdx.x) * VEC;
+    if (k >= nv) return;
+    const Vec<T, VEC> fi = ldv<T, VEC>(f + i * nv + k);
+    if constexpr (sizeof(T) == 4 && VEC == 4 && MAXS == 3) {
+        if (ncf & kFvRegularTri) {      // uniform over the block: one cell per block
+            int jc[kFvCentral];
+#pragma unroll
+            for (int q = 0; q < kFvCentral; ++q) jc[q] = __ldg(cen + i * kFvCentral + q);
+            gradient_tri_x2<false>(f, G, tb, jc, i, k, nv, make_float4(fi.v[0], fi.v[1], fi.v[2], fi.v[3]));
+            return;
+        }
+    }
+    gradient_generic<T, VEC, MAXS, false>(f, G, tb, cen, nsec, sec, i, ncf, k, nv, fi);
+}
+
 template <typename T, bool kGrad, int VEC, int MAXF>
 __global__ void __launch_bounds__(kFvThreads, (sizeof(T) == 4 && VEC == 4 && MAXF <= 3) ? 4 : 1)
 fv_flux_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__ L, FvTables<T> tb,
@@ -450,55 +460,157 @@ fv_flux_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restrict__
     stv<T, VEC>(L + i * nv + k, o);
 }
 
-// Flux pass over the face values of a triangle mesh without walls (FP32,
-// 4 velocities per thread): f_L is the cell's own value at face q, f_R the
-// neighbour's value at the same face (its face index from the position
-// record), or f_L on a boundary face; six row loads per thread in place of
-// the twelve rows of f and of the gradients.
-__global__ void __launch_bounds__(kFvThreads, 5)
-fv_flux_faces_kernel(const float *__restrict__ FV, float *__restrict__ L, FvTables<float> tb,
-                     const int4 *__restrict__ tripos, int nv, int N, float Lv, float dv) {
-    const int64_t p = gridDim.x - 1 - blockIdx.x;
-    const int4 r0 = __ldg(tripos + 3 * p), r2 = __ldg(tripos + 3 * p + 2);
-    const int64_t i = r0.x;
-    const int jn[3] = {r2.y, r2.z, r2.w};
-    const int k = (blockIdx.y * kFvThreads + threadIdx.x) * 4;
-    if (k >= nv) return;
-    float4 fl[3], fr[3];
+// ---- persistent forms of the two face-value passes --------------------------
+// A block takes one of every (SMs x blocks per SM) positions of the
+// processing order, walking them in steps of the grid; while it computes one cell, the rows of
+// the next one travel into shared memory by cp.async (16 bytes per thread and
+// row, each thread copying exactly the slots it reads back, so no block
+// barrier is needed and threads past nv leave at once), and the index
+// records of the cell after that are already being loaded.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+constexpr int kFaceRows = 6;         // rows staged per cell: f_i and 5 stencil rows / 3 own and 3 neighbour face rows
+// blocks per SM: 3 for the reconstruction (85 registers, no spills; 4 spill
+// its record prefetch), 4 for the flux pass (64 registers)
+constexpr int kFacesCtasPerSm = 3, kFluxCtasPerSm = 4;
+constexpr size_t kFaceStageBytes = 2 * kFaceRows * kFvThreads * sizeof(float4);   // 48 KB
+
+// Index record of position p needed by the reconstruction: cell, flags, stencil.
+struct RecG {
+    int i, ncf, c[kFvCentral];
+};
+__device__ __forceinline__ RecG rec_g(const int4 *__restrict__ tripos, int64_t p) {
+    const int4 a = __ldg(tripos + 3 * p), b = __ldg(tripos + 3 * p + 1), c = __ldg(tripos + 3 * p + 2);
+    return RecG{a.x, a.y, {b.x, b.y, b.z, b.w, c.x}};
+}
+
+template <int CPS>
+__global__ void __launch_bounds__(kFvThreads, CPS)
+fv_faces_persist_kernel(const float *__restrict__ f, float *__restrict__ FV, FvTables<float> tb,
+                        const int *__restrict__ cen, const int *__restrict__ nsec, const int *__restrict__ sec,
+                        const int4 *__restrict__ tripos, int64_t n, int nv) {
+    extern __shared__ float4 stage[];            // [2][kFaceRows][kFvThreads]
+    const int t = threadIdx.x;
+    const int k = (blockIdx.y * kFvThreads + t) * 4;
+    if (k >= nv || (int64_t)blockIdx.x >= n) return;
+    const int64_t G = gridDim.x;
+    auto issue = [&](const RecG &r, int buf) {
+        float4 *sl = stage + buf * kFaceRows * kFvThreads + t;
+        cp_async16(sl, f + (int64_t)r.i * nv + k);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) fl[q] = *reinterpret_cast<const float4 *>(FV + (i * 3 + q) * nv + k);
+        for (int q = 0; q < kFvCentral; ++q) cp_async16(sl + (q + 1) * kFvThreads, f + (int64_t)r.c[q] * nv + k);
+    };
+    int64_t p = blockIdx.x;
+    RecG cur = rec_g(tripos, p);
+    issue(cur, 0);
+    cp_async_commit();
+    RecG nxt = cur;
+    if (p + G < n) nxt = rec_g(tripos, p + G);
+    for (int it = 0;; ++it) {
+        const bool more = p + G < n;
+        if (more) issue(nxt, (it + 1) & 1);
+        cp_async_commit();
+        RecG nn = nxt;
+        if (p + 2 * G < n) nn = rec_g(tripos, p + 2 * G);
+        cp_async_wait_prev();
+        const float4 *sl = stage + (it & 1) * kFaceRows * kFvThreads + t;
+        const float4 fi = sl[0];
+        if (cur.ncf & kFvRegularTri) {
+            float4 fr[kFvCentral];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        fr[q] = fl[q];
-        if (jn[q] >= 0) {
-            const int qn = (r0.w >> (2 * q)) & 3;
-            fr[q] = *reinterpret_cast<const float4 *>(FV + ((int64_t)jn[q] * 3 + qn) * nv + k);
+            for (int q = 0; q < kFvCentral; ++q) fr[q] = sl[(q + 1) * kFvThreads];
+            tri_x2_rows<true>(FV, tb, fr, cur.i, k, nv, fi);
+        } else {
+            Vec<float, 4> fv;
+            fv.v[0] = fi.x; fv.v[1] = fi.y; fv.v[2] = fi.z; fv.v[3] = fi.w;
+            gradient_generic<float, 4, 3, true>(f, FV, tb, cen, nsec, sec, cur.i, cur.ncf, k, nv, fv);
         }
+        if (!more) break;
+        p += G;
+        cur = nxt;
+        nxt = nn;
     }
+}
+
+// Index record of position p needed by the flux pass: cell, neighbours, their face indices.
+struct RecF {
+    int i, qbits, nb[3];
+};
+__device__ __forceinline__ RecF rec_f(const int4 *__restrict__ tripos, int64_t p) {
+    const int4 a = __ldg(tripos + 3 * p), c = __ldg(tripos + 3 * p + 2);
+    return RecF{a.x, a.w, {c.y, c.z, c.w}};
+}
+
+__global__ void __launch_bounds__(kFvThreads, kFluxCtasPerSm)
+fv_flux_faces_persist_kernel(const float *__restrict__ FV, float *__restrict__ L, FvTables<float> tb,
+                             const int4 *__restrict__ tripos, int64_t n, int nv, int N, float Lv, float dv) {
+    extern __shared__ float4 stage[];            // [2][kFaceRows][kFvThreads]
+    const int t = threadIdx.x;
+    const int k = (blockIdx.y * kFvThreads + t) * 4;
+    if (k >= nv || (int64_t)blockIdx.x >= n) return;
+    const int64_t G = gridDim.x;
+    // positions from the end of the order (the rows the reconstruction wrote last are still in L2)
+    auto pos = [&](int64_t p) { return n - 1 - p; };
+    auto issue = [&](const RecF &r, int buf) {
+        float4 *sl = stage + buf * kFaceRows * kFvThreads + t;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            cp_async16(sl + q * kFvThreads, FV + ((int64_t)r.i * 3 + q) * nv + k);
+            if (r.nb[q] >= 0)
+                cp_async16(sl + (3 + q) * kFvThreads, FV + ((int64_t)r.nb[q] * 3 + ((r.qbits >> (2 * q)) & 3)) * nv + k);
+        }
+    };
     const int j1 = k / N, j2 = k - j1 * N;
     const float v1 = -Lv + (float)j1 * dv;
     float2 v2[2];
 #pragma unroll
-    for (int p = 0; p < 2; ++p) v2[p] = make_float2(-Lv + (float)(j2 + 2 * p) * dv, -Lv + (float)(j2 + 2 * p + 1) * dv);
-    float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (int h = 0; h < 2; ++h) v2[h] = make_float2(-Lv + (float)(j2 + 2 * h) * dv, -Lv + (float)(j2 + 2 * h + 1) * dv);
     const float2 hf = dup2(0.5f);
+    int64_t p = blockIdx.x;
+    RecF cur = rec_f(tripos, pos(p));
+    issue(cur, 0);
+    cp_async_commit();
+    RecF nxt = cur;
+    if (p + G < n) nxt = rec_f(tripos, pos(p + G));
+    for (int it = 0;; ++it) {
+        const bool more = p + G < n;
+        if (more) issue(nxt, (it + 1) & 1);
+        cp_async_commit();
+        RecF nn = nxt;
+        if (p + 2 * G < n) nn = rec_f(tripos, pos(p + 2 * G));
+        cp_async_wait_prev();
+        const float4 *sl = stage + (it & 1) * kFaceRows * kFvThreads + t;
+        const int64_t i = cur.i;
+        float2 acc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int64_t s = i * kFvMaxFaces + q;
-        const float nx = __ldg(tb.fn + 2 * s), ny = __ldg(tb.fn + 2 * s + 1);
-        const float2 v1nx = dup2(v1 * nx);
+        for (int q = 0; q < 3; ++q) {
+            const float4 fl = sl[q * kFvThreads];
+            const float4 fr = cur.nb[q] >= 0 ? sl[(3 + q) * kFvThreads] : fl;
+            const int64_t s = i * kFvMaxFaces + q;
+            const float nx = __ldg(tb.fn + 2 * s), ny = __ldg(tb.fn + 2 * s + 1);
+            const float2 v1nx = dup2(v1 * nx);
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const float2 a = p == 0 ? lo2(fl[q]) : hi2(fl[q]), b = p == 0 ? lo2(fr[q]) : hi2(fr[q]);
-            const float2 vn = fma2(v2[p], dup2(ny), v1nx);
-            const float2 h = mul2(hf, vn), nah = make_float2(-fabsf(h.x), -fabsf(h.y));
-            acc[p] = fma2(h, add2(a, b), acc[p]);
-            acc[p] = fma2(nah, add2(b, neg2(a)), acc[p]);
+            for (int h = 0; h < 2; ++h) {
+                const float2 a = h == 0 ? lo2(fl) : hi2(fl), b = h == 0 ? lo2(fr) : hi2(fr);
+                const float2 vn = fma2(v2[h], dup2(ny), v1nx);
+                const float2 hv = mul2(hf, vn), nah = make_float2(-fabsf(hv.x), -fabsf(hv.y));
+                acc[h] = fma2(hv, add2(a, b), acc[h]);
+                acc[h] = fma2(nah, add2(b, neg2(a)), acc[h]);
+            }
         }
+        const float2 ia = dup2(__ldg(tb.inv_area + i));
+        const float2 o0 = mul2(acc[0], ia), o1 = mul2(acc[1], ia);
+        *reinterpret_cast<float4 *>(L + i * nv + k) = make_float4(o0.x, o0.y, o1.x, o1.y);
+        if (!more) break;
+        p += G;
+        cur = nxt;
+        nxt = nn;
     }
-    const float2 ia = dup2(__ldg(tb.inv_area + i));
-    const float2 o0 = mul2(acc[0], ia), o1 = mul2(acc[1], ia);
-    *reinterpret_cast<float4 *>(L + i * nv + k) = make_float4(o0.x, o0.y, o1.x, o1.y);
 }
 
 // Flux pass of a mesh with walls (full accommodation, eq. BOU with alpha = 1,
@@ -1033,7 +1145,7 @@ template <typename T, int VEC, int MAXS>
 void gradient_launch(const bz_mesh *m, int nv, const T *f, T *G, cudaStream_t st) {
     const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / VEC + kFvThreads - 1) / kFvThreads));
     fv_gradient_kernel<T, VEC, MAXS><<<grid, kFvThreads, 0, st>>>(f, G, pick<T>(m), m->d_ncen, m->d_cen, m->d_nsec,
-                                                                  m->d_sec, m->d_order, m->d_tripos, nv);
+                                                                  m->d_sec, m->d_order, nv);
 }
 
 template <typename T, bool kGrad, int VEC, int MAXF>
@@ -1114,12 +1226,32 @@ bool fv_face_mode(const bz_mesh *m, const GridView &g, const void *f, const void
            aligned16(FV);
 }
 
+static int fv_sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
+// persistent grid: cps blocks per SM over the velocity blocks
+static dim3 faces_grid(const bz_mesh *m, int nv, int cps) {
+    const int gy = (nv / 4 + kFvThreads - 1) / kFvThreads;
+    const int64_t gx = std::max<int64_t>(1, std::min<int64_t>(m->n_cells, (int64_t)fv_sm_count() * cps / gy));
+    return dim3((unsigned)gx, (unsigned)gy);
+}
+
 cudaError_t launch_fv_faces_f32(const bz_mesh *m, const GridView &g, const float *f, float *FV, cudaStream_t st) {
     if (m->n_cells <= 0) return cudaSuccess;
     const int nv = (int)g.nv;
-    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / 4 + kFvThreads - 1) / kFvThreads));
-    fv_gradient_kernel<float, 4, 3, true><<<grid, kFvThreads, 0, st>>>(f, FV, m->t32, m->d_ncen, m->d_cen, m->d_nsec,
-                                                                      m->d_sec, m->d_order, m->d_tripos, nv);
+    fv_faces_persist_kernel<kFacesCtasPerSm><<<faces_grid(m, nv, kFacesCtasPerSm), kFvThreads, kFaceStageBytes, st>>>(
+        f, FV, m->t32, m->d_cen, m->d_nsec, m->d_sec, m->d_tripos, m->n_cells, nv);
     return cudaGetLastError();
 }
 
@@ -1127,8 +1259,8 @@ cudaError_t launch_fv_flux_faces_f32(const bz_mesh *m, const GridView &g, const 
                                      cudaStream_t st) {
     if (m->n_cells <= 0) return cudaSuccess;
     const int nv = (int)g.nv;
-    const dim3 grid((unsigned)m->n_cells, (unsigned)((nv / 4 + kFvThreads - 1) / kFvThreads));
-    fv_flux_faces_kernel<<<grid, kFvThreads, 0, st>>>(FV, L, m->t32, m->d_tripos, nv, g.N, (float)g.L, (float)g.dv);
+    fv_flux_faces_persist_kernel<<<faces_grid(m, nv, kFluxCtasPerSm), kFvThreads, kFaceStageBytes, st>>>(
+        FV, L, m->t32, m->d_tripos, m->n_cells, nv, g.N, (float)g.L, (float)g.dv);
     return cudaGetLastError();
 }
 
