@@ -476,39 +476,44 @@ int fv_mesh_create(int n_vertices, const double *xy, int64_t n_cells, const int6
             // neighbours in face order and the cell is flagged, so that the
             // FP32 reconstruction loads every neighbour row once for the
             // central and the sector gradients (sector s joins faces s and
-            // s + 1 mod 3).
-            if (k == 3 && ns == 3 && nc == kFvCentral) {
-                int perm[kFvCentral];
-                bool used[kFvCentral] = {};
-                bool ok = true;
-                for (int q = 0; q < 3 && ok; ++q) {
+            // s + 1 mod 3).  The same for the degree-2 stencil.
+            auto face_first = [&](int *cn, double *R, int nrow, int width, int ncs, int &flagged) {
+                if (k != 3 || ns != 3) return;
+                int perm[kFvCentral3];
+                bool used[kFvCentral3] = {};
+                for (int q = 0; q < 3; ++q) {
                     const int j = h.nb[(size_t)i * kFvMaxFaces + q];
                     int hit = -1;
-                    for (int t = 0; t < nc && hit < 0; ++t)
-                        if (!used[t] && h.cen[i * kFvCentral + t] == j) hit = t;
-                    ok = hit >= 0;
-                    if (ok) {
-                        used[hit] = true;
-                        perm[q] = hit;
-                    }
+                    for (int t = 0; t < ncs && hit < 0; ++t)
+                        if (!used[t] && cn[t] == j) hit = t;
+                    if (hit < 0) return;
+                    used[hit] = true;
+                    perm[q] = hit;
                 }
-                if (ok) {
-                    for (int t = 0, p = 3; t < nc; ++t)
-                        if (!used[t]) perm[p++] = t;
-                    int c0[kFvCentral];
-                    double r0[2][kFvCentral];
-                    for (int t = 0; t < nc; ++t) {
-                        c0[t] = h.cen[i * kFvCentral + t];
-                        r0[0][t] = h.Rc[(i * 2 + 0) * kFvCentral + t];
-                        r0[1][t] = h.Rc[(i * 2 + 1) * kFvCentral + t];
-                    }
-                    for (int t = 0; t < nc; ++t) {
-                        h.cen[i * kFvCentral + t] = c0[perm[t]];
-                        h.Rc[(i * 2 + 0) * kFvCentral + t] = r0[0][perm[t]];
-                        h.Rc[(i * 2 + 1) * kFvCentral + t] = r0[1][perm[t]];
-                    }
-                    h.ncen[i] = nc | kFvRegularTri;
+                for (int t = 0, p = 3; t < ncs; ++t)
+                    if (!used[t]) perm[p++] = t;
+                int c0[kFvCentral3];
+                std::vector<double> r0((size_t)nrow * ncs);
+                for (int t = 0; t < ncs; ++t) {
+                    c0[t] = cn[t];
+                    for (int r = 0; r < nrow; ++r) r0[(size_t)r * ncs + t] = R[(size_t)r * width + t];
                 }
+                for (int t = 0; t < ncs; ++t) {
+                    cn[t] = c0[perm[t]];
+                    for (int r = 0; r < nrow; ++r) R[(size_t)r * width + t] = r0[(size_t)r * ncs + perm[t]];
+                }
+                flagged |= kFvRegularTri;
+            };
+            if (nc == kFvCentral) {
+                int fl = 0;
+                face_first(&h.cen[i * kFvCentral], &h.Rc[i * 2 * kFvCentral], 2, kFvCentral, nc, fl);
+                h.ncen[i] = nc | fl;
+            }
+            if (order == 3 && h.ncen3[i] == kFvCentral3) {
+                int fl = 0;
+                face_first(&h.cen3[i * kFvCentral3], &h.Rc3[(size_t)i * kFvCoef3 * kFvCentral3], kFvCoef3,
+                           kFvCentral3, kFvCentral3, fl);
+                h.ncen3[i] = kFvCentral3 | fl;
             }
         }
     }

@@ -755,6 +755,96 @@ fv_flux_wall_kernel(const T *__restrict__ f, const T *__restrict__ G, T *__restr
 // derivatives (for the linear sectors: |h grad p|^2).  VEC velocities per
 // thread (4 on triangle meshes with aligned rows: the table entries, uniform
 // over the CTA, are then loaded once per 4 velocities); C is [cell][5][nv].
+// Degree-2 coefficients of the 4 velocities k..k+3 of a flagged triangle in
+// FP32x2 (its 11-cell stencil starts with the face neighbours; sector s joins
+// faces s and s + 1 mod 3): the steps of the generic kernel below, each
+// neighbour row loaded once.
+__device__ __forceinline__ void coef3_tri_x2(const float *__restrict__ f, float *__restrict__ C,
+                                             const FvTables<float> &tb, const FvTables3<float> &t3,
+                                             const int *__restrict__ cen, int64_t i, int k, int nv, const float4 fi) {
+    constexpr float kInvLam0 = (float)(4.0 / 3.0), kLam0 = 0.75f, kEps = 1e-14f;
+    const float lamL = 0.25f / 3.0f;
+    const float2 nf[2] = {neg2(lo2(fi)), neg2(hi2(fi))};
+    const float *Rc = t3.Rc + i * kFvCoef3 * kFvCentral3;
+    float2 c[kFvCoef3][2], dface[3][2];
+#pragma unroll
+    for (int q = 0; q < kFvCentral3; ++q) {
+        const int j = __ldg(cen + i * kFvCentral3 + q);
+        const float4 r = *reinterpret_cast<const float4 *>(f + (int64_t)j * nv + k);
+        const float2 d0 = add2(lo2(r), nf[0]), d1 = add2(hi2(r), nf[1]);
+        if (q < 3) {
+            dface[q][0] = d0;
+            dface[q][1] = d1;
+        }
+#pragma unroll
+        for (int l = 0; l < kFvCoef3; ++l) {
+            const float2 R = dup2(__ldg(Rc + l * kFvCentral3 + q));
+            c[l][0] = q == 0 ? mul2(R, d0) : fma2(R, d0, c[l][0]);
+            c[l][1] = q == 0 ? mul2(R, d1) : fma2(R, d1, c[l][1]);
+        }
+    }
+    float2 sx[3][2], sy[3][2];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const float4 R = __ldg(reinterpret_cast<const float4 *>(tb.Rs + (i * kFvMaxFaces + s) * 4));
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float2 da = dface[s][p], db = dface[(s + 1) % 3][p];
+            sx[s][p] = fma2(dup2(R.x), da, mul2(dup2(R.y), db));
+            sy[s][p] = fma2(dup2(R.z), da, mul2(dup2(R.w), db));
+        }
+    }
+    const float m20 = __ldg(t3.mu + 3 * i), m11 = __ldg(t3.mu + 3 * i + 1), m02 = __ldg(t3.mu + 3 * i + 2);
+    // smoothness of the central polynomial: sum of its squared derivatives
+    // over the scaled cell, a quadratic form in p0 with these coefficients
+    const float2 A22 = dup2(4.f * m20 + 4.f), A33 = dup2(m02 + m20 + 1.f), A44 = dup2(4.f * m02 + 4.f);
+    const float2 A23 = dup2(4.f * m11), E = dup2(kEps);
+    float2 out[kFvCoef3][2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const float2 sumx = add2(add2(sx[0][p], sx[1][p]), sx[2][p]), sumy = add2(add2(sy[0][p], sy[1][p]), sy[2][p]);
+        float2 p0[kFvCoef3];
+        p0[0] = mul2(fma2(dup2(-lamL), sumx, c[0][p]), dup2(kInvLam0));
+        p0[1] = mul2(fma2(dup2(-lamL), sumy, c[1][p]), dup2(kInvLam0));
+#pragma unroll
+        for (int l = 2; l < kFvCoef3; ++l) p0[l] = mul2(c[l][p], dup2(kInvLam0));
+        float2 sig0 = fma2(p0[0], p0[0], mul2(p0[1], p0[1]));
+        sig0 = fma2(mul2(A22, p0[2]), p0[2], sig0);
+        sig0 = fma2(mul2(A33, p0[3]), p0[3], sig0);
+        sig0 = fma2(mul2(A44, p0[4]), p0[4], sig0);
+        sig0 = fma2(mul2(A23, p0[2]), p0[3], sig0);
+        sig0 = fma2(mul2(A23, p0[3]), p0[4], sig0);
+        float2 sig[3];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) sig[s] = fma2(sx[s][p], sx[s][p], mul2(sy[s][p], sy[s][p]));
+        const float2 smin = make_float2(fminf(fminf(sig0.x, sig[0].x), fminf(sig[1].x, sig[2].x)),
+                                        fminf(fminf(sig0.y, sig[0].y), fminf(sig[1].y, sig[2].y)));
+        const float2 num = add2(smin, E);
+        float2 r = mul2(num, rcp2(add2(sig0, E)));
+        r = mul2(r, r);
+        float2 w = mul2(dup2(kLam0), mul2(r, r));
+        float2 wsum = w, acc[kFvCoef3];
+#pragma unroll
+        for (int l = 0; l < kFvCoef3; ++l) acc[l] = mul2(w, p0[l]);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            r = mul2(num, rcp2(add2(sig[s], E)));
+            r = mul2(r, r);
+            w = mul2(dup2(lamL), mul2(r, r));
+            wsum = add2(wsum, w);
+            acc[0] = fma2(w, sx[s][p], acc[0]);
+            acc[1] = fma2(w, sy[s][p], acc[1]);
+        }
+        const float2 iw = rcp2(wsum);
+#pragma unroll
+        for (int l = 0; l < kFvCoef3; ++l) out[l][p] = mul2(acc[l], iw);
+    }
+#pragma unroll
+    for (int l = 0; l < kFvCoef3; ++l)
+        *reinterpret_cast<float4 *>(C + (i * kFvCoef3 + l) * nv + k) =
+            make_float4(out[l][0].x, out[l][0].y, out[l][1].x, out[l][1].y);
+}
+
 template <typename T, int VEC, int MAXS>
 __global__ void __launch_bounds__(kFvThreads)
 fv_coef3_kernel(const T *__restrict__ f, T *__restrict__ C, FvTables<T> tb, FvTables3<T> t3,
@@ -764,12 +854,19 @@ fv_coef3_kernel(const T *__restrict__ f, T *__restrict__ C, FvTables<T> tb, FvTa
     const int k = (blockIdx.y * kFvThreads + threadIdx.x) * VEC;
     if (k >= nv) return;
     const Vec<T, VEC> fi = ldv<T, VEC>(f + i * nv + k);
+    const int ncf = __ldg(ncen + i);
+    if constexpr (sizeof(T) == 4 && VEC == 4 && MAXS == 3) {
+        if (ncf & kFvRegularTri) {      // uniform over the block: one cell per block
+            coef3_tri_x2(f, C, tb, t3, cen, i, k, nv, make_float4(fi.v[0], fi.v[1], fi.v[2], fi.v[3]));
+            return;
+        }
+    }
     T c[kFvCoef3][VEC];
 #pragma unroll
     for (int l = 0; l < kFvCoef3; ++l)
 #pragma unroll
         for (int u = 0; u < VEC; ++u) c[l][u] = (T)0;
-    const int nc = __ldg(ncen + i);
+    const int nc = ncf & (kFvRegularTri - 1);
     const T *Rc = t3.Rc + i * kFvCoef3 * kFvCentral3;
 #pragma unroll
     for (int q = 0; q < kFvCentral3; ++q) {
@@ -911,19 +1008,45 @@ fv_flux3_kernel(const T *__restrict__ f, const T *__restrict__ C, T *__restrict_
                 pi[l] = __ldg(t3.phi_i + (s * 2 + g) * kFvCoef3 + l);
                 pj[l] = jn >= 0 ? __ldg(t3.phi_j + (s * 2 + g) * kFvCoef3 + l) : (T)0;
             }
+            if constexpr (sizeof(T) == 4 && VEC == 4) {
+                // the same Gauss-point flux on pairs of velocities in FP32x2
+                const float2 v1nx = dup2(v1 * nx), qf = dup2(0.25f);
 #pragma unroll
-            for (int u = 0; u < VEC; ++u) {
-                T fl = fi.v[u];
+                for (int h = 0; h < 2; ++h) {
+                    const int u = 2 * h;
+                    float2 fl = make_float2(fi.v[u], fi.v[u + 1]);
 #pragma unroll
-                for (int l = 0; l < kFvCoef3; ++l) fl += ci[l].v[u] * pi[l];
-                T fr = fl;
-                if (jn >= 0) {
-                    fr = fj.v[u];
+                    for (int l = 0; l < kFvCoef3; ++l) fl = fma2(make_float2(ci[l].v[u], ci[l].v[u + 1]), dup2(pi[l]), fl);
+                    float2 fr = fl;
+                    if (jn >= 0) {
+                        fr = make_float2(fj.v[u], fj.v[u + 1]);
 #pragma unroll
-                    for (int l = 0; l < kFvCoef3; ++l) fr += cj[l].v[u] * pj[l];
+                        for (int l = 0; l < kFvCoef3; ++l)
+                            fr = fma2(make_float2(cj[l].v[u], cj[l].v[u + 1]), dup2(pj[l]), fr);
+                    }
+                    const float2 vn = fma2(make_float2(v2[u], v2[u + 1]), dup2(ny), v1nx);
+                    const float2 hv = mul2(qf, vn), nah = make_float2(-fabsf(hv.x), -fabsf(hv.y));
+                    float2 a = make_float2(acc[u], acc[u + 1]);
+                    a = fma2(hv, add2(fl, fr), a);
+                    a = fma2(nah, add2(fr, neg2(fl)), a);
+                    acc[u] = a.x;
+                    acc[u + 1] = a.y;
                 }
-                const T vn = v1 * nx + v2[u] * ny;
-                acc[u] += (T)0.25 * (vn * (fl + fr) - fabs(vn) * (fr - fl));
+            } else {
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) {
+                    T fl = fi.v[u];
+#pragma unroll
+                    for (int l = 0; l < kFvCoef3; ++l) fl += ci[l].v[u] * pi[l];
+                    T fr = fl;
+                    if (jn >= 0) {
+                        fr = fj.v[u];
+#pragma unroll
+                        for (int l = 0; l < kFvCoef3; ++l) fr += cj[l].v[u] * pj[l];
+                    }
+                    const T vn = v1 * nx + v2[u] * ny;
+                    acc[u] += (T)0.25 * (vn * (fl + fr) - fabs(vn) * (fr - fl));
+                }
             }
         }
     }
