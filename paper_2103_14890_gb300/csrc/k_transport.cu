@@ -29,8 +29,6 @@
 // neighbour (f_L on a boundary face: transmissive), Rusanov flux of v f:
 // |e| F = (v.|e|n)(f_L + f_R)/2 - |v.|e|n| (f_R - f_L)/2, summed and scaled
 // by 1/|P_i|.  The face midpoint rule is exact for degree-1 reconstructions.
-#include <stdlib.h>
-
 #include <algorithm>
 #include <atomic>
 

@@ -144,9 +144,12 @@ def test_transport_fp64_matches_oracle(bz, fvo, order, mesh_kind, N, jump):
 
 
 @pytest.mark.parametrize("order", [1, 2])
-@pytest.mark.parametrize("jump", [False, True])
-def test_transport_fp32_within_bound(bz, fvo, order, jump):
-    N, Lv = 16, 8.0
+@pytest.mark.parametrize("jump,N", [(False, 16), (True, 16), (False, 48)])
+def test_transport_fp32_within_bound(bz, fvo, order, jump, N):
+    """Triangles in FP32: at N = 16 (order 2) the persistent face-value passes
+    with one block per cell (fewer cells than blocks of the grid); at N = 48
+    the 2304 velocities span three velocity blocks per cell."""
+    Lv = 8.0
     pts, cells = _tri(14)
     om = fvo.Mesh(pts, cells)
     f = workloads.mesh_states(om.bary, N, Lv, jump=jump)
