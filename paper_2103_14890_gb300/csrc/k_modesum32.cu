@@ -776,70 +776,50 @@ __global__ void __launch_bounds__(WARPS * 32, WARPS <= 4 ? 3 : WARPS <= 8 ? 2 : 
 // error), and every error and the cross terms with the low part of b
 // accumulate in a second FP32 sum.  This is the compensated dot product
 // ("Dot2") of Ogita, Rump and Oishi (2005), accurate as if computed in twice
-// the working precision; the operations are pinned with __fmul_rn / __fadd_rn
+// the working precision; the operations are pinned with the _rn intrinsics
 // so the compiler cannot fuse them into FMAs that would break the exact splits.
+// The real and imaginary parts run as the two lanes of FP32x2 instructions:
+// every lane performs exactly the scalar operations in the scalar order
+// (the products (-y) x of the imaginary part are formed as y (-x), the same
+// value), so the result is that of the scalar form bit for bit.
 struct X2Acc {
-    float sx, sy;     // running sums of the high parts (real, imaginary)
-    float cx, cy;     // accumulated errors and low-order terms
+    float2 s;         // running sums of the high parts (real, imaginary)
+    float2 c;         // accumulated errors and low-order terms
 };
 
-__device__ __forceinline__ void x2_two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
+__device__ __forceinline__ float2 x2_neg(float2 a) { return make_float2(-a.x, -a.y); }
 
 // acc += w a b with w = wh + wl (real), a = ah + al (conjugated for DIR < 0),
-// b = bh + bl.
+// b = bh + bl; bs, ls are bh and bl with their lanes exchanged.
 template <int DIR>
 __device__ __forceinline__ void x2_term(X2Acc &acc, float wh, float wl, float2 ah, float2 al, float2 bh,
-                                        float2 bl) {
+                                        float2 bl, float2 bs, float2 ls) {
     // X = w a: high parts exact products, errors plus the low-part terms
-    const float xx = __fmul_rn(wh, ah.x);
-    float ex = fmaf(wh, ah.x, -xx);
-    ex = fmaf(wl, ah.x, ex);
-    ex = fmaf(wh, al.x, ex);
-    const float xy = __fmul_rn(wh, ah.y);
-    float ey = fmaf(wh, ah.y, -xy);
-    ey = fmaf(wl, ah.y, ey);
-    ey = fmaf(wh, al.y, ey);
+    const float2 W = make_float2(wh, wh);
+    const float2 X = __fmul2_rn(W, ah);
+    float2 E = __ffma2_rn(W, ah, x2_neg(X));
+    E = __ffma2_rn(make_float2(wl, wl), ah, E);
+    E = __ffma2_rn(W, al, E);
     // with xi the imaginary part of X after the optional conjugation, yn = -xi:
-    // re(X b) = xx bx + yn by, im(X b) = xx by - yn bx
-    const float yn = DIR > 0 ? -xy : xy;
-    const float en = DIR > 0 ? -ey : ey;
-    float p, q, s, d, c;
-    // real part
-    p = __fmul_rn(xx, bh.x);
-    q = fmaf(xx, bh.x, -p);
-    x2_two_sum(acc.sx, p, s, d);
-    acc.sx = s;
-    c = __fadd_rn(q, d);
-    p = __fmul_rn(yn, bh.y);
-    q = fmaf(yn, bh.y, -p);
-    x2_two_sum(acc.sx, p, s, d);
-    acc.sx = s;
-    c = __fadd_rn(c, __fadd_rn(q, d));
-    acc.cx = __fadd_rn(acc.cx, c);
-    acc.cx = fmaf(ex, bh.x, acc.cx);
-    acc.cx = fmaf(en, bh.y, acc.cx);
-    acc.cx = fmaf(xx, bl.x, acc.cx);
-    acc.cx = fmaf(yn, bl.y, acc.cx);
-    // imaginary part
-    p = __fmul_rn(xx, bh.y);
-    q = fmaf(xx, bh.y, -p);
-    x2_two_sum(acc.sy, p, s, d);
-    acc.sy = s;
-    c = __fadd_rn(q, d);
-    p = __fmul_rn(-yn, bh.x);
-    q = fmaf(-yn, bh.x, -p);
-    x2_two_sum(acc.sy, p, s, d);
-    acc.sy = s;
-    c = __fadd_rn(c, __fadd_rn(q, d));
-    acc.cy = __fadd_rn(acc.cy, c);
-    acc.cy = fmaf(ex, bh.y, acc.cy);
-    acc.cy = fmaf(-en, bh.x, acc.cy);
-    acc.cy = fmaf(xx, bl.y, acc.cy);
-    acc.cy = fmaf(-yn, bl.x, acc.cy);
+    // X b = xx (bx, by) + (yn by, -yn bx)
+    const float yn = DIR > 0 ? -X.y : X.y, en = DIR > 0 ? -E.y : E.y;
+    const float2 XX = make_float2(X.x, X.x), YN = make_float2(yn, -yn);
+    float2 sm, d;
+    const float2 P = __fmul2_rn(XX, bh);
+    const float2 qp = __ffma2_rn(XX, bh, x2_neg(P));
+    two_sum2(acc.s, P, sm, d);
+    acc.s = sm;
+    float2 c = __fadd2_rn(qp, d);
+    const float2 Q = __fmul2_rn(YN, bs);
+    const float2 qq = __ffma2_rn(YN, bs, x2_neg(Q));
+    two_sum2(acc.s, Q, sm, d);
+    acc.s = sm;
+    c = __fadd2_rn(c, __fadd2_rn(qq, d));
+    acc.c = __fadd2_rn(acc.c, c);
+    acc.c = __ffma2_rn(make_float2(E.x, E.x), bh, acc.c);
+    acc.c = __ffma2_rn(make_float2(en, -en), bs, acc.c);
+    acc.c = __ffma2_rn(XX, bl, acc.c);
+    acc.c = __ffma2_rn(YN, ls, acc.c);
 }
 
 // RR consecutive FP32 weights (RR = 4: 16-byte aligned, RR = 2: 8-byte aligned).
@@ -887,7 +867,8 @@ __device__ __forceinline__ void block_pass_x2_rt(float2 (&wh)[2 * RR], float2 (&
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
             const int q = (r - s + RR - 1 + PH * RR) & (2 * RR - 1);
-            x2_term<1>(acc[r], whi[r], wlo[r], ah, al, wh[q], wl[q]);
+            x2_term<1>(acc[r], whi[r], wlo[r], ah, al, wh[q], wl[q], make_float2(wh[q].y, wh[q].x),
+                       make_float2(wl[q].y, wl[q].x));
         }
     }
 }
@@ -968,7 +949,7 @@ modesum_x2_kernel(const double2 *__restrict__ fhat, float2 *__restrict__ Qhat, c
         const float *wsrc = W + 2 * (size_t)tk.woff;
         X2Acc acc[RR];
 #pragma unroll
-        for (int r = 0; r < RR; ++r) acc[r] = X2Acc{0.f, 0.f, 0.f, 0.f};
+        for (int r = 0; r < RR; ++r) acc[r] = X2Acc{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         const int k20 = tk.k20 + grp * RR;
         const int mbase0 = k20 - tk.l2lo - (RR - 1);
         stage_row(wbuf0, wsrc, rowb, lane);
@@ -993,7 +974,7 @@ modesum_x2_kernel(const double2 *__restrict__ fhat, float2 *__restrict__ Qhat, c
             for (int r = 0; r < RR; ++r) {
                 const int k2 = k20 + r;
                 if (grp * RR + r >= tk.rfirst && k2 <= h)
-                    out[(k2 + h) * 32] = make_float2(__fadd_rn(acc[r].sx, acc[r].cx), __fadd_rn(acc[r].sy, acc[r].cy));
+                    out[(k2 + h) * 32] = __fadd2_rn(acc[r].s, acc[r].c);
             }
         }
     }

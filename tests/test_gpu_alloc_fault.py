@@ -64,8 +64,11 @@ def test_handles(bz):
     time that grid is tuned in the process), build_fast_modes: each failing
     attempt frees its partial tables; the handle of the clean run computes what
     a handle built without injection computes."""
+    import gc
     import torch
     bz.check()                                       # the error word exists from here on
+    gc.collect()                                     # handles that earlier tests dropped are freed first
+    _idle()
     live0 = bz.alloc_stats()[0]
     ng, g = _sweep(bz, lambda: bz.Grid(2, 28, 10.0))
     assert ng == 2                                   # the FP64 and FP32 DFT tables
@@ -83,7 +86,6 @@ def test_handles(bz):
         assert torch.equal(a, b)
     print("allocations: grid %d, modes %d, fast modes %d" % (ng, nm, nf))
     del m, fm, g, g24
-    import gc
     gc.collect()
     _idle()
     assert bz.alloc_stats()[0] == live0
