@@ -8,11 +8,15 @@
 // warp-uniform load shared by 4 velocities and every f access is a 16-byte
 // vector of one coalesced row segment (neighbour rows come from L2: a 32^2
 // grid of 20k cells holds 81 MB in FP32).  Cells are taken along a Morton
-// curve of their barycentres (the mesh's order table).
+// curve of their barycentres (the mesh's order table).  On FP32 triangle
+// meshes without walls both passes of degree 1 are persistent: a block walks
+// the order in steps of the grid, staging the next cell's rows in shared
+// memory while it computes the current one.
 //
 // Pass 1 (order 2): gradient of the CWENO polynomial per (cell, velocity),
 // stored as G [cell][2][nv] (FP32 triangle meshes without walls: the values at
-// the three face midpoints, FV [cell][3][nv]).  The central (least-squares) gradient g_opt and
+// the three face midpoints, FV [cell][3][nv]).  The central (least-squares)
+// gradient g_opt and
 // the sector gradients g_L are linear in the averages (tables R_c, R_s of
 // fv_mesh.cpp); the central polynomial's gradient is g_0 = (g_opt - sum_L
 // lambda_L g_L) / lambda_0 (eq. CWENO:P0, lambda_0 = 3/4, lambda_L = 1/4 /
