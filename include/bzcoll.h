@@ -353,8 +353,9 @@ int fv_mesh_set_walls(bz_mesh *mesh, int64_t n_edges, const int64_t *edge_vertic
  *               BZ_FP64, float for BZ_FP32; must not overlap
  * Boundary faces are transmissive (the outer state equals the inner one)
  * unless fv_mesh_set_walls made them walls.
- * Scratch (order 2: 2 n_cells N^2 values, order 3: 5 n_cells N^2) comes from
- * the stream-ordered pool.
+ * Scratch (order 2: 2 n_cells N^2 values, 3 n_cells N^2 in FP32 on triangle
+ * meshes without walls; order 3: 5 n_cells N^2) comes from the
+ * stream-ordered pool.
  * Errors: BZ_EINVAL, BZ_ENOTSUP (3-D grid; walls with N not divisible by 4 or
  * N^2 > 1024), BZ_ECUDA. */
 int transport_residual(const bz_mesh *mesh, const bz_grid *g, int precision, const void *f, void *L,
