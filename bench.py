@@ -434,7 +434,8 @@ def _transport_measure(bz, workloads, st, check=True):
     ms3, k3 = timed_residual(bz.Mesh(pts, tri, order=3), f, Lr, 10)
     out["fp32_order3"] = {"ms_per_call": ms3, "kernel_ms": k3,
                           "cell_velocity_updates_per_s": f.numel() / (ms3 / 1e3),
-                          "note": "5 coefficients per (cell, velocity) written and read back; one velocity per thread"}
+                          "note": "5 coefficients per (cell, velocity) written and read back; 4 velocities per thread "
+                                  "(FP32x2 on triangle meshes)"}
     # a periodic Voronoi mesh (the polygonal cells of the vortex study), orders 2 and 3
     vp, vc = workloads.periodic_voronoi(2603)
     vbary = np.array([np.asarray(vp)[c].mean(axis=0) for c in vc])
